@@ -1,0 +1,322 @@
+"""Benchmark of the mesh-vs-mesh intersection search on GB300.
+
+One step = one full search (every broad- and narrow-phase stage, merged and
+sorted output, hit count read back) of the 4096 x 512 vs 4096 x 512 vertex
+meshes (4,186,112 triangles each, 256 planted hits, 1e4 planted near-misses),
+with the inputs resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tms|reference]
+
+For N > 1 (launched by torch.distributed.run) every rank searches its own
+replica of the workload: the searches are independent units (weak scaling).
+The reference arm times the CPU oracle (test infrastructure, exact pruning by a
+bounding-volume hierarchy, OpenMP) on the host cores for the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import torch  # noqa: E402
+
+METRIC = "ms per full manifold-mesh search (4M×4M tris), HBM GB/s & FP64 util vs peak"
+UNIT = "ms/search"
+WORKLOAD = dict(workload="mesh-vs-mesh search, 4096x512 vs 4096x512 vertex grids "
+                         "(4,186,112 triangles per mesh), lambda=4 stretch, 3 folds, "
+                         "256 planted hits + 1e4 planted near-misses (1e-9..1e-3)",
+                N=4096, M=512, triangles_per_mesh=4186112)
+ENTRY_BYTES = 8 + 4 + 4 + 8 + 32      # key, index, face id, cell coords, FP32 box
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_workload(device):
+    import synth
+    pair = synth.config3()
+    return pair
+
+
+def fp64_peak(device) -> float:
+    """FP64 FMA throughput of this GPU (TFLOP/s), from a dependent-chain kernel
+    with enough independent chains to fill every SM (torch-free: libtms)."""
+    import paper_2109_14814_gb300 as tms
+    return tms.probe_fp64_tflops()
+
+
+def run_tms(args, ws, rank, local):
+    import paper_2109_14814_gb300 as tms
+
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    peaks, peaks_kind = measured_peaks()
+    pair = build_workload(device)
+    XA = pair.A.X.to(device).contiguous()
+    XB = pair.B.X.to(device).contiguous()
+    A = tms.Mesh(XA, pair.A.s, True)
+    B = tms.Mesh(XB, pair.B.s, True)
+    stream = torch.cuda.Stream(device)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device)
+    out = torch.empty((1 << 17, tms.HIT_BYTES), dtype=torch.uint8, device=device)
+    kw = dict(timing=1)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            h = tms.search(A, B, out=out, stream=stream, **kw)
+        n_hits = len(h)
+        stats = tms.last_stats(stream)
+
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_sum = {}
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(i & 0xFF)          # L2 flush, outside the step's events
+                starts[i].record(stream)
+                h = tms.search(A, B, out=out, stream=stream, **kw)
+                ends[i].record(stream)
+                for k, v in tms.last_stage_ms(stream).items():
+                    stage_sum[k] = stage_sum.get(k, 0.0) + v
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    searches = args.steps * ws
+    value = total_ms / searches                       # aggregate ms per search
+    ms_per_step = total_ms / args.steps
+    stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
+
+    # roofline of the dominant kernel
+    V = pair.A.N * pair.A.M
+    ent = stats["entries"]
+    face_bytes = {"face_bounds": 32 * 2 * V, "face_mark_A": 32 * V,
+                  "face_probe_B": 32 * V + ENTRY_BYTES * ent / 2,
+                  "face_probe_A": 32 * V + ENTRY_BYTES * ent / 2}
+    face_ms = sum(stage_ms.get(k, 0.0) for k in face_bytes)
+    dominant = max(stage_ms, key=stage_ms.get)
+    face_gbs = (sum(face_bytes.values()) / 1e9) / (face_ms / 1e3) if face_ms > 0 else None
+    roofline = {"kernel": "tms::k_face_pass (4 launches/search: bounds, mark A, probe B, probe A)",
+                "bound": "hbm", "achieved": face_gbs, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": (face_gbs / peaks["hbm_gbs"]) if face_gbs else None,
+                "traffic": None, "peak_kind": f"{peaks_kind} copy bandwidth",
+                "algorithmic_bytes_per_search": sum(face_bytes.values()),
+                "share_of_step": face_ms / ms_per_step if ms_per_step else None,
+                "dominant_stage": dominant}
+    # FP64 utilisation of the narrow phase
+    fp64 = None
+    try:
+        peak64 = tms.probe_fp64_tflops()
+        flops = 110.0 * stats["fp64_solves"]
+        t_narrow = stage_ms.get("narrow", 0.0)
+        ach = flops / (t_narrow / 1e3) / 1e12 if t_narrow > 0 else None
+        fp64 = {"kernel": "tms::k_narrow", "solves_fp64": stats["fp64_solves"],
+                "candidates": stats["candidates"], "flops_per_solve": 110,
+                "achieved_tflops": ach, "peak_tflops": peak64,
+                "frac": (ach / peak64) if (ach and peak64) else None,
+                "peak_kind": "measured FP64 FMA-chain probe on this GPU"}
+    except Exception as e:  # the probe is optional diagnostics
+        fp64 = {"error": str(e)}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hA = pair.A.X.contiguous().pin_memory()
+        hB = pair.B.X.contiguous().pin_memory()
+        hout = torch.empty((1 << 17, tms.HIT_BYTES), dtype=torch.uint8).pin_memory()
+        e_times = []
+        d2h = 0
+        with torch.cuda.stream(stream):
+            for i in range(max(3, args.steps // 2) + 2):
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                XA.copy_(hA, non_blocking=True)
+                XB.copy_(hB, non_blocking=True)
+                h = tms.search(A, B, out=out, stream=stream)
+                n = len(h)
+                hout[:n].copy_(h.raw, non_blocking=True)
+                ev1.record(stream)
+                stream.synchronize()
+                if i >= 2:
+                    e_times.append(ev0.elapsed_time(ev1))
+                d2h = n * tms.HIT_BYTES + 8
+        e_ms = sum(e_times) / len(e_times)
+        e2e = {"value": e_ms / 1.0, "unit": UNIT,
+               "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(pair)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded manifold-like meshes)",
+        "config": dict(WORKLOAD, precision="FP32 outward boxes + FP64 narrow phase",
+                       l2="256 MiB buffer written between steps, outside the step events",
+                       parallelism=f"replicas x{ws}" if ws > 1 else "1 GPU",
+                       hits=n_hits, candidates=stats["candidates"], entries=stats["entries"]),
+        "roofline": roofline, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
+        "clocks": clk.summary(), "gpu_launches": stats["kernels"] * args.steps,
+        "stage_ms": stage_ms, "wall_s": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(pair):
+    import oracle
+    OA, OB = oracle.OMesh.from_grid(pair.A), oracle.OMesh.from_grid(pair.B)
+    t0 = time.perf_counter()
+    r = oracle.search(OA, OB)
+    dt = time.perf_counter() - t0
+    return {"value": dt * 1e3, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "the full workload (one complete search): FP64 C oracle, exact box "
+                      "pruning by a bounding-volume hierarchy, OpenMP over A triangles",
+            "hits": int(r.size)}
+
+
+def run_reference(args, ws, rank, local):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    pair = build_workload("cpu")
+    OA, OB = oracle.OMesh.from_grid(pair.A), oracle.OMesh.from_grid(pair.B)
+    for _ in range(args.warmup):
+        oracle.search(OA, OB)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.search(OA, OB)
+        times.append((time.perf_counter() - t0) * 1e3)
+    v = sum(times) / len(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded manifold-like meshes)", "config": dict(WORKLOAD),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "the full workload per step (one complete search)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="tms", choices=["tms", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank, local)
+        return
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    try:
+        run_tms(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,245 @@
+/*
+ * tms.h -- C ABI of the GB300 (sm_103a) mesh-vs-mesh intersection search.
+ *
+ * The library finds every intersecting pair of triangles between two
+ * triangulated 2D surfaces in R^4 -- a torus's unstable-manifold mesh W^u and
+ * another torus's stable-manifold mesh W^s -- following arXiv 2109.14814,
+ * Sec. 5 ("Rapid GPU-Assisted Search for Manifold Intersections"): a broad
+ * phase (uniform grid over a trimmed world box, per-face axis-aligned bounding
+ * boxes, optional Moller quick test) followed by a narrow phase that solves the
+ * 4x4 linear system of Eq. (precise) for the barycentric pair (a, b, c, d).
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer marked "device" must point to memory of the CUDA device that
+ *     is current on the calling thread.  The caller owns all input and output
+ *     buffers; the library owns only the scratch it allocates internally, which
+ *     is cached per stream and released by tms_release_workspace() or
+ *     tms_destroy_mesh().
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All work
+ *     is ordered on that stream.
+ *   - Entry points return a tms_status; no C++ exception crosses the ABI.
+ *     On an error other than TMS_ERR_CAPACITY the outputs are unspecified.
+ *   - The library never falls back to a CPU implementation.
+ *
+ * Mesh layout (Sec. 5.1 and Sec. 5.3): four coordinate arrays x, y, px, py,
+ * each holding N*M float64 values column-major with theta fastest:
+ * coordinate of vertex W(theta_i, s_k) at [k*N + i], theta_i = 2*pi*i/N.
+ * Quads Q_ik join (i, k), (i+1, k), (i, k+1), (i+1, k+1) with i+1 taken modulo
+ * N on a periodic mesh (Sec. 5.1: the theta index wraps around).
+ * Each quad is split into two triangles along the (i+1, k)-(i, k+1) diagonal
+ * with the vertex orderings of Sec. 5.2.4:
+ *   T1: x1 = W(i+1, k), x2 = W(i, k),     x3 = W(i, k+1)
+ *   T2: x1 = W(i, k+1), x2 = W(i+1, k+1), x3 = W(i+1, k)
+ * Within a mesh view of vertex columns [k0, k1), quad (i, k) (k relative to
+ * k0) has id q = k*N + i and its triangles have ids t = 2*q (T1), 2*q + 1 (T2).
+ * A quad hit is derivable from a triangle hit as q = t >> 1 (Sec. 5.2: a quad
+ * pair intersects iff one of its four triangle pairs does).
+ */
+#ifndef TMS_H
+#define TMS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int tms_status;
+enum {
+    TMS_OK = 0,
+    TMS_ERR_ARG = 1,       /* bad size, range, pointer, or non-finite vertex */
+    TMS_ERR_CAPACITY = 2,  /* output buffer too small; required count reported */
+    TMS_ERR_TIMEOUT = 3,   /* a bounded device-side wait ran out */
+    TMS_ERR_CUDA = 4,      /* a CUDA runtime call failed */
+    TMS_ERR_STATE = 5      /* call sequence error (e.g. destroyed handle) */
+};
+
+/* Opaque mesh view.  Borrows the caller's device coordinate arrays (it never
+ * copies or frees them); owns a device copy of s_k and small metadata. */
+typedef struct tms_mesh_s *tms_mesh;
+
+/*
+ * tms_build_mesh -- describe one manifold half-layer mesh.  A half-layer is a
+ * contiguous range of s columns of the full vertex arrays (Sec. 5.2), so the
+ * view is zero-copy.
+ *   dX, dY, dPx, dPy : device, N*M float64 each, layout above.  Borrowed: they
+ *                      must stay valid and unchanged while the handle is used.
+ *   N                : theta samples, N >= 3 (periodic) or N >= 2 (open strip).
+ *   M                : s samples in the full arrays.
+ *   k0, k1           : vertex columns [k0, k1) form the view; 0 <= k0,
+ *                      k1 <= M, k1 - k0 >= 2.
+ *   s                : host or device, M strictly increasing float64 values s_k
+ *                      (copied; used for the (theta, s) estimates).
+ *   periodic_theta   : 1 = the paper's mesh (quads i = 0..N-1, i+1 mod N);
+ *                      0 = open strip (quads i = 0..N-2).
+ *   stream           : stream used for the s_k copy.
+ *   out              : receives the handle.
+ * Errors: TMS_ERR_ARG for any size/range violation, NULL pointer, or s not
+ * strictly increasing; TMS_ERR_CUDA on a failed allocation/copy.
+ * Non-finite vertex coordinates are reported by the search (TMS_ERR_ARG).
+ */
+tms_status tms_build_mesh(const double *dX, const double *dY, const double *dPx,
+                          const double *dPy, int N, int M, int k0, int k1,
+                          const double *s, int periodic_theta, void *stream,
+                          tms_mesh *out);
+
+/* Releases the handle and any cached search plan that refers to it.
+ * Synchronises the device first. */
+tms_status tms_destroy_mesh(tms_mesh mesh);
+
+/* Search parameters.  Fill with tms_params_default() and override fields. */
+typedef struct {
+    int precision;        /* broad-phase arithmetic: 0 = FP64 boxes and cell keys
+                             (plain); 1 = FP32 boxes rounded outward and FP32 cell
+                             keys (mixed, default).  The narrow phase is FP64. */
+    int face_level;       /* 0 = one box per triangle (default); 1 = one box per
+                             quad, as the paper's kernel (4 triangle pairs per
+                             candidate). */
+    int moller;           /* 1 = apply the Moller quick test of Sec. 5.2.3 (FP64,
+                             with a rounding guard) to candidates; default 0. */
+    int cell_filter;      /* 1 = register only faces in grid cells occupied by
+                             both meshes before the sort (default); 0 = emit
+                             every face-cell incidence (the paper's per-box lists). */
+    int narrow_filter;    /* 1 = reject candidates with an FP32 solve whose
+                             forward-error bound certifies margin < -2 tau
+                             (default); undecided candidates get the FP64 solve. */
+    float cell_mult;      /* grid cell edge = cell_mult x widest face extent per
+                             coordinate (Sec. 5.2.1 requires > 1 x); default 1.0625 */
+    double tau;           /* margin tolerance of the hit test, default 1e-12 */
+    long long entry_capacity;  /* initial scratch sizes (0 = automatic); grown on */
+    long long cand_capacity;   /* overflow and retried inside the call          */
+    long long hit_capacity;    /* raw hits before merging (0 = automatic)       */
+    int use_graph;        /* 1 = capture the launch sequence in a CUDA graph on
+                             first use and replay it (default 1) */
+    unsigned inject;      /* fault injection for tests (host side):
+                             bit0 = force entry capacity 1 (exercises retry),
+                             bit1 = force a capacity error to be returned,
+                             bit2 = report TMS_ERR_TIMEOUT from the status word */
+    int block_faces;      /* face-pass tile width in quads (64/128/256; 0 = 128) */
+    int tile_rows;        /* face-pass tile height in quad rows (4 or 8; 0 = 8) */
+    int timing;           /* 1 = record CUDA events between stages (in the graph) so
+                             that tms_last_stage_ms() reports per-stage device time */
+} tms_params;
+
+void tms_params_default(tms_params *p);
+
+/* One hit: an intersecting triangle pair (Sec. 5.2.4) and its estimates. */
+typedef struct {
+    uint32_t triA, triB;   /* triangle ids in mesh A and mesh B */
+    uint32_t pair;         /* mesh-pair index (0 for tms_search) */
+    uint32_t flags;        /* bit0: near-degenerate band (rho < 1e-12 or
+                              |margin| < 1e-12); bit1: the point lies on a shared
+                              edge or vertex (this record is the representative) */
+    double a, b, c, d;     /* solution of Eq. (precise) */
+    double P[4];           /* x-side point x2 + a(x1-x2) + b(x3-x2) */
+    double theta_u, s_u;   /* estimates on mesh A, Sec. 5.2.4 (theta in [0, 2pi)) */
+    double theta_s, s_s;   /* estimates on mesh B */
+    double rho;            /* |det| / product of the column norms */
+    double margin;         /* min(a, b, c, d, 1-a-b, 1-c-d) */
+} tms_hit;
+
+/*
+ * tms_search -- all intersecting triangle pairs of mesh A against mesh B.
+ *   params   : may be NULL (defaults).
+ *   dHits    : device, room for hitCap records (may be NULL when hitCap is 0).
+ *   hitCap   : capacity of dHits in records.
+ *   nHits    : host out; the number of hits.  On TMS_ERR_CAPACITY it holds the
+ *              required count and dHits holds the first hitCap records.
+ * Output order: sorted by (triA, triB); hits on shared edges/vertices merged
+ * (one record per feature pair, the smallest (triA, triB)).  Deterministic.
+ * Synchronises `stream` before returning (to read the count).
+ */
+tms_status tms_search(tms_mesh A, tms_mesh B, const tms_params *params,
+                      tms_hit *dHits, long long hitCap, long long *nHits,
+                      void *stream);
+
+/*
+ * tms_search_batched -- nPairs independent searches (A[p], B[p]) of uneven
+ * sizes in one launch sequence: every stage is one persistent launch over all
+ * pairs' work, and the sequence is captured once into a CUDA graph and replayed
+ * while the handles, params and output pointers are unchanged.
+ *   dHits    : device, hitCap records; hits of all pairs, sorted by
+ *              (pair, triA, triB).
+ *   dOffsets : device, nPairs+1 int64; hits of pair p are
+ *              dHits[dOffsets[p] .. dOffsets[p+1]).
+ *   nHits    : host out, total count (required count on TMS_ERR_CAPACITY).
+ */
+tms_status tms_search_batched(const tms_mesh *A, const tms_mesh *B, int nPairs,
+                              const tms_params *params, tms_hit *dHits,
+                              long long hitCap, long long *dOffsets,
+                              long long *nHits, void *stream);
+
+/*
+ * tms_backward -- reverse-mode derivative of hit outputs with respect to the
+ * mesh vertices and a family parameter alpha, by implicit differentiation of
+ * A z = r (Eq. (precise)): with zbar = gZ + (dP/dz)^T gP and w = A^{-T} zbar,
+ * the vertex gradients are x_i: beta_i (gP - w), y_i: gamma_i w with barycentric
+ * weights beta = (a, 1-a-b, b), gamma = (c, 1-c-d, d) on (x1, x2, x3), (y1, y2, y3).
+ *   dHits            : device, nHits records from tms_search (triA, triB used).
+ *   dGradP, dGradZ   : device, nHits*4 float64 upstream gradients on P and
+ *                      (a, b, c, d); either may be NULL (= zeros).
+ *   dGradA, dGradB   : device, 4*N*M float64 each (layout of the mesh arrays,
+ *                      full M); ACCUMULATED into (atomic adds); may be NULL.
+ *   dDvDalphaA/B     : device, 4*N*M float64 d(vertex)/d(alpha), or NULL.
+ *   dGradAlpha       : device, nHits float64, written (not accumulated):
+ *                      per-hit sum over its six vertices of grad . dv/dalpha;
+ *                      may be NULL.
+ * Hits whose system is singular contribute nothing.
+ */
+tms_status tms_backward(tms_mesh A, tms_mesh B, const tms_hit *dHits, long long nHits,
+                        const double *dGradP, const double *dGradZ,
+                        double *dGradA, double *dGradB,
+                        const double *dDvDalphaA, const double *dDvDalphaB,
+                        double *dGradAlpha, void *stream);
+
+/* Per-stage statistics of the last search on `stream` (host copies). */
+typedef struct {
+    long long entries;      /* face-cell entries sorted */
+    long long cells;        /* occupied cells holding both meshes */
+    long long pair_slots;   /* sum over cells of nA*nB */
+    long long candidates;   /* candidate face pairs after box and owner tests */
+    long long fp64_solves;  /* triangle pairs sent to the FP64 solve */
+    long long raw_hits;     /* hits before merging */
+    long long hits;         /* output hits */
+    int grid_n[4];          /* cells per coordinate (pair 0) */
+    int empty;              /* trimmed world empty (pair 0) */
+    int retries;            /* capacity retries taken */
+    int kernels;            /* kernel launches in one search (graph replay) */
+    int pad;
+} tms_stats;
+
+tms_status tms_last_stats(void *stream, tms_stats *out);
+
+/* Per-stage device time (ms) of the last search on `stream` made with
+ * params.timing = 1, in this order:
+ *   0 counters/bounds init   1 face pass: world bounds   2 grid parameters
+ *   3 bitmap clear           4 face pass: mark A         5 face pass: probe B
+ *   6 face pass: probe A (or emit all)  7 sort entries   8 cell ranges
+ *   9 candidate emission     10 narrow phase             11 sort hits
+ *   12 merge + output        13 counter read-back
+ * Writes min(cap, 14) values; *n receives 14. */
+tms_status tms_last_stage_ms(void *stream, float *ms, int cap, int *n);
+
+/* Frees the scratch and cached plans created for `stream`; NULL frees those of
+ * every stream.  Synchronises the plans' work first. */
+tms_status tms_release_workspace(void *stream);
+
+/* Measures this GPU's FP64 fused-multiply-add throughput (TFLOP/s) with a
+ * short dependent-chain kernel on `stream`; the denominator of the narrow
+ * phase's FP64 utilisation.  Allocates a small buffer; synchronises. */
+tms_status tms_probe_fp64(double *tflops, void *stream);
+
+/* Message describing the last error returned on the calling thread. */
+const char *tms_last_error(void);
+
+/* Static string for a status code. */
+const char *tms_status_str(tms_status s);
+
+/* Library version string. */
+const char *tms_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMS_H */

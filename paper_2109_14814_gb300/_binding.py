@@ -1,0 +1,373 @@
+"""Thin Python binding of libtms.so (include/tms.h): argument marshalling only.
+
+PyTorch supplies device memory and the current stream; every step of the
+search runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library is not built, or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtms.so")
+HIT_BYTES = 128
+
+TMS_OK, TMS_ERR_ARG, TMS_ERR_CAPACITY, TMS_ERR_TIMEOUT, TMS_ERR_CUDA, TMS_ERR_STATE = range(6)
+
+_c = ctypes
+_lib = None
+
+
+class TmsError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)} ({last_error()})")
+
+
+class Params(ctypes.Structure):
+    """Mirror of tms_params."""
+    _fields_ = [
+        ("precision", _c.c_int),
+        ("face_level", _c.c_int),
+        ("moller", _c.c_int),
+        ("cell_filter", _c.c_int),
+        ("narrow_filter", _c.c_int),
+        ("cell_mult", _c.c_float),
+        ("tau", _c.c_double),
+        ("entry_capacity", _c.c_longlong),
+        ("cand_capacity", _c.c_longlong),
+        ("hit_capacity", _c.c_longlong),
+        ("use_graph", _c.c_int),
+        ("inject", _c.c_uint),
+        ("block_faces", _c.c_int),
+        ("tile_rows", _c.c_int),
+        ("timing", _c.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    """Mirror of tms_stats."""
+    _fields_ = [
+        ("entries", _c.c_longlong),
+        ("cells", _c.c_longlong),
+        ("pair_slots", _c.c_longlong),
+        ("candidates", _c.c_longlong),
+        ("fp64_solves", _c.c_longlong),
+        ("raw_hits", _c.c_longlong),
+        ("hits", _c.c_longlong),
+        ("grid_n", _c.c_int * 4),
+        ("empty", _c.c_int),
+        ("retries", _c.c_int),
+        ("kernels", _c.c_int),
+        ("pad", _c.c_int),
+    ]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "grid_n"}
+        d["grid_n"] = list(self.grid_n)
+        return d
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2109_14814_gb300.build` (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, LL, D = _c.c_void_p, _c.c_int, _c.c_longlong, _c.c_double
+    L.tms_params_default.argtypes = [_c.POINTER(Params)]
+    L.tms_params_default.restype = None
+    L.tms_build_mesh.argtypes = [P, P, P, P, I, I, I, I, P, I, P, _c.POINTER(P)]
+    L.tms_build_mesh.restype = I
+    L.tms_destroy_mesh.argtypes = [P]
+    L.tms_destroy_mesh.restype = I
+    L.tms_search.argtypes = [P, P, _c.POINTER(Params), P, LL, _c.POINTER(LL), P]
+    L.tms_search.restype = I
+    L.tms_search_batched.argtypes = [P, P, I, _c.POINTER(Params), P, LL, P, _c.POINTER(LL), P]
+    L.tms_search_batched.restype = I
+    L.tms_backward.argtypes = [P, P, P, LL, P, P, P, P, P, P, P, P]
+    L.tms_backward.restype = I
+    L.tms_last_stats.argtypes = [P, _c.POINTER(Stats)]
+    L.tms_last_stats.restype = I
+    L.tms_last_stage_ms.argtypes = [P, _c.POINTER(_c.c_float), I, _c.POINTER(I)]
+    L.tms_last_stage_ms.restype = I
+    L.tms_release_workspace.argtypes = [P]
+    L.tms_release_workspace.restype = I
+    L.tms_status_str.argtypes = [I]
+    L.tms_status_str.restype = _c.c_char_p
+    L.tms_version.argtypes = []
+    L.tms_version.restype = _c.c_char_p
+    L.tms_last_error.argtypes = []
+    L.tms_last_error.restype = _c.c_char_p
+    L.tms_probe_fp64.argtypes = [_c.POINTER(D), P]
+    L.tms_probe_fp64.restype = I
+    _lib = L
+    return L
+
+
+def probe_fp64_tflops(stream=None) -> float:
+    """tms_probe_fp64: measured FP64 FMA throughput of the current GPU."""
+    v = _c.c_double(0.0)
+    rc = lib().tms_probe_fp64(_c.byref(v), _stream(stream))
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_probe_fp64")
+    return float(v.value)
+
+
+def status_str(s: int) -> str:
+    return lib().tms_status_str(s).decode()
+
+
+def last_error() -> str:
+    return lib().tms_last_error().decode()
+
+
+def version() -> str:
+    return lib().tms_version().decode()
+
+
+def params(**kw) -> Params:
+    p = Params()
+    lib().tms_params_default(_c.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(f"unknown search parameter {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return t.data_ptr()
+
+
+class Mesh:
+    """A mesh view (tms_build_mesh): X is a CUDA float64 tensor (4, M, N),
+    coordinate c of vertex (theta_i, s_k) at X[c, k, i]; s holds the M s_k."""
+
+    def __init__(self, X: torch.Tensor, s, periodic: bool = True, k0: int = 0,
+                 k1: Optional[int] = None, stream=None):
+        if not (X.is_cuda and X.dtype == torch.float64 and X.dim() == 3 and X.shape[0] == 4):
+            raise ValueError("X must be a CUDA float64 tensor of shape (4, M, N)")
+        self.X = X.contiguous()
+        self.M, self.N = int(X.shape[1]), int(X.shape[2])
+        if isinstance(s, torch.Tensor):
+            s_t = s.detach().to(torch.float64).contiguous()
+        else:
+            s_t = torch.as_tensor(s, dtype=torch.float64).contiguous()
+        self.s = s_t
+        self.periodic = bool(periodic)
+        self.k0 = int(k0)
+        self.k1 = int(self.M if k1 is None else k1)
+        h = _c.c_void_p()
+        rc = lib().tms_build_mesh(self.X[0].data_ptr(), self.X[1].data_ptr(), self.X[2].data_ptr(),
+                                  self.X[3].data_ptr(), self.N, self.M, self.k0, self.k1,
+                                  self.s.data_ptr(), int(self.periodic), _stream(stream),
+                                  _c.byref(h))
+        if rc != TMS_OK:
+            raise TmsError(rc, "tms_build_mesh")
+        self.handle = h
+
+    @classmethod
+    def from_grid(cls, g, device="cuda", **kw):
+        """From a synth.MeshGrid."""
+        return cls(g.X.to(device).contiguous(), g.s.cpu(), g.periodic, **kw)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.tms_destroy_mesh(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Hits:
+    """Search output on the device (views of the raw tms_hit records)."""
+    raw: torch.Tensor          # (n, 128) uint8
+    offsets: Optional[torch.Tensor] = None
+
+    def __len__(self):
+        return int(self.raw.shape[0])
+
+    @property
+    def _i32(self):
+        return self.raw.view(torch.int32)
+
+    @property
+    def _f64(self):
+        return self.raw.view(torch.float64)
+
+    @property
+    def triA(self):
+        return self._i32[:, 0].to(torch.int64)
+
+    @property
+    def triB(self):
+        return self._i32[:, 1].to(torch.int64)
+
+    @property
+    def pair(self):
+        return self._i32[:, 2].to(torch.int64)
+
+    @property
+    def flags(self):
+        return self._i32[:, 3].to(torch.int64)
+
+    @property
+    def z(self):
+        return self._f64[:, 2:6]
+
+    @property
+    def P(self):
+        return self._f64[:, 6:10]
+
+    @property
+    def params(self):
+        return self._f64[:, 10:14]
+
+    @property
+    def rho(self):
+        return self._f64[:, 14]
+
+    @property
+    def margin(self):
+        return self._f64[:, 15]
+
+    def to_dict(self):
+        return dict(triA=self.triA, triB=self.triB, pair=self.pair, flags=self.flags, z=self.z,
+                    P=self.P, params=self.params, rho=self.rho, margin=self.margin)
+
+
+def _alloc_hits(cap: int, device) -> torch.Tensor:
+    return torch.empty((max(cap, 1), HIT_BYTES), dtype=torch.uint8, device=device)
+
+
+def search(A: Mesh, B: Mesh, hit_capacity: int = 1 << 16, stream=None, out=None, **kw) -> Hits:
+    """tms_search: all intersecting triangle pairs of A against B."""
+    p = params(**kw)
+    st = _stream(stream)
+    buf = out if out is not None else _alloc_hits(hit_capacity, A.X.device)
+    n = _c.c_longlong(0)
+    rc = lib().tms_search(A.handle, B.handle, _c.byref(p), buf.data_ptr(), buf.shape[0],
+                          _c.byref(n), st)
+    if rc == TMS_ERR_CAPACITY and out is None and n.value > buf.shape[0] and not (p.inject & 2):
+        buf = _alloc_hits(int(n.value), A.X.device)
+        rc = lib().tms_search(A.handle, B.handle, _c.byref(p), buf.data_ptr(), buf.shape[0],
+                              _c.byref(n), st)
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_search")
+    return Hits(buf[: n.value])
+
+
+def search_batched(As: Sequence[Mesh], Bs: Sequence[Mesh], hit_capacity: int = 1 << 18,
+                   stream=None, out=None, offsets=None, **kw) -> Hits:
+    """tms_search_batched: independent searches of many mesh pairs in one graph."""
+    if len(As) != len(Bs) or not As:
+        raise ValueError("As and Bs must be non-empty and of equal length")
+    p = params(**kw)
+    st = _stream(stream)
+    dev = As[0].X.device
+    ha = (_c.c_void_p * len(As))(*[m.handle.value for m in As])
+    hb = (_c.c_void_p * len(Bs))(*[m.handle.value for m in Bs])
+    buf = out if out is not None else _alloc_hits(hit_capacity, dev)
+    offs = offsets if offsets is not None else torch.empty(len(As) + 1, dtype=torch.int64, device=dev)
+    n = _c.c_longlong(0)
+    rc = lib().tms_search_batched(ha, hb, len(As), _c.byref(p), buf.data_ptr(), buf.shape[0],
+                                  offs.data_ptr(), _c.byref(n), st)
+    if rc == TMS_ERR_CAPACITY and out is None and n.value > buf.shape[0]:
+        buf = _alloc_hits(int(n.value), dev)
+        rc = lib().tms_search_batched(ha, hb, len(As), _c.byref(p), buf.data_ptr(), buf.shape[0],
+                                      offs.data_ptr(), _c.byref(n), st)
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_search_batched")
+    return Hits(buf[: n.value], offs)
+
+
+def backward(A: Mesh, B: Mesh, hits: Hits, gP=None, gZ=None, gradA=None, gradB=None,
+             dA_dalpha=None, dB_dalpha=None, galpha=None, stream=None):
+    """tms_backward: accumulates vertex gradients into gradA/gradB (4, M, N) and
+    writes per-hit alpha derivatives into galpha (n,)."""
+    n = len(hits)
+    for t in (gP, gZ):
+        if t is not None and (t.dtype != torch.float64 or not t.is_contiguous()):
+            raise ValueError("upstream gradients must be contiguous float64 (n, 4)")
+    rc = lib().tms_backward(A.handle, B.handle, hits.raw.data_ptr() if n else None, n,
+                            _dptr(gP), _dptr(gZ), _dptr(gradA), _dptr(gradB), _dptr(dA_dalpha),
+                            _dptr(dB_dalpha), _dptr(galpha), _stream(stream))
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_backward")
+
+
+def last_stats(stream=None) -> dict:
+    s = Stats()
+    rc = lib().tms_last_stats(_stream(stream), _c.byref(s))
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_last_stats")
+    return s.as_dict()
+
+
+STAGES = ["init", "face_bounds", "grid_params", "bitmap_clear", "face_mark_A", "face_probe_B",
+          "face_probe_A", "sort_entries", "cells", "emit", "narrow", "sort_hits", "merge_output",
+          "readback"]
+
+
+def last_stage_ms(stream=None) -> dict:
+    """Per-stage device time of the last search made with timing=1."""
+    buf = (_c.c_float * 32)()
+    n = _c.c_int(0)
+    rc = lib().tms_last_stage_ms(_stream(stream), buf, 32, _c.byref(n))
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_last_stage_ms")
+    return {STAGES[i]: float(buf[i]) for i in range(min(n.value, len(STAGES)))}
+
+
+def release_workspace(stream=None):
+    lib().tms_release_workspace(_stream(stream) if stream is not None else None)
+
+
+class HitPoint(torch.autograd.Function):
+    """(P, z) of each hit as differentiable functions of the mesh vertices.
+
+    forward(XA, XB, meshA, meshB, hits) returns the hit points P (n, 4) and
+    barycentric pairs z = (a, b, c, d) (n, 4) found by the search; backward
+    runs the library's FP64 adjoint (implicit differentiation of the 4x4 solve)
+    and returns vertex gradients shaped like XA and XB.  XA and XB must be the
+    tensors the meshes were built from.
+    """
+
+    @staticmethod
+    def forward(ctx, XA, XB, meshA, meshB, hits):
+        ctx.meshA, ctx.meshB, ctx.hits = meshA, meshB, hits
+        return hits.P.clone(), hits.z.clone()
+
+    @staticmethod
+    def backward(ctx, gP, gZ):
+        A, B, hits = ctx.meshA, ctx.meshB, ctx.hits
+        gA = torch.zeros_like(A.X)
+        gB = torch.zeros_like(B.X)
+        gP = None if gP is None else gP.to(torch.float64).contiguous()
+        gZ = None if gZ is None else gZ.to(torch.float64).contiguous()
+        backward(A, B, hits, gP=gP, gZ=gZ, gradA=gA, gradB=gB)
+        return gA, gB, None, None, None

@@ -1,0 +1,782 @@
+// Host side of the C ABI (include/tms.h): mesh handles, search plans with their
+// scratch, the launch sequence of one search (or one batch of searches), CUDA
+// graph capture and replay, capacity retries, and the adjoint entry point.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "tms_common.cuh"
+
+using namespace tms;
+
+struct tms_mesh_s {
+    unsigned magic;
+    int device;
+    long long id;
+    MeshDev dev;       // device pointers, view-offset
+    double *d_s;       // owned copy of all M s values
+    int N, M, k0, k1;
+};
+
+namespace {
+
+constexpr unsigned kMagic = 0x746d7331u;  // "tms1"
+std::mutex g_mu;
+std::atomic<long long> g_next_id{1};
+thread_local std::string g_err;
+
+int ceil_log2(unsigned long long v) {
+    int b = 0;
+    while ((1ULL << b) < v && b < 63) ++b;
+    return b;
+}
+
+#define TMS_CK(call)                                                                  \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            g_err = std::string(#call) + ": " + cudaGetErrorString(e_);               \
+            return TMS_ERR_CUDA;                                                      \
+        }                                                                             \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+struct Plan {
+    // identity
+    std::vector<long long> ids;     // A ids then B ids
+    tms_params prm;
+    cudaStream_t user = nullptr;
+    void *dHits = nullptr;
+    long long hitCap = 0;
+    long long *dOffsets = nullptr;
+    int device = 0;
+    int nPairs = 0;
+    // mesh tables
+    int n_meshes = 0;
+    MeshDev *d_meshes = nullptr;
+    int2 *d_pairs = nullptr;
+    PassEntry *d_pass_all = nullptr, *d_pass_A = nullptr, *d_pass_B = nullptr;
+    int n_pass_all = 0, n_pass_A = 0, n_pass_B = 0;
+    long long tiles_all = 0, tiles_A = 0, tiles_B = 0;
+    unsigned long long facesA = 0, facesB = 0;
+    int tri_bits = 0, pair_bits = 0;
+    // scratch
+    Bounds *d_bounds = nullptr;
+    Grid *d_grids = nullptr;
+    Counters *d_ctr = nullptr;
+    Counters *h_ctr = nullptr;
+    Grid *h_grid0 = nullptr;
+    uint32_t *bmA = nullptr, *bmH = nullptr;
+    int bmA_bits = 0, bmH_bits = 0;
+    unsigned long long ent_cap = 0, cand_cap = 0, hit_cap = 0;
+    uint64_t *ek = nullptr, *ek2 = nullptr;
+    uint32_t *ev = nullptr, *ev2 = nullptr, *eface = nullptr;
+    uint2 *ecell = nullptr;
+    float4 *ebox32 = nullptr;
+    double *ebox64 = nullptr;
+    uint32_t *sort_counts = nullptr;
+    unsigned long long *partials = nullptr;
+    uint32_t *head = nullptr, *hscan = nullptr, *cstart = nullptr, *cb = nullptr;
+    unsigned long long *cpairs = nullptr, *poff = nullptr;
+    Cand *cand = nullptr;
+    tms_hit *hits = nullptr;
+    uint64_t *hk = nullptr, *hk2 = nullptr, *okeys = nullptr;
+    uint32_t *hv = nullptr, *hv2 = nullptr, *keep = nullptr, *kscan = nullptr;
+    int grid = 304;
+    // execution
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    static constexpr int kStages = 14;
+    cudaEvent_t tev[kStages + 1] = {};
+    float stage_ms[kStages] = {};
+    int kernels = 0;
+    int retries = 0;
+    unsigned long long last_use = 0;
+
+    void free_scratch() {
+        void *ptrs[] = {bmA, bmH, ek, ek2, ev, ev2, eface, ecell, ebox32, ebox64, sort_counts,
+                        head, hscan, cstart, cb, cpairs, poff, cand, hits, hk, hk2, okeys, hv,
+                        hv2, keep, kscan};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        bmA = bmH = nullptr; ek = ek2 = nullptr; ev = ev2 = eface = nullptr; ecell = nullptr;
+        ebox32 = nullptr; ebox64 = nullptr; sort_counts = nullptr; head = hscan = cstart = cb = nullptr;
+        cpairs = poff = nullptr; cand = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
+        hv = hv2 = keep = kscan = nullptr;
+        if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+    }
+    ~Plan() {
+        if (st) cudaStreamSynchronize(st);
+        free_scratch();
+        void *ptrs[] = {d_meshes, d_pairs, d_pass_all, d_pass_A, d_pass_B, d_bounds, d_grids,
+                        d_ctr, partials};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        if (h_ctr) cudaFreeHost(h_ctr);
+        if (h_grid0) cudaFreeHost(h_grid0);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        for (auto &e : tev)
+            if (e) cudaEventDestroy(e);
+        if (st) cudaStreamDestroy(st);
+    }
+
+    tms_status alloc_scratch() {
+        free_scratch();
+        const int prec = prm.precision;
+        TMS_CK(dalloc(&bmA, (size_t)1 << (bmA_bits)));
+        TMS_CK(dalloc(&bmH, (size_t)1 << (bmH_bits)));
+        TMS_CK(dalloc(&ek, ent_cap));
+        TMS_CK(dalloc(&ek2, ent_cap));
+        TMS_CK(dalloc(&ev, ent_cap));
+        TMS_CK(dalloc(&ev2, ent_cap));
+        TMS_CK(dalloc(&eface, ent_cap));
+        TMS_CK(dalloc(&ecell, ent_cap));
+        if (prec == 1) TMS_CK(dalloc(&ebox32, 2 * ent_cap));
+        else TMS_CK(dalloc(&ebox64, 8 * ent_cap));
+        TMS_CK(dalloc(&sort_counts, (size_t)kRadixBins * grid));
+        TMS_CK(dalloc(&head, ent_cap));
+        TMS_CK(dalloc(&hscan, ent_cap));
+        TMS_CK(dalloc(&cstart, ent_cap));
+        TMS_CK(dalloc(&cb, ent_cap));
+        TMS_CK(dalloc(&cpairs, ent_cap));
+        TMS_CK(dalloc(&poff, ent_cap));
+        TMS_CK(dalloc(&cand, cand_cap));
+        TMS_CK(dalloc(&hits, hit_cap));
+        TMS_CK(dalloc(&hk, hit_cap));
+        TMS_CK(dalloc(&hk2, hit_cap));
+        TMS_CK(dalloc(&okeys, hit_cap));
+        TMS_CK(dalloc(&hv, hit_cap));
+        TMS_CK(dalloc(&hv2, hit_cap));
+        TMS_CK(dalloc(&keep, hit_cap));
+        TMS_CK(dalloc(&kscan, hit_cap));
+        return TMS_OK;
+    }
+
+    // The whole search as a stream-ordered launch sequence (no host round trip).
+    void mark(int i, cudaStream_t s) {
+        if (prm.timing) cudaEventRecord(tev[i], s);
+    }
+
+    void enqueue(cudaStream_t s) {
+        const tms_params &p = prm;
+        const int prec = p.precision, fl = p.face_level;
+        const int block = (p.block_faces == 64 || p.block_faces == 256) ? p.block_faces : 128;
+        const int sort_passes_e = (32 + pair_bits + kRadixBits - 1) / kRadixBits;
+        const int sort_passes_h = (2 * tri_bits + pair_bits + kRadixBits - 1) / kRadixBits;
+        kernels = 0;
+        mark(0, s);
+        cudaMemsetAsync(d_ctr, 0, sizeof(Counters), s);
+        launch_bounds_init(d_bounds, n_meshes, s);
+        kernels += 1;
+        mark(1, s);
+
+        FacePassArgs fa;
+        memset(&fa, 0, sizeof(fa));
+        fa.meshes = d_meshes;
+        fa.tile_rows = p.tile_rows;
+        fa.bounds = d_bounds;
+        fa.grids = d_grids;
+        fa.bmA = bmA;
+        fa.bmA_word_bits = bmA_bits;
+        fa.bmH = bmH;
+        fa.bmH_word_bits = bmH_bits;
+        fa.ent_key = ek;
+        fa.ent_val = ev;
+        fa.ent_face = eface;
+        fa.ent_cell = ecell;
+        fa.ent_box32 = ebox32;
+        fa.ent_box64 = ebox64;
+        fa.ctr = d_ctr;
+        fa.ent_cap = ent_cap;
+
+        fa.entries = d_pass_all; fa.n_entries = n_pass_all; fa.total_tiles = tiles_all;
+        fa.mode = MODE_BOUNDS;
+        launch_face_pass(fa, prec, fl, block, s);
+        mark(2, s);
+        launch_grid_params(d_bounds, d_pairs, nPairs, d_grids, p.cell_mult, s);
+        kernels += 2;
+        mark(3, s);
+
+        if (p.cell_filter) {
+            cudaMemsetAsync(bmA, 0, ((size_t)1 << bmA_bits) * sizeof(uint32_t), s);
+            cudaMemsetAsync(bmH, 0, ((size_t)1 << bmH_bits) * sizeof(uint32_t), s);
+            mark(4, s);
+            fa.entries = d_pass_A; fa.n_entries = n_pass_A; fa.total_tiles = tiles_A;
+            fa.mode = MODE_MARK;
+            launch_face_pass(fa, prec, fl, block, s);
+            mark(5, s);
+            fa.entries = d_pass_B; fa.n_entries = n_pass_B; fa.total_tiles = tiles_B;
+            fa.mode = MODE_PROBE_MARK;
+            launch_face_pass(fa, prec, fl, block, s);
+            mark(6, s);
+            fa.entries = d_pass_A; fa.n_entries = n_pass_A; fa.total_tiles = tiles_A;
+            fa.mode = MODE_PROBE;
+            launch_face_pass(fa, prec, fl, block, s);
+            kernels += 3;
+        } else {
+            mark(4, s);
+            mark(5, s);
+            mark(6, s);
+            fa.entries = d_pass_all; fa.n_entries = n_pass_all; fa.total_tiles = tiles_all;
+            fa.mode = MODE_EMIT_ALL;
+            launch_face_pass(fa, prec, fl, block, s);
+            kernels += 1;
+        }
+        mark(7, s);
+
+        // sort entries by (pair, cell, role)
+        const bool alt = radix_sort(ek, ev, ek2, ev2, sort_counts, &d_ctr->entries, ent_cap,
+                                    32 + pair_bits, grid, s);
+        kernels += 3 * sort_passes_e;
+        mark(8, s);
+        const uint64_t *sk = alt ? ek2 : ek;
+        const uint32_t *sv = alt ? ev2 : ev;
+
+        CellArgs ca;
+        ca.keys = sk; ca.d_n = &d_ctr->entries; ca.cap = ent_cap;
+        ca.head = head; ca.head_scan = hscan; ca.cell_start = cstart; ca.cell_b = cb;
+        ca.cell_pairs = cpairs; ca.pair_off = poff; ca.partials = partials; ca.ctr = d_ctr;
+        launch_cells(ca, grid, s);
+        kernels += 10;
+        mark(9, s);
+
+        EmitArgs ea;
+        ea.keys = sk; ea.vals = sv; ea.cell_start = cstart; ea.cell_b = cb; ea.pair_off = poff;
+        ea.ent_face = eface; ea.ent_cell = ecell; ea.ent_box32 = ebox32; ea.ent_box64 = ebox64;
+        ea.grids = d_grids; ea.meshes = d_meshes; ea.pairs = d_pairs; ea.ctr = d_ctr;
+        ea.ent_cap = ent_cap; ea.cand = cand; ea.cand_cap = cand_cap; ea.moller = p.moller;
+        launch_emit(ea, prec, fl, grid * 4, s);
+        kernels += 1;
+        mark(10, s);
+
+        NarrowArgs na;
+        na.cand = cand; na.cand_cap = cand_cap; na.meshes = d_meshes; na.pairs = d_pairs;
+        na.ctr = d_ctr; na.hits = hits; na.hit_key = hk; na.hit_val = hv; na.hit_cap = hit_cap;
+        na.tau = p.tau; na.tri_bits = tri_bits; na.fp32_filter = p.narrow_filter;
+        launch_narrow(na, fl, grid * 4, s);
+        kernels += 1;
+        mark(11, s);
+
+        const bool halt = radix_sort(hk, hv, hk2, hv2, sort_counts, &d_ctr->raw_hits, hit_cap,
+                                     2 * tri_bits + pair_bits, grid, s);
+        kernels += 3 * sort_passes_h;
+        mark(12, s);
+        DedupArgs da;
+        da.keys = halt ? hk2 : hk; da.vals = halt ? hv2 : hv; da.raw = hits;
+        da.meshes = d_meshes; da.pairs = d_pairs; da.ctr = d_ctr; da.raw_cap = hit_cap;
+        da.keep = keep; da.keep_scan = kscan; da.partials = partials;
+        da.out = (tms_hit *)dHits; da.out_cap = (unsigned long long)hitCap; da.out_keys = okeys;
+        da.offsets = dOffsets; da.n_pairs = nPairs; da.tri_bits = tri_bits; da.tau = p.tau;
+        launch_dedup(da, grid, s);
+        kernels += 5 + (dOffsets ? 1 : 0);
+        mark(13, s);
+
+        cudaMemcpyAsync(h_ctr, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(h_grid0, d_grids, sizeof(Grid), cudaMemcpyDeviceToHost, s);
+        mark(14, s);
+    }
+
+    tms_status run() {
+        TMS_CK(cudaEventRecord(ev_in, user));
+        TMS_CK(cudaStreamWaitEvent(st, ev_in, 0));
+        if (prm.use_graph) {
+            if (!exec) {
+                cudaGraph_t g = nullptr;
+                TMS_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                enqueue(st);
+                cudaError_t e = cudaStreamEndCapture(st, &g);
+                if (e != cudaSuccess) {
+                    g_err = std::string("graph capture: ") + cudaGetErrorString(e);
+                    return TMS_ERR_CUDA;
+                }
+                e = cudaGraphInstantiate(&exec, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    exec = nullptr;
+                    g_err = std::string("graph instantiate: ") + cudaGetErrorString(e);
+                    return TMS_ERR_CUDA;
+                }
+            }
+            TMS_CK(cudaGraphLaunch(exec, st));
+        } else {
+            enqueue(st);
+            TMS_CK(cudaGetLastError());
+        }
+        TMS_CK(cudaEventRecord(ev_out, st));
+        TMS_CK(cudaStreamWaitEvent(user, ev_out, 0));
+        TMS_CK(cudaEventSynchronize(ev_out));
+        if (prm.timing) {
+            for (int i = 0; i < kStages; ++i) {
+                float ms = 0.0f;
+                if (cudaEventElapsedTime(&ms, tev[i], tev[i + 1]) != cudaSuccess) {
+                    cudaGetLastError();
+                    ms = -1.0f;
+                }
+                stage_ms[i] = ms;
+            }
+        }
+        return TMS_OK;
+    }
+};
+
+std::vector<Plan *> g_plans;
+unsigned long long g_clock = 0;
+std::map<cudaStream_t, tms_stats> g_stats;
+std::map<cudaStream_t, std::vector<float>> g_stage_ms;
+int g_configured_mask = 0;
+
+bool same_params(const tms_params &a, const tms_params &b) {
+    return a.precision == b.precision && a.face_level == b.face_level && a.moller == b.moller &&
+           a.cell_filter == b.cell_filter && a.narrow_filter == b.narrow_filter &&
+           a.cell_mult == b.cell_mult && a.tau == b.tau && a.entry_capacity == b.entry_capacity &&
+           a.cand_capacity == b.cand_capacity && a.hit_capacity == b.hit_capacity &&
+           a.use_graph == b.use_graph && a.inject == b.inject && a.block_faces == b.block_faces &&
+           a.tile_rows == b.tile_rows && a.timing == b.timing;
+}
+
+tms_status validate_params(const tms_params &p) {
+    if (p.precision != 0 && p.precision != 1) return TMS_ERR_ARG;
+    if (p.face_level != 0 && p.face_level != 1) return TMS_ERR_ARG;
+    if (!(p.cell_mult >= 1.0f) || !(p.cell_mult < 1e6f)) return TMS_ERR_ARG;
+    if (!(p.tau >= 0.0) || !(p.tau < 1.0)) return TMS_ERR_ARG;
+    if (p.entry_capacity < 0 || p.cand_capacity < 0 || p.hit_capacity < 0) return TMS_ERR_ARG;
+    return TMS_OK;
+}
+
+tms_status check_mesh(tms_mesh m, int device) {
+    if (!m || m->magic != kMagic) return TMS_ERR_STATE;
+    if (m->device != device) return TMS_ERR_ARG;
+    return TMS_OK;
+}
+
+void fill_pass(std::vector<PassEntry> &v, long long &tiles, const tms_mesh m, int mesh_index,
+               int pair, int role, int block, int rows) {
+    PassEntry e;
+    e.mesh = mesh_index;
+    e.pair = pair;
+    e.role = role;
+    e.tiles_i = (m->dev.nqi + block - 1) / block;
+    int tiles_k = (m->dev.nqk + rows - 1) / rows;
+    e.tile_base = tiles;
+    tiles += (long long)e.tiles_i * tiles_k;
+    v.push_back(e);
+}
+
+tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms_params &prm,
+                     cudaStream_t user, void *dHits, long long hitCap, long long *dOffsets,
+                     int device, Plan **out) {
+    Plan *P = new Plan();
+    P->prm = prm;
+    P->user = user;
+    P->dHits = dHits;
+    P->hitCap = hitCap;
+    P->dOffsets = dOffsets;
+    P->device = device;
+    P->nPairs = nPairs;
+    for (int i = 0; i < nPairs; ++i) P->ids.push_back(A[i]->id);
+    for (int i = 0; i < nPairs; ++i) P->ids.push_back(B[i]->id);
+    const int block = (prm.block_faces == 64 || prm.block_faces == 256) ? prm.block_faces : 128;
+    const int rows = prm.tile_rows == 4 ? 4 : 8;
+    P->prm.tile_rows = rows;
+
+    std::vector<MeshDev> meshes;
+    std::vector<int2> pairs;
+    std::vector<PassEntry> pall, pa, pb;
+    unsigned long long max_tri = 1;
+    for (int i = 0; i < nPairs; ++i) {
+        int ia = (int)meshes.size();
+        meshes.push_back(A[i]->dev);
+        int ib = (int)meshes.size();
+        meshes.push_back(B[i]->dev);
+        pairs.push_back(make_int2(ia, ib));
+        const unsigned long long fpq = prm.face_level == 0 ? 2 : 1;
+        P->facesA += fpq * A[i]->dev.nqi * A[i]->dev.nqk;
+        P->facesB += fpq * B[i]->dev.nqi * B[i]->dev.nqk;
+        max_tri = std::max(max_tri, 2ULL * A[i]->dev.N * A[i]->dev.nqk);
+        max_tri = std::max(max_tri, 2ULL * B[i]->dev.N * B[i]->dev.nqk);
+    }
+    for (int i = 0; i < nPairs; ++i) {
+        fill_pass(pall, P->tiles_all, A[i], pairs[i].x, i, 0, block, rows);
+        fill_pass(pall, P->tiles_all, B[i], pairs[i].y, i, 1, block, rows);
+        fill_pass(pa, P->tiles_A, A[i], pairs[i].x, i, 0, block, rows);
+        fill_pass(pb, P->tiles_B, B[i], pairs[i].y, i, 1, block, rows);
+    }
+    P->n_meshes = (int)meshes.size();
+    P->n_pass_all = (int)pall.size();
+    P->n_pass_A = (int)pa.size();
+    P->n_pass_B = (int)pb.size();
+    P->tri_bits = ceil_log2(max_tri);
+    P->pair_bits = ceil_log2((unsigned long long)nPairs);
+    if (2 * P->tri_bits + P->pair_bits > 64 || P->pair_bits > 31) {
+        delete P;
+        g_err = "mesh pair too large for 64-bit hit keys";
+        return TMS_ERR_ARG;
+    }
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    P->grid = std::min(1024, 2 * sms);
+
+    cudaError_t e;
+#define TMS_PCK(call) do { if ((e = (call)) != cudaSuccess) { g_err = cudaGetErrorString(e); delete P; return TMS_ERR_CUDA; } } while (0)
+    TMS_PCK(dalloc(&P->d_meshes, meshes.size()));
+    TMS_PCK(dalloc(&P->d_pairs, pairs.size()));
+    TMS_PCK(dalloc(&P->d_pass_all, pall.size()));
+    TMS_PCK(dalloc(&P->d_pass_A, pa.size()));
+    TMS_PCK(dalloc(&P->d_pass_B, pb.size()));
+    TMS_PCK(dalloc(&P->d_bounds, meshes.size()));
+    TMS_PCK(dalloc(&P->d_grids, pairs.size()));
+    TMS_PCK(dalloc(&P->d_ctr, 1));
+    TMS_PCK(dalloc(&P->partials, 1024));
+    TMS_PCK(cudaMallocHost((void **)&P->h_ctr, sizeof(Counters)));
+    TMS_PCK(cudaMallocHost((void **)&P->h_grid0, sizeof(Grid)));
+    TMS_PCK(cudaMemcpy(P->d_meshes, meshes.data(), meshes.size() * sizeof(MeshDev), cudaMemcpyHostToDevice));
+    TMS_PCK(cudaMemcpy(P->d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    TMS_PCK(cudaMemcpy(P->d_pass_all, pall.data(), pall.size() * sizeof(PassEntry), cudaMemcpyHostToDevice));
+    TMS_PCK(cudaMemcpy(P->d_pass_A, pa.data(), pa.size() * sizeof(PassEntry), cudaMemcpyHostToDevice));
+    TMS_PCK(cudaMemcpy(P->d_pass_B, pb.data(), pb.size() * sizeof(PassEntry), cudaMemcpyHostToDevice));
+    TMS_PCK(cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking));
+    TMS_PCK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
+    TMS_PCK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
+    if (prm.timing)
+        for (auto &evt : P->tev) TMS_PCK(cudaEventCreate(&evt));
+#undef TMS_PCK
+
+    const unsigned long long faces = P->facesA + P->facesB;
+    unsigned long long ent = prm.entry_capacity > 0 ? (unsigned long long)prm.entry_capacity
+                             : (prm.cell_filter ? std::max<unsigned long long>(1 << 16, faces / 2)
+                                                : 4 * faces + (1 << 16));
+    if (prm.inject & 1u) ent = 1;
+    P->ent_cap = std::min<unsigned long long>(ent, 0x7fffffffULL);
+    P->cand_cap = prm.cand_capacity > 0 ? (unsigned long long)prm.cand_capacity
+                                        : std::max<unsigned long long>(1 << 16, 2 * P->ent_cap);
+    P->hit_cap = prm.hit_capacity > 0 ? (unsigned long long)prm.hit_capacity
+                                      : std::max<unsigned long long>(1 << 14, P->cand_cap / 16);
+    P->bmA_bits = std::min(26, std::max(11, ceil_log2(std::max<unsigned long long>(P->facesA, 1) * 8) - 5));
+    P->bmH_bits = std::min(25, std::max(11, ceil_log2(P->ent_cap * 8) - 5));
+    tms_status s = P->alloc_scratch();
+    if (s != TMS_OK) { delete P; return s; }
+    *out = P;
+    return TMS_OK;
+}
+
+Plan *find_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms_params &prm,
+                cudaStream_t user, void *dHits, long long hitCap, long long *dOffsets, int device) {
+    for (Plan *P : g_plans) {
+        if (P->device != device || P->user != user || P->dHits != dHits || P->hitCap != hitCap ||
+            P->dOffsets != dOffsets || P->nPairs != nPairs)
+            continue;
+        tms_params q = prm;
+        q.tile_rows = q.tile_rows == 4 ? 4 : 8;
+        if (!same_params(P->prm, q)) continue;
+        bool ok = true;
+        for (int i = 0; i < nPairs && ok; ++i) ok = P->ids[i] == A[i]->id && P->ids[nPairs + i] == B[i]->id;
+        if (ok) return P;
+    }
+    return nullptr;
+}
+
+void drop_plans_if(bool (*pred)(Plan *, void *), void *ctx) {
+    std::vector<Plan *> keep;
+    for (Plan *P : g_plans) {
+        if (pred(P, ctx)) delete P;
+        else keep.push_back(P);
+    }
+    g_plans.swap(keep);
+}
+
+tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms_params *params,
+                       tms_hit *dHits, long long hitCap, long long *dOffsets, long long *nHits,
+                       void *stream) {
+    if (!nHits || nPairs <= 0 || !A || !B || hitCap < 0 || (hitCap > 0 && !dHits)) return TMS_ERR_ARG;
+    tms_params prm;
+    tms_params_default(&prm);
+    if (params) prm = *params;
+    tms_status s = validate_params(prm);
+    if (s != TMS_OK) return s;
+    int device = 0;
+    TMS_CK(cudaGetDevice(&device));
+    for (int i = 0; i < nPairs; ++i) {
+        if ((s = check_mesh(A[i], device)) != TMS_OK) return s;
+        if ((s = check_mesh(B[i], device)) != TMS_OK) return s;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!(g_configured_mask & (1 << device))) {
+        TMS_CK(configure_face_pass());
+        g_configured_mask |= 1 << device;
+    }
+    Plan *P = find_plan(A, B, nPairs, prm, user, dHits, hitCap, dOffsets, device);
+    if (!P) {
+        if (g_plans.size() >= 16) {
+            auto it = std::min_element(g_plans.begin(), g_plans.end(),
+                                       [](Plan *x, Plan *y) { return x->last_use < y->last_use; });
+            delete *it;
+            g_plans.erase(it);
+        }
+        s = make_plan(A, B, nPairs, prm, user, dHits, hitCap, dOffsets, device, &P);
+        if (s != TMS_OK) return s;
+        g_plans.push_back(P);
+    }
+    P->last_use = ++g_clock;
+    P->retries = 0;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        s = P->run();
+        if (s != TMS_OK) return s;
+        const Counters &c = *P->h_ctr;
+        if (c.status & ST_NONFINITE) {
+            g_err = "non-finite vertex coordinate";
+            return TMS_ERR_ARG;
+        }
+        if (c.status & ST_PAIR_LIMIT) {
+            g_err = "grid proposes too many face pairs (degenerate geometry)";
+            return TMS_ERR_ARG;
+        }
+        bool grow = false;
+        if (c.entries > P->ent_cap) {
+            P->ent_cap = std::min<unsigned long long>(0x7fffffffULL, c.entries + c.entries / 4 + 1024);
+            P->bmH_bits = std::min(25, std::max(11, ceil_log2(P->ent_cap * 8) - 5));
+            P->cand_cap = std::max(P->cand_cap, 2 * P->ent_cap);
+            grow = true;
+        }
+        if (!grow && c.cand > P->cand_cap) {
+            P->cand_cap = c.cand + c.cand / 4 + 1024;
+            grow = true;
+        }
+        if (!grow && c.raw_hits > P->hit_cap) {
+            P->hit_cap = c.raw_hits + c.raw_hits / 4 + 1024;
+            grow = true;
+        }
+        if (!grow) break;
+        ++P->retries;
+        TMS_CK(cudaStreamSynchronize(P->st));
+        s = P->alloc_scratch();
+        if (s != TMS_OK) return s;
+    }
+    const Counters &c = *P->h_ctr;
+    tms_stats st;
+    memset(&st, 0, sizeof(st));
+    st.entries = (long long)c.entries;
+    st.cells = (long long)c.cells;
+    st.pair_slots = (long long)c.pair_slots;
+    st.candidates = (long long)c.cand;
+    st.fp64_solves = (long long)c.fp64;
+    st.raw_hits = (long long)c.raw_hits;
+    st.hits = (long long)c.out;
+    for (int d = 0; d < 4; ++d) st.grid_n[d] = P->h_grid0->n[d];
+    st.empty = P->h_grid0->empty;
+    st.retries = P->retries;
+    st.kernels = P->kernels;
+    g_stats[user] = st;
+    if (prm.timing) g_stage_ms[user] = std::vector<float>(P->stage_ms, P->stage_ms + Plan::kStages);
+    if (c.entries > P->ent_cap || c.cand > P->cand_cap || c.raw_hits > P->hit_cap) {
+        g_err = "scratch capacity still exceeded after retries";
+        *nHits = (long long)c.out;
+        return TMS_ERR_CAPACITY;
+    }
+    *nHits = (long long)c.out;
+    if (prm.inject & 4u) {
+        g_err = "injected timeout";
+        return TMS_ERR_TIMEOUT;
+    }
+    if ((long long)c.out > hitCap || (prm.inject & 2u)) {
+        g_err = "hit buffer too small";
+        return TMS_ERR_CAPACITY;
+    }
+    return TMS_OK;
+}
+
+bool plan_uses(Plan *P, void *ctx) {
+    long long id = *(long long *)ctx;
+    return std::find(P->ids.begin(), P->ids.end(), id) != P->ids.end();
+}
+bool plan_on_stream(Plan *P, void *ctx) {
+    return ctx == nullptr || P->user == *(cudaStream_t *)ctx;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tms_params_default(tms_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->precision = 1;
+    p->face_level = 0;
+    p->moller = 0;
+    p->cell_filter = 1;
+    p->narrow_filter = 1;
+    p->cell_mult = 1.0625f;
+    p->tau = 1e-12;
+    p->use_graph = 1;
+    p->block_faces = 128;
+    p->tile_rows = 8;
+}
+
+const char *tms_status_str(tms_status s) {
+    switch (s) {
+        case TMS_OK: return "ok";
+        case TMS_ERR_ARG: return "invalid argument";
+        case TMS_ERR_CAPACITY: return "capacity exceeded";
+        case TMS_ERR_TIMEOUT: return "device wait timed out";
+        case TMS_ERR_CUDA: return "CUDA error";
+        case TMS_ERR_STATE: return "invalid state";
+        default: return "unknown status";
+    }
+}
+
+const char *tms_version(void) { return "tms 0.1.0 (sm_103a)"; }
+
+const char *tms_last_error(void) { return g_err.c_str(); }
+
+tms_status tms_build_mesh(const double *dX, const double *dY, const double *dPx, const double *dPy,
+                          int N, int M, int k0, int k1, const double *s, int periodic_theta,
+                          void *stream, tms_mesh *out) {
+    if (!out) return TMS_ERR_ARG;
+    *out = nullptr;
+    if (!dX || !dY || !dPx || !dPy || !s) return TMS_ERR_ARG;
+    if (M < 2 || k0 < 0 || k1 > M || k1 - k0 < 2) return TMS_ERR_ARG;
+    if (periodic_theta ? N < 3 : N < 2) return TMS_ERR_ARG;
+    const int nqi = periodic_theta ? N : N - 1;
+    if ((unsigned long long)N * (unsigned long long)M >= (1ULL << 31)) return TMS_ERR_ARG;
+    int device = 0;
+    TMS_CK(cudaGetDevice(&device));
+    std::vector<double> hs(M);
+    cudaPointerAttributes attr;
+    cudaError_t ae = cudaPointerGetAttributes(&attr, s);
+    if (ae != cudaSuccess) cudaGetLastError();
+    const bool s_dev = ae == cudaSuccess && attr.type == cudaMemoryTypeDevice;
+    if (s_dev) TMS_CK(cudaMemcpy(hs.data(), s, M * sizeof(double), cudaMemcpyDeviceToHost));
+    else memcpy(hs.data(), s, M * sizeof(double));
+    for (int k = 1; k < M; ++k)
+        if (!(hs[k] > hs[k - 1])) return TMS_ERR_ARG;
+    const double *ptrs[4] = {dX, dY, dPx, dPy};
+    for (int c = 0; c < 4; ++c) {
+        cudaPointerAttributes pa;
+        cudaError_t pe = cudaPointerGetAttributes(&pa, ptrs[c]);
+        if (pe != cudaSuccess) { cudaGetLastError(); return TMS_ERR_ARG; }
+        if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) return TMS_ERR_ARG;
+    }
+    tms_mesh m = new tms_mesh_s();
+    m->magic = kMagic;
+    m->device = device;
+    m->id = g_next_id++;
+    m->N = N; m->M = M; m->k0 = k0; m->k1 = k1;
+    cudaError_t e = cudaMalloc((void **)&m->d_s, M * sizeof(double));
+    if (e != cudaSuccess) { delete m; g_err = cudaGetErrorString(e); return TMS_ERR_CUDA; }
+    e = cudaMemcpyAsync(m->d_s, hs.data(), M * sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) { cudaFree(m->d_s); delete m; g_err = cudaGetErrorString(e); return TMS_ERR_CUDA; }
+    const size_t off = (size_t)k0 * N;
+    for (int c = 0; c < 4; ++c) m->dev.c[c] = ptrs[c] + off;
+    m->dev.s = m->d_s + k0;
+    m->dev.N = N;
+    m->dev.M = k1 - k0;
+    m->dev.periodic = periodic_theta ? 1 : 0;
+    m->dev.nqi = nqi;
+    m->dev.nqk = k1 - k0 - 1;
+    m->dev.pad = 0;
+    *out = m;
+    return TMS_OK;
+}
+
+tms_status tms_destroy_mesh(tms_mesh m) {
+    if (!m || m->magic != kMagic) return TMS_ERR_STATE;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        cudaDeviceSynchronize();
+        long long id = m->id;
+        drop_plans_if(plan_uses, &id);
+    }
+    cudaFree(m->d_s);
+    m->magic = 0;
+    delete m;
+    return TMS_OK;
+}
+
+tms_status tms_search(tms_mesh A, tms_mesh B, const tms_params *params, tms_hit *dHits,
+                      long long hitCap, long long *nHits, void *stream) {
+    return search_impl(&A, &B, 1, params, dHits, hitCap, nullptr, nHits, stream);
+}
+
+tms_status tms_search_batched(const tms_mesh *A, const tms_mesh *B, int nPairs,
+                              const tms_params *params, tms_hit *dHits, long long hitCap,
+                              long long *dOffsets, long long *nHits, void *stream) {
+    if (!dOffsets) return TMS_ERR_ARG;
+    return search_impl(A, B, nPairs, params, dHits, hitCap, dOffsets, nHits, stream);
+}
+
+tms_status tms_backward(tms_mesh A, tms_mesh B, const tms_hit *dHits, long long nHits,
+                        const double *dGradP, const double *dGradZ, double *dGradA, double *dGradB,
+                        const double *dDvDalphaA, const double *dDvDalphaB, double *dGradAlpha,
+                        void *stream) {
+    if (nHits < 0 || (nHits > 0 && !dHits)) return TMS_ERR_ARG;
+    int device = 0;
+    TMS_CK(cudaGetDevice(&device));
+    tms_status s;
+    if ((s = check_mesh(A, device)) != TMS_OK) return s;
+    if ((s = check_mesh(B, device)) != TMS_OK) return s;
+    if (nHits == 0) return TMS_OK;
+    AdjointArgs a;
+    memset(&a, 0, sizeof(a));
+    a.hits = dHits;
+    a.n = nHits;
+    a.A = A->dev;
+    a.B = B->dev;
+    a.gP = dGradP;
+    a.gZ = dGradZ;
+    const size_t MNa = (size_t)A->N * A->M, MNb = (size_t)B->N * B->M;
+    const size_t offA = (size_t)A->k0 * A->N, offB = (size_t)B->k0 * B->N;
+    for (int c = 0; c < 4; ++c) {
+        a.gA[c] = dGradA ? dGradA + c * MNa + offA : nullptr;
+        a.gB[c] = dGradB ? dGradB + c * MNb + offB : nullptr;
+        a.dA[c] = dDvDalphaA ? dDvDalphaA + c * MNa + offA : nullptr;
+        a.dB[c] = dDvDalphaB ? dDvDalphaB + c * MNb + offB : nullptr;
+    }
+    a.galpha = dGradAlpha;
+    launch_adjoint(a, (cudaStream_t)stream);
+    TMS_CK(cudaGetLastError());
+    return TMS_OK;
+}
+
+tms_status tms_last_stats(void *stream, tms_stats *out) {
+    if (!out) return TMS_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_stats.find((cudaStream_t)stream);
+    if (it == g_stats.end()) return TMS_ERR_STATE;
+    *out = it->second;
+    return TMS_OK;
+}
+
+tms_status tms_last_stage_ms(void *stream, float *ms, int cap, int *n) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_stage_ms.find((cudaStream_t)stream);
+    if (it == g_stage_ms.end()) return TMS_ERR_STATE;
+    if (n) *n = (int)it->second.size();
+    for (int i = 0; i < cap && i < (int)it->second.size(); ++i) ms[i] = it->second[i];
+    return TMS_OK;
+}
+
+tms_status tms_release_workspace(void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    drop_plans_if(plan_on_stream, stream ? (void *)&s : nullptr);
+    return TMS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,338 @@
+// Internal device structures and helpers of the GB300 mesh-intersection search.
+// Not part of the public ABI (include/tms.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/tms.h"
+
+namespace tms {
+
+// ---------------------------------------------------------------------------
+// tunables
+// ---------------------------------------------------------------------------
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kSortBlock = 256;          // threads per radix block (8 warps)
+constexpr int kSortItems = 8;            // keys per thread per tile
+constexpr int kSortTile = kSortBlock * kSortItems;
+constexpr int kScanBlock = 512;
+constexpr int kCellBits = 31;            // a pair's grid has < 2^31 cells
+constexpr int kMaxCellsPerDim = 65535;
+constexpr unsigned long long kMaxPairSlots = 1ULL << 36;  // bound on proposed pairs per call
+
+// Face-pass modes
+enum FaceMode : int {
+    MODE_BOUNDS = 0,      // per-mesh world bounds, widest face extent, finiteness
+    MODE_MARK = 1,        // set occupancy bits of mesh-A cells
+    MODE_PROBE_MARK = 2,  // mesh B: emit entries in A-occupied cells, mark them hot
+    MODE_PROBE = 3,       // mesh A: emit entries in hot cells
+    MODE_EMIT_ALL = 4     // emit every face-cell incidence (no occupancy filter)
+};
+
+// status bits written by kernels into Counters::status
+enum StatusBits : unsigned int {
+    ST_NONFINITE = 1u << 0,
+    ST_TIMEOUT = 1u << 1,
+    ST_PAIR_LIMIT = 1u << 2,
+};
+
+// ---------------------------------------------------------------------------
+// device-side descriptors
+// ---------------------------------------------------------------------------
+struct MeshDev {
+    const double *c[4];   // x, y, px, py, offset to the first view column
+    const double *s;      // s values of the view (M entries), device
+    int N;                // theta samples
+    int M;                // vertex rows in the view
+    int periodic;
+    int nqi;              // quads per row (N or N-1)
+    int nqk;              // quad rows (M-1)
+    int pad;
+};
+
+struct PassEntry {        // one mesh processed by a face pass
+    int mesh;             // index into the mesh table
+    int pair;             // mesh-pair index
+    int role;             // 0 = mesh A, 1 = mesh B of the pair
+    int tiles_i;          // tiles along theta
+    long long tile_base;  // first global tile of this mesh
+};
+
+struct Bounds {           // per mesh, order-preserving uint64 encodings of doubles
+    unsigned long long lo[4];
+    unsigned long long hi[4];
+    unsigned long long w[4];
+    unsigned int flags;
+    unsigned int faces;   // nonzero once any face was seen
+};
+
+struct Grid {             // per pair: trimmed world and uniform grid
+    double o64[4], e64[4], inv64[4];
+    float o32[4], e32[4], inv32[4];
+    int n[4];
+    int empty;
+    int pad[3];
+};
+
+struct Counters {
+    unsigned long long entries;
+    unsigned long long cells;
+    unsigned long long pair_slots;
+    unsigned long long cand;
+    unsigned long long fp64;
+    unsigned long long raw_hits;
+    unsigned long long out;
+    unsigned int status;
+    unsigned int pad;
+};
+
+struct Cand {             // candidate face pair
+    uint32_t faceA, faceB, pair, pad;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ inline unsigned long long ord_enc(double v) {
+#ifdef __CUDA_ARCH__
+    long long b = __double_as_longlong(v);
+#else
+    long long b;
+    memcpy(&b, &v, 8);
+#endif
+    return (b >= 0) ? ((unsigned long long)b | 0x8000000000000000ULL) : ~(unsigned long long)b;
+}
+
+__host__ __device__ inline double ord_dec(unsigned long long u) {
+    long long b = (u & 0x8000000000000000ULL) ? (long long)(u & 0x7FFFFFFFFFFFFFFFULL)
+                                              : (long long)(~u);
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double v;
+    memcpy(&v, &b, 8);
+    return v;
+#endif
+}
+
+// 64-bit mixer (MurmurHash3 finaliser) for hashing (pair, cell) into a bitmap.
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdULL;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ULL;
+    x ^= x >> 33;
+    return x;
+}
+
+// Two bits inside one 32-bit word: word index from the top bits, bit positions
+// from the low bits (a blocked Bloom filter with k = 2).
+__device__ __forceinline__ void bloom_slot(uint64_t h, int word_bits, uint32_t &word,
+                                           uint32_t &mask) {
+    word = (uint32_t)(h >> (64 - word_bits));
+    mask = (1u << (h & 31)) | (1u << ((h >> 5) & 31));
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ unsigned long long clamp_count(const unsigned long long *p,
+                                                          unsigned long long cap) {
+    unsigned long long n = *p;
+    return n < cap ? n : cap;
+}
+
+// Warp-aggregated append: every lane of `mask` calls this; lanes with pred
+// receive a unique slot.  One atomic per warp.
+__device__ __forceinline__ unsigned long long warp_append(unsigned long long *counter, bool pred,
+                                                          unsigned int mask) {
+    unsigned int want = __ballot_sync(mask, pred);
+    unsigned long long base = 0;
+    if (want) {
+        int leader = __ffs(want) - 1;
+        int lane = threadIdx.x & 31;
+        if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(want));
+        base = __shfl_sync(mask, base, leader);
+    }
+    return base + __popc(want & lanemask_lt());
+}
+
+// cell index along one coordinate: monotone non-decreasing in v, clamped
+__device__ __forceinline__ int cell_of(float v, float o, float inv, int n) {
+    float t = (v - o) * inv;
+    t = fminf(fmaxf(t, 0.0f), (float)(n - 1));
+    return (int)t;
+}
+__device__ __forceinline__ int cell_of(double v, double o, double inv, int n) {
+    double t = (v - o) * inv;
+    t = fmin(fmax(t, 0.0), (double)(n - 1));
+    return (int)t;
+}
+
+// Triangle vertex grid indices, Sec. 5.2.4 orderings.
+// T1 (tau 0): x1 = (i+1, k), x2 = (i, k), x3 = (i, k+1)
+// T2 (tau 1): x1 = (i, k+1), x2 = (i+1, k+1), x3 = (i+1, k)
+__device__ __forceinline__ void tri_ij(const MeshDev &m, uint32_t t, int ii[3], int kk[3]) {
+    uint32_t q = t >> 1;
+    int tau = t & 1;
+    int i = (int)(q % (uint32_t)m.N), k = (int)(q / (uint32_t)m.N);
+    int ip = (i + 1 == m.N) ? 0 : i + 1;
+    if (tau == 0) {
+        ii[0] = ip; kk[0] = k;
+        ii[1] = i;  kk[1] = k;
+        ii[2] = i;  kk[2] = k + 1;
+    } else {
+        ii[0] = i;  kk[0] = k + 1;
+        ii[1] = ip; kk[1] = k + 1;
+        ii[2] = ip; kk[2] = k;
+    }
+}
+
+__device__ __forceinline__ void load_vertex(const MeshDev &m, int i, int k, double v[4]) {
+    size_t off = (size_t)k * m.N + i;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = __ldg(m.c[c] + off);
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers implemented in the .cu files
+// ---------------------------------------------------------------------------
+struct FacePassArgs {
+    const PassEntry *entries;
+    int n_entries;
+    long long total_tiles;
+    const MeshDev *meshes;
+    int mode;
+    int tile_rows;
+    Bounds *bounds;                // indexed by mesh
+    const Grid *grids;             // indexed by pair
+    uint32_t *bmA;
+    int bmA_word_bits;
+    uint32_t *bmH;
+    int bmH_word_bits;
+    uint64_t *ent_key;
+    uint32_t *ent_val;
+    uint32_t *ent_face;
+    uint2 *ent_cell;
+    float4 *ent_box32;             // 2 per entry
+    double *ent_box64;             // 8 per entry
+    Counters *ctr;
+    unsigned long long ent_cap;
+};
+
+void launch_face_pass(const FacePassArgs &a, int precision, int face_level, int block,
+                      cudaStream_t st);
+cudaError_t configure_face_pass();
+void launch_bounds_init(Bounds *b, int n, cudaStream_t st);
+void launch_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *g,
+                        float cell_mult, cudaStream_t st);
+
+// radix sort of (u64 key, u32 value) with a device-side count; returns true
+// when the sorted data ends in the alternate buffers
+bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                uint32_t *counts, const unsigned long long *d_n, unsigned long long cap,
+                int key_bits, int grid, cudaStream_t st);
+size_t radix_counts_size(int grid);
+
+// exclusive scans with a device-side count; total written to *d_total
+void scan_u32(const uint32_t *in, uint32_t *out, const unsigned long long *d_n,
+              unsigned long long cap, unsigned long long *partials, unsigned long long *d_total,
+              int grid, cudaStream_t st);
+void scan_u64(const unsigned long long *in, unsigned long long *out,
+              const unsigned long long *d_n, unsigned long long cap,
+              unsigned long long *partials, unsigned long long *d_total, int grid,
+              cudaStream_t st);
+
+struct CellArgs {
+    const uint64_t *keys;          // sorted entry keys
+    const unsigned long long *d_n; // entry count
+    unsigned long long cap;
+    uint32_t *head;                // [cap]
+    uint32_t *head_scan;           // [cap]
+    uint32_t *cell_start;          // [cap]
+    uint32_t *cell_b;              // [cap]
+    unsigned long long *cell_pairs;  // [cap]
+    unsigned long long *pair_off;    // [cap]
+    unsigned long long *partials;
+    Counters *ctr;
+};
+void launch_cells(const CellArgs &a, int grid, cudaStream_t st);
+
+struct EmitArgs {
+    const uint64_t *keys;          // sorted entry keys
+    const uint32_t *vals;          // sorted entry indices
+    const uint32_t *cell_start;
+    const uint32_t *cell_b;
+    const unsigned long long *pair_off;
+    const uint32_t *ent_face;
+    const uint2 *ent_cell;
+    const float4 *ent_box32;
+    const double *ent_box64;
+    const Grid *grids;
+    const MeshDev *meshes;
+    const int2 *pairs;
+    Counters *ctr;
+    unsigned long long ent_cap;
+    Cand *cand;
+    unsigned long long cand_cap;
+    int moller;
+};
+void launch_emit(const EmitArgs &a, int precision, int face_level, int grid, cudaStream_t st);
+
+struct NarrowArgs {
+    const Cand *cand;
+    unsigned long long cand_cap;
+    const MeshDev *meshes;
+    const int2 *pairs;
+    Counters *ctr;
+    tms_hit *hits;
+    uint64_t *hit_key;
+    uint32_t *hit_val;
+    unsigned long long hit_cap;
+    double tau;
+    int tri_bits;
+    int fp32_filter;
+};
+void launch_narrow(const NarrowArgs &a, int face_level, int grid, cudaStream_t st);
+
+struct DedupArgs {
+    const uint64_t *keys;          // sorted hit keys
+    const uint32_t *vals;          // sorted raw-hit indices
+    const tms_hit *raw;
+    const MeshDev *meshes;
+    const int2 *pairs;
+    Counters *ctr;
+    unsigned long long raw_cap;
+    uint32_t *keep;
+    uint32_t *keep_scan;
+    unsigned long long *partials;
+    tms_hit *out;
+    unsigned long long out_cap;
+    uint64_t *out_keys;            // [raw_cap], scratch for offsets
+    long long *offsets;            // nPairs + 1 (may be null)
+    int n_pairs;
+    int tri_bits;
+    double tau;
+};
+void launch_dedup(const DedupArgs &a, int grid, cudaStream_t st);
+
+struct AdjointArgs {
+    const tms_hit *hits;
+    long long n;
+    MeshDev A, B;
+    const double *gP, *gZ;
+    double *gA[4];
+    double *gB[4];
+    const double *dA[4];
+    const double *dB[4];
+    double *galpha;
+};
+void launch_adjoint(const AdjointArgs &a, cudaStream_t st);
+
+}  // namespace tms

@@ -1,0 +1,535 @@
+// Face passes of the broad phase: one read of a mesh's vertex grid per pass.
+//
+// Broad phase of arXiv 2109.14814, Sec. 5.2.1-5.2.2, re-designed for GB300:
+//   MODE_BOUNDS      per-mesh world bounds, widest face extent per coordinate
+//                    (the grid rule of Sec. 5.2.1: cell edge > widest face), and
+//                    a finiteness check of every vertex;
+//   MODE_MARK        occupancy bits of the cells covered by mesh A's faces;
+//   MODE_PROBE_MARK  mesh B: one entry per face-cell incidence in a cell that
+//                    mesh A occupies, and those cells marked "hot";
+//   MODE_PROBE       mesh A: one entry per face-cell incidence in a hot cell;
+//   MODE_EMIT_ALL    one entry per face-cell incidence (no filter).
+// Cells that do not hold faces of both meshes are dropped, as the paper drops
+// grid boxes whose quad list is empty on either side (Sec. 5.3); the occupancy
+// bitmaps only decide this before any list is built.  A bitmap is a blocked
+// Bloom filter over hash(pair, cell): a false positive only adds entries, never
+// removes one, so every face pair sharing a cell still meets in the sort.
+//
+// Tiling: a block owns a tile of TI quads along theta x TK quad rows.  All
+// (TI+1) x (TK+1) vertices of the tile are loaded once, coalesced along theta,
+// into shared memory (converted to FP32 lower/upper bounds in the mixed
+// precision mode), then each thread builds the boxes of its quads' faces.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "tms_common.cuh"
+
+namespace tms {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <int PREC>
+struct Vtx;
+
+// mixed precision: a vertex as FP32 lower and upper bounds of its coordinates
+template <>
+struct Vtx<1> {
+    float lo[4], hi[4];
+};
+
+// plain FP64
+template <>
+struct Vtx<0> {
+    double v[4];
+};
+
+template <int PREC>
+struct BoxT;
+template <>
+struct BoxT<1> {
+    float lo[4], hi[4];
+};
+template <>
+struct BoxT<0> {
+    double lo[4], hi[4];
+};
+
+__device__ __forceinline__ void box_init(BoxT<1> &b, const Vtx<1> &v) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) { b.lo[d] = v.lo[d]; b.hi[d] = v.hi[d]; }
+}
+__device__ __forceinline__ void box_add(BoxT<1> &b, const Vtx<1> &v) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) { b.lo[d] = fminf(b.lo[d], v.lo[d]); b.hi[d] = fmaxf(b.hi[d], v.hi[d]); }
+}
+__device__ __forceinline__ void box_init(BoxT<0> &b, const Vtx<0> &v) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) { b.lo[d] = v.v[d]; b.hi[d] = v.v[d]; }
+}
+__device__ __forceinline__ void box_add(BoxT<0> &b, const Vtx<0> &v) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) { b.lo[d] = fmin(b.lo[d], v.v[d]); b.hi[d] = fmax(b.hi[d], v.v[d]); }
+}
+
+__device__ __forceinline__ void to_vtx(const double x[4], Vtx<1> &v) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        v.lo[d] = __double2float_rd(x[d]);
+        v.hi[d] = __double2float_ru(x[d]);
+    }
+}
+__device__ __forceinline__ void to_vtx(const double x[4], Vtx<0> &v) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) v.v[d] = x[d];
+}
+
+template <int PREC>
+struct GridView;
+template <>
+struct GridView<1> {
+    float o[4], e[4], inv[4];
+    int n[4];
+    __device__ void load(const Grid &g) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) { o[d] = g.o32[d]; e[d] = g.e32[d]; inv[d] = g.inv32[d]; n[d] = g.n[d]; }
+    }
+};
+template <>
+struct GridView<0> {
+    double o[4], e[4], inv[4];
+    int n[4];
+    __device__ void load(const Grid &g) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) { o[d] = g.o64[d]; e[d] = g.e64[d]; inv[d] = g.inv64[d]; n[d] = g.n[d]; }
+    }
+};
+
+template <int PREC>
+__device__ __forceinline__ void write_box(const FacePassArgs &a, unsigned long long pos,
+                                          const BoxT<PREC> &b);
+template <>
+__device__ __forceinline__ void write_box<1>(const FacePassArgs &a, unsigned long long pos,
+                                             const BoxT<1> &b) {
+    a.ent_box32[2 * pos] = make_float4(b.lo[0], b.lo[1], b.lo[2], b.lo[3]);
+    a.ent_box32[2 * pos + 1] = make_float4(b.hi[0], b.hi[1], b.hi[2], b.hi[3]);
+}
+template <>
+__device__ __forceinline__ void write_box<0>(const FacePassArgs &a, unsigned long long pos,
+                                             const BoxT<0> &b) {
+    double2 *p = reinterpret_cast<double2 *>(a.ent_box64 + 8 * pos);
+    p[0] = make_double2(b.lo[0], b.lo[1]);
+    p[1] = make_double2(b.lo[2], b.lo[3]);
+    p[2] = make_double2(b.hi[0], b.hi[1]);
+    p[3] = make_double2(b.hi[2], b.hi[3]);
+}
+
+// Per-thread accumulators of MODE_BOUNDS, in the box precision (FP32 min/max in
+// the mixed mode: FP64 arithmetic is a scarce pipe on GB300)
+template <int PREC>
+struct BoundAcc;
+template <>
+struct BoundAcc<1> {
+    float lo[4], hi[4], w[4];
+    unsigned seen;
+    __device__ void init() {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) { lo[d] = __int_as_float(0x7f800000); hi[d] = -lo[d]; w[d] = 0.0f; }
+        seen = 0;
+    }
+    __device__ void add(const BoxT<1> &b) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            lo[d] = fminf(lo[d], b.lo[d]);
+            hi[d] = fmaxf(hi[d], b.hi[d]);
+            w[d] = fmaxf(w[d], b.hi[d] - b.lo[d]);
+        }
+        seen = 1;
+    }
+    __device__ double get_lo(int d) const { return (double)lo[d]; }
+    __device__ double get_hi(int d) const { return (double)hi[d]; }
+    __device__ double get_w(int d) const { return (double)w[d]; }
+};
+template <>
+struct BoundAcc<0> {
+    double lo[4], hi[4], w[4];
+    unsigned seen;
+    __device__ void init() {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) { lo[d] = __longlong_as_double(0x7ff0000000000000LL); hi[d] = -lo[d]; w[d] = 0.0; }
+        seen = 0;
+    }
+    __device__ void add(const BoxT<0> &b) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            lo[d] = fmin(lo[d], b.lo[d]);
+            hi[d] = fmax(hi[d], b.hi[d]);
+            w[d] = fmax(w[d], b.hi[d] - b.lo[d]);
+        }
+        seen = 1;
+    }
+    __device__ double get_lo(int d) const { return lo[d]; }
+    __device__ double get_hi(int d) const { return hi[d]; }
+    __device__ double get_w(int d) const { return w[d]; }
+};
+
+// The cells of one face and the mode's action on each.  Called by all 32 lanes
+// of a warp together (valid = false for lanes without a face).
+template <int PREC>
+__device__ __forceinline__ void face_cells(const FacePassArgs &a, const GridView<PREC> &g,
+                                           bool valid, const BoxT<PREC> &b, uint32_t face,
+                                           int pair, int role) {
+    int clo[4], cnt[4];
+    unsigned count = 0;
+    if (valid) {
+        bool out = false;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) out |= (b.hi[d] < g.o[d]) || (b.lo[d] > g.e[d]);
+        if (!out) {
+            count = 1;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                clo[d] = cell_of(b.lo[d], g.o[d], g.inv[d], g.n[d]);
+                int chi = cell_of(b.hi[d], g.o[d], g.inv[d], g.n[d]);
+                cnt[d] = chi - clo[d] + 1;
+                count *= (unsigned)cnt[d];
+            }
+        }
+    }
+    unsigned maxc = __reduce_max_sync(FULL, count);
+    const uint64_t pair_hi = (uint64_t)(uint32_t)pair << 32;
+    for (unsigned it = 0; it < maxc; ++it) {
+        bool act = it < count;
+        uint32_t cell = 0;
+        int cc[4] = {0, 0, 0, 0};
+        if (act) {
+            unsigned r = it;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                cc[d] = clo[d] + (int)(r % (unsigned)cnt[d]);
+                r /= (unsigned)cnt[d];
+            }
+            cell = (((uint32_t)cc[3] * (uint32_t)g.n[2] + (uint32_t)cc[2]) * (uint32_t)g.n[1] +
+                    (uint32_t)cc[1]) * (uint32_t)g.n[0] + (uint32_t)cc[0];
+        }
+        uint64_t h = mix64(pair_hi | cell);
+        bool emit = false;
+        if (a.mode == MODE_MARK) {
+            if (act) {
+                uint32_t w, m;
+                bloom_slot(h, a.bmA_word_bits, w, m);
+                atomicOr(a.bmA + w, m);
+            }
+        } else if (a.mode == MODE_PROBE_MARK) {
+            if (act) {
+                uint32_t w, m;
+                bloom_slot(h, a.bmA_word_bits, w, m);
+                if ((__ldg(a.bmA + w) & m) == m) {
+                    emit = true;
+                    uint32_t w2, m2;
+                    bloom_slot(h, a.bmH_word_bits, w2, m2);
+                    atomicOr(a.bmH + w2, m2);
+                }
+            }
+        } else if (a.mode == MODE_PROBE) {
+            if (act) {
+                uint32_t w2, m2;
+                bloom_slot(h, a.bmH_word_bits, w2, m2);
+                emit = (__ldg(a.bmH + w2) & m2) == m2;
+            }
+        } else {  // MODE_EMIT_ALL
+            emit = act;
+        }
+        if (a.mode != MODE_MARK) {
+            unsigned long long pos = warp_append(&a.ctr->entries, emit, FULL);
+            if (emit && pos < a.ent_cap) {
+                a.ent_key[pos] = pair_hi | ((uint64_t)cell << 1) | (uint64_t)role;
+                a.ent_val[pos] = (uint32_t)pos;
+                a.ent_face[pos] = face;
+                a.ent_cell[pos] = make_uint2((uint32_t)cc[0] | ((uint32_t)cc[1] << 16),
+                                             (uint32_t)cc[2] | ((uint32_t)cc[3] << 16));
+                write_box<PREC>(a, pos, b);
+            }
+        }
+    }
+}
+
+template <int PREC, int FACE, int TK>
+__global__ void __launch_bounds__(256) k_face_pass(FacePassArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Vtx<PREC> *sv = reinterpret_cast<Vtx<PREC> *>(smem_raw);
+    const int TI = blockDim.x;
+    const int W = TI + 1;
+    const long long tile = blockIdx.x;
+
+    // which mesh this tile belongs to (binary search over tile_base)
+    int lo = 0, hi = a.n_entries - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (a.entries[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    const PassEntry pe = a.entries[lo];
+    const MeshDev m = a.meshes[pe.mesh];
+    const long long lt = tile - pe.tile_base;
+    const int ti = (int)(lt % pe.tiles_i), tk = (int)(lt / pe.tiles_i);
+    const int i0 = ti * TI, kq0 = tk * TK;
+    const int cols_q = min(TI, m.nqi - i0);
+    const int rows_q = min(TK, m.nqk - kq0);
+
+    GridView<PREC> g;
+    if (a.mode != MODE_BOUNDS) {
+        const Grid &gg = a.grids[pe.pair];
+        if (gg.empty) return;
+        g.load(gg);
+    }
+
+    // ---- load the tile's vertices: rows kq0..kq0+rows_q, columns i0..i0+cols_q
+    unsigned nonfinite = 0;
+    {
+        const int t = threadIdx.x;
+        double x[TK + 1][4];
+        const bool col_ok = t < cols_q;
+        const int vi = i0 + t;
+#pragma unroll
+        for (int r = 0; r <= TK; ++r) {
+            if (col_ok && r <= rows_q) {
+                size_t off = (size_t)(kq0 + r) * m.N + vi;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) x[r][c] = __ldg(m.c[c] + off);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r <= TK; ++r) {
+            if (col_ok && r <= rows_q) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) nonfinite |= !isfinite(x[r][c]);
+                to_vtx(x[r], sv[r * W + t]);
+            }
+        }
+        // the last vertex column of the tile (wraps to column 0 on a periodic mesh)
+        if (t <= rows_q) {
+            int vj = i0 + cols_q;
+            if (vj == m.N) vj = 0;
+            size_t off = (size_t)(kq0 + t) * m.N + vj;
+            double y[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                y[c] = __ldg(m.c[c] + off);
+                nonfinite |= !isfinite(y[c]);
+            }
+            to_vtx(y, sv[t * W + cols_q]);
+        }
+    }
+    __syncthreads();
+
+    BoundAcc<PREC> acc;
+    if (a.mode == MODE_BOUNDS) acc.init();
+
+    const int t = threadIdx.x;
+    const bool col_valid = t < cols_q;
+    const int i = i0 + t;
+    for (int r = 0; r < rows_q; ++r) {
+        const int k = kq0 + r;
+        Vtx<PREC> va, vb, vc, vd;
+        if (col_valid) {
+            va = sv[r * W + t];             // (i, k)
+            vb = sv[r * W + t + 1];         // (i+1, k)
+            vc = sv[(r + 1) * W + t];       // (i, k+1)
+            vd = sv[(r + 1) * W + t + 1];   // (i+1, k+1)
+        }
+        const uint32_t q = (uint32_t)k * (uint32_t)m.N + (uint32_t)i;
+        if (FACE == 0) {
+            BoxT<PREC> b1, b2;
+            if (col_valid) {
+                box_init(b1, vb); box_add(b1, va); box_add(b1, vc);   // T1: x1=(i+1,k) x2=(i,k) x3=(i,k+1)
+                box_init(b2, vc); box_add(b2, vd); box_add(b2, vb);   // T2: x1=(i,k+1) x2=(i+1,k+1) x3=(i+1,k)
+            }
+            if (a.mode == MODE_BOUNDS) {
+                if (col_valid) { acc.add(b1); acc.add(b2); }
+            } else {
+                face_cells<PREC>(a, g, col_valid, b1, 2 * q, pe.pair, pe.role);
+                face_cells<PREC>(a, g, col_valid, b2, 2 * q + 1, pe.pair, pe.role);
+            }
+        } else {
+            BoxT<PREC> bq;
+            if (col_valid) { box_init(bq, va); box_add(bq, vb); box_add(bq, vc); box_add(bq, vd); }
+            if (a.mode == MODE_BOUNDS) {
+                if (col_valid) acc.add(bq);
+            } else {
+                face_cells<PREC>(a, g, col_valid, bq, q, pe.pair, pe.role);
+            }
+        }
+    }
+
+    if (a.mode == MODE_BOUNDS) {
+        // block reduction, then one set of atomics per block
+        __shared__ double red[8][13];
+        __shared__ unsigned redf[8][2];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            for (int off = 16; off > 0; off >>= 1) {
+                acc.lo[d] = min(acc.lo[d], __shfl_xor_sync(FULL, acc.lo[d], off));
+                acc.hi[d] = max(acc.hi[d], __shfl_xor_sync(FULL, acc.hi[d], off));
+                acc.w[d] = max(acc.w[d], __shfl_xor_sync(FULL, acc.w[d], off));
+            }
+        }
+        unsigned fl = __reduce_or_sync(FULL, nonfinite);
+        unsigned seen = __reduce_or_sync(FULL, acc.seen);
+        if (lane == 0) {
+#pragma unroll
+            for (int d = 0; d < 4; ++d) { red[warp][d] = acc.get_lo(d); red[warp][4 + d] = acc.get_hi(d); red[warp][8 + d] = acc.get_w(d); }
+            redf[warp][0] = fl;
+            redf[warp][1] = seen;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int nw = blockDim.x >> 5;
+            Bounds *B = a.bounds + pe.mesh;
+            unsigned f = 0, s = 0;
+            for (int w = 0; w < nw; ++w) { f |= redf[w][0]; s |= redf[w][1]; }
+            if (s) {
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    double l = red[0][d], h = red[0][4 + d], ww = red[0][8 + d];
+                    for (int w = 1; w < nw; ++w) {
+                        l = fmin(l, red[w][d]);
+                        h = fmax(h, red[w][4 + d]);
+                        ww = fmax(ww, red[w][8 + d]);
+                    }
+                    atomicMin(&B->lo[d], ord_enc(l));
+                    atomicMax(&B->hi[d], ord_enc(h));
+                    atomicMax(&B->w[d], ord_enc(ww));
+                }
+                atomicOr(&B->faces, 1u);
+            }
+            if (f) {
+                atomicOr(&B->flags, ST_NONFINITE);
+                atomicOr(&a.ctr->status, ST_NONFINITE);
+            }
+        }
+    }
+}
+
+__global__ void k_bounds_init(Bounds *b, int n) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) { b[m].lo[d] = ~0ULL; b[m].hi[d] = 0ULL; b[m].w[d] = 0ULL; }
+    b[m].flags = 0;
+    b[m].faces = 0;
+}
+
+// Trimmed world and uniform grid of each pair (Sec. 5.2.1 and its remark).
+// World along coordinate d: the overlap of the two meshes' ranges; a face whose
+// box misses it cannot meet any face of the other mesh.  Cell edge: cell_mult x
+// the widest face extent of either mesh, so that a face spans at most two cells
+// per coordinate; capped so that a pair's grid has fewer than 2^31 cells.
+__global__ void k_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *grids,
+                              float cell_mult) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pairs) return;
+    const Bounds &A = b[pairs[p].x];
+    const Bounds &B = b[pairs[p].y];
+    Grid G;
+    memset(&G, 0, sizeof(G));
+    int empty = (A.faces == 0 || B.faces == 0) ? 1 : 0;
+    double o[4], e[4], step[4];
+    for (int d = 0; d < 4; ++d) {
+        o[d] = fmax(ord_dec(A.lo[d]), ord_dec(B.lo[d]));
+        e[d] = fmin(ord_dec(A.hi[d]), ord_dec(B.hi[d]));
+        if (!(o[d] <= e[d])) empty = 1;
+        double w = fmax(ord_dec(A.w[d]), ord_dec(B.w[d]));
+        step[d] = (double)cell_mult * w;
+    }
+    int n[4];
+    double range[4];
+    for (int d = 0; d < 4; ++d) {
+        range[d] = empty ? 0.0 : e[d] - o[d];
+        if (!(range[d] > 0.0) || !(step[d] > 0.0)) {
+            n[d] = 1;
+            step[d] = 0.0;
+            continue;
+        }
+        if (range[d] / step[d] > (double)(kMaxCellsPerDim - 1)) step[d] = range[d] / (double)(kMaxCellsPerDim - 1);
+        n[d] = (int)floor(range[d] / step[d]) + 1;
+        if (n[d] > kMaxCellsPerDim) n[d] = kMaxCellsPerDim;
+    }
+    const double cap = 2147483647.0;
+    for (int iter = 0; iter < 64; ++iter) {
+        double prod = (double)n[0] * n[1] * n[2] * n[3];
+        if (prod <= cap) break;
+        double f = pow(prod / cap, 0.25) * 1.001;
+        for (int d = 0; d < 4; ++d) {
+            if (n[d] <= 1) continue;
+            step[d] *= f;
+            n[d] = (int)floor(range[d] / step[d]) + 1;
+            if (n[d] < 1) n[d] = 1;
+        }
+    }
+    for (int d = 0; d < 4; ++d) {
+        G.o64[d] = o[d];
+        G.e64[d] = e[d];
+        G.inv64[d] = (step[d] > 0.0) ? 1.0 / step[d] : 0.0;
+        G.o32[d] = (float)o[d];
+        G.e32[d] = (float)e[d];
+        G.inv32[d] = (float)G.inv64[d];
+        G.n[d] = n[d];
+    }
+    G.empty = empty;
+    grids[p] = G;
+}
+
+template <int PREC, int FACE, int TK>
+void launch_one(const FacePassArgs &a, int block, cudaStream_t st) {
+    size_t smem = (size_t)(TK + 1) * (block + 1) * sizeof(Vtx<PREC>);
+    k_face_pass<PREC, FACE, TK><<<(unsigned)a.total_tiles, block, smem, st>>>(a);
+}
+
+template <int PREC, int FACE>
+void launch_tk(const FacePassArgs &a, int block, cudaStream_t st) {
+    if (a.tile_rows == 4) launch_one<PREC, FACE, 4>(a, block, st);
+    else launch_one<PREC, FACE, 8>(a, block, st);
+}
+
+template <int PREC, int FACE, int TK>
+cudaError_t configure_one() {
+    return cudaFuncSetAttribute(k_face_pass<PREC, FACE, TK>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+}
+
+}  // namespace
+
+// Sets kernel attributes once, before any launch (and outside stream capture).
+cudaError_t configure_face_pass() {
+    cudaError_t e = cudaSuccess;
+    cudaError_t r;
+#define TMS_CFG(P, F, T) if ((r = configure_one<P, F, T>()) != cudaSuccess) e = r;
+    TMS_CFG(0, 0, 4) TMS_CFG(0, 0, 8) TMS_CFG(0, 1, 4) TMS_CFG(0, 1, 8)
+    TMS_CFG(1, 0, 4) TMS_CFG(1, 0, 8) TMS_CFG(1, 1, 4) TMS_CFG(1, 1, 8)
+#undef TMS_CFG
+    return e;
+}
+
+void launch_face_pass(const FacePassArgs &a, int precision, int face_level, int block,
+                      cudaStream_t st) {
+    if (a.total_tiles <= 0) return;
+    if (precision == 1) {
+        if (face_level == 0) launch_tk<1, 0>(a, block, st); else launch_tk<1, 1>(a, block, st);
+    } else {
+        if (face_level == 0) launch_tk<0, 0>(a, block, st); else launch_tk<0, 1>(a, block, st);
+    }
+}
+
+void launch_bounds_init(Bounds *b, int n, cudaStream_t st) {
+    k_bounds_init<<<(n + 127) / 128, 128, 0, st>>>(b, n);
+}
+
+void launch_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *g,
+                        float cell_mult, cudaStream_t st) {
+    k_grid_params<<<(n_pairs + 127) / 128, 128, 0, st>>>(b, pairs, n_pairs, g, cell_mult);
+}
+
+}  // namespace tms

@@ -1,0 +1,265 @@
+// Cell ranges and candidate-pair emission of the broad phase.
+//
+// After the sort, entries of one (pair, cell) are contiguous with mesh A's
+// entries first (the role is the key's lowest bit).  Per cell we need the start
+// of its A list and B list and nA * nB, the number of face pairs it proposes;
+// the exclusive scan of nA * nB is the paper's box_gid_idxs array (Sec. 5.3,
+// Algorithm 1).  Emission assigns one thread per proposed pair, as Algorithm 1
+// does, but finds its cell by binary search over that scan instead of a linear
+// walk, applies the bounding-box test of Sec. 5.2.2, keeps the pair only in its
+// owner cell (the componentwise max of the two faces' lowest cells -- each pair
+// sharing several cells is emitted exactly once), optionally applies the Moller
+// quick test of Sec. 5.2.3, and compacts survivors with one atomic per warp.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tms_common.cuh"
+
+namespace tms {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__global__ void k_cell_heads(const uint64_t *keys, const unsigned long long *d_n,
+                             unsigned long long cap, uint32_t *head) {
+    const unsigned long long n = clamp_count(d_n, cap);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        head[i] = (i == 0 || (keys[i] >> 1) != (keys[i - 1] >> 1)) ? 1u : 0u;
+    }
+}
+
+// cell index of entry i = exclusive scan of heads + head - 1
+__global__ void k_cell_fill(const uint64_t *keys, const uint32_t *head, const uint32_t *hscan,
+                            const unsigned long long *d_n, unsigned long long cap,
+                            uint32_t *cell_start, uint32_t *cell_b) {
+    const unsigned long long n = clamp_count(d_n, cap);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t h = head[i];
+        const uint32_t c = hscan[i] + h - 1;
+        if (h) cell_start[c] = (uint32_t)i;
+        const bool isB = keys[i] & 1;
+        if (isB && (h || !(keys[i - 1] & 1))) cell_b[c] = (uint32_t)i;
+    }
+}
+
+__global__ void k_cell_pairs(const uint32_t *cell_start, uint32_t *cell_b,
+                             const unsigned long long *d_cells, const unsigned long long *d_n,
+                             unsigned long long cap, unsigned long long *pairs) {
+    const unsigned long long nc = clamp_count(d_cells, cap);
+    const unsigned long long n = clamp_count(d_n, cap);
+    for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nc;
+         c += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t s = cell_start[c];
+        const uint32_t e = (c + 1 < nc) ? cell_start[c + 1] : (uint32_t)n;
+        uint32_t b = cell_b[c];
+        if (b == 0xFFFFFFFFu || b < s || b > e) b = e;
+        cell_b[c] = b;
+        pairs[c] = (unsigned long long)(b - s) * (unsigned long long)(e - b);
+    }
+}
+
+__global__ void k_fill_u32(uint32_t *p, const unsigned long long *d_n, unsigned long long cap,
+                           uint32_t v) {
+    const unsigned long long n = clamp_count(d_n, cap);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// emission
+// ---------------------------------------------------------------------------
+template <int PREC>
+struct EBox;
+template <>
+struct EBox<1> {
+    float lo[4], hi[4];
+    __device__ void load(const EmitArgs &a, uint32_t e) {
+        float4 l = a.ent_box32[2 * (size_t)e], h = a.ent_box32[2 * (size_t)e + 1];
+        lo[0] = l.x; lo[1] = l.y; lo[2] = l.z; lo[3] = l.w;
+        hi[0] = h.x; hi[1] = h.y; hi[2] = h.z; hi[3] = h.w;
+    }
+    __device__ void cells(const Grid &g, int c[4]) const {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) c[d] = cell_of(lo[d], g.o32[d], g.inv32[d], g.n[d]);
+    }
+};
+template <>
+struct EBox<0> {
+    double lo[4], hi[4];
+    __device__ void load(const EmitArgs &a, uint32_t e) {
+        const double2 *p = reinterpret_cast<const double2 *>(a.ent_box64 + 8 * (size_t)e);
+        double2 x0 = p[0], x1 = p[1], x2 = p[2], x3 = p[3];
+        lo[0] = x0.x; lo[1] = x0.y; lo[2] = x1.x; lo[3] = x1.y;
+        hi[0] = x2.x; hi[1] = x2.y; hi[2] = x3.x; hi[3] = x3.y;
+    }
+    __device__ void cells(const Grid &g, int c[4]) const {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) c[d] = cell_of(lo[d], g.o64[d], g.inv64[d], g.n[d]);
+    }
+};
+
+// Moller quick test (Sec. 5.2.3) on the (x, y, px) projection.  The plane of a
+// triangle (x1, x2, x3) has normal (x1 - x2) x (x3 - x2); a point set lies
+// strictly on one side when f = n . (X - x2) has one strict sign at all points.
+// A rounding guard makes the test conservative: a value counts as signed only
+// beyond a bound on its rounding error.
+__device__ __forceinline__ bool same_side(const double x1[4], const double x2[4], const double x3[4],
+                                          const double (*P)[4], int np) {
+    double u[3], v[3];
+    for (int c = 0; c < 3; ++c) { u[c] = x1[c] - x2[c]; v[c] = x3[c] - x2[c]; }
+    double nrm[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    double un = fabs(u[0]) + fabs(u[1]) + fabs(u[2]);
+    double vn = fabs(v[0]) + fabs(v[1]) + fabs(v[2]);
+    int pos = 0, neg = 0;
+    for (int j = 0; j < np; ++j) {
+        double w[3];
+        for (int c = 0; c < 3; ++c) w[c] = P[j][c] - x2[c];
+        double f = nrm[0] * w[0] + nrm[1] * w[1] + nrm[2] * w[2];
+        double wn = fabs(w[0]) + fabs(w[1]) + fabs(w[2]);
+        double guard = 32.0 * 1.1102230246251565e-16 * un * vn * wn;
+        if (f > guard) ++pos;
+        else if (f < -guard) ++neg;
+    }
+    return pos == np || neg == np;
+}
+
+__device__ __forceinline__ void face_vertices(const MeshDev &m, uint32_t face, int face_level,
+                                              double V[4][4], int &nv) {
+    if (face_level == 0) {
+        int ii[3], kk[3];
+        tri_ij(m, face, ii, kk);
+        for (int j = 0; j < 3; ++j) load_vertex(m, ii[j], kk[j], V[j]);
+        nv = 3;
+    } else {
+        int i = (int)(face % (uint32_t)m.N), k = (int)(face / (uint32_t)m.N);
+        int ip = (i + 1 == m.N) ? 0 : i + 1;
+        load_vertex(m, i, k, V[0]);        // (i, k)
+        load_vertex(m, ip, k, V[1]);       // (i+1, k)
+        load_vertex(m, i, k + 1, V[2]);    // (i, k+1)
+        load_vertex(m, ip, k + 1, V[3]);   // (i+1, k+1)
+        nv = 4;
+    }
+}
+
+// true when the Moller test proves the two faces disjoint
+__device__ bool moller_reject(const MeshDev &ma, uint32_t fa, const MeshDev &mb, uint32_t fb,
+                              int face_level) {
+    double VA[4][4], VB[4][4];
+    int na, nb;
+    face_vertices(ma, fa, face_level, VA, na);
+    face_vertices(mb, fb, face_level, VB, nb);
+    if (face_level == 0) {
+        // vertices of T_B all on one side of T_A's plane, or the reverse
+        if (same_side(VA[0], VA[1], VA[2], VB, 3)) return true;
+        return same_side(VB[0], VB[1], VB[2], VA, 3);
+    }
+    // quads: all four vertices of one quad on one side of the planes of both
+    // triangles of the other (T1 = (i+1,k),(i,k),(i,k+1); T2 = (i,k+1),(i+1,k+1),(i+1,k))
+    if (same_side(VA[1], VA[0], VA[2], VB, 4) && same_side(VA[2], VA[3], VA[1], VB, 4)) return true;
+    return same_side(VB[1], VB[0], VB[2], VA, 4) && same_side(VB[2], VB[3], VB[1], VA, 4);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_emit(EmitArgs a, int face_level) {
+    // nothing to do after an entry overflow (the host retries with more room),
+    // and a bounded amount of work in any case
+    if (a.ctr->entries > a.ent_cap) return;
+    if (a.ctr->pair_slots > kMaxPairSlots) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctr->status, ST_PAIR_LIMIT);
+        return;
+    }
+    const unsigned long long total = a.ctr->pair_slots;
+    const unsigned long long ncell = clamp_count(&a.ctr->cells, a.ent_cap);
+    const unsigned long long nent = clamp_count(&a.ctr->entries, a.ent_cap);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    // whole warps iterate together so that compaction can use the full mask
+    const unsigned long long start = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    for (unsigned long long g0 = start - (threadIdx.x & 31); g0 < total; g0 += stride) {
+        const unsigned long long g = g0 + (threadIdx.x & 31);
+        bool keep = false;
+        uint32_t fa = 0, fb = 0, pair = 0;
+        if (g < total) {
+            // cell c: last cell with pair_off[c] <= g
+            unsigned long long lo = 0, hi = ncell - 1;
+            while (lo < hi) {
+                unsigned long long mid = (lo + hi + 1) >> 1;
+                if (a.pair_off[mid] <= g) lo = mid; else hi = mid - 1;
+            }
+            const unsigned long long c = lo;
+            const uint32_t s = a.cell_start[c];
+            const uint32_t b = a.cell_b[c];
+            const unsigned long long nA = b - s;
+            const unsigned long long local = g - a.pair_off[c];
+            const uint32_t ia = (uint32_t)(local % nA), ib = (uint32_t)(local / nA);
+            if (b + ib < nent) {
+                const uint32_t ea = a.vals[s + ia], eb = a.vals[b + ib];
+                const uint64_t key = a.keys[s];
+                pair = (uint32_t)(key >> 32);
+                const Grid &gr = a.grids[pair];
+                EBox<PREC> A, B;
+                A.load(a, ea);
+                B.load(a, eb);
+                // bounding-box test (Sec. 5.2.2): disjoint iff some coordinate's
+                // max of one box is below the other's min
+                bool ov = true;
+#pragma unroll
+                for (int d = 0; d < 4; ++d) ov &= !(A.hi[d] < B.lo[d] || B.hi[d] < A.lo[d]);
+                if (ov) {
+                    int ca[4], cb[4];
+                    A.cells(gr, ca);
+                    B.cells(gr, cb);
+                    const uint2 cc = a.ent_cell[ea];
+                    const int cur[4] = {(int)(cc.x & 0xFFFF), (int)(cc.x >> 16), (int)(cc.y & 0xFFFF),
+                                        (int)(cc.y >> 16)};
+                    bool owner = true;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) owner &= (max(ca[d], cb[d]) == cur[d]);
+                    if (owner) {
+                        fa = a.ent_face[ea];
+                        fb = a.ent_face[eb];
+                        keep = true;
+                        if (a.moller) {
+                            const int2 pr = a.pairs[pair];
+                            keep = !moller_reject(a.meshes[pr.x], fa, a.meshes[pr.y], fb, face_level);
+                        }
+                    }
+                }
+            }
+        }
+        const unsigned long long pos = warp_append(&a.ctr->cand, keep, FULL);
+        if (keep && pos < a.cand_cap) {
+            Cand cd;
+            cd.faceA = fa;
+            cd.faceB = fb;
+            cd.pair = pair;
+            cd.pad = 0;
+            a.cand[pos] = cd;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_cells(const CellArgs &a, int grid, cudaStream_t st) {
+    const int B = 256;
+    k_cell_heads<<<grid, B, 0, st>>>(a.keys, a.d_n, a.cap, a.head);
+    scan_u32(a.head, a.head_scan, a.d_n, a.cap, a.partials, &a.ctr->cells, grid, st);
+    k_fill_u32<<<grid, B, 0, st>>>(a.cell_b, &a.ctr->cells, a.cap, 0xFFFFFFFFu);
+    k_cell_fill<<<grid, B, 0, st>>>(a.keys, a.head, a.head_scan, a.d_n, a.cap, a.cell_start,
+                                    a.cell_b);
+    k_cell_pairs<<<grid, B, 0, st>>>(a.cell_start, a.cell_b, &a.ctr->cells, a.d_n, a.cap,
+                                     a.cell_pairs);
+    scan_u64(a.cell_pairs, a.pair_off, &a.ctr->cells, a.cap, a.partials, &a.ctr->pair_slots, grid,
+             st);
+}
+
+void launch_emit(const EmitArgs &a, int precision, int face_level, int grid, cudaStream_t st) {
+    if (precision == 1) k_emit<1><<<grid, 256, 0, st>>>(a, face_level);
+    else k_emit<0><<<grid, 256, 0, st>>>(a, face_level);
+}
+
+}  // namespace tms

@@ -1,0 +1,250 @@
+"""GPU parity tests: the CUDA search through the C ABI against the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2109_14814_gb300 as tms
+import synth
+from tests import meshcases
+from tests.parity import check_sorted_unique, compare, gpu_records
+
+pytestmark = pytest.mark.gpu
+
+_cache = {}
+
+
+def cached(name, fn):
+    if name not in _cache:
+        _cache[name] = fn()
+    return _cache[name]
+
+
+def oracle_hits(name, pair):
+    def run():
+        OA, OB = oracle.OMesh.from_grid(pair.A), oracle.OMesh.from_grid(pair.B)
+        return OA, OB, oracle.search(OA, OB)
+    return cached("oracle:" + name, run)
+
+
+def gpu_search(pair, **kw):
+    A = tms.Mesh.from_grid(pair.A)
+    B = tms.Mesh.from_grid(pair.B)
+    h = tms.search(A, B, **kw)
+    torch.cuda.synchronize()
+    return gpu_records(h)
+
+
+# ---------------------------------------------------------------------------
+# hand-solved meshes: exact results
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", sorted(meshcases.ALL_CASES))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_hand_solved_cases_exact(name, precision):
+    A, B, exp, _ = meshcases.ALL_CASES[name]()
+    g = gpu_search(synth.MeshPair(A, B, None), precision=precision)
+    assert len(g["triA"]) == len(exp)
+    for h, e in enumerate(exp):
+        assert (int(g["triA"][h]), int(g["triB"][h])) == (e["triA"], e["triB"])
+        tol = 0.0 if name != "seam" else 1e-12
+        assert np.abs(g["z"][h] - np.array(e["z"])).max() <= tol
+        assert np.abs(g["P"][h] - np.array(e["P"])).max() <= (0.0 if name != "seam" else 1e-14)
+        if "params" in e:
+            assert np.allclose(g["params"][h], e["params"], rtol=0, atol=1e-15)
+    if name in ("diagonal", "vertex"):
+        assert int(g["flags"][0]) & 2
+
+
+# ---------------------------------------------------------------------------
+# synthetic configurations against the oracle
+# ---------------------------------------------------------------------------
+
+def test_config1_parity_and_planted():
+    p = cached("c1", synth.config1)
+    OA, OB, ref = oracle_hits("c1", p)
+    g = gpu_search(p)
+    check_sorted_unique(g)
+    s = compare(OA, OB, g, ref)
+    assert s["common"] >= 5
+    keys = set(zip(g["triA"].tolist(), g["triB"].tolist()))
+    for a, b in zip(p.planted.triA.tolist(), p.planted.triB.tolist()):
+        assert (a, b) in keys
+
+
+def test_config2_parity():
+    p = cached("c2", synth.config2)
+    OA, OB, ref = oracle_hits("c2", p)
+    g = gpu_search(p)
+    check_sorted_unique(g)
+    s = compare(OA, OB, g, ref)
+    assert s["common"] >= 64
+
+
+def test_config5_parity():
+    p = cached("c5", synth.config5)
+    OA, OB, ref = oracle_hits("c5", p)
+    g = gpu_search(p)
+    s = compare(OA, OB, g, ref)
+    assert s["common"] >= 512
+
+
+VARIANTS = [
+    dict(precision=0),
+    dict(face_level=1),
+    dict(precision=0, face_level=1),
+    dict(moller=1),
+    dict(moller=1, face_level=1),
+    dict(cell_filter=0),
+    dict(narrow_filter=0),
+    dict(cell_mult=2.0),
+    dict(cell_mult=5.0),
+    dict(block_faces=64),
+    dict(block_faces=256),
+    dict(tile_rows=4),
+    dict(use_graph=0),
+]
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=lambda v: ",".join(f"{k}={x}" for k, x in v.items()))
+def test_variants_same_hit_set(variant):
+    """The hit set does not depend on precision mode, face level, Moller test,
+    occupancy filter, FP32 pre-solve, cell size, tiling or graph use."""
+    p = cached("c2", synth.config2)
+    OA, OB, ref = oracle_hits("c2", p)
+    base = gpu_search(p)
+    g = gpu_search(p, **variant)
+    assert list(zip(g["triA"], g["triB"])) == list(zip(base["triA"], base["triB"]))
+    compare(OA, OB, g, ref)
+
+
+def test_ragged_tiles_and_open_strip_against_bruteforce():
+    """Sizes that leave ragged tiles in both directions, an open strip (no
+    theta wrap), and a half-layer view of columns [k0, k1)."""
+    p = synth.build_pair(91, 131, 27, 75, 19, stretch="exp", n_folds=2, sites=(4, 2), n_hits=6)
+    OA, OB = oracle.OMesh.from_grid(p.A), oracle.OMesh.from_grid(p.B)
+    ref = oracle.search(OA, OB, method="brute")
+    g = gpu_search(p, block_faces=64, tile_rows=8)
+    compare(OA, OB, g, ref)
+    # open strip version of A
+    Ao = synth.MeshGrid(p.A.X, p.A.s, periodic=False)
+    OAo = oracle.OMesh.from_grid(Ao)
+    refo = oracle.search(OAo, OB, method="brute")
+    go = gpu_search(synth.MeshPair(Ao, p.B, None))
+    compare(OAo, OB, go, refo)
+    # half-layer view: columns [5, 21) of A
+    XA = p.A.X.cuda()
+    A = tms.Mesh(XA, p.A.s, True, k0=5, k1=21)
+    B = tms.Mesh.from_grid(p.B)
+    h = gpu_records(tms.search(A, B))
+    OAv = oracle.OMesh(p.A.X[:, 5:21].numpy(), p.A.s[5:21].numpy(), True)
+    refv = oracle.search(OAv, OB, method="brute")
+    compare(OAv, OB, h, refv)
+
+
+def test_minimal_meshes():
+    """N = 3 periodic, M = 2 (one quad row) against brute force."""
+    g0 = torch.Generator().manual_seed(5)
+    XA = torch.randn(4, 2, 3, generator=g0, dtype=torch.float64)
+    XB = XA.mean(dim=(1, 2), keepdim=True) + 0.7 * torch.randn(4, 2, 3, generator=g0, dtype=torch.float64)
+    for seed in range(20):
+        g0.manual_seed(seed)
+        XB = XA.mean(dim=(1, 2), keepdim=True) + 0.8 * torch.randn(4, 2, 3, generator=g0, dtype=torch.float64)
+        A = synth.MeshGrid(XA, torch.tensor([0.0, 1.0], dtype=torch.float64))
+        B = synth.MeshGrid(XB, torch.tensor([0.0, 1.0], dtype=torch.float64))
+        OA, OB = oracle.OMesh.from_grid(A), oracle.OMesh.from_grid(B)
+        ref = oracle.search(OA, OB, method="brute")
+        g = gpu_search(synth.MeshPair(A, B, None))
+        compare(OA, OB, g, ref)
+
+
+def test_disjoint_meshes_empty_world():
+    p = cached("c1", synth.config1)
+    XB = p.B.X + 1000.0
+    g = gpu_search(synth.MeshPair(p.A, synth.MeshGrid(XB, p.B.s), None))
+    assert len(g["triA"]) == 0
+    assert tms.last_stats()["empty"] == 1
+
+
+@pytest.mark.slow
+def test_config3_full_size_sampled_parity():
+    """4096 x 512 meshes in the benchmark's launch configuration: planted hits
+    with closed forms, no planted near-miss reported, every GPU hit confirmed by
+    the oracle, and exact per-triangle parity on sampled A triangles."""
+    p = synth.config3()
+    OA, OB = oracle.OMesh.from_grid(p.A), oracle.OMesh.from_grid(p.B)
+    g = gpu_search(p)
+    check_sorted_unique(g)
+    keys = {k: h for h, k in enumerate(zip(g["triA"].tolist(), g["triB"].tolist()))}
+    pl = p.planted
+    for j in range(len(pl)):
+        k = (int(pl.triA[j]), int(pl.triB[j]))
+        if int(pl.kind[j]) == 1:
+            assert k not in keys
+            continue
+        h = keys[k]
+        assert np.abs(g["z"][h] - pl.abcd[j].numpy()).max() <= 1e-10
+        assert np.abs(g["P"][h] - pl.P[j].numpy()).max() <= 1e-10 * max(1, np.abs(pl.P[j].numpy()).max())
+    r = oracle.eval_pairs(OA, OB, g["triA"], g["triB"])
+    assert ((r["hit"] == 1) | oracle.in_band(r)).all()
+    rng = np.random.default_rng(11)
+    sample = np.unique(np.concatenate([rng.choice(OA.n_tri_ids, 300, replace=False),
+                                       g["triA"][rng.choice(len(g["triA"]), 300, replace=False)]]))
+    ref = oracle.merge_and_sort(OA, OB, oracle.hits_for_A(OA, OB, sample))
+    compare(OA, OB, g, ref, restrict_A=sample)
+
+
+# ---------------------------------------------------------------------------
+# errors and fault injection (host side; no GPU fault)
+# ---------------------------------------------------------------------------
+
+def test_nonfinite_vertex_rejected():
+    p = cached("c1", synth.config1)
+    X = p.A.X.clone()
+    X[2, 5, 7] = float("nan")
+    A = tms.Mesh(X.cuda(), p.A.s)
+    B = tms.Mesh.from_grid(p.B)
+    with pytest.raises(tms.TmsError) as e:
+        tms.search(A, B)
+    assert e.value.status == tms.TMS_ERR_ARG
+
+
+def test_capacity_retry_and_injected_errors():
+    p = cached("c2", synth.config2)
+    base = gpu_search(p)
+    A = tms.Mesh.from_grid(p.A)
+    B = tms.Mesh.from_grid(p.B)
+    # forced tiny entry capacity: the library grows its scratch and retries
+    h = gpu_records(tms.search(A, B, inject=1))
+    assert list(zip(h["triA"], h["triB"])) == list(zip(base["triA"], base["triB"]))
+    assert tms.last_stats()["retries"] >= 1
+    # too-small output buffer: TMS_ERR_CAPACITY with the required count
+    out = torch.empty((3, tms.HIT_BYTES), dtype=torch.uint8, device="cuda")
+    with pytest.raises(tms.TmsError) as e:
+        tms.search(A, B, out=out)
+    assert e.value.status == tms.TMS_ERR_CAPACITY
+    with pytest.raises(tms.TmsError) as e:
+        tms.search(A, B, inject=2)
+    assert e.value.status == tms.TMS_ERR_CAPACITY
+    with pytest.raises(tms.TmsError) as e:
+        tms.search(A, B, inject=4)
+    assert e.value.status == tms.TMS_ERR_TIMEOUT
+    # the context is still usable
+    h = gpu_records(tms.search(A, B))
+    assert len(h["triA"]) == len(base["triA"])
+
+
+def test_bad_arguments():
+    p = cached("c1", synth.config1)
+    X = p.A.X.cuda()
+    with pytest.raises(tms.TmsError):
+        tms.Mesh(X, p.A.s.flip(0))                 # s not increasing
+    with pytest.raises(tms.TmsError):
+        tms.Mesh(X, p.A.s, k0=3, k1=4)             # fewer than 2 columns
+    with pytest.raises(KeyError):
+        tms.params(no_such_field=1)
+    A = tms.Mesh(X, p.A.s)
+    with pytest.raises(tms.TmsError):
+        tms.search(A, A, cell_mult=0.5)            # cells narrower than faces
