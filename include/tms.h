@@ -92,9 +92,9 @@ typedef struct {
     int precision;        /* broad-phase arithmetic: 0 = FP64 boxes and cell keys
                              (plain); 1 = FP32 boxes rounded outward and FP32 cell
                              keys (mixed, default).  The narrow phase is FP64. */
-    int face_level;       /* 0 = one box per triangle (default); 1 = one box per
-                             quad, as the paper's kernel (4 triangle pairs per
-                             candidate). */
+    int face_level;       /* 0 = one box per triangle; 1 = one box per quad, as
+                             the paper's kernel (4 triangle pairs per candidate;
+                             default). */
     int moller;           /* 1 = apply the Moller quick test of Sec. 5.2.3 (FP64,
                              with a rounding guard) to candidates; default 0. */
     int cell_filter;      /* 1 = register only faces in grid cells occupied by

@@ -91,8 +91,12 @@ struct Plan {
     uint32_t *sort_counts = nullptr;
     unsigned long long *partials = nullptr;
     uint32_t *head = nullptr, *hscan = nullptr, *cstart = nullptr, *cb = nullptr;
-    unsigned long long *cpairs = nullptr, *poff = nullptr;
-    Cand *cand = nullptr;
+    unsigned long long *cpairs = nullptr, *poff = nullptr, *ctiles = nullptr, *toff = nullptr;
+    Cand *cand = nullptr, *surv = nullptr;
+    float4 *split = nullptr;          // FP32 split vertex copies of all meshes
+    unsigned long long split_total = 0;
+    std::vector<unsigned long long> split_off;
+    unsigned long long surv_cap = 0;
     tms_hit *hits = nullptr;
     uint64_t *hk = nullptr, *hk2 = nullptr, *okeys = nullptr;
     uint32_t *hv = nullptr, *hv2 = nullptr, *keep = nullptr, *kscan = nullptr;
@@ -110,13 +114,13 @@ struct Plan {
 
     void free_scratch() {
         void *ptrs[] = {bmA, bmH, ek, ek2, ev, ev2, eface, ecell, ebox32, ebox64, sort_counts,
-                        head, hscan, cstart, cb, cpairs, poff, cand, hits, hk, hk2, okeys, hv,
-                        hv2, keep, kscan};
+                        head, hscan, cstart, cb, cpairs, poff, ctiles, toff, cand, surv, hits, hk,
+                        hk2, okeys, hv, hv2, keep, kscan};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         bmA = bmH = nullptr; ek = ek2 = nullptr; ev = ev2 = eface = nullptr; ecell = nullptr;
         ebox32 = nullptr; ebox64 = nullptr; sort_counts = nullptr; head = hscan = cstart = cb = nullptr;
-        cpairs = poff = nullptr; cand = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
+        cpairs = poff = ctiles = toff = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
         hv = hv2 = keep = kscan = nullptr;
         if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
     }
@@ -124,7 +128,7 @@ struct Plan {
         if (st) cudaStreamSynchronize(st);
         free_scratch();
         void *ptrs[] = {d_meshes, d_pairs, d_pass_all, d_pass_A, d_pass_B, d_bounds, d_grids,
-                        d_ctr, partials};
+                        d_ctr, partials, split};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         if (h_ctr) cudaFreeHost(h_ctr);
@@ -156,7 +160,10 @@ struct Plan {
         TMS_CK(dalloc(&cb, ent_cap));
         TMS_CK(dalloc(&cpairs, ent_cap));
         TMS_CK(dalloc(&poff, ent_cap));
+        TMS_CK(dalloc(&ctiles, ent_cap));
+        TMS_CK(dalloc(&toff, ent_cap));
         TMS_CK(dalloc(&cand, cand_cap));
+        TMS_CK(dalloc(&surv, surv_cap));
         TMS_CK(dalloc(&hits, hit_cap));
         TMS_CK(dalloc(&hk, hit_cap));
         TMS_CK(dalloc(&hk2, hit_cap));
@@ -169,8 +176,13 @@ struct Plan {
     }
 
     // The whole search as a stream-ordered launch sequence (no host round trip).
+    // inside stream capture an event record becomes a graph node only with the
+    // external flag
+    bool capturing = false;
     void mark(int i, cudaStream_t s) {
-        if (prm.timing) cudaEventRecord(tev[i], s);
+        if (!prm.timing) return;
+        if (capturing) cudaEventRecordWithFlags(tev[i], s, cudaEventRecordExternal);
+        else cudaEventRecord(tev[i], s);
     }
 
     void enqueue(cudaStream_t s) {
@@ -251,13 +263,14 @@ struct Plan {
         CellArgs ca;
         ca.keys = sk; ca.d_n = &d_ctr->entries; ca.cap = ent_cap;
         ca.head = head; ca.head_scan = hscan; ca.cell_start = cstart; ca.cell_b = cb;
-        ca.cell_pairs = cpairs; ca.pair_off = poff; ca.partials = partials; ca.ctr = d_ctr;
+        ca.cell_pairs = cpairs; ca.pair_off = poff; ca.cell_tiles = ctiles; ca.tile_off = toff;
+        ca.partials = partials; ca.ctr = d_ctr;
         launch_cells(ca, grid, s);
-        kernels += 10;
+        kernels += 13;
         mark(9, s);
 
         EmitArgs ea;
-        ea.keys = sk; ea.vals = sv; ea.cell_start = cstart; ea.cell_b = cb; ea.pair_off = poff;
+        ea.keys = sk; ea.vals = sv; ea.cell_start = cstart; ea.cell_b = cb; ea.tile_off = toff;
         ea.ent_face = eface; ea.ent_cell = ecell; ea.ent_box32 = ebox32; ea.ent_box64 = ebox64;
         ea.grids = d_grids; ea.meshes = d_meshes; ea.pairs = d_pairs; ea.ctr = d_ctr;
         ea.ent_cap = ent_cap; ea.cand = cand; ea.cand_cap = cand_cap; ea.moller = p.moller;
@@ -266,15 +279,18 @@ struct Plan {
         mark(10, s);
 
         NarrowArgs na;
-        na.cand = cand; na.cand_cap = cand_cap; na.meshes = d_meshes; na.pairs = d_pairs;
+        na.cand = cand; na.cand_cap = cand_cap; na.surv = surv; na.surv_cap = surv_cap;
+        na.meshes = d_meshes; na.pairs = d_pairs;
         na.ctr = d_ctr; na.hits = hits; na.hit_key = hk; na.hit_val = hv; na.hit_cap = hit_cap;
         na.tau = p.tau; na.tri_bits = tri_bits; na.fp32_filter = p.narrow_filter;
         launch_narrow(na, fl, grid * 4, s);
-        kernels += 1;
+        kernels += 2;
         mark(11, s);
 
+        // the raw hits are few: a small grid keeps the per-pass fixed cost low
+        const int hgrid = std::max(1, std::min(grid, (int)((hit_cap + kSortTile * 8 - 1) / (kSortTile * 8))));
         const bool halt = radix_sort(hk, hv, hk2, hv2, sort_counts, &d_ctr->raw_hits, hit_cap,
-                                     2 * tri_bits + pair_bits, grid, s);
+                                     2 * tri_bits + pair_bits, hgrid, s);
         kernels += 3 * sort_passes_h;
         mark(12, s);
         DedupArgs da;
@@ -299,7 +315,9 @@ struct Plan {
             if (!exec) {
                 cudaGraph_t g = nullptr;
                 TMS_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                capturing = true;
                 enqueue(st);
+                capturing = false;
                 cudaError_t e = cudaStreamEndCapture(st, &g);
                 if (e != cudaSuccess) {
                     g_err = std::string("graph capture: ") + cudaGetErrorString(e);
@@ -417,6 +435,16 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
         fill_pass(pa, P->tiles_A, A[i], pairs[i].x, i, 0, block, rows);
         fill_pass(pb, P->tiles_B, B[i], pairs[i].y, i, 1, block, rows);
     }
+    // FP32 split vertex copies (32 bytes per view vertex), written by the bounds pass
+    for (auto &md : meshes) {
+        P->split_off.push_back(P->split_total);
+        P->split_total += 2ULL * (unsigned long long)md.N * (unsigned long long)md.M;
+    }
+    {
+        cudaError_t se = dalloc(&P->split, P->split_total);
+        if (se != cudaSuccess) { g_err = cudaGetErrorString(se); delete P; return TMS_ERR_CUDA; }
+        for (size_t i = 0; i < meshes.size(); ++i) meshes[i].split = P->split + P->split_off[i];
+    }
     P->n_meshes = (int)meshes.size();
     P->n_pass_all = (int)pall.size();
     P->n_pass_A = (int)pa.size();
@@ -467,6 +495,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
                                         : std::max<unsigned long long>(1 << 16, 2 * P->ent_cap);
     P->hit_cap = prm.hit_capacity > 0 ? (unsigned long long)prm.hit_capacity
                                       : std::max<unsigned long long>(1 << 14, P->cand_cap / 16);
+    P->surv_cap = std::max<unsigned long long>(1 << 16, P->cand_cap / 8);
     P->bmA_bits = std::min(26, std::max(11, ceil_log2(std::max<unsigned long long>(P->facesA, 1) * 8) - 5));
     P->bmH_bits = std::min(25, std::max(11, ceil_log2(P->ent_cap * 8) - 5));
     tms_status s = P->alloc_scratch();
@@ -558,6 +587,10 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
             P->cand_cap = c.cand + c.cand / 4 + 1024;
             grow = true;
         }
+        if (!grow && c.fp64 > P->surv_cap) {
+            P->surv_cap = c.fp64 + c.fp64 / 4 + 1024;
+            grow = true;
+        }
         if (!grow && c.raw_hits > P->hit_cap) {
             P->hit_cap = c.raw_hits + c.raw_hits / 4 + 1024;
             grow = true;
@@ -584,7 +617,8 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
     st.kernels = P->kernels;
     g_stats[user] = st;
     if (prm.timing) g_stage_ms[user] = std::vector<float>(P->stage_ms, P->stage_ms + Plan::kStages);
-    if (c.entries > P->ent_cap || c.cand > P->cand_cap || c.raw_hits > P->hit_cap) {
+    if (c.entries > P->ent_cap || c.cand > P->cand_cap || c.fp64 > P->surv_cap ||
+        c.raw_hits > P->hit_cap) {
         g_err = "scratch capacity still exceeded after retries";
         *nHits = (long long)c.out;
         return TMS_ERR_CAPACITY;
@@ -617,7 +651,7 @@ void tms_params_default(tms_params *p) {
     if (!p) return;
     memset(p, 0, sizeof(*p));
     p->precision = 1;
-    p->face_level = 0;
+    p->face_level = 1;
     p->moller = 0;
     p->cell_filter = 1;
     p->narrow_filter = 1;

@@ -45,6 +45,9 @@ enum StatusBits : unsigned int {
 struct MeshDev {
     const double *c[4];   // x, y, px, py, offset to the first view column
     const double *s;      // s values of the view (M entries), device
+    float4 *split;        // plan scratch: per view vertex (k*N + i) two float4,
+                          // hi = RN32(x) and lo = RN32(x - hi), written by the
+                          // bounds pass and gathered by the FP32 narrow filter
     int N;                // theta samples
     int M;                // vertex rows in the view
     int periodic;
@@ -81,6 +84,7 @@ struct Counters {
     unsigned long long entries;
     unsigned long long cells;
     unsigned long long pair_slots;
+    unsigned long long tiles;
     unsigned long long cand;
     unsigned long long fp64;
     unsigned long long raw_hits;
@@ -161,6 +165,64 @@ __device__ __forceinline__ unsigned long long warp_append(unsigned long long *co
         base = __shfl_sync(mask, base, leader);
     }
     return base + __popc(want & lanemask_lt());
+}
+
+// FP64 -> FP32 conversions from the IEEE-754 encodings, with integer operations
+// only (the FP64 pipe, which also carries FP64 conversions, is scarce on GB300).
+// Normal-range results equal round-down / round-up / round-to-nearest-even of
+// the value.  Outside the FP32 normal range the results are still valid bounds:
+// |x| < 2^-126 rounds outward to 0 or +-2^-126 (nearest: to +-0), |x| >= 2^128
+// to +-FLT_MAX or +-inf, NaN stays NaN.
+__device__ __forceinline__ unsigned f32_bits_trunc(unsigned long long b, int e32) {
+    return ((unsigned)(b >> 63) << 31) | ((unsigned)e32 << 23) |
+           (unsigned)((b & 0xFFFFFFFFFFFFFULL) >> 29);
+}
+__device__ __forceinline__ float f32_special(unsigned long long b, int e32, int dir) {
+    // dir: -1 down, +1 up, 0 nearest
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const bool is_nan = ((b >> 52) & 0x7ff) == 0x7ff && (b & 0xFFFFFFFFFFFFFULL) != 0;
+    if (is_nan) return __uint_as_float(0x7fc00000u);
+    if (e32 >= 255) {                       // |x| >= 2^128 or inf
+        const bool neg = sign != 0;
+        if (dir == 0) return __uint_as_float(sign | 0x7f800000u);
+        if (dir < 0) return __uint_as_float(neg ? 0xff800000u : 0x7f7fffffu);
+        return __uint_as_float(neg ? 0xff7fffffu : 0x7f800000u);
+    }
+    // |x| < 2^-126
+    const bool nonzero = (b & 0x7FFFFFFFFFFFFFFFULL) != 0;
+    if (dir == 0 || !nonzero) return __uint_as_float(sign);
+    const bool neg = sign != 0;
+    if (dir < 0) return neg ? -1.17549435e-38f : 0.0f;
+    return neg ? -0.0f : 1.17549435e-38f;
+}
+__device__ __forceinline__ float f32_rd(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e32 = (int)((b >> 52) & 0x7ff) - 896;
+    if (e32 <= 0 || e32 >= 255) return f32_special(b, e32, -1);
+    unsigned f = f32_bits_trunc(b, e32);
+    f += (unsigned)(b >> 63) & (unsigned)((b & 0x1FFFFFFFULL) != 0);   // negative, inexact
+    return __uint_as_float(f);
+}
+__device__ __forceinline__ float f32_ru(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e32 = (int)((b >> 52) & 0x7ff) - 896;
+    if (e32 <= 0 || e32 >= 255) return f32_special(b, e32, +1);
+    unsigned f = f32_bits_trunc(b, e32);
+    f += ((unsigned)(b >> 63) ^ 1u) & (unsigned)((b & 0x1FFFFFFFULL) != 0);  // positive, inexact
+    return __uint_as_float(f);
+}
+__device__ __forceinline__ float f32_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e32 = (int)((b >> 52) & 0x7ff) - 896;
+    if (e32 <= 0 || e32 >= 255) return f32_special(b, e32, 0);
+    unsigned f = f32_bits_trunc(b, e32) & 0x7fffffffu;
+    const unsigned rem = (unsigned)(b & 0x1FFFFFFFULL);
+    f += (unsigned)(rem > 0x10000000u) | ((unsigned)(rem == 0x10000000u) & (f & 1u));
+    return __uint_as_float(f | ((unsigned)(b >> 63) << 31));
+}
+// finiteness from the exponent bits (no FP64 compare)
+__device__ __forceinline__ bool finite64(double x) {
+    return (((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
 
 // cell index along one coordinate: monotone non-decreasing in v, clamped
@@ -257,8 +319,10 @@ struct CellArgs {
     uint32_t *head_scan;           // [cap]
     uint32_t *cell_start;          // [cap]
     uint32_t *cell_b;              // [cap]
-    unsigned long long *cell_pairs;  // [cap]
-    unsigned long long *pair_off;    // [cap]
+    unsigned long long *cell_pairs;  // [cap]  nA * nB
+    unsigned long long *pair_off;    // [cap]  exclusive scan of nA * nB
+    unsigned long long *cell_tiles;  // [cap]  32 x 32 tiles of the cell's pair matrix
+    unsigned long long *tile_off;    // [cap]  exclusive scan of the tiles
     unsigned long long *partials;
     Counters *ctr;
 };
@@ -269,9 +333,9 @@ struct EmitArgs {
     const uint32_t *vals;          // sorted entry indices
     const uint32_t *cell_start;
     const uint32_t *cell_b;
-    const unsigned long long *pair_off;
+    const unsigned long long *tile_off;
     const uint32_t *ent_face;
-    const uint2 *ent_cell;
+    const uint2 *ent_cell;          // lowest cell of the face box, 4 x u16
     const float4 *ent_box32;
     const double *ent_box64;
     const Grid *grids;
@@ -288,6 +352,8 @@ void launch_emit(const EmitArgs &a, int precision, int face_level, int grid, cud
 struct NarrowArgs {
     const Cand *cand;
     unsigned long long cand_cap;
+    Cand *surv;                    // triangle pairs left for the FP64 solve
+    unsigned long long surv_cap;
     const MeshDev *meshes;
     const int2 *pairs;
     Counters *ctr;
@@ -300,6 +366,28 @@ struct NarrowArgs {
     int fp32_filter;
 };
 void launch_narrow(const NarrowArgs &a, int face_level, int grid, cudaStream_t st);
+
+// FP32 split of a double: hi = RN32(x), lo = RN32(x - hi), integer operations
+// only in the normal range
+__device__ __forceinline__ void split_f32(double x, float &hi, float &lo) {
+    hi = f32_rn(x);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const int e32 = e - 896;
+    // x = sign * (2^52 + m) * 2^(e - 1075); the low 29 bits of m were rounded away
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+    const int rem = (int)(m & 0x1FFFFFFFULL);
+    const unsigned hb = __float_as_uint(hi) & 0x7fffffffu;
+    const unsigned trunc = ((unsigned)e32 << 23) | (unsigned)(m >> 29);
+    // rounded up (|hi| > |x|): x - hi = -(2^29 - rem) ulp, else +rem ulp (ulp = 2^(e-1075))
+    const int r = (hb != trunc) ? rem - (1 << 29) : rem;
+    const int ex = e - 1075 + 127;   // 2^(e - 1075) as an FP32 power of two
+    float l = 0.0f;
+    if (e32 > 0 && e32 < 255 && ex >= 1) l = __int2float_rn(r) * __uint_as_float((unsigned)ex << 23);
+    // outside that range lo is 0 and the caller's error bound carries an absolute
+    // term for coordinates below 2^-74
+    lo = (b >> 63) ? -l : l;
+}
 
 struct DedupArgs {
     const uint64_t *keys;          // sorted hit keys

@@ -77,13 +77,25 @@ __device__ __forceinline__ void box_add(BoxT<0> &b, const Vtx<0> &v) {
 __device__ __forceinline__ void to_vtx(const double x[4], Vtx<1> &v) {
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
-        v.lo[d] = __double2float_rd(x[d]);
-        v.hi[d] = __double2float_ru(x[d]);
+        v.lo[d] = f32_rd(x[d]);
+        v.hi[d] = f32_ru(x[d]);
     }
 }
 __device__ __forceinline__ void to_vtx(const double x[4], Vtx<0> &v) {
 #pragma unroll
     for (int d = 0; d < 4; ++d) v.v[d] = x[d];
+}
+
+// FP32 split copy of a vertex (hi and lo float4), gathered later by the FP32
+// narrow filter: one 32-byte record per vertex instead of four 8-byte loads
+__device__ __forceinline__ void write_split(const MeshDev &m, size_t idx, const double x[4]) {
+    float4 hi, lo;
+    split_f32(x[0], hi.x, lo.x);
+    split_f32(x[1], hi.y, lo.y);
+    split_f32(x[2], hi.z, lo.z);
+    split_f32(x[3], hi.w, lo.w);
+    m.split[2 * idx] = hi;
+    m.split[2 * idx + 1] = lo;
 }
 
 template <int PREC>
@@ -218,9 +230,11 @@ __device__ __forceinline__ void face_cells(const FacePassArgs &a, const GridView
         bool emit = false;
         if (a.mode == MODE_MARK) {
             if (act) {
+                // bits are only ever set during this pass, so a word that already
+                // holds them needs no atomic (a stale read only costs an atomic)
                 uint32_t w, m;
                 bloom_slot(h, a.bmA_word_bits, w, m);
-                atomicOr(a.bmA + w, m);
+                if ((a.bmA[w] & m) != m) atomicOr(a.bmA + w, m);
             }
         } else if (a.mode == MODE_PROBE_MARK) {
             if (act) {
@@ -230,7 +244,7 @@ __device__ __forceinline__ void face_cells(const FacePassArgs &a, const GridView
                     emit = true;
                     uint32_t w2, m2;
                     bloom_slot(h, a.bmH_word_bits, w2, m2);
-                    atomicOr(a.bmH + w2, m2);
+                    if ((a.bmH[w2] & m2) != m2) atomicOr(a.bmH + w2, m2);
                 }
             }
         } else if (a.mode == MODE_PROBE) {
@@ -248,8 +262,9 @@ __device__ __forceinline__ void face_cells(const FacePassArgs &a, const GridView
                 a.ent_key[pos] = pair_hi | ((uint64_t)cell << 1) | (uint64_t)role;
                 a.ent_val[pos] = (uint32_t)pos;
                 a.ent_face[pos] = face;
-                a.ent_cell[pos] = make_uint2((uint32_t)cc[0] | ((uint32_t)cc[1] << 16),
-                                             (uint32_t)cc[2] | ((uint32_t)cc[3] << 16));
+                // the face's lowest cell (for the owner-cell rule of the emission)
+                a.ent_cell[pos] = make_uint2((uint32_t)clo[0] | ((uint32_t)clo[1] << 16),
+                                             (uint32_t)clo[2] | ((uint32_t)clo[3] << 16));
                 write_box<PREC>(a, pos, b);
             }
         }
@@ -304,8 +319,9 @@ __global__ void __launch_bounds__(256) k_face_pass(FacePassArgs a) {
         for (int r = 0; r <= TK; ++r) {
             if (col_ok && r <= rows_q) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) nonfinite |= !isfinite(x[r][c]);
+                for (int c = 0; c < 4; ++c) nonfinite |= !finite64(x[r][c]);
                 to_vtx(x[r], sv[r * W + t]);
+                if (a.mode == MODE_BOUNDS) write_split(m, (size_t)(kq0 + r) * m.N + vi, x[r]);
             }
         }
         // the last vertex column of the tile (wraps to column 0 on a periodic mesh)
@@ -317,9 +333,10 @@ __global__ void __launch_bounds__(256) k_face_pass(FacePassArgs a) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 y[c] = __ldg(m.c[c] + off);
-                nonfinite |= !isfinite(y[c]);
+                nonfinite |= !finite64(y[c]);
             }
             to_vtx(y, sv[t * W + cols_q]);
+            if (a.mode == MODE_BOUNDS) write_split(m, off, y);
         }
     }
     __syncthreads();

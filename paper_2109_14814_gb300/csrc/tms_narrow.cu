@@ -11,14 +11,17 @@
 // and a singular system (a zero pivot) is not a hit.  The (theta, s) estimates
 // are the interpolation formulas that follow Eq. (precise).
 //
-// Mixed precision (optional): an FP32 solve first.  Its forward error is bounded
-// from the FP32 residual and the normalised-column determinant rho: for the
-// column-normalised matrix A_hat (unit columns, sigma_max <= 2),
-// sigma_min >= rho / 8, so |D (z - z~)|_2 <= (8 / rho) |r - A z~|_2.  The
-// residual is bounded rigorously from the FP32 computation (input rounding and
-// accumulated rounding), and rho_true >= rho_fp32 / 2 whenever rho_fp32 >= 1e-2.
-// A pair is rejected in FP32 only when the resulting upper bound of the margin
-// is below -2 tau; every other pair gets the FP64 solve.
+// Mixed precision (optional): a verified FP32 solve first.  The system is formed
+// in FP32 from a split copy of the vertices (hi + lo per coordinate), with a
+// bound on every entry's error.  Gaussian elimination on [A | I | r] gives z~
+// and an approximate inverse C; with alpha >= |I - C A|_inf (computed with its
+// rounding and input-error terms), A is nonsingular when alpha < 1 and
+//   |z - z~|_inf <= | |C| |r - A z~| |_inf / (1 - alpha),
+// the residual again bounded with its rounding and input errors.  A pair is
+// rejected in FP32 only when the resulting upper bound of the margin is below
+// -2 tau minus an allowance for the FP64 solve's own rounding (so an FP64 solve
+// of the same system could not call it a hit); all other pairs, and every
+// pair whose certificate fails, get the FP64 solve.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -58,12 +61,17 @@ __device__ __forceinline__ bool solve4_gepp(T A[4][4], T r[4], T z[4], T &det) {
         ok &= best != T(0);
 #pragma unroll
         for (int row = col + 1; row < 4; ++row) {
-            if (p == row) {
+            const bool sw = (p == row);     // branch-free select keeps A in registers
 #pragma unroll
-                for (int j = col; j < 4; ++j) swap_(A[col][j], A[row][j]);
-                swap_(r[col], r[row]);
-                sign = -sign;
+            for (int j = col; j < 4; ++j) {
+                const T lo = A[col][j], hi = A[row][j];
+                A[col][j] = sw ? hi : lo;
+                A[row][j] = sw ? lo : hi;
             }
+            const T rl = r[col], rh = r[row];
+            r[col] = sw ? rh : rl;
+            r[row] = sw ? rl : rh;
+            sign = sw ? -sign : sign;
         }
         inv[col] = T(1) / A[col][col];
 #pragma unroll
@@ -92,85 +100,206 @@ __device__ __forceinline__ void gather_tri(const MeshDev &m, uint32_t t, double 
     for (int j = 0; j < 3; ++j) load_vertex(m, ii[j], kk[j], v[j]);
 }
 
-__device__ __forceinline__ float f32_rn(double x) { return __double2float_rn(x); }
+// One entry of the FP32 system: the difference p - q of two split coordinates and
+// a bound on its error against the exact difference of the FP64 coordinates.
+__device__ __forceinline__ float split_diff(float hp, float lp, float hq, float lq, float &err) {
+    const float u = 5.9604645e-08f;
+    const float t1 = hp - hq, t2 = lp - lq;
+    const float d = t1 + t2;
+    // relative rounding of the three FP32 operations, the split remainders, and an
+    // absolute term for coordinates below 2^-74 (whose lo part is not kept)
+    err = (u * (fabsf(t1) + fabsf(t2) + fabsf(d))) * 1.0001f + (u * u) * (fabsf(hp) + fabsf(hq)) * 1.01f +
+          1e-29f;
+    return d;
+}
 
-// FP32 pre-solve; true when it certifies margin < -2 tau (pair is not a hit)
-__device__ __forceinline__ bool fp32_reject(const double x[3][4], const double y[3][4], double tau) {
-    const float u = 5.9604645e-08f;   // 2^-24
-    float A[4][4], Af[4][4], r[4], rf[4];
+__device__ __forceinline__ void gather_split(const MeshDev &m, uint32_t t, float4 v[3][2]) {
+    int ii[3], kk[3];
+    tri_ij(m, t, ii, kk);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        // differences formed from FP32-rounded vertices; the rounding of the
-        // vertices is an input perturbation bounded below
-        float x1 = f32_rn(x[0][c]), x2 = f32_rn(x[1][c]), x3 = f32_rn(x[2][c]);
-        float y1 = f32_rn(y[0][c]), y2 = f32_rn(y[1][c]), y3 = f32_rn(y[2][c]);
-        A[c][0] = x1 - x2;
-        A[c][1] = x3 - x2;
-        A[c][2] = y2 - y1;
-        A[c][3] = y2 - y3;
-        r[c] = y2 - x2;
-        // |exact entry - A| <= u (|v_i| + |v_j|) + u |A| per entry (vertex
-        // rounding, then the subtraction)
-        float ax1 = fabsf(x1), ax2 = fabsf(x2), ax3 = fabsf(x3);
-        float ay1 = fabsf(y1), ay2 = fabsf(y2), ay3 = fabsf(y3);
-        Af[c][0] = u * (ax1 + ax2) * 1.0001f + u * fabsf(A[c][0]);
-        Af[c][1] = u * (ax3 + ax2) * 1.0001f + u * fabsf(A[c][1]);
-        Af[c][2] = u * (ay2 + ay1) * 1.0001f + u * fabsf(A[c][2]);
-        Af[c][3] = u * (ay2 + ay3) * 1.0001f + u * fabsf(A[c][3]);
-        rf[c] = u * (ay2 + ax2) * 1.0001f + u * fabsf(r[c]);
+    for (int j = 0; j < 3; ++j) {
+        const size_t idx = 2 * ((size_t)kk[j] * m.N + ii[j]);
+        v[j][0] = __ldg(m.split + idx);
+        v[j][1] = __ldg(m.split + idx + 1);
     }
-    float cn[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) cn[j] = sqrtf(A[0][j] * A[0][j] + A[1][j] * A[1][j] +
-                                              A[2][j] * A[2][j] + A[3][j] * A[3][j]);
-    float M[4][4], rr[4], z[4], det;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        rr[i] = r[i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) M[i][j] = A[i][j];
-    }
-    solve4_gepp<float>(M, rr, z, det);
-    const float rho = fabsf(det) / (cn[0] * cn[1] * cn[2] * cn[3]);
-    if (!(rho >= 1e-2f)) return false;
-    // the input rounding must be a small perturbation of the normalised matrix
-    // (relative column perturbation <= 1e-3 rho keeps sigma_min >= rho / 8 up to
-    // 1%); otherwise leave the pair to the FP64 solve
+}
+
+__device__ __forceinline__ float comp(const float4 &v, int c) {
+    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+// split copies of the quad's vertices (i,k), (i+1,k), (i,k+1), (i+1,k+1)
+__device__ __forceinline__ void gather_quad_split(const MeshDev &m, uint32_t q, float4 v[4][2]) {
+    const int i = (int)(q % (uint32_t)m.N), k = (int)(q / (uint32_t)m.N);
+    const int ip = (i + 1 == m.N) ? 0 : i + 1;
+    const size_t idx[4] = {(size_t)k * m.N + i, (size_t)k * m.N + ip, (size_t)(k + 1) * m.N + i,
+                           (size_t)(k + 1) * m.N + ip};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float pj = sqrtf(Af[0][j] * Af[0][j] + Af[1][j] * Af[1][j] + Af[2][j] * Af[2][j] + Af[3][j] * Af[3][j]);
-        if (!(pj <= 1e-3f * rho * cn[j])) return false;
+        v[j][0] = __ldg(m.split + 2 * idx[j]);
+        v[j][1] = __ldg(m.split + 2 * idx[j] + 1);
     }
-    // residual r - A z with a bound on its error (FP32 accumulation of 5 terms)
-    float R2 = 0.0f;
+}
+
+// (x1, x2, x3) of T1 = ((i+1,k), (i,k), (i,k+1)) or T2 = ((i,k+1), (i+1,k+1), (i+1,k))
+__device__ __forceinline__ void quad_tri(const float4 Q[4][2], int tau, float4 X[3][2]) {
+    // constant indices and selects keep Q in registers
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        X[0][h] = tau ? Q[2][h] : Q[1][h];
+        X[1][h] = tau ? Q[3][h] : Q[0][h];
+        X[2][h] = tau ? Q[1][h] : Q[2][h];
+    }
+}
+
+// closed overlap of the two triangles' boxes, each coordinate widened by its
+// split remainder and a relative 1e-6 (more than the FP32 rounding of the test)
+__device__ __forceinline__ bool split_boxes_overlap(const float4 X[3][2], const float4 Y[3][2]) {
+    bool ov = true;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float xl = 3.4e38f, xh = -3.4e38f, yl = 3.4e38f, yh = -3.4e38f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float hx = comp(X[j][0], c), lx = comp(X[j][1], c);
+            const float dx = fabsf(lx) + 1e-6f * fabsf(hx) + 1e-29f;
+            xl = fminf(xl, hx - dx);
+            xh = fmaxf(xh, hx + dx);
+            const float hy = comp(Y[j][0], c), ly = comp(Y[j][1], c);
+            const float dy = fabsf(ly) + 1e-6f * fabsf(hy) + 1e-29f;
+            yl = fminf(yl, hy - dy);
+            yh = fmaxf(yh, hy + dy);
+        }
+        ov &= !(xh < yl || yh < xl);
+    }
+    return ov;
+}
+
+
+// true when the verified FP32 solve proves margin < -2 tau (not a hit)
+__device__ __forceinline__ bool fp32_verified_reject(const float4 X[3][2], const float4 Y[3][2],
+                                                  double tau) {
+    const float u = 5.9604645e-08f;
+    float A[4][4], EA[4][4], r[4], Er[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        A[c][0] = split_diff(comp(X[0][0], c), comp(X[0][1], c), comp(X[1][0], c), comp(X[1][1], c), EA[c][0]);
+        A[c][1] = split_diff(comp(X[2][0], c), comp(X[2][1], c), comp(X[1][0], c), comp(X[1][1], c), EA[c][1]);
+        A[c][2] = split_diff(comp(Y[1][0], c), comp(Y[1][1], c), comp(Y[0][0], c), comp(Y[0][1], c), EA[c][2]);
+        A[c][3] = split_diff(comp(Y[1][0], c), comp(Y[1][1], c), comp(Y[2][0], c), comp(Y[2][1], c), EA[c][3]);
+        r[c] = split_diff(comp(Y[1][0], c), comp(Y[1][1], c), comp(X[1][0], c), comp(X[1][1], c), Er[c]);
+    }
+    // Gaussian elimination with partial pivoting on [A | I | r]
+    float M[4][9];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        float res = r[i];
-        float mag = fabsf(r[i]);
-        float pert = rf[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { M[i][j] = A[i][j]; M[i][4 + j] = (i == j) ? 1.0f : 0.0f; }
+        M[i][8] = r[i];
+    }
+#pragma unroll
+    for (int col = 0; col < 4; ++col) {
+        int p = col;
+        float best = fabsf(M[col][col]);
+#pragma unroll
+        for (int row = col + 1; row < 4; ++row) {
+            float v = fabsf(M[row][col]);
+            if (v > best) { best = v; p = row; }
+        }
+        if (!(best > 0.0f)) return false;
+#pragma unroll
+        for (int row = col + 1; row < 4; ++row) {
+            const bool sw = (p == row);
+#pragma unroll
+            for (int j = col; j < 9; ++j) {
+                const float lo = M[col][j], hi = M[row][j];
+                M[col][j] = sw ? hi : lo;
+                M[row][j] = sw ? lo : hi;
+            }
+        }
+        const float inv = 1.0f / M[col][col];
+#pragma unroll
+        for (int row = col + 1; row < 4; ++row) {
+            const float f = M[row][col] * inv;
+#pragma unroll
+            for (int j = col + 1; j < 9; ++j) M[row][j] = fmaf(-f, M[col][j], M[row][j]);
+        }
+        M[col][col] = inv;   // keep the reciprocal pivot for the back substitution
+    }
+    // back substitution for the 5 right-hand sides: columns 4..7 give C, 8 gives z
+    float C[4][4], z[4];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        float x[4];
+#pragma unroll
+        for (int row = 3; row >= 0; --row) {
+            float acc = M[row][4 + k];
+#pragma unroll
+            for (int j = row + 1; j < 4; ++j) acc = fmaf(-M[row][j], x[j], acc);
+            x[row] = acc * M[row][row];
+        }
+#pragma unroll
+        for (int row = 0; row < 4; ++row) {
+            if (k < 4) C[row][k] = x[row];
+            else z[row] = x[row];
+        }
+    }
+    // alpha >= |I - C A_exact|_inf: computed I - C A, its rounding (6u (1 + |C||A|))
+    // and the input error |C| EA
+    float alpha = 0.0f, cnorm = 0.0f, anorm = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float row = 0.0f, crow = 0.0f, arow = 0.0f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            res = fmaf(-A[i][j], z[j], res);
-            mag += fabsf(A[i][j] * z[j]);
-            pert += Af[i][j] * fabsf(z[j]);
-        }
-        float bound = fabsf(res) + 8.0f * u * mag + pert * 1.0001f;
-        R2 += bound * bound;
-    }
-    const float R = sqrtf(R2) * 1.0001f;
-    const float K = 20.0f;   // 8 (sigma_min >= rho/8) x 2 (rho_true >= rho/2) x 1.25
-    float e[4];
+            float e = (i == j) ? 1.0f : 0.0f, ca = 0.0f, ce = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) e[j] = K * R / (rho * cn[j]) * 1.0001f + 1e-30f;
+            for (int k = 0; k < 4; ++k) {
+                e = fmaf(-C[i][k], A[k][j], e);
+                ca = fmaf(fabsf(C[i][k]), fabsf(A[k][j]), ca);
+                ce = fmaf(fabsf(C[i][k]), EA[k][j], ce);
+            }
+            row += fabsf(e) + 6.0f * u * (((i == j) ? 1.0f : 0.0f) + ca) + ce;
+            crow += fabsf(C[i][j]);
+            arow += fabsf(A[i][j]);
+        }
+        alpha = fmaxf(alpha, row);
+        cnorm = fmaxf(cnorm, crow);
+        anorm = fmaxf(anorm, arow);
+    }
+    alpha *= 1.0001f;
+    if (!(alpha < 0.5f)) return false;
+    // |r_exact - A_exact z~| componentwise
+    float res[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float acc = r[i], mag = fabsf(r[i]), pert = Er[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            acc = fmaf(-A[i][j], z[j], acc);
+            mag = fmaf(fabsf(A[i][j]), fabsf(z[j]), mag);
+            pert = fmaf(EA[i][j], fabsf(z[j]), pert);
+        }
+        res[i] = (fabsf(acc) + 6.0f * u * mag + pert) * 1.0001f;
+    }
+    float err = 0.0f, zmax = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float d = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d = fmaf(fabsf(C[i][j]), res[j], d);
+        err = fmaxf(err, d);
+        zmax = fmaxf(zmax, fabsf(z[i]));
+    }
+    err = err / (1.0f - alpha) * 1.001f;
     const float slack = 4.0f * u;
-    float m = z[0] + e[0];
-    m = fminf(m, z[1] + e[1]);
-    m = fminf(m, z[2] + e[2]);
-    m = fminf(m, z[3] + e[3]);
-    m = fminf(m, 1.0f - z[0] - z[1] + e[0] + e[1] + slack * (1.0f + fabsf(z[0]) + fabsf(z[1])));
-    m = fminf(m, 1.0f - z[2] - z[3] + e[2] + e[3] + slack * (1.0f + fabsf(z[2]) + fabsf(z[3])));
-    const bool finite = isfinite(m) && isfinite(R);
-    return finite && (m < (float)(-2.0 * tau));
+    float m = fminf(fminf(z[0], z[1]), fminf(z[2], z[3])) + err;
+    m = fminf(m, 1.0f - z[0] - z[1] + 2.0f * err + slack * (1.0f + fabsf(z[0]) + fabsf(z[1])));
+    m = fminf(m, 1.0f - z[2] - z[3] + 2.0f * err + slack * (1.0f + fabsf(z[2]) + fabsf(z[3])));
+    // allowance for an FP64 solve of the same system (its own rounding)
+    const float kappa = cnorm * anorm;
+    const float allow = 2.0f * (float)tau + 32.0f * 1.1102230e-16f * kappa * (1.0f + zmax);
+    return isfinite(m) && isfinite(err) && (m < -allow);
 }
 
 // (theta, s) estimate for weights (u, v) in triangle t (formulas after Eq. (precise))
@@ -193,15 +322,12 @@ __device__ __forceinline__ void tri_params(const MeshDev &m, uint32_t t, double 
     if (th < 0) th += kTwoPi;
 }
 
-__device__ __forceinline__ bool narrow_pair(const MeshDev &ma, const MeshDev &mb, uint32_t ta,
-                                            uint32_t tb, double tau, int use_filter, bool &used64,
-                                            tms_hit &h) {
+// FP64 narrow-phase test of one triangle pair (Eq. (precise)); fills h on a hit
+__device__ __forceinline__ bool narrow_fp64(const MeshDev &ma, const MeshDev &mb, uint32_t ta,
+                                            uint32_t tb, double tau, tms_hit &h) {
     double x[3][4], y[3][4];
     gather_tri(ma, ta, x);
     gather_tri(mb, tb, y);
-    used64 = false;
-    if (use_filter && fp32_reject(x, y, tau)) return false;
-    used64 = true;
     double A[4][4], r[4], col0[4], col1[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -238,8 +364,10 @@ __device__ __forceinline__ bool narrow_pair(const MeshDev &ma, const MeshDev &mb
     return true;
 }
 
+// Stage 1: every triangle pair of every candidate through the verified FP32
+// filter; pairs it cannot reject go to the survivor list.
 template <int FACE>
-__global__ void __launch_bounds__(256) k_narrow(NarrowArgs a) {
+__global__ void __launch_bounds__(256) k_narrow_filter(NarrowArgs a) {
     if (a.ctr->cand > a.cand_cap) return;
     const unsigned long long n = a.ctr->cand;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -255,24 +383,73 @@ __global__ void __launch_bounds__(256) k_narrow(NarrowArgs a) {
         const MeshDev ma = a.meshes[pr.x];
         const MeshDev mb = a.meshes[pr.y];
         const int nsub = FACE == 0 ? 1 : 4;
+        // quad candidates: the quads' four vertices once, (i,k) (i+1,k) (i,k+1) (i+1,k+1)
+        float4 QA[4][2], QB[4][2];
+        if (FACE == 1 && valid && a.fp32_filter) {
+            gather_quad_split(ma, cd.faceA, QA);
+            gather_quad_split(mb, cd.faceB, QB);
+        }
 #pragma unroll 1
         for (int sub = 0; sub < nsub; ++sub) {
             uint32_t ta, tb;
             if (FACE == 0) { ta = cd.faceA; tb = cd.faceB; }
             else { ta = 2 * cd.faceA + (sub & 1); tb = 2 * cd.faceB + (sub >> 1); }
-            tms_hit h;
-            bool hit = false, used64 = false;
-            if (valid) hit = narrow_pair(ma, mb, ta, tb, a.tau, a.fp32_filter, used64, h);
-            const unsigned n64 = __popc(__ballot_sync(FULL, used64));
-            if (lane == 0 && n64) atomicAdd(&a.ctr->fp64, (unsigned long long)n64);
-            const unsigned long long pos = warp_append(&a.ctr->raw_hits, hit, FULL);
-            if (hit && pos < a.hit_cap) {
-                h.pair = cd.pair;
-                a.hits[pos] = h;
-                a.hit_key[pos] = ((uint64_t)cd.pair << (2 * a.tri_bits)) |
-                                 ((uint64_t)ta << a.tri_bits) | (uint64_t)tb;
-                a.hit_val[pos] = (uint32_t)pos;
+            bool keep = false;
+            if (valid) {
+                if (a.fp32_filter) {
+                    float4 X[3][2], Y[3][2];
+                    if (FACE == 0) {
+                        gather_split(ma, ta, X);
+                        gather_split(mb, tb, Y);
+                        keep = !fp32_verified_reject(X, Y, a.tau);
+                    } else {
+                        quad_tri(QA, sub & 1, X);
+                        quad_tri(QB, sub >> 1, Y);
+                        // the two triangles' boxes first: disjoint boxes, no intersection
+                        keep = split_boxes_overlap(X, Y) && !fp32_verified_reject(X, Y, a.tau);
+                    }
+                } else {
+                    keep = true;
+                }
             }
+            const unsigned long long pos = warp_append(&a.ctr->fp64, keep, FULL);
+            if (keep && pos < a.surv_cap) {
+                Cand s;
+                s.faceA = ta;
+                s.faceB = tb;
+                s.pair = cd.pair;
+                s.pad = 0;
+                a.surv[pos] = s;
+            }
+        }
+    }
+}
+
+// Stage 2: the FP64 solve for the survivors
+__global__ void __launch_bounds__(256) k_narrow_fp64(NarrowArgs a) {
+    if (a.ctr->cand > a.cand_cap || a.ctr->fp64 > a.surv_cap) return;
+    const unsigned long long n = a.ctr->fp64;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long g0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x - lane;
+         g0 < n; g0 += stride) {
+        const unsigned long long g = g0 + lane;
+        bool hit = false;
+        tms_hit h;
+        Cand s;
+        s.faceA = s.faceB = s.pair = 0;
+        if (g < n) {
+            s = a.surv[g];
+            const int2 pr = a.pairs[s.pair];
+            hit = narrow_fp64(a.meshes[pr.x], a.meshes[pr.y], s.faceA, s.faceB, a.tau, h);
+        }
+        const unsigned long long pos = warp_append(&a.ctr->raw_hits, hit, FULL);
+        if (hit && pos < a.hit_cap) {
+            h.pair = s.pair;
+            a.hits[pos] = h;
+            a.hit_key[pos] = ((uint64_t)s.pair << (2 * a.tri_bits)) |
+                             ((uint64_t)s.faceA << a.tri_bits) | (uint64_t)s.faceB;
+            a.hit_val[pos] = (uint32_t)pos;
         }
     }
 }
@@ -484,8 +661,9 @@ __global__ void k_adjoint(AdjointArgs a) {
 }  // namespace
 
 void launch_narrow(const NarrowArgs &a, int face_level, int grid, cudaStream_t st) {
-    if (face_level == 0) k_narrow<0><<<grid, 256, 0, st>>>(a);
-    else k_narrow<1><<<grid, 256, 0, st>>>(a);
+    if (face_level == 0) k_narrow_filter<0><<<grid, 256, 0, st>>>(a);
+    else k_narrow_filter<1><<<grid, 256, 0, st>>>(a);
+    k_narrow_fp64<<<grid, 256, 0, st>>>(a);
 }
 
 void launch_dedup(const DedupArgs &a, int grid, cudaStream_t st) {

@@ -1,15 +1,21 @@
 // Cell ranges and candidate-pair emission of the broad phase.
 //
 // After the sort, entries of one (pair, cell) are contiguous with mesh A's
-// entries first (the role is the key's lowest bit).  Per cell we need the start
-// of its A list and B list and nA * nB, the number of face pairs it proposes;
-// the exclusive scan of nA * nB is the paper's box_gid_idxs array (Sec. 5.3,
-// Algorithm 1).  Emission assigns one thread per proposed pair, as Algorithm 1
-// does, but finds its cell by binary search over that scan instead of a linear
-// walk, applies the bounding-box test of Sec. 5.2.2, keeps the pair only in its
-// owner cell (the componentwise max of the two faces' lowest cells -- each pair
-// sharing several cells is emitted exactly once), optionally applies the Moller
-// quick test of Sec. 5.2.3, and compacts survivors with one atomic per warp.
+// entries first (the role is the key's lowest bit).  Per cell: the start of its
+// A list and B list and nA * nB, the number of face pairs it proposes; the
+// exclusive scan of nA * nB is the paper's box_gid_idxs array (Sec. 5.3,
+// Algorithm 1).
+//
+// Emission re-designed for GB300: the nA x nB pair matrix of a cell is cut
+// into 32 x 32 tiles and one warp tests one tile -- each lane holds one A box
+// in registers, the tile's B boxes sit in shared memory and are read by
+// broadcast, so a proposed pair costs a few compares and no memory traffic.
+// (Algorithm 1 gives every proposed pair its own work item that locates its
+// box with a linear walk and fetches vertices.)  Per pair: the bounding-box
+// test of Sec. 5.2.2, then the owner-cell rule -- the pair is kept only in the
+// cell that is the componentwise max of the two faces' lowest cells, so a pair
+// sharing several cells is emitted exactly once -- then optionally the Moller
+// quick test of Sec. 5.2.3; survivors are compacted with one atomic per warp.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,6 +26,8 @@ namespace tms {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int kTile = 32;
+constexpr int kEmitWarps = 8;
 
 __global__ void k_cell_heads(const uint64_t *keys, const unsigned long long *d_n,
                              unsigned long long cap, uint32_t *head) {
@@ -47,7 +55,8 @@ __global__ void k_cell_fill(const uint64_t *keys, const uint32_t *head, const ui
 
 __global__ void k_cell_pairs(const uint32_t *cell_start, uint32_t *cell_b,
                              const unsigned long long *d_cells, const unsigned long long *d_n,
-                             unsigned long long cap, unsigned long long *pairs) {
+                             unsigned long long cap, unsigned long long *pairs,
+                             unsigned long long *tiles) {
     const unsigned long long nc = clamp_count(d_cells, cap);
     const unsigned long long n = clamp_count(d_n, cap);
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nc;
@@ -57,7 +66,9 @@ __global__ void k_cell_pairs(const uint32_t *cell_start, uint32_t *cell_b,
         uint32_t b = cell_b[c];
         if (b == 0xFFFFFFFFu || b < s || b > e) b = e;
         cell_b[c] = b;
-        pairs[c] = (unsigned long long)(b - s) * (unsigned long long)(e - b);
+        const unsigned long long nA = b - s, nB = e - b;
+        pairs[c] = nA * nB;
+        tiles[c] = ((nA + kTile - 1) / kTile) * ((nB + kTile - 1) / kTile);
     }
 }
 
@@ -82,10 +93,6 @@ struct EBox<1> {
         lo[0] = l.x; lo[1] = l.y; lo[2] = l.z; lo[3] = l.w;
         hi[0] = h.x; hi[1] = h.y; hi[2] = h.z; hi[3] = h.w;
     }
-    __device__ void cells(const Grid &g, int c[4]) const {
-#pragma unroll
-        for (int d = 0; d < 4; ++d) c[d] = cell_of(lo[d], g.o32[d], g.inv32[d], g.n[d]);
-    }
 };
 template <>
 struct EBox<0> {
@@ -96,10 +103,14 @@ struct EBox<0> {
         lo[0] = x0.x; lo[1] = x0.y; lo[2] = x1.x; lo[3] = x1.y;
         hi[0] = x2.x; hi[1] = x2.y; hi[2] = x3.x; hi[3] = x3.y;
     }
-    __device__ void cells(const Grid &g, int c[4]) const {
-#pragma unroll
-        for (int d = 0; d < 4; ++d) c[d] = cell_of(lo[d], g.o64[d], g.inv64[d], g.n[d]);
-    }
+};
+
+template <int PREC>
+struct TileEntry {
+    EBox<PREC> box;
+    uint2 lo;         // lowest cell, 4 x u16
+    uint32_t face;
+    uint32_t pad;
 };
 
 // Moller quick test (Sec. 5.2.3) on the (x, y, px) projection.  The plane of a
@@ -153,7 +164,6 @@ __device__ bool moller_reject(const MeshDev &ma, uint32_t fa, const MeshDev &mb,
     face_vertices(ma, fa, face_level, VA, na);
     face_vertices(mb, fb, face_level, VB, nb);
     if (face_level == 0) {
-        // vertices of T_B all on one side of T_A's plane, or the reverse
         if (same_side(VA[0], VA[1], VA[2], VB, 3)) return true;
         return same_side(VB[0], VB[1], VB[2], VA, 3);
     }
@@ -163,8 +173,9 @@ __device__ bool moller_reject(const MeshDev &ma, uint32_t fa, const MeshDev &mb,
     return same_side(VB[1], VB[0], VB[2], VA, 4) && same_side(VB[2], VB[3], VB[1], VA, 4);
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(256) k_emit(EmitArgs a, int face_level) {
+template <int PREC, bool MOLLER>
+__global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_level) {
+    __shared__ TileEntry<PREC> sB[kEmitWarps][kTile];
     // nothing to do after an entry overflow (the host retries with more room),
     // and a bounded amount of work in any case
     if (a.ctr->entries > a.ent_cap) return;
@@ -172,73 +183,98 @@ __global__ void __launch_bounds__(256) k_emit(EmitArgs a, int face_level) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctr->status, ST_PAIR_LIMIT);
         return;
     }
-    const unsigned long long total = a.ctr->pair_slots;
+    const unsigned long long total = a.ctr->tiles;
     const unsigned long long ncell = clamp_count(&a.ctr->cells, a.ent_cap);
     const unsigned long long nent = clamp_count(&a.ctr->entries, a.ent_cap);
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    // whole warps iterate together so that compaction can use the full mask
-    const unsigned long long start = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-    for (unsigned long long g0 = start - (threadIdx.x & 31); g0 < total; g0 += stride) {
-        const unsigned long long g = g0 + (threadIdx.x & 31);
-        bool keep = false;
-        uint32_t fa = 0, fb = 0, pair = 0;
-        if (g < total) {
-            // cell c: last cell with pair_off[c] <= g
-            unsigned long long lo = 0, hi = ncell - 1;
-            while (lo < hi) {
-                unsigned long long mid = (lo + hi + 1) >> 1;
-                if (a.pair_off[mid] <= g) lo = mid; else hi = mid - 1;
-            }
-            const unsigned long long c = lo;
-            const uint32_t s = a.cell_start[c];
-            const uint32_t b = a.cell_b[c];
-            const unsigned long long nA = b - s;
-            const unsigned long long local = g - a.pair_off[c];
-            const uint32_t ia = (uint32_t)(local % nA), ib = (uint32_t)(local / nA);
-            if (b + ib < nent) {
-                const uint32_t ea = a.vals[s + ia], eb = a.vals[b + ib];
-                const uint64_t key = a.keys[s];
-                pair = (uint32_t)(key >> 32);
-                const Grid &gr = a.grids[pair];
-                EBox<PREC> A, B;
-                A.load(a, ea);
-                B.load(a, eb);
-                // bounding-box test (Sec. 5.2.2): disjoint iff some coordinate's
-                // max of one box is below the other's min
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long gw = blockIdx.x * (unsigned long long)kEmitWarps + warp;
+    const unsigned long long nw = (unsigned long long)gridDim.x * kEmitWarps;
+    // each warp owns a contiguous range of tiles: one binary search for its first
+    // tile's cell, then a forward walk over the cells
+    const unsigned long long per = (total + nw - 1) / nw;
+    const unsigned long long t_begin = gw * per;
+    const unsigned long long t_end = min(t_begin + per, total);
+    unsigned long long c = 0;
+    if (t_begin < t_end) {
+        unsigned long long lo = 0, hi = ncell - 1;
+        while (lo < hi) {
+            unsigned long long mid = (lo + hi + 1) >> 1;
+            if (a.tile_off[mid] <= t_begin) lo = mid; else hi = mid - 1;
+        }
+        c = lo;
+    }
+    for (unsigned long long t = t_begin; t < t_end; ++t) {
+        while (c + 1 < ncell && a.tile_off[c + 1] <= t) ++c;
+        const uint32_t s = a.cell_start[c];
+        const uint32_t bstart = a.cell_b[c];
+        const uint32_t e = (c + 1 < ncell) ? a.cell_start[c + 1] : (uint32_t)nent;
+        const uint32_t nAc = bstart - s;
+        const uint32_t tA = (nAc + kTile - 1) / kTile;
+        const uint32_t local = (uint32_t)(t - a.tile_off[c]);
+        const uint32_t a0 = s + (local % tA) * kTile, b0 = bstart + (local / tA) * kTile;
+        const int nAt0 = (int)min((uint32_t)kTile, bstart - a0);
+        const int nBt0 = (int)min((uint32_t)kTile, e - b0);
+        // lanes take the larger side of the tile, the loop the smaller one
+        const bool swapAB = nBt0 > nAt0;
+        const uint32_t l0 = swapAB ? b0 : a0, m0 = swapAB ? a0 : b0;
+        const int nAt = swapAB ? nBt0 : nAt0, nBt = swapAB ? nAt0 : nBt0;
+        const uint64_t key = a.keys[s];
+        const uint32_t pair = (uint32_t)(key >> 32);
+        const Grid &gr = a.grids[pair];
+        // this cell's coordinates, packed like the entries' lowest cells
+        uint32_t cell = (uint32_t)((key >> 1) & 0x7FFFFFFFu);
+        uint32_t cc[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            cc[d] = cell % (uint32_t)gr.n[d];
+            cell /= (uint32_t)gr.n[d];
+        }
+        const uint2 cur = make_uint2(cc[0] | (cc[1] << 16), cc[2] | (cc[3] << 16));
+        // own A entry in registers, the B tile in shared memory
+        TileEntry<PREC> A;
+        const bool hasA = lane < nAt;
+        if (hasA) {
+            const uint32_t ea = a.vals[l0 + lane];
+            A.box.load(a, ea);
+            A.lo = a.ent_cell[ea];
+            A.face = a.ent_face[ea];
+        }
+        if (lane < nBt) {
+            const uint32_t eb = a.vals[m0 + lane];
+            TileEntry<PREC> B;
+            B.box.load(a, eb);
+            B.lo = a.ent_cell[eb];
+            B.face = a.ent_face[eb];
+            B.pad = 0;
+            sB[warp][lane] = B;
+        }
+        __syncwarp();
+        for (int j = 0; j < nBt; ++j) {
+            const TileEntry<PREC> &B = sB[warp][j];
+            bool keep = false;
+            if (hasA) {
                 bool ov = true;
 #pragma unroll
-                for (int d = 0; d < 4; ++d) ov &= !(A.hi[d] < B.lo[d] || B.hi[d] < A.lo[d]);
-                if (ov) {
-                    int ca[4], cb[4];
-                    A.cells(gr, ca);
-                    B.cells(gr, cb);
-                    const uint2 cc = a.ent_cell[ea];
-                    const int cur[4] = {(int)(cc.x & 0xFFFF), (int)(cc.x >> 16), (int)(cc.y & 0xFFFF),
-                                        (int)(cc.y >> 16)};
-                    bool owner = true;
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) owner &= (max(ca[d], cb[d]) == cur[d]);
-                    if (owner) {
-                        fa = a.ent_face[ea];
-                        fb = a.ent_face[eb];
-                        keep = true;
-                        if (a.moller) {
-                            const int2 pr = a.pairs[pair];
-                            keep = !moller_reject(a.meshes[pr.x], fa, a.meshes[pr.y], fb, face_level);
-                        }
-                    }
+                for (int d = 0; d < 4; ++d) ov &= !(A.box.hi[d] < B.box.lo[d] || B.box.hi[d] < A.box.lo[d]);
+                // owner cell: componentwise max of the two lowest cells == this cell
+                keep = ov && (__vmaxu2(A.lo.x, B.lo.x) == cur.x) && (__vmaxu2(A.lo.y, B.lo.y) == cur.y);
+                if (MOLLER && keep) {
+                    const int2 pr = a.pairs[pair];
+                    const uint32_t fa = swapAB ? B.face : A.face, fb = swapAB ? A.face : B.face;
+                    keep = !moller_reject(a.meshes[pr.x], fa, a.meshes[pr.y], fb, face_level);
                 }
             }
+            const unsigned long long pos = warp_append(&a.ctr->cand, keep, FULL);
+            if (keep && pos < a.cand_cap) {
+                Cand cd;
+                cd.faceA = swapAB ? B.face : A.face;
+                cd.faceB = swapAB ? A.face : B.face;
+                cd.pair = pair;
+                cd.pad = 0;
+                a.cand[pos] = cd;
+            }
         }
-        const unsigned long long pos = warp_append(&a.ctr->cand, keep, FULL);
-        if (keep && pos < a.cand_cap) {
-            Cand cd;
-            cd.faceA = fa;
-            cd.faceB = fb;
-            cd.pair = pair;
-            cd.pad = 0;
-            a.cand[pos] = cd;
-        }
+        __syncwarp();
     }
 }
 
@@ -252,14 +288,21 @@ void launch_cells(const CellArgs &a, int grid, cudaStream_t st) {
     k_cell_fill<<<grid, B, 0, st>>>(a.keys, a.head, a.head_scan, a.d_n, a.cap, a.cell_start,
                                     a.cell_b);
     k_cell_pairs<<<grid, B, 0, st>>>(a.cell_start, a.cell_b, &a.ctr->cells, a.d_n, a.cap,
-                                     a.cell_pairs);
+                                     a.cell_pairs, a.cell_tiles);
     scan_u64(a.cell_pairs, a.pair_off, &a.ctr->cells, a.cap, a.partials, &a.ctr->pair_slots, grid,
              st);
+    scan_u64(a.cell_tiles, a.tile_off, &a.ctr->cells, a.cap, a.partials, &a.ctr->tiles, grid, st);
 }
 
 void launch_emit(const EmitArgs &a, int precision, int face_level, int grid, cudaStream_t st) {
-    if (precision == 1) k_emit<1><<<grid, 256, 0, st>>>(a, face_level);
-    else k_emit<0><<<grid, 256, 0, st>>>(a, face_level);
+    const dim3 b(32 * kEmitWarps);
+    if (precision == 1) {
+        if (a.moller) k_emit<1, true><<<grid, b, 0, st>>>(a, face_level);
+        else k_emit<1, false><<<grid, b, 0, st>>>(a, face_level);
+    } else {
+        if (a.moller) k_emit<0, true><<<grid, b, 0, st>>>(a, face_level);
+        else k_emit<0, false><<<grid, b, 0, st>>>(a, face_level);
+    }
 }
 
 }  // namespace tms

@@ -51,27 +51,51 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_upsweep(const uint64_t *ke
     for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) counts[d * gridDim.x + blockIdx.x] = hist[d];
 }
 
-// exclusive scan of len values in place, one block of 1024 threads
+// exclusive scan of len values in place, one block of 1024 threads: chunks of
+// 4096 values are staged in shared memory with coalesced loads and stores, each
+// thread scans 4 consecutive values, and a warp-shuffle scan joins the threads
 __global__ void __launch_bounds__(1024) k_scan_small(uint32_t *v, int len) {
-    __shared__ uint32_t part[1024];
-    const int per = (len + blockDim.x - 1) / blockDim.x;
-    const int b = threadIdx.x * per;
-    const int e = min(b + per, len);
-    uint32_t s = 0;
-    for (int i = b; i < e; ++i) s += v[i];
-    part[threadIdx.x] = s;
+    constexpr int CH = 4096;
+    __shared__ uint32_t buf[CH];
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        uint32_t x = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    for (int base = 0; base < len; base += CH) {
+        for (int i = threadIdx.x; i < CH; i += blockDim.x) buf[i] = (base + i < len) ? v[base + i] : 0u;
         __syncthreads();
-        part[threadIdx.x] += x;
+        const int o = 4 * threadIdx.x;
+        const uint32_t a0 = buf[o], a1 = buf[o + 1], a2 = buf[o + 2], a3 = buf[o + 3];
+        const uint32_t tot = a0 + a1 + a2 + a3;
+        uint32_t incl = tot;
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
         __syncthreads();
-    }
-    uint32_t run = part[threadIdx.x] - s;
-    for (int i = b; i < e; ++i) {
-        uint32_t x = v[i];
-        v[i] = run;
-        run += x;
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+            uint32_t wi = w;
+            for (int off = 1; off < 32; off <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, wi, off);
+                if (lane >= off) wi += y;
+            }
+            wsum[lane] = wi - w;
+        }
+        __syncthreads();
+        const uint32_t c0 = carry;
+        const uint32_t ex = c0 + wsum[warp] + incl - tot;
+        buf[o] = ex;
+        buf[o + 1] = ex + a0;
+        buf[o + 2] = ex + a0 + a1;
+        buf[o + 3] = ex + a0 + a1 + a2;
+        __syncthreads();
+        for (int i = threadIdx.x; i < CH; i += blockDim.x)
+            if (base + i < len) v[base + i] = buf[i];
+        if (threadIdx.x == blockDim.x - 1) carry = ex + tot;
+        __syncthreads();
     }
 }
 

@@ -93,10 +93,10 @@ def test_config5_parity():
 
 VARIANTS = [
     dict(precision=0),
-    dict(face_level=1),
-    dict(precision=0, face_level=1),
+    dict(face_level=0),
+    dict(precision=0, face_level=0),
     dict(moller=1),
-    dict(moller=1, face_level=1),
+    dict(moller=1, face_level=0),
     dict(cell_filter=0),
     dict(narrow_filter=0),
     dict(cell_mult=2.0),
