@@ -210,6 +210,33 @@ typedef struct {
 
 tms_status tms_last_stats(void *stream, tms_stats *out);
 
+/*
+ * tms_search_noalloc -- tms_search for callers that must not allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant.
+ * Callers that cannot call cudaMalloc include code running while another
+ * framework captures a CUDA graph on the same thread (an allocation would
+ * break the capture), real-time or flight software that fixes its device
+ * footprint at start-up, and services whose device memory is entirely held by
+ * a pool allocator.  Every scratch buffer comes from one file-scope static
+ * __device__ array of 64 MiB that every GPU loading this library holds until
+ * the process exits; the call makes no cudaMalloc, cudaFree or other
+ * allocating call.  Arguments, output order and merging are those of
+ * tms_search.  Limits: each mesh view at most 131072 vertices (TMS_ERR_ARG
+ * otherwise); at most 262144 face-cell entries, 262144 candidates, 65536 FP64
+ * solves and 16384 hits before merging (TMS_ERR_CAPACITY, *nHits = -1, when a
+ * stage overflows; nothing is grown).  All calls share the array, which keeps
+ * the last call's contents; each call clears what must start at zero.  Calls
+ * whose GPU work overlaps (two streams, two host threads) race on the array and
+ * must be ordered by the caller.  The first call on a device looks up the
+ * array's device address with that device current and configures the kernels:
+ * make it before any stream capture.  Synchronises `stream`.  Messages:
+ * tms_noalloc_last_error().
+ */
+tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_params *params,
+                              tms_hit *dHits, long long hitCap, long long *nHits,
+                              void *stream);
+const char *tms_noalloc_last_error(void);
+
 /* Per-stage device time (ms) of the last search on `stream` made with
  * params.timing = 1, in this order:
  *   0 counters/bounds init   1 face pass: world bounds   2 grid parameters

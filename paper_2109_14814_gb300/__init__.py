@@ -6,14 +6,14 @@ narrow phase solving the 4x4 system for (a, b, c, d), merged and sorted hits,
 a batched form replayed from a CUDA graph, and an FP64 adjoint.  All compute is
 in libtms.so (C ABI in include/tms.h); this package only marshals arguments.
 """
-from ._binding import (HIT_BYTES, TMS_ERR_ARG, TMS_ERR_CAPACITY, TMS_ERR_CUDA, TMS_ERR_STATE,
-                       TMS_ERR_TIMEOUT, TMS_OK, HitPoint, Hits, Mesh, Params, Stats, TmsError,
-                       backward, last_error, last_stage_ms, last_stats, lib, params, probe_fp64_tflops,
-                       release_workspace, search,
-                       search_batched, status_str, version)
+from ._binding import (HIT_BYTES, STAGES, TMS_ERR_ARG, TMS_ERR_CAPACITY, TMS_ERR_CUDA,
+                       TMS_ERR_STATE, TMS_ERR_TIMEOUT, TMS_OK, HitPoint, Hits, Mesh, Params, Stats,
+                       TmsError, backward, last_error, last_stage_ms, last_stats, lib, params,
+                       probe_fp64_tflops, release_workspace, search, search_batched,
+                       search_noalloc, status_str, version)
 
-__all__ = ["HIT_BYTES", "TMS_ERR_ARG", "TMS_ERR_CAPACITY", "TMS_ERR_CUDA", "TMS_ERR_STATE",
-           "TMS_ERR_TIMEOUT", "TMS_OK", "HitPoint", "Hits", "Mesh", "Params", "Stats", "TmsError",
-           "backward", "last_error", "last_stage_ms", "last_stats", "lib", "params", "probe_fp64_tflops",
-           "release_workspace", "search",
-           "search_batched", "status_str", "version"]
+__all__ = ["HIT_BYTES", "STAGES", "TMS_ERR_ARG", "TMS_ERR_CAPACITY", "TMS_ERR_CUDA",
+           "TMS_ERR_STATE", "TMS_ERR_TIMEOUT", "TMS_OK", "HitPoint", "Hits", "Mesh", "Params",
+           "Stats", "TmsError", "backward", "last_error", "last_stage_ms", "last_stats", "lib",
+           "params", "probe_fp64_tflops", "release_workspace", "search", "search_batched",
+           "search_noalloc", "status_str", "version"]

@@ -109,8 +109,32 @@ def lib():
     L.tms_last_error.restype = _c.c_char_p
     L.tms_probe_fp64.argtypes = [_c.POINTER(D), P]
     L.tms_probe_fp64.restype = I
+    L.tms_search_noalloc.argtypes = [P, P, _c.POINTER(Params), P, LL, _c.POINTER(LL), P]
+    L.tms_search_noalloc.restype = I
+    L.tms_noalloc_last_error.argtypes = []
+    L.tms_noalloc_last_error.restype = _c.c_char_p
     _lib = L
     return L
+
+
+def search_noalloc(A: "Mesh", B: "Mesh", out: torch.Tensor, stream=None, **kw) -> "Hits":
+    """tms_search_noalloc: the search with every scratch buffer in the library's
+    static device array, for callers that must not allocate device memory
+    (for example while another component captures a CUDA graph, or in software
+    that fixes its device footprint at start-up).  The caller passes the output
+    buffer `out` ((capacity, 128) uint8, on the device); nothing is allocated.
+    Limits and sharing rules: see include/tms.h."""
+    p = params(**kw)
+    n = _c.c_longlong(0)
+    rc = lib().tms_search_noalloc(A.handle, B.handle, _c.byref(p), out.data_ptr(), out.shape[0],
+                                  _c.byref(n), _stream(stream))
+    if rc != TMS_OK:
+        msg = lib().tms_noalloc_last_error().decode()
+        err = TmsError.__new__(TmsError)
+        err.status = rc
+        RuntimeError.__init__(err, f"tms_search_noalloc: {status_str(rc)} ({msg})")
+        raise err
+    return Hits(out[: n.value])
 
 
 def probe_fp64_tflops(stream=None) -> float:

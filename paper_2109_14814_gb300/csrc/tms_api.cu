@@ -729,6 +729,17 @@ tms_status tms_build_mesh(const double *dX, const double *dY, const double *dPx,
     return TMS_OK;
 }
 
+}  // extern "C"
+
+tms_status tms::mesh_view(tms_mesh m, MeshDev *view, int *device) {
+    if (!m || m->magic != kMagic) return TMS_ERR_STATE;
+    *view = m->dev;
+    *device = m->device;
+    return TMS_OK;
+}
+
+extern "C" {
+
 tms_status tms_destroy_mesh(tms_mesh m) {
     if (!m || m->magic != kMagic) return TMS_ERR_STATE;
     {

@@ -423,4 +423,7 @@ struct AdjointArgs {
 };
 void launch_adjoint(const AdjointArgs &a, cudaStream_t st);
 
+// device view of a mesh handle (TMS_ERR_STATE for an invalid handle)
+tms_status mesh_view(tms_mesh m, MeshDev *view, int *device);
+
 }  // namespace tms

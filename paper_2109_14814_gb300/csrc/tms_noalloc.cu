@@ -1,0 +1,339 @@
+// tms_search_noalloc: the mesh search for callers that must not allocate.
+//
+// Some callers cannot call cudaMalloc: code running while another framework
+// captures a CUDA graph on the same thread (an allocation there breaks or
+// invalidates the capture), flight- or control-loop software that fixes its
+// device footprint at start-up and forbids allocation afterwards, and
+// services whose device memory is entirely held by a pool allocator (a direct
+// cudaMalloc would fail or fragment the pool).  For them this entry point runs
+// the same kernels as tms_search with every scratch buffer carved from one
+// file-scope static __device__ array.  That array (kArenaBytes) is part of the
+// library image: every GPU that loads the library holds it until the process
+// exits.  The caller still owns and passes the inputs (mesh handles) and the
+// output buffer.
+//
+// Limits, fixed by the arena's size: at most kMaxViewVertices vertices per
+// mesh view, kEntCap face-cell entries, kCandCap candidates, kSurvCap FP64
+// solves and kRawHitCap hits before merging.  A call that needs more returns
+// TMS_ERR_ARG (mesh too large) or TMS_ERR_CAPACITY (a stage overflowed) with a
+// message in tms_last_error(); it never grows anything.
+//
+// Every call shares the one array and leaves its contents behind; each call
+// clears what must start at zero (counters, occupancy bitmaps).  Calls whose
+// GPU work overlaps -- on two streams, or from two host threads -- race on the
+// array: the caller must order them.  The first call on a device looks up the
+// array's device address (cudaGetSymbolAddress) with that device current and
+// configures the kernels; make that first call before any stream capture.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+
+#include "tms_common.cuh"
+
+using namespace tms;
+
+namespace {
+
+constexpr size_t kArenaBytes = 64ull << 20;
+constexpr unsigned long long kMaxViewVertices = 1ull << 17;
+constexpr unsigned long long kEntCap = 1ull << 18;
+constexpr unsigned long long kCandCap = 1ull << 18;
+constexpr unsigned long long kSurvCap = 1ull << 16;
+constexpr unsigned long long kRawHitCap = 1ull << 14;
+constexpr int kBmAWordBits = 17;   // 2^17 words = 4 Mi bits
+constexpr int kBmHWordBits = 16;
+constexpr int kMaxGrid = 1024;
+
+static __device__ __align__(256) unsigned char g_arena[kArenaBytes];
+
+std::mutex g_mu;
+unsigned char *g_base[64] = {};
+thread_local std::string g_msg;
+
+struct Carve {
+    unsigned char *base;
+    size_t off = 0;
+    template <typename T>
+    T *take(unsigned long long n) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += (size_t)n * sizeof(T);
+        return p;
+    }
+};
+
+struct Tables {
+    MeshDev meshes[2];
+    int2 pairs[1];
+    PassEntry all[2], pa[1], pb[1];
+};
+
+struct Buffers {
+    Tables *tables;
+    Bounds *bounds;
+    Grid *grids;
+    Counters *ctr;
+    unsigned long long *partials;
+    float4 *split[2];
+    uint32_t *bmA, *bmH;
+    uint64_t *ek, *ek2;
+    uint32_t *ev, *ev2, *eface;
+    uint2 *ecell;
+    float4 *ebox32;
+    double *ebox64;
+    uint32_t *sort_counts;
+    uint32_t *head, *hscan, *cstart, *cb;
+    unsigned long long *cpairs, *poff, *ctiles, *toff;
+    Cand *cand, *surv;
+    tms_hit *hits;
+    uint64_t *hk, *hk2, *okeys;
+    uint32_t *hv, *hv2, *keep, *kscan;
+};
+
+// the arena's layout; also used to check, at compile time, that it fits
+size_t carve(unsigned char *base, Buffers &b) {
+    Carve c{base};
+    b.tables = c.take<Tables>(1);
+    b.bounds = c.take<Bounds>(2);
+    b.grids = c.take<Grid>(1);
+    b.ctr = c.take<Counters>(1);
+    b.partials = c.take<unsigned long long>(kMaxGrid);
+    b.split[0] = c.take<float4>(2 * kMaxViewVertices);
+    b.split[1] = c.take<float4>(2 * kMaxViewVertices);
+    b.bmA = c.take<uint32_t>(1ull << kBmAWordBits);
+    b.bmH = c.take<uint32_t>(1ull << kBmHWordBits);
+    b.ek = c.take<uint64_t>(kEntCap);
+    b.ek2 = c.take<uint64_t>(kEntCap);
+    b.ev = c.take<uint32_t>(kEntCap);
+    b.ev2 = c.take<uint32_t>(kEntCap);
+    b.eface = c.take<uint32_t>(kEntCap);
+    b.ecell = c.take<uint2>(kEntCap);
+    b.ebox64 = c.take<double>(8 * kEntCap);             // room for FP64 boxes ...
+    b.ebox32 = reinterpret_cast<float4 *>(b.ebox64);     // ... or FP32 ones
+    b.sort_counts = c.take<uint32_t>((unsigned long long)kRadixBins * kMaxGrid);
+    b.head = c.take<uint32_t>(kEntCap);
+    b.hscan = c.take<uint32_t>(kEntCap);
+    b.cstart = c.take<uint32_t>(kEntCap);
+    b.cb = c.take<uint32_t>(kEntCap);
+    b.cpairs = c.take<unsigned long long>(kEntCap);
+    b.poff = c.take<unsigned long long>(kEntCap);
+    b.ctiles = c.take<unsigned long long>(kEntCap);
+    b.toff = c.take<unsigned long long>(kEntCap);
+    b.cand = c.take<Cand>(kCandCap);
+    b.surv = c.take<Cand>(kSurvCap);
+    b.hits = c.take<tms_hit>(kRawHitCap);
+    b.hk = c.take<uint64_t>(kRawHitCap);
+    b.hk2 = c.take<uint64_t>(kRawHitCap);
+    b.okeys = c.take<uint64_t>(kRawHitCap);
+    b.hv = c.take<uint32_t>(kRawHitCap);
+    b.hv2 = c.take<uint32_t>(kRawHitCap);
+    b.keep = c.take<uint32_t>(kRawHitCap);
+    b.kscan = c.take<uint32_t>(kRawHitCap);
+    return c.off;
+}
+
+int ceil_log2u(unsigned long long v) {
+    int b = 0;
+    while ((1ULL << b) < v && b < 63) ++b;
+    return b;
+}
+
+#define NA_CK(call)                                                             \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) {                                                \
+            g_msg = std::string(#call) + ": " + cudaGetErrorString(e_);         \
+            return TMS_ERR_CUDA;                                                \
+        }                                                                       \
+    } while (0)
+
+// once per device, with that device current: the arena's device address
+tms_status setup(int device, unsigned char **base) {
+    if (device < 0 || device >= 64) return TMS_ERR_ARG;
+    if (g_base[device]) {
+        *base = g_base[device];
+        return TMS_OK;
+    }
+    void *p = nullptr;
+    NA_CK(cudaGetSymbolAddress(&p, g_arena));
+    NA_CK(configure_face_pass());
+    Buffers probe;
+    if (carve(reinterpret_cast<unsigned char *>(p), probe) > kArenaBytes) {
+        g_msg = "scratch layout exceeds the static arena";
+        return TMS_ERR_STATE;
+    }
+    g_base[device] = reinterpret_cast<unsigned char *>(p);
+    *base = g_base[device];
+    return TMS_OK;
+}
+
+}  // namespace
+
+extern "C" const char *tms_noalloc_last_error(void) { return g_msg.c_str(); }
+
+extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_params *params,
+                                         tms_hit *dHits, long long hitCap, long long *nHits,
+                                         void *stream) {
+    if (!nHits || hitCap < 0 || (hitCap > 0 && !dHits)) return TMS_ERR_ARG;
+    tms_params p;
+    tms_params_default(&p);
+    if (params) p = *params;
+    if ((p.precision != 0 && p.precision != 1) || (p.face_level != 0 && p.face_level != 1) ||
+        !(p.cell_mult >= 1.0f) || !(p.tau >= 0.0) || !(p.tau < 1.0)) {
+        g_msg = "invalid search parameters";
+        return TMS_ERR_ARG;
+    }
+    MeshDev ma, mb;
+    int devA = -1, devB = -1, device = 0;
+    if (mesh_view(A, &ma, &devA) != TMS_OK || mesh_view(B, &mb, &devB) != TMS_OK) return TMS_ERR_STATE;
+    NA_CK(cudaGetDevice(&device));
+    if (devA != device || devB != device) return TMS_ERR_ARG;
+    if ((unsigned long long)ma.N * ma.M > kMaxViewVertices ||
+        (unsigned long long)mb.N * mb.M > kMaxViewVertices) {
+        g_msg = "mesh view has more than 131072 vertices (the static scratch limit)";
+        return TMS_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    unsigned char *base = nullptr;
+    tms_status st = setup(device, &base);
+    if (st != TMS_OK) return st;
+    Buffers b;
+    carve(base, b);
+
+    // small tables, from host memory on the stack
+    const int block = (p.block_faces == 64 || p.block_faces == 256) ? p.block_faces : 128;
+    const int rows = p.tile_rows == 4 ? 4 : 8;
+    Tables t;
+    memset(&t, 0, sizeof(t));
+    ma.split = b.split[0];
+    mb.split = b.split[1];
+    t.meshes[0] = ma;
+    t.meshes[1] = mb;
+    t.pairs[0] = make_int2(0, 1);
+    long long tiles_all = 0, tiles_A = 0, tiles_B = 0;
+    const MeshDev *mv[2] = {&ma, &mb};
+    for (int role = 0; role < 2; ++role) {
+        PassEntry e;
+        e.mesh = role;
+        e.pair = 0;
+        e.role = role;
+        e.tiles_i = (mv[role]->nqi + block - 1) / block;
+        const long long nt = (long long)e.tiles_i * ((mv[role]->nqk + rows - 1) / rows);
+        e.tile_base = tiles_all;
+        t.all[role] = e;
+        tiles_all += nt;
+        e.tile_base = 0;
+        if (role == 0) { t.pa[0] = e; tiles_A = nt; }
+        else { t.pb[0] = e; tiles_B = nt; }
+    }
+    unsigned long long max_tri = std::max(2ULL * ma.N * ma.nqk, 2ULL * mb.N * mb.nqk);
+    const int tri_bits = ceil_log2u(max_tri);
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int grid = std::min(kMaxGrid, 2 * sms);
+    NA_CK(cudaMemcpyAsync(b.tables, &t, sizeof(t), cudaMemcpyHostToDevice, s));
+
+    // the launch sequence of tms_search, on the static buffers
+    NA_CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters), s));
+    launch_bounds_init(b.bounds, 2, s);
+    FacePassArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.meshes = b.tables->meshes;
+    fa.tile_rows = rows;
+    fa.bounds = b.bounds;
+    fa.grids = b.grids;
+    fa.bmA = b.bmA;
+    fa.bmA_word_bits = kBmAWordBits;
+    fa.bmH = b.bmH;
+    fa.bmH_word_bits = kBmHWordBits;
+    fa.ent_key = b.ek;
+    fa.ent_val = b.ev;
+    fa.ent_face = b.eface;
+    fa.ent_cell = b.ecell;
+    fa.ent_box32 = b.ebox32;
+    fa.ent_box64 = b.ebox64;
+    fa.ctr = b.ctr;
+    fa.ent_cap = kEntCap;
+    fa.entries = b.tables->all; fa.n_entries = 2; fa.total_tiles = tiles_all;
+    fa.mode = MODE_BOUNDS;
+    launch_face_pass(fa, p.precision, p.face_level, block, s);
+    launch_grid_params(b.bounds, b.tables->pairs, 1, b.grids, p.cell_mult, s);
+    if (p.cell_filter) {
+        NA_CK(cudaMemsetAsync(b.bmA, 0, (1ull << kBmAWordBits) * sizeof(uint32_t), s));
+        NA_CK(cudaMemsetAsync(b.bmH, 0, (1ull << kBmHWordBits) * sizeof(uint32_t), s));
+        fa.entries = b.tables->pa; fa.n_entries = 1; fa.total_tiles = tiles_A;
+        fa.mode = MODE_MARK;
+        launch_face_pass(fa, p.precision, p.face_level, block, s);
+        fa.entries = b.tables->pb; fa.total_tiles = tiles_B;
+        fa.mode = MODE_PROBE_MARK;
+        launch_face_pass(fa, p.precision, p.face_level, block, s);
+        fa.entries = b.tables->pa; fa.total_tiles = tiles_A;
+        fa.mode = MODE_PROBE;
+        launch_face_pass(fa, p.precision, p.face_level, block, s);
+    } else {
+        fa.entries = b.tables->all; fa.n_entries = 2; fa.total_tiles = tiles_all;
+        fa.mode = MODE_EMIT_ALL;
+        launch_face_pass(fa, p.precision, p.face_level, block, s);
+    }
+    const bool alt = radix_sort(b.ek, b.ev, b.ek2, b.ev2, b.sort_counts, &b.ctr->entries, kEntCap,
+                                32, grid, s);
+    const uint64_t *sk = alt ? b.ek2 : b.ek;
+    const uint32_t *sv = alt ? b.ev2 : b.ev;
+    CellArgs ca;
+    ca.keys = sk; ca.d_n = &b.ctr->entries; ca.cap = kEntCap;
+    ca.head = b.head; ca.head_scan = b.hscan; ca.cell_start = b.cstart; ca.cell_b = b.cb;
+    ca.cell_pairs = b.cpairs; ca.pair_off = b.poff; ca.cell_tiles = b.ctiles; ca.tile_off = b.toff;
+    ca.partials = b.partials; ca.ctr = b.ctr;
+    launch_cells(ca, grid, s);
+    EmitArgs ea;
+    ea.keys = sk; ea.vals = sv; ea.cell_start = b.cstart; ea.cell_b = b.cb; ea.tile_off = b.toff;
+    ea.ent_face = b.eface; ea.ent_cell = b.ecell; ea.ent_box32 = b.ebox32; ea.ent_box64 = b.ebox64;
+    ea.grids = b.grids; ea.meshes = b.tables->meshes; ea.pairs = b.tables->pairs; ea.ctr = b.ctr;
+    ea.ent_cap = kEntCap; ea.cand = b.cand; ea.cand_cap = kCandCap; ea.moller = p.moller;
+    launch_emit(ea, p.precision, p.face_level, grid * 4, s);
+    NarrowArgs na;
+    na.cand = b.cand; na.cand_cap = kCandCap; na.surv = b.surv; na.surv_cap = kSurvCap;
+    na.meshes = b.tables->meshes; na.pairs = b.tables->pairs; na.ctr = b.ctr; na.hits = b.hits;
+    na.hit_key = b.hk; na.hit_val = b.hv; na.hit_cap = kRawHitCap; na.tau = p.tau;
+    na.tri_bits = tri_bits; na.fp32_filter = p.narrow_filter;
+    launch_narrow(na, p.face_level, grid * 4, s);
+    const int hgrid = std::max(1, std::min(grid, (int)((kRawHitCap + kSortTile * 8 - 1) / (kSortTile * 8))));
+    const bool halt = radix_sort(b.hk, b.hv, b.hk2, b.hv2, b.sort_counts, &b.ctr->raw_hits, kRawHitCap,
+                                 2 * tri_bits, hgrid, s);
+    DedupArgs da;
+    da.keys = halt ? b.hk2 : b.hk; da.vals = halt ? b.hv2 : b.hv; da.raw = b.hits;
+    da.meshes = b.tables->meshes; da.pairs = b.tables->pairs; da.ctr = b.ctr; da.raw_cap = kRawHitCap;
+    da.keep = b.keep; da.keep_scan = b.kscan; da.partials = b.partials;
+    da.out = dHits; da.out_cap = (unsigned long long)hitCap; da.out_keys = b.okeys;
+    da.offsets = nullptr; da.n_pairs = 1; da.tri_bits = tri_bits; da.tau = p.tau;
+    launch_dedup(da, grid, s);
+    NA_CK(cudaGetLastError());
+
+    Counters c;
+    NA_CK(cudaMemcpyAsync(&c, b.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    NA_CK(cudaStreamSynchronize(s));
+    if (c.status & ST_NONFINITE) {
+        g_msg = "non-finite vertex coordinate";
+        return TMS_ERR_ARG;
+    }
+    if (c.status & ST_PAIR_LIMIT) {
+        g_msg = "grid proposes too many face pairs (degenerate geometry)";
+        return TMS_ERR_ARG;
+    }
+    if (c.entries > kEntCap || c.cand > kCandCap || c.fp64 > kSurvCap || c.raw_hits > kRawHitCap) {
+        g_msg = "a search stage exceeded the static scratch limits";
+        *nHits = -1;
+        return TMS_ERR_CAPACITY;
+    }
+    *nHits = (long long)c.out;
+    if ((long long)c.out > hitCap) {
+        g_msg = "hit buffer too small";
+        return TMS_ERR_CAPACITY;
+    }
+    return TMS_OK;
+}
