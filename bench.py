@@ -45,6 +45,30 @@ def dist_env():
     return ws, rank, local
 
 
+def committed_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json), or None when absent or taken on other sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        entry = t.get(kernel)
+        if not entry or entry.get("source_hash") != source_hash():
+            return None
+        return entry.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+def source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2109_14814_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -177,22 +201,28 @@ def run_tms(args, ws, rank, local):
     ms_per_step = total_ms / args.steps
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel, the face pass (4 launches per search).
+    # Algorithmic bytes per launch: every vertex of the pass's meshes read once
+    # (32 B: four float64), plus the bounds pass's FP32 split copy (32 B per
+    # vertex written), plus the probe passes' entries (ENTRY_BYTES each; the
+    # entry total is split between the two probe launches by face count).
     V = pair.A.N * pair.A.M
     ent = stats["entries"]
-    face_bytes = {"face_bounds": 32 * 2 * V, "face_mark_A": 32 * V,
+    face_bytes = {"face_bounds": (32 + 32) * 2 * V, "face_mark_A": 32 * V,
                   "face_probe_B": 32 * V + ENTRY_BYTES * ent / 2,
                   "face_probe_A": 32 * V + ENTRY_BYTES * ent / 2}
     face_ms = sum(stage_ms.get(k, 0.0) for k in face_bytes)
     dominant = max(stage_ms, key=stage_ms.get)
     face_gbs = (sum(face_bytes.values()) / 1e9) / (face_ms / 1e3) if face_ms > 0 else None
+    traffic = committed_traffic("k_face_pass")
     roofline = {"kernel": "tms::k_face_pass (4 launches/search: bounds, mark A, probe B, probe A)",
                 "bound": "hbm", "achieved": face_gbs, "peak": peaks.get("hbm_gbs"),
                 "unit": "GB/s", "frac": (face_gbs / peaks["hbm_gbs"]) if face_gbs else None,
-                "traffic": None, "peak_kind": f"{peaks_kind} copy bandwidth",
-                "algorithmic_bytes_per_search": sum(face_bytes.values()),
+                "traffic": traffic, "peak_kind": f"{peaks_kind} copy bandwidth",
+                "algorithmic_bytes_per_launch": sum(face_bytes.values()) / 4,
+                "launch_ms": {k: stage_ms.get(k) for k in face_bytes},
                 "share_of_step": face_ms / ms_per_step if ms_per_step else None,
-                "dominant_stage": dominant}
+                "largest_stage": dominant}
     # FP64 utilisation of the narrow phase
     fp64 = None
     try:
@@ -243,14 +273,15 @@ def run_tms(args, ws, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded manifold-like meshes)",
-        "config": dict(WORKLOAD, precision="FP32 outward boxes + FP64 narrow phase",
+        "config": dict(WORKLOAD, precision="FP32 outward boxes and certified FP32 pre-solve, FP64 narrow phase",
                        l2="256 MiB buffer written between steps, outside the step events",
                        parallelism=f"replicas x{ws}" if ws > 1 else "1 GPU",
                        hits=n_hits, candidates=stats["candidates"], entries=stats["entries"]),
         "roofline": roofline, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clk.summary(), "gpu_launches": stats["kernels"] * args.steps,
+        "source_hash": source_hash(),
         "stage_ms": stage_ms, "wall_s": wall,
     }
     if rank == 0:
