@@ -4,7 +4,7 @@
  * The library finds every intersecting pair of triangles between two
  * triangulated 2D surfaces in R^4 -- a torus's unstable-manifold mesh W^u and
  * another torus's stable-manifold mesh W^s -- following arXiv 2109.14814,
- * Sec. 5 ("Rapid GPU-Assisted Search for Manifold Intersections"): a broad
+ * Sec. 6 ("Rapid GPU-Assisted Search for Manifold Intersections"): a broad
  * phase (uniform grid over a trimmed world box, per-face axis-aligned bounding
  * boxes, optional Moller quick test) followed by a narrow phase that solves the
  * 4x4 linear system of Eq. (precise) for the barycentric pair (a, b, c, d).
@@ -21,18 +21,18 @@
  *     On an error other than TMS_ERR_CAPACITY the outputs are unspecified.
  *   - The library never falls back to a CPU implementation.
  *
- * Mesh layout (Sec. 5.1 and Sec. 5.3): four coordinate arrays x, y, px, py,
+ * Mesh layout (Sec. 6.1 and Sec. 6.3): four coordinate arrays x, y, px, py,
  * each holding N*M float64 values column-major with theta fastest:
  * coordinate of vertex W(theta_i, s_k) at [k*N + i], theta_i = 2*pi*i/N.
  * Quads Q_ik join (i, k), (i+1, k), (i, k+1), (i+1, k+1) with i+1 taken modulo
- * N on a periodic mesh (Sec. 5.1: the theta index wraps around).
+ * N on a periodic mesh (Sec. 6.1: the theta index wraps around).
  * Each quad is split into two triangles along the (i+1, k)-(i, k+1) diagonal
- * with the vertex orderings of Sec. 5.2.4:
+ * with the vertex orderings of Sec. 6.2.4:
  *   T1: x1 = W(i+1, k), x2 = W(i, k),     x3 = W(i, k+1)
  *   T2: x1 = W(i, k+1), x2 = W(i+1, k+1), x3 = W(i+1, k)
  * Within a mesh view of vertex columns [k0, k1), quad (i, k) (k relative to
  * k0) has id q = k*N + i and its triangles have ids t = 2*q (T1), 2*q + 1 (T2).
- * A quad hit is derivable from a triangle hit as q = t >> 1 (Sec. 5.2: a quad
+ * A quad hit is derivable from a triangle hit as q = t >> 1 (Sec. 6.2: a quad
  * pair intersects iff one of its four triangle pairs does).
  */
 #ifndef TMS_H
@@ -60,7 +60,7 @@ typedef struct tms_mesh_s *tms_mesh;
 
 /*
  * tms_build_mesh -- describe one manifold half-layer mesh.  A half-layer is a
- * contiguous range of s columns of the full vertex arrays (Sec. 5.2), so the
+ * contiguous range of s columns of the full vertex arrays (Sec. 6.2), so the
  * view is zero-copy.
  *   dX, dY, dPx, dPy : device, N*M float64 each, layout above.  Borrowed: they
  *                      must stay valid and unchanged while the handle is used.
@@ -95,7 +95,7 @@ typedef struct {
     int face_level;       /* 0 = one box per triangle; 1 = one box per quad, as
                              the paper's kernel (4 triangle pairs per candidate;
                              default). */
-    int moller;           /* 1 = apply the Moller quick test of Sec. 5.2.3 (FP64,
+    int moller;           /* 1 = apply the Moller quick test of Sec. 6.2.3 (FP64,
                              with a rounding guard) to candidates; default 0. */
     int cell_filter;      /* 1 = register only faces in grid cells occupied by
                              both meshes before the sort (default); 0 = emit
@@ -104,7 +104,7 @@ typedef struct {
                              forward-error bound certifies margin < -2 tau
                              (default); undecided candidates get the FP64 solve. */
     float cell_mult;      /* grid cell edge = cell_mult x widest face extent per
-                             coordinate (Sec. 5.2.1 requires > 1 x); default 1.0625 */
+                             coordinate (Sec. 6.2.1 requires > 1 x); default 1.0625 */
     double tau;           /* margin tolerance of the hit test, default 1e-12 */
     long long entry_capacity;  /* initial scratch sizes (0 = automatic); grown on */
     long long cand_capacity;   /* overflow and retried inside the call          */
@@ -123,7 +123,7 @@ typedef struct {
 
 void tms_params_default(tms_params *p);
 
-/* One hit: an intersecting triangle pair (Sec. 5.2.4) and its estimates. */
+/* One hit: an intersecting triangle pair (Sec. 6.2.4) and its estimates. */
 typedef struct {
     uint32_t triA, triB;   /* triangle ids in mesh A and mesh B */
     uint32_t pair;         /* mesh-pair index (0 for tms_search) */
@@ -132,7 +132,7 @@ typedef struct {
                               edge or vertex (this record is the representative) */
     double a, b, c, d;     /* solution of Eq. (precise) */
     double P[4];           /* x-side point x2 + a(x1-x2) + b(x3-x2) */
-    double theta_u, s_u;   /* estimates on mesh A, Sec. 5.2.4 (theta in [0, 2pi)) */
+    double theta_u, s_u;   /* estimates on mesh A, Sec. 6.2.4 (theta in [0, 2pi)) */
     double theta_s, s_s;   /* estimates on mesh B */
     double rho;            /* |det| / product of the column norms */
     double margin;         /* min(a, b, c, d, 1-a-b, 1-c-d) */

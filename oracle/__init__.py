@@ -7,7 +7,7 @@ compiled without fused multiply-add); this module only loads it, runs it over
 mesh pairs and applies the post-processing rules written out below.
 
 Post-processing (no counterpart in the paper, which stores every hit of every
-triangle pair, Sec. 5.2.4 and Sec. 5.3):
+triangle pair, Sec. 6.2.4 and Sec. 6.3):
   * merging of duplicate hits: a hit whose point lies on a shared edge or vertex
     of a mesh is found by every triangle pair incident to that feature.  Each
     side's feature is read off its barycentric weights (w1, w2, w3) =
@@ -232,7 +232,7 @@ def pair_grad(x, y, gP, gz):
 # ----------------------------------------------------------------------------
 
 def tri_vertex_ids(m: OMesh, t: int):
-    """Vertex ids (k*N + i) of (x1, x2, x3) of triangle t (Sec. 5.2.3 orderings)."""
+    """Vertex ids (k*N + i) of (x1, x2, x3) of triangle t (Sec. 6.2.4 orderings)."""
     q, tau = divmod(int(t), 2)
     k, i = divmod(q, m.N)
     ip = (i + 1) % m.N

@@ -11,16 +11,16 @@
  * separately, as written).
  *
  * What it follows (arXiv 2109.14814):
- *   - mesh and triangle definitions: Sec. 5.1 (vertex grid, quads Q_ik with the
- *     theta index taken modulo N) and Sec. 5.2 (triangles T1, T2 of each quad);
- *   - the narrow-phase test: Sec. 5.2.4, Eq. (precise): solve
+ *   - mesh and triangle definitions: Sec. 6.1 (vertex grid, quads Q_ik with the
+ *     theta index taken modulo N) and Sec. 6.2 (triangles T1, T2 of each quad);
+ *   - the narrow-phase test: Sec. 6.2.4, Eq. (precise): solve
  *       x2 + (x1 - x2) a + (x3 - x2) b = y2 + (y1 - y2) c + (y3 - y2) d
  *     for (a, b, c, d); the triangles meet iff a, b, c, d >= 0, a + b <= 1 and
  *     c + d <= 1, and the common point is either side of the equation;
- *   - the (theta, s) estimates from (a, b) and (c, d): Sec. 5.2.4, the four
+ *   - the (theta, s) estimates from (a, b) and (c, d): Sec. 6.2.4, the four
  *     interpolation formulas that follow Eq. (precise), with the vertex orderings
  *     x1, x2, x3 (and y1, y2, y3) given there;
- *   - the bounding-box test used for exact pruning: Sec. 5.2.2
+ *   - the bounding-box test used for exact pruning: Sec. 6.2.2
  *     (two boxes are disjoint iff some coordinate's max of one is below the
  *     other's min); a triangle lies inside its box, so pruning by closed box
  *     overlap never removes an intersecting pair.
@@ -59,7 +59,7 @@ typedef struct {
 } oracle_rec;
 
 /* ---------------------------------------------------------------------- */
-/* mesh enumeration (Sec. 5.1, Sec. 5.2)                                   */
+/* mesh enumeration (Sec. 6.1, Sec. 6.2)                                   */
 /* ---------------------------------------------------------------------- */
 
 static long long n_tri_ids(const omesh *m) { return 2LL * m->N * (m->M - 1); }
@@ -172,7 +172,7 @@ int oracle_solve4_flat(const double *A16, const double *r4, double *z4, double *
 }
 
 /* ---------------------------------------------------------------------- */
-/* narrow phase for one triangle pair (Sec. 5.2.4, Eq. (precise))           */
+/* narrow phase for one triangle pair (Sec. 6.2.4, Eq. (precise))           */
 /* ---------------------------------------------------------------------- */
 
 static double min6(double a, double b, double c, double d, double e, double f) {

@@ -1,7 +1,7 @@
 """GB300-native (sm_103a) mesh-vs-mesh intersection search.
 
 Finds every intersecting triangle pair between two manifold meshes in R^4
-(arXiv 2109.14814, Sec. 5): uniform-grid broad phase with bounding boxes, FP64
+(arXiv 2109.14814, Sec. 6): uniform-grid broad phase with bounding boxes, FP64
 narrow phase solving the 4x4 system for (a, b, c, d), merged and sorted hits,
 a batched form replayed from a CUDA graph, and an FP64 adjoint.  All compute is
 in libtms.so (C ABI in include/tms.h); this package only marshals arguments.

@@ -237,7 +237,7 @@ __device__ __forceinline__ int cell_of(double v, double o, double inv, int n) {
     return (int)t;
 }
 
-// Triangle vertex grid indices, Sec. 5.2.4 orderings.
+// Triangle vertex grid indices, Sec. 6.2.4 orderings.
 // T1 (tau 0): x1 = (i+1, k), x2 = (i, k), x3 = (i, k+1)
 // T2 (tau 1): x1 = (i, k+1), x2 = (i+1, k+1), x3 = (i+1, k)
 __device__ __forceinline__ void tri_ij(const MeshDev &m, uint32_t t, int ii[3], int kk[3]) {

@@ -1,8 +1,8 @@
 // Face passes of the broad phase: one read of a mesh's vertex grid per pass.
 //
-// Broad phase of arXiv 2109.14814, Sec. 5.2.1-5.2.2, re-designed for GB300:
+// Broad phase of arXiv 2109.14814, Sec. 6.2.1-6.2.2, re-designed for GB300:
 //   MODE_BOUNDS      per-mesh world bounds, widest face extent per coordinate
-//                    (the grid rule of Sec. 5.2.1: cell edge > widest face), and
+//                    (the grid rule of Sec. 6.2.1: cell edge > widest face), and
 //                    a finiteness check of every vertex;
 //   MODE_MARK        occupancy bits of the cells covered by mesh A's faces;
 //   MODE_PROBE_MARK  mesh B: one entry per face-cell incidence in a cell that
@@ -10,7 +10,7 @@
 //   MODE_PROBE       mesh A: one entry per face-cell incidence in a hot cell;
 //   MODE_EMIT_ALL    one entry per face-cell incidence (no filter).
 // Cells that do not hold faces of both meshes are dropped, as the paper drops
-// grid boxes whose quad list is empty on either side (Sec. 5.3); the occupancy
+// grid boxes whose quad list is empty on either side (Sec. 6.3); the occupancy
 // bitmaps only decide this before any list is built.  A bitmap is a blocked
 // Bloom filter over hash(pair, cell): a false positive only adds entries, never
 // removes one, so every face pair sharing a cell still meets in the sort.
@@ -439,7 +439,7 @@ __global__ void k_bounds_init(Bounds *b, int n) {
     b[m].faces = 0;
 }
 
-// Trimmed world and uniform grid of each pair (Sec. 5.2.1 and its remark).
+// Trimmed world and uniform grid of each pair (Sec. 6.2.1 and its remark).
 // World along coordinate d: the overlap of the two meshes' ranges; a face whose
 // box misses it cannot meet any face of the other mesh.  Cell edge: cell_mult x
 // the widest face extent of either mesh, so that a face spans at most two cells

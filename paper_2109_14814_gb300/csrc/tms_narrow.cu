@@ -1,6 +1,6 @@
 // Narrow phase, merging of duplicate hits, output, and the adjoint.
 //
-// Narrow phase (arXiv 2109.14814, Sec. 5.2.4, Eq. (precise)): for triangles
+// Narrow phase (arXiv 2109.14814, Sec. 6.2.4, Eq. (precise)): for triangles
 // (x1, x2, x3) and (y1, y2, y3), the unknowns (a, b, c, d) solve the 4x4 system
 //   [x1-x2 | x3-x2 | y2-y1 | y2-y3] (a, b, c, d)^T = y2 - x2,
 // and the triangles meet iff a, b, c, d >= 0, a + b <= 1, c + d <= 1; the common

@@ -3,7 +3,7 @@
 // After the sort, entries of one (pair, cell) are contiguous with mesh A's
 // entries first (the role is the key's lowest bit).  Per cell: the start of its
 // A list and B list and nA * nB, the number of face pairs it proposes; the
-// exclusive scan of nA * nB is the paper's box_gid_idxs array (Sec. 5.3,
+// exclusive scan of nA * nB is the paper's box_gid_idxs array (Sec. 6.3,
 // Algorithm 1).
 //
 // Emission re-designed for GB300: the nA x nB pair matrix of a cell is cut
@@ -12,10 +12,10 @@
 // broadcast, so a proposed pair costs a few compares and no memory traffic.
 // (Algorithm 1 gives every proposed pair its own work item that locates its
 // box with a linear walk and fetches vertices.)  Per pair: the bounding-box
-// test of Sec. 5.2.2, then the owner-cell rule -- the pair is kept only in the
+// test of Sec. 6.2.2, then the owner-cell rule -- the pair is kept only in the
 // cell that is the componentwise max of the two faces' lowest cells, so a pair
 // sharing several cells is emitted exactly once -- then optionally the Moller
-// quick test of Sec. 5.2.3; survivors are compacted with one atomic per warp.
+// quick test of Sec. 6.2.3; survivors are compacted with one atomic per warp.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -113,7 +113,7 @@ struct TileEntry {
     uint32_t pad;
 };
 
-// Moller quick test (Sec. 5.2.3) on the (x, y, px) projection.  The plane of a
+// Moller quick test (Sec. 6.2.3) on the (x, y, px) projection.  The plane of a
 // triangle (x1, x2, x3) has normal (x1 - x2) x (x3 - x2); a point set lies
 // strictly on one side when f = n . (X - x2) has one strict sign at all points.
 // A rounding guard makes the test conservative: a value counts as signed only

@@ -9,12 +9,12 @@ triangle of mesh B is translated rigidly so that it contains that same point at
 chosen weights.  The recorded (a, b, c, d), point P and (theta, s) parameters are
 therefore known in closed form, independent of any solver.
 
-Mesh storage follows the paper's vertex-grid layout (Sec. 5.1 and Sec. 5.3):
+Mesh storage follows the paper's vertex-grid layout (Sec. 6.1 and Sec. 6.3):
 four N x M coordinate arrays x, y, px, py, theta fastest, here one float64
 tensor X of shape (4, M, N) with X[c, k, i] = coordinate c of W(theta_i, s_k),
 theta_i = 2*pi*i/N.  Quads are Q_ik for i in [0, N) (periodic in theta) and
 k in [0, M-1); quad id q = k*N + i and triangle id t = 2*q + tau (tau = 0 for
-T1, tau = 1 for T2), with the vertex orderings of Sec. 5.2.3:
+T1, tau = 1 for T2), with the vertex orderings of Sec. 6.2.4:
   T1: x1 = W(i+1, k), x2 = W(i, k),   x3 = W(i, k+1)
   T2: x1 = W(i, k+1), x2 = W(i+1, k+1), x3 = W(i+1, k)
 
@@ -217,7 +217,7 @@ def _normal_frame(Xt, Xs, gen_dirs, reg: float = 0.25):
 # ----------------------------------------------------------------------------
 
 def tri_vertex_ij(N: int, t: int):
-    """(i, k) grid indices of (x1, x2, x3) of triangle t, Sec. 5.2.3 orderings."""
+    """(i, k) grid indices of (x1, x2, x3) of triangle t, Sec. 6.2.4 orderings."""
     q, tau = divmod(t, 2)
     k, i = divmod(q, N)
     ip = (i + 1) % N
