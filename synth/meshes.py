@@ -363,6 +363,13 @@ def build_pair(seed: int, NA: int, MA: int, NB: int, MB: int, *, stretch: str = 
     usedB = torch.zeros(MB, NB, dtype=torch.bool)
     XA_cpu = XA.cpu()
     XB_cpu = XB.cpu()
+    # planting decisions (transversality) are taken on the alpha_ref surfaces in a
+    # family, so that every member of the family plants the same sites
+    if with_dalpha and alpha != alpha_ref:
+        XA_dec = _surface_A(fam, thA, sA, alpha_ref)[0].cpu()
+        XB_dec = (_surface_A(fam, thB + c0, 1.0 - sB, alpha_ref)[0] + H).cpu()
+    else:
+        XA_dec, XB_dec = XA_cpu, XB_cpu
     dXA_cpu = XAa.cpu()
     dXB_cpu = dXB.cpu()
     corr = torch.zeros(4, MB, NB, dtype=torch.float64)
@@ -397,7 +404,8 @@ def build_pair(seed: int, NA: int, MA: int, NB: int, MB: int, *, stretch: str = 
             c, d = -eta, min(max(d, 0.2), 0.7)
         va = tri_vertex_ij(NA, triA)
         xv = [XA_cpu[:, vk, vi] for (vi, vk) in va]
-        if _plane_transversality(xv, yv) < min_transversality:
+        if _plane_transversality([XA_dec[:, vk, vi] for (vi, vk) in va],
+                                 [XB_dec[:, vk, vi] for (vi, vk) in vb]) < min_transversality:
             continue
         # disjoint supports on B
         rows = [kb + dk for dk in range(-T_taper, 2 + T_taper) if 0 <= kb + dk < MB]
