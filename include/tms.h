@@ -192,6 +192,32 @@ tms_status tms_backward(tms_mesh A, tms_mesh B, const tms_hit *dHits, long long 
                         const double *dDvDalphaA, const double *dDvDalphaB,
                         double *dGradAlpha, void *stream);
 
+/*
+ * tms_autotune -- picks, for these meshes, the search parameters the paper
+ * leaves to the implementation (Sec. 6.2.1 grid cell size; Sec. 6.3 launch
+ * shape): face level (quads or triangles), cell_mult in {1.0625, 1.5, 2.5} and
+ * block_faces in {64, 128, 256}, by timing each of the 18 settings (one warm-up
+ * and three timed runs, median) with tms_search (nPairs == 1) or
+ * tms_search_batched (nPairs > 1) on `stream`.  The other fields (precision,
+ * filters, tau, capacities, use_graph) come from `base` (NULL = defaults) and
+ * are kept.  Results are unchanged by the choice: every setting finds the same
+ * hits.
+ *   A, B       : nPairs mesh handles each (host arrays).
+ *   best       : host out, `base` with the three fields set to the fastest.
+ *   cache_path : text file, or NULL for no cache.  A line per tuned key
+ *                "<device>|pairs=..|sizes=<hash of every N,M>|prec=..|... fl cm bf tr ms";
+ *                a matching line is returned without timing anything; a new
+ *                result is appended.
+ *   best_ms    : host out (may be NULL), median time of the chosen setting.
+ * Allocates trial output buffers with cudaMalloc and frees them, releases the
+ * trial plans of `stream` between settings, synchronises.  TMS_ERR_ARG on NULL
+ * handles or nPairs <= 0; a setting that fails is skipped; TMS_ERR_CUDA when
+ * none succeeds.
+ */
+tms_status tms_autotune(const tms_mesh *A, const tms_mesh *B, int nPairs,
+                        const tms_params *base, tms_params *best, const char *cache_path,
+                        double *best_ms, void *stream);
+
 /* Per-stage statistics of the last search on `stream` (host copies). */
 typedef struct {
     long long entries;      /* face-cell entries sorted */

@@ -8,12 +8,12 @@ in libtms.so (C ABI in include/tms.h); this package only marshals arguments.
 """
 from ._binding import (HIT_BYTES, STAGES, TMS_ERR_ARG, TMS_ERR_CAPACITY, TMS_ERR_CUDA,
                        TMS_ERR_STATE, TMS_ERR_TIMEOUT, TMS_OK, HitPoint, Hits, Mesh, Params, Stats,
-                       TmsError, backward, last_error, last_stage_ms, last_stats, lib, params,
+                       TmsError, autotune, backward, last_error, last_stage_ms, last_stats, lib, params,
                        probe_fp64_tflops, release_workspace, search, search_batched,
                        search_noalloc, status_str, version)
 
 __all__ = ["HIT_BYTES", "STAGES", "TMS_ERR_ARG", "TMS_ERR_CAPACITY", "TMS_ERR_CUDA",
            "TMS_ERR_STATE", "TMS_ERR_TIMEOUT", "TMS_OK", "HitPoint", "Hits", "Mesh", "Params",
-           "Stats", "TmsError", "backward", "last_error", "last_stage_ms", "last_stats", "lib",
+           "Stats", "TmsError", "autotune", "backward", "last_error", "last_stage_ms", "last_stats", "lib",
            "params", "probe_fp64_tflops", "release_workspace", "search", "search_batched",
            "search_noalloc", "status_str", "version"]

@@ -113,6 +113,9 @@ def lib():
     L.tms_search_noalloc.restype = I
     L.tms_noalloc_last_error.argtypes = []
     L.tms_noalloc_last_error.restype = _c.c_char_p
+    L.tms_autotune.argtypes = [P, P, I, _c.POINTER(Params), _c.POINTER(Params), _c.c_char_p,
+                               _c.POINTER(D), P]
+    L.tms_autotune.restype = I
     _lib = L
     return L
 
@@ -135,6 +138,26 @@ def search_noalloc(A: "Mesh", B: "Mesh", out: torch.Tensor, stream=None, **kw) -
         RuntimeError.__init__(err, f"tms_search_noalloc: {status_str(rc)} ({msg})")
         raise err
     return Hits(out[: n.value])
+
+
+def autotune(As: Sequence["Mesh"], Bs: Sequence["Mesh"], cache_path: Optional[str] = None,
+             stream=None, **kw):
+    """tms_autotune: the fastest (face_level, cell_mult, block_faces) for these
+    mesh pairs (one pair: tms_search; several: tms_search_batched), the other
+    parameters taken from **kw.  Returns (params dict, median ms)."""
+    if len(As) != len(Bs) or not As:
+        raise ValueError("As and Bs must be non-empty and of equal length")
+    base = params(**kw)
+    best = Params()
+    ms = _c.c_double(0.0)
+    ha = (_c.c_void_p * len(As))(*[m.handle.value for m in As])
+    hb = (_c.c_void_p * len(Bs))(*[m.handle.value for m in Bs])
+    rc = lib().tms_autotune(ha, hb, len(As), _c.byref(base), _c.byref(best),
+                            cache_path.encode() if cache_path else None, _c.byref(ms),
+                            _stream(stream))
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_autotune")
+    return {f: getattr(best, f) for f, _ in Params._fields_}, float(ms.value)
 
 
 def probe_fp64_tflops(stream=None) -> float:

@@ -67,3 +67,8 @@ def test_null_arguments_rejected_without_gpu():
     assert lib.tms_destroy_mesh(None) == tms.TMS_ERR_STATE
     n = ctypes.c_longlong()
     assert lib.tms_search(None, None, None, None, 0, ctypes.byref(n), None) != tms.TMS_OK
+    best = tms.Params()
+    assert lib.tms_autotune(None, None, 1, None, ctypes.byref(best), None, None,
+                            None) == tms.TMS_ERR_ARG
+    assert lib.tms_autotune(None, None, 0, None, ctypes.byref(best), None, None,
+                            None) == tms.TMS_ERR_ARG
