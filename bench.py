@@ -45,6 +45,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest `value` over all ranks of the process group (the job's time
+    is its slowest rank's); `value` itself when there is no group."""
+    dist = torch.distributed
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_times(total_ms: float, steps: int, ws: int):
+    """(ms per search over the whole job, ms per step) from the slowest rank's
+    time for `steps` steps; each rank searches one replica per step, so the job
+    completes steps * ws searches in total_ms."""
+    return total_ms / (steps * ws), total_ms / steps
+
+
 def committed_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary
     (profiles/traffic.json), or None when absent or taken on other sources."""
@@ -190,15 +208,10 @@ def run_tms(args, ws, rank, local):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), device)
     if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
-    searches = args.steps * ws
-    value = total_ms / searches                       # aggregate ms per search
-    ms_per_step = total_ms / args.steps
+    value, ms_per_step = job_times(total_ms, args.steps, ws)
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
 
     # roofline of the dominant kernel, the face pass (4 launches per search).
