@@ -35,7 +35,7 @@ WORKLOAD = dict(workload="mesh-vs-mesh search, 4096x512 vs 4096x512 vertex grids
                          "(4,186,112 triangles per mesh), lambda=4 stretch, 3 folds, "
                          "256 planted hits + 1e4 planted near-misses (1e-9..1e-3)",
                 N=4096, M=512, triangles_per_mesh=4186112)
-ENTRY_BYTES = 8 + 4 + 4 + 8 + 32      # key, index, face id, cell coords, FP32 box
+ENTRY_BYTES = 8 + 4                   # face-cell entry: u64 key, u32 face id
 
 
 def dist_env():
@@ -214,28 +214,46 @@ def run_tms(args, ws, rank, local):
     value, ms_per_step = job_times(total_ms, args.steps, ws)
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
 
-    # roofline of the dominant kernel, the face pass (4 launches per search).
-    # Algorithmic bytes per launch: every vertex of the pass's meshes read once
-    # (32 B: four float64), plus the bounds pass's FP32 split copy (32 B per
-    # vertex written), plus the probe passes' entries (ENTRY_BYTES each; the
-    # entry total is split between the two probe launches by face count).
+    # Roofline per kernel (stage), from its algorithmic bytes per launch -- what
+    # the stage must move at least, counted from the workload and the search's
+    # own statistics -- and its CUDA-event time; the slowest stage is reported
+    # as `roofline`.  V vertices and F faces per mesh (quads), E face-cell
+    # entries, C candidate quad pairs, S FP64 solves.
     V = pair.A.N * pair.A.M
-    ent = stats["entries"]
-    face_bytes = {"face_bounds": (32 + 32) * 2 * V, "face_mark_A": 32 * V,
-                  "face_probe_B": 32 * V + ENTRY_BYTES * ent / 2,
-                  "face_probe_A": 32 * V + ENTRY_BYTES * ent / 2}
-    face_ms = sum(stage_ms.get(k, 0.0) for k in face_bytes)
-    dominant = max(stage_ms, key=stage_ms.get)
-    face_gbs = (sum(face_bytes.values()) / 1e9) / (face_ms / 1e3) if face_ms > 0 else None
-    traffic = committed_traffic("k_face_pass")
-    roofline = {"kernel": "tms::k_face_pass (4 launches/search: bounds, mark A, probe B, probe A)",
-                "bound": "hbm", "achieved": face_gbs, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": (face_gbs / peaks["hbm_gbs"]) if face_gbs else None,
+    F = pair.A.N * (pair.A.M - 1)
+    E, C, S = stats["entries"], stats["candidates"], stats["fp64_solves"]
+    passes = math.ceil(32 / 8)
+    algo = {
+        # vertices read (4 x f64), FP32 split copy written (2 x float4), face box written (2 x float4)
+        "face_bounds": ("tms::k_bounds_pass", 1, 2 * (32 * V + 32 * V + 32 * F)),
+        # face boxes read (mark A, probe B, probe A) and entries written (u64 key + u32 face)
+        "face_mark_A": ("tms::k_cell_pass<MARK>", 1, 32 * F),
+        "face_probe_B+A": ("tms::k_cell_pass<PROBE_MARK, PROBE>", 2, 2 * 32 * F + ENTRY_BYTES * E),
+        # LSD radix sort of (key, face): every pass reads and writes both
+        "sort_entries": ("tms::k_radix_* (entry sort)", 3 * passes, passes * 2 * ENTRY_BYTES * E),
+        # each entry's face id and face box read once, candidates written
+        "emit": ("tms::k_emit", 1, E * (4 + 32) + C * 16),
+        # candidates read, the FP32 split vertices of both quads gathered, FP64 solves' vertices
+        "narrow": ("tms::k_narrow_filter + k_narrow_fp64", 2, C * (16 + 2 * 4 * 32) + S * 2 * 3 * 32),
+    }
+    stage_time = dict(stage_ms)
+    stage_time["face_probe_B+A"] = stage_ms.get("face_probe_B", 0.0) + stage_ms.get("face_probe_A", 0.0)
+    kernels = {}
+    for st_name, (kname, launches, nbytes) in algo.items():
+        t = stage_time.get(st_name, 0.0)
+        gbs = (nbytes / 1e9) / (t / 1e3) if t > 0 else None
+        kernels[st_name] = {"kernel": kname, "launches": launches, "ms": t,
+                            "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
+                            "frac": gbs / peaks["hbm_gbs"] if gbs else None}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    d = kernels[dom]
+    traffic = committed_traffic(d["kernel"])
+    roofline = {"kernel": d["kernel"], "stage": dom, "bound": "hbm", "achieved": d["achieved_gbs"],
+                "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": d["frac"],
                 "traffic": traffic, "peak_kind": f"{peaks_kind} copy bandwidth",
-                "algorithmic_bytes_per_launch": sum(face_bytes.values()) / 4,
-                "launch_ms": {k: stage_ms.get(k) for k in face_bytes},
-                "share_of_step": face_ms / ms_per_step if ms_per_step else None,
-                "largest_stage": dominant}
+                "algorithmic_bytes_per_launch": d["algorithmic_bytes"] / d["launches"],
+                "launches": d["launches"], "share_of_step": d["ms"] / ms_per_step if ms_per_step else None,
+                "largest_stage": max(stage_ms, key=stage_ms.get)}
     # FP64 utilisation of the narrow phase
     fp64 = None
     try:
@@ -291,8 +309,10 @@ def run_tms(args, ws, rank, local):
         "config": dict(WORKLOAD, precision="FP32 outward boxes and certified FP32 pre-solve, FP64 narrow phase",
                        l2="256 MiB buffer written between steps, outside the step events",
                        parallelism=f"replicas x{ws}" if ws > 1 else "1 GPU",
-                       hits=n_hits, candidates=stats["candidates"], entries=stats["entries"]),
-        "roofline": roofline, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
+                       hits=n_hits, candidates=stats["candidates"], entries=stats["entries"],
+                       cells=stats["cells"], pair_slots=stats["pair_slots"],
+                       fp64_solves=stats["fp64_solves"]),
+        "roofline": roofline, "kernels": kernels, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clk.summary(), "gpu_launches": stats["kernels"] * args.steps,
         "source_hash": source_hash(),
         "stage_ms": stage_ms, "wall_s": wall,

@@ -72,6 +72,7 @@ struct Plan {
     PassEntry *d_pass_all = nullptr, *d_pass_A = nullptr, *d_pass_B = nullptr;
     int n_pass_all = 0, n_pass_A = 0, n_pass_B = 0;
     long long tiles_all = 0, tiles_A = 0, tiles_B = 0;
+    long long fslots_all = 0, fslots_A = 0, fslots_B = 0;   // padded face slots per pass
     unsigned long long facesA = 0, facesB = 0;
     int tri_bits = 0, pair_bits = 0;
     // scratch
@@ -84,10 +85,7 @@ struct Plan {
     int bmA_bits = 0, bmH_bits = 0;
     unsigned long long ent_cap = 0, cand_cap = 0, hit_cap = 0;
     uint64_t *ek = nullptr, *ek2 = nullptr;
-    uint32_t *ev = nullptr, *ev2 = nullptr, *eface = nullptr;
-    uint2 *ecell = nullptr;
-    float4 *ebox32 = nullptr;
-    double *ebox64 = nullptr;
+    uint32_t *ev = nullptr, *ev2 = nullptr;
     uint32_t *sort_counts = nullptr;
     unsigned long long *partials = nullptr;
     uint32_t *head = nullptr, *hscan = nullptr, *cstart = nullptr, *cb = nullptr;
@@ -96,6 +94,7 @@ struct Plan {
     float4 *split = nullptr;          // FP32 split vertex copies of all meshes
     unsigned long long split_total = 0;
     std::vector<unsigned long long> split_off;
+    unsigned char *fbox = nullptr;    // face boxes of all meshes
     unsigned long long surv_cap = 0;
     tms_hit *hits = nullptr;
     uint64_t *hk = nullptr, *hk2 = nullptr, *okeys = nullptr;
@@ -113,13 +112,11 @@ struct Plan {
     unsigned long long last_use = 0;
 
     void free_scratch() {
-        void *ptrs[] = {bmA, bmH, ek, ek2, ev, ev2, eface, ecell, ebox32, ebox64, sort_counts,
-                        head, hscan, cstart, cb, cpairs, poff, ctiles, toff, cand, surv, hits, hk,
+        void *ptrs[] = {bmA, bmH, ek, ek2, ev, ev2, sort_counts, head, hscan, cstart, cb, cpairs, poff, ctiles, toff, cand, surv, hits, hk,
                         hk2, okeys, hv, hv2, keep, kscan};
         for (void *p : ptrs)
             if (p) cudaFree(p);
-        bmA = bmH = nullptr; ek = ek2 = nullptr; ev = ev2 = eface = nullptr; ecell = nullptr;
-        ebox32 = nullptr; ebox64 = nullptr; sort_counts = nullptr; head = hscan = cstart = cb = nullptr;
+        bmA = bmH = nullptr; ek = ek2 = nullptr; ev = ev2 = nullptr; sort_counts = nullptr; head = hscan = cstart = cb = nullptr;
         cpairs = poff = ctiles = toff = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
         hv = hv2 = keep = kscan = nullptr;
         if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
@@ -128,7 +125,7 @@ struct Plan {
         if (st) cudaStreamSynchronize(st);
         free_scratch();
         void *ptrs[] = {d_meshes, d_pairs, d_pass_all, d_pass_A, d_pass_B, d_bounds, d_grids,
-                        d_ctr, partials, split};
+                        d_ctr, partials, split, fbox};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         if (h_ctr) cudaFreeHost(h_ctr);
@@ -142,17 +139,12 @@ struct Plan {
 
     tms_status alloc_scratch() {
         free_scratch();
-        const int prec = prm.precision;
         TMS_CK(dalloc(&bmA, (size_t)1 << (bmA_bits)));
         TMS_CK(dalloc(&bmH, (size_t)1 << (bmH_bits)));
         TMS_CK(dalloc(&ek, ent_cap));
         TMS_CK(dalloc(&ek2, ent_cap));
         TMS_CK(dalloc(&ev, ent_cap));
         TMS_CK(dalloc(&ev2, ent_cap));
-        TMS_CK(dalloc(&eface, ent_cap));
-        TMS_CK(dalloc(&ecell, ent_cap));
-        if (prec == 1) TMS_CK(dalloc(&ebox32, 2 * ent_cap));
-        else TMS_CK(dalloc(&ebox64, 8 * ent_cap));
         TMS_CK(dalloc(&sort_counts, (size_t)kRadixBins * grid));
         TMS_CK(dalloc(&head, ent_cap));
         TMS_CK(dalloc(&hscan, ent_cap));
@@ -210,10 +202,6 @@ struct Plan {
         fa.bmH_word_bits = bmH_bits;
         fa.ent_key = ek;
         fa.ent_val = ev;
-        fa.ent_face = eface;
-        fa.ent_cell = ecell;
-        fa.ent_box32 = ebox32;
-        fa.ent_box64 = ebox64;
         fa.ctr = d_ctr;
         fa.ent_cap = ent_cap;
 
@@ -229,15 +217,15 @@ struct Plan {
             cudaMemsetAsync(bmA, 0, ((size_t)1 << bmA_bits) * sizeof(uint32_t), s);
             cudaMemsetAsync(bmH, 0, ((size_t)1 << bmH_bits) * sizeof(uint32_t), s);
             mark(4, s);
-            fa.entries = d_pass_A; fa.n_entries = n_pass_A; fa.total_tiles = tiles_A;
+            fa.entries = d_pass_A; fa.n_entries = n_pass_A; fa.total_faces = fslots_A;
             fa.mode = MODE_MARK;
             launch_face_pass(fa, prec, fl, block, s);
             mark(5, s);
-            fa.entries = d_pass_B; fa.n_entries = n_pass_B; fa.total_tiles = tiles_B;
+            fa.entries = d_pass_B; fa.n_entries = n_pass_B; fa.total_faces = fslots_B;
             fa.mode = MODE_PROBE_MARK;
             launch_face_pass(fa, prec, fl, block, s);
             mark(6, s);
-            fa.entries = d_pass_A; fa.n_entries = n_pass_A; fa.total_tiles = tiles_A;
+            fa.entries = d_pass_A; fa.n_entries = n_pass_A; fa.total_faces = fslots_A;
             fa.mode = MODE_PROBE;
             launch_face_pass(fa, prec, fl, block, s);
             kernels += 3;
@@ -245,7 +233,7 @@ struct Plan {
             mark(4, s);
             mark(5, s);
             mark(6, s);
-            fa.entries = d_pass_all; fa.n_entries = n_pass_all; fa.total_tiles = tiles_all;
+            fa.entries = d_pass_all; fa.n_entries = n_pass_all; fa.total_faces = fslots_all;
             fa.mode = MODE_EMIT_ALL;
             launch_face_pass(fa, prec, fl, block, s);
             kernels += 1;
@@ -271,7 +259,6 @@ struct Plan {
 
         EmitArgs ea;
         ea.keys = sk; ea.vals = sv; ea.cell_start = cstart; ea.cell_b = cb; ea.tile_off = toff;
-        ea.ent_face = eface; ea.ent_cell = ecell; ea.ent_box32 = ebox32; ea.ent_box64 = ebox64;
         ea.grids = d_grids; ea.meshes = d_meshes; ea.pairs = d_pairs; ea.ctr = d_ctr;
         ea.ent_cap = ent_cap; ea.cand = cand; ea.cand_cap = cand_cap; ea.moller = p.moller;
         launch_emit(ea, prec, fl, grid * 4, s);
@@ -383,8 +370,8 @@ tms_status check_mesh(tms_mesh m, int device) {
     return TMS_OK;
 }
 
-void fill_pass(std::vector<PassEntry> &v, long long &tiles, const tms_mesh m, int mesh_index,
-               int pair, int role, int block, int rows) {
+void fill_pass(std::vector<PassEntry> &v, long long &tiles, long long &fslots, const tms_mesh m,
+               int mesh_index, int pair, int role, int block, int rows, int face_level) {
     PassEntry e;
     e.mesh = mesh_index;
     e.pair = pair;
@@ -393,6 +380,9 @@ void fill_pass(std::vector<PassEntry> &v, long long &tiles, const tms_mesh m, in
     int tiles_k = (m->dev.nqk + rows - 1) / rows;
     e.tile_base = tiles;
     tiles += (long long)e.tiles_i * tiles_k;
+    e.face_base = fslots;
+    e.faces = (long long)face_slots(m->dev, face_level);
+    fslots += (e.faces + 31) / 32 * 32;
     v.push_back(e);
 }
 
@@ -429,21 +419,32 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
         max_tri = std::max(max_tri, 2ULL * A[i]->dev.N * A[i]->dev.nqk);
         max_tri = std::max(max_tri, 2ULL * B[i]->dev.N * B[i]->dev.nqk);
     }
+    const int fl = prm.face_level;
     for (int i = 0; i < nPairs; ++i) {
-        fill_pass(pall, P->tiles_all, A[i], pairs[i].x, i, 0, block, rows);
-        fill_pass(pall, P->tiles_all, B[i], pairs[i].y, i, 1, block, rows);
-        fill_pass(pa, P->tiles_A, A[i], pairs[i].x, i, 0, block, rows);
-        fill_pass(pb, P->tiles_B, B[i], pairs[i].y, i, 1, block, rows);
+        fill_pass(pall, P->tiles_all, P->fslots_all, A[i], pairs[i].x, i, 0, block, rows, fl);
+        fill_pass(pall, P->tiles_all, P->fslots_all, B[i], pairs[i].y, i, 1, block, rows, fl);
+        fill_pass(pa, P->tiles_A, P->fslots_A, A[i], pairs[i].x, i, 0, block, rows, fl);
+        fill_pass(pb, P->tiles_B, P->fslots_B, B[i], pairs[i].y, i, 1, block, rows, fl);
     }
-    // FP32 split vertex copies (32 bytes per view vertex), written by the bounds pass
+    // FP32 split vertex copies (32 bytes per view vertex) and face boxes (32 or
+    // 64 bytes per face slot), written by the bounds pass
+    const unsigned long long box_bytes = prm.precision == 1 ? 32 : 64;
+    std::vector<unsigned long long> fbox_off;
+    unsigned long long fbox_total = 0;
     for (auto &md : meshes) {
         P->split_off.push_back(P->split_total);
         P->split_total += 2ULL * (unsigned long long)md.N * (unsigned long long)md.M;
+        fbox_off.push_back(fbox_total);
+        fbox_total += (face_slots(md, fl) * box_bytes + 255) / 256 * 256;
     }
     {
         cudaError_t se = dalloc(&P->split, P->split_total);
+        if (se == cudaSuccess) se = dalloc(&P->fbox, fbox_total);
         if (se != cudaSuccess) { g_err = cudaGetErrorString(se); delete P; return TMS_ERR_CUDA; }
-        for (size_t i = 0; i < meshes.size(); ++i) meshes[i].split = P->split + P->split_off[i];
+        for (size_t i = 0; i < meshes.size(); ++i) {
+            meshes[i].split = P->split + P->split_off[i];
+            meshes[i].fbox = P->fbox + fbox_off[i];
+        }
     }
     P->n_meshes = (int)meshes.size();
     P->n_pass_all = (int)pall.size();

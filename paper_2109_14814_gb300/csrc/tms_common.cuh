@@ -48,6 +48,10 @@ struct MeshDev {
     float4 *split;        // plan scratch: per view vertex (k*N + i) two float4,
                           // hi = RN32(x) and lo = RN32(x - hi), written by the
                           // bounds pass and gathered by the FP32 narrow filter
+    void *fbox;           // plan scratch: per face slot its box, written by the
+                          // bounds pass (mixed precision: float4 lo, float4 hi,
+                          // rounded outward; plain: 8 doubles lo[4], hi[4]);
+                          // slot = face id (quad k*N + i, or triangle 2(k*N + i) + t)
     int N;                // theta samples
     int M;                // vertex rows in the view
     int periodic;
@@ -60,9 +64,18 @@ struct PassEntry {        // one mesh processed by a face pass
     int mesh;             // index into the mesh table
     int pair;             // mesh-pair index
     int role;             // 0 = mesh A, 1 = mesh B of the pair
-    int tiles_i;          // tiles along theta
-    long long tile_base;  // first global tile of this mesh
+    int tiles_i;          // tiles along theta (bounds pass)
+    long long tile_base;  // first global tile of this mesh (bounds pass)
+    long long face_base;  // first global face slot of this mesh (cell passes),
+                          // a multiple of 32 so that no warp spans two meshes
+    long long faces;      // face slots of this mesh
 };
+
+// face slots of a mesh view: quads k*N + i (i < N, k < nqk; slot i = N-1 of an
+// open mesh is unused), or two triangles per quad
+__host__ __device__ inline unsigned long long face_slots(const MeshDev &m, int face_level) {
+    return (face_level == 0 ? 2ULL : 1ULL) * (unsigned long long)m.N * (unsigned long long)m.nqk;
+}
 
 struct Bounds {           // per mesh, order-preserving uint64 encodings of doubles
     unsigned long long lo[4];
@@ -268,7 +281,8 @@ __device__ __forceinline__ void load_vertex(const MeshDev &m, int i, int k, doub
 struct FacePassArgs {
     const PassEntry *entries;
     int n_entries;
-    long long total_tiles;
+    long long total_tiles;         // bounds pass: tiles of all entries
+    long long total_faces;         // cell passes: face slots of all entries (padded)
     const MeshDev *meshes;
     int mode;
     int tile_rows;
@@ -278,12 +292,8 @@ struct FacePassArgs {
     int bmA_word_bits;
     uint32_t *bmH;
     int bmH_word_bits;
-    uint64_t *ent_key;
-    uint32_t *ent_val;
-    uint32_t *ent_face;
-    uint2 *ent_cell;
-    float4 *ent_box32;             // 2 per entry
-    double *ent_box64;             // 8 per entry
+    uint64_t *ent_key;             // pair << 32 | cell << 1 | role
+    uint32_t *ent_val;             // face id
     Counters *ctr;
     unsigned long long ent_cap;
 };
@@ -330,14 +340,10 @@ void launch_cells(const CellArgs &a, int grid, cudaStream_t st);
 
 struct EmitArgs {
     const uint64_t *keys;          // sorted entry keys
-    const uint32_t *vals;          // sorted entry indices
+    const uint32_t *vals;          // face ids in key order
     const uint32_t *cell_start;
     const uint32_t *cell_b;
     const unsigned long long *tile_off;
-    const uint32_t *ent_face;
-    const uint2 *ent_cell;          // lowest cell of the face box, 4 x u16
-    const float4 *ent_box32;
-    const double *ent_box64;
     const Grid *grids;
     const MeshDev *meshes;
     const int2 *pairs;

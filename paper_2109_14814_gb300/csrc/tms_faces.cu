@@ -1,24 +1,32 @@
-// Face passes of the broad phase: one read of a mesh's vertex grid per pass.
+// Face passes of the broad phase.
 //
 // Broad phase of arXiv 2109.14814, Sec. 6.2.1-6.2.2, re-designed for GB300:
-//   MODE_BOUNDS      per-mesh world bounds, widest face extent per coordinate
-//                    (the grid rule of Sec. 6.2.1: cell edge > widest face), and
-//                    a finiteness check of every vertex;
-//   MODE_MARK        occupancy bits of the cells covered by mesh A's faces;
-//   MODE_PROBE_MARK  mesh B: one entry per face-cell incidence in a cell that
-//                    mesh A occupies, and those cells marked "hot";
-//   MODE_PROBE       mesh A: one entry per face-cell incidence in a hot cell;
-//   MODE_EMIT_ALL    one entry per face-cell incidence (no filter).
+//   bounds pass      (one read of every vertex) per-mesh world bounds, widest
+//                    face extent per coordinate (the grid rule of Sec. 6.2.1:
+//                    cell edge > widest face), a finiteness check of every
+//                    vertex, the box of every face (Sec. 6.2.2) and the FP32
+//                    split copy of the vertices for the narrow filter;
+//   cell passes      (one read of every face box) the cells each face covers:
+//     MODE_MARK        occupancy bits of the cells covered by mesh A's faces;
+//     MODE_PROBE_MARK  mesh B: one entry per face-cell incidence in a cell that
+//                      mesh A occupies, and those cells marked "hot";
+//     MODE_PROBE       mesh A: one entry per face-cell incidence in a hot cell;
+//     MODE_EMIT_ALL    one entry per face-cell incidence (no filter).
 // Cells that do not hold faces of both meshes are dropped, as the paper drops
 // grid boxes whose quad list is empty on either side (Sec. 6.3); the occupancy
 // bitmaps only decide this before any list is built.  A bitmap is a blocked
 // Bloom filter over hash(pair, cell): a false positive only adds entries, never
 // removes one, so every face pair sharing a cell still meets in the sort.
 //
-// Tiling: a block owns a tile of TI quads along theta x TK quad rows.  All
-// (TI+1) x (TK+1) vertices of the tile are loaded once, coalesced along theta,
-// into shared memory (converted to FP32 lower/upper bounds in the mixed
-// precision mode), then each thread builds the boxes of its quads' faces.
+// Bounds pass tiling: a block owns a tile of TI quads along theta x TK quad
+// rows.  All (TI+1) x (TK+1) vertices of the tile are loaded once, coalesced
+// along theta, into shared memory (converted to FP32 lower/upper bounds in the
+// mixed precision mode), then each thread builds the boxes of its quads' faces.
+//
+// Cell passes: one thread per face slot; a warp expands its 32 faces' cell
+// ranges into one list of (face, cell) items and works through it 32 items at
+// a time, so its loop runs ceil(sum of cells / 32) times instead of 32 x the
+// largest count.  An entry is (key = pair << 32 | cell << 1 | role, face id).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -119,27 +127,43 @@ struct GridView<0> {
     }
 };
 
+// the box of a face into its slot of the mesh's face-box array
 template <int PREC>
-__device__ __forceinline__ void write_box(const FacePassArgs &a, unsigned long long pos,
-                                          const BoxT<PREC> &b);
+__device__ __forceinline__ void write_fbox(const MeshDev &m, uint32_t face, const BoxT<PREC> &b);
 template <>
-__device__ __forceinline__ void write_box<1>(const FacePassArgs &a, unsigned long long pos,
-                                             const BoxT<1> &b) {
-    a.ent_box32[2 * pos] = make_float4(b.lo[0], b.lo[1], b.lo[2], b.lo[3]);
-    a.ent_box32[2 * pos + 1] = make_float4(b.hi[0], b.hi[1], b.hi[2], b.hi[3]);
+__device__ __forceinline__ void write_fbox<1>(const MeshDev &m, uint32_t face, const BoxT<1> &b) {
+    float4 *p = reinterpret_cast<float4 *>(m.fbox) + 2 * (size_t)face;
+    p[0] = make_float4(b.lo[0], b.lo[1], b.lo[2], b.lo[3]);
+    p[1] = make_float4(b.hi[0], b.hi[1], b.hi[2], b.hi[3]);
 }
 template <>
-__device__ __forceinline__ void write_box<0>(const FacePassArgs &a, unsigned long long pos,
-                                             const BoxT<0> &b) {
-    double2 *p = reinterpret_cast<double2 *>(a.ent_box64 + 8 * pos);
+__device__ __forceinline__ void write_fbox<0>(const MeshDev &m, uint32_t face, const BoxT<0> &b) {
+    double2 *p = reinterpret_cast<double2 *>(m.fbox) + 4 * (size_t)face;
     p[0] = make_double2(b.lo[0], b.lo[1]);
     p[1] = make_double2(b.lo[2], b.lo[3]);
     p[2] = make_double2(b.hi[0], b.hi[1]);
     p[3] = make_double2(b.hi[2], b.hi[3]);
 }
 
-// Per-thread accumulators of MODE_BOUNDS, in the box precision (FP32 min/max in
-// the mixed mode: FP64 arithmetic is a scarce pipe on GB300)
+template <int PREC>
+__device__ __forceinline__ void read_fbox(const MeshDev &m, uint32_t face, BoxT<PREC> &b);
+template <>
+__device__ __forceinline__ void read_fbox<1>(const MeshDev &m, uint32_t face, BoxT<1> &b) {
+    const float4 *p = reinterpret_cast<const float4 *>(m.fbox) + 2 * (size_t)face;
+    const float4 l = __ldg(p), h = __ldg(p + 1);
+    b.lo[0] = l.x; b.lo[1] = l.y; b.lo[2] = l.z; b.lo[3] = l.w;
+    b.hi[0] = h.x; b.hi[1] = h.y; b.hi[2] = h.z; b.hi[3] = h.w;
+}
+template <>
+__device__ __forceinline__ void read_fbox<0>(const MeshDev &m, uint32_t face, BoxT<0> &b) {
+    const double2 *p = reinterpret_cast<const double2 *>(m.fbox) + 4 * (size_t)face;
+    const double2 x0 = __ldg(p), x1 = __ldg(p + 1), x2 = __ldg(p + 2), x3 = __ldg(p + 3);
+    b.lo[0] = x0.x; b.lo[1] = x0.y; b.lo[2] = x1.x; b.lo[3] = x1.y;
+    b.hi[0] = x2.x; b.hi[1] = x2.y; b.hi[2] = x3.x; b.hi[3] = x3.y;
+}
+
+// Per-thread accumulators of the bounds pass, in the box precision (FP32
+// min/max in the mixed mode: FP64 arithmetic is a scarce pipe on GB300)
 template <int PREC>
 struct BoundAcc;
 template <>
@@ -187,118 +211,35 @@ struct BoundAcc<0> {
     __device__ double get_w(int d) const { return w[d]; }
 };
 
-// The cells of one face and the mode's action on each.  Called by all 32 lanes
-// of a warp together (valid = false for lanes without a face).
-template <int PREC>
-__device__ __forceinline__ void face_cells(const FacePassArgs &a, const GridView<PREC> &g,
-                                           bool valid, const BoxT<PREC> &b, uint32_t face,
-                                           int pair, int role) {
-    int clo[4], cnt[4];
-    unsigned count = 0;
-    if (valid) {
-        bool out = false;
-#pragma unroll
-        for (int d = 0; d < 4; ++d) out |= (b.hi[d] < g.o[d]) || (b.lo[d] > g.e[d]);
-        if (!out) {
-            count = 1;
-#pragma unroll
-            for (int d = 0; d < 4; ++d) {
-                clo[d] = cell_of(b.lo[d], g.o[d], g.inv[d], g.n[d]);
-                int chi = cell_of(b.hi[d], g.o[d], g.inv[d], g.n[d]);
-                cnt[d] = chi - clo[d] + 1;
-                count *= (unsigned)cnt[d];
-            }
-        }
+// the pass entry (mesh of a pass) holding global index x, by binary search
+__device__ __forceinline__ int find_entry(const FacePassArgs &a, long long x, bool by_face) {
+    int lo = 0, hi = a.n_entries - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const long long b = by_face ? a.entries[mid].face_base : a.entries[mid].tile_base;
+        if (b <= x) lo = mid; else hi = mid - 1;
     }
-    unsigned maxc = __reduce_max_sync(FULL, count);
-    const uint64_t pair_hi = (uint64_t)(uint32_t)pair << 32;
-    for (unsigned it = 0; it < maxc; ++it) {
-        bool act = it < count;
-        uint32_t cell = 0;
-        int cc[4] = {0, 0, 0, 0};
-        if (act) {
-            unsigned r = it;
-#pragma unroll
-            for (int d = 0; d < 4; ++d) {
-                cc[d] = clo[d] + (int)(r % (unsigned)cnt[d]);
-                r /= (unsigned)cnt[d];
-            }
-            cell = (((uint32_t)cc[3] * (uint32_t)g.n[2] + (uint32_t)cc[2]) * (uint32_t)g.n[1] +
-                    (uint32_t)cc[1]) * (uint32_t)g.n[0] + (uint32_t)cc[0];
-        }
-        uint64_t h = mix64(pair_hi | cell);
-        bool emit = false;
-        if (a.mode == MODE_MARK) {
-            if (act) {
-                // bits are only ever set during this pass, so a word that already
-                // holds them needs no atomic (a stale read only costs an atomic)
-                uint32_t w, m;
-                bloom_slot(h, a.bmA_word_bits, w, m);
-                if ((a.bmA[w] & m) != m) atomicOr(a.bmA + w, m);
-            }
-        } else if (a.mode == MODE_PROBE_MARK) {
-            if (act) {
-                uint32_t w, m;
-                bloom_slot(h, a.bmA_word_bits, w, m);
-                if ((__ldg(a.bmA + w) & m) == m) {
-                    emit = true;
-                    uint32_t w2, m2;
-                    bloom_slot(h, a.bmH_word_bits, w2, m2);
-                    if ((a.bmH[w2] & m2) != m2) atomicOr(a.bmH + w2, m2);
-                }
-            }
-        } else if (a.mode == MODE_PROBE) {
-            if (act) {
-                uint32_t w2, m2;
-                bloom_slot(h, a.bmH_word_bits, w2, m2);
-                emit = (__ldg(a.bmH + w2) & m2) == m2;
-            }
-        } else {  // MODE_EMIT_ALL
-            emit = act;
-        }
-        if (a.mode != MODE_MARK) {
-            unsigned long long pos = warp_append(&a.ctr->entries, emit, FULL);
-            if (emit && pos < a.ent_cap) {
-                a.ent_key[pos] = pair_hi | ((uint64_t)cell << 1) | (uint64_t)role;
-                a.ent_val[pos] = (uint32_t)pos;
-                a.ent_face[pos] = face;
-                // the face's lowest cell (for the owner-cell rule of the emission)
-                a.ent_cell[pos] = make_uint2((uint32_t)clo[0] | ((uint32_t)clo[1] << 16),
-                                             (uint32_t)clo[2] | ((uint32_t)clo[3] << 16));
-                write_box<PREC>(a, pos, b);
-            }
-        }
-    }
+    return lo;
 }
 
+// ---------------------------------------------------------------------------
+// bounds pass
+// ---------------------------------------------------------------------------
 template <int PREC, int FACE, int TK>
-__global__ void __launch_bounds__(256) k_face_pass(FacePassArgs a) {
+__global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Vtx<PREC> *sv = reinterpret_cast<Vtx<PREC> *>(smem_raw);
     const int TI = blockDim.x;
     const int W = TI + 1;
     const long long tile = blockIdx.x;
 
-    // which mesh this tile belongs to (binary search over tile_base)
-    int lo = 0, hi = a.n_entries - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (a.entries[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
-    }
-    const PassEntry pe = a.entries[lo];
+    const PassEntry pe = a.entries[find_entry(a, tile, false)];
     const MeshDev m = a.meshes[pe.mesh];
     const long long lt = tile - pe.tile_base;
     const int ti = (int)(lt % pe.tiles_i), tk = (int)(lt / pe.tiles_i);
     const int i0 = ti * TI, kq0 = tk * TK;
     const int cols_q = min(TI, m.nqi - i0);
     const int rows_q = min(TK, m.nqk - kq0);
-
-    GridView<PREC> g;
-    if (a.mode != MODE_BOUNDS) {
-        const Grid &gg = a.grids[pe.pair];
-        if (gg.empty) return;
-        g.load(gg);
-    }
 
     // ---- load the tile's vertices: rows kq0..kq0+rows_q, columns i0..i0+cols_q
     unsigned nonfinite = 0;
@@ -321,7 +262,7 @@ __global__ void __launch_bounds__(256) k_face_pass(FacePassArgs a) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) nonfinite |= !finite64(x[r][c]);
                 to_vtx(x[r], sv[r * W + t]);
-                if (a.mode == MODE_BOUNDS) write_split(m, (size_t)(kq0 + r) * m.N + vi, x[r]);
+                write_split(m, (size_t)(kq0 + r) * m.N + vi, x[r]);
             }
         }
         // the last vertex column of the tile (wraps to column 0 on a periodic mesh)
@@ -336,95 +277,220 @@ __global__ void __launch_bounds__(256) k_face_pass(FacePassArgs a) {
                 nonfinite |= !finite64(y[c]);
             }
             to_vtx(y, sv[t * W + cols_q]);
-            if (a.mode == MODE_BOUNDS) write_split(m, off, y);
+            write_split(m, off, y);
         }
     }
     __syncthreads();
 
     BoundAcc<PREC> acc;
-    if (a.mode == MODE_BOUNDS) acc.init();
+    acc.init();
 
     const int t = threadIdx.x;
     const bool col_valid = t < cols_q;
     const int i = i0 + t;
-    for (int r = 0; r < rows_q; ++r) {
-        const int k = kq0 + r;
-        Vtx<PREC> va, vb, vc, vd;
-        if (col_valid) {
-            va = sv[r * W + t];             // (i, k)
-            vb = sv[r * W + t + 1];         // (i+1, k)
-            vc = sv[(r + 1) * W + t];       // (i, k+1)
-            vd = sv[(r + 1) * W + t + 1];   // (i+1, k+1)
-        }
-        const uint32_t q = (uint32_t)k * (uint32_t)m.N + (uint32_t)i;
-        if (FACE == 0) {
-            BoxT<PREC> b1, b2;
-            if (col_valid) {
+    if (col_valid) {
+        for (int r = 0; r < rows_q; ++r) {
+            const int k = kq0 + r;
+            const Vtx<PREC> va = sv[r * W + t];             // (i, k)
+            const Vtx<PREC> vb = sv[r * W + t + 1];         // (i+1, k)
+            const Vtx<PREC> vc = sv[(r + 1) * W + t];       // (i, k+1)
+            const Vtx<PREC> vd = sv[(r + 1) * W + t + 1];   // (i+1, k+1)
+            const uint32_t q = (uint32_t)k * (uint32_t)m.N + (uint32_t)i;
+            if (FACE == 0) {
+                BoxT<PREC> b1, b2;
                 box_init(b1, vb); box_add(b1, va); box_add(b1, vc);   // T1: x1=(i+1,k) x2=(i,k) x3=(i,k+1)
                 box_init(b2, vc); box_add(b2, vd); box_add(b2, vb);   // T2: x1=(i,k+1) x2=(i+1,k+1) x3=(i+1,k)
-            }
-            if (a.mode == MODE_BOUNDS) {
-                if (col_valid) { acc.add(b1); acc.add(b2); }
+                acc.add(b1);
+                acc.add(b2);
+                write_fbox<PREC>(m, 2 * q, b1);
+                write_fbox<PREC>(m, 2 * q + 1, b2);
             } else {
-                face_cells<PREC>(a, g, col_valid, b1, 2 * q, pe.pair, pe.role);
-                face_cells<PREC>(a, g, col_valid, b2, 2 * q + 1, pe.pair, pe.role);
-            }
-        } else {
-            BoxT<PREC> bq;
-            if (col_valid) { box_init(bq, va); box_add(bq, vb); box_add(bq, vc); box_add(bq, vd); }
-            if (a.mode == MODE_BOUNDS) {
-                if (col_valid) acc.add(bq);
-            } else {
-                face_cells<PREC>(a, g, col_valid, bq, q, pe.pair, pe.role);
+                BoxT<PREC> bq;
+                box_init(bq, va); box_add(bq, vb); box_add(bq, vc); box_add(bq, vd);
+                acc.add(bq);
+                write_fbox<PREC>(m, q, bq);
             }
         }
     }
 
-    if (a.mode == MODE_BOUNDS) {
-        // block reduction, then one set of atomics per block
-        __shared__ double red[8][13];
-        __shared__ unsigned redf[8][2];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // block reduction, then one set of atomics per block
+    __shared__ double red[8][13];
+    __shared__ unsigned redf[8][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            for (int off = 16; off > 0; off >>= 1) {
-                acc.lo[d] = min(acc.lo[d], __shfl_xor_sync(FULL, acc.lo[d], off));
-                acc.hi[d] = max(acc.hi[d], __shfl_xor_sync(FULL, acc.hi[d], off));
-                acc.w[d] = max(acc.w[d], __shfl_xor_sync(FULL, acc.w[d], off));
-            }
+    for (int d = 0; d < 4; ++d) {
+        for (int off = 16; off > 0; off >>= 1) {
+            acc.lo[d] = min(acc.lo[d], __shfl_xor_sync(FULL, acc.lo[d], off));
+            acc.hi[d] = max(acc.hi[d], __shfl_xor_sync(FULL, acc.hi[d], off));
+            acc.w[d] = max(acc.w[d], __shfl_xor_sync(FULL, acc.w[d], off));
         }
-        unsigned fl = __reduce_or_sync(FULL, nonfinite);
-        unsigned seen = __reduce_or_sync(FULL, acc.seen);
-        if (lane == 0) {
+    }
+    unsigned fl = __reduce_or_sync(FULL, nonfinite);
+    unsigned seen = __reduce_or_sync(FULL, acc.seen);
+    if (lane == 0) {
 #pragma unroll
-            for (int d = 0; d < 4; ++d) { red[warp][d] = acc.get_lo(d); red[warp][4 + d] = acc.get_hi(d); red[warp][8 + d] = acc.get_w(d); }
-            redf[warp][0] = fl;
-            redf[warp][1] = seen;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int nw = blockDim.x >> 5;
-            Bounds *B = a.bounds + pe.mesh;
-            unsigned f = 0, s = 0;
-            for (int w = 0; w < nw; ++w) { f |= redf[w][0]; s |= redf[w][1]; }
-            if (s) {
+        for (int d = 0; d < 4; ++d) { red[warp][d] = acc.get_lo(d); red[warp][4 + d] = acc.get_hi(d); red[warp][8 + d] = acc.get_w(d); }
+        redf[warp][0] = fl;
+        redf[warp][1] = seen;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        Bounds *B = a.bounds + pe.mesh;
+        unsigned f = 0, s = 0;
+        for (int w = 0; w < nw; ++w) { f |= redf[w][0]; s |= redf[w][1]; }
+        if (s) {
 #pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    double l = red[0][d], h = red[0][4 + d], ww = red[0][8 + d];
-                    for (int w = 1; w < nw; ++w) {
-                        l = fmin(l, red[w][d]);
-                        h = fmax(h, red[w][4 + d]);
-                        ww = fmax(ww, red[w][8 + d]);
-                    }
-                    atomicMin(&B->lo[d], ord_enc(l));
-                    atomicMax(&B->hi[d], ord_enc(h));
-                    atomicMax(&B->w[d], ord_enc(ww));
+            for (int d = 0; d < 4; ++d) {
+                double l = red[0][d], h = red[0][4 + d], ww = red[0][8 + d];
+                for (int w = 1; w < nw; ++w) {
+                    l = fmin(l, red[w][d]);
+                    h = fmax(h, red[w][4 + d]);
+                    ww = fmax(ww, red[w][8 + d]);
                 }
-                atomicOr(&B->faces, 1u);
+                atomicMin(&B->lo[d], ord_enc(l));
+                atomicMax(&B->hi[d], ord_enc(h));
+                atomicMax(&B->w[d], ord_enc(ww));
             }
-            if (f) {
-                atomicOr(&B->flags, ST_NONFINITE);
-                atomicOr(&a.ctr->status, ST_NONFINITE);
+            atomicOr(&B->faces, 1u);
+        }
+        if (f) {
+            atomicOr(&B->flags, ST_NONFINITE);
+            atomicOr(&a.ctr->status, ST_NONFINITE);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// cell passes
+// ---------------------------------------------------------------------------
+constexpr int kCellWarps = 8;
+
+// coordinate d of item r of a cell range (mixed radix over cnt[0..3]); counts
+// of 1 and 2 (the usual case: a cell is wider than any face) take no division
+__device__ __forceinline__ unsigned next_digit(unsigned &r, unsigned c) {
+    unsigned q;
+    if (c <= 2u) q = r >> (c - 1u);
+    else q = r / c;
+    const unsigned digit = r - q * c;
+    r = q;
+    return digit;
+}
+
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(32 * kCellWarps) k_cell_pass(FacePassArgs a, int face_level) {
+    __shared__ uint32_t s_excl[kCellWarps][32];
+    __shared__ uint2 s_lo[kCellWarps][32];
+    __shared__ uint2 s_cnt[kCellWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long wslot = slot - lane;           // the warp's first slot
+    if (wslot >= a.total_faces) return;            // whole warps only
+    // every mesh starts at a multiple of 32 slots: the warp lies in one mesh
+    const PassEntry pe = a.entries[find_entry(a, wslot, true)];
+    const Grid &gg = a.grids[pe.pair];
+    if (gg.empty) return;
+    GridView<PREC> g;
+    g.load(gg);
+    const MeshDev &mr = a.meshes[pe.mesh];
+    const int N = mr.N, nqi = mr.nqi;
+    const long long f = slot - pe.face_base;
+    // a valid face: inside this mesh's slots, and not the unused last column of
+    // an open mesh
+    bool valid = f < pe.faces;
+    const uint32_t face = (uint32_t)f;
+    if (valid) {
+        const uint32_t q = face >> (face_level == 0 ? 1 : 0);
+        valid = (int)(q % (uint32_t)N) < nqi;
+    }
+    int clo[4] = {0, 0, 0, 0}, cnt[4] = {1, 1, 1, 1};
+    unsigned count = 0;
+    if (valid) {
+        BoxT<PREC> b;
+        read_fbox<PREC>(mr, face, b);
+        bool out = false;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) out |= (b.hi[d] < g.o[d]) || (b.lo[d] > g.e[d]);
+        if (!out) {
+            count = 1;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                clo[d] = cell_of(b.lo[d], g.o[d], g.inv[d], g.n[d]);
+                const int chi = cell_of(b.hi[d], g.o[d], g.inv[d], g.n[d]);
+                cnt[d] = chi - clo[d] + 1;
+                count *= (unsigned)cnt[d];
+            }
+        }
+    }
+    // warp-wide exclusive scan of the counts
+    unsigned incl = count;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned v = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const unsigned total = __shfl_sync(FULL, incl, 31);
+    s_excl[warp][lane] = incl - count;
+    s_lo[warp][lane] = make_uint2((uint32_t)clo[0] | ((uint32_t)clo[1] << 16),
+                                  (uint32_t)clo[2] | ((uint32_t)clo[3] << 16));
+    s_cnt[warp][lane] = make_uint2((uint32_t)cnt[0] | ((uint32_t)cnt[1] << 16),
+                                   (uint32_t)cnt[2] | ((uint32_t)cnt[3] << 16));
+    __syncwarp();
+    const uint64_t pair_hi = (uint64_t)(uint32_t)pe.pair << 32;
+    const uint32_t n0 = (uint32_t)g.n[0], n1 = (uint32_t)g.n[1], n2 = (uint32_t)g.n[2];
+    for (unsigned base = 0; base < total; base += 32) {
+        const unsigned j = base + lane;
+        const bool act = j < total;
+        uint32_t cell = 0;
+        int owner = 0;
+        if (act) {
+            // the lane whose range holds item j: the last with excl <= j
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (s_excl[warp][owner + step] <= j) owner += step;
+            unsigned r = j - s_excl[warp][owner];
+            const uint2 lo = s_lo[warp][owner], cn = s_cnt[warp][owner];
+            const uint32_t c0 = (lo.x & 0xFFFFu) + next_digit(r, cn.x & 0xFFFFu);
+            const uint32_t c1 = (lo.x >> 16) + next_digit(r, cn.x >> 16);
+            const uint32_t c2 = (lo.y & 0xFFFFu) + next_digit(r, cn.y & 0xFFFFu);
+            const uint32_t c3 = (lo.y >> 16) + next_digit(r, cn.y >> 16);
+            cell = ((c3 * n2 + c2) * n1 + c1) * n0 + c0;
+        }
+        const uint64_t h = mix64(pair_hi | cell);
+        bool emit = false;
+        if (MODE == MODE_MARK) {
+            if (act) {
+                // bits are only ever set during this pass, so a word that already
+                // holds them needs no atomic (a stale read only costs an atomic)
+                uint32_t w, m;
+                bloom_slot(h, a.bmA_word_bits, w, m);
+                if ((a.bmA[w] & m) != m) atomicOr(a.bmA + w, m);
+            }
+        } else if (MODE == MODE_PROBE_MARK) {
+            if (act) {
+                uint32_t w, m;
+                bloom_slot(h, a.bmA_word_bits, w, m);
+                if ((__ldg(a.bmA + w) & m) == m) {
+                    emit = true;
+                    uint32_t w2, m2;
+                    bloom_slot(h, a.bmH_word_bits, w2, m2);
+                    if ((a.bmH[w2] & m2) != m2) atomicOr(a.bmH + w2, m2);
+                }
+            }
+        } else if (MODE == MODE_PROBE) {
+            if (act) {
+                uint32_t w2, m2;
+                bloom_slot(h, a.bmH_word_bits, w2, m2);
+                emit = (__ldg(a.bmH + w2) & m2) == m2;
+            }
+        } else {  // MODE_EMIT_ALL
+            emit = act;
+        }
+        if (MODE != MODE_MARK) {
+            const unsigned long long pos = warp_append(&a.ctr->entries, emit, FULL);
+            if (emit && pos < a.ent_cap) {
+                a.ent_key[pos] = pair_hi | ((uint64_t)cell << 1) | (uint64_t)pe.role;
+                a.ent_val[pos] = (uint32_t)(wslot - pe.face_base) + (uint32_t)owner;
             }
         }
     }
@@ -502,7 +568,7 @@ __global__ void k_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, G
 template <int PREC, int FACE, int TK>
 void launch_one(const FacePassArgs &a, int block, cudaStream_t st) {
     size_t smem = (size_t)(TK + 1) * (block + 1) * sizeof(Vtx<PREC>);
-    k_face_pass<PREC, FACE, TK><<<(unsigned)a.total_tiles, block, smem, st>>>(a);
+    k_bounds_pass<PREC, FACE, TK><<<(unsigned)a.total_tiles, block, smem, st>>>(a);
 }
 
 template <int PREC, int FACE>
@@ -513,8 +579,20 @@ void launch_tk(const FacePassArgs &a, int block, cudaStream_t st) {
 
 template <int PREC, int FACE, int TK>
 cudaError_t configure_one() {
-    return cudaFuncSetAttribute(k_face_pass<PREC, FACE, TK>,
+    return cudaFuncSetAttribute(k_bounds_pass<PREC, FACE, TK>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+}
+
+template <int PREC>
+void launch_cells_mode(const FacePassArgs &a, int face_level, cudaStream_t st) {
+    const int B = 32 * kCellWarps;
+    const unsigned grid = (unsigned)((a.total_faces + B - 1) / B);
+    switch (a.mode) {
+        case MODE_MARK: k_cell_pass<PREC, MODE_MARK><<<grid, B, 0, st>>>(a, face_level); break;
+        case MODE_PROBE_MARK: k_cell_pass<PREC, MODE_PROBE_MARK><<<grid, B, 0, st>>>(a, face_level); break;
+        case MODE_PROBE: k_cell_pass<PREC, MODE_PROBE><<<grid, B, 0, st>>>(a, face_level); break;
+        default: k_cell_pass<PREC, MODE_EMIT_ALL><<<grid, B, 0, st>>>(a, face_level); break;
+    }
 }
 
 }  // namespace
@@ -532,12 +610,18 @@ cudaError_t configure_face_pass() {
 
 void launch_face_pass(const FacePassArgs &a, int precision, int face_level, int block,
                       cudaStream_t st) {
-    if (a.total_tiles <= 0) return;
-    if (precision == 1) {
-        if (face_level == 0) launch_tk<1, 0>(a, block, st); else launch_tk<1, 1>(a, block, st);
-    } else {
-        if (face_level == 0) launch_tk<0, 0>(a, block, st); else launch_tk<0, 1>(a, block, st);
+    if (a.mode == MODE_BOUNDS) {
+        if (a.total_tiles <= 0) return;
+        if (precision == 1) {
+            if (face_level == 0) launch_tk<1, 0>(a, block, st); else launch_tk<1, 1>(a, block, st);
+        } else {
+            if (face_level == 0) launch_tk<0, 0>(a, block, st); else launch_tk<0, 1>(a, block, st);
+        }
+        return;
     }
+    if (a.total_faces <= 0) return;
+    if (precision == 1) launch_cells_mode<1>(a, face_level, st);
+    else launch_cells_mode<0>(a, face_level, st);
 }
 
 void launch_bounds_init(Bounds *b, int n, cudaStream_t st) {

@@ -79,12 +79,10 @@ struct Buffers {
     Counters *ctr;
     unsigned long long *partials;
     float4 *split[2];
+    unsigned char *fbox[2];
     uint32_t *bmA, *bmH;
     uint64_t *ek, *ek2;
-    uint32_t *ev, *ev2, *eface;
-    uint2 *ecell;
-    float4 *ebox32;
-    double *ebox64;
+    uint32_t *ev, *ev2;
     uint32_t *sort_counts;
     uint32_t *head, *hscan, *cstart, *cb;
     unsigned long long *cpairs, *poff, *ctiles, *toff;
@@ -94,7 +92,11 @@ struct Buffers {
     uint32_t *hv, *hv2, *keep, *kscan;
 };
 
-// the arena's layout; also used to check, at compile time, that it fits
+// the arena's layout; also used to check, at set-up, that it fits.  Buffers
+// live across the whole search come first; then the broad phase's buffers, and
+// over the same bytes the narrow phase's and the merge's, which are written
+// only after candidate emission, the broad phase's last reader, has run on the
+// same stream.
 size_t carve(unsigned char *base, Buffers &b) {
     Carve c{base};
     b.tables = c.take<Tables>(1);
@@ -104,17 +106,18 @@ size_t carve(unsigned char *base, Buffers &b) {
     b.partials = c.take<unsigned long long>(kMaxGrid);
     b.split[0] = c.take<float4>(2 * kMaxViewVertices);
     b.split[1] = c.take<float4>(2 * kMaxViewVertices);
+    b.sort_counts = c.take<uint32_t>((unsigned long long)kRadixBins * kMaxGrid);
+    b.cand = c.take<Cand>(kCandCap);
+    const size_t phase = c.off;
+    // broad phase: face boxes (two per quad, FP64 at most), bitmaps, entries, cells
+    b.fbox[0] = c.take<unsigned char>(2 * kMaxViewVertices * 64);
+    b.fbox[1] = c.take<unsigned char>(2 * kMaxViewVertices * 64);
     b.bmA = c.take<uint32_t>(1ull << kBmAWordBits);
     b.bmH = c.take<uint32_t>(1ull << kBmHWordBits);
     b.ek = c.take<uint64_t>(kEntCap);
     b.ek2 = c.take<uint64_t>(kEntCap);
     b.ev = c.take<uint32_t>(kEntCap);
     b.ev2 = c.take<uint32_t>(kEntCap);
-    b.eface = c.take<uint32_t>(kEntCap);
-    b.ecell = c.take<uint2>(kEntCap);
-    b.ebox64 = c.take<double>(8 * kEntCap);             // room for FP64 boxes ...
-    b.ebox32 = reinterpret_cast<float4 *>(b.ebox64);     // ... or FP32 ones
-    b.sort_counts = c.take<uint32_t>((unsigned long long)kRadixBins * kMaxGrid);
     b.head = c.take<uint32_t>(kEntCap);
     b.hscan = c.take<uint32_t>(kEntCap);
     b.cstart = c.take<uint32_t>(kEntCap);
@@ -123,7 +126,9 @@ size_t carve(unsigned char *base, Buffers &b) {
     b.poff = c.take<unsigned long long>(kEntCap);
     b.ctiles = c.take<unsigned long long>(kEntCap);
     b.toff = c.take<unsigned long long>(kEntCap);
-    b.cand = c.take<Cand>(kCandCap);
+    const size_t broad_end = c.off;
+    // narrow phase and merge, over the broad phase's bytes
+    c.off = phase;
     b.surv = c.take<Cand>(kSurvCap);
     b.hits = c.take<tms_hit>(kRawHitCap);
     b.hk = c.take<uint64_t>(kRawHitCap);
@@ -133,7 +138,7 @@ size_t carve(unsigned char *base, Buffers &b) {
     b.hv2 = c.take<uint32_t>(kRawHitCap);
     b.keep = c.take<uint32_t>(kRawHitCap);
     b.kscan = c.take<uint32_t>(kRawHitCap);
-    return c.off;
+    return std::max(broad_end, c.off);
 }
 
 int ceil_log2u(unsigned long long v) {
@@ -212,10 +217,13 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     memset(&t, 0, sizeof(t));
     ma.split = b.split[0];
     mb.split = b.split[1];
+    ma.fbox = b.fbox[0];
+    mb.fbox = b.fbox[1];
     t.meshes[0] = ma;
     t.meshes[1] = mb;
     t.pairs[0] = make_int2(0, 1);
-    long long tiles_all = 0, tiles_A = 0, tiles_B = 0;
+    long long tiles_all = 0;
+    long long fslots_all = 0, fslots_A = 0, fslots_B = 0;
     const MeshDev *mv[2] = {&ma, &mb};
     for (int role = 0; role < 2; ++role) {
         PassEntry e;
@@ -224,12 +232,17 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
         e.role = role;
         e.tiles_i = (mv[role]->nqi + block - 1) / block;
         const long long nt = (long long)e.tiles_i * ((mv[role]->nqk + rows - 1) / rows);
+        e.faces = (long long)face_slots(*mv[role], p.face_level);
+        const long long padded = (e.faces + 31) / 32 * 32;
         e.tile_base = tiles_all;
+        e.face_base = fslots_all;
         t.all[role] = e;
         tiles_all += nt;
+        fslots_all += padded;
         e.tile_base = 0;
-        if (role == 0) { t.pa[0] = e; tiles_A = nt; }
-        else { t.pb[0] = e; tiles_B = nt; }
+        e.face_base = 0;
+        if (role == 0) { t.pa[0] = e; fslots_A = padded; }
+        else { t.pb[0] = e; fslots_B = padded; }
     }
     unsigned long long max_tri = std::max(2ULL * ma.N * ma.nqk, 2ULL * mb.N * mb.nqk);
     const int tri_bits = ceil_log2u(max_tri);
@@ -253,10 +266,6 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     fa.bmH_word_bits = kBmHWordBits;
     fa.ent_key = b.ek;
     fa.ent_val = b.ev;
-    fa.ent_face = b.eface;
-    fa.ent_cell = b.ecell;
-    fa.ent_box32 = b.ebox32;
-    fa.ent_box64 = b.ebox64;
     fa.ctr = b.ctr;
     fa.ent_cap = kEntCap;
     fa.entries = b.tables->all; fa.n_entries = 2; fa.total_tiles = tiles_all;
@@ -266,17 +275,17 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     if (p.cell_filter) {
         NA_CK(cudaMemsetAsync(b.bmA, 0, (1ull << kBmAWordBits) * sizeof(uint32_t), s));
         NA_CK(cudaMemsetAsync(b.bmH, 0, (1ull << kBmHWordBits) * sizeof(uint32_t), s));
-        fa.entries = b.tables->pa; fa.n_entries = 1; fa.total_tiles = tiles_A;
+        fa.entries = b.tables->pa; fa.n_entries = 1; fa.total_faces = fslots_A;
         fa.mode = MODE_MARK;
         launch_face_pass(fa, p.precision, p.face_level, block, s);
-        fa.entries = b.tables->pb; fa.total_tiles = tiles_B;
+        fa.entries = b.tables->pb; fa.total_faces = fslots_B;
         fa.mode = MODE_PROBE_MARK;
         launch_face_pass(fa, p.precision, p.face_level, block, s);
-        fa.entries = b.tables->pa; fa.total_tiles = tiles_A;
+        fa.entries = b.tables->pa; fa.total_faces = fslots_A;
         fa.mode = MODE_PROBE;
         launch_face_pass(fa, p.precision, p.face_level, block, s);
     } else {
-        fa.entries = b.tables->all; fa.n_entries = 2; fa.total_tiles = tiles_all;
+        fa.entries = b.tables->all; fa.n_entries = 2; fa.total_faces = fslots_all;
         fa.mode = MODE_EMIT_ALL;
         launch_face_pass(fa, p.precision, p.face_level, block, s);
     }
@@ -292,7 +301,6 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     launch_cells(ca, grid, s);
     EmitArgs ea;
     ea.keys = sk; ea.vals = sv; ea.cell_start = b.cstart; ea.cell_b = b.cb; ea.tile_off = b.toff;
-    ea.ent_face = b.eface; ea.ent_cell = b.ecell; ea.ent_box32 = b.ebox32; ea.ent_box64 = b.ebox64;
     ea.grids = b.grids; ea.meshes = b.tables->meshes; ea.pairs = b.tables->pairs; ea.ctr = b.ctr;
     ea.ent_cap = kEntCap; ea.cand = b.cand; ea.cand_cap = kCandCap; ea.moller = p.moller;
     launch_emit(ea, p.precision, p.face_level, grid * 4, s);

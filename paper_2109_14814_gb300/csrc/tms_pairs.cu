@@ -83,25 +83,40 @@ __global__ void k_fill_u32(uint32_t *p, const unsigned long long *d_n, unsigned 
 // ---------------------------------------------------------------------------
 // emission
 // ---------------------------------------------------------------------------
+// a face's box from its mesh's face-box array (written by the bounds pass)
 template <int PREC>
 struct EBox;
 template <>
 struct EBox<1> {
     float lo[4], hi[4];
-    __device__ void load(const EmitArgs &a, uint32_t e) {
-        float4 l = a.ent_box32[2 * (size_t)e], h = a.ent_box32[2 * (size_t)e + 1];
+    __device__ void load(const void *fbox, uint32_t face) {
+        const float4 *p = reinterpret_cast<const float4 *>(fbox) + 2 * (size_t)face;
+        const float4 l = __ldg(p), h = __ldg(p + 1);
         lo[0] = l.x; lo[1] = l.y; lo[2] = l.z; lo[3] = l.w;
         hi[0] = h.x; hi[1] = h.y; hi[2] = h.z; hi[3] = h.w;
+    }
+    // the face's lowest cell, as the cell passes compute it, 4 x u16
+    __device__ uint2 low_cell(const Grid &g) const {
+        int c[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) c[d] = cell_of(lo[d], g.o32[d], g.inv32[d], g.n[d]);
+        return make_uint2((uint32_t)c[0] | ((uint32_t)c[1] << 16), (uint32_t)c[2] | ((uint32_t)c[3] << 16));
     }
 };
 template <>
 struct EBox<0> {
     double lo[4], hi[4];
-    __device__ void load(const EmitArgs &a, uint32_t e) {
-        const double2 *p = reinterpret_cast<const double2 *>(a.ent_box64 + 8 * (size_t)e);
-        double2 x0 = p[0], x1 = p[1], x2 = p[2], x3 = p[3];
+    __device__ void load(const void *fbox, uint32_t face) {
+        const double2 *p = reinterpret_cast<const double2 *>(fbox) + 4 * (size_t)face;
+        const double2 x0 = __ldg(p), x1 = __ldg(p + 1), x2 = __ldg(p + 2), x3 = __ldg(p + 3);
         lo[0] = x0.x; lo[1] = x0.y; lo[2] = x1.x; lo[3] = x1.y;
         hi[0] = x2.x; hi[1] = x2.y; hi[2] = x3.x; hi[3] = x3.y;
+    }
+    __device__ uint2 low_cell(const Grid &g) const {
+        int c[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) c[d] = cell_of(lo[d], g.o64[d], g.inv64[d], g.n[d]);
+        return make_uint2((uint32_t)c[0] | ((uint32_t)c[1] << 16), (uint32_t)c[2] | ((uint32_t)c[3] << 16));
     }
 };
 
@@ -231,20 +246,21 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         }
         const uint2 cur = make_uint2(cc[0] | (cc[1] << 16), cc[2] | (cc[3] << 16));
         // own A entry in registers, the B tile in shared memory
+        const int2 pr = a.pairs[pair];
+        const void *fbA = a.meshes[pr.x].fbox, *fbB = a.meshes[pr.y].fbox;
+        const void *fbL = swapAB ? fbB : fbA, *fbM = swapAB ? fbA : fbB;
         TileEntry<PREC> A;
         const bool hasA = lane < nAt;
         if (hasA) {
-            const uint32_t ea = a.vals[l0 + lane];
-            A.box.load(a, ea);
-            A.lo = a.ent_cell[ea];
-            A.face = a.ent_face[ea];
+            A.face = a.vals[l0 + lane];
+            A.box.load(fbL, A.face);
+            A.lo = A.box.low_cell(gr);
         }
         if (lane < nBt) {
-            const uint32_t eb = a.vals[m0 + lane];
             TileEntry<PREC> B;
-            B.box.load(a, eb);
-            B.lo = a.ent_cell[eb];
-            B.face = a.ent_face[eb];
+            B.face = a.vals[m0 + lane];
+            B.box.load(fbM, B.face);
+            B.lo = B.box.low_cell(gr);
             B.pad = 0;
             sB[warp][lane] = B;
         }
@@ -259,7 +275,6 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
                 // owner cell: componentwise max of the two lowest cells == this cell
                 keep = ov && (__vmaxu2(A.lo.x, B.lo.x) == cur.x) && (__vmaxu2(A.lo.y, B.lo.y) == cur.y);
                 if (MOLLER && keep) {
-                    const int2 pr = a.pairs[pair];
                     const uint32_t fa = swapAB ? B.face : A.face, fb = swapAB ? A.face : B.face;
                     keep = !moller_reject(a.meshes[pr.x], fa, a.meshes[pr.y], fb, face_level);
                 }
