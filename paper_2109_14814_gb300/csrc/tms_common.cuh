@@ -180,6 +180,45 @@ __device__ __forceinline__ unsigned long long warp_append(unsigned long long *co
     return base + __popc(want & lanemask_lt());
 }
 
+// Warp-staged append for high-volume outputs: lanes with pred place one record
+// each in the warp's shared-memory stage (64 records); every full 32 go out
+// with one atomic on the global counter and one coalesced store, so the
+// counter sees one atomic per 32 records instead of one per vote.  All 32
+// lanes call it together with the same n; store(pos, rec) writes record rec
+// at global position pos (the caller checks pos against its capacity).
+template <typename Rec, typename Store>
+__device__ __forceinline__ void stage_flush(Rec *stage, unsigned cnt, unsigned long long *counter,
+                                            const Store &store) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == 0 && cnt) base = atomicAdd(counter, (unsigned long long)cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((unsigned)lane < cnt) store(base + lane, stage[lane]);
+    __syncwarp();
+}
+
+template <typename Rec, typename Store>
+__device__ __forceinline__ void stage_push(Rec *stage, unsigned &n, bool pred, const Rec &rec,
+                                           unsigned long long *counter, const Store &store) {
+    const unsigned want = __ballot_sync(0xffffffffu, pred);
+    if (!want) return;
+    const int lane = threadIdx.x & 31;
+    if (pred) stage[n + __popc(want & lanemask_lt())] = rec;
+    n += __popc(want);
+    if (n >= 32) {
+        __syncwarp();
+        stage_flush(stage, 32u, counter, store);
+        // move the remainder (fewer than 32) to the front
+        const unsigned rem = n - 32;
+        Rec r;
+        if ((unsigned)lane < rem) r = stage[32 + lane];
+        __syncwarp();
+        if ((unsigned)lane < rem) stage[lane] = r;
+        __syncwarp();
+        n = rem;
+    }
+}
+
 // FP64 -> FP32 conversions from the IEEE-754 encodings, with integer operations
 // only (the FP64 pipe, which also carries FP64 conversions, is scarce on GB300).
 // Normal-range results equal round-down / round-up / round-to-nearest-even of

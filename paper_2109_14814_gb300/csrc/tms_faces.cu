@@ -366,6 +366,12 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kCellWarps = 8;
 
+struct EntryRec {
+    uint64_t key;
+    uint32_t face;
+    uint32_t pad;
+};
+
 // coordinate d of item r of a cell range (mixed radix over cnt[0..3]); counts
 // of 1 and 2 (the usual case: a cell is wider than any face) take no division
 __device__ __forceinline__ unsigned next_digit(unsigned &r, unsigned c) {
@@ -382,6 +388,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_cell_pass(FacePassArgs a, i
     __shared__ uint32_t s_excl[kCellWarps][32];
     __shared__ uint2 s_lo[kCellWarps][32];
     __shared__ uint2 s_cnt[kCellWarps][32];
+    __shared__ EntryRec s_out[kCellWarps][64];   // staged entries
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long wslot = slot - lane;           // the warp's first slot
@@ -438,6 +445,17 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_cell_pass(FacePassArgs a, i
     __syncwarp();
     const uint64_t pair_hi = (uint64_t)(uint32_t)pe.pair << 32;
     const uint32_t n0 = (uint32_t)g.n[0], n1 = (uint32_t)g.n[1], n2 = (uint32_t)g.n[2];
+    EntryRec *stage = s_out[warp];
+    unsigned staged = 0;
+    uint64_t *const ekey = a.ent_key;
+    uint32_t *const eval = a.ent_val;
+    const unsigned long long cap = a.ent_cap;
+    auto store = [ekey, eval, cap](unsigned long long pos, const EntryRec &r) {
+        if (pos < cap) {
+            ekey[pos] = r.key;
+            eval[pos] = r.face;
+        }
+    };
     for (unsigned base = 0; base < total; base += 32) {
         const unsigned j = base + lane;
         const bool act = j < total;
@@ -487,12 +505,15 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_cell_pass(FacePassArgs a, i
             emit = act;
         }
         if (MODE != MODE_MARK) {
-            const unsigned long long pos = warp_append(&a.ctr->entries, emit, FULL);
-            if (emit && pos < a.ent_cap) {
-                a.ent_key[pos] = pair_hi | ((uint64_t)cell << 1) | (uint64_t)pe.role;
-                a.ent_val[pos] = (uint32_t)(wslot - pe.face_base) + (uint32_t)owner;
-            }
+            EntryRec r;
+            r.key = pair_hi | ((uint64_t)cell << 1) | (uint64_t)pe.role;
+            r.face = (uint32_t)(wslot - pe.face_base) + (uint32_t)owner;
+            stage_push(stage, staged, emit, r, &a.ctr->entries, store);
         }
+    }
+    if (MODE != MODE_MARK) {
+        __syncwarp();
+        stage_flush(stage, staged, &a.ctr->entries, store);
     }
 }
 

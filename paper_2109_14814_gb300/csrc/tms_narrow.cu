@@ -245,21 +245,26 @@ __device__ __forceinline__ bool fp32_verified_reject(const float4 X[3][2], const
         }
     }
     // alpha >= |I - C A_exact|_inf: computed I - C A, its rounding (6u (1 + |C||A|))
-    // and the input error |C| EA
+    // and the input error |C| EA, the last two as one product |C| W with
+    // W = 6u |A| + EA
+    float W[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) W[k][j] = fmaf(6.0f * u, fabsf(A[k][j]), EA[k][j]);
     float alpha = 0.0f, cnorm = 0.0f, anorm = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         float row = 0.0f, crow = 0.0f, arow = 0.0f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            float e = (i == j) ? 1.0f : 0.0f, ca = 0.0f, ce = 0.0f;
+            float e = (i == j) ? 1.0f : 0.0f, cw = 0.0f;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 e = fmaf(-C[i][k], A[k][j], e);
-                ca = fmaf(fabsf(C[i][k]), fabsf(A[k][j]), ca);
-                ce = fmaf(fabsf(C[i][k]), EA[k][j], ce);
+                cw = fmaf(fabsf(C[i][k]), W[k][j], cw);
             }
-            row += fabsf(e) + 6.0f * u * (((i == j) ? 1.0f : 0.0f) + ca) + ce;
+            row += fabsf(e) + 6.0f * u * ((i == j) ? 1.0f : 0.0f) + cw;
             crow += fabsf(C[i][j]);
             arow += fabsf(A[i][j]);
         }

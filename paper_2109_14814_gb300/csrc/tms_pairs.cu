@@ -87,7 +87,7 @@ __global__ void k_fill_u32(uint32_t *p, const unsigned long long *d_n, unsigned 
 template <int PREC>
 struct EBox;
 template <>
-struct EBox<1> {
+struct __align__(16) EBox<1> {
     float lo[4], hi[4];
     __device__ void load(const void *fbox, uint32_t face) {
         const float4 *p = reinterpret_cast<const float4 *>(fbox) + 2 * (size_t)face;
@@ -104,7 +104,7 @@ struct EBox<1> {
     }
 };
 template <>
-struct EBox<0> {
+struct __align__(16) EBox<0> {
     double lo[4], hi[4];
     __device__ void load(const void *fbox, uint32_t face) {
         const double2 *p = reinterpret_cast<const double2 *>(fbox) + 4 * (size_t)face;
@@ -120,13 +120,6 @@ struct EBox<0> {
     }
 };
 
-template <int PREC>
-struct TileEntry {
-    EBox<PREC> box;
-    uint2 lo;         // lowest cell, 4 x u16
-    uint32_t face;
-    uint32_t pad;
-};
 
 // Moller quick test (Sec. 6.2.3) on the (x, y, px) projection.  The plane of a
 // triangle (x1, x2, x3) has normal (x1 - x2) x (x3 - x2); a point set lies
@@ -188,9 +181,21 @@ __device__ bool moller_reject(const MeshDev &ma, uint32_t fa, const MeshDev &mb,
     return same_side(VB[1], VB[0], VB[2], VA, 4) && same_side(VB[2], VB[3], VB[1], VA, 4);
 }
 
+template <int PREC>
+__device__ __forceinline__ bool boxes_overlap(const EBox<PREC> &x, const EBox<PREC> &y) {
+    bool ov = true;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) ov &= !(x.hi[d] < y.lo[d]) & !(y.hi[d] < x.lo[d]);
+    return ov;
+}
+
 template <int PREC, bool MOLLER>
 __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_level) {
-    __shared__ TileEntry<PREC> sB[kEmitWarps][kTile];
+    // the tile's B side, structure of arrays: the hot loop reads only the boxes
+    __shared__ EBox<PREC> sBox[kEmitWarps][kTile];
+    __shared__ uint2 sLo[kEmitWarps][kTile];
+    __shared__ uint32_t sFace[kEmitWarps][kTile];
+    __shared__ Cand sOut[kEmitWarps][2 * kTile];   // staged candidates
     // nothing to do after an entry overflow (the host retries with more room),
     // and a bounded amount of work in any case
     if (a.ctr->entries > a.ent_cap) return;
@@ -209,6 +214,13 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
     const unsigned long long per = (total + nw - 1) / nw;
     const unsigned long long t_begin = gw * per;
     const unsigned long long t_end = min(t_begin + per, total);
+    Cand *stage = sOut[warp];
+    unsigned staged = 0;
+    const unsigned long long cap = a.cand_cap;
+    Cand *cand_out = a.cand;
+    auto store = [cand_out, cap](unsigned long long pos, const Cand &cd) {
+        if (pos < cap) cand_out[pos] = cd;
+    };
     unsigned long long c = 0;
     if (t_begin < t_end) {
         unsigned long long lo = 0, hi = ncell - 1;
@@ -235,62 +247,74 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         const int nAt = swapAB ? nBt0 : nAt0, nBt = swapAB ? nAt0 : nBt0;
         const uint64_t key = a.keys[s];
         const uint32_t pair = (uint32_t)(key >> 32);
+        const uint32_t cell = (uint32_t)((key >> 1) & 0x7FFFFFFFu);
         const Grid &gr = a.grids[pair];
-        // this cell's coordinates, packed like the entries' lowest cells
-        uint32_t cell = (uint32_t)((key >> 1) & 0x7FFFFFFFu);
-        uint32_t cc[4];
-#pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            cc[d] = cell % (uint32_t)gr.n[d];
-            cell /= (uint32_t)gr.n[d];
-        }
-        const uint2 cur = make_uint2(cc[0] | (cc[1] << 16), cc[2] | (cc[3] << 16));
-        // own A entry in registers, the B tile in shared memory
+        const uint32_t n0 = (uint32_t)gr.n[0], n1 = (uint32_t)gr.n[1], n2 = (uint32_t)gr.n[2];
+        // own entry (the lanes' side) in registers, the other side in shared memory
         const int2 pr = a.pairs[pair];
         const void *fbA = a.meshes[pr.x].fbox, *fbB = a.meshes[pr.y].fbox;
         const void *fbL = swapAB ? fbB : fbA, *fbM = swapAB ? fbA : fbB;
-        TileEntry<PREC> A;
+        EBox<PREC> abox;
+        uint2 alo = make_uint2(0u, 0u);
+        uint32_t aface = 0;
         const bool hasA = lane < nAt;
         if (hasA) {
-            A.face = a.vals[l0 + lane];
-            A.box.load(fbL, A.face);
-            A.lo = A.box.low_cell(gr);
+            aface = a.vals[l0 + lane];
+            abox.load(fbL, aface);
+            alo = abox.low_cell(gr);
         }
         if (lane < nBt) {
-            TileEntry<PREC> B;
-            B.face = a.vals[m0 + lane];
-            B.box.load(fbM, B.face);
-            B.lo = B.box.low_cell(gr);
-            B.pad = 0;
-            sB[warp][lane] = B;
+            const uint32_t bface = a.vals[m0 + lane];
+            EBox<PREC> bb;
+            bb.load(fbM, bface);
+            sBox[warp][lane] = bb;
+            sLo[warp][lane] = bb.low_cell(gr);
+            sFace[warp][lane] = bface;
         }
         __syncwarp();
-        for (int j = 0; j < nBt; ++j) {
-            const TileEntry<PREC> &B = sB[warp][j];
+        // the owner-cell rule and the append, for lanes whose boxes overlap box j
+        auto resolve = [&](int j, bool ov) {
             bool keep = false;
-            if (hasA) {
-                bool ov = true;
-#pragma unroll
-                for (int d = 0; d < 4; ++d) ov &= !(A.box.hi[d] < B.box.lo[d] || B.box.hi[d] < A.box.lo[d]);
-                // owner cell: componentwise max of the two lowest cells == this cell
-                keep = ov && (__vmaxu2(A.lo.x, B.lo.x) == cur.x) && (__vmaxu2(A.lo.y, B.lo.y) == cur.y);
+            if (ov) {
+                // owner cell: componentwise max of the two lowest cells, compared
+                // with this cell by linear index
+                const uint2 bl = sLo[warp][j];
+                const uint32_t mx = __vmaxu2(alo.x, bl.x), my = __vmaxu2(alo.y, bl.y);
+                const uint32_t own =
+                    (((my >> 16) * n2 + (my & 0xFFFFu)) * n1 + (mx >> 16)) * n0 + (mx & 0xFFFFu);
+                keep = own == cell;
                 if (MOLLER && keep) {
-                    const uint32_t fa = swapAB ? B.face : A.face, fb = swapAB ? A.face : B.face;
+                    const uint32_t bface = sFace[warp][j];
+                    const uint32_t fa = swapAB ? bface : aface, fb = swapAB ? aface : bface;
                     keep = !moller_reject(a.meshes[pr.x], fa, a.meshes[pr.y], fb, face_level);
                 }
             }
-            const unsigned long long pos = warp_append(&a.ctr->cand, keep, FULL);
-            if (keep && pos < a.cand_cap) {
-                Cand cd;
-                cd.faceA = swapAB ? B.face : A.face;
-                cd.faceB = swapAB ? A.face : B.face;
-                cd.pair = pair;
-                cd.pad = 0;
-                a.cand[pos] = cd;
-            }
+            Cand cd;
+            const uint32_t bface = sFace[warp][j];
+            cd.faceA = swapAB ? bface : aface;
+            cd.faceB = swapAB ? aface : bface;
+            cd.pair = pair;
+            cd.pad = 0;
+            stage_push(stage, staged, keep, cd, &a.ctr->cand, store);
+        };
+        // two B boxes per step, one vote; the rest of the work only when a lane overlaps
+        int j = 0;
+        for (; j + 1 < nBt; j += 2) {
+            const EBox<PREC> b0x = sBox[warp][j], b1x = sBox[warp][j + 1];
+            const bool ov0 = hasA & boxes_overlap(abox, b0x);
+            const bool ov1 = hasA & boxes_overlap(abox, b1x);
+            if (__ballot_sync(FULL, ov0 | ov1) == 0u) continue;
+            resolve(j, ov0);
+            resolve(j + 1, ov1);
+        }
+        if (j < nBt) {
+            const bool ov0 = hasA & boxes_overlap(abox, sBox[warp][j]);
+            if (__ballot_sync(FULL, ov0) != 0u) resolve(j, ov0);
         }
         __syncwarp();
     }
+    __syncwarp();
+    stage_flush(stage, staged, &a.ctr->cand, store);
 }
 
 }  // namespace
