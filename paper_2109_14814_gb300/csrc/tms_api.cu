@@ -86,7 +86,7 @@ struct Plan {
     unsigned long long ent_cap = 0, cand_cap = 0, hit_cap = 0;
     uint64_t *ek = nullptr, *ek2 = nullptr;
     uint32_t *ev = nullptr, *ev2 = nullptr;
-    uint32_t *sort_counts = nullptr;
+    void *sort_scratch = nullptr;
     unsigned long long *partials = nullptr;
     uint32_t *head = nullptr, *hscan = nullptr, *cstart = nullptr, *cb = nullptr;
     unsigned long long *cpairs = nullptr, *poff = nullptr, *ctiles = nullptr, *toff = nullptr;
@@ -100,6 +100,7 @@ struct Plan {
     uint64_t *hk = nullptr, *hk2 = nullptr, *okeys = nullptr;
     uint32_t *hv = nullptr, *hv2 = nullptr, *keep = nullptr, *kscan = nullptr;
     int grid = 304;
+    int sort_grid = 608;
     // execution
     cudaStream_t st = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -112,11 +113,11 @@ struct Plan {
     unsigned long long last_use = 0;
 
     void free_scratch() {
-        void *ptrs[] = {bmA, bmH, ek, ek2, ev, ev2, sort_counts, head, hscan, cstart, cb, cpairs, poff, ctiles, toff, cand, surv, hits, hk,
+        void *ptrs[] = {bmA, bmH, ek, ek2, ev, ev2, sort_scratch, head, hscan, cstart, cb, cpairs, poff, ctiles, toff, cand, surv, hits, hk,
                         hk2, okeys, hv, hv2, keep, kscan};
         for (void *p : ptrs)
             if (p) cudaFree(p);
-        bmA = bmH = nullptr; ek = ek2 = nullptr; ev = ev2 = nullptr; sort_counts = nullptr; head = hscan = cstart = cb = nullptr;
+        bmA = bmH = nullptr; ek = ek2 = nullptr; ev = ev2 = nullptr; sort_scratch = nullptr; head = hscan = cstart = cb = nullptr;
         cpairs = poff = ctiles = toff = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
         hv = hv2 = keep = kscan = nullptr;
         if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
@@ -145,7 +146,9 @@ struct Plan {
         TMS_CK(dalloc(&ek2, ent_cap));
         TMS_CK(dalloc(&ev, ent_cap));
         TMS_CK(dalloc(&ev2, ent_cap));
-        TMS_CK(dalloc(&sort_counts, (size_t)kRadixBins * grid));
+        const size_t sort_bytes = std::max(radix_scratch_size(ent_cap, 32 + pair_bits),
+                                           radix_scratch_size(hit_cap, 2 * tri_bits + pair_bits));
+        TMS_CK(dalloc(reinterpret_cast<unsigned char **>(&sort_scratch), sort_bytes));
         TMS_CK(dalloc(&head, ent_cap));
         TMS_CK(dalloc(&hscan, ent_cap));
         TMS_CK(dalloc(&cstart, ent_cap));
@@ -241,9 +244,9 @@ struct Plan {
         mark(7, s);
 
         // sort entries by (pair, cell, role)
-        const bool alt = radix_sort(ek, ev, ek2, ev2, sort_counts, &d_ctr->entries, ent_cap,
-                                    32 + pair_bits, grid, s);
-        kernels += 3 * sort_passes_e;
+        const bool alt = radix_sort(ek, ev, ek2, ev2, sort_scratch, &d_ctr->entries, ent_cap,
+                                    32 + pair_bits, sort_grid, &d_ctr->status, s);
+        kernels += 2 + sort_passes_e;
         mark(8, s);
         const uint64_t *sk = alt ? ek2 : ek;
         const uint32_t *sv = alt ? ev2 : ev;
@@ -275,10 +278,9 @@ struct Plan {
         mark(11, s);
 
         // the raw hits are few: a small grid keeps the per-pass fixed cost low
-        const int hgrid = std::max(1, std::min(grid, (int)((hit_cap + kSortTile * 8 - 1) / (kSortTile * 8))));
-        const bool halt = radix_sort(hk, hv, hk2, hv2, sort_counts, &d_ctr->raw_hits, hit_cap,
-                                     2 * tri_bits + pair_bits, hgrid, s);
-        kernels += 3 * sort_passes_h;
+        const bool halt = radix_sort(hk, hv, hk2, hv2, sort_scratch, &d_ctr->raw_hits, hit_cap,
+                                     2 * tri_bits + pair_bits, sort_grid, &d_ctr->status, s);
+        kernels += 2 + sort_passes_h;
         mark(12, s);
         DedupArgs da;
         da.keys = halt ? hk2 : hk; da.vals = halt ? hv2 : hv; da.raw = hits;
@@ -460,6 +462,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     P->grid = std::min(1024, 2 * sms);
+    P->sort_grid = 4 * sms;
 
     cudaError_t e;
 #define TMS_PCK(call) do { if ((e = (call)) != cudaSuccess) { g_err = cudaGetErrorString(e); delete P; return TMS_ERR_CUDA; } } while (0)
@@ -576,6 +579,10 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
         if (c.status & ST_PAIR_LIMIT) {
             g_err = "grid proposes too many face pairs (degenerate geometry)";
             return TMS_ERR_ARG;
+        }
+        if (c.status & ST_TIMEOUT) {
+            g_err = "a device-side wait gave up (sort look-back)";
+            return TMS_ERR_TIMEOUT;
         }
         bool grow = false;
         if (c.entries > P->ent_cap) {

@@ -344,12 +344,14 @@ void launch_bounds_init(Bounds *b, int n, cudaStream_t st);
 void launch_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *g,
                         float cell_mult, cudaStream_t st);
 
-// radix sort of (u64 key, u32 value) with a device-side count; returns true
-// when the sorted data ends in the alternate buffers
+// radix sort of (u64 key, u32 value) with a device-side count (at most cap);
+// scratch holds radix_scratch_size(cap, key_bits) bytes; returns true when the
+// sorted data ends in the alternate buffers.  A look-back wait that gives up
+// sets ST_TIMEOUT in *status.
 bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
-                uint32_t *counts, const unsigned long long *d_n, unsigned long long cap,
-                int key_bits, int grid, cudaStream_t st);
-size_t radix_counts_size(int grid);
+                void *scratch, const unsigned long long *d_n, unsigned long long cap,
+                int key_bits, int grid, unsigned int *status, cudaStream_t st);
+size_t radix_scratch_size(unsigned long long cap, int key_bits);
 
 // exclusive scans with a device-side count; total written to *d_total
 void scan_u32(const uint32_t *in, uint32_t *out, const unsigned long long *d_n,

@@ -47,6 +47,7 @@ constexpr unsigned long long kRawHitCap = 1ull << 14;
 constexpr int kBmAWordBits = 17;   // 2^17 words = 4 Mi bits
 constexpr int kBmHWordBits = 16;
 constexpr int kMaxGrid = 1024;
+constexpr int kMaxTriBits = 18;    // triangles of a view: 2 N (M-1) < 2^18
 
 static __device__ __align__(256) unsigned char g_arena[kArenaBytes];
 
@@ -83,7 +84,7 @@ struct Buffers {
     uint32_t *bmA, *bmH;
     uint64_t *ek, *ek2;
     uint32_t *ev, *ev2;
-    uint32_t *sort_counts;
+    void *sort_scratch;
     uint32_t *head, *hscan, *cstart, *cb;
     unsigned long long *cpairs, *poff, *ctiles, *toff;
     Cand *cand, *surv;
@@ -106,7 +107,8 @@ size_t carve(unsigned char *base, Buffers &b) {
     b.partials = c.take<unsigned long long>(kMaxGrid);
     b.split[0] = c.take<float4>(2 * kMaxViewVertices);
     b.split[1] = c.take<float4>(2 * kMaxViewVertices);
-    b.sort_counts = c.take<uint32_t>((unsigned long long)kRadixBins * kMaxGrid);
+    b.sort_scratch = c.take<unsigned char>(std::max(radix_scratch_size(kEntCap, 32),
+                                                    radix_scratch_size(kRawHitCap, 2 * kMaxTriBits)));
     b.cand = c.take<Cand>(kCandCap);
     const size_t phase = c.off;
     // broad phase: face boxes (two per quad, FP64 at most), bitmaps, entries, cells
@@ -289,8 +291,8 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
         fa.mode = MODE_EMIT_ALL;
         launch_face_pass(fa, p.precision, p.face_level, block, s);
     }
-    const bool alt = radix_sort(b.ek, b.ev, b.ek2, b.ev2, b.sort_counts, &b.ctr->entries, kEntCap,
-                                32, grid, s);
+    const bool alt = radix_sort(b.ek, b.ev, b.ek2, b.ev2, b.sort_scratch, &b.ctr->entries, kEntCap,
+                                32, 2 * grid, &b.ctr->status, s);
     const uint64_t *sk = alt ? b.ek2 : b.ek;
     const uint32_t *sv = alt ? b.ev2 : b.ev;
     CellArgs ca;
@@ -310,9 +312,8 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     na.hit_key = b.hk; na.hit_val = b.hv; na.hit_cap = kRawHitCap; na.tau = p.tau;
     na.tri_bits = tri_bits; na.fp32_filter = p.narrow_filter;
     launch_narrow(na, p.face_level, grid * 4, s);
-    const int hgrid = std::max(1, std::min(grid, (int)((kRawHitCap + kSortTile * 8 - 1) / (kSortTile * 8))));
-    const bool halt = radix_sort(b.hk, b.hv, b.hk2, b.hv2, b.sort_counts, &b.ctr->raw_hits, kRawHitCap,
-                                 2 * tri_bits, hgrid, s);
+    const bool halt = radix_sort(b.hk, b.hv, b.hk2, b.hv2, b.sort_scratch, &b.ctr->raw_hits, kRawHitCap,
+                                 2 * tri_bits, 2 * grid, &b.ctr->status, s);
     DedupArgs da;
     da.keys = halt ? b.hk2 : b.hk; da.vals = halt ? b.hv2 : b.hv; da.raw = b.hits;
     da.meshes = b.tables->meshes; da.pairs = b.tables->pairs; da.ctr = b.ctr; da.raw_cap = kRawHitCap;
@@ -332,6 +333,10 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     if (c.status & ST_PAIR_LIMIT) {
         g_msg = "grid proposes too many face pairs (degenerate geometry)";
         return TMS_ERR_ARG;
+    }
+    if (c.status & ST_TIMEOUT) {
+        g_msg = "a device-side wait gave up (sort look-back)";
+        return TMS_ERR_TIMEOUT;
     }
     if (c.entries > kEntCap || c.cand > kCandCap || c.fp64 > kSurvCap || c.raw_hits > kRawHitCap) {
         g_msg = "a search stage exceeded the static scratch limits";

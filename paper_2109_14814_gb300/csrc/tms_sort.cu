@@ -2,16 +2,26 @@
 // exclusive scans, both with the element count read from device memory so that
 // a whole search can be captured in a CUDA graph without host round trips.
 //
-// Sort: per 8-bit digit, three launches over a fixed persistent grid of G
-// blocks, each block owning a contiguous chunk of 2048-key tiles:
-//   upsweep   per-block digit histograms  -> counts[digit][block]
-//   scan      one block: exclusive scan of counts in digit-major order
-//   downsweep stable ranking of each tile (warp match on the digit + per-warp
-//             running counts), scatter to base[digit][block] + running offset.
-// Stability: a block visits its tiles in order, warps own consecutive slices
-// of a tile, and lanes within a warp iteration are in index order.
+// Sort (one sweep per 8-bit digit):
+//   k_radix_hist   one read of the keys: the digit histograms of every pass,
+//                  and the look-back words of the tiles in use cleared;
+//   k_radix_bases  per pass, the exclusive scan of the 256 digit counts (the
+//                  global start of every digit);
+//   k_radix_pass   per pass, persistent blocks take 2048-key tiles in order
+//                  from an atomic counter; a tile is ranked (warp match on the
+//                  digit + per-warp counts), publishes its digit counts, finds
+//                  the counts of all earlier tiles by decoupled look-back,
+//                  reorders itself by digit in shared memory, and writes every
+//                  digit run to its place with consecutive threads on
+//                  consecutive addresses.
+// Stability: tiles are numbered in key order, warps own consecutive slices of
+// a tile, and lanes within a warp iteration are in index order.
+// A look-back wait on a tile that never publishes gives up after a bounded
+// number of polls and sets ST_TIMEOUT in the caller's status word.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "tms_common.cuh"
 
@@ -20,109 +30,112 @@ namespace tms {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int kMaxPasses = 8;                        // 64-bit keys
+constexpr uint64_t kFlagAgg = 1ull << 62;            // the tile's own count
+constexpr uint64_t kFlagInc = 2ull << 62;            // count of this and all earlier tiles
+constexpr uint64_t kCountMask = (1ull << 62) - 1;
+constexpr unsigned kSpinLimit = 1u << 22;            // polls of one look-back word
 
-__device__ __forceinline__ void chunk_of(unsigned long long n, int block, int grid,
-                                         unsigned long long &t0, unsigned long long &t1) {
-    unsigned long long tiles = (n + kSortTile - 1) / kSortTile;
-    unsigned long long per = (tiles + grid - 1) / grid;
-    t0 = per * block;
-    t1 = t0 + per;
-    if (t0 > tiles) t0 = tiles;
-    if (t1 > tiles) t1 = tiles;
+// scratch layout: hist[kMaxPasses][256] (u32), tile counters[kMaxPasses] (u32),
+// then per pass the look-back words of every tile, tiles x 256 (u64)
+constexpr size_t kHistBytes = (size_t)kMaxPasses * kRadixBins * sizeof(uint32_t);
+constexpr size_t kHeadBytes = kHistBytes + 256;
+
+__host__ __device__ inline unsigned long long tiles_for(unsigned long long cap) {
+    return cap == 0 ? 1 : (cap + kSortTile - 1) / kSortTile;
 }
 
-__global__ void __launch_bounds__(kSortBlock) k_radix_upsweep(const uint64_t *keys,
-                                                               const unsigned long long *d_n,
-                                                               unsigned long long cap, int shift,
-                                                               uint32_t *counts) {
-    __shared__ uint32_t hist[kRadixBins];
-    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) hist[d] = 0;
+__device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p) {
+    return *reinterpret_cast<const volatile uint64_t *>(p);
+}
+__device__ __forceinline__ void st_volatile_u64(uint64_t *p, uint64_t v) {
+    *reinterpret_cast<volatile uint64_t *>(p) = v;
+}
+
+__global__ void __launch_bounds__(kSortBlock) k_radix_hist(const uint64_t *keys,
+                                                            const unsigned long long *d_n,
+                                                            unsigned long long cap, int passes,
+                                                            uint32_t *hist, uint64_t *look,
+                                                            unsigned long long tiles_cap) {
+    __shared__ uint32_t h[kMaxPasses][kRadixBins];
+    for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     const unsigned long long n = clamp_count(d_n, cap);
-    unsigned long long t0, t1;
-    chunk_of(n, blockIdx.x, gridDim.x, t0, t1);
-    unsigned long long beg = t0 * kSortTile, end = t1 * kSortTile;
-    if (end > n) end = n;
-    for (unsigned long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        uint32_t d = (uint32_t)(keys[i] >> shift) & (kRadixBins - 1);
-        atomicAdd(&hist[d], 1u);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += stride) {
+        const uint64_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(uint32_t)(k >> (p * kRadixBits)) & (kRadixBins - 1)], 1u);
+    }
+    // clear the look-back words of the tiles this sort uses
+    const unsigned long long words = tiles_for(n) * kRadixBins;
+    for (int p = 0; p < passes; ++p) {
+        uint64_t *lp = look + (size_t)p * tiles_cap * kRadixBins;
+        for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < words;
+             i += stride)
+            lp[i] = 0;
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) counts[d * gridDim.x + blockIdx.x] = hist[d];
+    for (int i = threadIdx.x; i < passes * kRadixBins; i += blockDim.x) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(hist + i, c);
+    }
 }
 
-// exclusive scan of len values in place, one block of 1024 threads: chunks of
-// 4096 values are staged in shared memory with coalesced loads and stores, each
-// thread scans 4 consecutive values, and a warp-shuffle scan joins the threads
-__global__ void __launch_bounds__(1024) k_scan_small(uint32_t *v, int len) {
-    constexpr int CH = 4096;
-    __shared__ uint32_t buf[CH];
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < len; base += CH) {
-        for (int i = threadIdx.x; i < CH; i += blockDim.x) buf[i] = (base + i < len) ? v[base + i] : 0u;
-        __syncthreads();
-        const int o = 4 * threadIdx.x;
-        const uint32_t a0 = buf[o], a1 = buf[o + 1], a2 = buf[o + 2], a3 = buf[o + 3];
-        const uint32_t tot = a0 + a1 + a2 + a3;
-        uint32_t incl = tot;
+// per pass, exclusive scan of the 256 digit counts in place (one block of 256)
+__global__ void __launch_bounds__(kRadixBins) k_radix_bases(uint32_t *hist, int passes) {
+    __shared__ uint32_t wsum[kRadixBins / 32];
+    const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t c = hist[p * kRadixBins + d];
+        uint32_t incl = c;
         for (int off = 1; off < 32; off <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            const uint32_t y = __shfl_up_sync(FULL, incl, off);
             if (lane >= off) incl += y;
         }
         if (lane == 31) wsum[warp] = incl;
         __syncthreads();
-        if (warp == 0) {
-            uint32_t w = wsum[lane];
-            uint32_t wi = w;
-            for (int off = 1; off < 32; off <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, wi, off);
-                if (lane >= off) wi += y;
-            }
-            wsum[lane] = wi - w;
-        }
-        __syncthreads();
-        const uint32_t c0 = carry;
-        const uint32_t ex = c0 + wsum[warp] + incl - tot;
-        buf[o] = ex;
-        buf[o + 1] = ex + a0;
-        buf[o + 2] = ex + a0 + a1;
-        buf[o + 3] = ex + a0 + a1 + a2;
-        __syncthreads();
-        for (int i = threadIdx.x; i < CH; i += blockDim.x)
-            if (base + i < len) v[base + i] = buf[i];
-        if (threadIdx.x == blockDim.x - 1) carry = ex + tot;
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        hist[p * kRadixBins + d] = before + incl - c;
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kSortBlock) k_radix_downsweep(
+__global__ void __launch_bounds__(kSortBlock) k_radix_pass(
     const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out, uint32_t *vals_out,
-    const unsigned long long *d_n, unsigned long long cap, int shift, const uint32_t *counts) {
+    const unsigned long long *d_n, unsigned long long cap, int shift, const uint32_t *base,
+    uint64_t *look, uint32_t *tile_ctr, unsigned int *status) {
+    static_assert(kSortBlock == kRadixBins, "one thread per digit");
     constexpr int NW = kSortBlock / 32;
     __shared__ uint32_t wcnt[NW][kRadixBins];
-    __shared__ uint32_t base[kRadixBins];
-    __shared__ uint32_t tile_tot[kRadixBins];
+    __shared__ uint32_t t_excl[kRadixBins];     // start of each digit's run in the tile
+    __shared__ uint32_t g_off[kRadixBins];      // global start of that run
+    __shared__ uint32_t wsum[NW];
+    __shared__ uint64_t sk[kSortTile];
+    __shared__ uint32_t sv[kSortTile];
+    __shared__ uint32_t s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) base[d] = counts[d * gridDim.x + blockIdx.x];
+    const int dme = threadIdx.x;                 // the digit this thread speaks for
     const unsigned long long n = clamp_count(d_n, cap);
-    unsigned long long t0, t1;
-    chunk_of(n, blockIdx.x, gridDim.x, t0, t1);
+    const unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
     const uint32_t lt = lanemask_lt();
-    __syncthreads();
-    for (unsigned long long tile = t0; tile < t1; ++tile) {
-        const unsigned long long tbase = tile * kSortTile + (unsigned long long)warp * (32 * kSortItems);
+    const uint32_t my_base = base[dme];
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+        __syncthreads();
+        const unsigned long long tile = s_tile;
+        if (tile >= ntiles) break;
+        const unsigned long long t0 = tile * kSortTile;
+        const uint32_t tile_n = (uint32_t)min((unsigned long long)kSortTile, n - t0);
+        // ---- load this warp's slice and rank it
+        const unsigned long long wbase = t0 + (unsigned long long)warp * (32 * kSortItems);
         uint64_t k[kSortItems];
-        uint32_t v[kSortItems];
-        uint32_t dig[kSortItems];
-        uint32_t rank[kSortItems];
+        uint32_t v[kSortItems], dig[kSortItems], rank[kSortItems];
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
-            unsigned long long idx = tbase + (unsigned long long)j * 32 + lane;
-            bool ok = idx < n;
+            const unsigned long long idx = wbase + (unsigned long long)j * 32 + lane;
+            const bool ok = idx < n;
             k[j] = ok ? keys_in[idx] : 0;
             v[j] = ok ? vals_in[idx] : 0;
             dig[j] = ok ? ((uint32_t)(k[j] >> shift) & (kRadixBins - 1)) : 0xFFFFu;
@@ -134,39 +147,124 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_downsweep(
             const uint32_t d = dig[j];
             const uint32_t peers = __match_any_sync(FULL, d);
             const bool ok = d != 0xFFFFu;
-            uint32_t before = ok ? wcnt[warp][d] : 0;
+            const uint32_t before = ok ? wcnt[warp][d] : 0;
             __syncwarp();
-            const int leader = __ffs(peers) - 1;
-            if (ok && lane == leader) wcnt[warp][d] = before + __popc(peers);
+            if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
             __syncwarp();
             rank[j] = before + __popc(peers & lt);
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) {
-            uint32_t acc = 0;
+        // ---- per digit: offsets across warps and the tile's count
+        uint32_t cnt = 0;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                uint32_t c = wcnt[w][d];
-                wcnt[w][d] = acc;
-                acc += c;
-            }
-            tile_tot[d] = acc;
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t c = wcnt[w][dme];
+            wcnt[w][dme] = cnt;
+            cnt += c;
         }
+        // publish the count at once, so that later tiles never wait on this
+        // tile's own look-back
+        uint64_t *my_word = look + tile * kRadixBins + dme;
+        st_volatile_u64(my_word, (tile == 0 ? kFlagInc : kFlagAgg) | (uint64_t)cnt);
+        // start of each digit's run in the tile (block scan over digits)
+        uint32_t incl = cnt;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        // decoupled look-back over the earlier tiles
+        uint64_t prefix = 0;
+        if (tile > 0) {
+            unsigned long long t = tile - 1;
+            unsigned spins = 0;
+            for (;;) {
+                const uint64_t w = ld_volatile_u64(look + t * kRadixBins + dme);
+                const uint64_t flag = w & ~kCountMask;
+                if (flag == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(status, ST_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);
+                    continue;
+                }
+                prefix += w & kCountMask;
+                if (flag == kFlagInc || t == 0) break;
+                --t;
+            }
+            st_volatile_u64(my_word, kFlagInc | (prefix + cnt));
+        }
+        g_off[dme] = my_base + (uint32_t)prefix;
         __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        t_excl[dme] = before + incl - cnt;
+        __syncthreads();
+        // ---- reorder the tile by digit in shared memory
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const uint32_t d = dig[j];
             if (d != 0xFFFFu) {
-                const uint32_t pos = base[d] + wcnt[warp][d] + rank[j];
-                keys_out[pos] = k[j];
-                vals_out[pos] = v[j];
+                const uint32_t pos = t_excl[d] + wcnt[warp][d] + rank[j];
+                sk[pos] = k[j];
+                sv[pos] = v[j];
             }
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) base[d] += tile_tot[d];
+        // ---- write the digit runs: consecutive threads, consecutive addresses
+        for (uint32_t i = threadIdx.x; i < tile_n; i += kSortBlock) {
+            const uint64_t key = sk[i];
+            const uint32_t d = (uint32_t)(key >> shift) & (kRadixBins - 1);
+            const uint32_t out = g_off[d] + (i - t_excl[d]);
+            // in bounds whenever every look-back completed; a wait that gave up
+            // leaves wrong offsets, which must not reach memory
+            if (out < n) {
+                keys_out[out] = key;
+                vals_out[out] = sv[i];
+            }
+        }
         __syncthreads();
     }
 }
+
+}  // namespace
+
+size_t radix_scratch_size(unsigned long long cap, int key_bits) {
+    int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+    if (passes < 1) passes = 1;
+    return kHeadBytes + (size_t)passes * tiles_for(cap) * kRadixBins * sizeof(uint64_t);
+}
+
+bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                void *scratch, const unsigned long long *d_n, unsigned long long cap,
+                int key_bits, int grid, unsigned int *status, cudaStream_t st) {
+    int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+    if (passes < 1) passes = 1;
+    if (passes > kMaxPasses) passes = kMaxPasses;
+    unsigned char *sc = static_cast<unsigned char *>(scratch);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(sc);
+    uint32_t *tile_ctr = reinterpret_cast<uint32_t *>(sc + kHistBytes);
+    uint64_t *look = reinterpret_cast<uint64_t *>(sc + kHeadBytes);
+    const unsigned long long tcap = tiles_for(cap);
+    const int pgrid = (int)std::min<unsigned long long>((unsigned long long)grid, tcap);
+    cudaMemsetAsync(sc, 0, kHeadBytes, st);
+    k_radix_hist<<<grid, kSortBlock, 0, st>>>(keys, d_n, cap, passes, hist, look, tcap);
+    k_radix_bases<<<1, kRadixBins, 0, st>>>(hist, passes);
+    uint64_t *ki = keys, *ko = keys_alt;
+    uint32_t *vi = vals, *vo = vals_alt;
+    for (int p = 0; p < passes; ++p) {
+        k_radix_pass<<<pgrid, kSortBlock, 0, st>>>(ki, vi, ko, vo, d_n, cap, p * kRadixBits,
+                                                   hist + p * kRadixBins,
+                                                   look + (size_t)p * tcap * kRadixBins,
+                                                   tile_ctr + p, status);
+        uint64_t *tk = ki; ki = ko; ko = tk;
+        uint32_t *tv = vi; vi = vo; vo = tv;
+    }
+    return (passes & 1) != 0;
+}
+
+namespace {
 
 // ---------------------------------------------------------------------------
 // exclusive scan (reduce, scan partials, downsweep) with a device-side count
@@ -271,26 +369,6 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_down(const T *in, O *out,
 }
 
 }  // namespace
-
-size_t radix_counts_size(int grid) { return (size_t)kRadixBins * grid * sizeof(uint32_t); }
-
-bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
-                uint32_t *counts, const unsigned long long *d_n, unsigned long long cap,
-                int key_bits, int grid, cudaStream_t st) {
-    int passes = (key_bits + kRadixBits - 1) / kRadixBits;
-    if (passes < 1) passes = 1;
-    uint64_t *ki = keys, *ko = keys_alt;
-    uint32_t *vi = vals, *vo = vals_alt;
-    for (int p = 0; p < passes; ++p) {
-        const int shift = p * kRadixBits;
-        k_radix_upsweep<<<grid, kSortBlock, 0, st>>>(ki, d_n, cap, shift, counts);
-        k_scan_small<<<1, 1024, 0, st>>>(counts, kRadixBins * grid);
-        k_radix_downsweep<<<grid, kSortBlock, 0, st>>>(ki, vi, ko, vo, d_n, cap, shift, counts);
-        uint64_t *tk = ki; ki = ko; ko = tk;
-        uint32_t *tv = vi; vi = vo; vo = tv;
-    }
-    return (passes & 1) != 0;
-}
 
 void scan_u32(const uint32_t *in, uint32_t *out, const unsigned long long *d_n,
               unsigned long long cap, unsigned long long *partials, unsigned long long *d_total,
