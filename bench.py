@@ -16,7 +16,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -222,15 +221,17 @@ def run_tms(args, ws, rank, local):
     V = pair.A.N * pair.A.M
     F = pair.A.N * (pair.A.M - 1)
     E, C, S = stats["entries"], stats["candidates"], stats["fp64_solves"]
-    passes = math.ceil(32 / 8)
     algo = {
         # vertices read (4 x f64), FP32 split copy written (2 x float4), face box written (2 x float4)
         "face_bounds": ("tms::k_bounds_pass", 1, 2 * (32 * V + 32 * V + 32 * F)),
         # face boxes read (mark A, probe B, probe A) and entries written (u64 key + u32 face)
         "face_mark_A": ("tms::k_cell_pass<MARK>", 1, 32 * F),
         "face_probe_B+A": ("tms::k_cell_pass<PROBE_MARK, PROBE>", 2, 2 * 32 * F + ENTRY_BYTES * E),
-        # LSD radix sort of (key, face): every pass reads and writes both
-        "sort_entries": ("tms::k_radix_* (entry sort)", 3 * passes, passes * 2 * ENTRY_BYTES * E),
+        # grouping by cell: keys read, table slot and rank written ...
+        "group_count": ("tms::k_group_count", 1, E * (8 + 4 + 4)),
+        # ... then slot, key, rank and face read and the face written per entry,
+        # and per cell its key, starts and tile offset
+        "group_cells": ("tms::k_cells_* + k_group_scatter", 4, E * (4 + 8 + 4 + 4 + 4) + stats["cells"] * 24),
         # each entry's face id and face box read once, candidates written
         "emit": ("tms::k_emit", 1, E * (4 + 32) + C * 16),
         # candidates read, the FP32 split vertices of both quads gathered, FP64 solves' vertices

@@ -267,7 +267,8 @@ const char *tms_noalloc_last_error(void);
  * params.timing = 1, in this order:
  *   0 counters/bounds init   1 face pass: world bounds   2 grid parameters
  *   3 bitmap clear           4 face pass: mark A         5 face pass: probe B
- *   6 face pass: probe A (or emit all)  7 sort entries   8 cell ranges
+ *   6 face pass: probe A (or emit all)  7 cell table: counts and ranks
+ *   8 cells and scatter of the face ids
  *   9 candidate emission     10 narrow phase             11 sort hits
  *   12 merge + output        13 counter read-back
  * Writes min(cap, 14) values; *n receives 14. */

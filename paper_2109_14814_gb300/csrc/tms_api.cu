@@ -84,12 +84,16 @@ struct Plan {
     uint32_t *bmA = nullptr, *bmH = nullptr;
     int bmA_bits = 0, bmH_bits = 0;
     unsigned long long ent_cap = 0, cand_cap = 0, hit_cap = 0;
-    uint64_t *ek = nullptr, *ek2 = nullptr;
-    uint32_t *ev = nullptr, *ev2 = nullptr;
+    uint64_t *ek = nullptr;
+    uint32_t *ev = nullptr, *eslot = nullptr, *erank = nullptr, *grouped = nullptr;
+    unsigned long long tsize = 0;
+    unsigned long long *tkey = nullptr, *occ_n = nullptr, *ckey = nullptr;
+    uint2 *tcnt = nullptr;
+    uint32_t *tcell = nullptr, *occ = nullptr;
     void *sort_scratch = nullptr;
     unsigned long long *partials = nullptr;
-    uint32_t *head = nullptr, *hscan = nullptr, *cstart = nullptr, *cb = nullptr;
-    unsigned long long *cpairs = nullptr, *poff = nullptr, *ctiles = nullptr, *toff = nullptr;
+    uint32_t *cstart = nullptr, *cb = nullptr;
+    unsigned long long *toff = nullptr;
     Cand *cand = nullptr, *surv = nullptr;
     float4 *split = nullptr;          // FP32 split vertex copies of all meshes
     unsigned long long split_total = 0;
@@ -113,12 +117,14 @@ struct Plan {
     unsigned long long last_use = 0;
 
     void free_scratch() {
-        void *ptrs[] = {bmA, bmH, ek, ek2, ev, ev2, sort_scratch, head, hscan, cstart, cb, cpairs, poff, ctiles, toff, cand, surv, hits, hk,
-                        hk2, okeys, hv, hv2, keep, kscan};
+        void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, occ_n, ckey, tcnt, tcell, occ,
+                        sort_scratch, cstart, cb, toff, cand, surv, hits, hk, hk2, okeys, hv, hv2,
+                        keep, kscan};
         for (void *p : ptrs)
             if (p) cudaFree(p);
-        bmA = bmH = nullptr; ek = ek2 = nullptr; ev = ev2 = nullptr; sort_scratch = nullptr; head = hscan = cstart = cb = nullptr;
-        cpairs = poff = ctiles = toff = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
+        bmA = bmH = nullptr; ek = nullptr; ev = eslot = erank = grouped = nullptr;
+        tkey = occ_n = ckey = nullptr; tcnt = nullptr; tcell = occ = nullptr;
+        sort_scratch = nullptr; cstart = cb = nullptr; toff = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
         hv = hv2 = keep = kscan = nullptr;
         if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
     }
@@ -143,20 +149,28 @@ struct Plan {
         TMS_CK(dalloc(&bmA, (size_t)1 << (bmA_bits)));
         TMS_CK(dalloc(&bmH, (size_t)1 << (bmH_bits)));
         TMS_CK(dalloc(&ek, ent_cap));
-        TMS_CK(dalloc(&ek2, ent_cap));
         TMS_CK(dalloc(&ev, ent_cap));
-        TMS_CK(dalloc(&ev2, ent_cap));
-        const size_t sort_bytes = std::max(radix_scratch_size(ent_cap, 32 + pair_bits),
-                                           radix_scratch_size(hit_cap, 2 * tri_bits + pair_bits));
-        TMS_CK(dalloc(reinterpret_cast<unsigned char **>(&sort_scratch), sort_bytes));
-        TMS_CK(dalloc(&head, ent_cap));
-        TMS_CK(dalloc(&hscan, ent_cap));
+        TMS_CK(dalloc(&eslot, ent_cap));
+        TMS_CK(dalloc(&erank, ent_cap));
+        TMS_CK(dalloc(&grouped, ent_cap));
+        // cell table: a power of two at least the entry capacity, so that every
+        // distinct cell finds a slot; all slots free (zero)
+        tsize = 1024;
+        while (tsize < ent_cap) tsize <<= 1;
+        TMS_CK(dalloc(&tkey, tsize));
+        TMS_CK(dalloc(&tcnt, tsize));
+        TMS_CK(dalloc(&tcell, tsize));
+        TMS_CK(dalloc(&occ, tsize));
+        TMS_CK(dalloc(&occ_n, 1));
+        TMS_CK(cudaMemset(tkey, 0, tsize * sizeof(unsigned long long)));
+        TMS_CK(cudaMemset(tcnt, 0, tsize * sizeof(uint2)));
+        TMS_CK(cudaMemset(occ_n, 0, sizeof(unsigned long long)));
+        TMS_CK(dalloc(&ckey, ent_cap));
         TMS_CK(dalloc(&cstart, ent_cap));
         TMS_CK(dalloc(&cb, ent_cap));
-        TMS_CK(dalloc(&cpairs, ent_cap));
-        TMS_CK(dalloc(&poff, ent_cap));
-        TMS_CK(dalloc(&ctiles, ent_cap));
         TMS_CK(dalloc(&toff, ent_cap));
+        TMS_CK(dalloc(reinterpret_cast<unsigned char **>(&sort_scratch),
+                      radix_scratch_size(hit_cap, 2 * tri_bits + pair_bits)));
         TMS_CK(dalloc(&cand, cand_cap));
         TMS_CK(dalloc(&surv, surv_cap));
         TMS_CK(dalloc(&hits, hit_cap));
@@ -184,13 +198,20 @@ struct Plan {
         const tms_params &p = prm;
         const int prec = p.precision, fl = p.face_level;
         const int block = (p.block_faces == 64 || p.block_faces == 256) ? p.block_faces : 128;
-        const int sort_passes_e = (32 + pair_bits + kRadixBits - 1) / kRadixBits;
         const int sort_passes_h = (2 * tri_bits + pair_bits + kRadixBits - 1) / kRadixBits;
         kernels = 0;
         mark(0, s);
         cudaMemsetAsync(d_ctr, 0, sizeof(Counters), s);
         launch_bounds_init(d_bounds, n_meshes, s);
-        kernels += 1;
+        GroupArgs ga;
+        ga.ent_key = ek; ga.ent_face = ev; ga.d_n = &d_ctr->entries; ga.cap = ent_cap;
+        ga.ent_slot = eslot; ga.ent_rank = erank;
+        ga.tkey = tkey; ga.tcnt = tcnt; ga.tcell = tcell; ga.tsize = tsize;
+        ga.occ = occ; ga.occ_n = occ_n;
+        ga.cell_key = ckey; ga.cell_start = cstart; ga.cell_b = cb; ga.tile_off = toff;
+        ga.grouped = grouped; ga.partials = partials; ga.ctr = d_ctr;
+        launch_table_clear(ga, grid, s);   // the cells the previous search claimed
+        kernels += 2;
         mark(1, s);
 
         FacePassArgs fa;
@@ -243,25 +264,15 @@ struct Plan {
         }
         mark(7, s);
 
-        // sort entries by (pair, cell, role)
-        const bool alt = radix_sort(ek, ev, ek2, ev2, sort_scratch, &d_ctr->entries, ent_cap,
-                                    32 + pair_bits, sort_grid, &d_ctr->status, s);
-        kernels += 2 + sort_passes_e;
+        // group the entries by (pair, cell), mesh A's first
+        launch_group_count(ga, grid * 2, s);
         mark(8, s);
-        const uint64_t *sk = alt ? ek2 : ek;
-        const uint32_t *sv = alt ? ev2 : ev;
-
-        CellArgs ca;
-        ca.keys = sk; ca.d_n = &d_ctr->entries; ca.cap = ent_cap;
-        ca.head = head; ca.head_scan = hscan; ca.cell_start = cstart; ca.cell_b = cb;
-        ca.cell_pairs = cpairs; ca.pair_off = poff; ca.cell_tiles = ctiles; ca.tile_off = toff;
-        ca.partials = partials; ca.ctr = d_ctr;
-        launch_cells(ca, grid, s);
-        kernels += 13;
+        launch_group_cells(ga, grid * 2, s);
+        kernels += 5;
         mark(9, s);
 
         EmitArgs ea;
-        ea.keys = sk; ea.vals = sv; ea.cell_start = cstart; ea.cell_b = cb; ea.tile_off = toff;
+        ea.cell_key = ckey; ea.vals = grouped; ea.cell_start = cstart; ea.cell_b = cb; ea.tile_off = toff;
         ea.grids = d_grids; ea.meshes = d_meshes; ea.pairs = d_pairs; ea.ctr = d_ctr;
         ea.ent_cap = ent_cap; ea.cand = cand; ea.cand_cap = cand_cap; ea.moller = p.moller;
         launch_emit(ea, prec, fl, grid * 4, s);
@@ -474,7 +485,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     TMS_PCK(dalloc(&P->d_bounds, meshes.size()));
     TMS_PCK(dalloc(&P->d_grids, pairs.size()));
     TMS_PCK(dalloc(&P->d_ctr, 1));
-    TMS_PCK(dalloc(&P->partials, 1024));
+    TMS_PCK(dalloc(&P->partials, 4 * 1024));
     TMS_PCK(cudaMallocHost((void **)&P->h_ctr, sizeof(Counters)));
     TMS_PCK(cudaMallocHost((void **)&P->h_grid0, sizeof(Grid)));
     TMS_PCK(cudaMemcpy(P->d_meshes, meshes.data(), meshes.size() * sizeof(MeshDev), cudaMemcpyHostToDevice));
@@ -583,6 +594,10 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
         if (c.status & ST_TIMEOUT) {
             g_err = "a device-side wait gave up (sort look-back)";
             return TMS_ERR_TIMEOUT;
+        }
+        if (c.status & ST_TABLE_FULL) {
+            g_err = "cell table full";
+            return TMS_ERR_STATE;
         }
         bool grow = false;
         if (c.entries > P->ent_cap) {

@@ -37,6 +37,7 @@ enum StatusBits : unsigned int {
     ST_NONFINITE = 1u << 0,
     ST_TIMEOUT = 1u << 1,
     ST_PAIR_LIMIT = 1u << 2,
+    ST_TABLE_FULL = 1u << 3,
 };
 
 // ---------------------------------------------------------------------------
@@ -95,7 +96,8 @@ struct Grid {             // per pair: trimmed world and uniform grid
 
 struct Counters {
     unsigned long long entries;
-    unsigned long long cells;
+    unsigned long long cells;      // cells holding faces of both meshes
+    unsigned long long grouped;    // entries of those cells
     unsigned long long pair_slots;
     unsigned long long tiles;
     unsigned long long cand;
@@ -105,6 +107,9 @@ struct Counters {
     unsigned int status;
     unsigned int pad;
 };
+
+constexpr unsigned long long kHashEmpty = 0;   // free slot of the cell table (keys are stored + 1)
+constexpr uint32_t kNoCell = 0xFFFFFFFFu;
 
 struct Cand {             // candidate face pair
     uint32_t faceA, faceB, pair, pad;
@@ -362,26 +367,42 @@ void scan_u64(const unsigned long long *in, unsigned long long *out,
               unsigned long long *partials, unsigned long long *d_total, int grid,
               cudaStream_t st);
 
-struct CellArgs {
-    const uint64_t *keys;          // sorted entry keys
+// Grouping of the face-cell entries by (pair, cell), mesh A's faces first:
+// an open-addressing table of the (pair, cell) keys counts each cell's A and B
+// entries and ranks every entry within its (cell, role); the cells holding
+// faces of both meshes are compacted, and the face ids are scattered into one
+// array, cell by cell (the paper's per-grid-box quad lists, Sec. 6.3).
+struct GroupArgs {
+    const uint64_t *ent_key;       // pair << 32 | cell << 1 | role
+    const uint32_t *ent_face;
     const unsigned long long *d_n; // entry count
-    unsigned long long cap;
-    uint32_t *head;                // [cap]
-    uint32_t *head_scan;           // [cap]
-    uint32_t *cell_start;          // [cap]
-    uint32_t *cell_b;              // [cap]
-    unsigned long long *cell_pairs;  // [cap]  nA * nB
-    unsigned long long *pair_off;    // [cap]  exclusive scan of nA * nB
-    unsigned long long *cell_tiles;  // [cap]  32 x 32 tiles of the cell's pair matrix
-    unsigned long long *tile_off;    // [cap]  exclusive scan of the tiles
-    unsigned long long *partials;
+    unsigned long long cap;        // entry capacity
+    uint32_t *ent_slot;            // [cap] table slot of each entry
+    uint32_t *ent_rank;            // [cap] rank within (cell, role)
+    unsigned long long *tkey;      // [tsize] (pair << 31 | cell) + 1, or kHashEmpty
+    uint2 *tcnt;                   // [tsize] A and B entry counts
+    uint32_t *tcell;               // [tsize] compacted cell index or kNoCell
+    unsigned long long tsize;      // power of two >= cap
+    uint32_t *occ;                 // [tsize] slots claimed by this search
+    unsigned long long *occ_n;     // their number (cleared with the slots)
+    // per compacted cell, [cap]
+    unsigned long long *cell_key;
+    uint32_t *cell_start;          // first A entry in `grouped`
+    uint32_t *cell_b;              // first B entry
+    unsigned long long *tile_off;  // exclusive scan of the 32 x 32 tiles of nA x nB
+    uint32_t *grouped;             // [cap] face ids by cell, A then B
+    unsigned long long *partials;  // [4 * 1024]
     Counters *ctr;
 };
-void launch_cells(const CellArgs &a, int grid, cudaStream_t st);
+// table counts and ranks (1 launch), then the cells and the scatter (4 launches)
+void launch_group_count(const GroupArgs &a, int grid, cudaStream_t st);
+void launch_group_cells(const GroupArgs &a, int grid, cudaStream_t st);
+// returns the slots claimed by the previous search to the free state
+void launch_table_clear(const GroupArgs &a, int grid, cudaStream_t st);
 
 struct EmitArgs {
-    const uint64_t *keys;          // sorted entry keys
-    const uint32_t *vals;          // face ids in key order
+    const unsigned long long *cell_key;   // pair << 31 | cell
+    const uint32_t *vals;          // face ids grouped by cell
     const uint32_t *cell_start;
     const uint32_t *cell_b;
     const unsigned long long *tile_off;

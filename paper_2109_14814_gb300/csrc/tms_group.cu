@@ -1,0 +1,282 @@
+// Grouping of the broad phase's face-cell entries by grid cell.
+//
+// The paper's GPU broad phase keeps, per grid box, the list of quads of each
+// mesh that touch it, and proposes every (A quad, B quad) pair of a box
+// (Sec. 6.2.1, Sec. 6.3 and Algorithm 1, whose box_gid_idxs array is the
+// exclusive scan of nA * nB over the boxes).  Re-designed for GB300 without a
+// sort: the entries need only be grouped by (pair, cell), with mesh A's faces
+// first, so
+//   k_group_count    finds or claims each entry's (pair, cell) key in an
+//                    open-addressing table (linear probing), and one atomic per
+//                    group of equal keys in a warp gives every entry its rank
+//                    within (cell, role) and the cell its A and B counts;
+//   k_cells_*        scan the claimed slots (three launches: per-block sums,
+//                    one block over the sums, per-slot offsets): cells holding
+//                    faces of both meshes get consecutive indices, their
+//                    entries' start, their first B entry and their 32 x 32 tile
+//                    offset; the totals go to the counters;
+//   k_group_scatter  writes every entry's face id to its cell's A or B list.
+// The order of a cell's entries is left to the atomics; the search's output
+// does not depend on it.  Only the slots a search claimed are returned to the
+// free state, by k_table_clear at the start of the next search.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tms_common.cuh"
+
+namespace tms {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kGroupBlock = 256;
+constexpr int kCellScanBlock = 512;
+constexpr int kTileEdge = 32;
+
+// the table slot of stored key k (never kHashEmpty), claimed if new (the
+// claimer records it in occ)
+__device__ __forceinline__ uint32_t table_slot(const GroupArgs &a, unsigned long long k) {
+    const unsigned long long mask = a.tsize - 1;
+    unsigned long long h = mix64(k) & mask;
+    for (unsigned long long probe = 0; probe < a.tsize; ++probe) {
+        unsigned long long cur = __ldcg(a.tkey + h);
+        if (cur == k) return (uint32_t)h;
+        if (cur == kHashEmpty) {
+            cur = atomicCAS(a.tkey + h, kHashEmpty, k);
+            if (cur == kHashEmpty) {
+                const unsigned long long pos = atomicAdd(a.occ_n, 1ULL);
+                if (pos < a.tsize) a.occ[pos] = (uint32_t)h;
+                return (uint32_t)h;
+            }
+            if (cur == k) return (uint32_t)h;
+        }
+        h = (h + 1) & mask;
+    }
+    // unreachable while the table has at least as many slots as entries
+    atomicOr(&a.ctr->status, ST_TABLE_FULL);
+    return 0;
+}
+
+__global__ void __launch_bounds__(kGroupBlock) k_group_count(GroupArgs a) {
+    if (a.ctr->entries > a.cap) return;   // the host retries with more room
+    const unsigned long long n = a.ctr->entries;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x - lane;
+         i0 < n; i0 += stride) {
+        const unsigned long long i = i0 + lane;
+        const bool ok = i < n;
+        const uint64_t key = ok ? a.ent_key[i] : ~0ULL;
+        // lanes with the same (pair, cell, role) share one table lookup and one atomic
+        const uint32_t peers = __match_any_sync(FULL, key);
+        const int leader = __ffs(peers) - 1;
+        uint32_t slot = 0, base = 0;
+        if (ok && lane == leader) {
+            slot = table_slot(a, (key >> 1) + 1);
+            uint32_t *cnt = (key & 1) ? &a.tcnt[slot].y : &a.tcnt[slot].x;
+            base = atomicAdd(cnt, (uint32_t)__popc(peers));
+        }
+        slot = __shfl_sync(FULL, slot, leader);
+        base = __shfl_sync(FULL, base, leader);
+        if (ok) {
+            a.ent_slot[i] = slot;
+            a.ent_rank[i] = base + __popc(peers & lt);
+        }
+    }
+}
+
+struct CellVals {
+    unsigned long long both, size, tiles, pairs;
+};
+
+__device__ __forceinline__ CellVals cell_vals(const GroupArgs &a, uint32_t slot) {
+    const uint2 c = a.tcnt[slot];
+    CellVals v;
+    const bool both = c.x > 0 && c.y > 0;
+    v.both = both ? 1 : 0;
+    v.size = both ? (unsigned long long)c.x + c.y : 0;
+    v.tiles = both ? (unsigned long long)((c.x + kTileEdge - 1) / kTileEdge) * ((c.y + kTileEdge - 1) / kTileEdge) : 0;
+    v.pairs = both ? (unsigned long long)c.x * c.y : 0;
+    return v;
+}
+
+__device__ __forceinline__ void occ_chunk(unsigned long long n, unsigned long long &b,
+                                          unsigned long long &e) {
+    unsigned long long per = (n + gridDim.x - 1) / gridDim.x;
+    per = (per + 31) & ~31ULL;
+    b = per * blockIdx.x;
+    e = b + per;
+    if (b > n) b = n;
+    if (e > n) e = n;
+}
+
+__device__ __forceinline__ unsigned long long claimed(const GroupArgs &a) {
+    const unsigned long long n = *a.occ_n;
+    return n < a.tsize ? n : a.tsize;
+}
+
+__global__ void __launch_bounds__(kCellScanBlock) k_cells_reduce(GroupArgs a) {
+    __shared__ unsigned long long red[4][kCellScanBlock / 32];
+    if (a.ctr->entries > a.cap) return;
+    const unsigned long long n = claimed(a);
+    unsigned long long b, e;
+    occ_chunk(n, b, e);
+    unsigned long long s[4] = {0, 0, 0, 0};
+    for (unsigned long long j = b + threadIdx.x; j < e; j += blockDim.x) {
+        const CellVals v = cell_vals(a, a.occ[j]);
+        s[0] += v.both; s[1] += v.size; s[2] += v.tiles; s[3] += v.pairs;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        for (int off = 16; off > 0; off >>= 1) s[k] += __shfl_xor_sync(FULL, s[k], off);
+        if (lane == 0) red[k][warp] = s[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+        a.partials[threadIdx.x * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// exclusive scan of the per-block sums (one block of 1024 threads, g <= 1024)
+__global__ void __launch_bounds__(1024) k_cells_partials(GroupArgs a, int g) {
+    __shared__ unsigned long long p[1024];
+    if (a.ctr->entries > a.cap) return;
+    for (int k = 0; k < 4; ++k) {
+        const unsigned long long x = threadIdx.x < g ? a.partials[k * g + threadIdx.x] : 0;
+        p[threadIdx.x] = x;
+        __syncthreads();
+        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+            const unsigned long long y = threadIdx.x >= off ? p[threadIdx.x - off] : 0;
+            __syncthreads();
+            p[threadIdx.x] += y;
+            __syncthreads();
+        }
+        if (threadIdx.x < g) a.partials[k * g + threadIdx.x] = p[threadIdx.x] - x;
+        if (threadIdx.x == blockDim.x - 1) {
+            const unsigned long long tot = p[threadIdx.x];
+            if (k == 0) a.ctr->cells = tot;
+            else if (k == 1) a.ctr->grouped = tot;
+            else if (k == 2) a.ctr->tiles = tot;
+            else a.ctr->pair_slots = tot;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kCellScanBlock) k_cells_down(GroupArgs a) {
+    __shared__ unsigned long long wsum[3][kCellScanBlock / 32];
+    __shared__ unsigned long long carry[3];
+    if (a.ctr->entries > a.cap) return;
+    const unsigned long long n = claimed(a);
+    unsigned long long b, e;
+    occ_chunk(n, b, e);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 3) carry[threadIdx.x] = a.partials[threadIdx.x * gridDim.x + blockIdx.x];
+    __syncthreads();
+    for (unsigned long long base = b; base < e; base += blockDim.x) {
+        const unsigned long long j = base + threadIdx.x;
+        uint32_t slot = 0;
+        CellVals v = {0, 0, 0, 0};
+        if (j < e) {
+            slot = a.occ[j];
+            v = cell_vals(a, slot);
+        }
+        unsigned long long x[3] = {v.both, v.size, v.tiles}, incl[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            incl[k] = x[k];
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long y = __shfl_up_sync(FULL, incl[k], off);
+                if (lane >= off) incl[k] += y;
+            }
+            if (lane == 31) wsum[k][warp] = incl[k];
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const unsigned long long w = lane < (int)(blockDim.x >> 5) ? wsum[k][lane] : 0;
+                unsigned long long wi = w;
+                for (int off = 1; off < 32; off <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(FULL, wi, off);
+                    if (lane >= off) wi += y;
+                }
+                if (lane < (int)(blockDim.x >> 5)) wsum[k][lane] = wi - w;
+            }
+        }
+        __syncthreads();
+        unsigned long long ex[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ex[k] = carry[k] + wsum[k][warp] + incl[k] - x[k];
+        if (j < e) {
+            if (v.both) {
+                const unsigned long long c = ex[0];
+                const uint2 cnt = a.tcnt[slot];
+                a.cell_key[c] = a.tkey[slot] - 1;
+                a.cell_start[c] = (uint32_t)ex[1];
+                a.cell_b[c] = (uint32_t)ex[1] + cnt.x;
+                a.tile_off[c] = ex[2];
+                a.tcell[slot] = (uint32_t)c;
+            } else {
+                a.tcell[slot] = kNoCell;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) carry[k] = ex[k] + x[k];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kGroupBlock) k_group_scatter(GroupArgs a) {
+    if (a.ctr->entries > a.cap) return;
+    const unsigned long long n = a.ctr->entries;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += stride) {
+        const uint32_t slot = a.ent_slot[i];
+        const uint32_t c = a.tcell[slot];
+        if (c == kNoCell) continue;
+        const uint32_t start = (a.ent_key[i] & 1) ? a.cell_b[c] : a.cell_start[c];
+        const unsigned long long pos = (unsigned long long)start + a.ent_rank[i];
+        if (pos < a.cap) a.grouped[pos] = a.ent_face[i];
+    }
+}
+
+__global__ void __launch_bounds__(kGroupBlock) k_table_clear(GroupArgs a) {
+    const unsigned long long n = claimed(a);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
+         j += stride) {
+        const uint32_t s = a.occ[j];
+        a.tkey[s] = kHashEmpty;
+        a.tcnt[s] = make_uint2(0u, 0u);
+    }
+}
+
+}  // namespace
+
+void launch_group_count(const GroupArgs &a, int grid, cudaStream_t st) {
+    k_group_count<<<grid, kGroupBlock, 0, st>>>(a);
+}
+
+void launch_group_cells(const GroupArgs &a, int grid, cudaStream_t st) {
+    const int g = grid < 1024 ? grid : 1024;
+    k_cells_reduce<<<g, kCellScanBlock, 0, st>>>(a);
+    k_cells_partials<<<1, 1024, 0, st>>>(a, g);
+    k_cells_down<<<g, kCellScanBlock, 0, st>>>(a);
+    k_group_scatter<<<grid, kGroupBlock, 0, st>>>(a);
+}
+
+void launch_table_clear(const GroupArgs &a, int grid, cudaStream_t st) {
+    k_table_clear<<<grid, kGroupBlock, 0, st>>>(a);
+    cudaMemsetAsync(a.occ_n, 0, sizeof(unsigned long long), st);
+}
+
+}  // namespace tms

@@ -41,6 +41,7 @@ namespace {
 constexpr size_t kArenaBytes = 64ull << 20;
 constexpr unsigned long long kMaxViewVertices = 1ull << 17;
 constexpr unsigned long long kEntCap = 1ull << 18;
+constexpr unsigned long long kTableSize = kEntCap;      // cell table slots (>= entries)
 constexpr unsigned long long kCandCap = 1ull << 18;
 constexpr unsigned long long kSurvCap = 1ull << 16;
 constexpr unsigned long long kRawHitCap = 1ull << 14;
@@ -82,11 +83,14 @@ struct Buffers {
     float4 *split[2];
     unsigned char *fbox[2];
     uint32_t *bmA, *bmH;
-    uint64_t *ek, *ek2;
-    uint32_t *ev, *ev2;
+    uint64_t *ek;
+    uint32_t *ev, *eslot, *erank, *grouped;
+    unsigned long long *tkey, *occ_n, *ckey;
+    uint2 *tcnt;
+    uint32_t *tcell, *occ;
     void *sort_scratch;
-    uint32_t *head, *hscan, *cstart, *cb;
-    unsigned long long *cpairs, *poff, *ctiles, *toff;
+    uint32_t *cstart, *cb;
+    unsigned long long *toff;
     Cand *cand, *surv;
     tms_hit *hits;
     uint64_t *hk, *hk2, *okeys;
@@ -94,22 +98,26 @@ struct Buffers {
 };
 
 // the arena's layout; also used to check, at set-up, that it fits.  Buffers
-// live across the whole search come first; then the broad phase's buffers, and
-// over the same bytes the narrow phase's and the merge's, which are written
-// only after candidate emission, the broad phase's last reader, has run on the
-// same stream.
+// live across the whole search (and the cell table with the list of slots a
+// call claimed, which the next call frees) come first; then the broad phase's
+// buffers, and over the same bytes the narrow phase's and the merge's, which
+// are written only after candidate emission, the broad phase's last reader,
+// has run on the same stream.  The array starts zeroed: every table slot free.
 size_t carve(unsigned char *base, Buffers &b) {
     Carve c{base};
     b.tables = c.take<Tables>(1);
     b.bounds = c.take<Bounds>(2);
     b.grids = c.take<Grid>(1);
     b.ctr = c.take<Counters>(1);
-    b.partials = c.take<unsigned long long>(kMaxGrid);
+    b.partials = c.take<unsigned long long>(4 * kMaxGrid);
     b.split[0] = c.take<float4>(2 * kMaxViewVertices);
     b.split[1] = c.take<float4>(2 * kMaxViewVertices);
-    b.sort_scratch = c.take<unsigned char>(std::max(radix_scratch_size(kEntCap, 32),
-                                                    radix_scratch_size(kRawHitCap, 2 * kMaxTriBits)));
+    b.sort_scratch = c.take<unsigned char>(radix_scratch_size(kRawHitCap, 2 * kMaxTriBits));
     b.cand = c.take<Cand>(kCandCap);
+    b.tkey = c.take<unsigned long long>(kTableSize);
+    b.tcnt = c.take<uint2>(kTableSize);
+    b.occ = c.take<uint32_t>(kTableSize);
+    b.occ_n = c.take<unsigned long long>(1);
     const size_t phase = c.off;
     // broad phase: face boxes (two per quad, FP64 at most), bitmaps, entries, cells
     b.fbox[0] = c.take<unsigned char>(2 * kMaxViewVertices * 64);
@@ -117,16 +125,14 @@ size_t carve(unsigned char *base, Buffers &b) {
     b.bmA = c.take<uint32_t>(1ull << kBmAWordBits);
     b.bmH = c.take<uint32_t>(1ull << kBmHWordBits);
     b.ek = c.take<uint64_t>(kEntCap);
-    b.ek2 = c.take<uint64_t>(kEntCap);
     b.ev = c.take<uint32_t>(kEntCap);
-    b.ev2 = c.take<uint32_t>(kEntCap);
-    b.head = c.take<uint32_t>(kEntCap);
-    b.hscan = c.take<uint32_t>(kEntCap);
+    b.eslot = c.take<uint32_t>(kEntCap);
+    b.erank = c.take<uint32_t>(kEntCap);
+    b.grouped = c.take<uint32_t>(kEntCap);
+    b.tcell = c.take<uint32_t>(kTableSize);
+    b.ckey = c.take<unsigned long long>(kEntCap);
     b.cstart = c.take<uint32_t>(kEntCap);
     b.cb = c.take<uint32_t>(kEntCap);
-    b.cpairs = c.take<unsigned long long>(kEntCap);
-    b.poff = c.take<unsigned long long>(kEntCap);
-    b.ctiles = c.take<unsigned long long>(kEntCap);
     b.toff = c.take<unsigned long long>(kEntCap);
     const size_t broad_end = c.off;
     // narrow phase and merge, over the broad phase's bytes
@@ -256,6 +262,14 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     // the launch sequence of tms_search, on the static buffers
     NA_CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters), s));
     launch_bounds_init(b.bounds, 2, s);
+    GroupArgs ga;
+    ga.ent_key = b.ek; ga.ent_face = b.ev; ga.d_n = &b.ctr->entries; ga.cap = kEntCap;
+    ga.ent_slot = b.eslot; ga.ent_rank = b.erank;
+    ga.tkey = b.tkey; ga.tcnt = b.tcnt; ga.tcell = b.tcell; ga.tsize = kTableSize;
+    ga.occ = b.occ; ga.occ_n = b.occ_n;
+    ga.cell_key = b.ckey; ga.cell_start = b.cstart; ga.cell_b = b.cb; ga.tile_off = b.toff;
+    ga.grouped = b.grouped; ga.partials = b.partials; ga.ctr = b.ctr;
+    launch_table_clear(ga, grid, s);
     FacePassArgs fa;
     memset(&fa, 0, sizeof(fa));
     fa.meshes = b.tables->meshes;
@@ -291,18 +305,10 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
         fa.mode = MODE_EMIT_ALL;
         launch_face_pass(fa, p.precision, p.face_level, block, s);
     }
-    const bool alt = radix_sort(b.ek, b.ev, b.ek2, b.ev2, b.sort_scratch, &b.ctr->entries, kEntCap,
-                                32, 2 * grid, &b.ctr->status, s);
-    const uint64_t *sk = alt ? b.ek2 : b.ek;
-    const uint32_t *sv = alt ? b.ev2 : b.ev;
-    CellArgs ca;
-    ca.keys = sk; ca.d_n = &b.ctr->entries; ca.cap = kEntCap;
-    ca.head = b.head; ca.head_scan = b.hscan; ca.cell_start = b.cstart; ca.cell_b = b.cb;
-    ca.cell_pairs = b.cpairs; ca.pair_off = b.poff; ca.cell_tiles = b.ctiles; ca.tile_off = b.toff;
-    ca.partials = b.partials; ca.ctr = b.ctr;
-    launch_cells(ca, grid, s);
+    launch_group_count(ga, grid, s);
+    launch_group_cells(ga, grid, s);
     EmitArgs ea;
-    ea.keys = sk; ea.vals = sv; ea.cell_start = b.cstart; ea.cell_b = b.cb; ea.tile_off = b.toff;
+    ea.cell_key = b.ckey; ea.vals = b.grouped; ea.cell_start = b.cstart; ea.cell_b = b.cb; ea.tile_off = b.toff;
     ea.grids = b.grids; ea.meshes = b.tables->meshes; ea.pairs = b.tables->pairs; ea.ctr = b.ctr;
     ea.ent_cap = kEntCap; ea.cand = b.cand; ea.cand_cap = kCandCap; ea.moller = p.moller;
     launch_emit(ea, p.precision, p.face_level, grid * 4, s);
@@ -337,6 +343,10 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     if (c.status & ST_TIMEOUT) {
         g_msg = "a device-side wait gave up (sort look-back)";
         return TMS_ERR_TIMEOUT;
+    }
+    if (c.status & ST_TABLE_FULL) {
+        g_msg = "cell table full";
+        return TMS_ERR_STATE;
     }
     if (c.entries > kEntCap || c.cand > kCandCap || c.fp64 > kSurvCap || c.raw_hits > kRawHitCap) {
         g_msg = "a search stage exceeded the static scratch limits";

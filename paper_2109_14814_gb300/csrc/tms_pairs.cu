@@ -1,10 +1,9 @@
-// Cell ranges and candidate-pair emission of the broad phase.
+// Candidate-pair emission of the broad phase.
 //
-// After the sort, entries of one (pair, cell) are contiguous with mesh A's
-// entries first (the role is the key's lowest bit).  Per cell: the start of its
-// A list and B list and nA * nB, the number of face pairs it proposes; the
-// exclusive scan of nA * nB is the paper's box_gid_idxs array (Sec. 6.3,
-// Algorithm 1).
+// Input: the face ids grouped by cell, mesh A's first (tms_group.cu), with per
+// cell its key, the start of its A and B lists and the exclusive scan of its
+// 32 x 32 tiles.  nA * nB is the number of face pairs a cell proposes; its
+// exclusive scan is the paper's box_gid_idxs array (Sec. 6.3, Algorithm 1).
 //
 // Emission re-designed for GB300: the nA x nB pair matrix of a cell is cut
 // into 32 x 32 tiles and one warp tests one tile -- each lane holds one A box
@@ -15,7 +14,8 @@
 // test of Sec. 6.2.2, then the owner-cell rule -- the pair is kept only in the
 // cell that is the componentwise max of the two faces' lowest cells, so a pair
 // sharing several cells is emitted exactly once -- then optionally the Moller
-// quick test of Sec. 6.2.3; survivors are compacted with one atomic per warp.
+// quick test of Sec. 6.2.3; survivors are staged per warp and appended 32 at a
+// time.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,57 +28,6 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kTile = 32;
 constexpr int kEmitWarps = 8;
-
-__global__ void k_cell_heads(const uint64_t *keys, const unsigned long long *d_n,
-                             unsigned long long cap, uint32_t *head) {
-    const unsigned long long n = clamp_count(d_n, cap);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        head[i] = (i == 0 || (keys[i] >> 1) != (keys[i - 1] >> 1)) ? 1u : 0u;
-    }
-}
-
-// cell index of entry i = exclusive scan of heads + head - 1
-__global__ void k_cell_fill(const uint64_t *keys, const uint32_t *head, const uint32_t *hscan,
-                            const unsigned long long *d_n, unsigned long long cap,
-                            uint32_t *cell_start, uint32_t *cell_b) {
-    const unsigned long long n = clamp_count(d_n, cap);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t h = head[i];
-        const uint32_t c = hscan[i] + h - 1;
-        if (h) cell_start[c] = (uint32_t)i;
-        const bool isB = keys[i] & 1;
-        if (isB && (h || !(keys[i - 1] & 1))) cell_b[c] = (uint32_t)i;
-    }
-}
-
-__global__ void k_cell_pairs(const uint32_t *cell_start, uint32_t *cell_b,
-                             const unsigned long long *d_cells, const unsigned long long *d_n,
-                             unsigned long long cap, unsigned long long *pairs,
-                             unsigned long long *tiles) {
-    const unsigned long long nc = clamp_count(d_cells, cap);
-    const unsigned long long n = clamp_count(d_n, cap);
-    for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nc;
-         c += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t s = cell_start[c];
-        const uint32_t e = (c + 1 < nc) ? cell_start[c + 1] : (uint32_t)n;
-        uint32_t b = cell_b[c];
-        if (b == 0xFFFFFFFFu || b < s || b > e) b = e;
-        cell_b[c] = b;
-        const unsigned long long nA = b - s, nB = e - b;
-        pairs[c] = nA * nB;
-        tiles[c] = ((nA + kTile - 1) / kTile) * ((nB + kTile - 1) / kTile);
-    }
-}
-
-__global__ void k_fill_u32(uint32_t *p, const unsigned long long *d_n, unsigned long long cap,
-                           uint32_t v) {
-    const unsigned long long n = clamp_count(d_n, cap);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        p[i] = v;
-}
 
 // ---------------------------------------------------------------------------
 // emission
@@ -205,7 +154,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
     }
     const unsigned long long total = a.ctr->tiles;
     const unsigned long long ncell = clamp_count(&a.ctr->cells, a.ent_cap);
-    const unsigned long long nent = clamp_count(&a.ctr->entries, a.ent_cap);
+    const unsigned long long nent = clamp_count(&a.ctr->grouped, a.ent_cap);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long gw = blockIdx.x * (unsigned long long)kEmitWarps + warp;
     const unsigned long long nw = (unsigned long long)gridDim.x * kEmitWarps;
@@ -245,9 +194,9 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         const bool swapAB = nBt0 > nAt0;
         const uint32_t l0 = swapAB ? b0 : a0, m0 = swapAB ? a0 : b0;
         const int nAt = swapAB ? nBt0 : nAt0, nBt = swapAB ? nAt0 : nBt0;
-        const uint64_t key = a.keys[s];
-        const uint32_t pair = (uint32_t)(key >> 32);
-        const uint32_t cell = (uint32_t)((key >> 1) & 0x7FFFFFFFu);
+        const unsigned long long ck = a.cell_key[c];
+        const uint32_t pair = (uint32_t)(ck >> 31);
+        const uint32_t cell = (uint32_t)(ck & 0x7FFFFFFFu);
         const Grid &gr = a.grids[pair];
         const uint32_t n0 = (uint32_t)gr.n[0], n1 = (uint32_t)gr.n[1], n2 = (uint32_t)gr.n[2];
         // own entry (the lanes' side) in registers, the other side in shared memory
@@ -318,20 +267,6 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
 }
 
 }  // namespace
-
-void launch_cells(const CellArgs &a, int grid, cudaStream_t st) {
-    const int B = 256;
-    k_cell_heads<<<grid, B, 0, st>>>(a.keys, a.d_n, a.cap, a.head);
-    scan_u32(a.head, a.head_scan, a.d_n, a.cap, a.partials, &a.ctr->cells, grid, st);
-    k_fill_u32<<<grid, B, 0, st>>>(a.cell_b, &a.ctr->cells, a.cap, 0xFFFFFFFFu);
-    k_cell_fill<<<grid, B, 0, st>>>(a.keys, a.head, a.head_scan, a.d_n, a.cap, a.cell_start,
-                                    a.cell_b);
-    k_cell_pairs<<<grid, B, 0, st>>>(a.cell_start, a.cell_b, &a.ctr->cells, a.d_n, a.cap,
-                                     a.cell_pairs, a.cell_tiles);
-    scan_u64(a.cell_pairs, a.pair_off, &a.ctr->cells, a.cap, a.partials, &a.ctr->pair_slots, grid,
-             st);
-    scan_u64(a.cell_tiles, a.tile_off, &a.ctr->cells, a.cap, a.partials, &a.ctr->tiles, grid, st);
-}
 
 void launch_emit(const EmitArgs &a, int precision, int face_level, int grid, cudaStream_t st) {
     const dim3 b(32 * kEmitWarps);
