@@ -35,6 +35,13 @@ WORKLOAD = dict(workload="mesh-vs-mesh search, 4096x512 vs 4096x512 vertex grids
                          "256 planted hits + 1e4 planted near-misses (1e-9..1e-3)",
                 N=4096, M=512, triangles_per_mesh=4186112)
 ENTRY_BYTES = 8 + 4                   # face-cell entry: u64 key, u32 face id
+NOMINAL_SM_MAX_MHZ = 2070              # GB300 maximum SM clock
+# FP32 operations of one verified FP32 solve (an FMA counts 2): 20 system
+# entries with error bounds (12 each), elimination on [A | I | r] (98), back
+# substitution for five right-hand sides (80), the bound matrix W (32),
+# alpha = |I - C A| + |C| W (337), the residual bound (112), the error bound
+# (35) and the margin tests (22)
+FP32_SOLVE_FLOPS = 956
 
 
 def dist_env():
@@ -213,46 +220,64 @@ def run_tms(args, ws, rank, local):
     value, ms_per_step = job_times(total_ms, args.steps, ws)
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
 
-    # Roofline per kernel (stage), from its algorithmic bytes per launch -- what
-    # the stage must move at least, counted from the workload and the search's
-    # own statistics -- and its CUDA-event time; the slowest stage is reported
-    # as `roofline`.  V vertices and F faces per mesh (quads), E face-cell
-    # entries, C candidate quad pairs, S FP64 solves.
+    # Roofline per kernel (stage).  Memory-bound stages: algorithmic bytes per
+    # launch (what the stage must move at least, from the workload and the
+    # search's statistics) against the measured copy bandwidth.  ALU-bound
+    # stages: algorithmic FP32 operations against the FP32 lane rate of this
+    # GPU (SMs x 128 lanes x the maximum SM clock; an FMA counts 2 FLOPs).
+    # The slowest stage is reported as `roofline`.  V vertices and F faces per
+    # mesh (quads), E face-cell entries, P proposed face pairs, C candidate
+    # quad pairs, S32 / S64 triangle pairs through the FP32 / FP64 solve.
     V = pair.A.N * pair.A.M
     F = pair.A.N * (pair.A.M - 1)
     E, C, S = stats["entries"], stats["candidates"], stats["fp64_solves"]
+    P, S32 = stats["pair_slots"], stats["fp32_solves"]
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    sm_hz = float(NOMINAL_SM_MAX_MHZ) * 1e6
+    lane_ops = sms * 128 * sm_hz                   # FP32 lane operations per second
     algo = {
         # vertices read (4 x f64), FP32 split copy written (2 x float4), face box written (2 x float4)
-        "face_bounds": ("tms::k_bounds_pass", 1, 2 * (32 * V + 32 * V + 32 * F)),
+        "face_bounds": ("tms::k_bounds_pass", "hbm", 1, 2 * (32 * V + 32 * V + 32 * F)),
         # face boxes read (mark A, probe B, probe A) and entries written (u64 key + u32 face)
-        "face_mark_A": ("tms::k_cell_pass<MARK>", 1, 32 * F),
-        "face_probe_B+A": ("tms::k_cell_pass<PROBE_MARK, PROBE>", 2, 2 * 32 * F + ENTRY_BYTES * E),
+        "face_mark_A": ("tms::k_cell_pass<MARK>", "hbm", 1, 32 * F),
+        "face_probe_B+A": ("tms::k_cell_pass<PROBE_MARK, PROBE>", "hbm", 2, 2 * 32 * F + ENTRY_BYTES * E),
         # grouping by cell: keys read, table slot and rank written ...
-        "group_count": ("tms::k_group_count", 1, E * (8 + 4 + 4)),
+        "group_count": ("tms::k_group_count", "hbm", 1, E * (8 + 4 + 4)),
         # ... then slot, key, rank and face read and the face written per entry,
         # and per cell its key, starts and tile offset
-        "group_cells": ("tms::k_cells_* + k_group_scatter", 4, E * (4 + 8 + 4 + 4 + 4) + stats["cells"] * 24),
-        # each entry's face id and face box read once, candidates written
-        "emit": ("tms::k_emit", 1, E * (4 + 32) + C * 16),
-        # candidates read, the FP32 split vertices of both quads gathered, FP64 solves' vertices
-        "narrow": ("tms::k_narrow_filter + k_narrow_fp64", 2, C * (16 + 2 * 4 * 32) + S * 2 * 3 * 32),
+        "group_cells": ("tms::k_cells_* + k_group_scatter", "hbm", 4,
+                        E * (4 + 8 + 4 + 4 + 4) + stats["cells"] * 24),
+        # the box test of every proposed face pair: 8 FP32 compares
+        "emit": ("tms::k_emit", "alu", 1, 8 * P),
+        # the verified FP32 solve: FP32_SOLVE_FLOPS per triangle pair
+        "narrow": ("tms::k_narrow_filter + k_narrow_fp64", "alu", 2, FP32_SOLVE_FLOPS * S32),
     }
     stage_time = dict(stage_ms)
     stage_time["face_probe_B+A"] = stage_ms.get("face_probe_B", 0.0) + stage_ms.get("face_probe_A", 0.0)
     kernels = {}
-    for st_name, (kname, launches, nbytes) in algo.items():
+    for st_name, (kname, bound, launches, work) in algo.items():
         t = stage_time.get(st_name, 0.0)
-        gbs = (nbytes / 1e9) / (t / 1e3) if t > 0 else None
-        kernels[st_name] = {"kernel": kname, "launches": launches, "ms": t,
-                            "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
-                            "frac": gbs / peaks["hbm_gbs"] if gbs else None}
+        if bound == "hbm":
+            ach = (work / 1e9) / (t / 1e3) if t > 0 else None
+            peak, unit = peaks.get("hbm_gbs"), "GB/s"
+        elif st_name == "narrow":
+            ach = (work / 1e12) / (t / 1e3) if t > 0 else None
+            peak, unit = 2 * lane_ops / 1e12, "TFLOP/s"
+        else:
+            ach = (work / 1e12) / (t / 1e3) if t > 0 else None
+            peak, unit = lane_ops / 1e12, "Tops/s"
+        kernels[st_name] = {"kernel": kname, "bound": bound, "launches": launches, "ms": t,
+                            "algorithmic_work": work, "achieved": ach, "peak": peak, "unit": unit,
+                            "frac": ach / peak if (ach and peak) else None}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
-    traffic = committed_traffic(d["kernel"])
-    roofline = {"kernel": d["kernel"], "stage": dom, "bound": "hbm", "achieved": d["achieved_gbs"],
-                "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": d["frac"],
-                "traffic": traffic, "peak_kind": f"{peaks_kind} copy bandwidth",
-                "algorithmic_bytes_per_launch": d["algorithmic_bytes"] / d["launches"],
+    roofline = {"kernel": d["kernel"], "stage": dom, "bound": d["bound"], "achieved": d["achieved"],
+                "peak": d["peak"], "unit": d["unit"], "frac": d["frac"],
+                "traffic": committed_traffic(d["kernel"]),
+                "peak_kind": (f"{peaks_kind} copy bandwidth" if d["bound"] == "hbm" else
+                              f"derived: {sms} SMs x 128 FP32 lanes x {NOMINAL_SM_MAX_MHZ} MHz"
+                              + (" x 2 (FMA)" if d["unit"] == "TFLOP/s" else "")),
+                "algorithmic_work_per_launch": d["algorithmic_work"] / d["launches"],
                 "launches": d["launches"], "share_of_step": d["ms"] / ms_per_step if ms_per_step else None,
                 "largest_stage": max(stage_ms, key=stage_ms.get)}
     # FP64 utilisation of the narrow phase

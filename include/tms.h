@@ -232,6 +232,7 @@ typedef struct {
     int retries;            /* capacity retries taken */
     int kernels;            /* kernel launches in one search (graph replay) */
     int pad;
+    long long fp32_solves;  /* triangle pairs through the verified FP32 solve */
 } tms_stats;
 
 tms_status tms_last_stats(void *stream, tms_stats *out);

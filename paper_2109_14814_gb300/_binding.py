@@ -65,6 +65,7 @@ class Stats(ctypes.Structure):
         ("retries", _c.c_int),
         ("kernels", _c.c_int),
         ("pad", _c.c_int),
+        ("fp32_solves", _c.c_longlong),
     ]
 
     def as_dict(self):

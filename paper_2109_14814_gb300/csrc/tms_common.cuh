@@ -102,6 +102,7 @@ struct Counters {
     unsigned long long tiles;
     unsigned long long cand;
     unsigned long long fp64;
+    unsigned long long fp32;       // triangle pairs through the verified FP32 solve
     unsigned long long raw_hits;
     unsigned long long out;
     unsigned int status;

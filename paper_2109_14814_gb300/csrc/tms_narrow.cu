@@ -377,6 +377,7 @@ __global__ void __launch_bounds__(256) k_narrow_filter(NarrowArgs a) {
     const unsigned long long n = a.ctr->cand;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
+    unsigned long long nsolved = 0;   // pairs through the FP32 solve, per warp
     for (unsigned long long g0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x - lane;
          g0 < n; g0 += stride) {
         const unsigned long long g = g0 + lane;
@@ -399,24 +400,26 @@ __global__ void __launch_bounds__(256) k_narrow_filter(NarrowArgs a) {
             uint32_t ta, tb;
             if (FACE == 0) { ta = cd.faceA; tb = cd.faceB; }
             else { ta = 2 * cd.faceA + (sub & 1); tb = 2 * cd.faceB + (sub >> 1); }
-            bool keep = false;
+            bool keep = false, solved = false;
             if (valid) {
                 if (a.fp32_filter) {
                     float4 X[3][2], Y[3][2];
                     if (FACE == 0) {
                         gather_split(ma, ta, X);
                         gather_split(mb, tb, Y);
-                        keep = !fp32_verified_reject(X, Y, a.tau);
+                        solved = true;
                     } else {
                         quad_tri(QA, sub & 1, X);
                         quad_tri(QB, sub >> 1, Y);
                         // the two triangles' boxes first: disjoint boxes, no intersection
-                        keep = split_boxes_overlap(X, Y) && !fp32_verified_reject(X, Y, a.tau);
+                        solved = split_boxes_overlap(X, Y);
                     }
+                    keep = solved && !fp32_verified_reject(X, Y, a.tau);
                 } else {
                     keep = true;
                 }
             }
+            nsolved += __popc(__ballot_sync(FULL, solved));
             const unsigned long long pos = warp_append(&a.ctr->fp64, keep, FULL);
             if (keep && pos < a.surv_cap) {
                 Cand s;
@@ -428,6 +431,7 @@ __global__ void __launch_bounds__(256) k_narrow_filter(NarrowArgs a) {
             }
         }
     }
+    if (lane == 0 && nsolved) atomicAdd(&a.ctr->fp32, nsolved);
 }
 
 // Stage 2: the FP64 solve for the survivors
