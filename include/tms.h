@@ -98,7 +98,7 @@ typedef struct {
     int moller;           /* 1 = apply the Moller quick test of Sec. 6.2.3 (FP64,
                              with a rounding guard) to candidates; default 0. */
     int cell_filter;      /* 1 = register only faces in grid cells occupied by
-                             both meshes before the sort (default); 0 = emit
+                             both meshes before grouping (default); 0 = emit
                              every face-cell incidence (the paper's per-box lists). */
     int narrow_filter;    /* 1 = reject candidates with an FP32 solve whose
                              forward-error bound certifies margin < -2 tau
