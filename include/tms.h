@@ -114,9 +114,11 @@ typedef struct {
     unsigned inject;      /* fault injection for tests (host side):
                              bit0 = force entry capacity 1 (exercises retry),
                              bit1 = force a capacity error to be returned,
-                             bit2 = report TMS_ERR_TIMEOUT from the status word */
-    int block_faces;      /* face-pass tile width in quads (64/128/256; 0 = 128) */
-    int tile_rows;        /* face-pass tile height in quad rows (4 or 8; 0 = 8) */
+                             bit2 = report TMS_ERR_TIMEOUT from the status word,
+                             bit3 = start the cell table at 1024 slots (exercises
+                             its growth) */
+    int block_faces;      /* bounds-pass tile width in quads (64/128/256; 0 = 128) */
+    int tile_rows;        /* bounds-pass tile height in quad rows (4 or 8; 0 = 4) */
     int timing;           /* 1 = record CUDA events between stages (in the graph) so
                              that tms_last_stage_ms() reports per-stage device time */
 } tms_params;
@@ -195,15 +197,15 @@ tms_status tms_backward(tms_mesh A, tms_mesh B, const tms_hit *dHits, long long 
 /*
  * tms_autotune -- picks, for these meshes, the search parameters the paper
  * leaves to the implementation (Sec. 6.2.1 grid cell size; Sec. 6.3 launch
- * shape): face level (quads or triangles), cell_mult in {1.0625, 1.5, 2.5} and
- * block_faces in {64, 128, 256}, by timing each of the 18 settings (one warm-up
- * and three timed runs, median) with tms_search (nPairs == 1) or
+ * shape): face level (quads or triangles), cell_mult in {1.0625, 1.5, 2.5},
+ * block_faces in {64, 128} and tile_rows in {4, 8}, by timing each of the 24
+ * settings (one warm-up and three timed runs, median) with tms_search (nPairs == 1) or
  * tms_search_batched (nPairs > 1) on `stream`.  The other fields (precision,
  * filters, tau, capacities, use_graph) come from `base` (NULL = defaults) and
  * are kept.  Results are unchanged by the choice: every setting finds the same
  * hits.
  *   A, B       : nPairs mesh handles each (host arrays).
- *   best       : host out, `base` with the three fields set to the fastest.
+ *   best       : host out, `base` with the four fields set to the fastest.
  *   cache_path : text file, or NULL for no cache.  A line per tuned key
  *                "<device>|pairs=..|sizes=<hash of every N,M>|prec=..|... fl cm bf tr ms";
  *                a matching line is returned without timing anything; a new
@@ -220,7 +222,7 @@ tms_status tms_autotune(const tms_mesh *A, const tms_mesh *B, int nPairs,
 
 /* Per-stage statistics of the last search on `stream` (host copies). */
 typedef struct {
-    long long entries;      /* face-cell entries sorted */
+    long long entries;      /* face-cell entries (grouped by cell) */
     long long cells;        /* occupied cells holding both meshes */
     long long pair_slots;   /* sum over cells of nA*nB */
     long long candidates;   /* candidate face pairs after box and owner tests */

@@ -86,10 +86,10 @@ struct Plan {
     unsigned long long ent_cap = 0, cand_cap = 0, hit_cap = 0;
     uint64_t *ek = nullptr;
     uint32_t *ev = nullptr, *eslot = nullptr, *erank = nullptr, *grouped = nullptr;
-    unsigned long long tsize = 0;
-    unsigned long long *tkey = nullptr, *occ_n = nullptr, *ckey = nullptr;
+    unsigned long long tsize = 0, tsize_min = 0;
+    unsigned long long *tkey = nullptr, *ckey = nullptr;
     uint2 *tcnt = nullptr;
-    uint32_t *tcell = nullptr, *occ = nullptr;
+    uint32_t *tcell = nullptr;
     void *sort_scratch = nullptr;
     unsigned long long *partials = nullptr;
     uint32_t *cstart = nullptr, *cb = nullptr;
@@ -117,13 +117,13 @@ struct Plan {
     unsigned long long last_use = 0;
 
     void free_scratch() {
-        void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, occ_n, ckey, tcnt, tcell, occ,
+        void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, ckey, tcnt, tcell,
                         sort_scratch, cstart, cb, toff, cand, surv, hits, hk, hk2, okeys, hv, hv2,
                         keep, kscan};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         bmA = bmH = nullptr; ek = nullptr; ev = eslot = erank = grouped = nullptr;
-        tkey = occ_n = ckey = nullptr; tcnt = nullptr; tcell = occ = nullptr;
+        tkey = ckey = nullptr; tcnt = nullptr; tcell = nullptr;
         sort_scratch = nullptr; cstart = cb = nullptr; toff = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
         hv = hv2 = keep = kscan = nullptr;
         if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
@@ -153,18 +153,17 @@ struct Plan {
         TMS_CK(dalloc(&eslot, ent_cap));
         TMS_CK(dalloc(&erank, ent_cap));
         TMS_CK(dalloc(&grouped, ent_cap));
-        // cell table: a power of two at least the entry capacity, so that every
-        // distinct cell finds a slot; all slots free (zero)
+        // cell table: a power of two, all slots free (zero); distinct cells are
+        // far fewer than entries, so it starts at an eighth of the entry
+        // capacity (L2-resident) and grows when a search finds it crowded
         tsize = 1024;
-        while (tsize < ent_cap) tsize <<= 1;
+        const unsigned long long want = (prm.inject & 8u) ? 0 : ent_cap / 8;
+        while (tsize < want || tsize < tsize_min) tsize <<= 1;
         TMS_CK(dalloc(&tkey, tsize));
         TMS_CK(dalloc(&tcnt, tsize));
         TMS_CK(dalloc(&tcell, tsize));
-        TMS_CK(dalloc(&occ, tsize));
-        TMS_CK(dalloc(&occ_n, 1));
         TMS_CK(cudaMemset(tkey, 0, tsize * sizeof(unsigned long long)));
         TMS_CK(cudaMemset(tcnt, 0, tsize * sizeof(uint2)));
-        TMS_CK(cudaMemset(occ_n, 0, sizeof(unsigned long long)));
         TMS_CK(dalloc(&ckey, ent_cap));
         TMS_CK(dalloc(&cstart, ent_cap));
         TMS_CK(dalloc(&cb, ent_cap));
@@ -207,11 +206,9 @@ struct Plan {
         ga.ent_key = ek; ga.ent_face = ev; ga.d_n = &d_ctr->entries; ga.cap = ent_cap;
         ga.ent_slot = eslot; ga.ent_rank = erank;
         ga.tkey = tkey; ga.tcnt = tcnt; ga.tcell = tcell; ga.tsize = tsize;
-        ga.occ = occ; ga.occ_n = occ_n;
         ga.cell_key = ckey; ga.cell_start = cstart; ga.cell_b = cb; ga.tile_off = toff;
         ga.grouped = grouped; ga.partials = partials; ga.ctr = d_ctr;
-        launch_table_clear(ga, grid, s);   // the cells the previous search claimed
-        kernels += 2;
+        kernels += 1;
         mark(1, s);
 
         FacePassArgs fa;
@@ -413,7 +410,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     for (int i = 0; i < nPairs; ++i) P->ids.push_back(A[i]->id);
     for (int i = 0; i < nPairs; ++i) P->ids.push_back(B[i]->id);
     const int block = (prm.block_faces == 64 || prm.block_faces == 256) ? prm.block_faces : 128;
-    const int rows = prm.tile_rows == 4 ? 4 : 8;
+    const int rows = prm.tile_rows == 8 ? 8 : 4;
     P->prm.tile_rows = rows;
 
     std::vector<MeshDev> meshes;
@@ -485,7 +482,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     TMS_PCK(dalloc(&P->d_bounds, meshes.size()));
     TMS_PCK(dalloc(&P->d_grids, pairs.size()));
     TMS_PCK(dalloc(&P->d_ctr, 1));
-    TMS_PCK(dalloc(&P->partials, 4 * 1024));
+    TMS_PCK(dalloc(&P->partials, 5 * 1024));
     TMS_PCK(cudaMallocHost((void **)&P->h_ctr, sizeof(Counters)));
     TMS_PCK(cudaMallocHost((void **)&P->h_grid0, sizeof(Grid)));
     TMS_PCK(cudaMemcpy(P->d_meshes, meshes.data(), meshes.size() * sizeof(MeshDev), cudaMemcpyHostToDevice));
@@ -526,7 +523,7 @@ Plan *find_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms_para
             P->dOffsets != dOffsets || P->nPairs != nPairs)
             continue;
         tms_params q = prm;
-        q.tile_rows = q.tile_rows == 4 ? 4 : 8;
+        q.tile_rows = q.tile_rows == 8 ? 8 : 4;
         if (!same_params(P->prm, q)) continue;
         bool ok = true;
         for (int i = 0; i < nPairs && ok; ++i) ok = P->ids[i] == A[i]->id && P->ids[nPairs + i] == B[i]->id;
@@ -595,12 +592,12 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
             g_err = "a device-side wait gave up (sort look-back)";
             return TMS_ERR_TIMEOUT;
         }
-        if (c.status & ST_TABLE_FULL) {
-            g_err = "cell table full";
-            return TMS_ERR_STATE;
-        }
         bool grow = false;
-        if (c.entries > P->ent_cap) {
+        if ((c.status & ST_TABLE_FULL) || c.claimed > P->tsize / 2) {
+            P->tsize_min = P->tsize * 4;
+            grow = true;
+        }
+        if (!grow && c.entries > P->ent_cap) {
             P->ent_cap = std::min<unsigned long long>(0x7fffffffULL, c.entries + c.entries / 4 + 1024);
             P->bmH_bits = std::min(25, std::max(11, ceil_log2(P->ent_cap * 8) - 5));
             P->cand_cap = std::max(P->cand_cap, 2 * P->ent_cap);
@@ -625,6 +622,11 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
         if (s != TMS_OK) return s;
     }
     const Counters &c = *P->h_ctr;
+    if (c.status & ST_TABLE_FULL) {
+        g_err = "cell table still full after retries";
+        *nHits = (long long)c.out;
+        return TMS_ERR_CAPACITY;
+    }
     tms_stats st;
     memset(&st, 0, sizeof(st));
     st.entries = (long long)c.entries;
@@ -683,7 +685,7 @@ void tms_params_default(tms_params *p) {
     p->tau = 1e-12;
     p->use_graph = 1;
     p->block_faces = 128;
-    p->tile_rows = 8;
+    p->tile_rows = 4;
 }
 
 const char *tms_status_str(tms_status s) {

@@ -103,6 +103,7 @@ struct Counters {
     unsigned long long cand;
     unsigned long long fp64;
     unsigned long long fp32;       // triangle pairs through the verified FP32 solve
+    unsigned long long claimed;    // cell-table slots claimed by this search
     unsigned long long raw_hits;
     unsigned long long out;
     unsigned int status;
@@ -383,23 +384,20 @@ struct GroupArgs {
     unsigned long long *tkey;      // [tsize] (pair << 31 | cell) + 1, or kHashEmpty
     uint2 *tcnt;                   // [tsize] A and B entry counts
     uint32_t *tcell;               // [tsize] compacted cell index or kNoCell
-    unsigned long long tsize;      // power of two >= cap
-    uint32_t *occ;                 // [tsize] slots claimed by this search
-    unsigned long long *occ_n;     // their number (cleared with the slots)
+    unsigned long long tsize;      // power of two; grown by the host when over half full
     // per compacted cell, [cap]
     unsigned long long *cell_key;
     uint32_t *cell_start;          // first A entry in `grouped`
     uint32_t *cell_b;              // first B entry
     unsigned long long *tile_off;  // exclusive scan of the 32 x 32 tiles of nA x nB
     uint32_t *grouped;             // [cap] face ids by cell, A then B
-    unsigned long long *partials;  // [4 * 1024]
+    unsigned long long *partials;  // [5 * 1024]
     Counters *ctr;
 };
-// table counts and ranks (1 launch), then the cells and the scatter (4 launches)
+// table counts and ranks (1 launch), then the cells and the scatter (4 launches);
+// the table is left with every slot free
 void launch_group_count(const GroupArgs &a, int grid, cudaStream_t st);
 void launch_group_cells(const GroupArgs &a, int grid, cudaStream_t st);
-// returns the slots claimed by the previous search to the free state
-void launch_table_clear(const GroupArgs &a, int grid, cudaStream_t st);
 
 struct EmitArgs {
     const unsigned long long *cell_key;   // pair << 31 | cell

@@ -565,7 +565,7 @@ __global__ void k_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, G
     for (int iter = 0; iter < 64; ++iter) {
         double prod = (double)n[0] * n[1] * n[2] * n[3];
         if (prod <= cap) break;
-        double f = pow(prod / cap, 0.25) * 1.001;
+        double f = sqrt(sqrt(prod / cap)) * 1.001;
         for (int d = 0; d < 4; ++d) {
             if (n[d] <= 1) continue;
             step[d] *= f;

@@ -10,15 +10,18 @@
 //                    open-addressing table (linear probing), and one atomic per
 //                    group of equal keys in a warp gives every entry its rank
 //                    within (cell, role) and the cell its A and B counts;
-//   k_cells_*        scan the claimed slots (three launches: per-block sums,
-//                    one block over the sums, per-slot offsets): cells holding
+//   k_cells_*        scan the whole table (three launches: per-block sums, one
+//                    block over the sums, per-slot offsets): cells holding
 //                    faces of both meshes get consecutive indices, their
 //                    entries' start, their first B entry and their 32 x 32 tile
-//                    offset; the totals go to the counters;
+//                    offset; the totals go to the counters; every slot read is
+//                    returned to the free state;
 //   k_group_scatter  writes every entry's face id to its cell's A or B list.
 // The order of a cell's entries is left to the atomics; the search's output
-// does not depend on it.  Only the slots a search claimed are returned to the
-// free state, by k_table_clear at the start of the next search.
+// does not depend on it.  The table is sized from the entry capacity (an
+// eighth of it, so that it stays in L2 and a scan of all of it is cheap); a
+// search that finds it over half full, or full, is run again with a table four
+// times larger.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,8 +36,7 @@ constexpr int kGroupBlock = 256;
 constexpr int kCellScanBlock = 512;
 constexpr int kTileEdge = 32;
 
-// the table slot of stored key k (never kHashEmpty), claimed if new (the
-// claimer records it in occ)
+// the table slot of stored key k (never kHashEmpty), claimed if new
 __device__ __forceinline__ uint32_t table_slot(const GroupArgs &a, unsigned long long k) {
     const unsigned long long mask = a.tsize - 1;
     unsigned long long h = mix64(k) & mask;
@@ -43,16 +45,11 @@ __device__ __forceinline__ uint32_t table_slot(const GroupArgs &a, unsigned long
         if (cur == k) return (uint32_t)h;
         if (cur == kHashEmpty) {
             cur = atomicCAS(a.tkey + h, kHashEmpty, k);
-            if (cur == kHashEmpty) {
-                const unsigned long long pos = atomicAdd(a.occ_n, 1ULL);
-                if (pos < a.tsize) a.occ[pos] = (uint32_t)h;
-                return (uint32_t)h;
-            }
-            if (cur == k) return (uint32_t)h;
+            if (cur == kHashEmpty || cur == k) return (uint32_t)h;
         }
         h = (h + 1) & mask;
     }
-    // unreachable while the table has at least as many slots as entries
+    // every slot taken: the host grows the table and runs the search again
     atomicOr(&a.ctr->status, ST_TABLE_FULL);
     return 0;
 }
@@ -87,12 +84,13 @@ __global__ void __launch_bounds__(kGroupBlock) k_group_count(GroupArgs a) {
 }
 
 struct CellVals {
-    unsigned long long both, size, tiles, pairs;
+    unsigned long long both, size, tiles, pairs, claimed;
 };
 
-__device__ __forceinline__ CellVals cell_vals(const GroupArgs &a, uint32_t slot) {
+__device__ __forceinline__ CellVals cell_vals(const GroupArgs &a, unsigned long long slot) {
     const uint2 c = a.tcnt[slot];
     CellVals v;
+    v.claimed = (c.x | c.y) ? 1 : 0;
     const bool both = c.x > 0 && c.y > 0;
     v.both = both ? 1 : 0;
     v.size = both ? (unsigned long long)c.x + c.y : 0;
@@ -101,7 +99,7 @@ __device__ __forceinline__ CellVals cell_vals(const GroupArgs &a, uint32_t slot)
     return v;
 }
 
-__device__ __forceinline__ void occ_chunk(unsigned long long n, unsigned long long &b,
+__device__ __forceinline__ void slot_chunk(unsigned long long n, unsigned long long &b,
                                           unsigned long long &e) {
     unsigned long long per = (n + gridDim.x - 1) / gridDim.x;
     per = (per + 31) & ~31ULL;
@@ -111,30 +109,24 @@ __device__ __forceinline__ void occ_chunk(unsigned long long n, unsigned long lo
     if (e > n) e = n;
 }
 
-__device__ __forceinline__ unsigned long long claimed(const GroupArgs &a) {
-    const unsigned long long n = *a.occ_n;
-    return n < a.tsize ? n : a.tsize;
-}
-
 __global__ void __launch_bounds__(kCellScanBlock) k_cells_reduce(GroupArgs a) {
-    __shared__ unsigned long long red[4][kCellScanBlock / 32];
+    __shared__ unsigned long long red[5][kCellScanBlock / 32];
     if (a.ctr->entries > a.cap) return;
-    const unsigned long long n = claimed(a);
     unsigned long long b, e;
-    occ_chunk(n, b, e);
-    unsigned long long s[4] = {0, 0, 0, 0};
+    slot_chunk(a.tsize, b, e);
+    unsigned long long s[5] = {0, 0, 0, 0, 0};
     for (unsigned long long j = b + threadIdx.x; j < e; j += blockDim.x) {
-        const CellVals v = cell_vals(a, a.occ[j]);
-        s[0] += v.both; s[1] += v.size; s[2] += v.tiles; s[3] += v.pairs;
+        const CellVals v = cell_vals(a, j);
+        s[0] += v.both; s[1] += v.size; s[2] += v.tiles; s[3] += v.pairs; s[4] += v.claimed;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         for (int off = 16; off > 0; off >>= 1) s[k] += __shfl_xor_sync(FULL, s[k], off);
         if (lane == 0) red[k][warp] = s[k];
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < 5) {
         unsigned long long t = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
         a.partials[threadIdx.x * gridDim.x + blockIdx.x] = t;
@@ -145,7 +137,7 @@ __global__ void __launch_bounds__(kCellScanBlock) k_cells_reduce(GroupArgs a) {
 __global__ void __launch_bounds__(1024) k_cells_partials(GroupArgs a, int g) {
     __shared__ unsigned long long p[1024];
     if (a.ctr->entries > a.cap) return;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         const unsigned long long x = threadIdx.x < g ? a.partials[k * g + threadIdx.x] : 0;
         p[threadIdx.x] = x;
         __syncthreads();
@@ -161,7 +153,8 @@ __global__ void __launch_bounds__(1024) k_cells_partials(GroupArgs a, int g) {
             if (k == 0) a.ctr->cells = tot;
             else if (k == 1) a.ctr->grouped = tot;
             else if (k == 2) a.ctr->tiles = tot;
-            else a.ctr->pair_slots = tot;
+            else if (k == 3) a.ctr->pair_slots = tot;
+            else a.ctr->claimed = tot;   // the host grows a crowded table
         }
         __syncthreads();
     }
@@ -171,20 +164,16 @@ __global__ void __launch_bounds__(kCellScanBlock) k_cells_down(GroupArgs a) {
     __shared__ unsigned long long wsum[3][kCellScanBlock / 32];
     __shared__ unsigned long long carry[3];
     if (a.ctr->entries > a.cap) return;
-    const unsigned long long n = claimed(a);
     unsigned long long b, e;
-    occ_chunk(n, b, e);
+    slot_chunk(a.tsize, b, e);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < 3) carry[threadIdx.x] = a.partials[threadIdx.x * gridDim.x + blockIdx.x];
     __syncthreads();
     for (unsigned long long base = b; base < e; base += blockDim.x) {
         const unsigned long long j = base + threadIdx.x;
-        uint32_t slot = 0;
-        CellVals v = {0, 0, 0, 0};
-        if (j < e) {
-            slot = a.occ[j];
-            v = cell_vals(a, slot);
-        }
+        const unsigned long long slot = j;
+        CellVals v = {0, 0, 0, 0, 0};
+        if (j < e) v = cell_vals(a, slot);
         unsigned long long x[3] = {v.both, v.size, v.tiles}, incl[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -212,7 +201,7 @@ __global__ void __launch_bounds__(kCellScanBlock) k_cells_down(GroupArgs a) {
         unsigned long long ex[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) ex[k] = carry[k] + wsum[k][warp] + incl[k] - x[k];
-        if (j < e) {
+        if (j < e && v.claimed) {
             if (v.both) {
                 const unsigned long long c = ex[0];
                 const uint2 cnt = a.tcnt[slot];
@@ -224,6 +213,9 @@ __global__ void __launch_bounds__(kCellScanBlock) k_cells_down(GroupArgs a) {
             } else {
                 a.tcell[slot] = kNoCell;
             }
+            // the slot is free again for the next search (the scatter reads tcell only)
+            a.tkey[slot] = kHashEmpty;
+            a.tcnt[slot] = make_uint2(0u, 0u);
         }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) {
@@ -249,21 +241,17 @@ __global__ void __launch_bounds__(kGroupBlock) k_group_scatter(GroupArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(kGroupBlock) k_table_clear(GroupArgs a) {
-    const unsigned long long n = claimed(a);
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
-         j += stride) {
-        const uint32_t s = a.occ[j];
-        a.tkey[s] = kHashEmpty;
-        a.tcnt[s] = make_uint2(0u, 0u);
-    }
-}
-
 }  // namespace
 
+// one lane per entry slot: no warp walks a chain of dependent table lookups
+static int entry_grid(const GroupArgs &a) {
+    const unsigned long long b = (a.cap + kGroupBlock - 1) / kGroupBlock;
+    return (int)(b < 1 ? 1 : (b > (1ULL << 30) ? (1ULL << 30) : b));
+}
+
 void launch_group_count(const GroupArgs &a, int grid, cudaStream_t st) {
-    k_group_count<<<grid, kGroupBlock, 0, st>>>(a);
+    (void)grid;
+    k_group_count<<<entry_grid(a), kGroupBlock, 0, st>>>(a);
 }
 
 void launch_group_cells(const GroupArgs &a, int grid, cudaStream_t st) {
@@ -271,12 +259,7 @@ void launch_group_cells(const GroupArgs &a, int grid, cudaStream_t st) {
     k_cells_reduce<<<g, kCellScanBlock, 0, st>>>(a);
     k_cells_partials<<<1, 1024, 0, st>>>(a, g);
     k_cells_down<<<g, kCellScanBlock, 0, st>>>(a);
-    k_group_scatter<<<grid, kGroupBlock, 0, st>>>(a);
-}
-
-void launch_table_clear(const GroupArgs &a, int grid, cudaStream_t st) {
-    k_table_clear<<<grid, kGroupBlock, 0, st>>>(a);
-    cudaMemsetAsync(a.occ_n, 0, sizeof(unsigned long long), st);
+    k_group_scatter<<<entry_grid(a), kGroupBlock, 0, st>>>(a);
 }
 
 }  // namespace tms

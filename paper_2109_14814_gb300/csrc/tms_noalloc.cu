@@ -85,9 +85,9 @@ struct Buffers {
     uint32_t *bmA, *bmH;
     uint64_t *ek;
     uint32_t *ev, *eslot, *erank, *grouped;
-    unsigned long long *tkey, *occ_n, *ckey;
+    unsigned long long *tkey, *ckey;
     uint2 *tcnt;
-    uint32_t *tcell, *occ;
+    uint32_t *tcell;
     void *sort_scratch;
     uint32_t *cstart, *cb;
     unsigned long long *toff;
@@ -98,8 +98,8 @@ struct Buffers {
 };
 
 // the arena's layout; also used to check, at set-up, that it fits.  Buffers
-// live across the whole search (and the cell table with the list of slots a
-// call claimed, which the next call frees) come first; then the broad phase's
+// live across the whole search (and the cell table, which every call leaves
+// with all slots free) come first; then the broad phase's
 // buffers, and over the same bytes the narrow phase's and the merge's, which
 // are written only after candidate emission, the broad phase's last reader,
 // has run on the same stream.  The array starts zeroed: every table slot free.
@@ -109,15 +109,13 @@ size_t carve(unsigned char *base, Buffers &b) {
     b.bounds = c.take<Bounds>(2);
     b.grids = c.take<Grid>(1);
     b.ctr = c.take<Counters>(1);
-    b.partials = c.take<unsigned long long>(4 * kMaxGrid);
+    b.partials = c.take<unsigned long long>(5 * kMaxGrid);
     b.split[0] = c.take<float4>(2 * kMaxViewVertices);
     b.split[1] = c.take<float4>(2 * kMaxViewVertices);
     b.sort_scratch = c.take<unsigned char>(radix_scratch_size(kRawHitCap, 2 * kMaxTriBits));
     b.cand = c.take<Cand>(kCandCap);
     b.tkey = c.take<unsigned long long>(kTableSize);
     b.tcnt = c.take<uint2>(kTableSize);
-    b.occ = c.take<uint32_t>(kTableSize);
-    b.occ_n = c.take<unsigned long long>(1);
     const size_t phase = c.off;
     // broad phase: face boxes (two per quad, FP64 at most), bitmaps, entries, cells
     b.fbox[0] = c.take<unsigned char>(2 * kMaxViewVertices * 64);
@@ -220,7 +218,7 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
 
     // small tables, from host memory on the stack
     const int block = (p.block_faces == 64 || p.block_faces == 256) ? p.block_faces : 128;
-    const int rows = p.tile_rows == 4 ? 4 : 8;
+    const int rows = p.tile_rows == 8 ? 8 : 4;
     Tables t;
     memset(&t, 0, sizeof(t));
     ma.split = b.split[0];
@@ -266,10 +264,8 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     ga.ent_key = b.ek; ga.ent_face = b.ev; ga.d_n = &b.ctr->entries; ga.cap = kEntCap;
     ga.ent_slot = b.eslot; ga.ent_rank = b.erank;
     ga.tkey = b.tkey; ga.tcnt = b.tcnt; ga.tcell = b.tcell; ga.tsize = kTableSize;
-    ga.occ = b.occ; ga.occ_n = b.occ_n;
     ga.cell_key = b.ckey; ga.cell_start = b.cstart; ga.cell_b = b.cb; ga.tile_off = b.toff;
     ga.grouped = b.grouped; ga.partials = b.partials; ga.ctr = b.ctr;
-    launch_table_clear(ga, grid, s);
     FacePassArgs fa;
     memset(&fa, 0, sizeof(fa));
     fa.meshes = b.tables->meshes;

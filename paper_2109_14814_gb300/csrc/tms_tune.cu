@@ -1,5 +1,5 @@
 // Autotuner: picks the face level (triangle or quad boxes), the grid cell size
-// (cell_mult) and the face-pass tile width for a search or a batch of searches
+// (cell_mult) and the bounds-pass tile shape for a search or a batch of searches
 // by timing each candidate on the caller's meshes, and caches the choice in a
 // text file keyed by the device name and the meshes' sizes.  Used to set up a
 // sweep (the batched continuation search of many pairs replays one tuned plan).
@@ -127,17 +127,19 @@ extern "C" tms_status tms_autotune(const tms_mesh *A, const tms_mesh *B, int nPa
     cudaEventCreate(&e1);
     const int face_levels[2] = {1, 0};
     const float mults[3] = {1.0625f, 1.5f, 2.5f};
-    const int blocks[3] = {128, 64, 256};
+    const int blocks[2] = {128, 64};
+    const int rows[2] = {4, 8};
     double bestt = 1e300;
     tms_params bp = p0;
     for (int fl : face_levels)
         for (float cm : mults)
-            for (int bf : blocks) {
+            for (int bf : blocks)
+            for (int tr : rows) {
                 tms_params p = p0;
                 p.face_level = fl;
                 p.cell_mult = cm;
                 p.block_faces = bf;
-                p.tile_rows = 8;
+                p.tile_rows = tr;
                 if (run(p) != TMS_OK) continue;   // warm-up: plan, capture, growth
                 std::vector<float> ts;
                 for (int r = 0; r < 3; ++r) {

@@ -220,6 +220,11 @@ def test_capacity_retry_and_injected_errors():
     h = gpu_records(tms.search(A, B, inject=1))
     assert list(zip(h["triA"], h["triB"])) == list(zip(base["triA"], base["triB"]))
     assert tms.last_stats()["retries"] >= 1
+    # a cell table started at 1024 slots: grown (x4 per retry) until under half full
+    h = gpu_records(tms.search(A, B, inject=8))
+    assert list(zip(h["triA"], h["triB"])) == list(zip(base["triA"], base["triB"]))
+    assert np.array_equal(h["z"], base["z"])
+    assert tms.last_stats()["retries"] >= 1
     # too-small output buffer: TMS_ERR_CAPACITY with the required count
     out = torch.empty((3, tms.HIT_BYTES), dtype=torch.uint8, device="cuda")
     with pytest.raises(tms.TmsError) as e:
