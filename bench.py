@@ -42,6 +42,11 @@ NOMINAL_SM_MAX_MHZ = 2070              # GB300 maximum SM clock
 # alpha = |I - C A| + |C| W (337), the residual bound (112), the error bound
 # (35) and the margin tests (22)
 FP32_SOLVE_FLOPS = 956
+# FP32 operations of the separating-axis prefilter with all four axes: five
+# split difference vectors with bounds (80), two offset vectors (16), two sets
+# of Plucker coordinates (56), det A with its error bound (46), the Frobenius
+# bound and kappa (70), the two dual choices (28), four interval tests (260)
+SAT_FLOPS = 551
 
 
 def dist_env():
@@ -227,11 +232,12 @@ def run_tms(args, ws, rank, local):
     # GPU (SMs x 128 lanes x the maximum SM clock; an FMA counts 2 FLOPs).
     # The slowest stage is reported as `roofline`.  V vertices and F faces per
     # mesh (quads), E face-cell entries, P proposed face pairs, C candidate
-    # quad pairs, S32 / S64 triangle pairs through the FP32 / FP64 solve.
+    # quad pairs, SAT triangle pairs through the separating-axis prefilter,
+    # S32 / S64 triangle pairs through the FP32 / FP64 solve.
     V = pair.A.N * pair.A.M
     F = pair.A.N * (pair.A.M - 1)
     E, C, S = stats["entries"], stats["candidates"], stats["fp64_solves"]
-    P, S32 = stats["pair_slots"], stats["fp32_solves"]
+    P, S32, SAT = stats["pair_slots"], stats["fp32_solves"], stats["sat_tests"]
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     sm_hz = float(NOMINAL_SM_MAX_MHZ) * 1e6
     lane_ops = sms * 128 * sm_hz                   # FP32 lane operations per second
@@ -249,8 +255,10 @@ def run_tms(args, ws, rank, local):
                         E * (4 + 8 + 4 + 4 + 4) + stats["cells"] * 24),
         # the box test of every proposed face pair: 8 FP32 compares
         "emit": ("tms::k_emit", "alu", 1, 8 * P),
-        # the verified FP32 solve: FP32_SOLVE_FLOPS per triangle pair
-        "narrow": ("tms::k_narrow_filter + k_narrow_fp64", "alu", 2, FP32_SOLVE_FLOPS * S32),
+        # the separating-axis prefilter per triangle pair whose boxes overlap, the
+        # verified FP32 solve for the pairs it cannot reject
+        "narrow": ("tms::k_narrow_filter + k_narrow_fp64", "alu", 2,
+                   SAT_FLOPS * SAT + FP32_SOLVE_FLOPS * S32),
     }
     stage_time = dict(stage_ms)
     stage_time["face_probe_B+A"] = stage_ms.get("face_probe_B", 0.0) + stage_ms.get("face_probe_A", 0.0)

@@ -235,6 +235,7 @@ typedef struct {
     int kernels;            /* kernel launches in one search (graph replay) */
     int pad;
     long long fp32_solves;  /* triangle pairs through the verified FP32 solve */
+    long long sat_tests;    /* triangle pairs through the separating-axis prefilter */
 } tms_stats;
 
 tms_status tms_last_stats(void *stream, tms_stats *out);

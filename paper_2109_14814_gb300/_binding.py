@@ -66,6 +66,7 @@ class Stats(ctypes.Structure):
         ("kernels", _c.c_int),
         ("pad", _c.c_int),
         ("fp32_solves", _c.c_longlong),
+        ("sat_tests", _c.c_longlong),
     ]
 
     def as_dict(self):

@@ -158,7 +158,7 @@ struct Plan {
         // capacity (L2-resident) and grows when a search finds it crowded
         tsize = 1024;
         const unsigned long long want = (prm.inject & 8u) ? 0 : ent_cap / 8;
-        while (tsize < want || tsize < tsize_min) tsize <<= 1;
+        while ((tsize < want || tsize < tsize_min) && tsize < (1ULL << 31)) tsize <<= 1;
         TMS_CK(dalloc(&tkey, tsize));
         TMS_CK(dalloc(&tcnt, tsize));
         TMS_CK(dalloc(&tcell, tsize));
@@ -635,6 +635,7 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
     st.candidates = (long long)c.cand;
     st.fp64_solves = (long long)c.fp64;
     st.fp32_solves = (long long)c.fp32;
+    st.sat_tests = (long long)c.sat;
     st.raw_hits = (long long)c.raw_hits;
     st.hits = (long long)c.out;
     for (int d = 0; d < 4; ++d) st.grid_n[d] = P->h_grid0->n[d];

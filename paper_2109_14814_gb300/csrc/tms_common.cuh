@@ -103,6 +103,7 @@ struct Counters {
     unsigned long long cand;
     unsigned long long fp64;
     unsigned long long fp32;       // triangle pairs through the verified FP32 solve
+    unsigned long long sat;        // triangle pairs through the separating-axis prefilter
     unsigned long long claimed;    // cell-table slots claimed by this search
     unsigned long long raw_hits;
     unsigned long long out;
@@ -379,7 +380,7 @@ struct GroupArgs {
     const uint32_t *ent_face;
     const unsigned long long *d_n; // entry count
     unsigned long long cap;        // entry capacity
-    uint32_t *ent_slot;            // [cap] table slot of each entry
+    uint32_t *ent_slot;            // [cap] table slot of each entry | role << 31
     uint32_t *ent_rank;            // [cap] rank within (cell, role)
     unsigned long long *tkey;      // [tsize] (pair << 31 | cell) + 1, or kHashEmpty
     uint2 *tcnt;                   // [tsize] A and B entry counts

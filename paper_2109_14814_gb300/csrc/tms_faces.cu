@@ -533,57 +533,55 @@ __global__ void k_bounds_init(Bounds *b, int n) {
 // per coordinate; capped so that a pair's grid has fewer than 2^31 cells.
 __global__ void k_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *grids,
                               float cell_mult) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_pairs) return;
+    // one warp per pair, lane d & 3 speaks for coordinate d: the FP64 chain of
+    // one coordinate instead of four (FP64 arithmetic is slow on GB300)
+    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= n_pairs) return;                      // whole warps
+    const int lane = threadIdx.x & 31, d = lane & 3;
     const Bounds &A = b[pairs[p].x];
     const Bounds &B = b[pairs[p].y];
-    Grid G;
-    memset(&G, 0, sizeof(G));
-    int empty = (A.faces == 0 || B.faces == 0) ? 1 : 0;
-    double o[4], e[4], step[4];
-    for (int d = 0; d < 4; ++d) {
-        o[d] = fmax(ord_dec(A.lo[d]), ord_dec(B.lo[d]));
-        e[d] = fmin(ord_dec(A.hi[d]), ord_dec(B.hi[d]));
-        if (!(o[d] <= e[d])) empty = 1;
-        double w = fmax(ord_dec(A.w[d]), ord_dec(B.w[d]));
-        step[d] = (double)cell_mult * w;
-    }
-    int n[4];
-    double range[4];
-    for (int d = 0; d < 4; ++d) {
-        range[d] = empty ? 0.0 : e[d] - o[d];
-        if (!(range[d] > 0.0) || !(step[d] > 0.0)) {
-            n[d] = 1;
-            step[d] = 0.0;
-            continue;
-        }
-        if (range[d] / step[d] > (double)(kMaxCellsPerDim - 1)) step[d] = range[d] / (double)(kMaxCellsPerDim - 1);
-        n[d] = (int)floor(range[d] / step[d]) + 1;
-        if (n[d] > kMaxCellsPerDim) n[d] = kMaxCellsPerDim;
+    const double o = fmax(ord_dec(A.lo[d]), ord_dec(B.lo[d]));
+    const double e = fmin(ord_dec(A.hi[d]), ord_dec(B.hi[d]));
+    const int empty = (A.faces == 0 || B.faces == 0 || __any_sync(FULL, !(o <= e))) ? 1 : 0;
+    double step = (double)cell_mult * fmax(ord_dec(A.w[d]), ord_dec(B.w[d]));
+    const double range = empty ? 0.0 : e - o;
+    int n;
+    if (!(range > 0.0) || !(step > 0.0)) {
+        n = 1;
+        step = 0.0;
+    } else {
+        if (range / step > (double)(kMaxCellsPerDim - 1)) step = range / (double)(kMaxCellsPerDim - 1);
+        n = (int)floor(range / step) + 1;
+        if (n > kMaxCellsPerDim) n = kMaxCellsPerDim;
     }
     const double cap = 2147483647.0;
     for (int iter = 0; iter < 64; ++iter) {
-        double prod = (double)n[0] * n[1] * n[2] * n[3];
-        if (prod <= cap) break;
-        double f = sqrt(sqrt(prod / cap)) * 1.001;
-        for (int d = 0; d < 4; ++d) {
-            if (n[d] <= 1) continue;
-            step[d] *= f;
-            n[d] = (int)floor(range[d] / step[d]) + 1;
-            if (n[d] < 1) n[d] = 1;
+        double prod = (double)n;
+        prod *= __shfl_xor_sync(FULL, prod, 1);
+        prod *= __shfl_xor_sync(FULL, prod, 2);
+        if (prod <= cap) break;                    // the same in every lane
+        const double f = sqrt(sqrt(prod / cap)) * 1.001;
+        if (n > 1) {
+            step *= f;
+            n = (int)floor(range / step) + 1;
+            if (n < 1) n = 1;
         }
     }
-    for (int d = 0; d < 4; ++d) {
-        G.o64[d] = o[d];
-        G.e64[d] = e[d];
-        G.inv64[d] = (step[d] > 0.0) ? 1.0 / step[d] : 0.0;
-        G.o32[d] = (float)o[d];
-        G.e32[d] = (float)e[d];
-        G.inv32[d] = (float)G.inv64[d];
-        G.n[d] = n[d];
+    if (lane < 4) {
+        Grid &G = grids[p];
+        const double inv = (step > 0.0) ? 1.0 / step : 0.0;
+        G.o64[d] = o;
+        G.e64[d] = e;
+        G.inv64[d] = inv;
+        G.o32[d] = (float)o;
+        G.e32[d] = (float)e;
+        G.inv32[d] = (float)inv;
+        G.n[d] = n;
+        if (d == 0) {
+            G.empty = empty;
+            G.pad[0] = G.pad[1] = G.pad[2] = 0;
+        }
     }
-    G.empty = empty;
-    grids[p] = G;
 }
 
 template <int PREC, int FACE, int TK>
@@ -651,7 +649,7 @@ void launch_bounds_init(Bounds *b, int n, cudaStream_t st) {
 
 void launch_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *g,
                         float cell_mult, cudaStream_t st) {
-    k_grid_params<<<(n_pairs + 127) / 128, 128, 0, st>>>(b, pairs, n_pairs, g, cell_mult);
+    k_grid_params<<<(n_pairs + 3) / 4, 128, 0, st>>>(b, pairs, n_pairs, g, cell_mult);
 }
 
 }  // namespace tms

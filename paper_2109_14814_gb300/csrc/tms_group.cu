@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(kGroupBlock) k_group_count(GroupArgs a) {
         slot = __shfl_sync(FULL, slot, leader);
         base = __shfl_sync(FULL, base, leader);
         if (ok) {
-            a.ent_slot[i] = slot;
+            // the role rides in the slot's top bit (slots are below 2^31)
+            a.ent_slot[i] = slot | ((uint32_t)(key & 1) << 31);
             a.ent_rank[i] = base + __popc(peers & lt);
         }
     }
@@ -232,10 +233,10 @@ __global__ void __launch_bounds__(kGroupBlock) k_group_scatter(GroupArgs a) {
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += stride) {
-        const uint32_t slot = a.ent_slot[i];
-        const uint32_t c = a.tcell[slot];
+        const uint32_t sr = a.ent_slot[i];
+        const uint32_t c = a.tcell[sr & 0x7FFFFFFFu];
         if (c == kNoCell) continue;
-        const uint32_t start = (a.ent_key[i] & 1) ? a.cell_b[c] : a.cell_start[c];
+        const uint32_t start = (sr >> 31) ? a.cell_b[c] : a.cell_start[c];
         const unsigned long long pos = (unsigned long long)start + a.ent_rank[i];
         if (pos < a.cap) a.grouped[pos] = a.ent_face[i];
     }

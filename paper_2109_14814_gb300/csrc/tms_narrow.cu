@@ -307,6 +307,184 @@ __device__ __forceinline__ bool fp32_verified_reject(const float4 X[3][2], const
     return isfinite(m) && isfinite(err) && (m < -allow);
 }
 
+// ---------------------------------------------------------------------------
+// Separating-axis prefilter: a certificate of non-intersection cheaper than the
+// verified solve, which it precedes.
+//
+// Lemma.  For any direction w let I_X = [min_i w.x_i, max_i w.x_i] (length D_X)
+// and I_Y likewise.  If the exact margin m >= -delta, the common point
+// P = sum_i beta_i x_i = sum_j gamma_j y_j has weights >= -delta summing to 1,
+// so w.P lies within 2 delta D_X of I_X and within 2 delta D_Y of I_Y; hence a
+// gap g > 2 delta (D_X + D_Y) between I_X and I_Y proves m < -delta.
+// delta = 2 tau + 8192 u64 kappa covers the FP64 solve's own error: with
+// kappa >= cond_2(A) (here kappa = |A|_F^4 / |det A|, since
+// sigma_4 >= |det A| / sigma_1^3), partial pivoting on a 4x4 system moves z by
+// at most about 1536 u64 kappa |z|_inf; if |z|_inf <= 2 that is below delta - tau,
+// and if |z|_inf = L > 2 the exact margin is at most -(L - 1) / 2, which such
+// an error cannot lift to -tau while kappa <= 1e10 (checked).
+// Directions: for each triangle the two longest of the four vectors orthogonal
+// to its plane (the duals of e1 ^ e2 ^ axis_k, read off the plane's Plucker
+// coordinates m_ij = e1_i e2_j - e1_j e2_i); any direction is valid, these
+// make the triangle's own interval almost a point.  det A is the pairing of
+// the two planes' Plucker coordinates.  Every FP32 value carries a bound on its
+// rounding and on the error of the split inputs, so the test is rigorous for
+// the FP64 vertices.
+// ---------------------------------------------------------------------------
+struct SplitVec {
+    float v[4];
+    float E;       // |v_c - exact_c| <= E for every c
+    float M;       // max_c |v_c|
+};
+
+// p - q of split vertices: t1 = hp - hq, t2 = lp - lq, v = t1 + t2 with
+// |v - exact| <= 2u(1+u)|t1| + 3u^2 (|hp| + |hq|) (the split remainders and the
+// three roundings; |t2| <= u (1+u)^2 (|hp| + |hq|)), evaluated with margin
+__device__ __forceinline__ SplitVec split_vec(const float4 P[2], const float4 Q[2]) {
+    const float u = 5.9604645e-08f;
+    SplitVec r;
+    float t1m = 0.0f, hm = 0.0f, vm = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float hp = comp(P[0], c), lp = comp(P[1], c), hq = comp(Q[0], c), lq = comp(Q[1], c);
+        const float t1 = hp - hq, t2 = lp - lq;
+        r.v[c] = t1 + t2;
+        t1m = fmaxf(t1m, fabsf(t1));
+        hm = fmaxf(hm, fabsf(hp) + fabsf(hq));
+        vm = fmaxf(vm, fabsf(r.v[c]));
+    }
+    r.E = (2.001f * u) * t1m + (3.01f * u * u) * hm + 2e-29f;
+    r.M = vm;
+    return r;
+}
+
+// a + b of two vectors with bounds
+__device__ __forceinline__ SplitVec add_vec(const SplitVec &a, const SplitVec &b) {
+    const float u = 5.9604645e-08f;
+    SplitVec r;
+    float vm = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        r.v[c] = a.v[c] + b.v[c];
+        vm = fmaxf(vm, fabsf(r.v[c]));
+    }
+    r.E = (a.E + b.E + u * vm) * 1.001f;
+    r.M = vm;
+    return r;
+}
+
+// Plucker coordinates (01, 02, 03, 12, 13, 23) of the plane of u and v, and one
+// bound on the error of every coordinate
+__device__ __forceinline__ void plucker(const SplitVec &a, const SplitVec &b, float m[6], float &eps) {
+    const float u = 5.9604645e-08f;
+    const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {1, 2, 3, 2, 3, 3};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) m[k] = fmaf(a.v[I[k]], b.v[J[k]], -(a.v[J[k]] * b.v[I[k]]));
+    eps = ((4.02f * u) * a.M * b.M + 2.0f * (a.E * b.M + b.E * a.M + a.E * b.E)) * 1.001f;
+}
+
+// the dual direction k (orthogonal to the plane and to axis k) from its
+// Plucker coordinates m = (01, 02, 03, 12, 13, 23)
+__device__ __forceinline__ void dual_dir(const float m[6], int k, float w[4]) {
+    w[0] = k == 0 ? 0.0f : (k == 1 ? -m[5] : (k == 2 ? m[4] : -m[3]));
+    w[1] = k == 1 ? 0.0f : (k == 0 ? m[5] : (k == 2 ? -m[2] : m[1]));
+    w[2] = k == 2 ? 0.0f : (k == 0 ? -m[4] : (k == 1 ? m[2] : -m[0]));
+    w[3] = k == 3 ? 0.0f : (k == 0 ? m[3] : (k == 1 ? -m[1] : m[0]));
+}
+
+// indices of the two longest duals
+__device__ __forceinline__ void top2_duals(const float m[6], int &k1, int &k2) {
+    const float s01 = m[0] * m[0], s02 = m[1] * m[1], s03 = m[2] * m[2];
+    const float s12 = m[3] * m[3], s13 = m[4] * m[4], s23 = m[5] * m[5];
+    const float n[4] = {s12 + s13 + s23, s02 + s03 + s23, s01 + s03 + s13, s01 + s02 + s12};
+    k1 = 0;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) k1 = n[k] > n[k1] ? k : k1;
+    k2 = k1 == 0 ? 1 : 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) k2 = (k != k1 && n[k] > n[k2]) ? k : k2;
+}
+
+__device__ __forceinline__ float dot4(const float w[4], const SplitVec &v) {
+    return fmaf(w[3], v.v[3], fmaf(w[2], v.v[2], fmaf(w[1], v.v[1], w[0] * v.v[0])));
+}
+
+// the gap test along w for X = {0, e1, e2} and Y = {r, s1, s3} (all relative to x2)
+__device__ __forceinline__ bool separated(const float w[4], const SplitVec &e1, const SplitVec &e2,
+                                          const SplitVec &r, const SplitVec &s1, const SplitVec &s3,
+                                          float delta) {
+    const float u = 5.9604645e-08f;
+    const float w1 = fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]) + fabsf(w[3]);
+    // |fl(w.v) - w.v_exact| <= |w|_1 (4.01 u M_v + E_v)
+    const float a1 = dot4(w, e1), a3 = dot4(w, e2);
+    const float b2 = dot4(w, r), b1 = dot4(w, s1), b3 = dot4(w, s3);
+    const float ex = w1 * fmaxf(fmaf(4.01f * u, e1.M, e1.E), fmaf(4.01f * u, e2.M, e2.E));
+    const float ey = w1 * fmaxf(fmaxf(fmaf(4.01f * u, r.M, r.E), fmaf(4.01f * u, s1.M, s1.E)),
+                                fmaf(4.01f * u, s3.M, s3.E));
+    const float xl = fminf(0.0f, fminf(a1, a3)), xh = fmaxf(0.0f, fmaxf(a1, a3));
+    const float yl = fminf(b2, fminf(b1, b3)), yh = fmaxf(b2, fmaxf(b1, b3));
+    const float DX = (xh - xl) + 2.0f * ex, DY = (yh - yl) + 2.0f * ey;
+    const float need = (2.0f * delta * (DX + DY) + ex + ey) * 1.001f;
+    const float gap = fmaxf(yl - xh, xl - yh) * (1.0f - 4.0f * u);
+    return gap > need;
+}
+
+// true when the separating-axis test proves the margin below -delta (not a hit,
+// also for an FP64 solve of the same system)
+__device__ __forceinline__ bool fp32_sat_reject(const float4 X[3][2], const float4 Y[3][2],
+                                                double tau) {
+    const float u = 5.9604645e-08f;
+    // vectors relative to x2
+    const SplitVec e1 = split_vec(X[0], X[1]);    // x1 - x2
+    const SplitVec e2 = split_vec(X[2], X[1]);    // x3 - x2
+    const SplitVec f1 = split_vec(Y[0], Y[1]);    // y1 - y2
+    const SplitVec f2 = split_vec(Y[2], Y[1]);    // y3 - y2
+    const SplitVec r = split_vec(Y[1], X[1]);     // y2 - x2
+    const SplitVec s1 = add_vec(r, f1), s3 = add_vec(r, f2);
+    float mE[6], mF[6], epsE, epsF;
+    plucker(e1, e2, mE, epsE);
+    plucker(f1, f2, mF, epsF);
+    // det [e1 e2 f1 f2] (= det A up to sign) and a bound on its error
+    const float det = mE[0] * mF[5] - mE[1] * mF[4] + mE[2] * mF[3] + mE[3] * mF[2] - mE[4] * mF[1] +
+                      mE[5] * mF[0];
+    float tE = 0.0f, tF = 0.0f, sabs = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        tE += fabsf(mE[k]);
+        tF += fabsf(mF[k]);
+        sabs = fmaf(fabsf(mE[k]), fabsf(mF[5 - k]), sabs);
+    }
+    const float derr = (epsF * tE + epsE * tF + 6.0f * epsE * epsF + (8.0f * u) * sabs) * 1.01f;
+    const float det_lo = fabsf(det) - derr;
+    // |A|_F^2 upper bound from the four edge vectors
+    float f2sum = 0.0f;
+    const SplitVec *cols[4] = {&e1, &e2, &f1, &f2};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float q = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) q = fmaf(cols[j]->v[c], cols[j]->v[c], q);
+        f2sum += q + 8.0f * cols[j]->E * cols[j]->M + 4.0f * cols[j]->E * cols[j]->E;
+    }
+    f2sum *= 1.001f;
+    const float F4 = f2sum * f2sum;
+    // kappa = F4 / det_lo <= 1e10, and delta from it
+    if (!(det_lo > 0.0f) || !(F4 <= 1e10f * det_lo)) return false;
+    const float kappa = F4 / det_lo * 1.001f;
+    const float delta = 2.0f * (float)tau * 1.001f + 9.1e-13f * kappa;
+    int k1, k2;
+    float w[4];
+    top2_duals(mE, k1, k2);
+    dual_dir(mE, k1, w);
+    if (separated(w, e1, e2, r, s1, s3, delta)) return true;
+    dual_dir(mE, k2, w);
+    if (separated(w, e1, e2, r, s1, s3, delta)) return true;
+    top2_duals(mF, k1, k2);
+    dual_dir(mF, k1, w);
+    if (separated(w, e1, e2, r, s1, s3, delta)) return true;
+    dual_dir(mF, k2, w);
+    return separated(w, e1, e2, r, s1, s3, delta);
+}
+
 // (theta, s) estimate for weights (u, v) in triangle t (formulas after Eq. (precise))
 __device__ __forceinline__ void tri_params(const MeshDev &m, uint32_t t, double u, double v,
                                            double &th, double &sv) {
@@ -369,15 +547,55 @@ __device__ __forceinline__ bool narrow_fp64(const MeshDev &ma, const MeshDev &mb
     return true;
 }
 
-// Stage 1: every triangle pair of every candidate through the verified FP32
-// filter; pairs it cannot reject go to the survivor list.
+// Stage 1: every triangle pair of every candidate through the FP32 tests;
+// pairs they cannot reject go to the survivor list.  Per lane one candidate:
+// for quads, its four triangle pairs share the quads' vertices.  A pair whose
+// (widened) triangle boxes overlap meets the separating-axis prefilter; the
+// few it cannot reject wait in a per-warp queue in shared memory, and the
+// verified solve runs on that queue 32 pairs at a time, so that the expensive
+// certificate never runs with most lanes idle.
 template <int FACE>
-__global__ void __launch_bounds__(256) k_narrow_filter(NarrowArgs a) {
+__global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
+    constexpr int kW = 8, kQ = 32 + 4 * 32;
+    __shared__ uint32_t q_cand[kW][kQ];
+    __shared__ uint8_t q_sub[kW][kQ];
     if (a.ctr->cand > a.cand_cap) return;
     const unsigned long long n = a.ctr->cand;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    unsigned long long nsolved = 0;   // pairs through the FP32 solve, per warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    unsigned long long n_sat = 0, n_full = 0;   // pairs through each test, per warp
+    unsigned qn = 0;                            // queued pairs (warp-uniform)
+
+    // the verified solve of queue items [base, base + cnt)
+    auto drain = [&](unsigned base, unsigned cnt) {
+        bool keep = false;
+        uint32_t ta = 0, tb = 0, pair = 0;
+        if ((unsigned)lane < cnt) {
+            const uint32_t g = q_cand[warp][base + lane];
+            const unsigned sub = q_sub[warp][base + lane];
+            const Cand c2 = a.cand[g];
+            ta = FACE == 0 ? c2.faceA : 2 * c2.faceA + (sub & 1u);
+            tb = FACE == 0 ? c2.faceB : 2 * c2.faceB + (sub >> 1);
+            pair = c2.pair;
+            const int2 pr = a.pairs[pair];
+            float4 X[3][2], Y[3][2];
+            gather_split(a.meshes[pr.x], ta, X);
+            gather_split(a.meshes[pr.y], tb, Y);
+            keep = !fp32_verified_reject(X, Y, a.tau);
+        }
+        n_full += cnt;
+        const unsigned long long pos = warp_append(&a.ctr->fp64, keep, FULL);
+        if (keep && pos < a.surv_cap) {
+            Cand sv;
+            sv.faceA = ta;
+            sv.faceB = tb;
+            sv.pair = pair;
+            sv.pad = 0;
+            a.surv[pos] = sv;
+        }
+    };
+
     for (unsigned long long g0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x - lane;
          g0 < n; g0 += stride) {
         const unsigned long long g = g0 + lane;
@@ -385,53 +603,73 @@ __global__ void __launch_bounds__(256) k_narrow_filter(NarrowArgs a) {
         Cand cd;
         cd.faceA = cd.faceB = cd.pair = 0;
         if (valid) cd = a.cand[g];
-        const int2 pr = a.pairs[valid ? cd.pair : 0];
-        const MeshDev ma = a.meshes[pr.x];
-        const MeshDev mb = a.meshes[pr.y];
-        const int nsub = FACE == 0 ? 1 : 4;
-        // quad candidates: the quads' four vertices once, (i,k) (i+1,k) (i,k+1) (i+1,k+1)
-        float4 QA[4][2], QB[4][2];
-        if (FACE == 1 && valid && a.fp32_filter) {
-            gather_quad_split(ma, cd.faceA, QA);
-            gather_quad_split(mb, cd.faceB, QB);
-        }
-#pragma unroll 1
-        for (int sub = 0; sub < nsub; ++sub) {
-            uint32_t ta, tb;
-            if (FACE == 0) { ta = cd.faceA; tb = cd.faceB; }
-            else { ta = 2 * cd.faceA + (sub & 1); tb = 2 * cd.faceB + (sub >> 1); }
-            bool keep = false, solved = false;
-            if (valid) {
-                if (a.fp32_filter) {
-                    float4 X[3][2], Y[3][2];
-                    if (FACE == 0) {
-                        gather_split(ma, ta, X);
-                        gather_split(mb, tb, Y);
-                        solved = true;
-                    } else {
-                        quad_tri(QA, sub & 1, X);
-                        quad_tri(QB, sub >> 1, Y);
-                        // the two triangles' boxes first: disjoint boxes, no intersection
-                        solved = split_boxes_overlap(X, Y);
-                    }
-                    keep = solved && !fp32_verified_reject(X, Y, a.tau);
-                } else {
-                    keep = true;
+        if (!a.fp32_filter) {
+            // every triangle pair of the candidate to the FP64 solve
+            const int nsub = FACE == 0 ? 1 : 4;
+            for (int sub = 0; sub < nsub; ++sub) {
+                const uint32_t ta = FACE == 0 ? cd.faceA : 2 * cd.faceA + (sub & 1);
+                const uint32_t tb = FACE == 0 ? cd.faceB : 2 * cd.faceB + (sub >> 1);
+                const unsigned long long pos = warp_append(&a.ctr->fp64, valid, FULL);
+                if (valid && pos < a.surv_cap) {
+                    Cand sv;
+                    sv.faceA = ta;
+                    sv.faceB = tb;
+                    sv.pair = cd.pair;
+                    sv.pad = 0;
+                    a.surv[pos] = sv;
                 }
             }
-            nsolved += __popc(__ballot_sync(FULL, solved));
-            const unsigned long long pos = warp_append(&a.ctr->fp64, keep, FULL);
-            if (keep && pos < a.surv_cap) {
-                Cand s;
-                s.faceA = ta;
-                s.faceB = tb;
-                s.pair = cd.pair;
-                s.pad = 0;
-                a.surv[pos] = s;
+            continue;
+        }
+        const int2 pr = a.pairs[valid ? cd.pair : 0];
+        float4 QA[4][2], QB[4][2];
+        if (FACE == 1 && valid) {
+            // the quads' four vertices once, (i,k) (i+1,k) (i,k+1) (i+1,k+1)
+            gather_quad_split(a.meshes[pr.x], cd.faceA, QA);
+            gather_quad_split(a.meshes[pr.y], cd.faceB, QB);
+        }
+        const int nsub = FACE == 0 ? 1 : 4;
+#pragma unroll 1
+        for (int sub = 0; sub < nsub; ++sub) {
+            bool tested = false, need = false;
+            if (valid) {
+                float4 X[3][2], Y[3][2];
+                if (FACE == 0) {
+                    gather_split(a.meshes[pr.x], cd.faceA, X);
+                    gather_split(a.meshes[pr.y], cd.faceB, Y);
+                    tested = true;
+                } else {
+                    quad_tri(QA, sub & 1, X);
+                    quad_tri(QB, sub >> 1, Y);
+                    // the two triangles' boxes first: disjoint boxes, no intersection
+                    tested = split_boxes_overlap(X, Y);
+                }
+                need = tested && !fp32_sat_reject(X, Y, a.tau);
             }
+            n_sat += __popc(__ballot_sync(FULL, tested));
+            const uint32_t want = __ballot_sync(FULL, need);
+            if (need) {
+                const unsigned slot = qn + __popc(want & lt);
+                q_cand[warp][slot] = (uint32_t)g;
+                q_sub[warp][slot] = (uint8_t)sub;
+            }
+            qn += __popc(want);
+        }
+        __syncwarp();
+        while (qn >= 32) {
+            qn -= 32;
+            drain(qn, 32);
+            __syncwarp();
         }
     }
-    if (lane == 0 && nsolved) atomicAdd(&a.ctr->fp32, nsolved);
+    if (qn) {
+        drain(0, qn);
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (n_sat) atomicAdd(&a.ctr->sat, n_sat);
+        if (n_full) atomicAdd(&a.ctr->fp32, n_full);
+    }
 }
 
 // Stage 2: the FP64 solve for the survivors

@@ -173,25 +173,35 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_pass(
             if (lane >= off) incl += y;
         }
         if (lane == 31) wsum[warp] = incl;
-        // decoupled look-back over the earlier tiles
+        // decoupled look-back over the earlier tiles, four words per poll
         uint64_t prefix = 0;
         if (tile > 0) {
-            unsigned long long t = tile - 1;
+            long long t = (long long)tile - 1;
             unsigned spins = 0;
-            for (;;) {
-                const uint64_t w = ld_volatile_u64(look + t * kRadixBins + dme);
-                const uint64_t flag = w & ~kCountMask;
-                if (flag == 0) {
+            bool done = false;
+            while (!done) {
+                uint64_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    w[q] = (t - q >= 0) ? ld_volatile_u64(look + (t - q) * kRadixBins + dme) : kFlagInc;
+                int used = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (done || used < q) continue;        // stop at a gap or an inclusive count
+                    const uint64_t flag = w[q] & ~kCountMask;
+                    if (flag == 0) continue;               // not yet published: poll again from here
+                    if (t - q >= 0) prefix += w[q] & kCountMask;
+                    ++used;
+                    if (flag == kFlagInc || t - q <= 0) done = true;
+                }
+                t -= used;
+                if (!done && used == 0) {
                     if (++spins > kSpinLimit) {
                         atomicOr(status, ST_TIMEOUT);
                         break;
                     }
                     __nanosleep(64);
-                    continue;
                 }
-                prefix += w & kCountMask;
-                if (flag == kFlagInc || t == 0) break;
-                --t;
             }
             st_volatile_u64(my_word, kFlagInc | (prefix + cnt));
         }
