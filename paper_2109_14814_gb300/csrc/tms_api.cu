@@ -89,7 +89,7 @@ struct Plan {
     unsigned long long tsize = 0, tsize_min = 0;
     unsigned long long *tkey = nullptr, *ckey = nullptr;
     uint2 *tcnt = nullptr;
-    uint32_t *tcell = nullptr;
+    uint2 *tstart = nullptr;
     void *sort_scratch = nullptr;
     unsigned long long *partials = nullptr;
     uint32_t *cstart = nullptr, *cb = nullptr;
@@ -117,13 +117,13 @@ struct Plan {
     unsigned long long last_use = 0;
 
     void free_scratch() {
-        void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, ckey, tcnt, tcell,
+        void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, ckey, tcnt, tstart,
                         sort_scratch, cstart, cb, toff, cand, surv, hits, hk, hk2, okeys, hv, hv2,
                         keep, kscan};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         bmA = bmH = nullptr; ek = nullptr; ev = eslot = erank = grouped = nullptr;
-        tkey = ckey = nullptr; tcnt = nullptr; tcell = nullptr;
+        tkey = ckey = nullptr; tcnt = nullptr; tstart = nullptr;
         sort_scratch = nullptr; cstart = cb = nullptr; toff = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
         hv = hv2 = keep = kscan = nullptr;
         if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
@@ -161,7 +161,7 @@ struct Plan {
         while ((tsize < want || tsize < tsize_min) && tsize < (1ULL << 31)) tsize <<= 1;
         TMS_CK(dalloc(&tkey, tsize));
         TMS_CK(dalloc(&tcnt, tsize));
-        TMS_CK(dalloc(&tcell, tsize));
+        TMS_CK(dalloc(&tstart, tsize));
         TMS_CK(cudaMemset(tkey, 0, tsize * sizeof(unsigned long long)));
         TMS_CK(cudaMemset(tcnt, 0, tsize * sizeof(uint2)));
         TMS_CK(dalloc(&ckey, ent_cap));
@@ -205,7 +205,7 @@ struct Plan {
         GroupArgs ga;
         ga.ent_key = ek; ga.ent_face = ev; ga.d_n = &d_ctr->entries; ga.cap = ent_cap;
         ga.ent_slot = eslot; ga.ent_rank = erank;
-        ga.tkey = tkey; ga.tcnt = tcnt; ga.tcell = tcell; ga.tsize = tsize;
+        ga.tkey = tkey; ga.tcnt = tcnt; ga.tstart = tstart; ga.tsize = tsize;
         ga.cell_key = ckey; ga.cell_start = cstart; ga.cell_b = cb; ga.tile_off = toff;
         ga.grouped = grouped; ga.partials = partials; ga.ctr = d_ctr;
         kernels += 1;

@@ -189,37 +189,47 @@ __device__ __forceinline__ unsigned long long warp_append(unsigned long long *co
 }
 
 // Warp-staged append for high-volume outputs: lanes with pred place one record
-// each in the warp's shared-memory stage (64 records); every full 32 go out
-// with one atomic on the global counter and one coalesced store, so the
-// counter sees one atomic per 32 records instead of one per vote.  All 32
-// lanes call it together with the same n; store(pos, rec) writes record rec
-// at global position pos (the caller checks pos against its capacity).
-template <typename Rec, typename Store>
+// each in the warp's shared-memory stage (FLUSH + 32 records); every FLUSH
+// records go out with one atomic on the global counter and coalesced stores,
+// so the counter sees one atomic per FLUSH records (a single global counter
+// serialises its atomics).  All 32 lanes call it together with the same n;
+// store(pos, rec) writes record rec at global position pos (the caller checks
+// pos against its capacity).
+// the records left in the stage (fewer than FLUSH) at the end of a kernel
+template <unsigned FLUSH, typename Rec, typename Store>
 __device__ __forceinline__ void stage_flush(Rec *stage, unsigned cnt, unsigned long long *counter,
                                             const Store &store) {
     const int lane = threadIdx.x & 31;
     unsigned long long base = 0;
     if (lane == 0 && cnt) base = atomicAdd(counter, (unsigned long long)cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
-    if ((unsigned)lane < cnt) store(base + lane, stage[lane]);
+#pragma unroll
+    for (unsigned k = 0; k < FLUSH; k += 32)
+        if (k + lane < cnt) store(base + k + lane, stage[k + lane]);
     __syncwarp();
 }
 
-template <typename Rec, typename Store>
+template <unsigned FLUSH, typename Rec, typename Store>
 __device__ __forceinline__ void stage_push(Rec *stage, unsigned &n, bool pred, const Rec &rec,
                                            unsigned long long *counter, const Store &store) {
+    static_assert(FLUSH % 32 == 0, "flush whole warps");
     const unsigned want = __ballot_sync(0xffffffffu, pred);
     if (!want) return;
     const int lane = threadIdx.x & 31;
     if (pred) stage[n + __popc(want & lanemask_lt())] = rec;
     n += __popc(want);
-    if (n >= 32) {
+    if (n >= FLUSH) {
         __syncwarp();
-        stage_flush(stage, 32u, counter, store);
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(counter, (unsigned long long)FLUSH);
+        base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+        for (unsigned k = 0; k < FLUSH; k += 32) store(base + k + lane, stage[k + lane]);
+        __syncwarp();
         // move the remainder (fewer than 32) to the front
-        const unsigned rem = n - 32;
+        const unsigned rem = n - FLUSH;
         Rec r;
-        if ((unsigned)lane < rem) r = stage[32 + lane];
+        if ((unsigned)lane < rem) r = stage[FLUSH + lane];
         __syncwarp();
         if ((unsigned)lane < rem) stage[lane] = r;
         __syncwarp();
@@ -384,7 +394,7 @@ struct GroupArgs {
     uint32_t *ent_rank;            // [cap] rank within (cell, role)
     unsigned long long *tkey;      // [tsize] (pair << 31 | cell) + 1, or kHashEmpty
     uint2 *tcnt;                   // [tsize] A and B entry counts
-    uint32_t *tcell;               // [tsize] compacted cell index or kNoCell
+    uint2 *tstart;                 // [tsize] the slot's A and B list starts (kNoCell: no cell)
     unsigned long long tsize;      // power of two; grown by the host when over half full
     // per compacted cell, [cap]
     unsigned long long *cell_key;

@@ -366,6 +366,8 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kCellWarps = 8;
 
+constexpr unsigned kEntryFlush = 224;   // entries per atomic on the entry counter
+
 struct EntryRec {
     uint64_t key;
     uint32_t face;
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_cell_pass(FacePassArgs a, i
     __shared__ uint32_t s_excl[kCellWarps][32];
     __shared__ uint2 s_lo[kCellWarps][32];
     __shared__ uint2 s_cnt[kCellWarps][32];
-    __shared__ EntryRec s_out[kCellWarps][64];   // staged entries
+    __shared__ EntryRec s_out[kCellWarps][kEntryFlush + 32];   // staged entries
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long wslot = slot - lane;           // the warp's first slot
@@ -508,12 +510,12 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_cell_pass(FacePassArgs a, i
             EntryRec r;
             r.key = pair_hi | ((uint64_t)cell << 1) | (uint64_t)pe.role;
             r.face = (uint32_t)(wslot - pe.face_base) + (uint32_t)owner;
-            stage_push(stage, staged, emit, r, &a.ctr->entries, store);
+            stage_push<kEntryFlush>(stage, staged, emit, r, &a.ctr->entries, store);
         }
     }
     if (MODE != MODE_MARK) {
         __syncwarp();
-        stage_flush(stage, staged, &a.ctr->entries, store);
+        stage_flush<kEntryFlush>(stage, staged, &a.ctr->entries, store);
     }
 }
 

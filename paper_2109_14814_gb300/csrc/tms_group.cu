@@ -210,11 +210,12 @@ __global__ void __launch_bounds__(kCellScanBlock) k_cells_down(GroupArgs a) {
                 a.cell_start[c] = (uint32_t)ex[1];
                 a.cell_b[c] = (uint32_t)ex[1] + cnt.x;
                 a.tile_off[c] = ex[2];
-                a.tcell[slot] = (uint32_t)c;
+                // the scatter's one gather: both list starts of the slot
+                a.tstart[slot] = make_uint2((uint32_t)ex[1], (uint32_t)ex[1] + cnt.x);
             } else {
-                a.tcell[slot] = kNoCell;
+                a.tstart[slot] = make_uint2(kNoCell, kNoCell);
             }
-            // the slot is free again for the next search (the scatter reads tcell only)
+            // the slot is free again for the next search (the scatter reads tstart only)
             a.tkey[slot] = kHashEmpty;
             a.tcnt[slot] = make_uint2(0u, 0u);
         }
@@ -234,9 +235,9 @@ __global__ void __launch_bounds__(kGroupBlock) k_group_scatter(GroupArgs a) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += stride) {
         const uint32_t sr = a.ent_slot[i];
-        const uint32_t c = a.tcell[sr & 0x7FFFFFFFu];
-        if (c == kNoCell) continue;
-        const uint32_t start = (sr >> 31) ? a.cell_b[c] : a.cell_start[c];
+        const uint2 st = a.tstart[sr & 0x7FFFFFFFu];
+        if (st.x == kNoCell) continue;
+        const uint32_t start = (sr >> 31) ? st.y : st.x;
         const unsigned long long pos = (unsigned long long)start + a.ent_rank[i];
         if (pos < a.cap) a.grouped[pos] = a.ent_face[i];
     }

@@ -87,7 +87,7 @@ struct Buffers {
     uint32_t *ev, *eslot, *erank, *grouped;
     unsigned long long *tkey, *ckey;
     uint2 *tcnt;
-    uint32_t *tcell;
+    uint2 *tstart;
     void *sort_scratch;
     uint32_t *cstart, *cb;
     unsigned long long *toff;
@@ -127,7 +127,7 @@ size_t carve(unsigned char *base, Buffers &b) {
     b.eslot = c.take<uint32_t>(kEntCap);
     b.erank = c.take<uint32_t>(kEntCap);
     b.grouped = c.take<uint32_t>(kEntCap);
-    b.tcell = c.take<uint32_t>(kTableSize);
+    b.tstart = c.take<uint2>(kTableSize);
     b.ckey = c.take<unsigned long long>(kEntCap);
     b.cstart = c.take<uint32_t>(kEntCap);
     b.cb = c.take<uint32_t>(kEntCap);
@@ -263,7 +263,7 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     GroupArgs ga;
     ga.ent_key = b.ek; ga.ent_face = b.ev; ga.d_n = &b.ctr->entries; ga.cap = kEntCap;
     ga.ent_slot = b.eslot; ga.ent_rank = b.erank;
-    ga.tkey = b.tkey; ga.tcnt = b.tcnt; ga.tcell = b.tcell; ga.tsize = kTableSize;
+    ga.tkey = b.tkey; ga.tcnt = b.tcnt; ga.tstart = b.tstart; ga.tsize = kTableSize;
     ga.cell_key = b.ckey; ga.cell_start = b.cstart; ga.cell_b = b.cb; ga.tile_off = b.toff;
     ga.grouped = b.grouped; ga.partials = b.partials; ga.ctr = b.ctr;
     FacePassArgs fa;

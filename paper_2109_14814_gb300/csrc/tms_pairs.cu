@@ -28,6 +28,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kTile = 32;
 constexpr int kEmitWarps = 8;
+constexpr unsigned kCandFlush = 64;    // candidates per atomic on the candidate counter
 
 // ---------------------------------------------------------------------------
 // emission
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
     __shared__ EBox<PREC> sBox[kEmitWarps][kTile];
     __shared__ uint2 sLo[kEmitWarps][kTile];
     __shared__ uint32_t sFace[kEmitWarps][kTile];
-    __shared__ Cand sOut[kEmitWarps][2 * kTile];   // staged candidates
+    __shared__ Cand sOut[kEmitWarps][kCandFlush + 32];   // staged candidates
     // nothing to do after an entry overflow (the host retries with more room),
     // and a bounded amount of work in any case
     if (a.ctr->entries > a.ent_cap) return;
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
             cd.faceB = swapAB ? aface : bface;
             cd.pair = pair;
             cd.pad = 0;
-            stage_push(stage, staged, keep, cd, &a.ctr->cand, store);
+            stage_push<kCandFlush>(stage, staged, keep, cd, &a.ctr->cand, store);
         };
         // two B boxes per step, one vote; the rest of the work only when a lane overlaps
         int j = 0;
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         __syncwarp();
     }
     __syncwarp();
-    stage_flush(stage, staged, &a.ctr->cand, store);
+    stage_flush<kCandFlush>(stage, staged, &a.ctr->cand, store);
 }
 
 }  // namespace
