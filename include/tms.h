@@ -267,6 +267,11 @@ tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_params *params,
                               void *stream);
 const char *tms_noalloc_last_error(void);
 
+/* Bytes of the static array the layout of tms_search_noalloc uses (*needed)
+ * and holds (*reserved); host only, no device call.  A build whose layout
+ * does not fit refuses every call with TMS_ERR_STATE. */
+tms_status tms_noalloc_footprint(unsigned long long *needed, unsigned long long *reserved);
+
 /* Per-stage device time (ms) of the last search on `stream` made with
  * params.timing = 1, in this order:
  *   0 counters/bounds init   1 face pass: world bounds   2 grid parameters

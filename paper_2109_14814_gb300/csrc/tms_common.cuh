@@ -398,6 +398,8 @@ struct GroupArgs {
     unsigned long long tsize;      // power of two; grown by the host when over half full
     // per compacted cell, [cap]
     unsigned long long *cell_key;
+    uint2 *cell_xy;                // the cell's coordinates, 4 x u16
+    const Grid *grids;             // per pair (cells per coordinate)
     uint32_t *cell_start;          // first A entry in `grouped`
     uint32_t *cell_b;              // first B entry
     unsigned long long *tile_off;  // exclusive scan of the 32 x 32 tiles of nA x nB
@@ -412,6 +414,7 @@ void launch_group_cells(const GroupArgs &a, int grid, cudaStream_t st);
 
 struct EmitArgs {
     const unsigned long long *cell_key;   // pair << 31 | cell
+    const uint2 *cell_xy;          // the cell's coordinates, 4 x u16
     const uint32_t *vals;          // face ids grouped by cell
     const uint32_t *cell_start;
     const uint32_t *cell_b;

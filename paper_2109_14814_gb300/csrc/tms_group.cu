@@ -206,7 +206,17 @@ __global__ void __launch_bounds__(kCellScanBlock) k_cells_down(GroupArgs a) {
             if (v.both) {
                 const unsigned long long c = ex[0];
                 const uint2 cnt = a.tcnt[slot];
-                a.cell_key[c] = a.tkey[slot] - 1;
+                const unsigned long long key = a.tkey[slot] - 1;
+                a.cell_key[c] = key;
+                // the cell's coordinates (the emission's owner test needs them per tile)
+                const Grid &g = a.grids[(uint32_t)(key >> 31)];
+                uint32_t cell = (uint32_t)(key & 0x7FFFFFFFu), cc[4];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    cc[d] = cell % (uint32_t)g.n[d];
+                    cell /= (uint32_t)g.n[d];
+                }
+                a.cell_xy[c] = make_uint2(cc[0] | (cc[1] << 16), cc[2] | (cc[3] << 16));
                 a.cell_start[c] = (uint32_t)ex[1];
                 a.cell_b[c] = (uint32_t)ex[1] + cnt.x;
                 a.tile_off[c] = ex[2];

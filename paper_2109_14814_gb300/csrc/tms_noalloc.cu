@@ -57,7 +57,7 @@ unsigned char *g_base[64] = {};
 thread_local std::string g_msg;
 
 struct Carve {
-    unsigned char *base;
+    uintptr_t base;      // the arena's address (0 when only the size is wanted)
     size_t off = 0;
     template <typename T>
     T *take(unsigned long long n) {
@@ -86,6 +86,7 @@ struct Buffers {
     uint64_t *ek;
     uint32_t *ev, *eslot, *erank, *grouped;
     unsigned long long *tkey, *ckey;
+    uint2 *cxy;
     uint2 *tcnt;
     uint2 *tstart;
     void *sort_scratch;
@@ -104,7 +105,7 @@ struct Buffers {
 // are written only after candidate emission, the broad phase's last reader,
 // has run on the same stream.  The array starts zeroed: every table slot free.
 size_t carve(unsigned char *base, Buffers &b) {
-    Carve c{base};
+    Carve c{reinterpret_cast<uintptr_t>(base)};
     b.tables = c.take<Tables>(1);
     b.bounds = c.take<Bounds>(2);
     b.grids = c.take<Grid>(1);
@@ -128,10 +129,12 @@ size_t carve(unsigned char *base, Buffers &b) {
     b.erank = c.take<uint32_t>(kEntCap);
     b.grouped = c.take<uint32_t>(kEntCap);
     b.tstart = c.take<uint2>(kTableSize);
-    b.ckey = c.take<unsigned long long>(kEntCap);
-    b.cstart = c.take<uint32_t>(kEntCap);
-    b.cb = c.take<uint32_t>(kEntCap);
-    b.toff = c.take<unsigned long long>(kEntCap);
+    // per cell: a cell holding both meshes has at least two entries
+    b.ckey = c.take<unsigned long long>(kEntCap / 2);
+    b.cxy = c.take<uint2>(kEntCap / 2);
+    b.cstart = c.take<uint32_t>(kEntCap / 2);
+    b.cb = c.take<uint32_t>(kEntCap / 2);
+    b.toff = c.take<unsigned long long>(kEntCap / 2);
     const size_t broad_end = c.off;
     // narrow phase and merge, over the broad phase's bytes
     c.off = phase;
@@ -185,6 +188,14 @@ tms_status setup(int device, unsigned char **base) {
 }  // namespace
 
 extern "C" const char *tms_noalloc_last_error(void) { return g_msg.c_str(); }
+
+extern "C" tms_status tms_noalloc_footprint(unsigned long long *needed, unsigned long long *reserved) {
+    if (!needed || !reserved) return TMS_ERR_ARG;
+    Buffers b;
+    *needed = (unsigned long long)carve(nullptr, b);
+    *reserved = (unsigned long long)kArenaBytes;
+    return TMS_OK;
+}
 
 extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_params *params,
                                          tms_hit *dHits, long long hitCap, long long *nHits,
@@ -264,7 +275,7 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     ga.ent_key = b.ek; ga.ent_face = b.ev; ga.d_n = &b.ctr->entries; ga.cap = kEntCap;
     ga.ent_slot = b.eslot; ga.ent_rank = b.erank;
     ga.tkey = b.tkey; ga.tcnt = b.tcnt; ga.tstart = b.tstart; ga.tsize = kTableSize;
-    ga.cell_key = b.ckey; ga.cell_start = b.cstart; ga.cell_b = b.cb; ga.tile_off = b.toff;
+    ga.cell_key = b.ckey; ga.cell_xy = b.cxy; ga.grids = b.grids; ga.cell_start = b.cstart; ga.cell_b = b.cb; ga.tile_off = b.toff;
     ga.grouped = b.grouped; ga.partials = b.partials; ga.ctr = b.ctr;
     FacePassArgs fa;
     memset(&fa, 0, sizeof(fa));
@@ -304,7 +315,7 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     launch_group_count(ga, grid, s);
     launch_group_cells(ga, grid, s);
     EmitArgs ea;
-    ea.cell_key = b.ckey; ea.vals = b.grouped; ea.cell_start = b.cstart; ea.cell_b = b.cb; ea.tile_off = b.toff;
+    ea.cell_key = b.ckey; ea.cell_xy = b.cxy; ea.vals = b.grouped; ea.cell_start = b.cstart; ea.cell_b = b.cb; ea.tile_off = b.toff;
     ea.grids = b.grids; ea.meshes = b.tables->meshes; ea.pairs = b.tables->pairs; ea.ctr = b.ctr;
     ea.ent_cap = kEntCap; ea.cand = b.cand; ea.cand_cap = kCandCap; ea.moller = p.moller;
     launch_emit(ea, p.precision, p.face_level, grid * 4, s);

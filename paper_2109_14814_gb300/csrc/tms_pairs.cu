@@ -131,6 +131,13 @@ __device__ bool moller_reject(const MeshDev &ma, uint32_t fa, const MeshDev &mb,
     return same_side(VB[1], VB[0], VB[2], VA, 4) && same_side(VB[2], VB[3], VB[1], VA, 4);
 }
 
+// the coordinates in which a face's lowest cell is this cell: bit d set when
+// lo_d == cur_d (both packed 4 x u16); a face in the cell has lo_d <= cur_d
+__device__ __forceinline__ uint32_t own_mask(uint2 lo, uint2 cur) {
+    const uint32_t ex = __vcmpeq2(lo.x, cur.x), ey = __vcmpeq2(lo.y, cur.y);
+    return (ex & 1u) | ((ex >> 15) & 2u) | ((ey & 1u) << 2) | ((ey >> 13) & 8u);
+}
+
 template <int PREC>
 __device__ __forceinline__ bool boxes_overlap(const EBox<PREC> &x, const EBox<PREC> &y) {
     bool ov = true;
@@ -143,7 +150,7 @@ template <int PREC, bool MOLLER>
 __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_level) {
     // the tile's B side, structure of arrays: the hot loop reads only the boxes
     __shared__ EBox<PREC> sBox[kEmitWarps][kTile];
-    __shared__ uint2 sLo[kEmitWarps][kTile];
+    __shared__ uint32_t sMask[kEmitWarps][kTile];
     __shared__ uint32_t sFace[kEmitWarps][kTile];
     __shared__ Cand sOut[kEmitWarps][kCandFlush + 32];   // staged candidates
     // nothing to do after an entry overflow (the host retries with more room),
@@ -195,71 +202,59 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         const bool swapAB = nBt0 > nAt0;
         const uint32_t l0 = swapAB ? b0 : a0, m0 = swapAB ? a0 : b0;
         const int nAt = swapAB ? nBt0 : nAt0, nBt = swapAB ? nAt0 : nBt0;
-        const unsigned long long ck = a.cell_key[c];
-        const uint32_t pair = (uint32_t)(ck >> 31);
-        const uint32_t cell = (uint32_t)(ck & 0x7FFFFFFFu);
+        const uint32_t pair = (uint32_t)(a.cell_key[c] >> 31);
+        const uint2 cur = a.cell_xy[c];
         const Grid &gr = a.grids[pair];
-        const uint32_t n0 = (uint32_t)gr.n[0], n1 = (uint32_t)gr.n[1], n2 = (uint32_t)gr.n[2];
         // own entry (the lanes' side) in registers, the other side in shared memory
         const int2 pr = a.pairs[pair];
         const void *fbA = a.meshes[pr.x].fbox, *fbB = a.meshes[pr.y].fbox;
         const void *fbL = swapAB ? fbB : fbA, *fbM = swapAB ? fbA : fbB;
         EBox<PREC> abox;
-        uint2 alo = make_uint2(0u, 0u);
-        uint32_t aface = 0;
+        uint32_t amask = 0, aface = 0;
         const bool hasA = lane < nAt;
         if (hasA) {
             aface = a.vals[l0 + lane];
             abox.load(fbL, aface);
-            alo = abox.low_cell(gr);
+            amask = own_mask(abox.low_cell(gr), cur);
         }
         if (lane < nBt) {
             const uint32_t bface = a.vals[m0 + lane];
             EBox<PREC> bb;
             bb.load(fbM, bface);
             sBox[warp][lane] = bb;
-            sLo[warp][lane] = bb.low_cell(gr);
+            sMask[warp][lane] = own_mask(bb.low_cell(gr), cur);
             sFace[warp][lane] = bface;
         }
         __syncwarp();
-        // the owner-cell rule and the append, for lanes whose boxes overlap box j
-        auto resolve = [&](int j, bool ov) {
-            bool keep = false;
-            if (ov) {
-                // owner cell: componentwise max of the two lowest cells, compared
-                // with this cell by linear index
-                const uint2 bl = sLo[warp][j];
-                const uint32_t mx = __vmaxu2(alo.x, bl.x), my = __vmaxu2(alo.y, bl.y);
-                const uint32_t own =
-                    (((my >> 16) * n2 + (my & 0xFFFFu)) * n1 + (mx >> 16)) * n0 + (mx & 0xFFFFu);
-                keep = own == cell;
-                if (MOLLER && keep) {
-                    const uint32_t bface = sFace[warp][j];
-                    const uint32_t fa = swapAB ? bface : aface, fb = swapAB ? aface : bface;
-                    keep = !moller_reject(a.meshes[pr.x], fa, a.meshes[pr.y], fb, face_level);
-                }
+        // the append of the pairs with box j that survive (and, optionally, Moller)
+        auto emit_j = [&](int j, bool keep) {
+            const uint32_t bface = sFace[warp][j];
+            if (MOLLER && keep) {
+                const uint32_t fa = swapAB ? bface : aface, fb = swapAB ? aface : bface;
+                keep = !moller_reject(a.meshes[pr.x], fa, a.meshes[pr.y], fb, face_level);
             }
             Cand cd;
-            const uint32_t bface = sFace[warp][j];
             cd.faceA = swapAB ? bface : aface;
             cd.faceB = swapAB ? aface : bface;
             cd.pair = pair;
             cd.pad = 0;
             stage_push<kCandFlush>(stage, staged, keep, cd, &a.ctr->cand, store);
         };
-        // two B boxes per step, one vote; the rest of the work only when a lane overlaps
+        // owner cell: the componentwise max of the two faces' lowest cells is this
+        // cell iff every coordinate is owned by one of them (masks OR to 0xF);
+        // two B boxes per step, one vote, the append only when a lane keeps a pair
         int j = 0;
         for (; j + 1 < nBt; j += 2) {
             const EBox<PREC> b0x = sBox[warp][j], b1x = sBox[warp][j + 1];
-            const bool ov0 = hasA & boxes_overlap(abox, b0x);
-            const bool ov1 = hasA & boxes_overlap(abox, b1x);
-            if (__ballot_sync(FULL, ov0 | ov1) == 0u) continue;
-            resolve(j, ov0);
-            resolve(j + 1, ov1);
+            const bool k0 = hasA & ((amask | sMask[warp][j]) == 0xFu) & boxes_overlap(abox, b0x);
+            const bool k1 = hasA & ((amask | sMask[warp][j + 1]) == 0xFu) & boxes_overlap(abox, b1x);
+            if (__ballot_sync(FULL, k0 | k1) == 0u) continue;
+            emit_j(j, k0);
+            emit_j(j + 1, k1);
         }
         if (j < nBt) {
-            const bool ov0 = hasA & boxes_overlap(abox, sBox[warp][j]);
-            if (__ballot_sync(FULL, ov0) != 0u) resolve(j, ov0);
+            const bool k0 = hasA & ((amask | sMask[warp][j]) == 0xFu) & boxes_overlap(abox, sBox[warp][j]);
+            if (__ballot_sync(FULL, k0) != 0u) emit_j(j, k0);
         }
         __syncwarp();
     }

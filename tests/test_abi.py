@@ -72,3 +72,12 @@ def test_null_arguments_rejected_without_gpu():
                             None) == tms.TMS_ERR_ARG
     assert lib.tms_autotune(None, None, 0, None, ctypes.byref(best), None, None,
                             None) == tms.TMS_ERR_ARG
+
+
+def test_noalloc_layout_fits_its_static_array():
+    lib = tms.lib()
+    needed, reserved = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    lib.tms_noalloc_footprint.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.tms_noalloc_footprint(ctypes.byref(needed), ctypes.byref(reserved)) == tms.TMS_OK
+    assert reserved.value == 64 << 20
+    assert 0 < needed.value <= reserved.value
