@@ -47,6 +47,12 @@ FP32_SOLVE_FLOPS = 956
 # of Plucker coordinates (56), det A with its error bound (46), the Frobenius
 # bound and kappa (70), the two dual choices (28), four interval tests (260)
 SAT_FLOPS = 551
+# FP32 operations of the quad-level test of one quad candidate: seven split
+# difference vectors (112), four edge differences (32), four sets of Plucker
+# coordinates (112), eight squared-norm bounds (112), four determinant bounds
+# (180), kappa and delta (40), two dual choices (28), four interval tests over
+# eight vertices (360)
+QUAD_SAT_FLOPS = 964
 
 
 def dist_env():
@@ -232,12 +238,14 @@ def run_tms(args, ws, rank, local):
     # GPU (SMs x 128 lanes x the maximum SM clock; an FMA counts 2 FLOPs).
     # The slowest stage is reported as `roofline`.  V vertices and F faces per
     # mesh (quads), E face-cell entries, P proposed face pairs, C candidate
-    # quad pairs, SAT triangle pairs through the separating-axis prefilter,
+    # quad pairs, QSAT quad candidates through the quad-level test, SAT triangle
+    # pairs through the separating-axis prefilter,
     # S32 / S64 triangle pairs through the FP32 / FP64 solve.
     V = pair.A.N * pair.A.M
     F = pair.A.N * (pair.A.M - 1)
     E, C, S = stats["entries"], stats["candidates"], stats["fp64_solves"]
     P, S32, SAT = stats["pair_slots"], stats["fp32_solves"], stats["sat_tests"]
+    QSAT = stats["quad_tests"]
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     sm_hz = float(NOMINAL_SM_MAX_MHZ) * 1e6
     lane_ops = sms * 128 * sm_hz                   # FP32 lane operations per second
@@ -255,10 +263,11 @@ def run_tms(args, ws, rank, local):
                         E * (4 + 8 + 4 + 4 + 4) + stats["cells"] * 24),
         # the box test of every proposed face pair: 8 FP32 compares
         "emit": ("tms::k_emit", "alu", 1, 8 * P),
-        # the separating-axis prefilter per triangle pair whose boxes overlap, the
-        # verified FP32 solve for the pairs it cannot reject
+        # the quad-level test per quad candidate, the triangle-level test per pair
+        # of the candidates it cannot clear whose boxes overlap, the verified FP32
+        # solve for the pairs left
         "narrow": ("tms::k_narrow_filter + k_narrow_fp64", "alu", 2,
-                   SAT_FLOPS * SAT + FP32_SOLVE_FLOPS * S32),
+                   QUAD_SAT_FLOPS * QSAT + SAT_FLOPS * SAT + FP32_SOLVE_FLOPS * S32),
     }
     stage_time = dict(stage_ms)
     stage_time["face_probe_B+A"] = stage_ms.get("face_probe_B", 0.0) + stage_ms.get("face_probe_A", 0.0)

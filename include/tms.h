@@ -236,6 +236,7 @@ typedef struct {
     int pad;
     long long fp32_solves;  /* triangle pairs through the verified FP32 solve */
     long long sat_tests;    /* triangle pairs through the separating-axis prefilter */
+    long long quad_tests;   /* quad candidates through the quad-level prefilter */
 } tms_stats;
 
 tms_status tms_last_stats(void *stream, tms_stats *out);

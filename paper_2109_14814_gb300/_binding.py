@@ -67,6 +67,7 @@ class Stats(ctypes.Structure):
         ("pad", _c.c_int),
         ("fp32_solves", _c.c_longlong),
         ("sat_tests", _c.c_longlong),
+        ("quad_tests", _c.c_longlong),
     ]
 
     def as_dict(self):

@@ -640,6 +640,7 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
     st.fp64_solves = (long long)c.fp64;
     st.fp32_solves = (long long)c.fp32;
     st.sat_tests = (long long)c.sat;
+    st.quad_tests = (long long)c.quad;
     st.raw_hits = (long long)c.raw_hits;
     st.hits = (long long)c.out;
     for (int d = 0; d < 4; ++d) st.grid_n[d] = P->h_grid0->n[d];

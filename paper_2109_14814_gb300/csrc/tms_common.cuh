@@ -104,6 +104,7 @@ struct Counters {
     unsigned long long fp64;
     unsigned long long fp32;       // triangle pairs through the verified FP32 solve
     unsigned long long sat;        // triangle pairs through the separating-axis prefilter
+    unsigned long long quad;       // quad candidates through the quad-level prefilter
     unsigned long long claimed;    // cell-table slots claimed by this search
     unsigned long long raw_hits;
     unsigned long long out;

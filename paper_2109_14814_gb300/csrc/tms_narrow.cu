@@ -428,6 +428,114 @@ __device__ __forceinline__ bool separated(const float w[4], const SplitVec &e1, 
     return gap > need;
 }
 
+// a - b of two vectors with bounds
+__device__ __forceinline__ SplitVec sub_vec(const SplitVec &a, const SplitVec &b) {
+    const float u = 5.9604645e-08f;
+    SplitVec r;
+    float vm = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        r.v[c] = a.v[c] - b.v[c];
+        vm = fmaxf(vm, fabsf(r.v[c]));
+    }
+    r.E = (a.E + b.E + u * vm) * 1.001f;
+    r.M = vm;
+    return r;
+}
+
+// an upper bound of |v|^2 for the exact vector
+__device__ __forceinline__ float sq_hi(const SplitVec &v) {
+    float q = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) q = fmaf(v.v[c], v.v[c], q);
+    return (q + 8.0f * v.E * v.M + 4.0f * v.E * v.E) * 1.0005f;
+}
+
+// a lower bound of |det [e1 e2 f1 f2]| from the two planes' Plucker coordinates
+__device__ __forceinline__ float det_lo_of(const float mE[6], float epsE, const float mF[6], float epsF) {
+    const float u = 5.9604645e-08f;
+    const float det = mE[0] * mF[5] - mE[1] * mF[4] + mE[2] * mF[3] + mE[3] * mF[2] - mE[4] * mF[1] +
+                      mE[5] * mF[0];
+    float tE = 0.0f, tF = 0.0f, sabs = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        tE += fabsf(mE[k]);
+        tF += fabsf(mF[k]);
+        sabs = fmaf(fabsf(mE[k]), fabsf(mF[5 - k]), sabs);
+    }
+    return fabsf(det) - (epsF * tE + epsE * tF + 6.0f * epsE * epsF + (8.0f * u) * sabs) * 1.01f;
+}
+
+// Quad-level form of the separating-axis test: true when every one of the four
+// triangle pairs of the quad candidate is proven to have margin below -delta.
+// A triangle's vertices are among its quad's, so its projected interval lies
+// inside the quad's: a gap between the quads' intervals larger than
+// 2 delta (D_A + D_B) is larger than 2 delta (D_Ta + D_Tb) for every pair.
+// delta uses the largest kappa of the four pairs.  Axes: the two longest
+// duals of each quad's first triangle.
+__device__ __forceinline__ bool quad_sat_reject(const float4 QA[4][2], const float4 QB[4][2],
+                                                double tau) {
+    const float u = 5.9604645e-08f;
+    // vertices v0 (i,k), v1 (i+1,k), v2 (i,k+1), v3 (i+1,k+1); T1 = (v1, v0, v2),
+    // T2 = (v2, v3, v1): T1's edges are (v1 - v0, v2 - v0), T2's (v2 - v3, v1 - v3)
+    const SplitVec a1 = split_vec(QA[1], QA[0]), a2 = split_vec(QA[2], QA[0]);
+    const SplitVec a3 = split_vec(QA[3], QA[0]);
+    const SplitVec b1 = split_vec(QB[1], QB[0]), b2 = split_vec(QB[2], QB[0]);
+    const SplitVec b3 = split_vec(QB[3], QB[0]);
+    const SplitVec r0 = split_vec(QB[0], QA[0]);
+    float mA1[6], mB1[6], epsA1, epsB1;
+    plucker(a1, a2, mA1, epsA1);
+    plucker(b1, b2, mB1, epsB1);
+    float kmax;
+    {
+        const SplitVec a23 = sub_vec(a2, a3), a13 = sub_vec(a1, a3);
+        const SplitVec b23 = sub_vec(b2, b3), b13 = sub_vec(b1, b3);
+        float mA2[6], mB2[6], epsA2, epsB2;
+        plucker(a23, a13, mA2, epsA2);
+        plucker(b23, b13, mB2, epsB2);
+        const float FA[2] = {sq_hi(a1) + sq_hi(a2), sq_hi(a23) + sq_hi(a13)};
+        const float FB[2] = {sq_hi(b1) + sq_hi(b2), sq_hi(b23) + sq_hi(b13)};
+        const float d11 = det_lo_of(mA1, epsA1, mB1, epsB1), d12 = det_lo_of(mA1, epsA1, mB2, epsB2);
+        const float d21 = det_lo_of(mA2, epsA2, mB1, epsB1), d22 = det_lo_of(mA2, epsA2, mB2, epsB2);
+        const float f11 = (FA[0] + FB[0]) * 1.0005f, f12 = (FA[0] + FB[1]) * 1.0005f;
+        const float f21 = (FA[1] + FB[0]) * 1.0005f, f22 = (FA[1] + FB[1]) * 1.0005f;
+        const float F4[4] = {f11 * f11, f12 * f12, f21 * f21, f22 * f22};
+        const float D[4] = {d11, d12, d21, d22};
+        kmax = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!(D[k] > 0.0f) || !(F4[k] <= 1e10f * D[k])) return false;
+            kmax = fmaxf(kmax, F4[k] / D[k]);
+        }
+    }
+    const float delta = 2.0f * (float)tau * 1.001f + 9.1e-13f * kmax * 1.001f;
+    int k1, k2;
+    float w[4];
+#pragma unroll
+    for (int ax = 0; ax < 4; ++ax) {
+        if (ax == 0) top2_duals(mA1, k1, k2);
+        if (ax == 2) top2_duals(mB1, k1, k2);
+        dual_dir(ax < 2 ? mA1 : mB1, (ax & 1) ? k2 : k1, w);
+        const float w1 = fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]) + fabsf(w[3]);
+        const float p1 = dot4(w, a1), p2 = dot4(w, a2), p3 = dot4(w, a3);
+        const float ea = w1 * fmaxf(fmaxf(fmaf(4.01f * u, a1.M, a1.E), fmaf(4.01f * u, a2.M, a2.E)),
+                                    fmaf(4.01f * u, a3.M, a3.E));
+        const float q0 = dot4(w, r0);
+        const float s1 = q0 + dot4(w, b1), s2 = q0 + dot4(w, b2), s3 = q0 + dot4(w, b3);
+        const float eb = w1 * (fmaf(4.01f * u, r0.M, r0.E) +
+                               fmaxf(fmaxf(fmaf(4.01f * u, b1.M, b1.E), fmaf(4.01f * u, b2.M, b2.E)),
+                                     fmaf(4.01f * u, b3.M, b3.E))) +
+                         u * fmaxf(fmaxf(fabsf(s1), fabsf(s2)), fabsf(s3));
+        const float xl = fminf(fminf(0.0f, p1), fminf(p2, p3)), xh = fmaxf(fmaxf(0.0f, p1), fmaxf(p2, p3));
+        const float yl = fminf(fminf(q0, s1), fminf(s2, s3)), yh = fmaxf(fmaxf(q0, s1), fmaxf(s2, s3));
+        const float DX = (xh - xl) + 2.0f * ea, DY = (yh - yl) + 2.0f * eb;
+        const float need = (2.0f * delta * (DX + DY) + ea + eb) * 1.001f;
+        const float gap = fmaxf(yl - xh, xl - yh) * (1.0f - 4.0f * u);
+        if (gap > need) return true;
+    }
+    return false;
+}
+
 // true when the separating-axis test proves the margin below -delta (not a hit,
 // also for an FP64 solve of the same system)
 __device__ __forceinline__ bool fp32_sat_reject(const float4 X[3][2], const float4 Y[3][2],
@@ -548,26 +656,29 @@ __device__ __forceinline__ bool narrow_fp64(const MeshDev &ma, const MeshDev &mb
 }
 
 // Stage 1: every triangle pair of every candidate through the FP32 tests;
-// pairs they cannot reject go to the survivor list.  Per lane one candidate:
-// for quads, its four triangle pairs share the quads' vertices.  A pair whose
-// (widened) triangle boxes overlap meets the separating-axis prefilter; the
-// few it cannot reject wait in a per-warp queue in shared memory, and the
-// verified solve runs on that queue 32 pairs at a time, so that the expensive
-// certificate never runs with most lanes idle.
+// pairs they cannot reject go to the survivor list.  Quad candidates first meet
+// the quad-level separating-axis test, which clears all four triangle pairs at
+// once for most of them; the rest wait in a per-warp candidate queue and are
+// taken 32 at a time through the per-pair path: the (widened) triangle boxes,
+// the triangle-level separating-axis test, and for the few pairs left a
+// second queue feeding the verified solve 32 pairs at a time -- so that no
+// expensive step runs with most lanes idle.
 template <int FACE>
 __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
     constexpr int kW = 8, kQ = 32 + 4 * 32;
-    __shared__ uint32_t q_cand[kW][kQ];
+    __shared__ uint32_t q_cand[kW][kQ];          // triangle pairs for the verified solve
     __shared__ uint8_t q_sub[kW][kQ];
+    __shared__ uint32_t c_cand[kW][64];          // quad candidates for the per-pair path
     if (a.ctr->cand > a.cand_cap) return;
     const unsigned long long n = a.ctr->cand;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
-    unsigned long long n_sat = 0, n_full = 0;   // pairs through each test, per warp
-    unsigned qn = 0;                            // queued pairs (warp-uniform)
+    unsigned long long n_quad = 0, n_sat = 0, n_full = 0;   // tests run, per warp
+    unsigned qn = 0;                                        // queued pairs (warp-uniform)
+    unsigned cn = 0;                                        // queued candidates
 
-    // the verified solve of queue items [base, base + cnt)
+    // the verified solve of pair-queue items [base, base + cnt)
     auto drain = [&](unsigned base, unsigned cnt) {
         bool keep = false;
         uint32_t ta = 0, tb = 0, pair = 0;
@@ -594,6 +705,51 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
             sv.pad = 0;
             a.surv[pos] = sv;
         }
+    };
+    // one triangle pair through the box and separating-axis tests; the pairs
+    // they cannot reject join the pair queue (all lanes call it together)
+    auto pair_tests = [&](bool valid, uint32_t g, int sub, const float4 X[3][2], const float4 Y[3][2],
+                          bool boxes) {
+        const bool tested = valid && (!boxes || split_boxes_overlap(X, Y));
+        const bool need = tested && !fp32_sat_reject(X, Y, a.tau);
+        n_sat += __popc(__ballot_sync(FULL, tested));
+        const uint32_t want = __ballot_sync(FULL, need);
+        if (need) {
+            const unsigned slot = qn + __popc(want & lt);
+            q_cand[warp][slot] = g;
+            q_sub[warp][slot] = (uint8_t)sub;
+        }
+        qn += __popc(want);
+    };
+    auto drain_full = [&]() {
+        __syncwarp();
+        while (qn >= 32) {
+            qn -= 32;
+            drain(qn, 32);
+            __syncwarp();
+        }
+    };
+    // the per-pair path for candidate-queue items [base, base + cnt)
+    auto cand_round = [&](unsigned base, unsigned cnt) {
+        const bool valid = (unsigned)lane < cnt;
+        const uint32_t g = valid ? c_cand[warp][base + lane] : 0u;
+        Cand cd;
+        cd.faceA = cd.faceB = cd.pair = 0;
+        if (valid) cd = a.cand[g];
+        const int2 pr = a.pairs[valid ? cd.pair : 0];
+        float4 QA[4][2], QB[4][2];
+        if (valid) {
+            gather_quad_split(a.meshes[pr.x], cd.faceA, QA);
+            gather_quad_split(a.meshes[pr.y], cd.faceB, QB);
+        }
+#pragma unroll 1
+        for (int sub = 0; sub < 4; ++sub) {
+            float4 X[3][2], Y[3][2];
+            quad_tri(QA, sub & 1, X);
+            quad_tri(QB, sub >> 1, Y);
+            pair_tests(valid, g, sub, X, Y, true);
+        }
+        drain_full();
     };
 
     for (unsigned long long g0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x - lane;
@@ -622,51 +778,46 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
             continue;
         }
         const int2 pr = a.pairs[valid ? cd.pair : 0];
-        float4 QA[4][2], QB[4][2];
-        if (FACE == 1 && valid) {
-            // the quads' four vertices once, (i,k) (i+1,k) (i,k+1) (i+1,k+1)
-            gather_quad_split(a.meshes[pr.x], cd.faceA, QA);
-            gather_quad_split(a.meshes[pr.y], cd.faceB, QB);
-        }
-        const int nsub = FACE == 0 ? 1 : 4;
-#pragma unroll 1
-        for (int sub = 0; sub < nsub; ++sub) {
-            bool tested = false, need = false;
+        if (FACE == 0) {
+            float4 X[3][2], Y[3][2];
             if (valid) {
-                float4 X[3][2], Y[3][2];
-                if (FACE == 0) {
-                    gather_split(a.meshes[pr.x], cd.faceA, X);
-                    gather_split(a.meshes[pr.y], cd.faceB, Y);
-                    tested = true;
-                } else {
-                    quad_tri(QA, sub & 1, X);
-                    quad_tri(QB, sub >> 1, Y);
-                    // the two triangles' boxes first: disjoint boxes, no intersection
-                    tested = split_boxes_overlap(X, Y);
-                }
-                need = tested && !fp32_sat_reject(X, Y, a.tau);
+                gather_split(a.meshes[pr.x], cd.faceA, X);
+                gather_split(a.meshes[pr.y], cd.faceB, Y);
             }
-            n_sat += __popc(__ballot_sync(FULL, tested));
+            pair_tests(valid, (uint32_t)g, 0, X, Y, false);
+            drain_full();
+        } else {
+            // the quads' four vertices, (i,k) (i+1,k) (i,k+1) (i+1,k+1), and the
+            // quad-level test
+            bool need = false;
+            if (valid) {
+                float4 QA[4][2], QB[4][2];
+                gather_quad_split(a.meshes[pr.x], cd.faceA, QA);
+                gather_quad_split(a.meshes[pr.y], cd.faceB, QB);
+                need = !quad_sat_reject(QA, QB, a.tau);
+            }
+            n_quad += __popc(__ballot_sync(FULL, valid));
             const uint32_t want = __ballot_sync(FULL, need);
-            if (need) {
-                const unsigned slot = qn + __popc(want & lt);
-                q_cand[warp][slot] = (uint32_t)g;
-                q_sub[warp][slot] = (uint8_t)sub;
-            }
-            qn += __popc(want);
-        }
-        __syncwarp();
-        while (qn >= 32) {
-            qn -= 32;
-            drain(qn, 32);
+            if (need) c_cand[warp][cn + __popc(want & lt)] = (uint32_t)g;
+            cn += __popc(want);
             __syncwarp();
+            if (cn >= 32) {
+                cn -= 32;
+                cand_round(cn, 32);
+                __syncwarp();
+            }
         }
+    }
+    if (FACE == 1 && cn) {
+        cand_round(0, cn);
+        __syncwarp();
     }
     if (qn) {
         drain(0, qn);
         __syncwarp();
     }
     if (lane == 0) {
+        if (n_quad) atomicAdd(&a.ctr->quad, n_quad);
         if (n_sat) atomicAdd(&a.ctr->sat, n_sat);
         if (n_full) atomicAdd(&a.ctr->fp32, n_full);
     }
