@@ -155,10 +155,10 @@ struct Plan {
         TMS_CK(dalloc(&erank, ent_cap));
         TMS_CK(dalloc(&grouped, ent_cap));
         // cell table: a power of two, all slots free (zero); distinct cells are
-        // far fewer than entries, so it starts at an eighth of the entry
-        // capacity (L2-resident) and grows when a search finds it crowded
+        // far fewer than entries, so it starts at a sixteenth of the entry
+        // capacity (L2-resident) and grows when a search finds it over half full
         tsize = 1024;
-        const unsigned long long want = (prm.inject & 8u) ? 0 : ent_cap / 8;
+        const unsigned long long want = (prm.inject & 8u) ? 0 : ent_cap / 16;
         while ((tsize < want || tsize < tsize_min) && tsize < (1ULL << 31)) tsize <<= 1;
         TMS_CK(dalloc(&tkey, tsize));
         TMS_CK(dalloc(&tcnt, tsize));

@@ -19,7 +19,7 @@
 //   k_group_scatter  writes every entry's face id to its cell's A or B list.
 // The order of a cell's entries is left to the atomics; the search's output
 // does not depend on it.  The table is sized from the entry capacity (an
-// eighth of it, so that it stays in L2 and a scan of all of it is cheap); a
+// sixteenth of it, so that it stays in L2 and a scan of all of it is cheap); a
 // search that finds it over half full, or full, is run again with a table four
 // times larger.
 #include <cuda_runtime.h>
