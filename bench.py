@@ -36,6 +36,7 @@ WORKLOAD = dict(workload="mesh-vs-mesh search, 4096x512 vs 4096x512 vertex grids
                 N=4096, M=512, triangles_per_mesh=4186112)
 ENTRY_BYTES = 8 + 4                   # face-cell entry: u64 key, u32 face id
 NOMINAL_SM_MAX_MHZ = 2070              # GB300 maximum SM clock
+REF_MAX_STEPS = 10                     # timed oracle searches of the reference arm
 # FP32 operations of one verified FP32 solve (an FMA counts 2): 20 system
 # entries with error bounds (12 each), elimination on [A | I | r] (98), back
 # substitution for five right-hand sides (80), the bound matrix W (32),
@@ -129,7 +130,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
         time.sleep(0.3)
@@ -377,26 +378,34 @@ def cpu_baseline(pair):
 
 
 def run_reference(args, ws, rank, local):
+    """The oracle (CPU, FP64) on the same workload and metric.  Its cost is
+    dominated by the bounding-volume hierarchy over mesh B, so a step cannot be
+    a smaller sample of the search: every step is one complete search, and the
+    steps are capped (REF_MAX_STEPS timed, one warm-up) so that the run ends in
+    well under a minute on the host cores."""
     if rank != 0:
         return
     import oracle
     oracle.build()
     pair = build_workload("cpu")
     OA, OB = oracle.OMesh.from_grid(pair.A), oracle.OMesh.from_grid(pair.B)
-    for _ in range(args.warmup):
+    steps, warmup = max(1, min(args.steps, REF_MAX_STEPS)), min(args.warmup, 1)
+    for _ in range(warmup):
         oracle.search(OA, OB)
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
         oracle.search(OA, OB)
         times.append((time.perf_counter() - t0) * 1e3)
     v = sum(times) / len(times)
+    sample = (f"the full workload per step (one complete search); {steps} timed steps and "
+              f"{warmup} warm-up of the {args.steps} + {args.warmup} requested")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
+            "steps": steps, "warmup": warmup, "ms_per_step": v,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded manifold-like meshes)", "config": dict(WORKLOAD),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "the full workload per step (one complete search)"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -404,7 +413,7 @@ def run_reference(args, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tms", choices=["tms", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
