@@ -509,13 +509,15 @@ __device__ __forceinline__ bool quad_sat_reject(const float4 QA[4][2], const flo
         }
     }
     const float delta = 2.0f * (float)tau * 1.001f + 9.1e-13f * kmax * 1.001f;
-    int k1, k2;
-    float w[4];
-#pragma unroll
+    int kA1, kA2, kB1, kB2;
+    top2_duals(mA1, kA1, kA2);
+    top2_duals(mB1, kB1, kB2);
+#pragma unroll 1
     for (int ax = 0; ax < 4; ++ax) {
-        if (ax == 0) top2_duals(mA1, k1, k2);
-        if (ax == 2) top2_duals(mB1, k1, k2);
-        dual_dir(ax < 2 ? mA1 : mB1, (ax & 1) ? k2 : k1, w);
+        float m[6], w[4];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) m[k] = ax < 2 ? mA1[k] : mB1[k];
+        dual_dir(m, ax == 0 ? kA1 : (ax == 1 ? kA2 : (ax == 2 ? kB1 : kB2)), w);
         const float w1 = fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]) + fabsf(w[3]);
         const float p1 = dot4(w, a1), p2 = dot4(w, a2), p3 = dot4(w, a3);
         const float ea = w1 * fmaxf(fmaxf(fmaf(4.01f * u, a1.M, a1.E), fmaf(4.01f * u, a2.M, a2.E)),
@@ -579,18 +581,21 @@ __device__ __forceinline__ bool fp32_sat_reject(const float4 X[3][2], const floa
     if (!(det_lo > 0.0f) || !(F4 <= 1e10f * det_lo)) return false;
     const float kappa = F4 / det_lo * 1.001f;
     const float delta = 2.0f * (float)tau * 1.001f + 9.1e-13f * kappa;
-    int k1, k2;
-    float w[4];
-    top2_duals(mE, k1, k2);
-    dual_dir(mE, k1, w);
-    if (separated(w, e1, e2, r, s1, s3, delta)) return true;
-    dual_dir(mE, k2, w);
-    if (separated(w, e1, e2, r, s1, s3, delta)) return true;
-    top2_duals(mF, k1, k2);
-    dual_dir(mF, k1, w);
-    if (separated(w, e1, e2, r, s1, s3, delta)) return true;
-    dual_dir(mF, k2, w);
-    return separated(w, e1, e2, r, s1, s3, delta);
+    int kE1, kE2, kF1, kF2;
+    top2_duals(mE, kE1, kE2);
+    top2_duals(mF, kF1, kF2);
+    // one loop over the four axes (a small kernel fetches its code faster);
+    // the plane of each axis is chosen by selects, not by an indexed array
+#pragma unroll 1
+    for (int ax = 0; ax < 4; ++ax) {
+        float m[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) m[k] = ax < 2 ? mE[k] : mF[k];
+        float w[4];
+        dual_dir(m, ax == 0 ? kE1 : (ax == 1 ? kE2 : (ax == 2 ? kF1 : kF2)), w);
+        if (separated(w, e1, e2, r, s1, s3, delta)) return true;
+    }
+    return false;
 }
 
 // (theta, s) estimate for weights (u, v) in triangle t (formulas after Eq. (precise))
