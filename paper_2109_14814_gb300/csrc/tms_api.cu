@@ -87,14 +87,12 @@ struct Plan {
     uint64_t *ek = nullptr;
     uint32_t *ev = nullptr, *eslot = nullptr, *erank = nullptr, *grouped = nullptr;
     unsigned long long tsize = 0, tsize_min = 0;
-    unsigned long long *tkey = nullptr, *ckey = nullptr;
-    uint2 *cxy = nullptr;
+    unsigned long long *tkey = nullptr;
+    CellRec *crec = nullptr;
     uint2 *tcnt = nullptr;
     uint2 *tstart = nullptr;
     void *sort_scratch = nullptr;
     unsigned long long *partials = nullptr;
-    uint32_t *cstart = nullptr, *cb = nullptr;
-    unsigned long long *toff = nullptr;
     Cand *cand = nullptr, *surv = nullptr;
     float4 *split = nullptr;          // FP32 split vertex copies of all meshes
     unsigned long long split_total = 0;
@@ -118,14 +116,14 @@ struct Plan {
     unsigned long long last_use = 0;
 
     void free_scratch() {
-        void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, ckey, cxy, tcnt, tstart,
-                        sort_scratch, cstart, cb, toff, cand, surv, hits, hk, hk2, okeys, hv, hv2,
+        void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, crec, tcnt, tstart,
+                        sort_scratch, cand, surv, hits, hk, hk2, okeys, hv, hv2,
                         keep, kscan};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         bmA = bmH = nullptr; ek = nullptr; ev = eslot = erank = grouped = nullptr;
-        tkey = ckey = nullptr; cxy = nullptr; tcnt = nullptr; tstart = nullptr;
-        sort_scratch = nullptr; cstart = cb = nullptr; toff = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
+        tkey = nullptr; crec = nullptr; tcnt = nullptr; tstart = nullptr;
+        sort_scratch = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
         hv = hv2 = keep = kscan = nullptr;
         if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
     }
@@ -166,12 +164,7 @@ struct Plan {
         TMS_CK(cudaMemset(tkey, 0, tsize * sizeof(unsigned long long)));
         TMS_CK(cudaMemset(tcnt, 0, tsize * sizeof(uint2)));
         // per cell: a cell holding both meshes has at least two entries
-        const unsigned long long cell_cap = ent_cap / 2 + 1;
-        TMS_CK(dalloc(&ckey, cell_cap));
-        TMS_CK(dalloc(&cxy, cell_cap));
-        TMS_CK(dalloc(&cstart, cell_cap));
-        TMS_CK(dalloc(&cb, cell_cap));
-        TMS_CK(dalloc(&toff, cell_cap));
+        TMS_CK(dalloc(&crec, ent_cap / 2 + 1));
         TMS_CK(dalloc(reinterpret_cast<unsigned char **>(&sort_scratch),
                       radix_scratch_size(hit_cap, 2 * tri_bits + pair_bits)));
         TMS_CK(dalloc(&cand, cand_cap));
@@ -210,7 +203,7 @@ struct Plan {
         ga.ent_key = ek; ga.ent_face = ev; ga.d_n = &d_ctr->entries; ga.cap = ent_cap;
         ga.ent_slot = eslot; ga.ent_rank = erank;
         ga.tkey = tkey; ga.tcnt = tcnt; ga.tstart = tstart; ga.tsize = tsize;
-        ga.cell_key = ckey; ga.cell_xy = cxy; ga.grids = d_grids; ga.cell_start = cstart; ga.cell_b = cb; ga.tile_off = toff;
+        ga.cells = crec; ga.grids = d_grids;
         ga.grouped = grouped; ga.partials = partials; ga.ctr = d_ctr;
         kernels += 1;
         mark(1, s);
@@ -273,7 +266,7 @@ struct Plan {
         mark(9, s);
 
         EmitArgs ea;
-        ea.cell_key = ckey; ea.cell_xy = cxy; ea.vals = grouped; ea.cell_start = cstart; ea.cell_b = cb; ea.tile_off = toff;
+        ea.cells = crec; ea.vals = grouped;
         ea.grids = d_grids; ea.meshes = d_meshes; ea.pairs = d_pairs; ea.ctr = d_ctr;
         ea.ent_cap = ent_cap; ea.cand = cand; ea.cand_cap = cand_cap; ea.moller = p.moller;
         launch_emit(ea, prec, fl, grid * 4, s);

@@ -381,6 +381,16 @@ void scan_u64(const unsigned long long *in, unsigned long long *out,
               unsigned long long *partials, unsigned long long *d_total, int grid,
               cudaStream_t st);
 
+// One cell holding faces of both meshes, as the emission reads it (32 bytes).
+struct CellRec {
+    uint32_t start;                // first A entry in `grouped`
+    uint32_t bstart;               // first B entry
+    unsigned long long tile_off;   // exclusive scan of the 32 x 32 tiles of nA x nB
+    uint2 xy;                      // the cell's coordinates, 4 x u16
+    uint32_t pair;
+    uint32_t pad;
+};
+
 // Grouping of the face-cell entries by (pair, cell), mesh A's faces first:
 // an open-addressing table of the (pair, cell) keys counts each cell's A and B
 // entries and ranks every entry within its (cell, role); the cells holding
@@ -397,13 +407,9 @@ struct GroupArgs {
     uint2 *tcnt;                   // [tsize] A and B entry counts
     uint2 *tstart;                 // [tsize] the slot's A and B list starts (kNoCell: no cell)
     unsigned long long tsize;      // power of two; grown by the host when over half full
-    // per compacted cell, [cap]
-    unsigned long long *cell_key;
-    uint2 *cell_xy;                // the cell's coordinates, 4 x u16
+    // per compacted cell, [cap / 2]
+    CellRec *cells;
     const Grid *grids;             // per pair (cells per coordinate)
-    uint32_t *cell_start;          // first A entry in `grouped`
-    uint32_t *cell_b;              // first B entry
-    unsigned long long *tile_off;  // exclusive scan of the 32 x 32 tiles of nA x nB
     uint32_t *grouped;             // [cap] face ids by cell, A then B
     unsigned long long *partials;  // [5 * 1024]
     Counters *ctr;
@@ -414,12 +420,8 @@ void launch_group_count(const GroupArgs &a, int grid, cudaStream_t st);
 void launch_group_cells(const GroupArgs &a, int grid, cudaStream_t st);
 
 struct EmitArgs {
-    const unsigned long long *cell_key;   // pair << 31 | cell
-    const uint2 *cell_xy;          // the cell's coordinates, 4 x u16
+    const CellRec *cells;          // the cells holding faces of both meshes
     const uint32_t *vals;          // face ids grouped by cell
-    const uint32_t *cell_start;
-    const uint32_t *cell_b;
-    const unsigned long long *tile_off;
     const Grid *grids;
     const MeshDev *meshes;
     const int2 *pairs;

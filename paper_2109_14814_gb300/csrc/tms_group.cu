@@ -207,19 +207,22 @@ __global__ void __launch_bounds__(kCellScanBlock) k_cells_down(GroupArgs a) {
                 const unsigned long long c = ex[0];
                 const uint2 cnt = a.tcnt[slot];
                 const unsigned long long key = a.tkey[slot] - 1;
-                a.cell_key[c] = key;
+                CellRec rec;
+                rec.pair = (uint32_t)(key >> 31);
                 // the cell's coordinates (the emission's owner test needs them per tile)
-                const Grid &g = a.grids[(uint32_t)(key >> 31)];
+                const Grid &g = a.grids[rec.pair];
                 uint32_t cell = (uint32_t)(key & 0x7FFFFFFFu), cc[4];
 #pragma unroll
                 for (int d = 0; d < 4; ++d) {
                     cc[d] = cell % (uint32_t)g.n[d];
                     cell /= (uint32_t)g.n[d];
                 }
-                a.cell_xy[c] = make_uint2(cc[0] | (cc[1] << 16), cc[2] | (cc[3] << 16));
-                a.cell_start[c] = (uint32_t)ex[1];
-                a.cell_b[c] = (uint32_t)ex[1] + cnt.x;
-                a.tile_off[c] = ex[2];
+                rec.xy = make_uint2(cc[0] | (cc[1] << 16), cc[2] | (cc[3] << 16));
+                rec.start = (uint32_t)ex[1];
+                rec.bstart = (uint32_t)ex[1] + cnt.x;
+                rec.tile_off = ex[2];
+                rec.pad = 0;
+                a.cells[c] = rec;
                 // the scatter's one gather: both list starts of the slot
                 a.tstart[slot] = make_uint2((uint32_t)ex[1], (uint32_t)ex[1] + cnt.x);
             } else {

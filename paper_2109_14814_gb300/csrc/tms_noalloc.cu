@@ -85,13 +85,11 @@ struct Buffers {
     uint32_t *bmA, *bmH;
     uint64_t *ek;
     uint32_t *ev, *eslot, *erank, *grouped;
-    unsigned long long *tkey, *ckey;
-    uint2 *cxy;
+    unsigned long long *tkey;
+    CellRec *crec;
     uint2 *tcnt;
     uint2 *tstart;
     void *sort_scratch;
-    uint32_t *cstart, *cb;
-    unsigned long long *toff;
     Cand *cand, *surv;
     tms_hit *hits;
     uint64_t *hk, *hk2, *okeys;
@@ -130,11 +128,7 @@ size_t carve(unsigned char *base, Buffers &b) {
     b.grouped = c.take<uint32_t>(kEntCap);
     b.tstart = c.take<uint2>(kTableSize);
     // per cell: a cell holding both meshes has at least two entries
-    b.ckey = c.take<unsigned long long>(kEntCap / 2);
-    b.cxy = c.take<uint2>(kEntCap / 2);
-    b.cstart = c.take<uint32_t>(kEntCap / 2);
-    b.cb = c.take<uint32_t>(kEntCap / 2);
-    b.toff = c.take<unsigned long long>(kEntCap / 2);
+    b.crec = c.take<CellRec>(kEntCap / 2);
     const size_t broad_end = c.off;
     // narrow phase and merge, over the broad phase's bytes
     c.off = phase;
@@ -275,7 +269,7 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     ga.ent_key = b.ek; ga.ent_face = b.ev; ga.d_n = &b.ctr->entries; ga.cap = kEntCap;
     ga.ent_slot = b.eslot; ga.ent_rank = b.erank;
     ga.tkey = b.tkey; ga.tcnt = b.tcnt; ga.tstart = b.tstart; ga.tsize = kTableSize;
-    ga.cell_key = b.ckey; ga.cell_xy = b.cxy; ga.grids = b.grids; ga.cell_start = b.cstart; ga.cell_b = b.cb; ga.tile_off = b.toff;
+    ga.cells = b.crec; ga.grids = b.grids;
     ga.grouped = b.grouped; ga.partials = b.partials; ga.ctr = b.ctr;
     FacePassArgs fa;
     memset(&fa, 0, sizeof(fa));
@@ -315,7 +309,7 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     launch_group_count(ga, grid, s);
     launch_group_cells(ga, grid, s);
     EmitArgs ea;
-    ea.cell_key = b.ckey; ea.cell_xy = b.cxy; ea.vals = b.grouped; ea.cell_start = b.cstart; ea.cell_b = b.cb; ea.tile_off = b.toff;
+    ea.cells = b.crec; ea.vals = b.grouped;
     ea.grids = b.grids; ea.meshes = b.tables->meshes; ea.pairs = b.tables->pairs; ea.ctr = b.ctr;
     ea.ent_cap = kEntCap; ea.cand = b.cand; ea.cand_cap = kCandCap; ea.moller = p.moller;
     launch_emit(ea, p.precision, p.face_level, grid * 4, s);

@@ -183,18 +183,23 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         unsigned long long lo = 0, hi = ncell - 1;
         while (lo < hi) {
             unsigned long long mid = (lo + hi + 1) >> 1;
-            if (a.tile_off[mid] <= t_begin) lo = mid; else hi = mid - 1;
+            if (a.cells[mid].tile_off <= t_begin) lo = mid; else hi = mid - 1;
         }
         c = lo;
     }
+    // the pair's face-box arrays, looked up again only when the pair changes
+    uint32_t cached_pair = 0xFFFFFFFFu;
+    const void *fbA = nullptr, *fbB = nullptr;
+    int2 pr = make_int2(0, 0);
     for (unsigned long long t = t_begin; t < t_end; ++t) {
-        while (c + 1 < ncell && a.tile_off[c + 1] <= t) ++c;
-        const uint32_t s = a.cell_start[c];
-        const uint32_t bstart = a.cell_b[c];
-        const uint32_t e = (c + 1 < ncell) ? a.cell_start[c + 1] : (uint32_t)nent;
+        while (c + 1 < ncell && a.cells[c + 1].tile_off <= t) ++c;
+        const CellRec cr = a.cells[c];
+        const uint32_t s = cr.start;
+        const uint32_t bstart = cr.bstart;
+        const uint32_t e = (c + 1 < ncell) ? a.cells[c + 1].start : (uint32_t)nent;
         const uint32_t nAc = bstart - s;
         const uint32_t tA = (nAc + kTile - 1) / kTile;
-        const uint32_t local = (uint32_t)(t - a.tile_off[c]);
+        const uint32_t local = (uint32_t)(t - cr.tile_off);
         const uint32_t a0 = s + (local % tA) * kTile, b0 = bstart + (local / tA) * kTile;
         const int nAt0 = (int)min((uint32_t)kTile, bstart - a0);
         const int nBt0 = (int)min((uint32_t)kTile, e - b0);
@@ -202,12 +207,16 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         const bool swapAB = nBt0 > nAt0;
         const uint32_t l0 = swapAB ? b0 : a0, m0 = swapAB ? a0 : b0;
         const int nAt = swapAB ? nBt0 : nAt0, nBt = swapAB ? nAt0 : nBt0;
-        const uint32_t pair = (uint32_t)(a.cell_key[c] >> 31);
-        const uint2 cur = a.cell_xy[c];
+        const uint32_t pair = cr.pair;
+        const uint2 cur = cr.xy;
         const Grid &gr = a.grids[pair];
+        if (pair != cached_pair) {
+            pr = a.pairs[pair];
+            fbA = a.meshes[pr.x].fbox;
+            fbB = a.meshes[pr.y].fbox;
+            cached_pair = pair;
+        }
         // own entry (the lanes' side) in registers, the other side in shared memory
-        const int2 pr = a.pairs[pair];
-        const void *fbA = a.meshes[pr.x].fbox, *fbB = a.meshes[pr.y].fbox;
         const void *fbL = swapAB ? fbB : fbA, *fbM = swapAB ? fbA : fbB;
         EBox<PREC> abox;
         uint32_t amask = 0, aface = 0;
