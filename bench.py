@@ -345,6 +345,12 @@ def run_tms(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(pair)
 
+    extras = None
+    if args.extras:
+        extras = {"plain_fp64": plain_fp64(tms, A, B, out, stream, flush, h),
+                  "batched": batched_search(tms, device, stream, flush),
+                  "adjoint": adjoint_timing(tms, device, stream)}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
@@ -361,8 +367,102 @@ def run_tms(args, ws, rank, local):
         "source_hash": source_hash(),
         "stage_ms": stage_ms, "wall_s": wall,
     }
+    if extras is not None:
+        line["extras"] = extras
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _timed(fn, stream, flush, steps):
+    """Median CUDA-event time (ms) of fn() over `steps` runs, L2 flushed before each."""
+    ts = []
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def plain_fp64(tms, A, B, out, stream, flush, mixed_hits):
+    """The same search with FP64 boxes and cell keys and no FP32 filters (the
+    plain path): its time and whether it finds the identical hit set."""
+    kw = dict(precision=0, narrow_filter=0)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            h = tms.search(A, B, out=out, stream=stream, **kw)
+        same = (torch.equal(h.triA, mixed_hits.triA) and torch.equal(h.triB, mixed_hits.triB))
+    ms = _timed(lambda: tms.search(A, B, out=out, stream=stream, **kw), stream, flush, 20)
+    return {"ms_per_search": ms, "hits": len(h), "identical_hit_set_to_mixed": bool(same),
+            "params": "precision=0 (FP64 boxes and keys), narrow_filter=0 (every pair to FP64)"}
+
+
+def batched_search(tms, device, stream, flush, n_pairs=256):
+    """The batched search of the 256 uneven mesh pairs of the alpha sweep (one
+    CUDA graph replay per batch): total and per-pair time."""
+    import synth
+    sizes = synth.config4_sizes(n_pairs=n_pairs)
+    pairs = [synth.config4_pair(p, n_pairs=n_pairs, sizes=sizes) for p in range(n_pairs)]
+    XA = [p.A.X.to(device).contiguous() for p in pairs]
+    XB = [p.B.X.to(device).contiguous() for p in pairs]
+    As = [tms.Mesh(x, p.A.s, True) for x, p in zip(XA, pairs)]
+    Bs = [tms.Mesh(x, p.B.s, True) for x, p in zip(XB, pairs)]
+    tris = sum(2 * p.A.N * (p.A.M - 1) + 2 * p.B.N * (p.B.M - 1) for p in pairs)
+    out = torch.empty((1 << 18, tms.HIT_BYTES), dtype=torch.uint8, device=device)
+    offs = torch.empty(n_pairs + 1, dtype=torch.int64, device=device)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            h = tms.search_batched(As, Bs, out=out, offsets=offs, stream=stream)
+    stats = tms.last_stats(stream)
+    ms = _timed(lambda: tms.search_batched(As, Bs, out=out, offsets=offs, stream=stream),
+                stream, flush, 10)
+    return {"pairs": n_pairs, "triangles_total": tris, "ms_per_batch": ms,
+            "ms_per_pair": ms / n_pairs, "hits": len(h), "launches_per_batch": stats["kernels"],
+            "entries": stats["entries"], "candidates": stats["candidates"]}
+
+
+def adjoint_timing(tms, device, stream):
+    """tms_backward on the 512-hit differentiation workload (config 5): time per
+    call and FP64 rate at ~150 FLOPs per hit."""
+    import synth
+    pair = synth.config5()
+    XA = pair.A.X.to(device).contiguous()
+    XB = pair.B.X.to(device).contiguous()
+    A = tms.Mesh(XA, pair.A.s, True)
+    B = tms.Mesh(XB, pair.B.s, True)
+    hits = tms.search(A, B, stream=stream)
+    n = len(hits)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    gP = torch.randn(n, 4, generator=g, dtype=torch.float64).to(device)
+    gZ = torch.randn(n, 4, generator=g, dtype=torch.float64).to(device)
+    gA = torch.zeros_like(XA)
+    gB = torch.zeros_like(XB)
+    dA = pair.A.dXdalpha.to(device).contiguous()
+    dB = pair.B.dXdalpha.to(device).contiguous()
+    ga = torch.zeros(n, dtype=torch.float64, device=device)
+    call = lambda: tms.backward(A, B, hits, gP=gP, gZ=gZ, gradA=gA, gradB=gB, dA_dalpha=dA,
+                                dB_dalpha=dB, galpha=ga, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            call()
+    ts = []
+    with torch.cuda.stream(stream):
+        for _ in range(20):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    return {"hits": n, "ms_per_backward": ms, "fp64_gflops": 150.0 * n / (ms / 1e3) / 1e9,
+            "note": "latency-bound: a few hundred hits, one thread each"}
 
 
 def cpu_baseline(pair):
@@ -418,6 +518,8 @@ def main():
     ap.add_argument("--impl", default="tms", choices=["tms", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--extras", action="store_true",
+                    help="also time the plain FP64 path, the batched 256-pair search and the adjoint")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
