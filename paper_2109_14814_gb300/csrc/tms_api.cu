@@ -197,8 +197,9 @@ struct Plan {
         const int sort_passes_h = (2 * tri_bits + pair_bits + kRadixBits - 1) / kRadixBits;
         kernels = 0;
         mark(0, s);
-        cudaMemsetAsync(d_ctr, 0, sizeof(Counters), s);
-        launch_bounds_init(d_bounds, n_meshes, s);
+        launch_search_init(d_bounds, n_meshes, d_ctr, p.cell_filter ? bmA : nullptr,
+                           (unsigned long long)1 << bmA_bits, p.cell_filter ? bmH : nullptr,
+                           (unsigned long long)1 << bmH_bits, grid, s);
         GroupArgs ga;
         ga.ent_key = ek; ga.ent_face = ev; ga.d_n = &d_ctr->entries; ga.cap = ent_cap;
         ga.ent_slot = eslot; ga.ent_rank = erank;
@@ -232,8 +233,6 @@ struct Plan {
         mark(3, s);
 
         if (p.cell_filter) {
-            cudaMemsetAsync(bmA, 0, ((size_t)1 << bmA_bits) * sizeof(uint32_t), s);
-            cudaMemsetAsync(bmH, 0, ((size_t)1 << bmH_bits) * sizeof(uint32_t), s);
             mark(4, s);
             fa.entries = d_pass_A; fa.n_entries = n_pass_A; fa.total_faces = fslots_A;
             fa.mode = MODE_MARK;

@@ -359,7 +359,10 @@ struct FacePassArgs {
 void launch_face_pass(const FacePassArgs &a, int precision, int face_level, int block,
                       cudaStream_t st);
 cudaError_t configure_face_pass();
-void launch_bounds_init(Bounds *b, int n, cudaStream_t st);
+// counters zeroed, bounds reset, bitmaps cleared (NULL: not cleared); word
+// counts are multiples of four
+void launch_search_init(Bounds *b, int n, Counters *ctr, uint32_t *bmA, unsigned long long n32a,
+                        uint32_t *bmH, unsigned long long n32h, int grid, cudaStream_t st);
 void launch_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *g,
                         float cell_mult, cudaStream_t st);
 

@@ -519,13 +519,26 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_cell_pass(FacePassArgs a, i
     }
 }
 
-__global__ void k_bounds_init(Bounds *b, int n) {
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= n) return;
+// The start of a search, in one launch: counters zeroed, per-mesh bounds
+// reset, and the two occupancy bitmaps cleared (n32a and n32h words, each a
+// multiple of four).
+__global__ void k_search_init(Bounds *b, int n, Counters *ctr, uint32_t *bmA,
+                              unsigned long long n32a, uint32_t *bmH, unsigned long long n32h) {
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    if (tid == 0) memset(ctr, 0, sizeof(Counters));
+    if (tid < (unsigned long long)n) {
+        Bounds &m = b[tid];
 #pragma unroll
-    for (int d = 0; d < 4; ++d) { b[m].lo[d] = ~0ULL; b[m].hi[d] = 0ULL; b[m].w[d] = 0ULL; }
-    b[m].flags = 0;
-    b[m].faces = 0;
+        for (int d = 0; d < 4; ++d) { m.lo[d] = ~0ULL; m.hi[d] = 0ULL; m.w[d] = 0ULL; }
+        m.flags = 0;
+        m.faces = 0;
+    }
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    if (bmA)
+        for (unsigned long long i = tid; i < n32a / 4; i += stride) reinterpret_cast<uint4 *>(bmA)[i] = z;
+    if (bmH)
+        for (unsigned long long i = tid; i < n32h / 4; i += stride) reinterpret_cast<uint4 *>(bmH)[i] = z;
 }
 
 // Trimmed world and uniform grid of each pair (Sec. 6.2.1 and its remark).
@@ -645,8 +658,9 @@ void launch_face_pass(const FacePassArgs &a, int precision, int face_level, int 
     else launch_cells_mode<0>(a, face_level, st);
 }
 
-void launch_bounds_init(Bounds *b, int n, cudaStream_t st) {
-    k_bounds_init<<<(n + 127) / 128, 128, 0, st>>>(b, n);
+void launch_search_init(Bounds *b, int n, Counters *ctr, uint32_t *bmA, unsigned long long n32a,
+                        uint32_t *bmH, unsigned long long n32h, int grid, cudaStream_t st) {
+    k_search_init<<<grid, 256, 0, st>>>(b, n, ctr, bmA, n32a, bmH, n32h);
 }
 
 void launch_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *g,

@@ -263,8 +263,8 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     NA_CK(cudaMemcpyAsync(b.tables, &t, sizeof(t), cudaMemcpyHostToDevice, s));
 
     // the launch sequence of tms_search, on the static buffers
-    NA_CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters), s));
-    launch_bounds_init(b.bounds, 2, s);
+    launch_search_init(b.bounds, 2, b.ctr, p.cell_filter ? b.bmA : nullptr, 1ull << kBmAWordBits,
+                       p.cell_filter ? b.bmH : nullptr, 1ull << kBmHWordBits, grid, s);
     GroupArgs ga;
     ga.ent_key = b.ek; ga.ent_face = b.ev; ga.d_n = &b.ctr->entries; ga.cap = kEntCap;
     ga.ent_slot = b.eslot; ga.ent_rank = b.erank;
@@ -290,8 +290,6 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     launch_face_pass(fa, p.precision, p.face_level, block, s);
     launch_grid_params(b.bounds, b.tables->pairs, 1, b.grids, p.cell_mult, s);
     if (p.cell_filter) {
-        NA_CK(cudaMemsetAsync(b.bmA, 0, (1ull << kBmAWordBits) * sizeof(uint32_t), s));
-        NA_CK(cudaMemsetAsync(b.bmH, 0, (1ull << kBmHWordBits) * sizeof(uint32_t), s));
         fa.entries = b.tables->pa; fa.n_entries = 1; fa.total_faces = fslots_A;
         fa.mode = MODE_MARK;
         launch_face_pass(fa, p.precision, p.face_level, block, s);

@@ -187,6 +187,12 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         }
         c = lo;
     }
+    // the lanes' face, kept across tiles of one A row
+    EBox<PREC> abox;
+    uint32_t amask = 0, aface = 0;
+    uint32_t prev_a0 = 0xFFFFFFFFu;
+    unsigned long long prev_c = ~0ULL;
+    bool prev_swap = true;
     // the pair's face-box arrays, looked up again only when the pair changes
     uint32_t cached_pair = 0xFFFFFFFFu;
     const void *fbA = nullptr, *fbB = nullptr;
@@ -197,10 +203,11 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         const uint32_t s = cr.start;
         const uint32_t bstart = cr.bstart;
         const uint32_t e = (c + 1 < ncell) ? a.cells[c + 1].start : (uint32_t)nent;
-        const uint32_t nAc = bstart - s;
-        const uint32_t tA = (nAc + kTile - 1) / kTile;
+        const uint32_t nBc = e - bstart;
+        const uint32_t tB = (nBc + kTile - 1) / kTile;
         const uint32_t local = (uint32_t)(t - cr.tile_off);
-        const uint32_t a0 = s + (local % tA) * kTile, b0 = bstart + (local / tA) * kTile;
+        // B-fastest order: consecutive tiles of a cell share their A row
+        const uint32_t a0 = s + (local / tB) * kTile, b0 = bstart + (local % tB) * kTile;
         const int nAt0 = (int)min((uint32_t)kTile, bstart - a0);
         const int nBt0 = (int)min((uint32_t)kTile, e - b0);
         // lanes take the larger side of the tile, the loop the smaller one
@@ -218,10 +225,14 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         }
         // own entry (the lanes' side) in registers, the other side in shared memory
         const void *fbL = swapAB ? fbB : fbA, *fbM = swapAB ? fbA : fbB;
-        EBox<PREC> abox;
-        uint32_t amask = 0, aface = 0;
+        // the lanes keep their face when the previous tile had the same A row on
+        // the lanes' side (a full A row always does: only a partial one swaps)
+        const bool reuse = !swapAB && !prev_swap && a0 == prev_a0 && c == prev_c;
+        prev_swap = swapAB;
+        prev_a0 = a0;
+        prev_c = c;
         const bool hasA = lane < nAt;
-        if (hasA) {
+        if (hasA && !reuse) {
             aface = a.vals[l0 + lane];
             abox.load(fbL, aface);
             amask = own_mask(abox.low_cell(gr), cur);
