@@ -101,11 +101,52 @@ class Planted:
 
 
 @dataclass
+class SurfacePair:
+    """Closed form of the two analytic sheets a mesh pair samples (planted
+    corrections excluded), for refinement on the true surfaces:
+
+      W_A(theta, s) = g(s) T(theta; alpha) + F(s)
+      W_B(theta, s) = W_A(theta + c0, 1 - s) + h_amp (sin(P (theta - theta0)) n1
+                                                    + sin(Q pi (s - s0)) n2)
+      T(theta; alpha) = sum_k ((ca_k + alpha dca_k) cos k theta
+                               + (cb_k + alpha dcb_k) sin k theta) / k
+      g = 1 + s ("linear") or lam**s ("exp");  F = sum_f amp_f prod_j (s - r_fj) e_f
+      (n1, n2)(theta, s): v1, v2 minus their regularised least-squares projection
+        on span(t1, t2), t1, t2 = the theta- and s-partials of the underlying
+        sheet g(s') T(theta'; alpha_ref) + F(s') at theta' = theta + c0,
+        s' = 1 - s; regulariser eps = reg (|t1|^2 + |t2|^2) / 2.
+    sites: (n, 2) lattice points (theta, s) of B where both sines vanish; each
+    is an exact crossing of the sheets at (theta + c0, 1 - s, theta, s)."""
+    ca: torch.Tensor
+    cb: torch.Tensor
+    dca: torch.Tensor
+    dcb: torch.Tensor
+    alpha: float
+    alpha_ref: float
+    stretch: str
+    lam: float
+    fold_amp: torch.Tensor
+    fold_roots: torch.Tensor
+    fold_dir: torch.Tensor
+    c0: float
+    h_amp: float
+    P: float
+    Q: float
+    theta0: float
+    s0: float
+    v1: torch.Tensor
+    v2: torch.Tensor
+    reg: float
+    sites: torch.Tensor
+
+
+@dataclass
 class MeshPair:
     A: MeshGrid
     B: MeshGrid
     planted: Planted
     meta: dict = field(default_factory=dict)
+    surface: Optional[SurfacePair] = None
 
 
 # ----------------------------------------------------------------------------
@@ -462,7 +503,14 @@ def build_pair(seed: int, NA: int, MA: int, NB: int, MB: int, *, stretch: str = 
                  dXB.contiguous() if with_dalpha else None)
     meta = dict(seed=seed, NA=NA, MA=MA, NB=NB, MB=MB, alpha=alpha, h_amp=h_amp,
                 sites=len(site_list), stretch=stretch)
-    return MeshPair(A, B, planted, meta)
+    surface = SurfacePair(
+        ca=fam.ca.clone(), cb=fam.cb.clone(), dca=fam.dca.clone(), dcb=fam.dcb.clone(),
+        alpha=float(alpha), alpha_ref=float(alpha_ref), stretch=stretch, lam=float(lam),
+        fold_amp=fam.fold_amp.clone(), fold_roots=fam.fold_roots.clone(),
+        fold_dir=fam.fold_dir.clone(), c0=c0, h_amp=float(h_amp), P=float(P), Q=float(Q),
+        theta0=th0, s0=s0, v1=dirs[0].clone(), v2=dirs[1].clone(), reg=0.25,
+        sites=torch.tensor(sorted(site_list), dtype=torch.float64).reshape(-1, 2))
+    return MeshPair(A, B, planted, meta, surface)
 
 
 # ----------------------------------------------------------------------------
