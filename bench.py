@@ -26,6 +26,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
 import torch  # noqa: E402
 
 METRIC = "ms per full manifold-mesh search (4M×4M tris), HBM GB/s & FP64 util vs peak"
@@ -349,7 +350,9 @@ def run_tms(args, ws, rank, local):
     if args.extras:
         extras = {"plain_fp64": plain_fp64(tms, A, B, out, stream, flush, h),
                   "batched": batched_search(tms, device, stream, flush),
-                  "adjoint": adjoint_timing(tms, device, stream)}
+                  "adjoint": adjoint_timing(tms, device, stream),
+                  "refine": refine_timing(tms, pair, h, stream, flush,
+                                          (fp64 or {}).get("peak_tflops") or tms.probe_fp64_tflops())}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -465,6 +468,61 @@ def adjoint_timing(tms, device, stream):
             "note": "latency-bound: a few hundred hits, one thread each"}
 
 
+def refine_flops_per_eval(K: int, n_folds: int) -> int:
+    """Algorithmic FP64 flops of one evaluation of f, Df and the damped-Newton
+    update for one seed (FMA = 2), counted from the closed-form sheets:
+    128 per harmonic (three harmonic sums over 4 coordinates plus two
+    angle-addition steps), 66 per fold (two cubics and five 4-vector
+    accumulations), 695 for the rest (sheet assembly 68, 19 dot products 133,
+    normal frame and its partials 270, crossing term and row of Df 92, norms 42,
+    4x4 elimination 70, arguments 12, update 8).  Sines, cosines, exponentials,
+    square roots and divisions are not counted."""
+    return 695 + 128 * K + 66 * n_folds
+
+
+def refine_timing(tms, pair, hits, stream, flush, fp64_tf):
+    """tms_refine on the search's own hits, seeds read in place from the hit
+    records (default schedule: alpha 0.5, tol 1e-10): time per call, seeds/s,
+    iterations and FP64 rate against the measured FP64 peak; plus the oracle
+    on a bounded sample of generator seeds (the planted records' estimates)."""
+    from oracle import refine as oref
+    sp = tms.surface_pair(pair.surface)
+    n = len(hits)
+    dev = hits.raw.device
+    res = tms.Refined(torch.empty((n, 4), dtype=torch.float64, device=dev),
+                      torch.empty(n, dtype=torch.float64, device=dev),
+                      torch.empty(n, dtype=torch.float64, device=dev),
+                      torch.empty(n, dtype=torch.int32, device=dev),
+                      torch.empty(n, dtype=torch.int32, device=dev))
+    call = lambda: tms.refine(sp, hits, stream=stream, out=res)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            call()
+    ms = _timed(call, stream, flush, 20)
+    st = res.status.cpu().numpy()
+    it = res.iters.cpu().numpy().astype(np.int64)
+    evals = int(it.sum() + np.isin(st, (0, 1, 2)).sum())
+    fpe = refine_flops_per_eval(sp.n_harmonics, sp.n_folds)
+    achieved = fpe * evals / (ms * 1e-3) / 1e12
+    seeds = pair.planted.params.numpy()
+    t0 = time.perf_counter()
+    o = oref.damped_newton(pair.surface, seeds)
+    cpu_s = time.perf_counter() - t0
+    o_evals = int(o["iters"].sum() + np.isin(o["status"], (0, 1, 2)).sum())
+    return {"seeds": n, "ms_per_call": ms, "seeds_per_s": n / (ms * 1e-3),
+            "iterations_total": int(it.sum()), "evaluations": evals,
+            "iterations_median": float(np.median(it)) if n else 0.0,
+            "status_counts": {tms.REFINE_STATUS[k]: int((st == k).sum()) for k in range(5)},
+            "roofline": {"kernel": "tms::k_refine", "bound": "alu (fp64)", "achieved": achieved,
+                         "peak": fp64_tf, "unit": "TFLOP/s", "frac": achieved / fp64_tf,
+                         "flops_per_evaluation": fpe,
+                         "peak_kind": "measured FP64 FMA-chain probe on this GPU"},
+            "cpu_baseline": {"value": cpu_s * 1e3 / max(o_evals, 1), "unit": "ms/evaluation",
+                             "gpu_value": ms / max(evals, 1), "cores": 1, "kind": "oracle",
+                             "sample": f"{len(seeds)} planted-record seeds of the same meshes, "
+                                       "numpy FP64 vectorised over seeds"}}
+
+
 def cpu_baseline(pair):
     import oracle
     OA, OB = oracle.OMesh.from_grid(pair.A), oracle.OMesh.from_grid(pair.B)
@@ -519,7 +577,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--extras", action="store_true",
-                    help="also time the plain FP64 path, the batched 256-pair search and the adjoint")
+                    help="also time the plain FP64 path, the batched 256-pair search, the adjoint "
+                         "and the refinement of the hits")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()

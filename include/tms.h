@@ -273,6 +273,106 @@ const char *tms_noalloc_last_error(void);
  * does not fit refuses every call with TMS_ERR_STATE. */
 tms_status tms_noalloc_footprint(unsigned long long *needed, unsigned long long *reserved);
 
+/*
+ * Refinement of approximate intersections (Sec. 7, Eqs. tosolve and
+ * dampedNewtonEquation).  Each seed x0 = (theta_u, s_u, theta_s, s_s) -- for
+ * example a hit's parameter estimates (Sec. 6.2.4) -- is corrected by the
+ * damped Newton iteration x_{k+1} = x_k - alpha Df(x_k)^{-1} f(x_k) on
+ *     f(x) = W_A(theta_u, s_u) - W_B(theta_s, s_s),
+ *     Df   = [df/dtheta_u, df/ds_u, df/dtheta_s, df/ds_s]   (4x4, FP64),
+ * evaluated on the true surfaces rather than their meshes.  The paper obtains
+ * W and its partials from Fourier-Taylor series and the flow
+ * (Eqs. wuequation-dwsdsequation); this library evaluates the closed-form
+ * sheet pair below, which its synthetic meshes sample, with exact partials.
+ *
+ * The sheet pair (all lengths 4 = the coordinates x, y, px, py):
+ *   S(theta, s; a)  = g(s) T(theta; a) + F(s)
+ *   T(theta; a)     = sum_{k=1..K} ((ca_k + a dca_k) cos k theta
+ *                                   + (cb_k + a dcb_k) sin k theta) / k
+ *   g(s)            = 1 + s (stretch 0) or lam^s (stretch 1)
+ *   F(s)            = sum_f fold_amp_f (s - r_f1)(s - r_f2)(s - r_f3) fold_dir_f
+ *   W_A(theta, s)   = S(theta, s; alpha)
+ *   W_B(theta, s)   = S(theta + c0, 1 - s; alpha)
+ *                     + h_amp (sin(P (theta - theta0)) n1 + sin(Q pi (s - s0)) n2)
+ *   n_r(theta, s)   = v_r - t1 y1 - t2 y2,  (y1, y2) = (J^T J + eps I)^{-1} J^T v_r,
+ *                     J = [t1 t2] = the theta- and s-partials of
+ *                     S(theta', s'; alpha_ref) at theta' = theta + c0, s' = 1 - s,
+ *                     eps = reg (|t1|^2 + |t2|^2) / 2.
+ */
+#define TMS_SURF_MAX_HARMONICS 8
+#define TMS_SURF_MAX_FOLDS 4
+
+typedef struct {
+    int n_harmonics;            /* K, 1..TMS_SURF_MAX_HARMONICS */
+    int n_folds;                /* 0..TMS_SURF_MAX_FOLDS */
+    int stretch;                /* 0: g = 1 + s; 1: g = lam^s */
+    int pad;
+    double ca[TMS_SURF_MAX_HARMONICS][4];    /* row k-1 holds harmonic k */
+    double cb[TMS_SURF_MAX_HARMONICS][4];
+    double dca[TMS_SURF_MAX_HARMONICS][4];   /* derivatives in the family parameter */
+    double dcb[TMS_SURF_MAX_HARMONICS][4];
+    double alpha;               /* family parameter of both sheets */
+    double alpha_ref;           /* family parameter of the normal frame */
+    double lam;                 /* stretch base (stretch 1), > 0 */
+    double fold_amp[TMS_SURF_MAX_FOLDS];
+    double fold_root[TMS_SURF_MAX_FOLDS][3];
+    double fold_dir[TMS_SURF_MAX_FOLDS][4];
+    double c0;                  /* theta offset of B's underlying sheet */
+    double h_amp, P, Q;         /* crossing term amplitude and frequencies */
+    double theta0, s0;          /* crossing lattice origin */
+    double v1[4], v2[4];        /* generating directions of the normal frame */
+    double reg;                 /* frame regulariser, >= 0 */
+} tms_surface_pair;
+
+typedef struct {
+    double alpha0;        /* damping while ||f||_2 > switch_below, in (0, 1] */
+    double alpha1;        /* damping once ||f||_2 <= switch_below, in (0, 1] */
+    double switch_below;  /* >= 0 (0: alpha0 throughout) */
+    double tol;           /* converged when ||f(x_k)||_2 <= tol, >= 0 */
+    double s_lo, s_hi;    /* a seed whose s_u or s_s leaves [s_lo, s_hi] stops */
+    double rho_min;       /* singular when |det Df| / prod_j ||Df e_j|| < rho_min */
+    int max_iter;         /* at most this many updates, 0..1000000 */
+    int pad;
+} tms_refine_params;
+
+/* alpha0 = alpha1 = 0.5, switch_below = 0, tol = 1e-10, s in [-0.5, 1.5],
+ * rho_min = 1e-14, max_iter = 200. */
+void tms_refine_params_default(tms_refine_params *p);
+
+enum {
+    TMS_REFINE_CONVERGED = 0,   /* ||f|| <= tol at the returned x */
+    TMS_REFINE_MAX_ITER = 1,    /* max_iter updates made without converging */
+    TMS_REFINE_SINGULAR = 2,    /* normalised |det Df| below rho_min */
+    TMS_REFINE_ESCAPED = 3,     /* s_u or s_s left [s_lo, s_hi] */
+    TMS_REFINE_NON_FINITE = 4   /* a non-finite iterate, f or Df */
+};
+
+/*
+ * tms_refine -- damped Newton from n seeds, one independent iteration each.
+ *   surf, params : host; params may be NULL (defaults).
+ *   dX0          : device, seed i at dX0[i*ldx0 + 0..3] = (theta_u, s_u,
+ *                  theta_s, s_s); ldx0 >= 4 doubles (16 reads seeds straight
+ *                  out of tms_hit records: dX0 = (const double *)dHits + 10).
+ *   dX           : device, n*4 doubles out: the last iterate, theta_u and
+ *                  theta_s reduced to [0, 2 pi).  May equal dX0 when ldx0 == 4.
+ *   dFnorm       : device, n doubles: ||f||_2 at the last evaluation (NaN when
+ *                  the seed stopped before one: escaped or non-finite).
+ *   dRho         : device, n doubles: det Df / prod_j ||Df e_j|| at the last
+ *                  evaluation (signed; NaN as for dFnorm).
+ *   dIters       : device, n int32: updates made.
+ *   dStatus      : device, n int32: TMS_REFINE_*.
+ *   dFnorm, dRho, dIters, dStatus may be NULL.
+ * Checks in order at every iterate: non-finite or escaped x stops; then f and
+ * Df are evaluated; non-finite f or Df stops; ||f|| <= tol converges;
+ * max_iter updates made stops; a singular Df stops; else x is updated.
+ * Asynchronous on `stream`; allocates nothing.  TMS_ERR_ARG on a bad argument
+ * (message in tms_last_error()), TMS_ERR_CUDA on a launch failure.
+ */
+tms_status tms_refine(const tms_surface_pair *surf, const tms_refine_params *params,
+                      const double *dX0, long long ldx0, long long n, double *dX,
+                      double *dFnorm, double *dRho, int32_t *dIters, int32_t *dStatus,
+                      void *stream);
+
 /* Per-stage device time (ms) of the last search on `stream` made with
  * params.timing = 1, in this order:
  *   0 counters/bounds init   1 face pass: world bounds   2 grid parameters

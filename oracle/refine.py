@@ -171,8 +171,8 @@ def residual(sp, x):
 def damped_newton(sp, x0, history: bool = False, **kw):
     """Eq. (dampedNewtonEquation) from seeds x0 (n, 4).  Returns a dict of
     x (n, 4), fnorm (n,) (||f|| at the last evaluation, NaN if none), iters (n,)
-    (updates made), status (n,), rho (n,) (|det Df| / prod of column norms at
-    the last evaluation) and, if history, per-seed lists of ||f_k||."""
+    (updates made), status (n,), rho (n,) (det Df / prod of column norms at
+    the last evaluation, signed) and, if history, per-seed lists of ||f_k||."""
     opt = dict(DEFAULTS)
     for k, v in kw.items():
         if k not in opt:
@@ -201,7 +201,7 @@ def damped_newton(sp, x0, history: bool = False, **kw):
             r = np.sqrt(np.sum(f * f, axis=1))
             fin = np.isfinite(f).all(axis=1) & np.isfinite(Df).all(axis=(1, 2))
             Dfs = np.where(fin[:, None, None], Df, np.eye(4))
-            rh = np.abs(np.linalg.det(Dfs)) / np.sqrt(np.sum(Dfs * Dfs, axis=1)).prod(axis=1)
+            rh = np.linalg.det(Dfs) / np.sqrt(np.sum(Dfs * Dfs, axis=1)).prod(axis=1)
             fnorm[ev_idx] = r
             rho[ev_idx] = rh
             if history:
@@ -212,7 +212,7 @@ def damped_newton(sp, x0, history: bool = False, **kw):
             sub[(sub < 0) & (r <= opt["tol"])] = CONVERGED
             if k == opt["max_iter"]:
                 sub[sub < 0] = MAX_ITER
-            sub[(sub < 0) & ~(rh >= opt["rho_min"])] = SINGULAR
+            sub[(sub < 0) & ~(np.abs(rh) >= opt["rho_min"])] = SINGULAR
             code[ev] = sub
             go = sub < 0
             if go.any():
@@ -225,8 +225,9 @@ def damped_newton(sp, x0, history: bool = False, **kw):
         iters[idx[done]] = k
         active[idx[done]] = False
         k += 1
-    x[:, 0] = np.mod(x[:, 0], TWO_PI)
-    x[:, 2] = np.mod(x[:, 2], TWO_PI)
+    with np.errstate(invalid="ignore"):       # non-finite iterates stay non-finite
+        x[:, 0] = np.mod(x[:, 0], TWO_PI)
+        x[:, 2] = np.mod(x[:, 2], TWO_PI)
     res = dict(x=x, fnorm=fnorm, iters=iters, status=status, rho=rho)
     if history:
         res["history"] = hist

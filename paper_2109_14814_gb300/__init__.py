@@ -3,16 +3,19 @@
 Finds every intersecting triangle pair between two manifold meshes in R^4
 (arXiv 2109.14814, Sec. 6): uniform-grid broad phase with bounding boxes, FP64
 narrow phase solving the 4x4 system for (a, b, c, d), merged and sorted hits,
-a batched form replayed from a CUDA graph, and an FP64 adjoint.  All compute is
+a batched form replayed from a CUDA graph, an FP64 adjoint, and the damped-Newton
+refinement of hits on the true surfaces (Sec. 7).  All compute is
 in libtms.so (C ABI in include/tms.h); this package only marshals arguments.
 """
-from ._binding import (HIT_BYTES, STAGES, TMS_ERR_ARG, TMS_ERR_CAPACITY, TMS_ERR_CUDA,
+from ._binding import (HIT_BYTES, REFINE_STATUS, STAGES, Refined, RefineParams, SurfacePair,
+                       refine, refine_params, surface_pair, TMS_ERR_ARG, TMS_ERR_CAPACITY, TMS_ERR_CUDA,
                        TMS_ERR_STATE, TMS_ERR_TIMEOUT, TMS_OK, HitPoint, Hits, Mesh, Params, Stats,
                        TmsError, autotune, backward, last_error, last_stage_ms, last_stats, lib, params,
                        probe_fp64_tflops, release_workspace, search, search_batched,
                        search_noalloc, status_str, version)
 
-__all__ = ["HIT_BYTES", "STAGES", "TMS_ERR_ARG", "TMS_ERR_CAPACITY", "TMS_ERR_CUDA",
+__all__ = ["HIT_BYTES", "REFINE_STATUS", "STAGES", "Refined", "RefineParams", "SurfacePair",
+           "refine", "refine_params", "surface_pair", "TMS_ERR_ARG", "TMS_ERR_CAPACITY", "TMS_ERR_CUDA",
            "TMS_ERR_STATE", "TMS_ERR_TIMEOUT", "TMS_OK", "HitPoint", "Hits", "Mesh", "Params",
            "Stats", "TmsError", "autotune", "backward", "last_error", "last_stage_ms", "last_stats", "lib",
            "params", "probe_fp64_tflops", "release_workspace", "search", "search_batched",

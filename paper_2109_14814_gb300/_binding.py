@@ -76,6 +76,33 @@ class Stats(ctypes.Structure):
         return d
 
 
+class SurfacePair(ctypes.Structure):
+    """Mirror of tms_surface_pair (the closed-form sheet pair refined on)."""
+    _fields_ = [
+        ("n_harmonics", _c.c_int), ("n_folds", _c.c_int), ("stretch", _c.c_int), ("pad", _c.c_int),
+        ("ca", (_c.c_double * 4) * 8), ("cb", (_c.c_double * 4) * 8),
+        ("dca", (_c.c_double * 4) * 8), ("dcb", (_c.c_double * 4) * 8),
+        ("alpha", _c.c_double), ("alpha_ref", _c.c_double), ("lam", _c.c_double),
+        ("fold_amp", _c.c_double * 4), ("fold_root", (_c.c_double * 3) * 4),
+        ("fold_dir", (_c.c_double * 4) * 4),
+        ("c0", _c.c_double), ("h_amp", _c.c_double), ("P", _c.c_double), ("Q", _c.c_double),
+        ("theta0", _c.c_double), ("s0", _c.c_double),
+        ("v1", _c.c_double * 4), ("v2", _c.c_double * 4), ("reg", _c.c_double),
+    ]
+
+
+class RefineParams(ctypes.Structure):
+    """Mirror of tms_refine_params."""
+    _fields_ = [
+        ("alpha0", _c.c_double), ("alpha1", _c.c_double), ("switch_below", _c.c_double),
+        ("tol", _c.c_double), ("s_lo", _c.c_double), ("s_hi", _c.c_double),
+        ("rho_min", _c.c_double), ("max_iter", _c.c_int), ("pad", _c.c_int),
+    ]
+
+
+REFINE_STATUS = ("converged", "max_iter", "singular", "escaped", "non_finite")
+
+
 def lib():
     """The loaded library (raises if it has not been built)."""
     global _lib
@@ -119,6 +146,11 @@ def lib():
     L.tms_autotune.argtypes = [P, P, I, _c.POINTER(Params), _c.POINTER(Params), _c.c_char_p,
                                _c.POINTER(D), P]
     L.tms_autotune.restype = I
+    L.tms_refine_params_default.argtypes = [_c.POINTER(RefineParams)]
+    L.tms_refine_params_default.restype = None
+    L.tms_refine.argtypes = [_c.POINTER(SurfacePair), _c.POINTER(RefineParams), P, LL, LL, P, P, P,
+                             P, P, P]
+    L.tms_refine.restype = I
     _lib = L
     return L
 
@@ -391,6 +423,97 @@ def last_stage_ms(stream=None) -> dict:
     if rc != TMS_OK:
         raise TmsError(rc, "tms_last_stage_ms")
     return {STAGES[i]: float(buf[i]) for i in range(min(n.value, len(STAGES)))}
+
+
+def surface_pair(sp) -> SurfacePair:
+    """tms_surface_pair from a description with the fields of synth.SurfacePair
+    (coefficient tables (K, 4), fold tables (F, 3) and (F, 4), scalars)."""
+    def rows(t):
+        return [[float(v) for v in r] for r in (t.tolist() if hasattr(t, "tolist") else t)]
+    out = SurfacePair()
+    ca, cb, dca, dcb = rows(sp.ca), rows(sp.cb), rows(sp.dca), rows(sp.dcb)
+    if not 1 <= len(ca) <= 8:
+        raise ValueError("1..8 harmonics supported")
+    out.n_harmonics = len(ca)
+    for dst, src in ((out.ca, ca), (out.cb, cb), (out.dca, dca), (out.dcb, dcb)):
+        for k, r in enumerate(src):
+            for c in range(4):
+                dst[k][c] = r[c]
+    amp = [float(v) for v in (sp.fold_amp.tolist() if hasattr(sp.fold_amp, "tolist") else sp.fold_amp)]
+    if len(amp) > 4:
+        raise ValueError("at most 4 folds supported")
+    out.n_folds = len(amp)
+    roots, dirs = rows(sp.fold_roots), rows(sp.fold_dir)
+    for f in range(len(amp)):
+        out.fold_amp[f] = amp[f]
+        for j in range(3):
+            out.fold_root[f][j] = roots[f][j]
+        for c in range(4):
+            out.fold_dir[f][c] = dirs[f][c]
+    out.stretch = {"linear": 0, "exp": 1}[sp.stretch]
+    out.lam = float(sp.lam)
+    for name in ("alpha", "alpha_ref", "c0", "h_amp", "P", "Q", "theta0", "s0", "reg"):
+        setattr(out, name, float(getattr(sp, name)))
+    v1 = sp.v1.tolist() if hasattr(sp.v1, "tolist") else sp.v1
+    v2 = sp.v2.tolist() if hasattr(sp.v2, "tolist") else sp.v2
+    for c in range(4):
+        out.v1[c], out.v2[c] = float(v1[c]), float(v2[c])
+    return out
+
+
+def refine_params(**kw) -> RefineParams:
+    p = RefineParams()
+    lib().tms_refine_params_default(_c.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k) or k == "pad":
+            raise KeyError(f"unknown refinement parameter {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+@dataclass
+class Refined:
+    """tms_refine output on the device."""
+    x: torch.Tensor        # (n, 4) float64: theta_u, s_u, theta_s, s_s
+    fnorm: torch.Tensor    # (n,) float64
+    rho: torch.Tensor      # (n,) float64, det Df / prod of column norms
+    iters: torch.Tensor    # (n,) int32
+    status: torch.Tensor   # (n,) int32, index into REFINE_STATUS
+
+
+def refine(surface, seeds, stream=None, out: Optional[Refined] = None, **kw) -> Refined:
+    """tms_refine: damped Newton (Sec. 7) from each seed on the sheet pair
+    `surface` (a SurfacePair mirror or anything surface_pair() accepts).
+    seeds: a Hits (their parameter estimates are read in place) or a CUDA
+    float64 tensor (n, 4) with unit column stride."""
+    sp = surface if isinstance(surface, SurfacePair) else surface_pair(surface)
+    p = refine_params(**kw)
+    if isinstance(seeds, Hits):
+        n = len(seeds)
+        dev = seeds.raw.device
+        ptr = seeds.raw.data_ptr() + 10 * 8 if n else None
+        ld = HIT_BYTES // 8
+    else:
+        if not (seeds.is_cuda and seeds.dtype == torch.float64 and seeds.dim() == 2
+                and seeds.shape[1] == 4 and seeds.stride(1) == 1):
+            raise ValueError("seeds must be a CUDA float64 (n, 4) tensor with unit column stride")
+        n = int(seeds.shape[0])
+        dev = seeds.device
+        ptr = seeds.data_ptr() if n else None
+        ld = max(int(seeds.stride(0)), 4)
+    if out is None:
+        out = Refined(torch.empty((n, 4), dtype=torch.float64, device=dev),
+                      torch.empty(n, dtype=torch.float64, device=dev),
+                      torch.empty(n, dtype=torch.float64, device=dev),
+                      torch.empty(n, dtype=torch.int32, device=dev),
+                      torch.empty(n, dtype=torch.int32, device=dev))
+    rc = lib().tms_refine(_c.byref(sp), _c.byref(p), ptr, ld, n, _dptr(out.x) if n else None,
+                          _dptr(out.fnorm) if n else None, _dptr(out.rho) if n else None,
+                          _dptr(out.iters) if n else None, _dptr(out.status) if n else None,
+                          _stream(stream))
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_refine")
+    return out
 
 
 def release_workspace(stream=None):

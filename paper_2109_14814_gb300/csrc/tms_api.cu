@@ -755,6 +755,8 @@ tms_status tms_build_mesh(const double *dX, const double *dY, const double *dPx,
 
 }  // extern "C"
 
+void tms::set_last_error(const std::string &msg) { g_err = msg; }
+
 tms_status tms::mesh_view(tms_mesh m, MeshDev *view, int *device) {
     if (!m || m->magic != kMagic) return TMS_ERR_STATE;
     *view = m->dev;

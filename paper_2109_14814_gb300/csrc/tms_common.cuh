@@ -6,6 +6,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <string>
+
 #include "../../include/tms.h"
 
 namespace tms {
@@ -512,5 +514,8 @@ void launch_adjoint(const AdjointArgs &a, cudaStream_t st);
 
 // device view of a mesh handle (TMS_ERR_STATE for an invalid handle)
 tms_status mesh_view(tms_mesh m, MeshDev *view, int *device);
+
+// Message returned by tms_last_error() on the calling thread.
+void set_last_error(const std::string &msg);
 
 }  // namespace tms

@@ -1,0 +1,448 @@
+// Refinement of approximate manifold intersections (Sec. 7, Eqs. tosolve and
+// dampedNewtonEquation): from each seed x = (theta_u, s_u, theta_s, s_s) the
+// damped Newton iteration x <- x - alpha Df^{-1} f on
+// f = W_A(theta_u, s_u) - W_B(theta_s, s_s), with W_A, W_B the closed-form
+// sheet pair of tms_surface_pair and Df their exact partials, all in FP64.
+//
+// Layout: four lanes per seed, lane c owning coordinate c of every 4-vector
+// (W, its partials, the normal frame, one row of Df).  The four sines/cosines
+// and two exponentials an iteration needs are spread over the four lanes and
+// exchanged by shuffles; dot products are butterfly sums over the quad (the
+// same bits on every lane); the 4x4 solve is a partial-pivot elimination whose
+// rows live in the lanes.  Every stop decision is taken on the quad's first
+// lane and broadcast, so the four lanes always agree.  A warp loops while any
+// of its eight seeds is still iterating; the loop is bounded by max_iter + 1
+// evaluations per seed.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <cstddef>
+#include <string>
+
+#include "tms_common.cuh"
+
+namespace {
+
+constexpr int kH = TMS_SURF_MAX_HARMONICS;
+constexpr int kF = TMS_SURF_MAX_FOLDS;
+constexpr int kThreads = 128;          // 32 seeds per block
+constexpr int kSeedsPerBlock = kThreads / 4;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr double kPi = 3.141592653589793;
+constexpr double kTwoPi = 6.283185307179586;
+
+struct RefineArgs {
+    tms_surface_pair sp;
+    tms_refine_params p;
+    const double *x0;
+    long long ld;
+    long long n;
+    double *x;
+    double *fnorm;
+    double *rho;
+    int *iters;
+    int *status;
+};
+
+// Per-block tables, coordinate fastest (lane c reads column c).
+struct Coef {
+    double a[kH][4], b[kH][4];      // harmonic coefficients at alpha
+    double ar[kH][4], br[kH][4];    // at alpha_ref (normal frame)
+    double fd[kF][4];               // fold_amp * fold_dir
+    double v1[4], v2[4];
+};
+
+__device__ __forceinline__ double quad_sum(double v) {
+    v += __shfl_xor_sync(kFull, v, 1);
+    v += __shfl_xor_sync(kFull, v, 2);
+    return v;
+}
+
+__device__ __forceinline__ double lane_val(double v, int base, int j) {
+    return __shfl_sync(kFull, v, base + j);
+}
+
+// p = (s - r0)(s - r1)(s - r2) and its first two derivatives.
+__device__ __forceinline__ void cubic(double s, const double r[3], double &p, double &p1,
+                                      double &p2) {
+    const double d0 = s - r[0], d1 = s - r[1], d2 = s - r[2];
+    p = d0 * d1 * d2;
+    p1 = d1 * d2 + d0 * d2 + d0 * d1;
+    p2 = 2.0 * (d0 + d1 + d2);
+}
+
+__global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ RefineArgs a) {
+    __shared__ Coef cf;
+    const tms_surface_pair &sp = a.sp;
+    const tms_refine_params &pr = a.p;
+    const int t = threadIdx.x;
+    for (int q = t; q < kH * 4; q += kThreads) {
+        const int h = q >> 2, c = q & 3;
+        cf.a[h][c] = sp.ca[h][c] + sp.alpha * sp.dca[h][c];
+        cf.b[h][c] = sp.cb[h][c] + sp.alpha * sp.dcb[h][c];
+        cf.ar[h][c] = sp.ca[h][c] + sp.alpha_ref * sp.dca[h][c];
+        cf.br[h][c] = sp.cb[h][c] + sp.alpha_ref * sp.dcb[h][c];
+    }
+    if (t < kF * 4) cf.fd[t >> 2][t & 3] = sp.fold_amp[t >> 2] * sp.fold_dir[t >> 2][t & 3];
+    if (t < 4) {
+        cf.v1[t] = sp.v1[t];
+        cf.v2[t] = sp.v2[t];
+    }
+    __syncthreads();
+
+    const int lane = t & 31;
+    const int c = lane & 3;
+    const int base = lane & ~3;
+    const long long i = (long long)blockIdx.x * kSeedsPerBlock + (t >> 2);
+    const bool live = i < a.n;
+    double x0 = 0.0, x1 = 0.5, x2 = 0.0, x3 = 0.5;
+    if (live) {
+        const double *s = a.x0 + i * a.ld;
+        x0 = s[0];
+        x1 = s[1];
+        x2 = s[2];
+        x3 = s[3];
+    }
+    int code = live ? -1 : TMS_REFINE_CONVERGED;
+    int iters = 0;
+    double fn = __longlong_as_double(0x7ff8000000000000LL);   // NaN until evaluated
+    double rh = fn;
+    const int K = sp.n_harmonics;
+    const int NF = sp.n_folds;
+    const double lnlam = sp.stretch ? log(sp.lam) : 0.0;
+
+    for (int k = 0; __any_sync(kFull, code < 0); ++k) {
+        // ---- stop checks on the iterate (identical on the quad's lanes)
+        int pre = -1;
+        if (!(isfinite(x0) && isfinite(x1) && isfinite(x2) && isfinite(x3)))
+            pre = TMS_REFINE_NON_FINITE;
+        else if (x1 < pr.s_lo || x1 > pr.s_hi || x3 < pr.s_lo || x3 > pr.s_hi)
+            pre = TMS_REFINE_ESCAPED;
+
+        // ---- sines/cosines and exponentials, one per lane
+        const double arg = c == 0 ? x0
+                         : c == 1 ? x2 + sp.c0
+                         : c == 2 ? sp.P * (x2 - sp.theta0)
+                                  : sp.Q * kPi * (x3 - sp.s0);
+        double sn, cs;
+        sincos(arg, &sn, &cs);
+        const double sA = lane_val(sn, base, 0), cA = lane_val(cs, base, 0);
+        const double sB = lane_val(sn, base, 1), cB = lane_val(cs, base, 1);
+        const double sh1 = lane_val(sn, base, 2), ch1 = lane_val(cs, base, 2);
+        const double sh2 = lane_val(sn, base, 3), ch2 = lane_val(cs, base, 3);
+        const double s1 = 1.0 - x3;   // s' of B's underlying sheet
+        double gA, gA1, gB, gB1, gB2;
+        if (sp.stretch) {
+            const double e = exp(lnlam * (c == 0 ? x1 : s1));
+            gA = lane_val(e, base, 0);
+            gB = lane_val(e, base, 1);
+            gA1 = lnlam * gA;
+            gB1 = lnlam * gB;
+            gB2 = lnlam * gB1;
+        } else {
+            gA = 1.0 + x1;
+            gA1 = 1.0;
+            gB = 1.0 + s1;
+            gB1 = 1.0;
+            gB2 = 0.0;
+        }
+
+        // ---- folds F(s) at s_u and at s'
+        double FA = 0.0, FA1 = 0.0, FB = 0.0, FB1 = 0.0, FB2 = 0.0;
+#pragma unroll
+        for (int f = 0; f < kF; ++f) {
+            if (f < NF) {
+                double p, p1, p2, q, q1, q2;
+                cubic(x1, sp.fold_root[f], p, p1, p2);
+                cubic(s1, sp.fold_root[f], q, q1, q2);
+                const double w = cf.fd[f][c];
+                FA += w * p;
+                FA1 += w * p1;
+                FB += w * q;
+                FB1 += w * q1;
+                FB2 += w * q2;
+            }
+        }
+
+        // ---- harmonic sums: T, T' at theta_u (alpha); T, T' at theta' (alpha);
+        //      T, T', T'' at theta' (alpha_ref).  cos/sin of k theta by angle addition.
+        double TA = 0.0, TAt = 0.0, TB = 0.0, TBt = 0.0, TR = 0.0, TRt = 0.0, TRtt = 0.0;
+        double ckA = cA, skA = sA, ckB = cB, skB = sB;
+#pragma unroll
+        for (int h = 0; h < kH; ++h) {
+            if (h < K) {
+                const double kk = (double)(h + 1), ik = 1.0 / (double)(h + 1);
+                const double ah = cf.a[h][c], bh = cf.b[h][c];
+                const double arh = cf.ar[h][c], brh = cf.br[h][c];
+                const double ua = ah * ckA + bh * skA, va = bh * ckA - ah * skA;
+                TA += ua * ik;
+                TAt += va;
+                const double ub = ah * ckB + bh * skB, vb = bh * ckB - ah * skB;
+                TB += ub * ik;
+                TBt += vb;
+                const double ur = arh * ckB + brh * skB, vr = brh * ckB - arh * skB;
+                TR += ur * ik;
+                TRt += vr;
+                TRtt -= kk * ur;
+                const double nA = ckA * cA - skA * sA;
+                skA = skA * cA + ckA * sA;
+                ckA = nA;
+                const double nB = ckB * cB - skB * sB;
+                skB = skB * cB + ckB * sB;
+                ckB = nB;
+            }
+        }
+
+        // ---- W_A and its partials; B's underlying sheet; the frame sheet
+        const double WA = gA * TA + FA, WAt = gA * TAt, WAs = gA1 * TA + FA1;
+        const double SB = gB * TB + FB, SBt = gB * TBt, SBs = gB1 * TB + FB1;
+        const double t1 = gB * TRt, t2 = gB1 * TR + FB1;
+        const double Wtt = gB * TRtt, Wts = gB1 * TRt, Wss = gB2 * TR + FB2;
+        const double v1 = cf.v1[c], v2 = cf.v2[c];
+
+        // ---- normal frame (n1, n2) and its theta- and s-partials
+        const double g11 = quad_sum(t1 * t1), g12 = quad_sum(t1 * t2), g22 = quad_sum(t2 * t2);
+        const double j11 = quad_sum(t1 * v1), j21 = quad_sum(t2 * v1);
+        const double j12 = quad_sum(t1 * v2), j22 = quad_sum(t2 * v2);
+        const double P1 = quad_sum(t1 * Wtt), P2 = quad_sum(t1 * Wts), P3 = quad_sum(Wtt * t2);
+        const double P4 = quad_sum(t2 * Wts), P5 = quad_sum(t1 * Wss), P6 = quad_sum(t2 * Wss);
+        const double Lt1 = quad_sum(Wtt * v1), Ls1 = quad_sum(Wts * v1), Ss1 = quad_sum(Wss * v1);
+        const double Lt2 = quad_sum(Wtt * v2), Ls2 = quad_sum(Wts * v2), Ss2 = quad_sum(Wss * v2);
+        const double eps = sp.reg * 0.5 * (g11 + g22);
+        const double G11 = g11 + eps, G12 = g12, G22 = g22 + eps;
+        const double idet = 1.0 / (G11 * G22 - G12 * G12);
+        // d/dtheta and d/ds of G (J^T J + eps I)
+        const double tg11 = 2.0 * P1, tg12 = P2 + P3, tg22 = 2.0 * P4;
+        const double te = sp.reg * 0.5 * (tg11 + tg22);
+        const double tG11 = tg11 + te, tG22 = tg22 + te;
+        const double sg11 = -2.0 * P2, sg12 = -(P5 + P4), sg22 = -2.0 * P6;
+        const double se = sp.reg * 0.5 * (sg11 + sg22);
+        const double sG11 = sg11 + se, sG22 = sg22 + se;
+
+        double n[2], nt[2], ns[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const double v = r == 0 ? v1 : v2;
+            const double j1 = r == 0 ? j11 : j12, j2 = r == 0 ? j21 : j22;
+            const double Lt = r == 0 ? Lt1 : Lt2, Ls = r == 0 ? Ls1 : Ls2, Ss = r == 0 ? Ss1 : Ss2;
+            const double y1 = (G22 * j1 - G12 * j2) * idet, y2 = (-G12 * j1 + G11 * j2) * idet;
+            n[r] = v - t1 * y1 - t2 * y2;
+            // theta: d t1 = Wtt, d t2 = Wts
+            double r1 = Lt - (tG11 * y1 + tg12 * y2), r2 = Ls - (tg12 * y1 + tG22 * y2);
+            double dy1 = (G22 * r1 - G12 * r2) * idet, dy2 = (-G12 * r1 + G11 * r2) * idet;
+            nt[r] = -(Wtt * y1 + Wts * y2) - (t1 * dy1 + t2 * dy2);
+            // s: d t1 = -Wts, d t2 = -Wss
+            r1 = -Ls - (sG11 * y1 + sg12 * y2);
+            r2 = -Ss - (sg12 * y1 + sG22 * y2);
+            dy1 = (G22 * r1 - G12 * r2) * idet;
+            dy2 = (-G12 * r1 + G11 * r2) * idet;
+            ns[r] = (Wts * y1 + Wss * y2) - (t1 * dy1 + t2 * dy2);
+        }
+
+        // ---- W_B, f and the row of Df this lane owns
+        const double h = sp.h_amp;
+        const double H = h * (sh1 * n[0] + sh2 * n[1]);
+        const double Ht = h * (sp.P * ch1 * n[0] + sh1 * nt[0] + sh2 * nt[1]);
+        const double Hs = h * (sh1 * ns[0] + sp.Q * kPi * ch2 * n[1] + sh2 * ns[1]);
+        const double fc = WA - (SB + H);
+        double m[4] = {WAt, WAs, -(SBt + Ht), -(-SBs + Hs)};
+
+        const double r2 = quad_sum(fc * fc);
+        double cn = 1.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cn *= sqrt(quad_sum(m[j] * m[j]));
+        int fin = isfinite(fc) && isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) &&
+                  isfinite(m[3]);
+        fin &= __shfl_xor_sync(kFull, fin, 1);
+        fin &= __shfl_xor_sync(kFull, fin, 2);
+
+        // ---- Df dx = f by partial-pivot elimination over the quad's rows
+        double rr = fc, det = 1.0, ip[4];
+        int used = 0, pl[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            double cand = ((used >> c) & 1) ? -1.0 : fabs(m[j]);
+            int bl = c;
+#pragma unroll
+            for (int off = 1; off <= 2; off <<= 1) {
+                const double oc = __shfl_xor_sync(kFull, cand, off);
+                const int ol = __shfl_xor_sync(kFull, bl, off);
+                if (oc > cand || (oc == cand && ol < bl)) {
+                    cand = oc;
+                    bl = ol;
+                }
+            }
+            used |= 1 << bl;
+            pl[j] = bl;
+            double pj[4];
+#pragma unroll
+            for (int q = j; q < 4; ++q) pj[q] = lane_val(m[q], base, bl);
+            const double prr = lane_val(rr, base, bl);
+            det *= pj[j];
+            ip[j] = pj[j] != 0.0 ? 1.0 / pj[j] : 0.0;
+            if (!((used >> c) & 1)) {
+                const double fct = m[j] * ip[j];
+#pragma unroll
+                for (int q = j + 1; q < 4; ++q) m[q] -= fct * pj[q];
+                rr -= fct * prr;
+                m[j] = 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = u + 1; w < 4; ++w)
+                if (pl[u] > pl[w]) det = -det;
+        double dx[4];
+#pragma unroll
+        for (int j = 3; j >= 0; --j) {
+            double v = rr;
+#pragma unroll
+            for (int q = j + 1; q < 4; ++q) v -= m[q] * dx[q];
+            dx[j] = lane_val(v * ip[j], base, pl[j]);
+        }
+
+        // ---- decision on the quad's first lane, then the update
+        const double r = sqrt(r2);
+        const double rho = det / cn;
+        int dec = pre;
+        if (dec < 0) {
+            if (!fin) dec = TMS_REFINE_NON_FINITE;
+            else if (r <= pr.tol) dec = TMS_REFINE_CONVERGED;
+            else if (k == pr.max_iter) dec = TMS_REFINE_MAX_ITER;
+            else if (!(fabs(rho) >= pr.rho_min)) dec = TMS_REFINE_SINGULAR;
+        }
+        dec = __shfl_sync(kFull, dec, base);
+        if (code < 0) {
+            if (pre < 0) {
+                fn = r;
+                rh = rho;
+            }
+            if (dec >= 0) {
+                code = dec;
+                iters = k;
+            } else {
+                const double al = r > pr.switch_below ? pr.alpha0 : pr.alpha1;
+                x0 -= al * dx[0];
+                x1 -= al * dx[1];
+                x2 -= al * dx[2];
+                x3 -= al * dx[3];
+            }
+        }
+    }
+
+    if (live) {
+        double xc = c == 0 ? x0 : c == 1 ? x1 : c == 2 ? x2 : x3;
+        if (c == 0 || c == 2) {
+            double w = fmod(xc, kTwoPi);
+            if (w < 0.0) w += kTwoPi;
+            else if (w == 0.0) w = 0.0;   // +0 for a -0 remainder
+            xc = w;
+        }
+        a.x[i * 4 + c] = xc;
+        if (c == 0) {
+            if (a.fnorm) a.fnorm[i] = fn;
+            if (a.rho) a.rho[i] = rh;
+            if (a.iters) a.iters[i] = iters;
+            if (a.status) a.status[i] = code;
+        }
+    }
+}
+
+bool all_finite(const double *v, size_t n) {
+    for (size_t j = 0; j < n; ++j)
+        if (!isfinite(v[j])) return false;
+    return true;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+tms_status arg_error(const char *msg) {
+    tms::set_last_error(msg);
+    return TMS_ERR_ARG;
+}
+
+}  // namespace
+
+extern "C" void tms_refine_params_default(tms_refine_params *p) {
+    if (!p) return;
+    p->alpha0 = 0.5;
+    p->alpha1 = 0.5;
+    p->switch_below = 0.0;
+    p->tol = 1e-10;
+    p->s_lo = -0.5;
+    p->s_hi = 1.5;
+    p->rho_min = 1e-14;
+    p->max_iter = 200;
+    p->pad = 0;
+}
+
+extern "C" tms_status tms_refine(const tms_surface_pair *surf, const tms_refine_params *params,
+                                 const double *dX0, long long ldx0, long long n, double *dX,
+                                 double *dFnorm, double *dRho, int32_t *dIters, int32_t *dStatus,
+                                 void *stream) {
+    if (!surf) return arg_error("tms_refine: surface is NULL");
+    if (n < 0) return arg_error("tms_refine: n < 0");
+    tms_refine_params p;
+    if (params) p = *params;
+    else tms_refine_params_default(&p);
+    const tms_surface_pair &s = *surf;
+    if (s.n_harmonics < 1 || s.n_harmonics > TMS_SURF_MAX_HARMONICS)
+        return arg_error("tms_refine: n_harmonics outside 1..8");
+    if (s.n_folds < 0 || s.n_folds > TMS_SURF_MAX_FOLDS)
+        return arg_error("tms_refine: n_folds outside 0..4");
+    if (s.stretch != 0 && s.stretch != 1) return arg_error("tms_refine: stretch must be 0 or 1");
+    if (s.stretch == 1 && !(s.lam > 0.0)) return arg_error("tms_refine: lam must be > 0");
+    bool fin = true;
+    for (int h = 0; h < s.n_harmonics; ++h)
+        fin = fin && all_finite(s.ca[h], 4) && all_finite(s.cb[h], 4) && all_finite(s.dca[h], 4) &&
+              all_finite(s.dcb[h], 4);
+    for (int f = 0; f < s.n_folds; ++f)
+        fin = fin && isfinite(s.fold_amp[f]) && all_finite(s.fold_root[f], 3) &&
+              all_finite(s.fold_dir[f], 4);
+    const size_t ns = (sizeof(tms_surface_pair) - offsetof(tms_surface_pair, c0)) / sizeof(double);
+    fin = fin && isfinite(s.alpha) && isfinite(s.alpha_ref) && (s.stretch == 0 || isfinite(s.lam)) &&
+          all_finite(&s.c0, ns);
+    if (!fin) return arg_error("tms_refine: non-finite surface value");
+    if (!(s.reg >= 0.0)) return arg_error("tms_refine: reg must be >= 0");
+    if (!(p.alpha0 > 0.0 && p.alpha0 <= 1.0 && p.alpha1 > 0.0 && p.alpha1 <= 1.0))
+        return arg_error("tms_refine: alpha0 and alpha1 must lie in (0, 1]");
+    if (!(p.tol >= 0.0) || !(p.switch_below >= 0.0) || !(p.rho_min >= 0.0))
+        return arg_error("tms_refine: tol, switch_below and rho_min must be >= 0");
+    if (!(p.s_lo < p.s_hi)) return arg_error("tms_refine: need s_lo < s_hi");
+    if (p.max_iter < 0 || p.max_iter > 1000000)
+        return arg_error("tms_refine: max_iter outside 0..1000000");
+    if (n == 0) return TMS_OK;
+    if (ldx0 < 4) return arg_error("tms_refine: ldx0 < 4");
+    if (!dX0 || !dX || !is_device_ptr(dX0) || !is_device_ptr(dX))
+        return arg_error("tms_refine: seeds and output must be device pointers");
+    if (dX == dX0 && ldx0 != 4) return arg_error("tms_refine: in place needs ldx0 == 4");
+    RefineArgs a;
+    a.sp = s;
+    a.p = p;
+    a.x0 = dX0;
+    a.ld = ldx0;
+    a.n = n;
+    a.x = dX;
+    a.fnorm = dFnorm;
+    a.rho = dRho;
+    a.iters = dIters;
+    a.status = dStatus;
+    const long long blocks = (n + kSeedsPerBlock - 1) / kSeedsPerBlock;
+    if (blocks > 0x7fffffffLL) return arg_error("tms_refine: too many seeds");
+    k_refine<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(a);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        tms::set_last_error(std::string("tms_refine launch: ") + cudaGetErrorString(e));
+        return TMS_ERR_CUDA;
+    }
+    return TMS_OK;
+}

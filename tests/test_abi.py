@@ -81,3 +81,50 @@ def test_noalloc_layout_fits_its_static_array():
     assert lib.tms_noalloc_footprint(ctypes.byref(needed), ctypes.byref(reserved)) == tms.TMS_OK
     assert reserved.value == 64 << 20
     assert 0 < needed.value <= reserved.value
+
+
+def test_refine_struct_layouts_match_ctypes(tmp_path):
+    prog = tmp_path / "rsizes.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "tms.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(tms_surface_pair),"
+        " sizeof(tms_refine_params), offsetof(tms_surface_pair, alpha),"
+        " offsetof(tms_surface_pair, c0), offsetof(tms_surface_pair, reg),"
+        " offsetof(tms_refine_params, max_iter)); return 0;}\n")
+    exe = tmp_path / "rsizes"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
+                   check=True)
+    vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                        check=True).stdout.split()))
+    S, R = tms.SurfacePair, tms.RefineParams
+    assert vals == [ctypes.sizeof(S), ctypes.sizeof(R), S.alpha.offset, S.c0.offset,
+                    S.reg.offset, R.max_iter.offset]
+
+
+def test_refine_arguments_checked_without_gpu():
+    import synth
+    lib = tms.lib()
+    sp = tms.surface_pair(synth.config1().surface)
+    assert sp.n_harmonics == 6 and sp.n_folds == 0 and sp.stretch == 0
+    p = tms.refine_params()
+    assert (p.alpha0, p.alpha1, p.tol, p.max_iter) == (0.5, 0.5, 1e-10, 200)
+    B = ctypes.byref
+    # n == 0 is a no-op; everything below is rejected before any device call
+    assert lib.tms_refine(B(sp), B(p), None, 4, 0, None, None, None, None, None, None) == tms.TMS_OK
+    assert lib.tms_refine(None, B(p), None, 4, 0, None, None, None, None, None, None) == tms.TMS_ERR_ARG
+    assert lib.tms_refine(B(sp), B(p), None, 4, -1, None, None, None, None, None, None) == tms.TMS_ERR_ARG
+    for field, bad in (("alpha0", 0.0), ("alpha1", 1.5), ("tol", -1.0), ("max_iter", -1),
+                       ("s_hi", -1.0), ("rho_min", float("nan"))):
+        q = tms.refine_params(**{field: bad})
+        assert lib.tms_refine(B(sp), B(q), None, 4, 0, None, None, None, None, None,
+                              None) == tms.TMS_ERR_ARG, field
+    bad = tms.surface_pair(synth.config1().surface)
+    bad.n_harmonics = 9
+    assert lib.tms_refine(B(bad), B(p), None, 4, 0, None, None, None, None, None, None) == tms.TMS_ERR_ARG
+    bad = tms.surface_pair(synth.config1().surface)
+    bad.h_amp = float("inf")
+    assert lib.tms_refine(B(bad), B(p), None, 4, 0, None, None, None, None, None, None) == tms.TMS_ERR_ARG
+    assert "non-finite" in tms.last_error()
+    # seeds must be given for n > 0 (rejected before the pointer query)
+    assert lib.tms_refine(B(sp), B(p), None, 4, 3, None, None, None, None, None, None) == tms.TMS_ERR_ARG
+    assert lib.tms_refine(B(sp), B(p), None, 3, 3, None, None, None, None, None, None) == tms.TMS_ERR_ARG

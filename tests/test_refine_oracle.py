@@ -141,7 +141,7 @@ def test_stop_statuses():
     # Hadamard: |det Df| <= prod of column norms, so rho_min > 1 makes every
     # non-root seed singular at its first evaluation
     res = R.damped_newton(sp, x0[3:4], rho_min=1.0 + 1e-9)
-    assert res["status"][0] == R.SINGULAR and 0.0 < res["rho"][0] <= 1.0
+    assert res["status"][0] == R.SINGULAR and 0.0 < abs(res["rho"][0]) <= 1.0
 
 
 def test_frame_vanishes_only_at_h_zero_keeps_roots():
