@@ -44,11 +44,17 @@ struct RefineArgs {
     int *status;
 };
 
-// Per-block tables, coordinate fastest (lane c reads column c).
+// Per-block tables, coordinate fastest (lane c reads column c).  With
+// a_k = ca_k + alpha dca_k, b_k likewise (and a_k^r, b_k^r at alpha_ref):
+//   T   = sum (a_k/k) cos + (b_k/k) sin     T' = sum b_k cos + (-a_k) sin
+//   T'' = sum (-k a_k) cos + (-k b_k) sin
+// so every harmonic term is two fused multiply-adds.
 struct Coef {
-    double a[kH][4], b[kH][4];      // harmonic coefficients at alpha
-    double ar[kH][4], br[kH][4];    // at alpha_ref (normal frame)
+    double ak[kH][4], bk[kH][4], na[kH][4], b[kH][4];        // at alpha
+    double ark[kH][4], brk[kH][4], nar[kH][4], br[kH][4];    // at alpha_ref
+    double kar[kH][4], kbr[kH][4];                            // at alpha_ref, T''
     double fd[kF][4];               // fold_amp * fold_dir
+    double root[kF][3];             // fold roots
     double v1[4], v2[4];
 };
 
@@ -63,7 +69,7 @@ __device__ __forceinline__ double lane_val(double v, int base, int j) {
 }
 
 // p = (s - r0)(s - r1)(s - r2) and its first two derivatives.
-__device__ __forceinline__ void cubic(double s, const double r[3], double &p, double &p1,
+__device__ __forceinline__ void cubic(double s, const double *r, double &p, double &p1,
                                       double &p2) {
     const double d0 = s - r[0], d1 = s - r[1], d2 = s - r[2];
     p = d0 * d1 * d2;
@@ -78,12 +84,24 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
     const int t = threadIdx.x;
     for (int q = t; q < kH * 4; q += kThreads) {
         const int h = q >> 2, c = q & 3;
-        cf.a[h][c] = sp.ca[h][c] + sp.alpha * sp.dca[h][c];
-        cf.b[h][c] = sp.cb[h][c] + sp.alpha * sp.dcb[h][c];
-        cf.ar[h][c] = sp.ca[h][c] + sp.alpha_ref * sp.dca[h][c];
-        cf.br[h][c] = sp.cb[h][c] + sp.alpha_ref * sp.dcb[h][c];
+        const double k = (double)(h + 1);
+        const double a = sp.ca[h][c] + sp.alpha * sp.dca[h][c];
+        const double b = sp.cb[h][c] + sp.alpha * sp.dcb[h][c];
+        const double ar = sp.ca[h][c] + sp.alpha_ref * sp.dca[h][c];
+        const double br = sp.cb[h][c] + sp.alpha_ref * sp.dcb[h][c];
+        cf.ak[h][c] = a / k;
+        cf.bk[h][c] = b / k;
+        cf.na[h][c] = -a;
+        cf.b[h][c] = b;
+        cf.ark[h][c] = ar / k;
+        cf.brk[h][c] = br / k;
+        cf.nar[h][c] = -ar;
+        cf.br[h][c] = br;
+        cf.kar[h][c] = -k * ar;
+        cf.kbr[h][c] = -k * br;
     }
     if (t < kF * 4) cf.fd[t >> 2][t & 3] = sp.fold_amp[t >> 2] * sp.fold_dir[t >> 2][t & 3];
+    if (t < kF * 3) cf.root[t / 3][t % 3] = sp.fold_root[t / 3][t % 3];
     if (t < 4) {
         cf.v1[t] = sp.v1[t];
         cf.v2[t] = sp.v2[t];
@@ -105,8 +123,9 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
     }
     int code = live ? -1 : TMS_REFINE_CONVERGED;
     int iters = 0;
-    double fn = __longlong_as_double(0x7ff8000000000000LL);   // NaN until evaluated
-    double rh = fn;
+    double fn = __longlong_as_double(0x7ff8000000000000LL);   // ||f||^2, NaN until evaluated
+    double rh = fn, rc2 = 1.0;                                 // det Df, prod ||col||^2
+    const double tol2 = pr.tol * pr.tol, sw2 = pr.switch_below * pr.switch_below;
     const int K = sp.n_harmonics;
     const int NF = sp.n_folds;
     const double lnlam = sp.stretch ? log(sp.lam) : 0.0;
@@ -147,20 +166,23 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
             gB2 = 0.0;
         }
 
-        // ---- folds F(s) at s_u and at s'
+        // ---- folds F(s) at s_u and at s': lane f evaluates fold f's cubics
         double FA = 0.0, FA1 = 0.0, FB = 0.0, FB1 = 0.0, FB2 = 0.0;
+        if (NF > 0) {
+            double p, p1, p2, q, q1, q2;
+            const int fo = c < NF ? c : 0;
+            cubic(x1, cf.root[fo], p, p1, p2);
+            cubic(s1, cf.root[fo], q, q1, q2);
 #pragma unroll
-        for (int f = 0; f < kF; ++f) {
-            if (f < NF) {
-                double p, p1, p2, q, q1, q2;
-                cubic(x1, sp.fold_root[f], p, p1, p2);
-                cubic(s1, sp.fold_root[f], q, q1, q2);
-                const double w = cf.fd[f][c];
-                FA += w * p;
-                FA1 += w * p1;
-                FB += w * q;
-                FB1 += w * q1;
-                FB2 += w * q2;
+            for (int f = 0; f < kF; ++f) {
+                if (f < NF) {
+                    const double w = cf.fd[f][c];
+                    FA = fma(w, lane_val(p, base, f), FA);
+                    FA1 = fma(w, lane_val(p1, base, f), FA1);
+                    FB = fma(w, lane_val(q, base, f), FB);
+                    FB1 = fma(w, lane_val(q1, base, f), FB1);
+                    FB2 = fma(w, lane_val(q2, base, f), FB2);
+                }
             }
         }
 
@@ -171,25 +193,21 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
 #pragma unroll
         for (int h = 0; h < kH; ++h) {
             if (h < K) {
-                const double kk = (double)(h + 1), ik = 1.0 / (double)(h + 1);
-                const double ah = cf.a[h][c], bh = cf.b[h][c];
-                const double arh = cf.ar[h][c], brh = cf.br[h][c];
-                const double ua = ah * ckA + bh * skA, va = bh * ckA - ah * skA;
-                TA += ua * ik;
-                TAt += va;
-                const double ub = ah * ckB + bh * skB, vb = bh * ckB - ah * skB;
-                TB += ub * ik;
-                TBt += vb;
-                const double ur = arh * ckB + brh * skB, vr = brh * ckB - arh * skB;
-                TR += ur * ik;
-                TRt += vr;
-                TRtt -= kk * ur;
-                const double nA = ckA * cA - skA * sA;
-                skA = skA * cA + ckA * sA;
-                ckA = nA;
-                const double nB = ckB * cB - skB * sB;
-                skB = skB * cB + ckB * sB;
-                ckB = nB;
+                TA = fma(cf.ak[h][c], ckA, fma(cf.bk[h][c], skA, TA));
+                TAt = fma(cf.b[h][c], ckA, fma(cf.na[h][c], skA, TAt));
+                TB = fma(cf.ak[h][c], ckB, fma(cf.bk[h][c], skB, TB));
+                TBt = fma(cf.b[h][c], ckB, fma(cf.na[h][c], skB, TBt));
+                TR = fma(cf.ark[h][c], ckB, fma(cf.brk[h][c], skB, TR));
+                TRt = fma(cf.br[h][c], ckB, fma(cf.nar[h][c], skB, TRt));
+                TRtt = fma(cf.kar[h][c], ckB, fma(cf.kbr[h][c], skB, TRtt));
+                if (h + 1 < K) {
+                    const double nA = ckA * cA - skA * sA;
+                    skA = skA * cA + ckA * sA;
+                    ckA = nA;
+                    const double nB = ckB * cB - skB * sB;
+                    skB = skB * cB + ckB * sB;
+                    ckB = nB;
+                }
             }
         }
 
@@ -219,24 +237,33 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
         const double se = sp.reg * 0.5 * (sg11 + sg22);
         const double sG11 = sg11 + se, sG22 = sg22 + se;
 
+        // lane c solves for frame vector r = c & 1, then both are shared
+        double yv[6];
+        {
+            const int r = c & 1;
+            const double j1 = r ? j12 : j11, j2 = r ? j22 : j21;
+            const double Lt = r ? Lt2 : Lt1, Ls = r ? Ls2 : Ls1, Ss = r ? Ss2 : Ss1;
+            const double y1 = (G22 * j1 - G12 * j2) * idet, y2 = (G11 * j2 - G12 * j1) * idet;
+            // theta: d t1 = Wtt, d t2 = Wts;  s: d t1 = -Wts, d t2 = -Wss
+            const double a1 = Lt - (tG11 * y1 + tg12 * y2), a2 = Ls - (tg12 * y1 + tG22 * y2);
+            const double b1 = -Ls - (sG11 * y1 + sg12 * y2), b2 = -Ss - (sg12 * y1 + sG22 * y2);
+            yv[0] = y1;
+            yv[1] = y2;
+            yv[2] = (G22 * a1 - G12 * a2) * idet;
+            yv[3] = (G11 * a2 - G12 * a1) * idet;
+            yv[4] = (G22 * b1 - G12 * b2) * idet;
+            yv[5] = (G11 * b2 - G12 * b1) * idet;
+        }
         double n[2], nt[2], ns[2];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const double v = r == 0 ? v1 : v2;
-            const double j1 = r == 0 ? j11 : j12, j2 = r == 0 ? j21 : j22;
-            const double Lt = r == 0 ? Lt1 : Lt2, Ls = r == 0 ? Ls1 : Ls2, Ss = r == 0 ? Ss1 : Ss2;
-            const double y1 = (G22 * j1 - G12 * j2) * idet, y2 = (-G12 * j1 + G11 * j2) * idet;
+            const double y1 = lane_val(yv[0], base, r), y2 = lane_val(yv[1], base, r);
+            const double dt1 = lane_val(yv[2], base, r), dt2 = lane_val(yv[3], base, r);
+            const double ds1 = lane_val(yv[4], base, r), ds2 = lane_val(yv[5], base, r);
             n[r] = v - t1 * y1 - t2 * y2;
-            // theta: d t1 = Wtt, d t2 = Wts
-            double r1 = Lt - (tG11 * y1 + tg12 * y2), r2 = Ls - (tg12 * y1 + tG22 * y2);
-            double dy1 = (G22 * r1 - G12 * r2) * idet, dy2 = (-G12 * r1 + G11 * r2) * idet;
-            nt[r] = -(Wtt * y1 + Wts * y2) - (t1 * dy1 + t2 * dy2);
-            // s: d t1 = -Wts, d t2 = -Wss
-            r1 = -Ls - (sG11 * y1 + sg12 * y2);
-            r2 = -Ss - (sg12 * y1 + sG22 * y2);
-            dy1 = (G22 * r1 - G12 * r2) * idet;
-            dy2 = (-G12 * r1 + G11 * r2) * idet;
-            ns[r] = (Wts * y1 + Wss * y2) - (t1 * dy1 + t2 * dy2);
+            nt[r] = -(Wtt * y1 + Wts * y2) - (t1 * dt1 + t2 * dt2);
+            ns[r] = (Wts * y1 + Wss * y2) - (t1 * ds1 + t2 * ds2);
         }
 
         // ---- W_B, f and the row of Df this lane owns
@@ -248,9 +275,9 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
         double m[4] = {WAt, WAs, -(SBt + Ht), -(-SBs + Hs)};
 
         const double r2 = quad_sum(fc * fc);
-        double cn = 1.0;
+        double cn2 = 1.0;   // product of the squared column norms
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cn *= sqrt(quad_sum(m[j] * m[j]));
+        for (int j = 0; j < 4; ++j) cn2 *= quad_sum(m[j] * m[j]);
         int fin = isfinite(fc) && isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) &&
                   isfinite(m[3]);
         fin &= __shfl_xor_sync(kFull, fin, 1);
@@ -303,26 +330,27 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
         }
 
         // ---- decision on the quad's first lane, then the update
-        const double r = sqrt(r2);
-        const double rho = det / cn;
+        // ||f|| <= tol as ||f||^2 <= tol^2; |det| / prod ||col|| >= rho_min as
+        // |det| >= rho_min sqrt(prod ||col||^2)
         int dec = pre;
         if (dec < 0) {
             if (!fin) dec = TMS_REFINE_NON_FINITE;
-            else if (r <= pr.tol) dec = TMS_REFINE_CONVERGED;
+            else if (r2 <= tol2) dec = TMS_REFINE_CONVERGED;
             else if (k == pr.max_iter) dec = TMS_REFINE_MAX_ITER;
-            else if (!(fabs(rho) >= pr.rho_min)) dec = TMS_REFINE_SINGULAR;
+            else if (!(fabs(det) >= pr.rho_min * sqrt(cn2))) dec = TMS_REFINE_SINGULAR;
         }
         dec = __shfl_sync(kFull, dec, base);
         if (code < 0) {
             if (pre < 0) {
-                fn = r;
-                rh = rho;
+                fn = r2;
+                rh = det;
+                rc2 = cn2;
             }
             if (dec >= 0) {
                 code = dec;
                 iters = k;
             } else {
-                const double al = r > pr.switch_below ? pr.alpha0 : pr.alpha1;
+                const double al = r2 > sw2 ? pr.alpha0 : pr.alpha1;
                 x0 -= al * dx[0];
                 x1 -= al * dx[1];
                 x2 -= al * dx[2];
@@ -341,8 +369,8 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
         }
         a.x[i * 4 + c] = xc;
         if (c == 0) {
-            if (a.fnorm) a.fnorm[i] = fn;
-            if (a.rho) a.rho[i] = rh;
+            if (a.fnorm) a.fnorm[i] = sqrt(fn);
+            if (a.rho) a.rho[i] = rh / sqrt(rc2);
             if (a.iters) a.iters[i] = iters;
             if (a.status) a.status[i] = code;
         }
