@@ -352,7 +352,9 @@ def run_tms(args, ws, rank, local):
                   "batched": batched_search(tms, device, stream, flush),
                   "adjoint": adjoint_timing(tms, device, stream),
                   "refine": refine_timing(tms, pair, h, stream, flush,
-                                          (fp64 or {}).get("peak_tflops") or tms.probe_fp64_tflops())}
+                                          (fp64 or {}).get("peak_tflops") or tms.probe_fp64_tflops()),
+                  "continuation": continue_timing(tms, pair, h, stream,
+                                                  (fp64 or {}).get("peak_tflops") or tms.probe_fp64_tflops())}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -523,6 +525,55 @@ def refine_timing(tms, pair, hits, stream, flush, fp64_tf):
                                        "numpy FP64 vectorised over seeds"}}
 
 
+def continue_timing(tms, pair, hits, stream, fp64_tf, n_steps=50, dalpha=1e-3):
+    """tms_continue from the search's own hits (seeds read in place) through
+    n_steps values of alpha_u (step 0 refines the hits at the meshes' alpha):
+    time per call, branch-steps/s and FP64 rate; plus the oracle on a bounded
+    sample of generator seeds (the planted records' estimates)."""
+    from oracle import refine as oref
+    sp = tms.surface_pair(pair.surface)
+    alphas = torch.tensor([pair.surface.alpha + dalpha * (j + 1) for j in range(n_steps)],
+                          dtype=torch.float64)
+    call = lambda: tms.continue_branches(sp, hits, alphas, stream=stream, max_jump=0.05)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            out = call()
+        ts = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = call()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    st = out.status.cpu().numpy()
+    it = out.iters.cpu().numpy().astype(np.int64)
+    evals = int(it.sum() + np.isin(st, (0, 1, 2, 5, 6)).sum())
+    fpe = refine_flops_per_eval(sp.n_harmonics, sp.n_folds)
+    achieved = fpe * evals / (ms * 1e-3) / 1e12
+    n = len(hits)
+    seeds = pair.planted.params.numpy()[:256]
+    t0 = time.perf_counter()
+    o = oref.continuation(pair.surface, seeds, alphas.numpy(), param="u", max_jump=0.05)
+    cpu_s = time.perf_counter() - t0
+    o_evals = int(o["iters"].sum() + np.isin(o["status"], (0, 1, 2, 5, 6)).sum())
+    final = st[:, -1] if n else st
+    return {"branches": n, "steps": n_steps + 1, "dalpha": dalpha, "ms_per_call": ms,
+            "branch_steps_per_s": n * (n_steps + 1) / (ms * 1e-3), "evaluations": evals,
+            "branches_alive_at_end": int((final == 0).sum()),
+            "status_at_end": {tms.CONTINUE_STATUS[k]: int((final == k).sum()) for k in range(8)},
+            "roofline": {"kernel": "tms::k_continue", "bound": "alu (fp64)", "achieved": achieved,
+                         "peak": fp64_tf, "unit": "TFLOP/s", "frac": achieved / fp64_tf,
+                         "flops_per_evaluation": fpe,
+                         "peak_kind": "measured FP64 FMA-chain probe on this GPU"},
+            "cpu_baseline": {"value": cpu_s * 1e3 / max(o_evals, 1), "unit": "ms/evaluation",
+                             "gpu_value": ms / max(evals, 1), "cores": 1, "kind": "oracle",
+                             "sample": f"{len(seeds)} planted-record branches of the same meshes "
+                                       "over the same steps, numpy FP64 vectorised over branches"}}
+
+
 def cpu_baseline(pair):
     import oracle
     OA, OB = oracle.OMesh.from_grid(pair.A), oracle.OMesh.from_grid(pair.B)
@@ -577,8 +628,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--extras", action="store_true",
-                    help="also time the plain FP64 path, the batched 256-pair search, the adjoint "
-                         "and the refinement of the hits")
+                    help="also time the plain FP64 path, the batched 256-pair search, the adjoint, "
+                         "the refinement of the hits and their continuation")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()

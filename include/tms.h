@@ -291,8 +291,8 @@ tms_status tms_noalloc_footprint(unsigned long long *needed, unsigned long long 
  *                                   + (cb_k + a dcb_k) sin k theta) / k
  *   g(s)            = 1 + s (stretch 0) or lam^s (stretch 1)
  *   F(s)            = sum_f fold_amp_f (s - r_f1)(s - r_f2)(s - r_f3) fold_dir_f
- *   W_A(theta, s)   = S(theta, s; alpha)
- *   W_B(theta, s)   = S(theta + c0, 1 - s; alpha)
+ *   W_A(theta, s)   = S(theta, s; alpha_u)
+ *   W_B(theta, s)   = S(theta + c0, 1 - s; alpha_s)
  *                     + h_amp (sin(P (theta - theta0)) n1 + sin(Q pi (s - s0)) n2)
  *   n_r(theta, s)   = v_r - t1 y1 - t2 y2,  (y1, y2) = (J^T J + eps I)^{-1} J^T v_r,
  *                     J = [t1 t2] = the theta- and s-partials of
@@ -311,7 +311,8 @@ typedef struct {
     double cb[TMS_SURF_MAX_HARMONICS][4];
     double dca[TMS_SURF_MAX_HARMONICS][4];   /* derivatives in the family parameter */
     double dcb[TMS_SURF_MAX_HARMONICS][4];
-    double alpha;               /* family parameter of both sheets */
+    double alpha_u;             /* family parameter of W_A (the paper's omega_u) */
+    double alpha_s;             /* family parameter of B's sheet (omega_s) */
     double alpha_ref;           /* family parameter of the normal frame */
     double lam;                 /* stretch base (stretch 1), > 0 */
     double fold_amp[TMS_SURF_MAX_FOLDS];
@@ -372,6 +373,63 @@ tms_status tms_refine(const tms_surface_pair *surf, const tms_refine_params *par
                       const double *dX0, long long ldx0, long long n, double *dX,
                       double *dFnorm, double *dRho, int32_t *dIters, int32_t *dStatus,
                       void *stream);
+
+/*
+ * Continuation of connections through the torus families (Sec. 8, Eq.
+ * predictor): the family parameter alpha_u of W_A (param 0) or alpha_s of B's
+ * sheet (param 1) -- the paper's rotation numbers omega_u, omega_s -- walks
+ * alpha_0 (the pair's own value), alpha_1, ..., alpha_nSteps while the other is
+ * held.  Per branch (one per seed) and step j:
+ *   predictor  j = 0: the seed; j = 1: x_0;
+ *              j >= 2: x_{j-1} + (alpha_j - alpha_{j-1}) / (alpha_{j-1} - alpha_{j-2})
+ *                                (x_{j-1} - x_{j-2}), angle differences in [-pi, pi]
+ *              (consecutive parameter values must differ);
+ *   corrector  tms_refine's damped Newton at alpha_j (params.corrector);
+ *   monitor    a converged step whose point lies farther than max_jump from its
+ *              prediction in some coordinate (angles on the circle) is
+ *              TMS_CONT_JUMPED; else one whose normalised det Df is below
+ *              rho_turn in magnitude or of the other sign than at step j-1 is
+ *              TMS_CONT_TURNING (a fold of the branch).
+ * A branch stops at its first step that is not TMS_REFINE_CONVERGED (the
+ * corrector's status, TURNING or JUMPED; that step's x is kept); its later
+ * steps are TMS_CONT_STOPPED with NaN outputs.
+ */
+enum {
+    TMS_CONT_TURNING = 5,
+    TMS_CONT_JUMPED = 6,
+    TMS_CONT_STOPPED = 7
+};
+
+typedef struct {
+    tms_refine_params corrector;  /* damped Newton of every step */
+    double rho_turn;              /* >= 0 */
+    double max_jump;              /* > 0 */
+    int param;                    /* 0: continue in alpha_u; 1: in alpha_s */
+    int pad;
+} tms_continue_params;
+
+/* corrector = tms_refine_params_default(), rho_turn = 1e-8, max_jump = 0.25,
+ * param = 0. */
+void tms_continue_params_default(tms_continue_params *p);
+
+/*
+ * tms_continue -- nBranches independent continuations.
+ *   surf, params : host; params may be NULL (defaults).
+ *   dAlphas      : device, nSteps parameter values alpha_1..alpha_nSteps
+ *                  (may be NULL when nSteps is 0).
+ *   dX0          : device, seed b at dX0[b*ldx0 + 0..3], ldx0 >= 4.
+ *   dX           : device, nBranches*(nSteps+1)*4 doubles: step j of branch b
+ *                  at [(b*(nSteps+1) + j)*4], angles in [0, 2 pi).
+ *   dStatus      : device, nBranches*(nSteps+1) int32 (TMS_REFINE_*, TMS_CONT_*).
+ *   dIters, dRho, dFnorm : device, same count, or NULL: corrector updates, det Df /
+ *                  prod of column norms and ||f||_2 at the step's last evaluation.
+ * Asynchronous on `stream`; allocates nothing.  TMS_ERR_ARG on a bad argument,
+ * TMS_ERR_CUDA on a launch failure.
+ */
+tms_status tms_continue(const tms_surface_pair *surf, const tms_continue_params *params,
+                        const double *dAlphas, int nSteps, const double *dX0, long long ldx0,
+                        long long nBranches, double *dX, int32_t *dStatus, int32_t *dIters,
+                        double *dRho, double *dFnorm, void *stream);
 
 /* Per-stage device time (ms) of the last search on `stream` made with
  * params.timing = 1, in this order:

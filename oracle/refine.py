@@ -9,7 +9,10 @@ solving Eq. (tosolve),
 with the damped Newton iteration of Eq. (dampedNewtonEquation),
     x_{k+1} = x_k - alpha Df(x_k)^{-1} f(x_k),
     Df = [d f/d theta_u, d f/d s_u, d f/d theta_s, d f/d s_s],
-iterating until f is within a tolerance.  In the paper W and its partials come
+iterating until f is within a tolerance.  W_A is taken at the family parameter
+alpha_u and the sheet under W_B at alpha_s (both default to the pair's alpha),
+standing in for the two tori's rotation numbers omega_u, omega_s of Sec. 8.
+In the paper W and its partials come
 from Fourier-Taylor series and the flow (Eqs. wuequation-dwsdsequation); here
 the two manifolds are the closed-form synthetic sheets that the seeded meshes
 sample (synth.SurfacePair), and the partials are their exact derivatives,
@@ -29,6 +32,7 @@ Readings of the paper taken here (the paper fixes none of them):
 """
 from __future__ import annotations
 
+import copy
 import math
 
 import numpy as np
@@ -44,6 +48,11 @@ DEFAULTS = dict(alpha0=0.5, alpha1=0.5, switch_below=0.0, tol=1e-10, max_iter=20
 
 def _np(t):
     return np.asarray(t.detach().cpu().numpy() if hasattr(t, "detach") else t, dtype=np.float64)
+
+
+def alphas(sp):
+    """(alpha_u, alpha_s): the family parameters of W_A and of B's sheet."""
+    return float(getattr(sp, "alpha_u", sp.alpha)), float(getattr(sp, "alpha_s", sp.alpha))
 
 
 def _coeffs(sp, alpha):
@@ -136,7 +145,7 @@ def frame(sp, theta, s):
 
 def surface_A(sp, theta, s):
     """W_A and its partials (n, 4): (W, W_theta, W_s)."""
-    S = sheet(sp, theta, s, sp.alpha)
+    S = sheet(sp, theta, s, alphas(sp)[0])
     return S["W"], S["Wt"], S["Ws"]
 
 
@@ -144,7 +153,7 @@ def surface_B(sp, theta, s):
     """W_B and its partials (n, 4): (W, W_theta, W_s)."""
     theta = np.atleast_1d(np.asarray(theta, dtype=np.float64))
     s = np.atleast_1d(np.asarray(s, dtype=np.float64))
-    S = sheet(sp, theta + sp.c0, 1.0 - s, sp.alpha)
+    S = sheet(sp, theta + sp.c0, 1.0 - s, alphas(sp)[1])
     fr = frame(sp, theta, s)
     ph1 = sp.P * (theta - sp.theta0)
     ph2 = sp.Q * math.pi * (s - sp.s0)
@@ -239,3 +248,83 @@ def site_roots(sp):
     (theta, s) of B, x* = (theta + c0 mod 2 pi, 1 - s, theta, s)."""
     st = _np(sp.sites)
     return np.stack([np.mod(st[:, 0] + sp.c0, TWO_PI), 1.0 - st[:, 1], st[:, 0], st[:, 1]], axis=1)
+
+
+# ---------------------------------------------------------------------------
+# continuation of connections through the family parameter (Sec. 8)
+# ---------------------------------------------------------------------------
+
+TURNING, JUMPED, STOPPED = 5, 6, 7
+CONT_STATUS_NAMES = STATUS_NAMES + ("turning", "jumped", "stopped")
+
+
+def with_alphas(sp, alpha_u, alpha_s):
+    """A shallow copy of the sheet pair at (alpha_u, alpha_s)."""
+    out = copy.copy(sp)
+    out.alpha_u, out.alpha_s = float(alpha_u), float(alpha_s)
+    return out
+
+
+def continuation(sp, x0, alpha_steps, param: str = "u", rho_turn: float = 1e-8,
+                 max_jump: float = 0.25, **kw):
+    """Continuation of connections x(alpha) (Sec. 8, Eq. predictor) through the
+    values alpha_steps (K,) of alpha_u (param "u") or alpha_s ("s"), the other
+    parameter held at the pair's value.  Step 0 corrects the seeds x0 (n, 4) at
+    the pair's own parameters; step j >= 1 at alpha_j predicts
+        j = 1:  x_0
+        j >= 2: x_{j-1} + (alpha_j - alpha_{j-1}) / (alpha_{j-1} - alpha_{j-2}) (x_{j-1} - x_{j-2})
+    (theta differences taken on the circle, in [-pi, pi]) and corrects by
+    damped_newton(**kw) at alpha_j.  A branch stops at the first step whose
+    corrector does not converge (that step keeps the corrector's status), whose
+    corrected point lies farther than max_jump from its prediction in some
+    coordinate (theta on the circle; JUMPED: the corrector left the branch), or
+    whose normalised det Df is below rho_turn in magnitude or has the other sign
+    than at the previous step (TURNING); x is kept for those steps.  Later steps
+    are STOPPED with NaN outputs.  Returns x (n, K+1, 4), status, iters (n, K+1), rho, fnorm (n, K+1)
+    and the parameter values (K+1,)."""
+    au, as_ = alphas(sp)
+    a0 = au if param == "u" else as_
+    avals = np.concatenate([[a0], np.asarray(alpha_steps, dtype=np.float64)])
+    x0 = np.atleast_2d(np.asarray(x0, dtype=np.float64))
+    n, K1 = x0.shape[0], avals.size
+    X = np.full((n, K1, 4), np.nan)
+    G = np.full((n, K1, 4), np.nan)
+    ST = np.full((n, K1), STOPPED, dtype=np.int64)
+    IT = np.zeros((n, K1), dtype=np.int64)
+    RH = np.full((n, K1), np.nan)
+    FN = np.full((n, K1), np.nan)
+    alive = np.ones(n, dtype=bool)
+    for j in range(K1):
+        idx = np.nonzero(alive)[0]
+        if idx.size == 0:
+            break
+        if j == 0:
+            guess = x0[idx]
+        elif j == 1:
+            guess = X[idx, 0]
+        else:
+            d = X[idx, j - 1] - X[idx, j - 2]
+            d[:, [0, 2]] -= TWO_PI * np.round(d[:, [0, 2]] / TWO_PI)
+            guess = X[idx, j - 1] + (avals[j] - avals[j - 1]) / (avals[j - 1] - avals[j - 2]) * d
+        G[idx, j] = guess
+        spj = with_alphas(sp, avals[j] if param == "u" else au, avals[j] if param == "s" else as_)
+        r = damped_newton(spj, guess, **kw)
+        X[idx, j] = r["x"]
+        IT[idx, j] = r["iters"]
+        RH[idx, j] = r["rho"]
+        FN[idx, j] = r["fnorm"]
+        st = r["status"].copy()
+        conv = st == CONVERGED
+        dj = np.abs(r["x"] - guess)
+        dj[:, [0, 2]] = np.abs(dj[:, [0, 2]] - TWO_PI * np.round(dj[:, [0, 2]] / TWO_PI))
+        jump = conv & ~(dj.max(axis=1) <= max_jump)
+        turn = conv & ~jump & ~(np.abs(r["rho"]) >= rho_turn)
+        if j > 0:
+            turn |= conv & ~jump & ((r["rho"] > 0) != (RH[idx, j - 1] > 0))
+        st[turn] = TURNING
+        st[jump] = JUMPED
+        ST[idx, j] = st
+        alive[idx[st != CONVERGED]] = False
+    stopped = ST == STOPPED
+    X[stopped] = np.nan
+    return dict(x=X, status=ST, iters=IT, rho=RH, fnorm=FN, alphas=avals, predicted=G)

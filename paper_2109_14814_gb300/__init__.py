@@ -3,19 +3,22 @@
 Finds every intersecting triangle pair between two manifold meshes in R^4
 (arXiv 2109.14814, Sec. 6): uniform-grid broad phase with bounding boxes, FP64
 narrow phase solving the 4x4 system for (a, b, c, d), merged and sorted hits,
-a batched form replayed from a CUDA graph, an FP64 adjoint, and the damped-Newton
-refinement of hits on the true surfaces (Sec. 7).  All compute is
+a batched form replayed from a CUDA graph, an FP64 adjoint, the damped-Newton
+refinement of hits on the true surfaces (Sec. 7) and its continuation through
+the family parameter (Sec. 8).  All compute is
 in libtms.so (C ABI in include/tms.h); this package only marshals arguments.
 """
-from ._binding import (HIT_BYTES, REFINE_STATUS, STAGES, Refined, RefineParams, SurfacePair,
-                       refine, refine_params, surface_pair, TMS_ERR_ARG, TMS_ERR_CAPACITY, TMS_ERR_CUDA,
+from ._binding import (CONTINUE_STATUS, HIT_BYTES, REFINE_STATUS, STAGES, ContinueParams, Continued,
+                       Refined, RefineParams, SurfacePair, continue_branches, refine, refine_params,
+                       surface_pair, TMS_ERR_ARG, TMS_ERR_CAPACITY, TMS_ERR_CUDA,
                        TMS_ERR_STATE, TMS_ERR_TIMEOUT, TMS_OK, HitPoint, Hits, Mesh, Params, Stats,
                        TmsError, autotune, backward, last_error, last_stage_ms, last_stats, lib, params,
                        probe_fp64_tflops, release_workspace, search, search_batched,
                        search_noalloc, status_str, version)
 
-__all__ = ["HIT_BYTES", "REFINE_STATUS", "STAGES", "Refined", "RefineParams", "SurfacePair",
-           "refine", "refine_params", "surface_pair", "TMS_ERR_ARG", "TMS_ERR_CAPACITY", "TMS_ERR_CUDA",
+__all__ = ["CONTINUE_STATUS", "HIT_BYTES", "REFINE_STATUS", "STAGES", "ContinueParams", "Continued",
+           "Refined", "RefineParams", "SurfacePair", "continue_branches", "refine", "refine_params",
+           "surface_pair", "TMS_ERR_ARG", "TMS_ERR_CAPACITY", "TMS_ERR_CUDA",
            "TMS_ERR_STATE", "TMS_ERR_TIMEOUT", "TMS_OK", "HitPoint", "Hits", "Mesh", "Params",
            "Stats", "TmsError", "autotune", "backward", "last_error", "last_stage_ms", "last_stats", "lib",
            "params", "probe_fp64_tflops", "release_workspace", "search", "search_batched",

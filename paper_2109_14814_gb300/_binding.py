@@ -82,7 +82,8 @@ class SurfacePair(ctypes.Structure):
         ("n_harmonics", _c.c_int), ("n_folds", _c.c_int), ("stretch", _c.c_int), ("pad", _c.c_int),
         ("ca", (_c.c_double * 4) * 8), ("cb", (_c.c_double * 4) * 8),
         ("dca", (_c.c_double * 4) * 8), ("dcb", (_c.c_double * 4) * 8),
-        ("alpha", _c.c_double), ("alpha_ref", _c.c_double), ("lam", _c.c_double),
+        ("alpha_u", _c.c_double), ("alpha_s", _c.c_double), ("alpha_ref", _c.c_double),
+        ("lam", _c.c_double),
         ("fold_amp", _c.c_double * 4), ("fold_root", (_c.c_double * 3) * 4),
         ("fold_dir", (_c.c_double * 4) * 4),
         ("c0", _c.c_double), ("h_amp", _c.c_double), ("P", _c.c_double), ("Q", _c.c_double),
@@ -100,7 +101,14 @@ class RefineParams(ctypes.Structure):
     ]
 
 
+class ContinueParams(ctypes.Structure):
+    """Mirror of tms_continue_params."""
+    _fields_ = [("corrector", RefineParams), ("rho_turn", _c.c_double), ("max_jump", _c.c_double),
+                ("param", _c.c_int), ("pad", _c.c_int)]
+
+
 REFINE_STATUS = ("converged", "max_iter", "singular", "escaped", "non_finite")
+CONTINUE_STATUS = REFINE_STATUS + ("turning", "jumped", "stopped")
 
 
 def lib():
@@ -151,6 +159,11 @@ def lib():
     L.tms_refine.argtypes = [_c.POINTER(SurfacePair), _c.POINTER(RefineParams), P, LL, LL, P, P, P,
                              P, P, P]
     L.tms_refine.restype = I
+    L.tms_continue_params_default.argtypes = [_c.POINTER(ContinueParams)]
+    L.tms_continue_params_default.restype = None
+    L.tms_continue.argtypes = [_c.POINTER(SurfacePair), _c.POINTER(ContinueParams), P, I, P, LL, LL,
+                               P, P, P, P, P, P]
+    L.tms_continue.restype = I
     _lib = L
     return L
 
@@ -425,9 +438,11 @@ def last_stage_ms(stream=None) -> dict:
     return {STAGES[i]: float(buf[i]) for i in range(min(n.value, len(STAGES)))}
 
 
-def surface_pair(sp) -> SurfacePair:
+def surface_pair(sp, alpha_u=None, alpha_s=None) -> SurfacePair:
     """tms_surface_pair from a description with the fields of synth.SurfacePair
-    (coefficient tables (K, 4), fold tables (F, 3) and (F, 4), scalars)."""
+    (coefficient tables (K, 4), fold tables (F, 3) and (F, 4), scalars).  W_A is
+    taken at alpha_u and B's sheet at alpha_s; each defaults to the
+    description's alpha_u / alpha_s attribute, else its alpha."""
     def rows(t):
         return [[float(v) for v in r] for r in (t.tolist() if hasattr(t, "tolist") else t)]
     out = SurfacePair()
@@ -452,8 +467,10 @@ def surface_pair(sp) -> SurfacePair:
             out.fold_dir[f][c] = dirs[f][c]
     out.stretch = {"linear": 0, "exp": 1}[sp.stretch]
     out.lam = float(sp.lam)
-    for name in ("alpha", "alpha_ref", "c0", "h_amp", "P", "Q", "theta0", "s0", "reg"):
+    for name in ("alpha_ref", "c0", "h_amp", "P", "Q", "theta0", "s0", "reg"):
         setattr(out, name, float(getattr(sp, name)))
+    out.alpha_u = float(alpha_u if alpha_u is not None else getattr(sp, "alpha_u", sp.alpha))
+    out.alpha_s = float(alpha_s if alpha_s is not None else getattr(sp, "alpha_s", sp.alpha))
     v1 = sp.v1.tolist() if hasattr(sp.v1, "tolist") else sp.v1
     v2 = sp.v2.tolist() if hasattr(sp.v2, "tolist") else sp.v2
     for c in range(4):
@@ -513,6 +530,59 @@ def refine(surface, seeds, stream=None, out: Optional[Refined] = None, **kw) -> 
                           _stream(stream))
     if rc != TMS_OK:
         raise TmsError(rc, "tms_refine")
+    return out
+
+
+@dataclass
+class Continued:
+    """tms_continue output on the device; step j of branch b at [b, j]."""
+    x: torch.Tensor        # (n, K+1, 4) float64
+    status: torch.Tensor   # (n, K+1) int32, index into CONTINUE_STATUS
+    iters: torch.Tensor    # (n, K+1) int32
+    rho: torch.Tensor      # (n, K+1) float64
+    fnorm: torch.Tensor    # (n, K+1) float64
+    alphas: torch.Tensor   # (K+1,) float64: the start value, then the steps
+
+
+def continue_branches(surface, seeds, alphas, param: str = "u", stream=None, rho_turn=None,
+                      max_jump=None, **kw) -> Continued:
+    """tms_continue: continuation (Sec. 8) of each seed's connection through the
+    parameter values `alphas` (K,) of alpha_u (param "u") or alpha_s ("s").
+    seeds: CUDA float64 (n, 4) with unit column stride, or a Hits.  **kw are
+    corrector (tms_refine_params) fields."""
+    sp = surface if isinstance(surface, SurfacePair) else surface_pair(surface)
+    p = ContinueParams()
+    lib().tms_continue_params_default(_c.byref(p))
+    p.corrector = refine_params(**kw)
+    p.param = {"u": 0, "s": 1}[param]
+    if rho_turn is not None:
+        p.rho_turn = rho_turn
+    if max_jump is not None:
+        p.max_jump = max_jump
+    if isinstance(seeds, Hits):
+        n, dev = len(seeds), seeds.raw.device
+        ptr, ld = (seeds.raw.data_ptr() + 10 * 8 if n else None), HIT_BYTES // 8
+    else:
+        if not (seeds.is_cuda and seeds.dtype == torch.float64 and seeds.dim() == 2
+                and seeds.shape[1] == 4 and seeds.stride(1) == 1):
+            raise ValueError("seeds must be a CUDA float64 (n, 4) tensor with unit column stride")
+        n, dev = int(seeds.shape[0]), seeds.device
+        ptr, ld = (seeds.data_ptr() if n else None), max(int(seeds.stride(0)), 4)
+    a = torch.as_tensor(alphas, dtype=torch.float64).reshape(-1).to(dev).contiguous()
+    K = int(a.numel())
+    start = sp.alpha_u if p.param == 0 else sp.alpha_s
+    out = Continued(torch.empty((n, K + 1, 4), dtype=torch.float64, device=dev),
+                    torch.empty((n, K + 1), dtype=torch.int32, device=dev),
+                    torch.empty((n, K + 1), dtype=torch.int32, device=dev),
+                    torch.empty((n, K + 1), dtype=torch.float64, device=dev),
+                    torch.empty((n, K + 1), dtype=torch.float64, device=dev),
+                    torch.cat([torch.tensor([start], dtype=torch.float64, device=dev), a]))
+    rc = lib().tms_continue(_c.byref(sp), _c.byref(p), a.data_ptr() if K else None, K, ptr, ld, n,
+                            _dptr(out.x) if n else None, _dptr(out.status) if n else None,
+                            _dptr(out.iters) if n else None, _dptr(out.rho) if n else None,
+                            _dptr(out.fnorm) if n else None, _stream(stream))
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_continue")
     return out
 
 

@@ -44,18 +44,79 @@ struct RefineArgs {
     int *status;
 };
 
+struct ContArgs {
+    tms_surface_pair sp;
+    tms_continue_params p;
+    const double *alphas;   // nSteps values after the start
+    int steps;              // nSteps
+    const double *x0;
+    long long ld;
+    long long n;
+    double *x;
+    int *status;
+    int *iters;
+    double *rho;
+    double *fnorm;
+};
+
 // Per-block tables, coordinate fastest (lane c reads column c).  With
-// a_k = ca_k + alpha dca_k, b_k likewise (and a_k^r, b_k^r at alpha_ref):
+// a_k = ca_k + alpha dca_k, b_k likewise:
 //   T   = sum (a_k/k) cos + (b_k/k) sin     T' = sum b_k cos + (-a_k) sin
 //   T'' = sum (-k a_k) cos + (-k b_k) sin
-// so every harmonic term is two fused multiply-adds.
+// so every harmonic term is two fused multiply-adds.  W_A's sheet is taken at
+// alpha_u, B's underlying sheet at alpha_s, the normal frame at alpha_ref.
 struct Coef {
-    double ak[kH][4], bk[kH][4], na[kH][4], b[kH][4];        // at alpha
-    double ark[kH][4], brk[kH][4], nar[kH][4], br[kH][4];    // at alpha_ref
+    double uak[kH][4], ubk[kH][4], una[kH][4], ub[kH][4];     // at alpha_u
+    double sak[kH][4], sbk[kH][4], sna[kH][4], sb[kH][4];     // at alpha_s
+    double ark[kH][4], brk[kH][4], nar[kH][4], br[kH][4];     // at alpha_ref
     double kar[kH][4], kbr[kH][4];                            // at alpha_ref, T''
     double fd[kF][4];               // fold_amp * fold_dir
     double root[kF][3];             // fold roots
     double v1[4], v2[4];
+};
+
+// Fills the tables for (alpha_u, alpha_s); called by every thread of the block
+// between two barriers.
+__device__ void build_tables(Coef &cf, const tms_surface_pair &sp, double au, double as, int t,
+                             int nt) {
+    for (int q = t; q < kH * 4; q += nt) {
+        const int h = q >> 2, c = q & 3;
+        const double k = (double)(h + 1);
+        const double a = sp.ca[h][c] + au * sp.dca[h][c];
+        const double b = sp.cb[h][c] + au * sp.dcb[h][c];
+        const double a2 = sp.ca[h][c] + as * sp.dca[h][c];
+        const double b2 = sp.cb[h][c] + as * sp.dcb[h][c];
+        const double ar = sp.ca[h][c] + sp.alpha_ref * sp.dca[h][c];
+        const double br = sp.cb[h][c] + sp.alpha_ref * sp.dcb[h][c];
+        cf.uak[h][c] = a / k;
+        cf.ubk[h][c] = b / k;
+        cf.una[h][c] = -a;
+        cf.ub[h][c] = b;
+        cf.sak[h][c] = a2 / k;
+        cf.sbk[h][c] = b2 / k;
+        cf.sna[h][c] = -a2;
+        cf.sb[h][c] = b2;
+        cf.ark[h][c] = ar / k;
+        cf.brk[h][c] = br / k;
+        cf.nar[h][c] = -ar;
+        cf.br[h][c] = br;
+        cf.kar[h][c] = -k * ar;
+        cf.kbr[h][c] = -k * br;
+    }
+    if (t < kF * 4) cf.fd[t >> 2][t & 3] = sp.fold_amp[t >> 2] * sp.fold_dir[t >> 2][t & 3];
+    if (t < kF * 3) cf.root[t / 3][t % 3] = sp.fold_root[t / 3][t % 3];
+    if (t < 4) {
+        cf.v1[t] = sp.v1[t];
+        cf.v2[t] = sp.v2[t];
+    }
+}
+
+// One seed's Newton solve, held identically by the quad's four lanes.
+struct Solve {
+    double x0, x1, x2, x3;   // iterate (angles unwrapped)
+    int code;                // -1 while iterating, else TMS_REFINE_*
+    int iters;               // updates made
+    double fn, rh, rc2;      // ||f||^2, det Df, prod ||Df e_j||^2 at the last evaluation
 };
 
 __device__ __forceinline__ double quad_sum(double v) {
@@ -77,58 +138,19 @@ __device__ __forceinline__ void cubic(double s, const double *r, double &p, doub
     p2 = 2.0 * (d0 + d1 + d2);
 }
 
-__global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ RefineArgs a) {
-    __shared__ Coef cf;
-    const tms_surface_pair &sp = a.sp;
-    const tms_refine_params &pr = a.p;
-    const int t = threadIdx.x;
-    for (int q = t; q < kH * 4; q += kThreads) {
-        const int h = q >> 2, c = q & 3;
-        const double k = (double)(h + 1);
-        const double a = sp.ca[h][c] + sp.alpha * sp.dca[h][c];
-        const double b = sp.cb[h][c] + sp.alpha * sp.dcb[h][c];
-        const double ar = sp.ca[h][c] + sp.alpha_ref * sp.dca[h][c];
-        const double br = sp.cb[h][c] + sp.alpha_ref * sp.dcb[h][c];
-        cf.ak[h][c] = a / k;
-        cf.bk[h][c] = b / k;
-        cf.na[h][c] = -a;
-        cf.b[h][c] = b;
-        cf.ark[h][c] = ar / k;
-        cf.brk[h][c] = br / k;
-        cf.nar[h][c] = -ar;
-        cf.br[h][c] = br;
-        cf.kar[h][c] = -k * ar;
-        cf.kbr[h][c] = -k * br;
-    }
-    if (t < kF * 4) cf.fd[t >> 2][t & 3] = sp.fold_amp[t >> 2] * sp.fold_dir[t >> 2][t & 3];
-    if (t < kF * 3) cf.root[t / 3][t % 3] = sp.fold_root[t / 3][t % 3];
-    if (t < 4) {
-        cf.v1[t] = sp.v1[t];
-        cf.v2[t] = sp.v2[t];
-    }
-    __syncthreads();
-
-    const int lane = t & 31;
-    const int c = lane & 3;
-    const int base = lane & ~3;
-    const long long i = (long long)blockIdx.x * kSeedsPerBlock + (t >> 2);
-    const bool live = i < a.n;
-    double x0 = 0.0, x1 = 0.5, x2 = 0.0, x3 = 0.5;
-    if (live) {
-        const double *s = a.x0 + i * a.ld;
-        x0 = s[0];
-        x1 = s[1];
-        x2 = s[2];
-        x3 = s[3];
-    }
-    int code = live ? -1 : TMS_REFINE_CONVERGED;
-    int iters = 0;
-    double fn = __longlong_as_double(0x7ff8000000000000LL);   // ||f||^2, NaN until evaluated
-    double rh = fn, rc2 = 1.0;                                 // det Df, prod ||col||^2
+// Damped Newton (Eq. dampedNewtonEquation) on f = W_A - W_B from S's iterate
+// until S.code is set; every lane of the warp calls it (the loop runs while any
+// of the warp's quads iterates).
+__device__ __forceinline__ void newton_solve(const Coef &cf, const tms_surface_pair &sp,
+                                             const tms_refine_params &pr, Solve &S, int c,
+                                             int base) {
     const double tol2 = pr.tol * pr.tol, sw2 = pr.switch_below * pr.switch_below;
     const int K = sp.n_harmonics;
     const int NF = sp.n_folds;
     const double lnlam = sp.stretch ? log(sp.lam) : 0.0;
+    double x0 = S.x0, x1 = S.x1, x2 = S.x2, x3 = S.x3;
+    int code = S.code, iters = S.iters;
+    double fn = S.fn, rh = S.rh, rc2 = S.rc2;
 
     for (int k = 0; __any_sync(kFull, code < 0); ++k) {
         // ---- stop checks on the iterate (identical on the quad's lanes)
@@ -186,17 +208,17 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
             }
         }
 
-        // ---- harmonic sums: T, T' at theta_u (alpha); T, T' at theta' (alpha);
+        // ---- harmonic sums: T, T' at theta_u (alpha_u); T, T' at theta' (alpha_s);
         //      T, T', T'' at theta' (alpha_ref).  cos/sin of k theta by angle addition.
         double TA = 0.0, TAt = 0.0, TB = 0.0, TBt = 0.0, TR = 0.0, TRt = 0.0, TRtt = 0.0;
         double ckA = cA, skA = sA, ckB = cB, skB = sB;
 #pragma unroll
         for (int h = 0; h < kH; ++h) {
             if (h < K) {
-                TA = fma(cf.ak[h][c], ckA, fma(cf.bk[h][c], skA, TA));
-                TAt = fma(cf.b[h][c], ckA, fma(cf.na[h][c], skA, TAt));
-                TB = fma(cf.ak[h][c], ckB, fma(cf.bk[h][c], skB, TB));
-                TBt = fma(cf.b[h][c], ckB, fma(cf.na[h][c], skB, TBt));
+                TA = fma(cf.uak[h][c], ckA, fma(cf.ubk[h][c], skA, TA));
+                TAt = fma(cf.ub[h][c], ckA, fma(cf.una[h][c], skA, TAt));
+                TB = fma(cf.sak[h][c], ckB, fma(cf.sbk[h][c], skB, TB));
+                TBt = fma(cf.sb[h][c], ckB, fma(cf.sna[h][c], skB, TBt));
                 TR = fma(cf.ark[h][c], ckB, fma(cf.brk[h][c], skB, TR));
                 TRt = fma(cf.br[h][c], ckB, fma(cf.nar[h][c], skB, TRt));
                 TRtt = fma(cf.kar[h][c], ckB, fma(cf.kbr[h][c], skB, TRtt));
@@ -358,22 +380,172 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
             }
         }
     }
+    S.x0 = x0;
+    S.x1 = x1;
+    S.x2 = x2;
+    S.x3 = x3;
+    S.code = code;
+    S.iters = iters;
+    S.fn = fn;
+    S.rh = rh;
+    S.rc2 = rc2;
+}
+
+__device__ __forceinline__ double wrap_angle(double v) {
+    double w = fmod(v, kTwoPi);
+    if (w < 0.0) w += kTwoPi;
+    else if (w == 0.0) w = 0.0;   // +0 for a -0 remainder
+    return w;
+}
+
+__device__ __forceinline__ double nan_value() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+__global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ RefineArgs a) {
+    __shared__ Coef cf;
+    const tms_surface_pair &sp = a.sp;
+    const int t = threadIdx.x;
+    build_tables(cf, sp, sp.alpha_u, sp.alpha_s, t, kThreads);
+    __syncthreads();
+
+    const int lane = t & 31;
+    const int c = lane & 3;
+    const int base = lane & ~3;
+    const long long i = (long long)blockIdx.x * kSeedsPerBlock + (t >> 2);
+    const bool live = i < a.n;
+    Solve S;
+    S.x0 = 0.0;
+    S.x1 = 0.5;
+    S.x2 = 0.0;
+    S.x3 = 0.5;
+    if (live) {
+        const double *s = a.x0 + i * a.ld;
+        S.x0 = s[0];
+        S.x1 = s[1];
+        S.x2 = s[2];
+        S.x3 = s[3];
+    }
+    S.code = live ? -1 : TMS_REFINE_CONVERGED;
+    S.iters = 0;
+    S.fn = nan_value();
+    S.rh = S.fn;
+    S.rc2 = 1.0;
+    newton_solve(cf, sp, a.p, S, c, base);
 
     if (live) {
-        double xc = c == 0 ? x0 : c == 1 ? x1 : c == 2 ? x2 : x3;
-        if (c == 0 || c == 2) {
-            double w = fmod(xc, kTwoPi);
-            if (w < 0.0) w += kTwoPi;
-            else if (w == 0.0) w = 0.0;   // +0 for a -0 remainder
-            xc = w;
-        }
+        double xc = c == 0 ? S.x0 : c == 1 ? S.x1 : c == 2 ? S.x2 : S.x3;
+        if (c == 0 || c == 2) xc = wrap_angle(xc);
         a.x[i * 4 + c] = xc;
         if (c == 0) {
-            if (a.fnorm) a.fnorm[i] = sqrt(fn);
-            if (a.rho) a.rho[i] = rh / sqrt(rc2);
-            if (a.iters) a.iters[i] = iters;
-            if (a.status) a.status[i] = code;
+            if (a.fnorm) a.fnorm[i] = sqrt(S.fn);
+            if (a.rho) a.rho[i] = S.rh / sqrt(S.rc2);
+            if (a.iters) a.iters[i] = S.iters;
+            if (a.status) a.status[i] = S.code;
         }
+    }
+}
+
+// Continuation (Sec. 8): one quad per branch walks the parameter values
+// alpha_0 (the pair's own), alphas[0..steps); the tables are rebuilt for every
+// step between two block barriers, so every warp of the block takes part in
+// every step even when its branches have stopped.
+__global__ void __launch_bounds__(kThreads) k_continue(const __grid_constant__ ContArgs a) {
+    __shared__ Coef cf;
+    const tms_surface_pair &sp = a.sp;
+    const tms_continue_params &cp = a.p;
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int c = lane & 3;
+    const int base = lane & ~3;
+    const long long i = (long long)blockIdx.x * kSeedsPerBlock + (t >> 2);
+    const bool live = i < a.n;
+    double x[4] = {0.0, 0.5, 0.0, 0.5};
+    if (live) {
+        const double *s = a.x0 + i * a.ld;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = s[q];
+    }
+    double p1[4] = {0.0, 0.0, 0.0, 0.0}, p2[4] = {0.0, 0.0, 0.0, 0.0};   // x_{j-1}, x_{j-2}
+    bool alive = live;
+    double rho_prev = nan_value();
+    const double a0 = cp.param == 0 ? sp.alpha_u : sp.alpha_s;
+    double am1 = a0, am2 = a0;   // alpha_{j-1}, alpha_{j-2}
+    const long long K1 = (long long)a.steps + 1;
+    for (int j = 0; j <= a.steps; ++j) {
+        const double aj = j == 0 ? a0 : a.alphas[j - 1];
+        __syncthreads();
+        build_tables(cf, sp, cp.param == 0 ? aj : sp.alpha_u, cp.param == 0 ? sp.alpha_s : aj, t,
+                     kThreads);
+        __syncthreads();
+        // predictor, Eq. (predictor); angle differences taken on the circle
+        double g[4];
+        if (j == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) g[q] = x[q];
+        } else if (j == 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) g[q] = p1[q];
+        } else {
+            const double ratio = (aj - am1) / (am1 - am2);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double d = p1[q] - p2[q];
+                if (q == 0 || q == 2) d -= kTwoPi * rint(d / kTwoPi);
+                g[q] = p1[q] + ratio * d;
+            }
+        }
+        Solve S;
+        S.x0 = g[0];
+        S.x1 = g[1];
+        S.x2 = g[2];
+        S.x3 = g[3];
+        S.code = alive ? -1 : TMS_REFINE_CONVERGED;
+        S.iters = 0;
+        S.fn = nan_value();
+        S.rh = S.fn;
+        S.rc2 = 1.0;
+        newton_solve(cf, sp, cp.corrector, S, c, base);
+        const long long o = i * K1 + j;
+        if (alive) {
+            const double xs[4] = {wrap_angle(S.x0), S.x1, wrap_angle(S.x2), S.x3};
+            const double rho = S.rh / sqrt(S.rc2);
+            int st = S.code;
+            if (st == TMS_REFINE_CONVERGED) {
+                double jump = 0.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    double d = fabs(xs[q] - g[q]);
+                    if (q == 0 || q == 2) d = fabs(d - kTwoPi * rint(d / kTwoPi));
+                    jump = fmax(jump, d);
+                }
+                if (!(jump <= cp.max_jump)) st = TMS_CONT_JUMPED;
+                else if (!(fabs(rho) >= cp.rho_turn)) st = TMS_CONT_TURNING;
+                else if (j > 0 && (rho > 0.0) != (rho_prev > 0.0)) st = TMS_CONT_TURNING;
+            }
+            a.x[o * 4 + c] = xs[c];
+            if (c == 0) {
+                a.status[o] = st;
+                if (a.iters) a.iters[o] = S.iters;
+                if (a.rho) a.rho[o] = rho;
+                if (a.fnorm) a.fnorm[o] = sqrt(S.fn);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                p2[q] = p1[q];
+                p1[q] = xs[q];
+            }
+            rho_prev = rho;
+            if (st != TMS_REFINE_CONVERGED) alive = false;
+        } else if (live) {
+            a.x[o * 4 + c] = nan_value();
+            if (c == 0) {
+                a.status[o] = TMS_CONT_STOPPED;
+                if (a.iters) a.iters[o] = 0;
+                if (a.rho) a.rho[o] = nan_value();
+                if (a.fnorm) a.fnorm[o] = nan_value();
+            }
+        }
+        am2 = am1;
+        am1 = aj;
     }
 }
 
@@ -396,6 +568,42 @@ bool is_device_ptr(const void *p) {
 tms_status arg_error(const char *msg) {
     tms::set_last_error(msg);
     return TMS_ERR_ARG;
+}
+
+
+tms_status check_surface(const tms_surface_pair &s, const char *who) {
+    const std::string w(who);
+    if (s.n_harmonics < 1 || s.n_harmonics > TMS_SURF_MAX_HARMONICS)
+        return arg_error((w + ": n_harmonics outside 1..8").c_str());
+    if (s.n_folds < 0 || s.n_folds > TMS_SURF_MAX_FOLDS)
+        return arg_error((w + ": n_folds outside 0..4").c_str());
+    if (s.stretch != 0 && s.stretch != 1) return arg_error((w + ": stretch must be 0 or 1").c_str());
+    if (s.stretch == 1 && !(s.lam > 0.0)) return arg_error((w + ": lam must be > 0").c_str());
+    bool fin = true;
+    for (int h = 0; h < s.n_harmonics; ++h)
+        fin = fin && all_finite(s.ca[h], 4) && all_finite(s.cb[h], 4) && all_finite(s.dca[h], 4) &&
+              all_finite(s.dcb[h], 4);
+    for (int f = 0; f < s.n_folds; ++f)
+        fin = fin && isfinite(s.fold_amp[f]) && all_finite(s.fold_root[f], 3) &&
+              all_finite(s.fold_dir[f], 4);
+    const size_t ns = (sizeof(tms_surface_pair) - offsetof(tms_surface_pair, c0)) / sizeof(double);
+    fin = fin && isfinite(s.alpha_u) && isfinite(s.alpha_s) && isfinite(s.alpha_ref) &&
+          (s.stretch == 0 || isfinite(s.lam)) && all_finite(&s.c0, ns);
+    if (!fin) return arg_error((w + ": non-finite surface value").c_str());
+    if (!(s.reg >= 0.0)) return arg_error((w + ": reg must be >= 0").c_str());
+    return TMS_OK;
+}
+
+tms_status check_corrector(const tms_refine_params &p, const char *who) {
+    const std::string w(who);
+    if (!(p.alpha0 > 0.0 && p.alpha0 <= 1.0 && p.alpha1 > 0.0 && p.alpha1 <= 1.0))
+        return arg_error((w + ": alpha0 and alpha1 must lie in (0, 1]").c_str());
+    if (!(p.tol >= 0.0) || !(p.switch_below >= 0.0) || !(p.rho_min >= 0.0))
+        return arg_error((w + ": tol, switch_below and rho_min must be >= 0").c_str());
+    if (!(p.s_lo < p.s_hi)) return arg_error((w + ": need s_lo < s_hi").c_str());
+    if (p.max_iter < 0 || p.max_iter > 1000000)
+        return arg_error((w + ": max_iter outside 0..1000000").c_str());
+    return TMS_OK;
 }
 
 }  // namespace
@@ -422,39 +630,16 @@ extern "C" tms_status tms_refine(const tms_surface_pair *surf, const tms_refine_
     tms_refine_params p;
     if (params) p = *params;
     else tms_refine_params_default(&p);
-    const tms_surface_pair &s = *surf;
-    if (s.n_harmonics < 1 || s.n_harmonics > TMS_SURF_MAX_HARMONICS)
-        return arg_error("tms_refine: n_harmonics outside 1..8");
-    if (s.n_folds < 0 || s.n_folds > TMS_SURF_MAX_FOLDS)
-        return arg_error("tms_refine: n_folds outside 0..4");
-    if (s.stretch != 0 && s.stretch != 1) return arg_error("tms_refine: stretch must be 0 or 1");
-    if (s.stretch == 1 && !(s.lam > 0.0)) return arg_error("tms_refine: lam must be > 0");
-    bool fin = true;
-    for (int h = 0; h < s.n_harmonics; ++h)
-        fin = fin && all_finite(s.ca[h], 4) && all_finite(s.cb[h], 4) && all_finite(s.dca[h], 4) &&
-              all_finite(s.dcb[h], 4);
-    for (int f = 0; f < s.n_folds; ++f)
-        fin = fin && isfinite(s.fold_amp[f]) && all_finite(s.fold_root[f], 3) &&
-              all_finite(s.fold_dir[f], 4);
-    const size_t ns = (sizeof(tms_surface_pair) - offsetof(tms_surface_pair, c0)) / sizeof(double);
-    fin = fin && isfinite(s.alpha) && isfinite(s.alpha_ref) && (s.stretch == 0 || isfinite(s.lam)) &&
-          all_finite(&s.c0, ns);
-    if (!fin) return arg_error("tms_refine: non-finite surface value");
-    if (!(s.reg >= 0.0)) return arg_error("tms_refine: reg must be >= 0");
-    if (!(p.alpha0 > 0.0 && p.alpha0 <= 1.0 && p.alpha1 > 0.0 && p.alpha1 <= 1.0))
-        return arg_error("tms_refine: alpha0 and alpha1 must lie in (0, 1]");
-    if (!(p.tol >= 0.0) || !(p.switch_below >= 0.0) || !(p.rho_min >= 0.0))
-        return arg_error("tms_refine: tol, switch_below and rho_min must be >= 0");
-    if (!(p.s_lo < p.s_hi)) return arg_error("tms_refine: need s_lo < s_hi");
-    if (p.max_iter < 0 || p.max_iter > 1000000)
-        return arg_error("tms_refine: max_iter outside 0..1000000");
+    tms_status st = check_surface(*surf, "tms_refine");
+    if (st == TMS_OK) st = check_corrector(p, "tms_refine");
+    if (st != TMS_OK) return st;
     if (n == 0) return TMS_OK;
     if (ldx0 < 4) return arg_error("tms_refine: ldx0 < 4");
     if (!dX0 || !dX || !is_device_ptr(dX0) || !is_device_ptr(dX))
         return arg_error("tms_refine: seeds and output must be device pointers");
     if (dX == dX0 && ldx0 != 4) return arg_error("tms_refine: in place needs ldx0 == 4");
     RefineArgs a;
-    a.sp = s;
+    a.sp = *surf;
     a.p = p;
     a.x0 = dX0;
     a.ld = ldx0;
@@ -470,6 +655,62 @@ extern "C" tms_status tms_refine(const tms_surface_pair *surf, const tms_refine_
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         tms::set_last_error(std::string("tms_refine launch: ") + cudaGetErrorString(e));
+        return TMS_ERR_CUDA;
+    }
+    return TMS_OK;
+}
+
+extern "C" void tms_continue_params_default(tms_continue_params *p) {
+    if (!p) return;
+    tms_refine_params_default(&p->corrector);
+    p->rho_turn = 1e-8;
+    p->max_jump = 0.25;
+    p->param = 0;
+    p->pad = 0;
+}
+
+extern "C" tms_status tms_continue(const tms_surface_pair *surf, const tms_continue_params *params,
+                                   const double *dAlphas, int nSteps, const double *dX0,
+                                   long long ldx0, long long n, double *dX, int32_t *dStatus,
+                                   int32_t *dIters, double *dRho, double *dFnorm, void *stream) {
+    if (!surf) return arg_error("tms_continue: surface is NULL");
+    if (n < 0) return arg_error("tms_continue: n < 0");
+    if (nSteps < 0) return arg_error("tms_continue: nSteps < 0");
+    tms_continue_params p;
+    if (params) p = *params;
+    else tms_continue_params_default(&p);
+    tms_status st = check_surface(*surf, "tms_continue");
+    if (st == TMS_OK) st = check_corrector(p.corrector, "tms_continue");
+    if (st != TMS_OK) return st;
+    if (p.param != 0 && p.param != 1) return arg_error("tms_continue: param must be 0 or 1");
+    if (!(p.rho_turn >= 0.0)) return arg_error("tms_continue: rho_turn must be >= 0");
+    if (!(p.max_jump > 0.0)) return arg_error("tms_continue: max_jump must be > 0");
+    if (n == 0) return TMS_OK;
+    if (ldx0 < 4) return arg_error("tms_continue: ldx0 < 4");
+    if (!dX0 || !dX || !dStatus || !is_device_ptr(dX0) || !is_device_ptr(dX) ||
+        !is_device_ptr(dStatus))
+        return arg_error("tms_continue: seeds, dX and dStatus must be device pointers");
+    if (nSteps > 0 && (!dAlphas || !is_device_ptr(dAlphas)))
+        return arg_error("tms_continue: dAlphas must be a device pointer");
+    ContArgs a;
+    a.sp = *surf;
+    a.p = p;
+    a.alphas = dAlphas;
+    a.steps = nSteps;
+    a.x0 = dX0;
+    a.ld = ldx0;
+    a.n = n;
+    a.x = dX;
+    a.status = dStatus;
+    a.iters = dIters;
+    a.rho = dRho;
+    a.fnorm = dFnorm;
+    const long long blocks = (n + kSeedsPerBlock - 1) / kSeedsPerBlock;
+    if (blocks > 0x7fffffffLL) return arg_error("tms_continue: too many branches");
+    k_continue<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(a);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        tms::set_last_error(std::string("tms_continue launch: ") + cudaGetErrorString(e));
         return TMS_ERR_CUDA;
     }
     return TMS_OK;

@@ -88,7 +88,7 @@ def test_refine_struct_layouts_match_ctypes(tmp_path):
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "tms.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(tms_surface_pair),"
-        " sizeof(tms_refine_params), offsetof(tms_surface_pair, alpha),"
+        " sizeof(tms_refine_params), offsetof(tms_surface_pair, alpha_s),"
         " offsetof(tms_surface_pair, c0), offsetof(tms_surface_pair, reg),"
         " offsetof(tms_refine_params, max_iter)); return 0;}\n")
     exe = tmp_path / "rsizes"
@@ -97,7 +97,7 @@ def test_refine_struct_layouts_match_ctypes(tmp_path):
     vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
                                         check=True).stdout.split()))
     S, R = tms.SurfacePair, tms.RefineParams
-    assert vals == [ctypes.sizeof(S), ctypes.sizeof(R), S.alpha.offset, S.c0.offset,
+    assert vals == [ctypes.sizeof(S), ctypes.sizeof(R), S.alpha_s.offset, S.c0.offset,
                     S.reg.offset, R.max_iter.offset]
 
 

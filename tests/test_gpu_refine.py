@@ -199,3 +199,76 @@ def test_full_size_planted_seeds_and_search_hits():
     pick = rng.choice(len(x), min(3000, len(x)), replace=False)
     f, _ = R.residual(sp, x[pick])
     assert np.sqrt((f * f).sum(axis=1)).max() <= 1.5e-10
+
+
+# ---------------------------------------------------------------------------
+# continuation (Sec. 8)
+# ---------------------------------------------------------------------------
+
+def _gpu_continue(surface, seeds_np, alphas, param="u", **kw):
+    seeds = torch.as_tensor(np.ascontiguousarray(seeds_np), dtype=torch.float64, device="cuda")
+    out = tms.continue_branches(surface, seeds, alphas, param=param, **kw)
+    torch.cuda.synchronize()
+    return {k: getattr(out, k).cpu().numpy() for k in ("x", "status", "iters", "rho", "fnorm")}
+
+
+def compare_continuation(g, o, max_iter=200, rho_turn=1e-8):
+    """Branch by branch: identical up to the first step where either side did not
+    converge; there both sides stop, or the side that went on had wandered
+    (a corrector of at least max_iter/2 updates) or sat on the turning threshold.
+    At least 75% of the branches must agree at every step."""
+    n, K1 = o["status"].shape
+    identical = 0
+    for b in range(n):
+        gs, os_ = g["status"][b], o["status"][b]
+        bad = np.nonzero((gs != R.CONVERGED) | (os_ != R.CONVERGED))[0]
+        js = int(bad[0]) if bad.size else K1
+        upto = slice(0, js + 1) if js < K1 and gs[js] == os_[js] == R.TURNING else slice(0, js)
+        ok = np.isfinite(o["x"][b, upto]).all(axis=1)
+        d = _xdiff(g["x"][b, upto][ok], o["x"][b, upto][ok])
+        assert d.max(initial=0.0) <= 1e-8, (b, d.max())
+        assert np.all(np.abs(g["iters"][b, :js].astype(np.int64) - o["iters"][b, :js]) <= 1)
+        if js == K1 or (gs[js] == os_[js] and np.array_equal(gs, os_)):
+            identical += 1
+            continue
+        if gs[js] != os_[js]:
+            wandered = max(g["iters"][b, js], o["iters"][b, js]) >= max_iter // 2
+            on_edge = abs(abs(o["rho"][b, js]) - rho_turn) <= 1e-6 * rho_turn
+            both_fail = gs[js] not in (R.CONVERGED, R.TURNING) and os_[js] not in (R.CONVERGED, R.TURNING)
+            assert wandered or on_edge or both_fail, (b, js, gs[js], os_[js])
+    assert identical >= 0.75 * n, (identical, n)
+
+
+@pytest.mark.parametrize("param,steps", [
+    ("u", np.linspace(0.002, 0.2, 100)),
+    ("s", np.linspace(0.002, 0.2, 100)),
+    ("u", -0.1 * (np.geomspace(1e-3, 1.0, 40))),          # backwards, uneven steps
+])
+def test_continuation_parity(param, steps):
+    pair = cached("c2", synth.config2)
+    sp = pair.surface
+    x0 = R.site_roots(sp)[:64]
+    g = _gpu_continue(sp, x0, steps, param=param, max_jump=0.05)
+    o = R.continuation(sp, x0, steps, param=param, max_jump=0.05)
+    compare_continuation(g, o)
+    assert (g["status"][:, -1] == R.CONVERGED).mean() >= 0.5
+
+
+def test_continuation_edges():
+    pair = cached("c2", synth.config2)
+    sp = pair.surface
+    x0 = R.site_roots(sp)[:7]
+    steps = np.linspace(0.002, 0.01, 5)
+    # no steps: exactly the refinement of the seeds
+    g = _gpu_continue(sp, x0, [])
+    r = _gpu_refine(sp, x0)
+    assert g["x"].shape == (7, 1, 4)
+    assert np.array_equal(g["x"][:, 0], r["x"]) and np.array_equal(g["status"][:, 0], r["status"])
+    # turning at step 0 (rho_turn above the Hadamard bound), jumps at step 1
+    for kw in (dict(rho_turn=1.0 + 1e-9), dict(max_jump=1e-12), dict(alpha0=1.0, alpha1=1.0)):
+        g = _gpu_continue(sp, x0, steps, **kw)
+        o = R.continuation(sp, x0, steps, **kw)
+        compare_continuation(g, o)
+        assert np.array_equal(g["status"], o["status"])
+    empty = tms.continue_branches(sp, torch.empty((0, 4), dtype=torch.float64, device="cuda"), steps)
+    assert empty.x.shape == (0, 6, 4)

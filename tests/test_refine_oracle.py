@@ -156,3 +156,87 @@ def test_frame_vanishes_only_at_h_zero_keeps_roots():
     assert np.abs(f).max() <= 1e-12 * (1 + np.abs(R.surface_A(sp, x[:, 0], x[:, 1])[0]).max())
     assert np.allclose(Df[:, :, 2], -Df[:, :, 0], rtol=0, atol=1e-12 * np.abs(Df).max())
     assert np.allclose(Df[:, :, 3], Df[:, :, 1], rtol=0, atol=1e-12 * np.abs(Df).max())
+
+
+# ---------------------------------------------------------------------------
+# continuation (Sec. 8)
+# ---------------------------------------------------------------------------
+
+def _dW_dalpha(sp, theta, s):
+    """Closed-form d/d alpha of the sheet g(s) T(theta; alpha) + F(s)."""
+    k = np.arange(1, 7, dtype=np.float64)
+    Ta = (np.cos(np.outer(theta, k)) / k) @ sp.dca.numpy() + \
+        (np.sin(np.outer(theta, k)) / k) @ sp.dcb.numpy()
+    g = np.exp(math.log(sp.lam) * s) if sp.stretch == "exp" else 1.0 + s
+    return g[:, None] * Ta
+
+
+@pytest.mark.parametrize("param", ["u", "s"])
+def test_continued_branches_follow_the_implicit_function_theorem(param):
+    # along a branch f(x(alpha); alpha) = 0, so dx/dalpha = -Df^{-1} df/dalpha with
+    # df/dalpha_u = dW_A/dalpha and df/dalpha_s = -dW_B/dalpha (closed forms); the
+    # central difference of the continued branch converges to it as O(h^2)
+    sp = synth.config2().surface
+    x0 = R.site_roots(sp)[:16]
+    au, as_ = R.alphas(sp)
+    errs = {}
+    for h in (0.001, 0.0005):
+        n_to = int(round(0.01 / h))
+        res = R.continuation(sp, x0, h * np.arange(1, n_to + 2), param=param, tol=1e-13)
+        a = res["alphas"]
+        for b in range(x0.shape[0]):
+            # well-conditioned stretches only (away from folds, where the branch bends hard)
+            if not (res["status"][b, :n_to + 2] == R.CONVERGED).all() or \
+                    np.abs(res["rho"][b, :n_to + 2]).min() < 0.02:
+                continue
+            x = res["x"][b, n_to]
+            spj = R.with_alphas(sp, a[n_to] if param == "u" else au, a[n_to] if param == "s" else as_)
+            _, Df = R.residual(spj, x[None])
+            if param == "u":
+                dfa = _dW_dalpha(sp, x[0:1], x[1:2])[0]
+            else:
+                dfa = -_dW_dalpha(sp, x[2:3] + sp.c0, 1.0 - x[3:4])[0]
+            want = -np.linalg.solve(Df[0], dfa)
+            d = res["x"][b, n_to + 1] - res["x"][b, n_to - 1]
+            d[[0, 2]] -= 2 * math.pi * np.round(d[[0, 2]] / (2 * math.pi))
+            got = d / (a[n_to + 1] - a[n_to - 1])
+            errs.setdefault(b, []).append(np.abs(got - want).max() / (1.0 + np.abs(want).max()))
+    pairs = [e for e in errs.values() if len(e) == 2]
+    assert len(pairs) >= 6
+    for e1, e2 in pairs:
+        assert e2 <= 1e-3 and (e2 <= 1e-9 or 3.0 < e1 / e2 < 5.0), (e1, e2)
+
+
+def test_predictor_error_is_second_order():
+    # Eq. (predictor) extrapolates linearly: its error shrinks 4x when the step halves
+    sp = synth.config2().surface
+    x0 = R.site_roots(sp)[:16]
+    errs = []
+    for h in (0.004, 0.002):
+        steps = h * np.arange(1, 6)
+        res = R.continuation(sp, x0, steps, param="u", tol=1e-13)
+        ok = (res["status"][:, :6] == R.CONVERGED).all(axis=1)
+        e = np.abs(res["predicted"][ok, 2:6] - res["x"][ok, 2:6])
+        errs.append(np.median(e.max(axis=2)))
+    assert 3.0 < errs[0] / errs[1] < 5.5
+
+
+def test_continuation_statuses():
+    sp = synth.config2().surface
+    x0 = R.site_roots(sp)[:6]
+    steps = np.linspace(0.002, 0.01, 5)
+    base = R.continuation(sp, x0, steps)
+    # step 0 is the corrector at the pair's own parameters
+    ref = R.damped_newton(sp, x0)
+    assert np.array_equal(base["x"][:, 0], ref["x"]) and np.array_equal(base["iters"][:, 0], ref["iters"])
+    # Hadamard: |rho| <= 1, so rho_turn above 1 turns every branch at step 0
+    res = R.continuation(sp, x0, steps, rho_turn=1.0 + 1e-9)
+    assert (res["status"][:, 0] == R.TURNING).all() and (res["status"][:, 1:] == R.STOPPED).all()
+    assert np.isnan(res["x"][:, 1:]).all() and np.isfinite(res["x"][:, 0]).all()
+    # a tiny jump allowance stops every branch whose corrector moved at step 1
+    res = R.continuation(sp, x0, steps, max_jump=1e-12)
+    moved = res["iters"][:, 1] > 0
+    assert moved.all() and (res["status"][:, 1] == R.JUMPED).all()
+    # no steps: the start only
+    res = R.continuation(sp, x0, [])
+    assert res["x"].shape == (6, 1, 4) and (res["status"][:, 0] == R.CONVERGED).all()
