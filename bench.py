@@ -525,7 +525,7 @@ def refine_timing(tms, pair, hits, stream, flush, fp64_tf):
                                        "numpy FP64 vectorised over seeds"}}
 
 
-def continue_timing(tms, pair, hits, stream, fp64_tf, n_steps=50, dalpha=1e-3):
+def continue_timing(tms, pair, hits, stream, fp64_tf, n_steps=50, dalpha=1e-3, max_iter=60):
     """tms_continue from the search's own hits (seeds read in place) through
     n_steps values of alpha_u (step 0 refines the hits at the meshes' alpha):
     time per call, branch-steps/s and FP64 rate; plus the oracle on a bounded
@@ -534,7 +534,8 @@ def continue_timing(tms, pair, hits, stream, fp64_tf, n_steps=50, dalpha=1e-3):
     sp = tms.surface_pair(pair.surface)
     alphas = torch.tensor([pair.surface.alpha + dalpha * (j + 1) for j in range(n_steps)],
                           dtype=torch.float64)
-    call = lambda: tms.continue_branches(sp, hits, alphas, stream=stream, max_jump=0.05)
+    call = lambda: tms.continue_branches(sp, hits, alphas, stream=stream, max_jump=0.05,
+                                         max_iter=max_iter)
     with torch.cuda.stream(stream):
         for _ in range(2):
             out = call()
@@ -556,11 +557,13 @@ def continue_timing(tms, pair, hits, stream, fp64_tf, n_steps=50, dalpha=1e-3):
     n = len(hits)
     seeds = pair.planted.params.numpy()[:256]
     t0 = time.perf_counter()
-    o = oref.continuation(pair.surface, seeds, alphas.numpy(), param="u", max_jump=0.05)
+    o = oref.continuation(pair.surface, seeds, alphas.numpy(), param="u", max_jump=0.05,
+                          max_iter=max_iter)
     cpu_s = time.perf_counter() - t0
     o_evals = int(o["iters"].sum() + np.isin(o["status"], (0, 1, 2, 5, 6)).sum())
     final = st[:, -1] if n else st
     return {"branches": n, "steps": n_steps + 1, "dalpha": dalpha, "ms_per_call": ms,
+            "corrector": f"alpha 0.5, tol 1e-10, max_iter {max_iter} per step; max_jump 0.05",
             "branch_steps_per_s": n * (n_steps + 1) / (ms * 1e-3), "evaluations": evals,
             "branches_alive_at_end": int((final == 0).sum()),
             "status_at_end": {tms.CONTINUE_STATUS[k]: int((final == k).sum()) for k in range(8)},

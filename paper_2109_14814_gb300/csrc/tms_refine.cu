@@ -445,11 +445,13 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
 }
 
 // Continuation (Sec. 8): one quad per branch walks the parameter values
-// alpha_0 (the pair's own), alphas[0..steps); the tables are rebuilt for every
-// step between two block barriers, so every warp of the block takes part in
-// every step even when its branches have stopped.
+// alpha_0 (the pair's own), alphas[0..steps).  Each warp owns a copy of the
+// tables and rebuilds it for every step between two warp barriers, so the
+// warps of a block step independently; a warp whose eight branches have all
+// stopped writes their remaining steps and leaves.
 __global__ void __launch_bounds__(kThreads) k_continue(const __grid_constant__ ContArgs a) {
-    __shared__ Coef cf;
+    __shared__ Coef cfw[kThreads / 32];
+    Coef &cf = cfw[threadIdx.x >> 5];
     const tms_surface_pair &sp = a.sp;
     const tms_continue_params &cp = a.p;
     const int t = threadIdx.x;
@@ -471,11 +473,26 @@ __global__ void __launch_bounds__(kThreads) k_continue(const __grid_constant__ C
     double am1 = a0, am2 = a0;   // alpha_{j-1}, alpha_{j-2}
     const long long K1 = (long long)a.steps + 1;
     for (int j = 0; j <= a.steps; ++j) {
+        if (!__any_sync(kFull, alive)) {
+            if (live) {
+                for (int r = j; r <= a.steps; ++r) {
+                    const long long o = i * K1 + r;
+                    a.x[o * 4 + c] = nan_value();
+                    if (c == 0) {
+                        a.status[o] = TMS_CONT_STOPPED;
+                        if (a.iters) a.iters[o] = 0;
+                        if (a.rho) a.rho[o] = nan_value();
+                        if (a.fnorm) a.fnorm[o] = nan_value();
+                    }
+                }
+            }
+            break;
+        }
         const double aj = j == 0 ? a0 : a.alphas[j - 1];
-        __syncthreads();
-        build_tables(cf, sp, cp.param == 0 ? aj : sp.alpha_u, cp.param == 0 ? sp.alpha_s : aj, t,
-                     kThreads);
-        __syncthreads();
+        __syncwarp();
+        build_tables(cf, sp, cp.param == 0 ? aj : sp.alpha_u, cp.param == 0 ? sp.alpha_s : aj,
+                     lane, 32);
+        __syncwarp();
         // predictor, Eq. (predictor); angle differences taken on the circle
         double g[4];
         if (j == 0) {
