@@ -579,3 +579,48 @@ def family_pair(seed: int, alpha: float, N: int = 96, M: int = 48, device: str =
     return build_pair(seed, N, M, N, M, stretch="exp", lam=4.0, n_folds=3,
                       sites=(8, 2), n_hits=n_hits, alpha=alpha, with_dalpha=True,
                       device=device, family_seed=seed, alpha_ref=0.5)
+
+
+# ----------------------------------------------------------------------------
+# globalized meshes with layer structure (method of layers)
+# ----------------------------------------------------------------------------
+
+def layered_s_grid(D: float, lam: float, n_lo: int, n_hi: int, per_layer: int,
+                   fund: int) -> torch.Tensor:
+    """Sorted s values of a globalized mesh whose half-layers are
+    [D lam^(n-1), D lam^n] (lam > 1) for n = n_lo..n_hi and their mirror images,
+    each sampled by per_layer + 1 geometrically spaced columns (boundaries
+    shared), plus fund - 1 evenly spaced columns strictly inside the innermost
+    boundary.  A stable-manifold grid with multiplier mu < 1 is the same grid
+    with lam = 1 / mu (its half-layer m spans [D / mu^(m-1), D / mu^m])."""
+    pos = []
+    for n in range(n_lo, n_hi + 1):
+        for j in range(per_layer + (1 if n == n_hi else 0)):
+            pos.append(D * lam ** (n - 1 + j / per_layer))
+    inner = pos[0]
+    mid = [inner * (2.0 * i / fund - 1.0) for i in range(1, fund)]
+    vals = [-v for v in reversed(pos)] + mid + pos
+    return torch.tensor(vals, dtype=torch.float64)
+
+
+def layered_pair(seed: int = SEED_BASE + 600, NA: int = 1024, NB: int = 2048, n_max: int = 14,
+                 per_layer: int = 34, D_u: float = 1e-2, lam_u: float = 2.0, D_s: float = 1e-2,
+                 lam_s: float = 0.5, fund: int = 4, n_hits: int = 64, sites=(16, 12),
+                 device: str = "cpu") -> MeshPair:
+    """Globalized unstable and stable meshes for the method of layers: the
+    surface geometry of build_pair (vertex columns in order), with s values
+    relabelled so that the columns group into half-layers U_n^+-, n = 1..n_max,
+    of per_layer quads ([D_u lam_u^(n-1), D_u lam_u^n]) and S_m^+-, m = 0..n_max
+    ([D_s / lam_s^(m-1), D_s / lam_s^m]), with fund - 1 columns of the
+    fundamental domain between the two signs.  With the defaults the meshes
+    have the paper's benchmark shapes: N1 = 1024, N2 = 2048 and 35 columns per
+    half-layer, 14 layers, 112 half-layer pairs."""
+    sA = layered_s_grid(D_u, lam_u, 1, n_max, per_layer, fund)
+    sB = layered_s_grid(D_s, 1.0 / lam_s, 0, n_max, per_layer, fund)
+    pair = build_pair(seed, NA, sA.numel(), NB, sB.numel(), stretch="exp", lam=4.0, n_folds=3,
+                      sites=sites, n_hits=n_hits, device=device)
+    pair.A = MeshGrid(pair.A.X, sA.to(pair.A.X.device), True)
+    pair.B = MeshGrid(pair.B.X, sB.to(pair.B.X.device), True)
+    pair.meta.update(layers=dict(D_u=D_u, lam_u=lam_u, D_s=D_s, lam_s=lam_s, n_max=n_max,
+                                 per_layer=per_layer, fund=fund))
+    return pair
