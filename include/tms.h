@@ -274,6 +274,61 @@ const char *tms_noalloc_last_error(void);
 tms_status tms_noalloc_footprint(unsigned long long *needed, unsigned long long *reserved);
 
 /*
+ * Method of layers (Sec. 5, Eq. layerintersection; Sec. 6.2).  With the
+ * fundamental domains (-D_u, D_u), (-D_s, D_s) and multipliers lam_u > 1,
+ * 0 < lam_s < 1, the half-layers are
+ *   U_n^+- = W^u(T x +-[D_u lam_u^(n-1), D_u lam_u^n]),
+ *   S_m^+- = W^s(T x +-[D_s / lam_s^(m-1), D_s / lam_s^m]),
+ * and every heteroclinic orbit has a point in some U_n cap S_n or
+ * U_n cap S_(n-1), n >= 1.  On globalized meshes whose stored s values include
+ * the boundaries, a half-layer is a contiguous range of vertex columns, so
+ * each of the 8 pairs of a layer is one search between two mesh views.
+ */
+typedef struct {
+    int n, m;             /* U_n and S_m, m = n or n - 1 */
+    int sign_u, sign_s;   /* +1 or -1: positive or negative half-layer */
+    int a_k0, a_k1;       /* vertex columns [a_k0, a_k1) of U_n^sign_u in A's arrays */
+    int b_k0, b_k1;       /* vertex columns [b_k0, b_k1) of S_m^sign_s in B's arrays */
+} tms_layer_pair;
+
+/*
+ * tms_layer_pairs -- the 8 n_max half-layer pairs for layers 1..n_max, in the
+ * order n ascending, then sign_u (+1 first), then m = n before m = n - 1, then
+ * sign_s (+1 first).  Host only, no device call.
+ *   sA, sB   : host, MA and MB strictly increasing s values of the full meshes.
+ *   rel_tol  : a boundary value b matches the stored s_k with |s_k - b| <= rel_tol |b|.
+ *   out, cap : host, room for cap pairs; *count receives 8 n_max.
+ * TMS_ERR_ARG when a boundary is not a stored value (message names the layer)
+ * or an argument is out of range; TMS_ERR_CAPACITY when cap < 8 n_max (the
+ * first cap pairs are written).
+ */
+tms_status tms_layer_pairs(const double *sA, int MA, double Du, double lam_u, const double *sB,
+                           int MB, double Ds, double lam_s, int n_max, double rel_tol,
+                           tms_layer_pair *out, int cap, int *count);
+
+/* A layer sweep: one mesh view per distinct half-layer of the full meshes A
+ * and B (borrowing their arrays, like tms_build_mesh) and the per-pair id
+ * shifts.  The pairs' column ranges are indices into the arrays A and B were
+ * built on and must lie inside their views.  Creating it synchronises. */
+typedef struct tms_layer_plan_s *tms_layer_plan;
+tms_status tms_layer_plan_create(tms_mesh A, tms_mesh B, const tms_layer_pair *pairs,
+                                 int nPairs, void *stream, tms_layer_plan *out);
+tms_status tms_layer_plan_destroy(tms_layer_plan plan);
+
+/*
+ * tms_layer_search -- every intersecting triangle pair of every half-layer
+ * pair of the plan, as one tms_search_batched over the views (one graph
+ * replay), with triangle ids shifted to the views of A and B the plan was
+ * made from (so they are unique across pairs).  Output as tms_search_batched:
+ * sorted by (pair, triA, triB), pair = index into the plan's pairs, dOffsets
+ * (device, nPairs + 1) required.  The id shift runs on `stream` after the
+ * search's own synchronisation.  TMS_ERR_CAPACITY as tms_search_batched (the
+ * first hitCap records are shifted too).
+ */
+tms_status tms_layer_search(tms_layer_plan plan, const tms_params *params, tms_hit *dHits,
+                            long long hitCap, long long *dOffsets, long long *nHits, void *stream);
+
+/*
  * Refinement of approximate intersections (Sec. 7, Eqs. tosolve and
  * dampedNewtonEquation).  Each seed x0 = (theta_u, s_u, theta_s, s_s) -- for
  * example a hit's parameter estimates (Sec. 6.2.4) -- is corrected by the

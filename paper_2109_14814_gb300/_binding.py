@@ -76,6 +76,15 @@ class Stats(ctypes.Structure):
         return d
 
 
+class LayerPair(ctypes.Structure):
+    """Mirror of tms_layer_pair."""
+    _fields_ = [(f, _c.c_int) for f in ("n", "m", "sign_u", "sign_s", "a_k0", "a_k1", "b_k0", "b_k1")]
+
+    def as_dict(self):
+        return dict(n=self.n, m=self.m, sign_u=self.sign_u, sign_s=self.sign_s,
+                    a=(self.a_k0, self.a_k1), b=(self.b_k0, self.b_k1))
+
+
 class SurfacePair(ctypes.Structure):
     """Mirror of tms_surface_pair (the closed-form sheet pair refined on)."""
     _fields_ = [
@@ -164,6 +173,14 @@ def lib():
     L.tms_continue.argtypes = [_c.POINTER(SurfacePair), _c.POINTER(ContinueParams), P, I, P, LL, LL,
                                P, P, P, P, P, P]
     L.tms_continue.restype = I
+    L.tms_layer_pairs.argtypes = [P, I, D, D, P, I, D, D, I, D, P, I, _c.POINTER(I)]
+    L.tms_layer_pairs.restype = I
+    L.tms_layer_plan_create.argtypes = [P, P, P, I, P, _c.POINTER(P)]
+    L.tms_layer_plan_create.restype = I
+    L.tms_layer_plan_destroy.argtypes = [P]
+    L.tms_layer_plan_destroy.restype = I
+    L.tms_layer_search.argtypes = [P, _c.POINTER(Params), P, LL, P, _c.POINTER(LL), P]
+    L.tms_layer_search.restype = I
     _lib = L
     return L
 
@@ -584,6 +601,70 @@ def continue_branches(surface, seeds, alphas, param: str = "u", stream=None, rho
     if rc != TMS_OK:
         raise TmsError(rc, "tms_continue")
     return out
+
+
+def layer_pairs(sA, D_u: float, lam_u: float, sB, D_s: float, lam_s: float, n_max: int,
+                rel_tol: float = 1e-9) -> list:
+    """tms_layer_pairs: the 8 n_max half-layer pairs (Sec. 5, Sec. 6.2) of the
+    full meshes with s values sA, sB, as dicts (n, m, sign_u, sign_s, a, b)."""
+    def host(v):
+        arr = (v.detach().cpu() if isinstance(v, torch.Tensor) else torch.as_tensor(v))
+        return arr.to(torch.float64).contiguous()
+    a, b = host(sA), host(sB)
+    cnt = _c.c_int(0)
+    buf = (LayerPair * (8 * n_max))()
+    rc = lib().tms_layer_pairs(a.data_ptr(), a.numel(), D_u, lam_u, b.data_ptr(), b.numel(), D_s,
+                               lam_s, n_max, rel_tol, buf, 8 * n_max, _c.byref(cnt))
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_layer_pairs")
+    return [buf[i].as_dict() for i in range(cnt.value)]
+
+
+class LayerSweep:
+    """tms_layer_plan: the half-layer pairs of two full meshes searched as one
+    batched search; hits carry the pair index and full-mesh triangle ids."""
+
+    def __init__(self, A: "Mesh", B: "Mesh", pairs, stream=None):
+        self.A, self.B, self.pairs = A, B, list(pairs)
+        arr = (LayerPair * len(self.pairs))()
+        for i, p in enumerate(self.pairs):
+            arr[i] = LayerPair(p["n"], p["m"], p["sign_u"], p["sign_s"], p["a"][0], p["a"][1],
+                               p["b"][0], p["b"][1])
+        h = _c.c_void_p()
+        rc = lib().tms_layer_plan_create(A.handle, B.handle, arr, len(self.pairs), _stream(stream),
+                                         _c.byref(h))
+        if rc != TMS_OK:
+            raise TmsError(rc, "tms_layer_plan_create")
+        self.handle = h
+
+    def search(self, hit_capacity: int = 1 << 16, stream=None, out=None, offsets=None, **kw) -> "Hits":
+        p = params(**kw)
+        st = _stream(stream)
+        dev = self.A.X.device
+        buf = out if out is not None else _alloc_hits(hit_capacity, dev)
+        offs = offsets if offsets is not None else torch.empty(len(self.pairs) + 1, dtype=torch.int64,
+                                                              device=dev)
+        n = _c.c_longlong(0)
+        rc = lib().tms_layer_search(self.handle, _c.byref(p), buf.data_ptr(), buf.shape[0],
+                                    offs.data_ptr(), _c.byref(n), st)
+        if rc == TMS_ERR_CAPACITY and out is None and n.value > buf.shape[0]:
+            buf = _alloc_hits(int(n.value), dev)
+            rc = lib().tms_layer_search(self.handle, _c.byref(p), buf.data_ptr(), buf.shape[0],
+                                        offs.data_ptr(), _c.byref(n), st)
+        if rc != TMS_OK:
+            raise TmsError(rc, "tms_layer_search")
+        return Hits(buf[: n.value], offs)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.tms_layer_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def release_workspace(stream=None):

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <string>
@@ -848,6 +849,213 @@ tms_status tms_release_workspace(void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     drop_plans_if(plan_on_stream, stream ? (void *)&s : nullptr);
     return TMS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Method of layers (Sec. 5, Sec. 6.2): half-layer column ranges and the sweep
+// over the 8 n_max half-layer pairs as one batched search.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr unsigned kLayerMagic = 0x746d736cu;   // "tmsl"
+
+// Shifts view-relative triangle ids to ids of the full meshes the plan was
+// built from; shift[p] = (2 N_A (a_k0 - A.k0), 2 N_B (b_k0 - B.k0)).
+__global__ void k_layer_ids(tms_hit *hits, long long n, const uint2 *shift, int nPairs) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned p = hits[i].pair;
+    if (p >= (unsigned)nPairs) return;
+    const uint2 d = shift[p];
+    hits[i].triA += d.x;
+    hits[i].triB += d.y;
+}
+
+// Column holding the boundary value b (within rel_tol |b|), or -1.
+int boundary_column(const double *s, int M, double b, double rel_tol) {
+    const double *it = std::lower_bound(s, s + M, b);
+    int best = -1;
+    double bd = 0.0;
+    for (const double *q : {it - 1, it}) {
+        if (q < s || q >= s + M) continue;
+        const double d = std::fabs(*q - b);
+        if (d <= rel_tol * std::fabs(b) && (best < 0 || d < bd)) {
+            best = (int)(q - s);
+            bd = d;
+        }
+    }
+    return best;
+}
+
+}  // namespace
+
+struct tms_layer_plan_s {
+    unsigned magic;
+    int nPairs;
+    std::vector<tms_mesh> A, B;       // per pair (shared handles repeat)
+    std::vector<tms_mesh> owned;      // distinct sub-view handles
+    uint2 *d_shift;
+};
+
+extern "C" {
+
+tms_status tms_layer_pairs(const double *sA, int MA, double Du, double lam_u, const double *sB,
+                           int MB, double Ds, double lam_s, int n_max, double rel_tol,
+                           tms_layer_pair *out, int cap, int *count) {
+    if (!count || !sA || !sB || MA < 2 || MB < 2 || n_max < 1 || cap < 0 || (cap > 0 && !out)) {
+        g_err = "tms_layer_pairs: bad argument";
+        return TMS_ERR_ARG;
+    }
+    if (!(Du > 0.0) || !(lam_u > 1.0) || !(Ds > 0.0) || !(lam_s > 0.0 && lam_s < 1.0) ||
+        !(rel_tol >= 0.0) || !std::isfinite(Du * lam_u) || !std::isfinite(Ds / lam_s)) {
+        g_err = "tms_layer_pairs: need D > 0, lam_u > 1, 0 < lam_s < 1, rel_tol >= 0";
+        return TMS_ERR_ARG;
+    }
+    for (int k = 1; k < MA; ++k)
+        if (!(sA[k] > sA[k - 1])) { g_err = "tms_layer_pairs: sA not increasing"; return TMS_ERR_ARG; }
+    for (int k = 1; k < MB; ++k)
+        if (!(sB[k] > sB[k - 1])) { g_err = "tms_layer_pairs: sB not increasing"; return TMS_ERR_ARG; }
+    const long long total = 8LL * n_max;
+    if (total > 0x7fffffffLL) { g_err = "tms_layer_pairs: n_max too large"; return TMS_ERR_ARG; }
+    *count = (int)total;
+    // column range [k(lo), k(hi) + 1) of the closed interval between two boundaries
+    auto range = [&](const double *s, int M, double v0, double v1, int &k0, int &k1) -> bool {
+        const double lo = std::min(v0, v1), hi = std::max(v0, v1);
+        const int a = boundary_column(s, M, lo, rel_tol), b = boundary_column(s, M, hi, rel_tol);
+        if (a < 0 || b < 0 || b - a < 1) return false;
+        k0 = a;
+        k1 = b + 1;
+        return true;
+    };
+    int w = 0;
+    for (int n = 1; n <= n_max; ++n) {
+        for (int su : {1, -1}) {
+            int a0, a1;
+            if (!range(sA, MA, su * Du * std::pow(lam_u, n - 1), su * Du * std::pow(lam_u, n), a0, a1)) {
+                g_err = "tms_layer_pairs: a U half-layer boundary is not a stored s value (layer " +
+                        std::to_string(n) + ")";
+                return TMS_ERR_ARG;
+            }
+            for (int m : {n, n - 1}) {
+                for (int ss : {1, -1}) {
+                    int b0, b1;
+                    if (!range(sB, MB, ss * Ds / std::pow(lam_s, m - 1), ss * Ds / std::pow(lam_s, m),
+                               b0, b1)) {
+                        g_err = "tms_layer_pairs: an S half-layer boundary is not a stored s value "
+                                "(layer " + std::to_string(m) + ")";
+                        return TMS_ERR_ARG;
+                    }
+                    if (w < cap) {
+                        tms_layer_pair &p = out[w];
+                        p.n = n;
+                        p.m = m;
+                        p.sign_u = su;
+                        p.sign_s = ss;
+                        p.a_k0 = a0;
+                        p.a_k1 = a1;
+                        p.b_k0 = b0;
+                        p.b_k1 = b1;
+                    }
+                    ++w;
+                }
+            }
+        }
+    }
+    if (cap < total) {
+        g_err = "tms_layer_pairs: output too small";
+        return TMS_ERR_CAPACITY;
+    }
+    return TMS_OK;
+}
+
+tms_status tms_layer_plan_destroy(tms_layer_plan plan) {
+    if (!plan || plan->magic != kLayerMagic) return TMS_ERR_STATE;
+    for (tms_mesh m : plan->owned) tms_destroy_mesh(m);
+    cudaFree(plan->d_shift);
+    plan->magic = 0;
+    delete plan;
+    return TMS_OK;
+}
+
+tms_status tms_layer_plan_create(tms_mesh A, tms_mesh B, const tms_layer_pair *pairs, int nPairs,
+                                 void *stream, tms_layer_plan *out) {
+    if (!out) return TMS_ERR_ARG;
+    *out = nullptr;
+    if (!A || !B || A->magic != kMagic || B->magic != kMagic) return TMS_ERR_STATE;
+    if (!pairs || nPairs < 1) { g_err = "tms_layer_plan_create: no pairs"; return TMS_ERR_ARG; }
+    if (2ULL * A->N * (unsigned long long)A->M >= (1ULL << 32) ||
+        2ULL * B->N * (unsigned long long)B->M >= (1ULL << 32)) {
+        g_err = "tms_layer_plan_create: mesh too large for 32-bit triangle ids";
+        return TMS_ERR_ARG;
+    }
+    for (int p = 0; p < nPairs; ++p) {
+        const tms_layer_pair &q = pairs[p];
+        if (q.a_k0 < A->k0 || q.a_k1 > A->k1 || q.a_k1 - q.a_k0 < 2 || q.b_k0 < B->k0 ||
+            q.b_k1 > B->k1 || q.b_k1 - q.b_k0 < 2) {
+            g_err = "tms_layer_plan_create: pair " + std::to_string(p) + " outside the meshes";
+            return TMS_ERR_ARG;
+        }
+    }
+    tms_layer_plan P = new tms_layer_plan_s();
+    P->magic = kLayerMagic;
+    P->nPairs = nPairs;
+    P->d_shift = nullptr;
+    std::map<std::pair<int, int>, tms_mesh> va, vb;
+    auto view = [&](tms_mesh full, std::map<std::pair<int, int>, tms_mesh> &cache, int k0, int k1,
+                    tms_mesh *h) -> tms_status {
+        auto it = cache.find({k0, k1});
+        if (it != cache.end()) { *h = it->second; return TMS_OK; }
+        const size_t off = (size_t)full->k0 * full->N;
+        tms_status st = tms_build_mesh(full->dev.c[0] - off, full->dev.c[1] - off,
+                                       full->dev.c[2] - off, full->dev.c[3] - off, full->N, full->M,
+                                       k0, k1, full->d_s, full->dev.periodic, stream, h);
+        if (st != TMS_OK) return st;
+        cache[{k0, k1}] = *h;
+        P->owned.push_back(*h);
+        return TMS_OK;
+    };
+    std::vector<uint2> shift(nPairs);
+    for (int p = 0; p < nPairs; ++p) {
+        const tms_layer_pair &q = pairs[p];
+        tms_mesh ha = nullptr, hb = nullptr;
+        tms_status st = view(A, va, q.a_k0, q.a_k1, &ha);
+        if (st == TMS_OK) st = view(B, vb, q.b_k0, q.b_k1, &hb);
+        if (st != TMS_OK) { tms_layer_plan_destroy(P); return st; }
+        P->A.push_back(ha);
+        P->B.push_back(hb);
+        shift[p] = make_uint2((unsigned)(2LL * A->N * (q.a_k0 - A->k0)),
+                              (unsigned)(2LL * B->N * (q.b_k0 - B->k0)));
+    }
+    cudaError_t e = cudaMalloc((void **)&P->d_shift, nPairs * sizeof(uint2));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->d_shift, shift.data(), nPairs * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        g_err = cudaGetErrorString(e);
+        tms_layer_plan_destroy(P);
+        return TMS_ERR_CUDA;
+    }
+    *out = P;
+    return TMS_OK;
+}
+
+tms_status tms_layer_search(tms_layer_plan plan, const tms_params *params, tms_hit *dHits,
+                            long long hitCap, long long *dOffsets, long long *nHits, void *stream) {
+    if (!plan || plan->magic != kLayerMagic) return TMS_ERR_STATE;
+    if (!dOffsets || !nHits) return TMS_ERR_ARG;
+    tms_status st = search_impl(plan->A.data(), plan->B.data(), plan->nPairs, params, dHits, hitCap,
+                                dOffsets, nHits, stream);
+    if (st != TMS_OK && st != TMS_ERR_CAPACITY) return st;
+    const long long n = std::min(*nHits, hitCap);
+    if (n > 0) {
+        k_layer_ids<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+            dHits, n, plan->d_shift, plan->nPairs);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { g_err = cudaGetErrorString(e); return TMS_ERR_CUDA; }
+    }
+    return st;
 }
 
 }  // extern "C"

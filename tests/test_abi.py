@@ -128,3 +128,28 @@ def test_refine_arguments_checked_without_gpu():
     # seeds must be given for n > 0 (rejected before the pointer query)
     assert lib.tms_refine(B(sp), B(p), None, 4, 3, None, None, None, None, None, None) == tms.TMS_ERR_ARG
     assert lib.tms_refine(B(sp), B(p), None, 3, 3, None, None, None, None, None, None) == tms.TMS_ERR_ARG
+
+
+def test_layer_pairs_host_enumeration_matches_oracle():
+    import synth
+    from oracle import layers as L
+    p = synth.layered_pair(NA=96, NB=128, n_max=3, per_layer=8, sites=(8, 6), n_hits=12)
+    lay = p.meta["layers"]
+    args = (lay["D_u"], lay["lam_u"])
+    got = tms.layer_pairs(p.A.s, *args, p.B.s, lay["D_s"], lay["lam_s"], lay["n_max"])
+    want = L.layer_pairs(p.A.s.numpy(), *args, p.B.s.numpy(), lay["D_s"], lay["lam_s"], lay["n_max"])
+    assert got == want and len(got) == 24
+    lib = tms.lib()
+    a, b = p.A.s.contiguous(), p.B.s.contiguous()
+    buf = (tms.LayerPair * 4)()
+    cnt = ctypes.c_int(0)
+    rc = lib.tms_layer_pairs(a.data_ptr(), a.numel(), *args, b.data_ptr(), b.numel(), lay["D_s"],
+                             lay["lam_s"], 3, 1e-9, buf, 4, ctypes.byref(cnt))
+    assert rc == tms.TMS_ERR_CAPACITY and cnt.value == 24
+    assert buf[3].as_dict() == want[3]
+    with pytest.raises(tms.TmsError):
+        tms.layer_pairs(p.A.s, lay["D_u"] * 1.3, lay["lam_u"], p.B.s, lay["D_s"], lay["lam_s"], 3)
+    with pytest.raises(tms.TmsError):
+        tms.layer_pairs(p.A.s, lay["D_u"], 0.5, p.B.s, lay["D_s"], lay["lam_s"], 3)
+    with pytest.raises(tms.TmsError):                     # more layers than the mesh holds
+        tms.layer_pairs(p.A.s, lay["D_u"], lay["lam_u"], p.B.s, lay["D_s"], lay["lam_s"], 4)
