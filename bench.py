@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -355,7 +356,8 @@ def run_tms(args, ws, rank, local):
                                           (fp64 or {}).get("peak_tflops") or tms.probe_fp64_tflops()),
                   "continuation": continue_timing(tms, pair, h, stream,
                                                   (fp64 or {}).get("peak_tflops") or tms.probe_fp64_tflops()),
-                  "layers": layer_timing(tms, device, stream, flush)}
+                  "layers": layer_timing(tms, device, stream, flush),
+                  "theta": theta_timing(tms, device, stream, flush)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -622,6 +624,55 @@ def layer_timing(tms, device, stream, flush):
                              "0.04160 s on its three GPUs (broad phase only, narrow phase on the CPU)"}
 
 
+def theta_timing(tms, device, stream, flush):
+    """Globalization-style translation of every s column of a 2048 x 1025 x 4
+    coordinate array by its own shift (Eq. translate), the theta-derivative of
+    the same array (Eq. translate2), and 16 phase alignments of 4 x 4096
+    circles (Eq. rhoEquationDiscrete); with the numpy oracle on the same data."""
+    from oracle import theta as oth
+    g = torch.Generator().manual_seed(11)
+    C, M, N = 4, 1025, 2048
+    X = torch.randn(C, M, N, generator=g, dtype=torch.float64)
+    rho = torch.rand(M, generator=g, dtype=torch.float64) * 6.0 - 3.0
+    Xd, rd, out = X.to(device), rho.to(device), torch.empty(C, M, N, dtype=torch.float64, device=device)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            tms.theta_translate(Xd, rd, out=out, stream=stream)
+    ms_t = _timed(lambda: tms.theta_translate(Xd, rd, out=out, stream=stream), stream, flush, 10)
+    ms_d = _timed(lambda: tms.theta_translate(Xd, rd, derivative=True, out=out, stream=stream),
+                  stream, flush, 10)
+    logn = int(round(math.log2(N)))
+    # two complex transforms of N points per pair of real rows, 10 flops per butterfly,
+    # plus the per-frequency multiply (6 flops)
+    flops = (C // 2) * M * (2 * 10 * (N // 2) * logn + 6 * N)
+    nbytes = 2 * C * M * N * 8
+    t0 = time.perf_counter()
+    oth.translate(X.numpy(), rho.numpy()[None, :])
+    cpu_t = time.perf_counter() - t0
+    A, Np = 16, 4096
+    Wp = torch.randn(A, 4, Np, generator=g, dtype=torch.float64)
+    Wr = torch.roll(Wp, 100, dims=-1) + 1e-3 * torch.randn(A, 4, Np, generator=g, dtype=torch.float64)
+    Wpd, Wrd = Wp.to(device), Wr.to(device)
+    with torch.cuda.stream(stream):
+        tms.phase_align(Wrd, Wpd, stream=stream)
+    ms_p = _timed(lambda: tms.phase_align(Wrd, Wpd, stream=stream), stream, flush, 5)
+    t0 = time.perf_counter()
+    oth.phase_align(Wr[0].numpy(), Wp[0].numpy())
+    cpu_p = (time.perf_counter() - t0) * A
+    fp64 = tms.probe_fp64_tflops()
+    return {"translate": {"array": f"{C} x {M} x {N} (one shift per s column)", "ms": ms_t,
+                          "derivative_ms": ms_d, "fp64_tflops": flops / (ms_t * 1e-3) / 1e12,
+                          "fp64_frac": flops / (ms_t * 1e-3) / 1e12 / fp64,
+                          "hbm_gbs": nbytes / (ms_t * 1e-3) / 1e9,
+                          "flops_counted": "per pair of real rows: two N-point complex radix-2 "
+                                           "transforms (10 flops per butterfly) + 6 per frequency",
+                          "cpu_baseline_ms": cpu_t * 1e3, "cpu_kind": "oracle (numpy FFT, 1 core)"},
+            "phase_align": {"alignments": A, "N": Np, "coords": 4, "ms": ms_p,
+                            "norms_per_s": A * Np * Np / (ms_p * 1e-3),
+                            "cpu_baseline_ms": cpu_p * 1e3,
+                            "cpu_kind": "oracle (numpy, one roll per shift), one alignment timed x 16"}}
+
+
 def cpu_baseline(pair):
     import oracle
     OA, OB = oracle.OMesh.from_grid(pair.A), oracle.OMesh.from_grid(pair.B)
@@ -677,7 +728,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--extras", action="store_true",
                     help="also time the plain FP64 path, the batched 256-pair search, the adjoint, "
-                         "the refinement of the hits, their continuation and the layer sweep")
+                         "the refinement of the hits, their continuation, the layer sweep and "
+                         "the theta-grid operations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()

@@ -486,6 +486,48 @@ tms_status tms_continue(const tms_surface_pair *surf, const tms_continue_params 
                         long long nBranches, double *dX, int32_t *dStatus, int32_t *dIters,
                         double *dRho, double *dFnorm, void *stream);
 
+/*
+ * Operations on theta grids (functions of theta stored at theta_i = 2 pi i / N,
+ * Sec. 4 and Sec. 6.1).
+ *
+ * tms_theta_translate -- Eq. (translate): every column of a coordinate array
+ * replaced by the samples of its trigonometric interpolant at theta_i + rho
+ * (FFT, multiply the k-th coefficient by e^{j k rho}, inverse FFT); with
+ * derivative = 1, by those of its theta-derivative at theta_i + rho (the
+ * coefficient times j k e^{j k rho}, Eq. translate2).  k runs over the signed
+ * frequencies -N/2 < k < N/2; the Nyquist coefficient is multiplied by
+ * cos(N rho / 2) (0 for the derivative), so real data stay real.  Globalizing
+ * a manifold (Sec. 6.1) translates each s column by rho = -n omega.
+ *   dIn, dOut : device, nCoord blocks of nCols columns of N doubles (theta
+ *               fastest; block c at c * ldc, column k at c * ldc + k * N) --
+ *               the mesh layout.  dOut may equal dIn.
+ *   N         : power of two, 8..8192.
+ *   dRho      : device, nCols shifts (one per column, shared by its
+ *               coordinates), or NULL to use rho0 for every column.
+ * FP64 throughout.  Asynchronous; allocates nothing.  TMS_ERR_ARG on a bad
+ * size or pointer.
+ */
+tms_status tms_theta_translate(const double *dIn, double *dOut, int N, int nCols, int nCoord,
+                               long long ldc, const double *dRho, double rho0, int derivative,
+                               void *stream);
+
+/*
+ * tms_phase_align -- Eq. (rhoEquationDiscrete) for nAlign independent pairs of
+ * circles: cost(m) = sum_i || Wr(theta_i + 2 pi m / N) - Wprev(theta_i) ||
+ * (Euclidean norm over the nCoord coordinates; Wr(theta_i + 2 pi m / N) is the
+ * sample (i + m) mod N) for m = 0..N-1, and its minimiser (ties to the
+ * smallest m).  The paper aligns each torus of a family with the previous,
+ * already aligned one; since a grid shift only reindexes, aligning every
+ * consecutive raw pair at once and summing the shifts gives the same result.
+ *   dWr, dWprev : device, nAlign x nCoord x N doubles (alignment a at
+ *                 a * nCoord * N, coordinate c at + c * N).  1 <= nCoord <= 8.
+ *   dCost       : device, nAlign x N doubles out.
+ *   dShift      : device, nAlign int32 out: the minimising m.
+ * FP64; each cost is summed in order of i.  Asynchronous; allocates nothing.
+ */
+tms_status tms_phase_align(const double *dWr, const double *dWprev, int N, int nCoord,
+                           int nAlign, double *dCost, int32_t *dShift, void *stream);
+
 /* Per-stage device time (ms) of the last search on `stream` made with
  * params.timing = 1, in this order:
  *   0 counters/bounds init   1 face pass: world bounds   2 grid parameters

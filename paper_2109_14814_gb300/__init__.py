@@ -6,11 +6,12 @@ narrow phase solving the 4x4 system for (a, b, c, d), merged and sorted hits,
 a batched form replayed from a CUDA graph, an FP64 adjoint, the damped-Newton
 refinement of hits on the true surfaces (Sec. 7) and its continuation through
 the family parameter (Sec. 8), and the method-of-layers sweep over half-layer
-pairs (Sec. 5) as one batched search.  All compute is
+pairs (Sec. 5) as one batched search, and the FFT translation / derivative and
+phase alignment of theta grids (Sec. 6.1, Sec. 7, Sec. 8.2).  All compute is
 in libtms.so (C ABI in include/tms.h); this package only marshals arguments.
 """
 from ._binding import (CONTINUE_STATUS, HIT_BYTES, REFINE_STATUS, STAGES, ContinueParams, Continued,
-                       LayerPair, LayerSweep, layer_pairs,
+                       LayerPair, LayerSweep, layer_pairs, phase_align, theta_translate,
                        Refined, RefineParams, SurfacePair, continue_branches, refine, refine_params,
                        surface_pair, TMS_ERR_ARG, TMS_ERR_CAPACITY, TMS_ERR_CUDA,
                        TMS_ERR_STATE, TMS_ERR_TIMEOUT, TMS_OK, HitPoint, Hits, Mesh, Params, Stats,
@@ -19,7 +20,7 @@ from ._binding import (CONTINUE_STATUS, HIT_BYTES, REFINE_STATUS, STAGES, Contin
                        search_noalloc, status_str, version)
 
 __all__ = ["CONTINUE_STATUS", "HIT_BYTES", "REFINE_STATUS", "STAGES", "ContinueParams", "Continued",
-           "LayerPair", "LayerSweep", "layer_pairs",
+           "LayerPair", "LayerSweep", "layer_pairs", "phase_align", "theta_translate",
            "Refined", "RefineParams", "SurfacePair", "continue_branches", "refine", "refine_params",
            "surface_pair", "TMS_ERR_ARG", "TMS_ERR_CAPACITY", "TMS_ERR_CUDA",
            "TMS_ERR_STATE", "TMS_ERR_TIMEOUT", "TMS_OK", "HitPoint", "Hits", "Mesh", "Params",

@@ -181,6 +181,10 @@ def lib():
     L.tms_layer_plan_destroy.restype = I
     L.tms_layer_search.argtypes = [P, _c.POINTER(Params), P, LL, P, _c.POINTER(LL), P]
     L.tms_layer_search.restype = I
+    L.tms_theta_translate.argtypes = [P, P, I, I, I, LL, P, D, I, P]
+    L.tms_theta_translate.restype = I
+    L.tms_phase_align.argtypes = [P, P, I, I, I, P, P, P]
+    L.tms_phase_align.restype = I
     _lib = L
     return L
 
@@ -665,6 +669,50 @@ class LayerSweep:
             self.close()
         except Exception:
             pass
+
+
+def theta_translate(X: torch.Tensor, rho, derivative: bool = False, out=None, stream=None):
+    """tms_theta_translate: each theta column of X (CUDA float64, (C, M, N) or
+    (M, N), theta fastest) moved to theta + rho (Eq. translate) or, with
+    `derivative`, its theta-derivative there (Eq. translate2).  rho: a float,
+    or a CUDA float64 tensor of M per-column shifts.  Returns `out` (a new
+    tensor unless given; may be X itself)."""
+    if not (X.is_cuda and X.dtype == torch.float64 and X.is_contiguous() and X.dim() in (2, 3)):
+        raise ValueError("X must be a contiguous CUDA float64 tensor (C, M, N) or (M, N)")
+    C = 1 if X.dim() == 2 else int(X.shape[0])
+    M, N = int(X.shape[-2]), int(X.shape[-1])
+    out = torch.empty_like(X) if out is None else out
+    if isinstance(rho, torch.Tensor):
+        r = rho.to(device=X.device, dtype=torch.float64).contiguous()
+        if r.numel() != M:
+            raise ValueError("rho must hold one shift per column")
+        rp, r0 = r.data_ptr(), 0.0
+    else:
+        r, rp, r0 = None, None, float(rho)
+    rc = lib().tms_theta_translate(X.data_ptr(), out.data_ptr(), N, M, C, M * N, rp, r0,
+                                   int(bool(derivative)), _stream(stream))
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_theta_translate")
+    return out
+
+
+def phase_align(Wr: torch.Tensor, Wprev: torch.Tensor, stream=None):
+    """tms_phase_align: the grid shift m minimising Eq. (rhoEquationDiscrete)
+    for each pair of circles.  Wr, Wprev: CUDA float64 (A, C, N) or (C, N).
+    Returns (shift int32 (A,), cost float64 (A, N))."""
+    single = Wr.dim() == 2
+    a, b = (Wr[None], Wprev[None]) if single else (Wr, Wprev)
+    if a.shape != b.shape or not (a.is_cuda and a.dtype == torch.float64):
+        raise ValueError("Wr and Wprev must be CUDA float64 tensors of one shape")
+    a, b = a.contiguous(), b.contiguous()
+    A, C, N = (int(v) for v in a.shape)
+    cost = torch.empty((A, N), dtype=torch.float64, device=a.device)
+    shift = torch.empty(A, dtype=torch.int32, device=a.device)
+    rc = lib().tms_phase_align(a.data_ptr(), b.data_ptr(), N, C, A, cost.data_ptr(),
+                               shift.data_ptr(), _stream(stream))
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_phase_align")
+    return (shift[0], cost[0]) if single else (shift, cost)
 
 
 def release_workspace(stream=None):

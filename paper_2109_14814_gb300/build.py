@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtms.so")
 SOURCES = ["tms_faces.cu", "tms_sort.cu", "tms_pairs.cu", "tms_narrow.cu", "tms_api.cu", "tms_probe.cu",
-           "tms_noalloc.cu", "tms_tune.cu", "tms_group.cu", "tms_refine.cu"]
+           "tms_noalloc.cu", "tms_tune.cu", "tms_group.cu", "tms_refine.cu", "tms_theta.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -153,3 +153,15 @@ def test_layer_pairs_host_enumeration_matches_oracle():
         tms.layer_pairs(p.A.s, lay["D_u"], 0.5, p.B.s, lay["D_s"], lay["lam_s"], 3)
     with pytest.raises(tms.TmsError):                     # more layers than the mesh holds
         tms.layer_pairs(p.A.s, lay["D_u"], lay["lam_u"], p.B.s, lay["D_s"], lay["lam_s"], 4)
+
+
+def test_theta_arguments_checked_without_gpu():
+    lib = tms.lib()
+    # sizes are checked before any device call; an empty batch is a no-op
+    assert lib.tms_theta_translate(None, None, 12, 4, 4, 48, None, 0.0, 0, None) == tms.TMS_ERR_ARG
+    assert lib.tms_theta_translate(None, None, 16384, 4, 4, 65536, None, 0.0, 0, None) == tms.TMS_ERR_ARG
+    assert lib.tms_theta_translate(None, None, 64, 0, 4, 0, None, 0.0, 0, None) == tms.TMS_OK
+    assert lib.tms_theta_translate(None, None, 64, 4, 4, 64, None, 0.0, 0, None) == tms.TMS_ERR_ARG
+    assert lib.tms_theta_translate(None, None, 64, 4, 4, 256, None, float("nan"), 0, None) == tms.TMS_ERR_ARG
+    assert lib.tms_phase_align(None, None, 64, 9, 1, None, None, None) == tms.TMS_ERR_ARG
+    assert lib.tms_phase_align(None, None, 64, 4, 0, None, None, None) == tms.TMS_OK
