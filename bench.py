@@ -209,6 +209,24 @@ def run_tms(args, ws, rank, local):
         n_hits = len(h)
         stats = tms.last_stats(stream)
 
+    if args.only_extras:
+        # just the named secondary measurements (for profiling them on their own)
+        fp64_tf = tms.probe_fp64_tflops()
+        runs = {"plain_fp64": lambda: plain_fp64(tms, A, B, out, stream, flush, h),
+                "batched": lambda: batched_search(tms, device, stream, flush),
+                "adjoint": lambda: adjoint_timing(tms, device, stream),
+                "refine": lambda: refine_timing(tms, pair, h, stream, flush, fp64_tf),
+                "continuation": lambda: continue_timing(tms, pair, h, stream, fp64_tf),
+                "layers": lambda: layer_timing(tms, device, stream, flush),
+                "theta": lambda: theta_timing(tms, device, stream, flush)}
+        names = [x for x in args.only_extras.split(",") if x]
+        unknown = [x for x in names if x not in runs]
+        if unknown:
+            raise SystemExit(f"unknown extras {unknown}; choose from {sorted(runs)}")
+        if rank == 0:
+            print(json.dumps({"extras": {x: runs[x]() for x in names}}), flush=True)
+        return
+
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -730,6 +748,9 @@ def main():
                     help="also time the plain FP64 path, the batched 256-pair search, the adjoint, "
                          "the refinement of the hits, their continuation, the layer sweep and "
                          "the theta-grid operations")
+    ap.add_argument("--only-extras", default="",
+                    help="comma-separated extras to run alone (no main timing): plain_fp64, batched, "
+                         "adjoint, refine, continuation, layers, theta")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
