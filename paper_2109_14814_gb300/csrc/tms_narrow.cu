@@ -177,7 +177,7 @@ __device__ __forceinline__ bool split_boxes_overlap(const float4 X[3][2], const 
 
 
 // true when the verified FP32 solve proves margin < -2 tau (not a hit)
-__device__ __forceinline__ bool fp32_verified_reject(const float4 X[3][2], const float4 Y[3][2],
+__device__ __noinline__ bool fp32_verified_reject(const float4 X[3][2], const float4 Y[3][2],
                                                   double tau) {
     const float u = 5.9604645e-08f;
     float A[4][4], EA[4][4], r[4], Er[4];
@@ -540,7 +540,7 @@ __device__ __forceinline__ bool quad_sat_reject(const float4 QA[4][2], const flo
 
 // true when the separating-axis test proves the margin below -delta (not a hit,
 // also for an FP64 solve of the same system)
-__device__ __forceinline__ bool fp32_sat_reject(const float4 X[3][2], const float4 Y[3][2],
+__device__ __noinline__ bool fp32_sat_reject(const float4 X[3][2], const float4 Y[3][2],
                                                 double tau) {
     const float u = 5.9604645e-08f;
     // vectors relative to x2
