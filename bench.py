@@ -97,11 +97,77 @@ def committed_traffic(kernel: str):
         return None
 
 
+# ncu kernel names of each stage label (the keys of profiles/traffic.json)
+TRAFFIC_STAGES = {
+    "tms::k_bounds_pass": ("k_bounds_pass",),
+    "tms::k_cell_pass<MARK>": ("k_cell_pass<1, 1>",),
+    "tms::k_cell_pass<PROBE_MARK, PROBE>": ("k_cell_pass<1, 2>", "k_cell_pass<1, 3>"),
+    "tms::k_group_count": ("k_group_count",),
+    "tms::k_cells_* + k_group_scatter": ("k_cells_reduce", "k_cells_partials", "k_cells_down",
+                                         "k_group_scatter"),
+    "tms::k_emit": ("k_emit",),
+    "tms::k_narrow_filter + k_narrow_fp64": ("k_narrow_filter", "k_narrow_fp64"),
+}
+TRAFFIC_COMMAND = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                   "--clock-control none -s 60 -c 60 --csv --log-file traffic.csv "
+                   "python bench.py --steps 1 --warmup 3 --no-e2e --no-cpu")
+
+
+def write_traffic(csv_path: str) -> dict:
+    """profiles/traffic.json from an ncu CSV of TRAFFIC_COMMAND: the DRAM bytes of
+    the last complete search in the capture (from k_search_init to the last
+    kernel before the next one), per stage label and per launch."""
+    import csv
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1024.0, "MB": 1048576.0}
+    rows = list(csv.reader(open(csv_path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
+    h = rows[hi]
+    ci = {k: h.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
+    launches = {}
+    for r in rows[hi + 1:]:
+        if len(r) < len(h):
+            continue
+        name = r[ci["Kernel Name"]].split("(")[0].replace("tms::", "").replace("void ", "")
+        name = name.replace("(anonymous namespace)::", "").replace("<unnamed>::", "").strip()
+        L = launches.setdefault(int(r[ci["ID"]]), {"name": name, "bytes": 0.0})
+        if r[ci["Metric Name"]] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            L["bytes"] += float(r[ci["Metric Value"]].replace(",", "")) * scale[r[ci["Metric Unit"]]]
+    seq = [launches[k] for k in sorted(launches)]
+    starts = [i for i, L in enumerate(seq) if L["name"].startswith(("k_search_init", "k_bounds_init"))]
+    if len(starts) < 2:
+        raise SystemExit("the capture holds no complete search")
+    one = seq[starts[-2]:starts[-1]]
+    out = {}
+    for label, names in TRAFFIC_STAGES.items():
+        ks = [L for L in one if any(L["name"].startswith(n) for n in names)]
+        if not ks:
+            continue
+        per = {}
+        for L in ks:
+            per[L["name"]] = per.get(L["name"], 0.0) + L["bytes"]
+        out[label] = {"dram_bytes_per_launch": sum(L["bytes"] for L in ks) / len(ks),
+                      "kernels": per, "source_hash": source_hash(),
+                      "workload": "4096x512 vs 4096x512 vertex meshes, quad faces, mixed precision "
+                                  "(the bench workload)",
+                      "command": TRAFFIC_COMMAND}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    return out
+
+
+# the files that hold the search's kernels and their launch sequence
+SEARCH_SOURCES = ("tms_common.cuh", "tms_faces.cu", "tms_group.cu", "tms_pairs.cu",
+                  "tms_narrow.cu", "tms_sort.cu", "tms_api.cu")
+
+
 def source_hash() -> str:
+    """Hash of the search's kernel sources: committed DRAM counters taken on other
+    sources are not reported."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2109_14814_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in SEARCH_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -306,7 +372,8 @@ def run_tms(args, ws, rank, local):
             peak, unit = lane_ops / 1e12, "Tops/s"
         kernels[st_name] = {"kernel": kname, "bound": bound, "launches": launches, "ms": t,
                             "algorithmic_work": work, "achieved": ach, "peak": peak, "unit": unit,
-                            "frac": ach / peak if (ach and peak) else None}
+                            "frac": ach / peak if (ach and peak) else None,
+                            "traffic": committed_traffic(kname)}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
     roofline = {"kernel": d["kernel"], "stage": dom, "bound": d["bound"], "achieved": d["achieved"],
@@ -748,10 +815,17 @@ def main():
                     help="also time the plain FP64 path, the batched 256-pair search, the adjoint, "
                          "the refinement of the hits, their continuation, the layer sweep and "
                          "the theta-grid operations")
+    ap.add_argument("--write-traffic", default="", metavar="CSV",
+                    help="write profiles/traffic.json from an ncu CSV of one search's DRAM bytes "
+                         "(see TRAFFIC_COMMAND) and exit; needs no GPU")
     ap.add_argument("--only-extras", default="",
                     help="comma-separated extras to run alone (no main timing): plain_fp64, batched, "
                          "adjoint, refine, continuation, layers, theta")
     args = ap.parse_args()
+    if args.write_traffic:
+        for k, v in write_traffic(args.write_traffic).items():
+            print(f"{k}: {v['dram_bytes_per_launch'] / 1e6:.1f} MB per launch")
+        return
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
     if args.impl == "reference":
