@@ -284,7 +284,8 @@ def run_tms(args, ws, rank, local):
                 "refine": lambda: refine_timing(tms, pair, h, stream, flush, fp64_tf),
                 "continuation": lambda: continue_timing(tms, pair, h, stream, fp64_tf),
                 "layers": lambda: layer_timing(tms, device, stream, flush),
-                "theta": lambda: theta_timing(tms, device, stream, flush)}
+                "theta": lambda: theta_timing(tms, device, stream, flush),
+                "e2e_pipelined": lambda: pipelined_e2e(tms, pair, device)}
         names = [x for x in args.only_extras.split(",") if x]
         unknown = [x for x in names if x not in runs]
         if unknown:
@@ -442,7 +443,8 @@ def run_tms(args, ws, rank, local):
                   "continuation": continue_timing(tms, pair, h, stream,
                                                   (fp64 or {}).get("peak_tflops") or tms.probe_fp64_tflops()),
                   "layers": layer_timing(tms, device, stream, flush),
-                  "theta": theta_timing(tms, device, stream, flush)}
+                  "theta": theta_timing(tms, device, stream, flush),
+                  "e2e_pipelined": pipelined_e2e(tms, pair, device)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -758,6 +760,56 @@ def theta_timing(tms, device, stream, flush):
                             "cpu_kind": "oracle (numpy, one roll per shift), one alignment timed x 16"}}
 
 
+def pipelined_e2e(tms, pair, device, steps: int = 50):
+    """End to end through tms_search with host buffers, as a job of many steps
+    would run it: two device buffer sets, the host-to-device copy of step i+1 on
+    a copy stream while step i searches, each step's hits copied back to pinned
+    host memory.  The bench line's own e2e keeps every copy on the critical path."""
+    hA = pair.A.X.contiguous().pin_memory()
+    hB = pair.B.X.contiguous().pin_memory()
+    XA = [torch.empty_like(hA, device=device) for _ in range(2)]
+    XB = [torch.empty_like(hB, device=device) for _ in range(2)]
+    As = [tms.Mesh(x, pair.A.s, True) for x in XA]
+    Bs = [tms.Mesh(x, pair.B.s, True) for x in XB]
+    outs = [torch.empty((1 << 17, tms.HIT_BYTES), dtype=torch.uint8, device=device) for _ in range(2)]
+    hout = torch.empty((1 << 17, tms.HIT_BYTES), dtype=torch.uint8).pin_memory()
+    s_copy, s_comp = torch.cuda.Stream(device), torch.cuda.Stream(device)
+    copied = [torch.cuda.Event() for _ in range(2)]
+
+    def copy_into(b):
+        with torch.cuda.stream(s_copy):
+            XA[b].copy_(hA, non_blocking=True)
+            XB[b].copy_(hB, non_blocking=True)
+            copied[b].record(s_copy)
+
+    def run(n):
+        copy_into(0)
+        n_hits = 0
+        for i in range(n):
+            b = i % 2
+            s_comp.wait_event(copied[b])
+            if i + 1 < n:
+                copy_into(1 - b)          # overlaps this step's search
+            h = tms.search(As[b], Bs[b], out=outs[b], stream=s_comp)
+            n_hits = len(h)
+            with torch.cuda.stream(s_comp):
+                hout[:n_hits].copy_(h.raw, non_blocking=True)
+        return n_hits
+
+    run(4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s_copy)
+    n_hits = run(steps)
+    e1.record(s_comp)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"ms_per_step": ms, "steps": steps, "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
+            "d2h_bytes_per_step": int(n_hits * tms.HIT_BYTES),
+            "scheme": "two device buffer sets; the H2D copy of step i+1 on a copy stream during "
+                      "the search of step i; hits of every step copied to pinned host memory"}
+
+
 def cpu_baseline(pair):
     import oracle
     OA, OB = oracle.OMesh.from_grid(pair.A), oracle.OMesh.from_grid(pair.B)
@@ -820,7 +872,7 @@ def main():
                          "(see TRAFFIC_COMMAND) and exit; needs no GPU")
     ap.add_argument("--only-extras", default="",
                     help="comma-separated extras to run alone (no main timing): plain_fp64, batched, "
-                         "adjoint, refine, continuation, layers, theta")
+                         "adjoint, refine, continuation, layers, theta, e2e_pipelined")
     args = ap.parse_args()
     if args.write_traffic:
         for k, v in write_traffic(args.write_traffic).items():
