@@ -478,6 +478,38 @@ __device__ __forceinline__ void split_f32(double x, float &hi, float &lo) {
     lo = (b >> 63) ? -l : l;
 }
 
+// All four FP32 roundings the bounds pass needs from one decomposition of x:
+// rd / ru the FP32 numbers just below and above x (outward box bounds) and the
+// split hi = RN32(x), lo = RN32(x - hi); identical to f32_rd, f32_ru and
+// split_f32, which take the special cases (zero, subnormal, huge, NaN).
+__device__ __forceinline__ void f32_all(double x, float &rd, float &ru, float &hi, float &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const int e32 = e - 896;
+    if (e32 <= 0 || e32 >= 255) {
+        rd = f32_rd(x);
+        ru = f32_ru(x);
+        split_f32(x, hi, lo);
+        return;
+    }
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+    const unsigned mag = ((unsigned)e32 << 23) | (unsigned)(m >> 29);   // truncated |x|
+    const unsigned rem = (unsigned)(m & 0x1FFFFFFFULL);               // the 29 bits dropped
+    const unsigned neg = (unsigned)(b >> 63);
+    const unsigned sgn = neg << 31;
+    const unsigned inexact = rem != 0u;
+    rd = __uint_as_float(sgn | (mag + (neg & inexact)));
+    ru = __uint_as_float(sgn | (mag + ((neg ^ 1u) & inexact)));
+    const unsigned up = (unsigned)(rem > 0x10000000u) | ((unsigned)(rem == 0x10000000u) & (mag & 1u));
+    hi = __uint_as_float(sgn | (mag + up));
+    // x - hi = (rem - up 2^29) ulp, ulp = 2^(e - 1075)
+    const int r = up ? (int)rem - (1 << 29) : (int)rem;
+    const int ex = e - 1075 + 127;
+    float l = 0.0f;
+    if (ex >= 1) l = __int2float_rn(r) * __uint_as_float((unsigned)ex << 23);
+    lo = neg ? -l : l;
+}
+
 struct DedupArgs {
     const uint64_t *keys;          // sorted hit keys
     const uint32_t *vals;          // sorted raw-hit indices

@@ -106,6 +106,31 @@ __device__ __forceinline__ void write_split(const MeshDev &m, size_t idx, const 
     m.split[2 * idx + 1] = lo;
 }
 
+// The tile's own vertex: its FP32 bounds for the boxes and its split copy,
+// from one decomposition per coordinate in the mixed mode.
+template <int PREC>
+__device__ __forceinline__ void vtx_and_split(const double x[4], Vtx<PREC> &out, const MeshDev &m,
+                                              size_t idx);
+template <>
+__device__ __forceinline__ void vtx_and_split<1>(const double x[4], Vtx<1> &out, const MeshDev &m,
+                                                 size_t idx) {
+    Vtx<1> v;
+    float4 hi, lo;
+    f32_all(x[0], v.lo[0], v.hi[0], hi.x, lo.x);
+    f32_all(x[1], v.lo[1], v.hi[1], hi.y, lo.y);
+    f32_all(x[2], v.lo[2], v.hi[2], hi.z, lo.z);
+    f32_all(x[3], v.lo[3], v.hi[3], hi.w, lo.w);
+    out = v;
+    m.split[2 * idx] = hi;
+    m.split[2 * idx + 1] = lo;
+}
+template <>
+__device__ __forceinline__ void vtx_and_split<0>(const double x[4], Vtx<0> &out, const MeshDev &m,
+                                                 size_t idx) {
+    to_vtx(x, out);
+    write_split(m, idx, x);
+}
+
 template <int PREC>
 struct GridView;
 template <>
@@ -256,16 +281,22 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
                 for (int c = 0; c < 4; ++c) x[r][c] = __ldg(m.c[c] + off);
             }
         }
+        // a vertex's split copy is written by the tile that owns it: rows below the
+        // tile's last (the next tile's first) and the mesh's last row
+        const bool last_rows = kq0 + rows_q == m.nqk;
 #pragma unroll
         for (int r = 0; r <= TK; ++r) {
             if (col_ok && r <= rows_q) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) nonfinite |= !finite64(x[r][c]);
-                to_vtx(x[r], sv[r * W + t]);
-                write_split(m, (size_t)(kq0 + r) * m.N + vi, x[r]);
+                if (r < rows_q || last_rows)
+                    vtx_and_split<PREC>(x[r], sv[r * W + t], m, (size_t)(kq0 + r) * m.N + vi);
+                else
+                    to_vtx(x[r], sv[r * W + t]);
             }
         }
-        // the last vertex column of the tile (wraps to column 0 on a periodic mesh)
+        // the last vertex column of the tile (wraps to column 0 on a periodic mesh);
+        // it belongs to the next tile, except an open mesh's last column
         if (t <= rows_q) {
             int vj = i0 + cols_q;
             if (vj == m.N) vj = 0;
@@ -276,8 +307,9 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
                 y[c] = __ldg(m.c[c] + off);
                 nonfinite |= !finite64(y[c]);
             }
-            to_vtx(y, sv[t * W + cols_q]);
-            write_split(m, off, y);
+            const bool own_col = !m.periodic && vj == m.N - 1 && (t < rows_q || last_rows);
+            if (own_col) vtx_and_split<PREC>(y, sv[t * W + cols_q], m, off);
+            else to_vtx(y, sv[t * W + cols_q]);
         }
     }
     __syncthreads();
