@@ -70,15 +70,19 @@ struct Coef {
     double sak[kH][4], sbk[kH][4], sna[kH][4], sb[kH][4];     // at alpha_s
     double ark[kH][4], brk[kH][4], nar[kH][4], br[kH][4];     // at alpha_ref
     double kar[kH][4], kbr[kH][4];                            // at alpha_ref, T''
+    // continuation: the walking sheet's tables above are taken at parameter 0 and
+    // these hold their derivatives, so a branch at its own alpha uses
+    // fma(alpha, d, table) -- the coefficients are affine in the parameter
+    double dak[kH][4], dbk[kH][4], dna[kH][4], db[kH][4];
     double fd[kF][4];               // fold_amp * fold_dir
     double root[kF][3];             // fold roots
     double v1[4], v2[4];
 };
 
-// Fills the tables for (alpha_u, alpha_s); called by every thread of the block
-// between two barriers.
-__device__ void build_tables(Coef &cf, const tms_surface_pair &sp, double au, double as, int t,
-                             int nt) {
+// Fills the tables for (alpha_u, alpha_s) and, for a walking sheet (walk != 0),
+// the derivative tables; called by the threads of the block before a barrier.
+__device__ void build_tables(Coef &cf, const tms_surface_pair &sp, double au, double as, int walk,
+                             int t, int nt) {
     for (int q = t; q < kH * 4; q += nt) {
         const int h = q >> 2, c = q & 3;
         const double k = (double)(h + 1);
@@ -102,6 +106,12 @@ __device__ void build_tables(Coef &cf, const tms_surface_pair &sp, double au, do
         cf.br[h][c] = br;
         cf.kar[h][c] = -k * ar;
         cf.kbr[h][c] = -k * br;
+        if (walk) {
+            cf.dak[h][c] = sp.dca[h][c] / k;
+            cf.dbk[h][c] = sp.dcb[h][c] / k;
+            cf.dna[h][c] = -sp.dca[h][c];
+            cf.db[h][c] = sp.dcb[h][c];
+        }
     }
     if (t < kF * 4) cf.fd[t >> 2][t & 3] = sp.fold_amp[t >> 2] * sp.fold_dir[t >> 2][t & 3];
     if (t < kF * 3) cf.root[t / 3][t % 3] = sp.fold_root[t / 3][t % 3];
@@ -115,7 +125,8 @@ __device__ void build_tables(Coef &cf, const tms_surface_pair &sp, double au, do
 struct Solve {
     double x0, x1, x2, x3;   // iterate (angles unwrapped)
     int code;                // -1 while iterating, else TMS_REFINE_*
-    int iters;               // updates made
+    int iters;               // updates made when the solve stopped
+    int k;                   // updates made so far
     double fn, rh, rc2;      // ||f||^2, det Df, prod ||Df e_j||^2 at the last evaluation
 };
 
@@ -138,257 +149,304 @@ __device__ __forceinline__ void cubic(double s, const double *r, double &p, doub
     p2 = 2.0 * (d0 + d1 + d2);
 }
 
-// Damped Newton (Eq. dampedNewtonEquation) on f = W_A - W_B from S's iterate
-// until S.code is set; every lane of the warp calls it (the loop runs while any
-// of the warp's quads iterates).
-__device__ __forceinline__ void newton_solve(const Coef &cf, const tms_surface_pair &sp,
-                                             const tms_refine_params &pr, Solve &S, int c,
-                                             int base) {
-    const double tol2 = pr.tol * pr.tol, sw2 = pr.switch_below * pr.switch_below;
+// The quantities one damped-Newton iteration needs at the iterate (x0..x3): the
+// stop checks, ||f||^2, the product of Df's squared column norms, det Df and the
+// Newton step dx = Df^{-1} f.  Every lane of the warp calls it together (it
+// exchanges values within the quad).  WALK = 1 or 2: the sheet of W_A or of B
+// is taken at the quad's own parameter aw (continuation); 0: both at the
+// tables' values.
+struct Eval {
+    int pre;       // stop decided before evaluating (non-finite or escaped iterate), or -1
+    int fin;       // f and Df finite
+    double r2, cn2, det, dx[4];
+};
+
+template <int WALK>
+__device__ __forceinline__ void evaluate(const Coef &cf, const tms_surface_pair &sp,
+                                         const tms_refine_params &pr, double lnlam, double x0,
+                                         double x1, double x2, double x3, double aw, int c,
+                                         int base, Eval &E) {
     const int K = sp.n_harmonics;
     const int NF = sp.n_folds;
-    const double lnlam = sp.stretch ? log(sp.lam) : 0.0;
-    double x0 = S.x0, x1 = S.x1, x2 = S.x2, x3 = S.x3;
-    int code = S.code, iters = S.iters;
-    double fn = S.fn, rh = S.rh, rc2 = S.rc2;
+    // ---- stop checks on the iterate (identical on the quad's lanes)
+    int pre = -1;
+    if (!(isfinite(x0) && isfinite(x1) && isfinite(x2) && isfinite(x3)))
+        pre = TMS_REFINE_NON_FINITE;
+    else if (x1 < pr.s_lo || x1 > pr.s_hi || x3 < pr.s_lo || x3 > pr.s_hi)
+        pre = TMS_REFINE_ESCAPED;
 
-    for (int k = 0; __any_sync(kFull, code < 0); ++k) {
-        // ---- stop checks on the iterate (identical on the quad's lanes)
-        int pre = -1;
-        if (!(isfinite(x0) && isfinite(x1) && isfinite(x2) && isfinite(x3)))
-            pre = TMS_REFINE_NON_FINITE;
-        else if (x1 < pr.s_lo || x1 > pr.s_hi || x3 < pr.s_lo || x3 > pr.s_hi)
-            pre = TMS_REFINE_ESCAPED;
+    // ---- sines/cosines and exponentials, one per lane
+    const double arg = c == 0 ? x0
+                     : c == 1 ? x2 + sp.c0
+                     : c == 2 ? sp.P * (x2 - sp.theta0)
+                              : sp.Q * kPi * (x3 - sp.s0);
+    double sn, cs;
+    sincos(arg, &sn, &cs);
+    const double sA = lane_val(sn, base, 0), cA = lane_val(cs, base, 0);
+    const double sB = lane_val(sn, base, 1), cB = lane_val(cs, base, 1);
+    const double sh1 = lane_val(sn, base, 2), ch1 = lane_val(cs, base, 2);
+    const double sh2 = lane_val(sn, base, 3), ch2 = lane_val(cs, base, 3);
+    const double s1 = 1.0 - x3;   // s' of B's underlying sheet
+    double gA, gA1, gB, gB1, gB2;
+    if (sp.stretch) {
+        const double e = exp(lnlam * (c == 0 ? x1 : s1));
+        gA = lane_val(e, base, 0);
+        gB = lane_val(e, base, 1);
+        gA1 = lnlam * gA;
+        gB1 = lnlam * gB;
+        gB2 = lnlam * gB1;
+    } else {
+        gA = 1.0 + x1;
+        gA1 = 1.0;
+        gB = 1.0 + s1;
+        gB1 = 1.0;
+        gB2 = 0.0;
+    }
 
-        // ---- sines/cosines and exponentials, one per lane
-        const double arg = c == 0 ? x0
-                         : c == 1 ? x2 + sp.c0
-                         : c == 2 ? sp.P * (x2 - sp.theta0)
-                                  : sp.Q * kPi * (x3 - sp.s0);
-        double sn, cs;
-        sincos(arg, &sn, &cs);
-        const double sA = lane_val(sn, base, 0), cA = lane_val(cs, base, 0);
-        const double sB = lane_val(sn, base, 1), cB = lane_val(cs, base, 1);
-        const double sh1 = lane_val(sn, base, 2), ch1 = lane_val(cs, base, 2);
-        const double sh2 = lane_val(sn, base, 3), ch2 = lane_val(cs, base, 3);
-        const double s1 = 1.0 - x3;   // s' of B's underlying sheet
-        double gA, gA1, gB, gB1, gB2;
-        if (sp.stretch) {
-            const double e = exp(lnlam * (c == 0 ? x1 : s1));
-            gA = lane_val(e, base, 0);
-            gB = lane_val(e, base, 1);
-            gA1 = lnlam * gA;
-            gB1 = lnlam * gB;
-            gB2 = lnlam * gB1;
-        } else {
-            gA = 1.0 + x1;
-            gA1 = 1.0;
-            gB = 1.0 + s1;
-            gB1 = 1.0;
-            gB2 = 0.0;
-        }
-
-        // ---- folds F(s) at s_u and at s': lane f evaluates fold f's cubics
-        double FA = 0.0, FA1 = 0.0, FB = 0.0, FB1 = 0.0, FB2 = 0.0;
-        if (NF > 0) {
-            double p, p1, p2, q, q1, q2;
-            const int fo = c < NF ? c : 0;
-            cubic(x1, cf.root[fo], p, p1, p2);
-            cubic(s1, cf.root[fo], q, q1, q2);
+    // ---- folds F(s) at s_u and at s': lane f evaluates fold f's cubics
+    double FA = 0.0, FA1 = 0.0, FB = 0.0, FB1 = 0.0, FB2 = 0.0;
+    if (NF > 0) {
+        double p, p1, p2, q, q1, q2;
+        const int fo = c < NF ? c : 0;
+        cubic(x1, cf.root[fo], p, p1, p2);
+        cubic(s1, cf.root[fo], q, q1, q2);
 #pragma unroll
-            for (int f = 0; f < kF; ++f) {
-                if (f < NF) {
-                    const double w = cf.fd[f][c];
-                    FA = fma(w, lane_val(p, base, f), FA);
-                    FA1 = fma(w, lane_val(p1, base, f), FA1);
-                    FB = fma(w, lane_val(q, base, f), FB);
-                    FB1 = fma(w, lane_val(q1, base, f), FB1);
-                    FB2 = fma(w, lane_val(q2, base, f), FB2);
-                }
-            }
-        }
-
-        // ---- harmonic sums: T, T' at theta_u (alpha_u); T, T' at theta' (alpha_s);
-        //      T, T', T'' at theta' (alpha_ref).  cos/sin of k theta by angle addition.
-        double TA = 0.0, TAt = 0.0, TB = 0.0, TBt = 0.0, TR = 0.0, TRt = 0.0, TRtt = 0.0;
-        double ckA = cA, skA = sA, ckB = cB, skB = sB;
-#pragma unroll
-        for (int h = 0; h < kH; ++h) {
-            if (h < K) {
-                TA = fma(cf.uak[h][c], ckA, fma(cf.ubk[h][c], skA, TA));
-                TAt = fma(cf.ub[h][c], ckA, fma(cf.una[h][c], skA, TAt));
-                TB = fma(cf.sak[h][c], ckB, fma(cf.sbk[h][c], skB, TB));
-                TBt = fma(cf.sb[h][c], ckB, fma(cf.sna[h][c], skB, TBt));
-                TR = fma(cf.ark[h][c], ckB, fma(cf.brk[h][c], skB, TR));
-                TRt = fma(cf.br[h][c], ckB, fma(cf.nar[h][c], skB, TRt));
-                TRtt = fma(cf.kar[h][c], ckB, fma(cf.kbr[h][c], skB, TRtt));
-                if (h + 1 < K) {
-                    const double nA = ckA * cA - skA * sA;
-                    skA = skA * cA + ckA * sA;
-                    ckA = nA;
-                    const double nB = ckB * cB - skB * sB;
-                    skB = skB * cB + ckB * sB;
-                    ckB = nB;
-                }
-            }
-        }
-
-        // ---- W_A and its partials; B's underlying sheet; the frame sheet
-        const double WA = gA * TA + FA, WAt = gA * TAt, WAs = gA1 * TA + FA1;
-        const double SB = gB * TB + FB, SBt = gB * TBt, SBs = gB1 * TB + FB1;
-        const double t1 = gB * TRt, t2 = gB1 * TR + FB1;
-        const double Wtt = gB * TRtt, Wts = gB1 * TRt, Wss = gB2 * TR + FB2;
-        const double v1 = cf.v1[c], v2 = cf.v2[c];
-
-        // ---- normal frame (n1, n2) and its theta- and s-partials
-        const double g11 = quad_sum(t1 * t1), g12 = quad_sum(t1 * t2), g22 = quad_sum(t2 * t2);
-        const double j11 = quad_sum(t1 * v1), j21 = quad_sum(t2 * v1);
-        const double j12 = quad_sum(t1 * v2), j22 = quad_sum(t2 * v2);
-        const double P1 = quad_sum(t1 * Wtt), P2 = quad_sum(t1 * Wts), P3 = quad_sum(Wtt * t2);
-        const double P4 = quad_sum(t2 * Wts), P5 = quad_sum(t1 * Wss), P6 = quad_sum(t2 * Wss);
-        const double Lt1 = quad_sum(Wtt * v1), Ls1 = quad_sum(Wts * v1), Ss1 = quad_sum(Wss * v1);
-        const double Lt2 = quad_sum(Wtt * v2), Ls2 = quad_sum(Wts * v2), Ss2 = quad_sum(Wss * v2);
-        const double eps = sp.reg * 0.5 * (g11 + g22);
-        const double G11 = g11 + eps, G12 = g12, G22 = g22 + eps;
-        const double idet = 1.0 / (G11 * G22 - G12 * G12);
-        // d/dtheta and d/ds of G (J^T J + eps I)
-        const double tg11 = 2.0 * P1, tg12 = P2 + P3, tg22 = 2.0 * P4;
-        const double te = sp.reg * 0.5 * (tg11 + tg22);
-        const double tG11 = tg11 + te, tG22 = tg22 + te;
-        const double sg11 = -2.0 * P2, sg12 = -(P5 + P4), sg22 = -2.0 * P6;
-        const double se = sp.reg * 0.5 * (sg11 + sg22);
-        const double sG11 = sg11 + se, sG22 = sg22 + se;
-
-        // lane c solves for frame vector r = c & 1, then both are shared
-        double yv[6];
-        {
-            const int r = c & 1;
-            const double j1 = r ? j12 : j11, j2 = r ? j22 : j21;
-            const double Lt = r ? Lt2 : Lt1, Ls = r ? Ls2 : Ls1, Ss = r ? Ss2 : Ss1;
-            const double y1 = (G22 * j1 - G12 * j2) * idet, y2 = (G11 * j2 - G12 * j1) * idet;
-            // theta: d t1 = Wtt, d t2 = Wts;  s: d t1 = -Wts, d t2 = -Wss
-            const double a1 = Lt - (tG11 * y1 + tg12 * y2), a2 = Ls - (tg12 * y1 + tG22 * y2);
-            const double b1 = -Ls - (sG11 * y1 + sg12 * y2), b2 = -Ss - (sg12 * y1 + sG22 * y2);
-            yv[0] = y1;
-            yv[1] = y2;
-            yv[2] = (G22 * a1 - G12 * a2) * idet;
-            yv[3] = (G11 * a2 - G12 * a1) * idet;
-            yv[4] = (G22 * b1 - G12 * b2) * idet;
-            yv[5] = (G11 * b2 - G12 * b1) * idet;
-        }
-        double n[2], nt[2], ns[2];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const double v = r == 0 ? v1 : v2;
-            const double y1 = lane_val(yv[0], base, r), y2 = lane_val(yv[1], base, r);
-            const double dt1 = lane_val(yv[2], base, r), dt2 = lane_val(yv[3], base, r);
-            const double ds1 = lane_val(yv[4], base, r), ds2 = lane_val(yv[5], base, r);
-            n[r] = v - t1 * y1 - t2 * y2;
-            nt[r] = -(Wtt * y1 + Wts * y2) - (t1 * dt1 + t2 * dt2);
-            ns[r] = (Wts * y1 + Wss * y2) - (t1 * ds1 + t2 * ds2);
-        }
-
-        // ---- W_B, f and the row of Df this lane owns
-        const double h = sp.h_amp;
-        const double H = h * (sh1 * n[0] + sh2 * n[1]);
-        const double Ht = h * (sp.P * ch1 * n[0] + sh1 * nt[0] + sh2 * nt[1]);
-        const double Hs = h * (sh1 * ns[0] + sp.Q * kPi * ch2 * n[1] + sh2 * ns[1]);
-        const double fc = WA - (SB + H);
-        double m[4] = {WAt, WAs, -(SBt + Ht), -(-SBs + Hs)};
-
-        const double r2 = quad_sum(fc * fc);
-        double cn2 = 1.0;   // product of the squared column norms
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cn2 *= quad_sum(m[j] * m[j]);
-        int fin = isfinite(fc) && isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) &&
-                  isfinite(m[3]);
-        fin &= __shfl_xor_sync(kFull, fin, 1);
-        fin &= __shfl_xor_sync(kFull, fin, 2);
-
-        // ---- Df dx = f by partial-pivot elimination over the quad's rows
-        double rr = fc, det = 1.0, ip[4];
-        int used = 0, pl[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            double cand = ((used >> c) & 1) ? -1.0 : fabs(m[j]);
-            int bl = c;
-#pragma unroll
-            for (int off = 1; off <= 2; off <<= 1) {
-                const double oc = __shfl_xor_sync(kFull, cand, off);
-                const int ol = __shfl_xor_sync(kFull, bl, off);
-                if (oc > cand || (oc == cand && ol < bl)) {
-                    cand = oc;
-                    bl = ol;
-                }
-            }
-            used |= 1 << bl;
-            pl[j] = bl;
-            double pj[4];
-#pragma unroll
-            for (int q = j; q < 4; ++q) pj[q] = lane_val(m[q], base, bl);
-            const double prr = lane_val(rr, base, bl);
-            det *= pj[j];
-            ip[j] = pj[j] != 0.0 ? 1.0 / pj[j] : 0.0;
-            if (!((used >> c) & 1)) {
-                const double fct = m[j] * ip[j];
-#pragma unroll
-                for (int q = j + 1; q < 4; ++q) m[q] -= fct * pj[q];
-                rr -= fct * prr;
-                m[j] = 0.0;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int w = u + 1; w < 4; ++w)
-                if (pl[u] > pl[w]) det = -det;
-        double dx[4];
-#pragma unroll
-        for (int j = 3; j >= 0; --j) {
-            double v = rr;
-#pragma unroll
-            for (int q = j + 1; q < 4; ++q) v -= m[q] * dx[q];
-            dx[j] = lane_val(v * ip[j], base, pl[j]);
-        }
-
-        // ---- decision on the quad's first lane, then the update
-        // ||f|| <= tol as ||f||^2 <= tol^2; |det| / prod ||col|| >= rho_min as
-        // |det| >= rho_min sqrt(prod ||col||^2)
-        int dec = pre;
-        if (dec < 0) {
-            if (!fin) dec = TMS_REFINE_NON_FINITE;
-            else if (r2 <= tol2) dec = TMS_REFINE_CONVERGED;
-            else if (k == pr.max_iter) dec = TMS_REFINE_MAX_ITER;
-            else if (!(fabs(det) >= pr.rho_min * sqrt(cn2))) dec = TMS_REFINE_SINGULAR;
-        }
-        dec = __shfl_sync(kFull, dec, base);
-        if (code < 0) {
-            if (pre < 0) {
-                fn = r2;
-                rh = det;
-                rc2 = cn2;
-            }
-            if (dec >= 0) {
-                code = dec;
-                iters = k;
-            } else {
-                const double al = r2 > sw2 ? pr.alpha0 : pr.alpha1;
-                x0 -= al * dx[0];
-                x1 -= al * dx[1];
-                x2 -= al * dx[2];
-                x3 -= al * dx[3];
+        for (int f = 0; f < kF; ++f) {
+            if (f < NF) {
+                const double w = cf.fd[f][c];
+                FA = fma(w, lane_val(p, base, f), FA);
+                FA1 = fma(w, lane_val(p1, base, f), FA1);
+                FB = fma(w, lane_val(q, base, f), FB);
+                FB1 = fma(w, lane_val(q1, base, f), FB1);
+                FB2 = fma(w, lane_val(q2, base, f), FB2);
             }
         }
     }
-    S.x0 = x0;
-    S.x1 = x1;
-    S.x2 = x2;
-    S.x3 = x3;
-    S.code = code;
-    S.iters = iters;
-    S.fn = fn;
-    S.rh = rh;
-    S.rc2 = rc2;
+
+    // ---- harmonic sums: T, T' at theta_u (alpha_u); T, T' at theta' (alpha_s);
+    //      T, T', T'' at theta' (alpha_ref).  cos/sin of k theta by angle addition.
+    double TA = 0.0, TAt = 0.0, TB = 0.0, TBt = 0.0, TR = 0.0, TRt = 0.0, TRtt = 0.0;
+    double ckA = cA, skA = sA, ckB = cB, skB = sB;
+#pragma unroll
+    for (int h = 0; h < kH; ++h) {
+        if (h < K) {
+            double uak = cf.uak[h][c], ubk = cf.ubk[h][c], una = cf.una[h][c], ub = cf.ub[h][c];
+            double sak = cf.sak[h][c], sbk = cf.sbk[h][c], sna = cf.sna[h][c], sb = cf.sb[h][c];
+            if (WALK == 1) {
+                uak = fma(aw, cf.dak[h][c], uak);
+                ubk = fma(aw, cf.dbk[h][c], ubk);
+                una = fma(aw, cf.dna[h][c], una);
+                ub = fma(aw, cf.db[h][c], ub);
+            } else if (WALK == 2) {
+                sak = fma(aw, cf.dak[h][c], sak);
+                sbk = fma(aw, cf.dbk[h][c], sbk);
+                sna = fma(aw, cf.dna[h][c], sna);
+                sb = fma(aw, cf.db[h][c], sb);
+            }
+            TA = fma(uak, ckA, fma(ubk, skA, TA));
+            TAt = fma(ub, ckA, fma(una, skA, TAt));
+            TB = fma(sak, ckB, fma(sbk, skB, TB));
+            TBt = fma(sb, ckB, fma(sna, skB, TBt));
+            TR = fma(cf.ark[h][c], ckB, fma(cf.brk[h][c], skB, TR));
+            TRt = fma(cf.br[h][c], ckB, fma(cf.nar[h][c], skB, TRt));
+            TRtt = fma(cf.kar[h][c], ckB, fma(cf.kbr[h][c], skB, TRtt));
+            if (h + 1 < K) {
+                const double nA = ckA * cA - skA * sA;
+                skA = skA * cA + ckA * sA;
+                ckA = nA;
+                const double nB = ckB * cB - skB * sB;
+                skB = skB * cB + ckB * sB;
+                ckB = nB;
+            }
+        }
+    }
+
+    // ---- W_A and its partials; B's underlying sheet; the frame sheet
+    const double WA = gA * TA + FA, WAt = gA * TAt, WAs = gA1 * TA + FA1;
+    const double SB = gB * TB + FB, SBt = gB * TBt, SBs = gB1 * TB + FB1;
+    const double t1 = gB * TRt, t2 = gB1 * TR + FB1;
+    const double Wtt = gB * TRtt, Wts = gB1 * TRt, Wss = gB2 * TR + FB2;
+    const double v1 = cf.v1[c], v2 = cf.v2[c];
+
+    // ---- normal frame (n1, n2) and its theta- and s-partials
+    const double g11 = quad_sum(t1 * t1), g12 = quad_sum(t1 * t2), g22 = quad_sum(t2 * t2);
+    const double j11 = quad_sum(t1 * v1), j21 = quad_sum(t2 * v1);
+    const double j12 = quad_sum(t1 * v2), j22 = quad_sum(t2 * v2);
+    const double P1 = quad_sum(t1 * Wtt), P2 = quad_sum(t1 * Wts), P3 = quad_sum(Wtt * t2);
+    const double P4 = quad_sum(t2 * Wts), P5 = quad_sum(t1 * Wss), P6 = quad_sum(t2 * Wss);
+    const double Lt1 = quad_sum(Wtt * v1), Ls1 = quad_sum(Wts * v1), Ss1 = quad_sum(Wss * v1);
+    const double Lt2 = quad_sum(Wtt * v2), Ls2 = quad_sum(Wts * v2), Ss2 = quad_sum(Wss * v2);
+    const double eps = sp.reg * 0.5 * (g11 + g22);
+    const double G11 = g11 + eps, G12 = g12, G22 = g22 + eps;
+    const double idet = 1.0 / (G11 * G22 - G12 * G12);
+    // d/dtheta and d/ds of G (J^T J + eps I)
+    const double tg11 = 2.0 * P1, tg12 = P2 + P3, tg22 = 2.0 * P4;
+    const double te = sp.reg * 0.5 * (tg11 + tg22);
+    const double tG11 = tg11 + te, tG22 = tg22 + te;
+    const double sg11 = -2.0 * P2, sg12 = -(P5 + P4), sg22 = -2.0 * P6;
+    const double se = sp.reg * 0.5 * (sg11 + sg22);
+    const double sG11 = sg11 + se, sG22 = sg22 + se;
+
+    // lane c solves for frame vector r = c & 1, then both are shared
+    double yv[6];
+    {
+        const int r = c & 1;
+        const double j1 = r ? j12 : j11, j2 = r ? j22 : j21;
+        const double Lt = r ? Lt2 : Lt1, Ls = r ? Ls2 : Ls1, Ss = r ? Ss2 : Ss1;
+        const double y1 = (G22 * j1 - G12 * j2) * idet, y2 = (G11 * j2 - G12 * j1) * idet;
+        // theta: d t1 = Wtt, d t2 = Wts;  s: d t1 = -Wts, d t2 = -Wss
+        const double a1 = Lt - (tG11 * y1 + tg12 * y2), a2 = Ls - (tg12 * y1 + tG22 * y2);
+        const double b1 = -Ls - (sG11 * y1 + sg12 * y2), b2 = -Ss - (sg12 * y1 + sG22 * y2);
+        yv[0] = y1;
+        yv[1] = y2;
+        yv[2] = (G22 * a1 - G12 * a2) * idet;
+        yv[3] = (G11 * a2 - G12 * a1) * idet;
+        yv[4] = (G22 * b1 - G12 * b2) * idet;
+        yv[5] = (G11 * b2 - G12 * b1) * idet;
+    }
+    double n[2], nt[2], ns[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const double v = r == 0 ? v1 : v2;
+        const double y1 = lane_val(yv[0], base, r), y2 = lane_val(yv[1], base, r);
+        const double dt1 = lane_val(yv[2], base, r), dt2 = lane_val(yv[3], base, r);
+        const double ds1 = lane_val(yv[4], base, r), ds2 = lane_val(yv[5], base, r);
+        n[r] = v - t1 * y1 - t2 * y2;
+        nt[r] = -(Wtt * y1 + Wts * y2) - (t1 * dt1 + t2 * dt2);
+        ns[r] = (Wts * y1 + Wss * y2) - (t1 * ds1 + t2 * ds2);
+    }
+
+    // ---- W_B, f and the row of Df this lane owns
+    const double h = sp.h_amp;
+    const double H = h * (sh1 * n[0] + sh2 * n[1]);
+    const double Ht = h * (sp.P * ch1 * n[0] + sh1 * nt[0] + sh2 * nt[1]);
+    const double Hs = h * (sh1 * ns[0] + sp.Q * kPi * ch2 * n[1] + sh2 * ns[1]);
+    const double fc = WA - (SB + H);
+    double m[4] = {WAt, WAs, -(SBt + Ht), -(-SBs + Hs)};
+
+    const double r2 = quad_sum(fc * fc);
+    double cn2 = 1.0;   // product of the squared column norms
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cn2 *= quad_sum(m[j] * m[j]);
+    int fin = isfinite(fc) && isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) &&
+              isfinite(m[3]);
+    fin &= __shfl_xor_sync(kFull, fin, 1);
+    fin &= __shfl_xor_sync(kFull, fin, 2);
+
+    // ---- Df dx = f by partial-pivot elimination over the quad's rows
+    double rr = fc, det = 1.0, ip[4];
+    int used = 0, pl[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        double cand = ((used >> c) & 1) ? -1.0 : fabs(m[j]);
+        int bl = c;
+#pragma unroll
+        for (int off = 1; off <= 2; off <<= 1) {
+            const double oc = __shfl_xor_sync(kFull, cand, off);
+            const int ol = __shfl_xor_sync(kFull, bl, off);
+            if (oc > cand || (oc == cand && ol < bl)) {
+                cand = oc;
+                bl = ol;
+            }
+        }
+        used |= 1 << bl;
+        pl[j] = bl;
+        double pj[4];
+#pragma unroll
+        for (int q = j; q < 4; ++q) pj[q] = lane_val(m[q], base, bl);
+        const double prr = lane_val(rr, base, bl);
+        det *= pj[j];
+        ip[j] = pj[j] != 0.0 ? 1.0 / pj[j] : 0.0;
+        if (!((used >> c) & 1)) {
+            const double fct = m[j] * ip[j];
+#pragma unroll
+            for (int q = j + 1; q < 4; ++q) m[q] -= fct * pj[q];
+            rr -= fct * prr;
+            m[j] = 0.0;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = u + 1; w < 4; ++w)
+            if (pl[u] > pl[w]) det = -det;
+    double dx[4];
+#pragma unroll
+    for (int j = 3; j >= 0; --j) {
+        double v = rr;
+#pragma unroll
+        for (int q = j + 1; q < 4; ++q) v -= m[q] * dx[q];
+        dx[j] = lane_val(v * ip[j], base, pl[j]);
+    }
+
+    E.pre = pre;
+    E.fin = fin;
+    E.r2 = r2;
+    E.cn2 = cn2;
+    E.det = det;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) E.dx[q] = dx[q];
+}
+
+// The decision of Eq. (dampedNewtonEquation)'s iteration k from an evaluation:
+// -1 to update, else the stop status (taken on the quad's first lane).
+__device__ __forceinline__ int decide(const Eval &E, const tms_refine_params &pr, int k, int base) {
+    // ||f|| <= tol as ||f||^2 <= tol^2; |det| / prod ||col|| >= rho_min as
+    // |det| >= rho_min sqrt(prod ||col||^2)
+    int dec = E.pre;
+    if (dec < 0) {
+        if (!E.fin) dec = TMS_REFINE_NON_FINITE;
+        else if (E.r2 <= pr.tol * pr.tol) dec = TMS_REFINE_CONVERGED;
+        else if (k == pr.max_iter) dec = TMS_REFINE_MAX_ITER;
+        else if (!(fabs(E.det) >= pr.rho_min * sqrt(E.cn2))) dec = TMS_REFINE_SINGULAR;
+    }
+    return __shfl_sync(kFull, dec, base);
+}
+
+// Applies a decision to a quad that is still iterating.
+__device__ __forceinline__ void apply(const Eval &E, const tms_refine_params &pr, int dec, int k,
+                                      Solve &S) {
+    if (S.code >= 0) return;
+    if (E.pre < 0) {
+        S.fn = E.r2;
+        S.rh = E.det;
+        S.rc2 = E.cn2;
+    }
+    if (dec >= 0) {
+        S.code = dec;
+        S.iters = k;
+    } else {
+        const double sw2 = pr.switch_below * pr.switch_below;
+        const double al = E.r2 > sw2 ? pr.alpha0 : pr.alpha1;
+        S.x0 -= al * E.dx[0];
+        S.x1 -= al * E.dx[1];
+        S.x2 -= al * E.dx[2];
+        S.x3 -= al * E.dx[3];
+        S.k = k + 1;
+    }
+}
+
+// The whole solve for every quad of the warp at once (the refinement): the
+// iteration counter is the warp's; at most max_iter + 1 evaluations each.
+__device__ __forceinline__ void newton_solve(const Coef &cf, const tms_surface_pair &sp,
+                                             const tms_refine_params &pr, Solve &S, int c,
+                                             int base) {
+    const double lnlam = sp.stretch ? log(sp.lam) : 0.0;
+    for (int k = 0; __any_sync(kFull, S.code < 0); ++k) {
+        Eval E;
+        evaluate<0>(cf, sp, pr, lnlam, S.x0, S.x1, S.x2, S.x3, 0.0, c, base, E);
+        apply(E, pr, decide(E, pr, k, base), k, S);
+    }
+}
+
+// One iteration for each quad at its own count S.k (the continuation).
+template <int WALK>
+__device__ __forceinline__ void newton_iter(const Coef &cf, const tms_surface_pair &sp,
+                                            const tms_refine_params &pr, double lnlam, Solve &S,
+                                            double aw, int c, int base) {
+    Eval E;
+    evaluate<WALK>(cf, sp, pr, lnlam, S.x0, S.x1, S.x2, S.x3, aw, c, base, E);
+    apply(E, pr, decide(E, pr, S.k, base), S.k, S);
 }
 
 __device__ __forceinline__ double wrap_angle(double v) {
@@ -404,7 +462,7 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
     __shared__ Coef cf;
     const tms_surface_pair &sp = a.sp;
     const int t = threadIdx.x;
-    build_tables(cf, sp, sp.alpha_u, sp.alpha_s, t, kThreads);
+    build_tables(cf, sp, sp.alpha_u, sp.alpha_s, 0, t, kThreads);
     __syncthreads();
 
     const int lane = t & 31;
@@ -426,6 +484,7 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
     }
     S.code = live ? -1 : TMS_REFINE_CONVERGED;
     S.iters = 0;
+    S.k = 0;
     S.fn = nan_value();
     S.rh = S.fn;
     S.rc2 = 1.0;
@@ -445,60 +504,105 @@ __global__ void __launch_bounds__(kThreads) k_refine(const __grid_constant__ Ref
 }
 
 // Continuation (Sec. 8): one quad per branch walks the parameter values
-// alpha_0 (the pair's own), alphas[0..steps).  Each warp owns a copy of the
-// tables and rebuilds it for every step between two warp barriers, so the
-// warps of a block step independently; a warp whose eight branches have all
-// stopped writes their remaining steps and leaves.
+// alpha_0 (the pair's own), alphas[0..steps) of the walking sheet (WALK = 1:
+// W_A's alpha_u, 2: B's alpha_s).  The branches of a warp do not wait for one
+// another between steps: each quad evaluates its sheet at its own current
+// parameter (the coefficients are affine in it), and when its corrector stops
+// it records the step and, unless the branch stopped, predicts the next step
+// and goes on in the same warp-wide iteration loop, which ends when all of the
+// warp's branches have.
+template <int WALK>
 __global__ void __launch_bounds__(kThreads) k_continue(const __grid_constant__ ContArgs a) {
-    __shared__ Coef cfw[kThreads / 32];
-    Coef &cf = cfw[threadIdx.x >> 5];
+    __shared__ Coef cf;
     const tms_surface_pair &sp = a.sp;
     const tms_continue_params &cp = a.p;
     const int t = threadIdx.x;
+    build_tables(cf, sp, WALK == 1 ? 0.0 : sp.alpha_u, WALK == 2 ? 0.0 : sp.alpha_s, WALK, t,
+                 kThreads);
+    __syncthreads();
     const int lane = t & 31;
     const int c = lane & 3;
     const int base = lane & ~3;
     const long long i = (long long)blockIdx.x * kSeedsPerBlock + (t >> 2);
     const bool live = i < a.n;
-    double x[4] = {0.0, 0.5, 0.0, 0.5};
+    double g[4] = {0.0, 0.5, 0.0, 0.5};   // the current step's starting point
     if (live) {
         const double *s = a.x0 + i * a.ld;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) x[q] = s[q];
+        for (int q = 0; q < 4; ++q) g[q] = s[q];
     }
     double p1[4] = {0.0, 0.0, 0.0, 0.0}, p2[4] = {0.0, 0.0, 0.0, 0.0};   // x_{j-1}, x_{j-2}
     bool alive = live;
+    int j = 0;
     double rho_prev = nan_value();
-    const double a0 = cp.param == 0 ? sp.alpha_u : sp.alpha_s;
-    double am1 = a0, am2 = a0;   // alpha_{j-1}, alpha_{j-2}
+    const double a0 = WALK == 1 ? sp.alpha_u : sp.alpha_s;
+    double aj = a0, am1 = a0, am2 = a0;   // alpha_j, alpha_{j-1}, alpha_{j-2}
     const long long K1 = (long long)a.steps + 1;
-    for (int j = 0; j <= a.steps; ++j) {
-        if (!__any_sync(kFull, alive)) {
-            if (live) {
-                for (int r = j; r <= a.steps; ++r) {
-                    const long long o = i * K1 + r;
-                    a.x[o * 4 + c] = nan_value();
-                    if (c == 0) {
-                        a.status[o] = TMS_CONT_STOPPED;
-                        if (a.iters) a.iters[o] = 0;
-                        if (a.rho) a.rho[o] = nan_value();
-                        if (a.fnorm) a.fnorm[o] = nan_value();
-                    }
+    Solve S;
+    S.x0 = g[0];
+    S.x1 = g[1];
+    S.x2 = g[2];
+    S.x3 = g[3];
+    S.code = alive ? -1 : TMS_REFINE_CONVERGED;
+    S.iters = 0;
+    S.k = 0;
+    S.fn = nan_value();
+    S.rh = S.fn;
+    S.rc2 = 1.0;
+    const double lnlam = sp.stretch ? log(sp.lam) : 0.0;
+    while (__any_sync(kFull, alive)) {
+        newton_iter<WALK>(cf, sp, cp.corrector, lnlam, S, aj, c, base);
+        if (!(alive && S.code >= 0)) continue;
+        // ---- step j is done (identical on the quad's lanes; no shuffles below)
+        const double xs[4] = {wrap_angle(S.x0), S.x1, wrap_angle(S.x2), S.x3};
+        const double rho = S.rh / sqrt(S.rc2);
+        int st = S.code;
+        if (st == TMS_REFINE_CONVERGED) {
+            double jump = 0.0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double d = fabs(xs[q] - g[q]);
+                if (q == 0 || q == 2) d = fabs(d - kTwoPi * rint(d / kTwoPi));
+                jump = fmax(jump, d);
+            }
+            if (!(jump <= cp.max_jump)) st = TMS_CONT_JUMPED;
+            else if (!(fabs(rho) >= cp.rho_turn)) st = TMS_CONT_TURNING;
+            else if (j > 0 && (rho > 0.0) != (rho_prev > 0.0)) st = TMS_CONT_TURNING;
+        }
+        const long long o = i * K1 + j;
+        a.x[o * 4 + c] = xs[c];
+        if (c == 0) {
+            a.status[o] = st;
+            if (a.iters) a.iters[o] = S.iters;
+            if (a.rho) a.rho[o] = rho;
+            if (a.fnorm) a.fnorm[o] = sqrt(S.fn);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            p2[q] = p1[q];
+            p1[q] = xs[q];
+        }
+        rho_prev = rho;
+        if (st != TMS_REFINE_CONVERGED || j == a.steps) {
+            alive = false;
+            for (long long r = j + 1; r <= a.steps; ++r) {
+                const long long oo = i * K1 + r;
+                a.x[oo * 4 + c] = nan_value();
+                if (c == 0) {
+                    a.status[oo] = TMS_CONT_STOPPED;
+                    if (a.iters) a.iters[oo] = 0;
+                    if (a.rho) a.rho[oo] = nan_value();
+                    if (a.fnorm) a.fnorm[oo] = nan_value();
                 }
             }
-            break;
+            continue;
         }
-        const double aj = j == 0 ? a0 : a.alphas[j - 1];
-        __syncwarp();
-        build_tables(cf, sp, cp.param == 0 ? aj : sp.alpha_u, cp.param == 0 ? sp.alpha_s : aj,
-                     lane, 32);
-        __syncwarp();
-        // predictor, Eq. (predictor); angle differences taken on the circle
-        double g[4];
-        if (j == 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) g[q] = x[q];
-        } else if (j == 1) {
+        // ---- next step: predictor, Eq. (predictor); angle differences on the circle
+        ++j;
+        am2 = am1;
+        am1 = aj;
+        aj = a.alphas[j - 1];
+        if (j == 1) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) g[q] = p1[q];
         } else {
@@ -510,59 +614,16 @@ __global__ void __launch_bounds__(kThreads) k_continue(const __grid_constant__ C
                 g[q] = p1[q] + ratio * d;
             }
         }
-        Solve S;
         S.x0 = g[0];
         S.x1 = g[1];
         S.x2 = g[2];
         S.x3 = g[3];
-        S.code = alive ? -1 : TMS_REFINE_CONVERGED;
+        S.code = -1;
         S.iters = 0;
+        S.k = 0;
         S.fn = nan_value();
         S.rh = S.fn;
         S.rc2 = 1.0;
-        newton_solve(cf, sp, cp.corrector, S, c, base);
-        const long long o = i * K1 + j;
-        if (alive) {
-            const double xs[4] = {wrap_angle(S.x0), S.x1, wrap_angle(S.x2), S.x3};
-            const double rho = S.rh / sqrt(S.rc2);
-            int st = S.code;
-            if (st == TMS_REFINE_CONVERGED) {
-                double jump = 0.0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    double d = fabs(xs[q] - g[q]);
-                    if (q == 0 || q == 2) d = fabs(d - kTwoPi * rint(d / kTwoPi));
-                    jump = fmax(jump, d);
-                }
-                if (!(jump <= cp.max_jump)) st = TMS_CONT_JUMPED;
-                else if (!(fabs(rho) >= cp.rho_turn)) st = TMS_CONT_TURNING;
-                else if (j > 0 && (rho > 0.0) != (rho_prev > 0.0)) st = TMS_CONT_TURNING;
-            }
-            a.x[o * 4 + c] = xs[c];
-            if (c == 0) {
-                a.status[o] = st;
-                if (a.iters) a.iters[o] = S.iters;
-                if (a.rho) a.rho[o] = rho;
-                if (a.fnorm) a.fnorm[o] = sqrt(S.fn);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                p2[q] = p1[q];
-                p1[q] = xs[q];
-            }
-            rho_prev = rho;
-            if (st != TMS_REFINE_CONVERGED) alive = false;
-        } else if (live) {
-            a.x[o * 4 + c] = nan_value();
-            if (c == 0) {
-                a.status[o] = TMS_CONT_STOPPED;
-                if (a.iters) a.iters[o] = 0;
-                if (a.rho) a.rho[o] = nan_value();
-                if (a.fnorm) a.fnorm[o] = nan_value();
-            }
-        }
-        am2 = am1;
-        am1 = aj;
     }
 }
 
@@ -724,7 +785,8 @@ extern "C" tms_status tms_continue(const tms_surface_pair *surf, const tms_conti
     a.fnorm = dFnorm;
     const long long blocks = (n + kSeedsPerBlock - 1) / kSeedsPerBlock;
     if (blocks > 0x7fffffffLL) return arg_error("tms_continue: too many branches");
-    k_continue<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(a);
+    if (p.param == 0) k_continue<1><<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(a);
+    else k_continue<2><<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(a);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         tms::set_last_error(std::string("tms_continue launch: ") + cudaGetErrorString(e));
