@@ -77,6 +77,7 @@ struct Coef {
     double fd[kF][4];               // fold_amp * fold_dir
     double root[kF][3];             // fold roots
     double v1[4], v2[4];
+    double qpi, hreg;               // Q pi and reg / 2
 };
 
 // Fills the tables for (alpha_u, alpha_s) and, for a walking sheet (walk != 0),
@@ -118,6 +119,10 @@ __device__ void build_tables(Coef &cf, const tms_surface_pair &sp, double au, do
     if (t < 4) {
         cf.v1[t] = sp.v1[t];
         cf.v2[t] = sp.v2[t];
+    }
+    if (t == 0) {
+        cf.qpi = sp.Q * kPi;
+        cf.hreg = sp.reg * 0.5;
     }
 }
 
@@ -179,7 +184,7 @@ __device__ __forceinline__ void evaluate(const Coef &cf, const tms_surface_pair 
     const double arg = c == 0 ? x0
                      : c == 1 ? x2 + sp.c0
                      : c == 2 ? sp.P * (x2 - sp.theta0)
-                              : sp.Q * kPi * (x3 - sp.s0);
+                              : cf.qpi * (x3 - sp.s0);
     double sn, cs;
     sincos(arg, &sn, &cs);
     const double sA = lane_val(sn, base, 0), cA = lane_val(cs, base, 0);
@@ -276,15 +281,15 @@ __device__ __forceinline__ void evaluate(const Coef &cf, const tms_surface_pair 
     const double P4 = quad_sum(t2 * Wts), P5 = quad_sum(t1 * Wss), P6 = quad_sum(t2 * Wss);
     const double Lt1 = quad_sum(Wtt * v1), Ls1 = quad_sum(Wts * v1), Ss1 = quad_sum(Wss * v1);
     const double Lt2 = quad_sum(Wtt * v2), Ls2 = quad_sum(Wts * v2), Ss2 = quad_sum(Wss * v2);
-    const double eps = sp.reg * 0.5 * (g11 + g22);
+    const double eps = cf.hreg * (g11 + g22);
     const double G11 = g11 + eps, G12 = g12, G22 = g22 + eps;
     const double idet = 1.0 / (G11 * G22 - G12 * G12);
     // d/dtheta and d/ds of G (J^T J + eps I)
     const double tg11 = 2.0 * P1, tg12 = P2 + P3, tg22 = 2.0 * P4;
-    const double te = sp.reg * 0.5 * (tg11 + tg22);
+    const double te = cf.hreg * (tg11 + tg22);
     const double tG11 = tg11 + te, tG22 = tg22 + te;
     const double sg11 = -2.0 * P2, sg12 = -(P5 + P4), sg22 = -2.0 * P6;
-    const double se = sp.reg * 0.5 * (sg11 + sg22);
+    const double se = cf.hreg * (sg11 + sg22);
     const double sG11 = sg11 + se, sG22 = sg22 + se;
 
     // lane c solves for frame vector r = c & 1, then both are shared
@@ -320,7 +325,7 @@ __device__ __forceinline__ void evaluate(const Coef &cf, const tms_surface_pair 
     const double h = sp.h_amp;
     const double H = h * (sh1 * n[0] + sh2 * n[1]);
     const double Ht = h * (sp.P * ch1 * n[0] + sh1 * nt[0] + sh2 * nt[1]);
-    const double Hs = h * (sh1 * ns[0] + sp.Q * kPi * ch2 * n[1] + sh2 * ns[1]);
+    const double Hs = h * (sh1 * ns[0] + cf.qpi * ch2 * n[1] + sh2 * ns[1]);
     const double fc = WA - (SB + H);
     double m[4] = {WAt, WAs, -(SBt + Ht), -(-SBs + Hs)};
 
@@ -390,13 +395,14 @@ __device__ __forceinline__ void evaluate(const Coef &cf, const tms_surface_pair 
 
 // The decision of Eq. (dampedNewtonEquation)'s iteration k from an evaluation:
 // -1 to update, else the stop status (taken on the quad's first lane).
-__device__ __forceinline__ int decide(const Eval &E, const tms_refine_params &pr, int k, int base) {
+__device__ __forceinline__ int decide(const Eval &E, const tms_refine_params &pr, double tol2, int k,
+                                      int base) {
     // ||f|| <= tol as ||f||^2 <= tol^2; |det| / prod ||col|| >= rho_min as
     // |det| >= rho_min sqrt(prod ||col||^2)
     int dec = E.pre;
     if (dec < 0) {
         if (!E.fin) dec = TMS_REFINE_NON_FINITE;
-        else if (E.r2 <= pr.tol * pr.tol) dec = TMS_REFINE_CONVERGED;
+        else if (E.r2 <= tol2) dec = TMS_REFINE_CONVERGED;
         else if (k == pr.max_iter) dec = TMS_REFINE_MAX_ITER;
         else if (!(fabs(E.det) >= pr.rho_min * sqrt(E.cn2))) dec = TMS_REFINE_SINGULAR;
     }
@@ -404,8 +410,8 @@ __device__ __forceinline__ int decide(const Eval &E, const tms_refine_params &pr
 }
 
 // Applies a decision to a quad that is still iterating.
-__device__ __forceinline__ void apply(const Eval &E, const tms_refine_params &pr, int dec, int k,
-                                      Solve &S) {
+__device__ __forceinline__ void apply(const Eval &E, const tms_refine_params &pr, double sw2, int dec,
+                                      int k, Solve &S) {
     if (S.code >= 0) return;
     if (E.pre < 0) {
         S.fn = E.r2;
@@ -416,7 +422,6 @@ __device__ __forceinline__ void apply(const Eval &E, const tms_refine_params &pr
         S.code = dec;
         S.iters = k;
     } else {
-        const double sw2 = pr.switch_below * pr.switch_below;
         const double al = E.r2 > sw2 ? pr.alpha0 : pr.alpha1;
         S.x0 -= al * E.dx[0];
         S.x1 -= al * E.dx[1];
@@ -432,21 +437,22 @@ __device__ __forceinline__ void newton_solve(const Coef &cf, const tms_surface_p
                                              const tms_refine_params &pr, Solve &S, int c,
                                              int base) {
     const double lnlam = sp.stretch ? log(sp.lam) : 0.0;
+    const double tol2 = pr.tol * pr.tol, sw2 = pr.switch_below * pr.switch_below;
     for (int k = 0; __any_sync(kFull, S.code < 0); ++k) {
         Eval E;
         evaluate<0>(cf, sp, pr, lnlam, S.x0, S.x1, S.x2, S.x3, 0.0, c, base, E);
-        apply(E, pr, decide(E, pr, k, base), k, S);
+        apply(E, pr, sw2, decide(E, pr, tol2, k, base), k, S);
     }
 }
 
 // One iteration for each quad at its own count S.k (the continuation).
 template <int WALK>
 __device__ __forceinline__ void newton_iter(const Coef &cf, const tms_surface_pair &sp,
-                                            const tms_refine_params &pr, double lnlam, Solve &S,
-                                            double aw, int c, int base) {
+                                            const tms_refine_params &pr, double lnlam, double tol2,
+                                            double sw2, Solve &S, double aw, int c, int base) {
     Eval E;
     evaluate<WALK>(cf, sp, pr, lnlam, S.x0, S.x1, S.x2, S.x3, aw, c, base, E);
-    apply(E, pr, decide(E, pr, S.k, base), S.k, S);
+    apply(E, pr, sw2, decide(E, pr, tol2, S.k, base), S.k, S);
 }
 
 __device__ __forceinline__ double wrap_angle(double v) {
@@ -550,8 +556,10 @@ __global__ void __launch_bounds__(kThreads) k_continue(const __grid_constant__ C
     S.rh = S.fn;
     S.rc2 = 1.0;
     const double lnlam = sp.stretch ? log(sp.lam) : 0.0;
+    const double tol2 = cp.corrector.tol * cp.corrector.tol;
+    const double sw2 = cp.corrector.switch_below * cp.corrector.switch_below;
     while (__any_sync(kFull, alive)) {
-        newton_iter<WALK>(cf, sp, cp.corrector, lnlam, S, aj, c, base);
+        newton_iter<WALK>(cf, sp, cp.corrector, lnlam, tol2, sw2, S, aj, c, base);
         if (!(alive && S.code >= 0)) continue;
         // ---- step j is done (identical on the quad's lanes; no shuffles below)
         const double xs[4] = {wrap_angle(S.x0), S.x1, wrap_angle(S.x2), S.x3};
