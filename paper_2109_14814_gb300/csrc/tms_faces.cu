@@ -320,7 +320,28 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
     const int t = threadIdx.x;
     const bool col_valid = t < cols_q;
     const int i = i0 + t;
-    if (col_valid) {
+    if (FACE == 1 && col_valid) {
+        // quad faces: the extremes of the two vertex columns of each row once, each
+        // quad box from two consecutive rows (exact: min and max only)
+        BoxT<PREC> prev;
+        box_init(prev, sv[t]);
+        box_add(prev, sv[t + 1]);
+        for (int r = 0; r < rows_q; ++r) {
+            BoxT<PREC> next;
+            box_init(next, sv[(r + 1) * W + t]);
+            box_add(next, sv[(r + 1) * W + t + 1]);
+            BoxT<PREC> bq;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                bq.lo[d] = min(prev.lo[d], next.lo[d]);
+                bq.hi[d] = max(prev.hi[d], next.hi[d]);
+            }
+            const uint32_t q = (uint32_t)(kq0 + r) * (uint32_t)m.N + (uint32_t)i;
+            acc.add(bq);
+            write_fbox<PREC>(m, q, bq);
+            prev = next;
+        }
+    } else if (col_valid) {
         for (int r = 0; r < rows_q; ++r) {
             const int k = kq0 + r;
             const Vtx<PREC> va = sv[r * W + t];             // (i, k)
