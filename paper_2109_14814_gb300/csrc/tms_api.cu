@@ -84,12 +84,6 @@ struct Plan {
     Grid *h_grid0 = nullptr;
     uint32_t *bmA = nullptr, *bmH = nullptr;
     int bmA_bits = 0, bmH_bits = 0;
-    // the occupancy bitmaps and the cell table, read and written at random by the
-    // cell passes and the grouping: one allocation, kept in L2 by a persisting
-    // access-policy window on the plan's stream (the streams of vertices, boxes
-    // and entries around them would otherwise evict it)
-    unsigned char *hot = nullptr;
-    size_t hot_bytes = 0;
     unsigned long long ent_cap = 0, cand_cap = 0, hit_cap = 0;
     uint64_t *ek = nullptr;
     uint32_t *ev = nullptr, *eslot = nullptr, *erank = nullptr, *grouped = nullptr;
@@ -123,13 +117,11 @@ struct Plan {
     unsigned long long last_use = 0;
 
     void free_scratch() {
-        void *ptrs[] = {hot, ek, ev, eslot, erank, grouped, crec,
+        void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, crec, tcnt, tstart,
                         sort_scratch, cand, surv, hits, hk, hk2, okeys, hv, hv2,
                         keep, kscan};
         for (void *p : ptrs)
             if (p) cudaFree(p);
-        hot = nullptr;
-        hot_bytes = 0;
         bmA = bmH = nullptr; ek = nullptr; ev = eslot = erank = grouped = nullptr;
         tkey = nullptr; crec = nullptr; tcnt = nullptr; tstart = nullptr;
         sort_scratch = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
@@ -152,35 +144,10 @@ struct Plan {
         if (st) cudaStreamDestroy(st);
     }
 
-    // Marks `hot` persisting in L2 for the plan's stream (the graph captured on it
-    // keeps the window).  The budget is this process's own limit; a device or
-    // driver that offers none leaves the search as it was.
-    void keep_hot_in_l2() {
-        int max_persist = 0, max_window = 0;
-        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, device);
-        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, device);
-        if (max_persist <= 0 || max_window <= 0 || !hot) return;
-        size_t limit = 0;
-        cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize);
-        const size_t want = std::min((size_t)max_persist, hot_bytes);
-        if (limit < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess)
-            limit = want;
-        cudaGetLastError();
-        if (limit == 0) return;
-        cudaStreamAttrValue v;
-        memset(&v, 0, sizeof(v));
-        v.accessPolicyWindow.base_ptr = hot;
-        v.accessPolicyWindow.num_bytes = std::min(hot_bytes, (size_t)max_window);
-        v.accessPolicyWindow.hitRatio =
-            (float)std::min(1.0, (double)limit / (double)v.accessPolicyWindow.num_bytes);
-        v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-        v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-        cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v);
-        cudaGetLastError();
-    }
-
     tms_status alloc_scratch() {
         free_scratch();
+        TMS_CK(dalloc(&bmA, (size_t)1 << (bmA_bits)));
+        TMS_CK(dalloc(&bmH, (size_t)1 << (bmH_bits)));
         TMS_CK(dalloc(&ek, ent_cap));
         TMS_CK(dalloc(&ev, ent_cap));
         TMS_CK(dalloc(&eslot, ent_cap));
@@ -192,24 +159,9 @@ struct Plan {
         tsize = 1024;
         const unsigned long long want = (prm.inject & 8u) ? 0 : ent_cap / 16;
         while ((tsize < want || tsize < tsize_min) && tsize < (1ULL << 31)) tsize <<= 1;
-        // bitmaps and table in one allocation (see `hot`)
-        auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-        const size_t ba = ((size_t)1 << bmA_bits) * sizeof(uint32_t);
-        const size_t bh = ((size_t)1 << bmH_bits) * sizeof(uint32_t);
-        const size_t bk = tsize * sizeof(unsigned long long), bc = tsize * sizeof(uint2);
-        hot_bytes = up(ba) + up(bh) + up(bk) + 2 * up(bc);
-        TMS_CK(cudaMalloc((void **)&hot, hot_bytes));
-        unsigned char *q = hot;
-        bmA = reinterpret_cast<uint32_t *>(q);
-        q += up(ba);
-        bmH = reinterpret_cast<uint32_t *>(q);
-        q += up(bh);
-        tkey = reinterpret_cast<unsigned long long *>(q);
-        q += up(bk);
-        tcnt = reinterpret_cast<uint2 *>(q);
-        q += up(bc);
-        tstart = reinterpret_cast<uint2 *>(q);
-        keep_hot_in_l2();
+        TMS_CK(dalloc(&tkey, tsize));
+        TMS_CK(dalloc(&tcnt, tsize));
+        TMS_CK(dalloc(&tstart, tsize));
         TMS_CK(cudaMemset(tkey, 0, tsize * sizeof(unsigned long long)));
         TMS_CK(cudaMemset(tcnt, 0, tsize * sizeof(uint2)));
         // per cell: a cell holding both meshes has at least two entries
