@@ -269,7 +269,7 @@ struct Plan {
         ea.cells = crec; ea.vals = grouped;
         ea.grids = d_grids; ea.meshes = d_meshes; ea.pairs = d_pairs; ea.ctr = d_ctr;
         ea.ent_cap = ent_cap; ea.cand = cand; ea.cand_cap = cand_cap; ea.moller = p.moller;
-        launch_emit(ea, prec, fl, grid * 4, s);
+        launch_emit(ea, prec, fl, grid / 2, s);
         kernels += 1;
         mark(10, s);
 
@@ -557,6 +557,7 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
     std::lock_guard<std::mutex> lk(g_mu);
     if (!(g_configured_mask & (1 << device))) {
         TMS_CK(configure_face_pass());
+        configure_emit();
         g_configured_mask |= 1 << device;
     }
     Plan *P = find_plan(A, B, nPairs, prm, user, dHits, hitCap, dOffsets, device);

@@ -436,7 +436,9 @@ struct EmitArgs {
     unsigned long long cand_cap;
     int moller;
 };
-void launch_emit(const EmitArgs &a, int precision, int face_level, int grid, cudaStream_t st);
+// whole waves of resident blocks on `sms` SMs
+void launch_emit(const EmitArgs &a, int precision, int face_level, int sms, cudaStream_t st);
+void configure_emit();
 
 struct NarrowArgs {
     const Cand *cand;

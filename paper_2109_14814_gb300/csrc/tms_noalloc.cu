@@ -169,6 +169,7 @@ tms_status setup(int device, unsigned char **base) {
     void *p = nullptr;
     NA_CK(cudaGetSymbolAddress(&p, g_arena));
     NA_CK(configure_face_pass());
+    configure_emit();
     Buffers probe;
     if (carve(reinterpret_cast<unsigned char *>(p), probe) > kArenaBytes) {
         g_msg = "scratch layout exceeds the static arena";
@@ -310,7 +311,7 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     ea.cells = b.crec; ea.vals = b.grouped;
     ea.grids = b.grids; ea.meshes = b.tables->meshes; ea.pairs = b.tables->pairs; ea.ctr = b.ctr;
     ea.ent_cap = kEntCap; ea.cand = b.cand; ea.cand_cap = kCandCap; ea.moller = p.moller;
-    launch_emit(ea, p.precision, p.face_level, grid * 4, s);
+    launch_emit(ea, p.precision, p.face_level, grid / 2, s);
     NarrowArgs na;
     na.cand = b.cand; na.cand_cap = kCandCap; na.surv = b.surv; na.surv_cap = kSurvCap;
     na.meshes = b.tables->meshes; na.pairs = b.tables->pairs; na.ctr = b.ctr; na.hits = b.hits;

@@ -14,8 +14,12 @@
 // test of Sec. 6.2.2, then the owner-cell rule -- the pair is kept only in the
 // cell that is the componentwise max of the two faces' lowest cells, so a pair
 // sharing several cells is emitted exactly once -- then optionally the Moller
-// quick test of Sec. 6.2.3; survivors are staged per warp and appended 32 at a
-// time.
+// quick test of Sec. 6.2.3.  Each lane collects the tile's overlaps as a bit
+// mask over the rows (no vote per row: at about 3% overlapping pairs most
+// groups of rows hold one somewhere in the warp); the owner rule is applied
+// per tile from four ballots of the rows' owned coordinates; one warp scan
+// places the survivors in a per-warp stage that is appended at one atomic per
+// 64 or more.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,7 +32,8 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kTile = 32;
 constexpr int kEmitWarps = 8;
-constexpr unsigned kCandFlush = 64;    // candidates per atomic on the candidate counter
+constexpr unsigned kCandFlush = 64;    // the stage is appended once it holds this many
+constexpr unsigned kStageCap = 192;    // staged candidates per warp
 
 // ---------------------------------------------------------------------------
 // emission
@@ -44,6 +49,11 @@ struct __align__(16) EBox<1> {
         const float4 l = __ldg(p), h = __ldg(p + 1);
         lo[0] = l.x; lo[1] = l.y; lo[2] = l.z; lo[3] = l.w;
         hi[0] = h.x; hi[1] = h.y; hi[2] = h.z; hi[3] = h.w;
+    }
+    // a box that overlaps nothing
+    __device__ void set_empty() {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) { lo[d] = __int_as_float(0x7f800000); hi[d] = -lo[d]; }
     }
     // the face's lowest cell, as the cell passes compute it, 4 x u16
     __device__ uint2 low_cell(const Grid &g) const {
@@ -61,6 +71,10 @@ struct __align__(16) EBox<0> {
         const double2 x0 = __ldg(p), x1 = __ldg(p + 1), x2 = __ldg(p + 2), x3 = __ldg(p + 3);
         lo[0] = x0.x; lo[1] = x0.y; lo[2] = x1.x; lo[3] = x1.y;
         hi[0] = x2.x; hi[1] = x2.y; hi[2] = x3.x; hi[3] = x3.y;
+    }
+    __device__ void set_empty() {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) { lo[d] = __longlong_as_double(0x7ff0000000000000LL); hi[d] = -lo[d]; }
     }
     __device__ uint2 low_cell(const Grid &g) const {
         int c[4];
@@ -147,12 +161,11 @@ __device__ __forceinline__ bool boxes_overlap(const EBox<PREC> &x, const EBox<PR
 }
 
 template <int PREC, bool MOLLER>
-__global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_level) {
-    // the tile's B side, structure of arrays: the hot loop reads only the boxes
+__global__ void __launch_bounds__(32 * kEmitWarps, (PREC == 1 && !MOLLER) ? 5 : 2) k_emit(EmitArgs a, int face_level) {
+    // the tile's B side: boxes (read by broadcast in the hot loop) and face ids
     __shared__ EBox<PREC> sBox[kEmitWarps][kTile];
-    __shared__ uint32_t sMask[kEmitWarps][kTile];
     __shared__ uint32_t sFace[kEmitWarps][kTile];
-    __shared__ Cand sOut[kEmitWarps][kCandFlush + 32];   // staged candidates
+    __shared__ Cand sOut[kEmitWarps][kStageCap];   // staged candidates
     // nothing to do after an entry overflow (the host retries with more room),
     // and a bounded amount of work in any case
     if (a.ctr->entries > a.ent_cap) return;
@@ -160,7 +173,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctr->status, ST_PAIR_LIMIT);
         return;
     }
-    const unsigned long long total = a.ctr->tiles;
+    const unsigned long long total_tiles = a.ctr->tiles;
     const unsigned long long ncell = clamp_count(&a.ctr->cells, a.ent_cap);
     const unsigned long long nent = clamp_count(&a.ctr->grouped, a.ent_cap);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -168,15 +181,23 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
     const unsigned long long nw = (unsigned long long)gridDim.x * kEmitWarps;
     // each warp owns a contiguous range of tiles: one binary search for its first
     // tile's cell, then a forward walk over the cells
-    const unsigned long long per = (total + nw - 1) / nw;
+    const unsigned long long per = (total_tiles + nw - 1) / nw;
     const unsigned long long t_begin = gw * per;
-    const unsigned long long t_end = min(t_begin + per, total);
+    const unsigned long long t_end = min(t_begin + per, total_tiles);
     Cand *stage = sOut[warp];
-    unsigned staged = 0;
+    unsigned staged = 0;                       // warp-uniform
     const unsigned long long cap = a.cand_cap;
     Cand *cand_out = a.cand;
-    auto store = [cand_out, cap](unsigned long long pos, const Cand &cd) {
-        if (pos < cap) cand_out[pos] = cd;
+    // the whole stage to one atomically reserved range of the candidate array
+    auto flush = [&]() {
+        __syncwarp();
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&a.ctr->cand, (unsigned long long)staged);
+        base = __shfl_sync(FULL, base, 0);
+        for (unsigned k = lane; k < staged; k += 32)
+            if (base + k < cap) cand_out[base + k] = stage[k];
+        __syncwarp();
+        staged = 0;
     };
     unsigned long long c = 0;
     if (t_begin < t_end) {
@@ -187,9 +208,11 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         }
         c = lo;
     }
-    // the lanes' face, kept across tiles of one A row
+    // the lanes' face, kept across tiles of one A row: its box and the
+    // coordinates in which it is not in its lowest cell (its partner must be)
     EBox<PREC> abox;
-    uint32_t amask = 0, aface = 0;
+    abox.set_empty();
+    uint32_t aneed = 0, aface = 0;
     uint32_t prev_a0 = 0xFFFFFFFFu;
     unsigned long long prev_c = ~0ULL;
     bool prev_swap = true;
@@ -231,67 +254,139 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit(EmitArgs a, int face_l
         prev_swap = swapAB;
         prev_a0 = a0;
         prev_c = c;
-        const bool hasA = lane < nAt;
-        if (hasA && !reuse) {
-            aface = a.vals[l0 + lane];
-            abox.load(fbL, aface);
-            amask = own_mask(abox.low_cell(gr), cur);
+        if (!reuse) {
+            abox.set_empty();
+            if (lane < nAt) {
+                aface = a.vals[l0 + lane];
+                abox.load(fbL, aface);
+                aneed = ~own_mask(abox.low_cell(gr), cur) & 0xFu;
+            }
         }
+        // every row of the B side is written; rows past nBt hold an empty box
+        EBox<PREC> bb;
+        bb.set_empty();
+        uint32_t bown = 0;
+        __syncwarp();                          // the previous tile's rows are read
         if (lane < nBt) {
             const uint32_t bface = a.vals[m0 + lane];
-            EBox<PREC> bb;
             bb.load(fbM, bface);
-            sBox[warp][lane] = bb;
-            sMask[warp][lane] = own_mask(bb.low_cell(gr), cur);
+            bown = own_mask(bb.low_cell(gr), cur);
             sFace[warp][lane] = bface;
         }
+        sBox[warp][lane] = bb;
+        // owner cell: the componentwise max of the two faces' lowest cells is this
+        // cell iff every coordinate is owned by one of them, so a lane's face may
+        // pair only with rows owning every coordinate it does not own
+        uint32_t rows = ~0u;
+        {
+            const uint32_t w0 = __ballot_sync(FULL, bown & 1u), w1 = __ballot_sync(FULL, bown & 2u);
+            const uint32_t w2 = __ballot_sync(FULL, bown & 4u), w3 = __ballot_sync(FULL, bown & 8u);
+            if (aneed & 1u) rows &= w0;
+            if (aneed & 2u) rows &= w1;
+            if (aneed & 4u) rows &= w2;
+            if (aneed & 8u) rows &= w3;
+        }
         __syncwarp();
-        // the append of the pairs with box j that survive (and, optionally, Moller)
-        auto emit_j = [&](int j, bool keep) {
-            const uint32_t bface = sFace[warp][j];
-            if (MOLLER && keep) {
+        // the box test against every row, four rows per step
+        uint32_t K = 0;
+        const int nB4 = (nBt + 3) & ~3;
+        for (int j = 0; j < nB4; j += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                K |= (boxes_overlap(abox, sBox[warp][j + u]) ? 1u : 0u) << (j + u);
+        }
+        K &= rows;
+        if (MOLLER) {
+            for (uint32_t k = K; k; k &= k - 1) {
+                const int j = __ffs(k) - 1;
+                const uint32_t bface = sFace[warp][j];
                 const uint32_t fa = swapAB ? bface : aface, fb = swapAB ? aface : bface;
-                keep = !moller_reject(a.meshes[pr.x], fa, a.meshes[pr.y], fb, face_level);
+                if (moller_reject(a.meshes[pr.x], fa, a.meshes[pr.y], fb, face_level)) K &= ~(1u << j);
             }
+        }
+        // the survivors' places: a warp scan of the per-lane counts
+        const uint32_t cnt = __popc(K);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        if (total == 0) continue;
+        auto cand_of = [&](int j) {
+            const uint32_t bface = sFace[warp][j];
             Cand cd;
             cd.faceA = swapAB ? bface : aface;
             cd.faceB = swapAB ? aface : bface;
             cd.pair = pair;
             cd.pad = 0;
-            stage_push<kCandFlush>(stage, staged, keep, cd, &a.ctr->cand, store);
+            return cd;
         };
-        // owner cell: the componentwise max of the two faces' lowest cells is this
-        // cell iff every coordinate is owned by one of them (masks OR to 0xF);
-        // two B boxes per step, one vote, the append only when a lane keeps a pair
-        int j = 0;
-        for (; j + 1 < nBt; j += 2) {
-            const EBox<PREC> b0x = sBox[warp][j], b1x = sBox[warp][j + 1];
-            const bool k0 = hasA & ((amask | sMask[warp][j]) == 0xFu) & boxes_overlap(abox, b0x);
-            const bool k1 = hasA & ((amask | sMask[warp][j + 1]) == 0xFu) & boxes_overlap(abox, b1x);
-            if (__ballot_sync(FULL, k0 | k1) == 0u) continue;
-            emit_j(j, k0);
-            emit_j(j + 1, k1);
+        if (staged + total > kStageCap && staged) flush();
+        if (total > kStageCap) {
+            // a dense tile: its candidates straight to one reserved range
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&a.ctr->cand, (unsigned long long)total);
+            base = __shfl_sync(FULL, base, 0);
+            unsigned long long pos = base + incl - cnt;
+            for (uint32_t k = K; k; k &= k - 1, ++pos)
+                if (pos < cap) cand_out[pos] = cand_of(__ffs(k) - 1);
+        } else {
+            unsigned pos = staged + incl - cnt;
+            for (uint32_t k = K; k; k &= k - 1) stage[pos++] = cand_of(__ffs(k) - 1);
+            staged += total;
+            if (staged >= kCandFlush) flush();
         }
-        if (j < nBt) {
-            const bool k0 = hasA & ((amask | sMask[warp][j]) == 0xFu) & boxes_overlap(abox, sBox[warp][j]);
-            if (__ballot_sync(FULL, k0) != 0u) emit_j(j, k0);
-        }
-        __syncwarp();
     }
-    __syncwarp();
-    stage_flush<kCandFlush>(stage, staged, &a.ctr->cand, store);
+    if (staged) flush();
+}
+
+// Whole waves of resident blocks: every warp owns the same number of tiles, so
+// a partial last wave would leave SMs idle at the end; several waves let the
+// block scheduler even out tiles of unequal cost (dense cells).  Resident
+// blocks per SM of each kernel variant, the same on every GB300; looked up by
+// configure_emit (outside stream capture) or at the first launch.
+constexpr int kEmitWaves = 4;
+int g_emit_resident[2][2] = {};
+
+template <int PREC, bool MOLLER>
+int emit_resident() {
+    int &r = g_emit_resident[PREC][MOLLER ? 1 : 0];
+    if (r == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_emit<PREC, MOLLER>, 32 * kEmitWarps, 0) !=
+                cudaSuccess || nb < 1)
+            nb = 1;
+        r = nb;
+    }
+    return r;
+}
+
+template <int PREC, bool MOLLER>
+void emit_waves(const EmitArgs &a, int face_level, int sms, cudaStream_t st) {
+    k_emit<PREC, MOLLER><<<sms * emit_resident<PREC, MOLLER>() * kEmitWaves, 32 * kEmitWarps, 0, st>>>(
+        a, face_level);
 }
 
 }  // namespace
 
-void launch_emit(const EmitArgs &a, int precision, int face_level, int grid, cudaStream_t st) {
-    const dim3 b(32 * kEmitWarps);
+// Looks up the emission's resident blocks per SM once, outside stream capture
+// (a failed lookup leaves one block per SM).
+void configure_emit() {
+    emit_resident<0, false>();
+    emit_resident<0, true>();
+    emit_resident<1, false>();
+    emit_resident<1, true>();
+}
+
+void launch_emit(const EmitArgs &a, int precision, int face_level, int sms, cudaStream_t st) {
     if (precision == 1) {
-        if (a.moller) k_emit<1, true><<<grid, b, 0, st>>>(a, face_level);
-        else k_emit<1, false><<<grid, b, 0, st>>>(a, face_level);
+        if (a.moller) emit_waves<1, true>(a, face_level, sms, st);
+        else emit_waves<1, false>(a, face_level, sms, st);
     } else {
-        if (a.moller) k_emit<0, true><<<grid, b, 0, st>>>(a, face_level);
-        else k_emit<0, false><<<grid, b, 0, st>>>(a, face_level);
+        if (a.moller) emit_waves<0, true>(a, face_level, sms, st);
+        else emit_waves<0, false>(a, face_level, sms, st);
     }
 }
 
