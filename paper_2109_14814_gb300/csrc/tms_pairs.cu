@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps, (PREC == 1 && !MOLLER) ? 5 : 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long gw = blockIdx.x * (unsigned long long)kEmitWarps + warp;
     const unsigned long long nw = (unsigned long long)gridDim.x * kEmitWarps;
-    // each warp owns a contiguous range of tiles: one binary search for its first
+    // each warp owns a contiguous range of tiles: one search for its first
     // tile's cell, then a forward walk over the cells
     const unsigned long long per = (total_tiles + nw - 1) / nw;
     const unsigned long long t_begin = gw * per;
@@ -199,12 +199,26 @@ __global__ void __launch_bounds__(32 * kEmitWarps, (PREC == 1 && !MOLLER) ? 5 : 
         __syncwarp();
         staged = 0;
     };
+    // the last cell whose first tile is at or before t_begin (cell 0 starts at
+    // tile 0; tile offsets increase strictly): a 32-way search, each step one
+    // probe per lane and one vote, about four dependent steps for 10^5 cells
     unsigned long long c = 0;
     if (t_begin < t_end) {
         unsigned long long lo = 0, hi = ncell - 1;
         while (lo < hi) {
-            unsigned long long mid = (lo + hi + 1) >> 1;
-            if (a.cells[mid].tile_off <= t_begin) lo = mid; else hi = mid - 1;
+            const unsigned long long span = hi - lo;
+            // probe k at lo + (k + 1) * span / 32 (k < span when span < 32); the
+            // probes rise with k, so the lanes at or before t_begin are a prefix
+            const unsigned long long q = lo + ((unsigned long long)(lane + 1) * span) / 32;
+            const bool probe = span >= 32 || (unsigned long long)lane < span;
+            const unsigned long long qq = span >= 32 ? q : lo + 1 + lane;
+            const bool le = probe && a.cells[qq].tile_off <= t_begin;
+            const int n_le = __popc(__ballot_sync(FULL, le));
+            const int n_probe = span >= 32 ? 32 : (int)span;
+            const unsigned long long q_le = n_le ? __shfl_sync(FULL, qq, n_le - 1) : lo;
+            const unsigned long long q_gt = __shfl_sync(FULL, qq, n_le < n_probe ? n_le : 0);
+            lo = q_le;
+            hi = n_le < n_probe ? q_gt - 1 : hi;
         }
         c = lo;
     }

@@ -160,6 +160,40 @@ def test_minimal_meshes():
         compare(OA, OB, g, ref)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_dense_cells_every_overlap_emitted_once(precision):
+    """Both meshes inside one small ball: 89% of all quad pairs have overlapping
+    boxes, the grid has 1 x 2 x 2 x 1 cells and every face lies in several of
+    them, and one 32 x 32 tile keeps about 980 pairs (more than the emission's
+    per-warp stage holds, so its dense-tile path writes them).  Every
+    box-overlapping pair must be a candidate exactly once (the nearest
+    non-overlapping pair is 1.6e-6 apart, far above FP32 rounding), and the hits
+    must match brute force."""
+    g0 = torch.Generator().manual_seed(11)
+    XA = 0.01 * torch.randn(4, 13, 12, generator=g0, dtype=torch.float64)
+    XB = 0.01 * torch.randn(4, 13, 12, generator=g0, dtype=torch.float64)
+    s = torch.linspace(0.0, 1.0, 13, dtype=torch.float64)
+    A, B = synth.MeshGrid(XA, s), synth.MeshGrid(XB, s)
+    OA, OB = oracle.OMesh.from_grid(A), oracle.OMesh.from_grid(B)
+    ref = oracle.search(OA, OB, method="brute")
+    g = gpu_search(synth.MeshPair(A, B, None), precision=precision)
+    compare(OA, OB, g, ref)
+
+    def quad_boxes(X):
+        X = X.numpy()
+        Xn = np.roll(X, -1, axis=2)
+        v = [X[:, :-1, :], Xn[:, :-1, :], X[:, 1:, :], Xn[:, 1:, :]]
+        lo = np.minimum(np.minimum(v[0], v[1]), np.minimum(v[2], v[3])).reshape(4, -1).T
+        hi = np.maximum(np.maximum(v[0], v[1]), np.maximum(v[2], v[3])).reshape(4, -1).T
+        return lo, hi
+
+    la, ha = quad_boxes(XA)
+    lb, hb = quad_boxes(XB)
+    overlapping = int(((la[:, None, :] <= hb[None, :, :]) & (lb[None, :, :] <= ha[:, None, :])).all(-1).sum())
+    assert overlapping == 18556
+    assert tms.last_stats()["candidates"] == overlapping
+
+
 def test_disjoint_meshes_empty_world():
     p = cached("c1", synth.config1)
     XB = p.B.X + 1000.0
