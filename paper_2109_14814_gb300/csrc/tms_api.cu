@@ -278,7 +278,7 @@ struct Plan {
         na.meshes = d_meshes; na.pairs = d_pairs;
         na.ctr = d_ctr; na.hits = hits; na.hit_key = hk; na.hit_val = hv; na.hit_cap = hit_cap;
         na.tau = p.tau; na.tri_bits = tri_bits; na.fp32_filter = p.narrow_filter;
-        launch_narrow(na, fl, grid * 4, s);
+        launch_narrow(na, fl, grid / 2, grid * 4, s);
         kernels += 2;
         mark(11, s);
 
@@ -558,6 +558,7 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
     if (!(g_configured_mask & (1 << device))) {
         TMS_CK(configure_face_pass());
         configure_emit();
+        configure_narrow();
         g_configured_mask |= 1 << device;
     }
     Plan *P = find_plan(A, B, nPairs, prm, user, dHits, hitCap, dOffsets, device);

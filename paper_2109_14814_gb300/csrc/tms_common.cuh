@@ -456,7 +456,9 @@ struct NarrowArgs {
     int tri_bits;
     int fp32_filter;
 };
-void launch_narrow(const NarrowArgs &a, int face_level, int grid, cudaStream_t st);
+// the filter as one wave of resident blocks on `sms` SMs, the FP64 solve on `grid` blocks
+void launch_narrow(const NarrowArgs &a, int face_level, int sms, int grid, cudaStream_t st);
+void configure_narrow();
 
 // FP32 split of a double: hi = RN32(x), lo = RN32(x - hi), integer operations
 // only in the normal range

@@ -170,6 +170,7 @@ tms_status setup(int device, unsigned char **base) {
     NA_CK(cudaGetSymbolAddress(&p, g_arena));
     NA_CK(configure_face_pass());
     configure_emit();
+    configure_narrow();
     Buffers probe;
     if (carve(reinterpret_cast<unsigned char *>(p), probe) > kArenaBytes) {
         g_msg = "scratch layout exceeds the static arena";
@@ -317,7 +318,7 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     na.meshes = b.tables->meshes; na.pairs = b.tables->pairs; na.ctr = b.ctr; na.hits = b.hits;
     na.hit_key = b.hk; na.hit_val = b.hv; na.hit_cap = kRawHitCap; na.tau = p.tau;
     na.tri_bits = tri_bits; na.fp32_filter = p.narrow_filter;
-    launch_narrow(na, p.face_level, grid * 4, s);
+    launch_narrow(na, p.face_level, grid / 2, grid * 4, s);
     const bool halt = radix_sort(b.hk, b.hv, b.hk2, b.hv2, b.sort_scratch, &b.ctr->raw_hits, kRawHitCap,
                                  2 * tri_bits, 2 * grid, &b.ctr->status, s);
     DedupArgs da;
