@@ -1,5 +1,6 @@
 """Host-side logic of bench.py that needs no GPU: the DRAM-traffic summary
-written from an ncu CSV, and the source hash it is keyed to."""
+written from an ncu CSV, the source hash it is keyed to, and the summary of the
+clock samples taken during the timed region."""
 import csv
 import io
 import json
@@ -72,3 +73,31 @@ def test_source_hash_covers_only_the_search_sources():
     assert len(bench.SEARCH_SOURCES) == 7
     assert "tms_refine.cu" not in bench.SEARCH_SOURCES and "tms_faces.cu" in bench.SEARCH_SOURCES
     assert len(bench.source_hash()) == 16
+
+
+def test_clock_summary_median_max_and_throttle_reasons(tmp_path):
+    """The clock line the bench attaches: median SM clock under load, the
+    maximum, and every throttle reason seen active at least once ("Not Active"
+    is not active); malformed lines are skipped and the sample file removed."""
+    path = tmp_path / "clocks.csv"
+    rows = [
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1100.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "truncated line",
+        "0, 1410, 2070, 700.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+    ]
+    path.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler(0)
+    cs.path = str(path)
+    out = cs.summary()
+    assert out["samples"] == 4
+    assert out["sm_mhz"] == 2025.0          # median of 2070, 1980, 2070, 1410
+    assert out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert not path.exists()
+    # no sampler output at all (nvidia-smi missing): no clock figures, no reasons
+    cs2 = bench.ClockSampler(0)
+    cs2.path = str(tmp_path / "absent.csv")
+    assert cs2.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
