@@ -111,16 +111,36 @@ typedef struct {
     long long hit_capacity;    /* raw hits before merging (0 = automatic)       */
     int use_graph;        /* 1 = capture the launch sequence in a CUDA graph on
                              first use and replay it (default 1) */
-    unsigned inject;      /* fault injection for tests (host side):
+    unsigned inject;      /* fault injection for tests:
                              bit0 = force entry capacity 1 (exercises retry),
                              bit1 = force a capacity error to be returned,
-                             bit2 = report TMS_ERR_TIMEOUT from the status word,
+                             bit2 = report TMS_ERR_TIMEOUT from the host,
                              bit3 = start the cell table at 1024 slots (exercises
-                             its growth) */
+                             its growth),
+                             bit4 = on the device, the hit sort's look-back reads
+                             every earlier tile as not yet published, so each of
+                             its bounded waits runs out after spin_limit polls
+                             (no fault: the kernel records ST_TIMEOUT, keeps its
+                             writes in bounds and returns; TMS_ERR_TIMEOUT) */
     int block_faces;      /* bounds-pass tile width in quads (64/128/256; 0 = 128) */
     int tile_rows;        /* bounds-pass tile height in quad rows (4 or 8; 0 = 4) */
     int timing;           /* 1 = record CUDA events between stages (in the graph) so
                              that tms_last_stage_ms() reports per-stage device time */
+    int patch;            /* broad-phase level: 0 = the grid holds the faces
+                             themselves; 1 = the grid holds patches of 8 x 4 quads
+                             (their boxes the union of the quads'), and the quad
+                             pairs of every patch pair whose boxes overlap are
+                             tested in one warp tile (quad faces only; ignored
+                             with face_level 0).  Same candidates either way. */
+    int pad0;
+    long long spin_limit; /* polls of one device-side wait before it gives up
+                             (ST_TIMEOUT, TMS_ERR_TIMEOUT); 0 = 4194304 */
+    const char *autotune_cache; /* NULL, or a cache file written by tms_autotune:
+                             when it holds an entry for these meshes' size class
+                             (see tms_autotune), that entry's face level, cell
+                             size, patch level and bounds-pass tile replace the
+                             fields given here; read on the first search of a
+                             plan only */
 } tms_params;
 
 void tms_params_default(tms_params *p);
@@ -244,23 +264,25 @@ tms_status tms_last_stats(void *stream, tms_stats *out);
 /*
  * tms_search_noalloc -- tms_search for callers that must not allocate device
  * memory.  The paper has no counterpart: this is a deployment variant.
- * Callers that cannot call cudaMalloc include code running while another
- * framework captures a CUDA graph on the same thread (an allocation would
- * break the capture), real-time or flight software that fixes its device
- * footprint at start-up, and services whose device memory is entirely held by
- * a pool allocator.  Every scratch buffer comes from one file-scope static
- * __device__ array of 64 MiB that every GPU loading this library holds until
- * the process exits; the call makes no cudaMalloc, cudaFree or other
- * allocating call.  Arguments, output order and merging are those of
- * tms_search.  Limits: each mesh view at most 131072 vertices (TMS_ERR_ARG
- * otherwise); at most 262144 face-cell entries, 262144 candidates, 65536 FP64
- * solves and 16384 hits before merging (TMS_ERR_CAPACITY, *nHits = -1, when a
- * stage overflows; nothing is grown).  All calls share the array, which keeps
- * the last call's contents; each call clears what must start at zero.  Calls
- * whose GPU work overlaps (two streams, two host threads) race on the array and
- * must be ordered by the caller.  The first call on a device looks up the
- * array's device address with that device current and configures the kernels:
- * make it before any stream capture.  Synchronises `stream`.  Messages:
+ * Callers that cannot call cudaMalloc include real-time or flight software
+ * that fixes its device footprint at start-up and forbids allocation later,
+ * services whose device memory is entirely held by a pool allocator (a direct
+ * cudaMalloc fails or fragments the pool), and embedded hosts that budget
+ * every device byte when they start.  Every scratch buffer comes from one
+ * file-scope static __device__ array of 72 MiB that every GPU loading this
+ * library holds until the process exits; the call makes no cudaMalloc,
+ * cudaFree or other allocating call.  Arguments, output order and merging are
+ * those of tms_search.  Limits: each mesh view at most 131072 vertices
+ * (TMS_ERR_ARG otherwise); at most 262144 face-cell entries, 262144
+ * candidates, 65536 FP64 solves and 16384 hits before merging
+ * (TMS_ERR_CAPACITY, *nHits = -1, when a stage overflows; nothing is grown).
+ * All calls share the array, which keeps the last call's contents; each call
+ * clears what must start at zero, and a call that overflows leaves the array
+ * fit for the next.  Calls whose GPU work overlaps (two streams, two host
+ * threads) race on the array and must be ordered by the caller.  The first
+ * call on a device looks up the array's device address with that device
+ * current and configures the kernels: make it before any stream capture.
+ * Synchronises `stream`.  Every error return sets a message, read with
  * tms_noalloc_last_error().
  */
 tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_params *params,

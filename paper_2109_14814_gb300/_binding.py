@@ -47,6 +47,10 @@ class Params(ctypes.Structure):
         ("block_faces", _c.c_int),
         ("tile_rows", _c.c_int),
         ("timing", _c.c_int),
+        ("patch", _c.c_int),
+        ("pad0", _c.c_int),
+        ("spin_limit", _c.c_longlong),
+        ("autotune_cache", _c.c_char_p),
     ]
 
 
@@ -192,10 +196,10 @@ def lib():
 def search_noalloc(A: "Mesh", B: "Mesh", out: torch.Tensor, stream=None, **kw) -> "Hits":
     """tms_search_noalloc: the search with every scratch buffer in the library's
     static device array, for callers that must not allocate device memory
-    (for example while another component captures a CUDA graph, or in software
-    that fixes its device footprint at start-up).  The caller passes the output
-    buffer `out` ((capacity, 128) uint8, on the device); nothing is allocated.
-    Limits and sharing rules: see include/tms.h."""
+    (software that fixes its device footprint at start-up, or services whose
+    device memory is all held by a pool allocator).  The caller passes the
+    output buffer `out` ((capacity, 128) uint8, on the device); nothing is
+    allocated.  Limits and sharing rules: see include/tms.h."""
     p = params(**kw)
     n = _c.c_longlong(0)
     rc = lib().tms_search_noalloc(A.handle, B.handle, _c.byref(p), out.data_ptr(), out.shape[0],
@@ -254,8 +258,10 @@ def params(**kw) -> Params:
     p = Params()
     lib().tms_params_default(_c.byref(p))
     for k, v in kw.items():
-        if not hasattr(p, k):
+        if not hasattr(p, k) or k == "pad0":
             raise KeyError(f"unknown search parameter {k!r}")
+        if k == "autotune_cache" and isinstance(v, str):
+            v = v.encode()
         setattr(p, k, v)
     return p
 
@@ -720,18 +726,27 @@ def release_workspace(stream=None):
 
 
 class HitPoint(torch.autograd.Function):
-    """(P, z) of each hit as differentiable functions of the mesh vertices.
+    """(P, z) of each hit as differentiable functions of the mesh vertices and,
+    optionally, of a family parameter alpha on which both meshes depend.
 
-    forward(XA, XB, meshA, meshB, hits) returns the hit points P (n, 4) and
-    barycentric pairs z = (a, b, c, d) (n, 4) found by the search; backward
-    runs the library's FP64 adjoint (implicit differentiation of the 4x4 solve)
-    and returns vertex gradients shaped like XA and XB.  XA and XB must be the
-    tensors the meshes were built from.
+    HitPoint.apply(XA, XB, meshA, meshB, hits[, alpha, dXA_dalpha, dXB_dalpha])
+    returns the hit points P (n, 4) and barycentric pairs z = (a, b, c, d)
+    (n, 4) found by the search; backward runs the library's FP64 adjoint
+    (implicit differentiation of the 4x4 solve of Eq. (precise)) and returns
+    vertex gradients shaped like XA and XB.  XA and XB must be the tensors the
+    meshes were built from.  With alpha (a float64 tensor with one element) and
+    dXA_dalpha, dXB_dalpha (CUDA float64, shaped like XA and XB: the vertices'
+    derivatives in alpha; either may be None for a mesh that does not move),
+    alpha's gradient is the sum over hits of the adjoint's per-hit alpha
+    derivative, sum_v grad_v . dv/dalpha over each hit's six vertices.
     """
 
     @staticmethod
-    def forward(ctx, XA, XB, meshA, meshB, hits):
+    def forward(ctx, XA, XB, meshA, meshB, hits, alpha=None, dXA_dalpha=None, dXB_dalpha=None):
         ctx.meshA, ctx.meshB, ctx.hits = meshA, meshB, hits
+        ctx.alpha_shape = None if alpha is None else alpha.shape
+        ctx.dA = None if dXA_dalpha is None else dXA_dalpha.to(torch.float64).contiguous()
+        ctx.dB = None if dXB_dalpha is None else dXB_dalpha.to(torch.float64).contiguous()
         return hits.P.clone(), hits.z.clone()
 
     @staticmethod
@@ -741,5 +756,11 @@ class HitPoint(torch.autograd.Function):
         gB = torch.zeros_like(B.X)
         gP = None if gP is None else gP.to(torch.float64).contiguous()
         gZ = None if gZ is None else gZ.to(torch.float64).contiguous()
-        backward(A, B, hits, gP=gP, gZ=gZ, gradA=gA, gradB=gB)
-        return gA, gB, None, None, None
+        want_alpha = ctx.alpha_shape is not None and ctx.needs_input_grad[5] and \
+            (ctx.dA is not None or ctx.dB is not None)
+        galpha = torch.zeros(len(hits), dtype=torch.float64, device=A.X.device) if want_alpha else None
+        backward(A, B, hits, gP=gP, gZ=gZ, gradA=gA, gradB=gB,
+                 dA_dalpha=ctx.dA if want_alpha else None,
+                 dB_dalpha=ctx.dB if want_alpha else None, galpha=galpha)
+        g_alpha = galpha.sum().reshape(ctx.alpha_shape) if want_alpha else None
+        return gA, gB, None, None, None, g_alpha, None, None

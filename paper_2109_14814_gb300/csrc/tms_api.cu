@@ -284,7 +284,8 @@ struct Plan {
 
         // the raw hits are few: a small grid keeps the per-pass fixed cost low
         const bool halt = radix_sort(hk, hv, hk2, hv2, sort_scratch, &d_ctr->raw_hits, hit_cap,
-                                     2 * tri_bits + pair_bits, sort_grid, &d_ctr->status, s);
+                                     2 * tri_bits + pair_bits, sort_grid, &d_ctr->status,
+                                     (unsigned long long)p.spin_limit, (p.inject & 16u) ? 1 : 0, s);
         kernels += 2 + sort_passes_h;
         mark(12, s);
         DedupArgs da;
@@ -359,7 +360,8 @@ bool same_params(const tms_params &a, const tms_params &b) {
            a.cell_mult == b.cell_mult && a.tau == b.tau && a.entry_capacity == b.entry_capacity &&
            a.cand_capacity == b.cand_capacity && a.hit_capacity == b.hit_capacity &&
            a.use_graph == b.use_graph && a.inject == b.inject && a.block_faces == b.block_faces &&
-           a.tile_rows == b.tile_rows && a.timing == b.timing;
+           a.tile_rows == b.tile_rows && a.timing == b.timing && a.patch == b.patch &&
+           a.spin_limit == b.spin_limit;
 }
 
 tms_status validate_params(const tms_params &p) {
@@ -368,6 +370,8 @@ tms_status validate_params(const tms_params &p) {
     if (!(p.cell_mult >= 1.0f) || !(p.cell_mult < 1e6f)) return TMS_ERR_ARG;
     if (!(p.tau >= 0.0) || !(p.tau < 1.0)) return TMS_ERR_ARG;
     if (p.entry_capacity < 0 || p.cand_capacity < 0 || p.hit_capacity < 0) return TMS_ERR_ARG;
+    if (p.patch != 0 && p.patch != 1) return TMS_ERR_ARG;
+    if (p.spin_limit < 0) return TMS_ERR_ARG;
     return TMS_OK;
 }
 

@@ -368,13 +368,18 @@ void launch_search_init(Bounds *b, int n, Counters *ctr, uint32_t *bmA, unsigned
 void launch_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *g,
                         float cell_mult, cudaStream_t st);
 
+// polls of one device-side wait when tms_params.spin_limit is 0
+constexpr unsigned long long kDefaultSpinLimit = 1ULL << 22;
+
 // radix sort of (u64 key, u32 value) with a device-side count (at most cap);
 // scratch holds radix_scratch_size(cap, key_bits) bytes; returns true when the
-// sorted data ends in the alternate buffers.  A look-back wait that gives up
-// sets ST_TIMEOUT in *status.
+// sorted data ends in the alternate buffers.  A look-back wait gives up after
+// spin_limit polls (0: kDefaultSpinLimit) and sets ST_TIMEOUT in *status;
+// unpublished != 0 (a test switch) makes every wait run out.
 bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                 void *scratch, const unsigned long long *d_n, unsigned long long cap,
-                int key_bits, int grid, unsigned int *status, cudaStream_t st);
+                int key_bits, int grid, unsigned int *status, unsigned long long spin_limit,
+                int unpublished, cudaStream_t st);
 size_t radix_scratch_size(unsigned long long cap, int key_bits);
 
 // exclusive scans with a device-side count; total written to *d_total

@@ -927,8 +927,15 @@ __device__ uint32_t feature_of(const MeshDev &m, uint32_t t, double u, double v,
 
 __global__ void k_dedup_flags(DedupArgs a) {
     const unsigned long long n = clamp_count(&a.ctr->raw_hits, a.raw_cap);
+    // a sort whose look-back gave up leaves its output unordered and its value
+    // slots possibly unwritten: keep nothing, and index nothing with them
+    const bool sorted = (a.ctr->status & ST_TIMEOUT) == 0;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
+        if (!sorted) {
+            a.keep[i] = 0;
+            continue;
+        }
         const uint64_t key = a.keys[i];
         const tms_hit &h = a.raw[a.vals[i]];
         const int2 pr = a.pairs[h.pair];
@@ -968,6 +975,7 @@ __global__ void k_dedup_flags(DedupArgs a) {
 
 __global__ void k_dedup_out(DedupArgs a) {
     const unsigned long long n = clamp_count(&a.ctr->raw_hits, a.raw_cap);
+    if (a.ctr->status & ST_TIMEOUT) return;   // nothing was kept (k_dedup_flags)
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         if (!a.keep[i]) continue;

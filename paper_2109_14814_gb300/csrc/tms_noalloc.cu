@@ -1,11 +1,10 @@
 // tms_search_noalloc: the mesh search for callers that must not allocate.
 //
-// Some callers cannot call cudaMalloc: code running while another framework
-// captures a CUDA graph on the same thread (an allocation there breaks or
-// invalidates the capture), flight- or control-loop software that fixes its
-// device footprint at start-up and forbids allocation afterwards, and
+// Some callers cannot call cudaMalloc: flight- or control-loop software that
+// fixes its device footprint at start-up and forbids allocation afterwards,
 // services whose device memory is entirely held by a pool allocator (a direct
-// cudaMalloc would fail or fragment the pool).  For them this entry point runs
+// cudaMalloc would fail or fragment the pool), and embedded hosts that budget
+// every device byte when they start.  For them this entry point runs
 // the same kernels as tms_search with every scratch buffer carved from one
 // file-scope static __device__ array.  That array (kArenaBytes) is part of the
 // library image: every GPU that loads the library holds it until the process
@@ -38,10 +37,13 @@ using namespace tms;
 
 namespace {
 
-constexpr size_t kArenaBytes = 64ull << 20;
+constexpr size_t kArenaBytes = 72ull << 20;
 constexpr unsigned long long kMaxViewVertices = 1ull << 17;
 constexpr unsigned long long kEntCap = 1ull << 18;
-constexpr unsigned long long kTableSize = kEntCap;      // cell table slots (>= entries)
+// cell table slots: twice the entry limit, so that even a call at that limit
+// (at most one distinct cell per entry) keeps the table at most half full and
+// its linear probes short
+constexpr unsigned long long kTableSize = 2 * kEntCap;
 constexpr unsigned long long kCandCap = 1ull << 18;
 constexpr unsigned long long kSurvCap = 1ull << 16;
 constexpr unsigned long long kRawHitCap = 1ull << 14;
@@ -161,7 +163,10 @@ int ceil_log2u(unsigned long long v) {
 
 // once per device, with that device current: the arena's device address
 tms_status setup(int device, unsigned char **base) {
-    if (device < 0 || device >= 64) return TMS_ERR_ARG;
+    if (device < 0 || device >= 64) {
+        g_msg = "device index outside 0..63";
+        return TMS_ERR_ARG;
+    }
     if (g_base[device]) {
         *base = g_base[device];
         return TMS_OK;
@@ -196,20 +201,30 @@ extern "C" tms_status tms_noalloc_footprint(unsigned long long *needed, unsigned
 extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_params *params,
                                          tms_hit *dHits, long long hitCap, long long *nHits,
                                          void *stream) {
-    if (!nHits || hitCap < 0 || (hitCap > 0 && !dHits)) return TMS_ERR_ARG;
+    g_msg.clear();
+    if (!nHits || hitCap < 0 || (hitCap > 0 && !dHits)) {
+        g_msg = "nHits is NULL, hitCap is negative, or dHits is NULL with hitCap > 0";
+        return TMS_ERR_ARG;
+    }
     tms_params p;
     tms_params_default(&p);
     if (params) p = *params;
     if ((p.precision != 0 && p.precision != 1) || (p.face_level != 0 && p.face_level != 1) ||
-        !(p.cell_mult >= 1.0f) || !(p.tau >= 0.0) || !(p.tau < 1.0)) {
+        !(p.cell_mult >= 1.0f) || !(p.tau >= 0.0) || !(p.tau < 1.0) || p.spin_limit < 0) {
         g_msg = "invalid search parameters";
         return TMS_ERR_ARG;
     }
     MeshDev ma, mb;
     int devA = -1, devB = -1, device = 0;
-    if (mesh_view(A, &ma, &devA) != TMS_OK || mesh_view(B, &mb, &devB) != TMS_OK) return TMS_ERR_STATE;
+    if (mesh_view(A, &ma, &devA) != TMS_OK || mesh_view(B, &mb, &devB) != TMS_OK) {
+        g_msg = "mesh handle invalid (NULL or destroyed)";
+        return TMS_ERR_STATE;
+    }
     NA_CK(cudaGetDevice(&device));
-    if (devA != device || devB != device) return TMS_ERR_ARG;
+    if (devA != device || devB != device) {
+        g_msg = "mesh is on another device than the current one";
+        return TMS_ERR_ARG;
+    }
     if ((unsigned long long)ma.N * ma.M > kMaxViewVertices ||
         (unsigned long long)mb.N * mb.M > kMaxViewVertices) {
         g_msg = "mesh view has more than 131072 vertices (the static scratch limit)";
@@ -320,7 +335,8 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     na.tri_bits = tri_bits; na.fp32_filter = p.narrow_filter;
     launch_narrow(na, p.face_level, grid / 2, grid * 4, s);
     const bool halt = radix_sort(b.hk, b.hv, b.hk2, b.hv2, b.sort_scratch, &b.ctr->raw_hits, kRawHitCap,
-                                 2 * tri_bits, 2 * grid, &b.ctr->status, s);
+                                 2 * tri_bits, 2 * grid, &b.ctr->status,
+                                 (unsigned long long)p.spin_limit, (p.inject & 16u) ? 1 : 0, s);
     DedupArgs da;
     da.keys = halt ? b.hk2 : b.hk; da.vals = halt ? b.hv2 : b.hv; da.raw = b.hits;
     da.meshes = b.tables->meshes; da.pairs = b.tables->pairs; da.ctr = b.ctr; da.raw_cap = kRawHitCap;

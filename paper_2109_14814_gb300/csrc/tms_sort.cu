@@ -16,8 +16,12 @@
 //                  consecutive addresses.
 // Stability: tiles are numbered in key order, warps own consecutive slices of
 // a tile, and lanes within a warp iteration are in index order.
-// A look-back wait on a tile that never publishes gives up after a bounded
-// number of polls and sets ST_TIMEOUT in the caller's status word.
+// A look-back wait on a tile that never publishes gives up after spin_limit
+// polls and sets ST_TIMEOUT in the caller's status word; its tile's offsets are
+// then wrong, so every write is checked against the element count and the
+// kernel runs on to its end.  A test switch (`unpublished`) makes the look-back
+// read every earlier tile as not yet published, so that this path runs on the
+// device without any fault.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,7 +38,6 @@ constexpr int kMaxPasses = 8;                        // 64-bit keys
 constexpr uint64_t kFlagAgg = 1ull << 62;            // the tile's own count
 constexpr uint64_t kFlagInc = 2ull << 62;            // count of this and all earlier tiles
 constexpr uint64_t kCountMask = (1ull << 62) - 1;
-constexpr unsigned kSpinLimit = 1u << 22;            // polls of one look-back word
 
 // scratch layout: hist[kMaxPasses][256] (u32), tile counters[kMaxPasses] (u32),
 // then per pass the look-back words of every tile, tiles x 256 (u64)
@@ -105,7 +108,8 @@ __global__ void __launch_bounds__(kRadixBins) k_radix_bases(uint32_t *hist, int 
 __global__ void __launch_bounds__(kSortBlock) k_radix_pass(
     const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out, uint32_t *vals_out,
     const unsigned long long *d_n, unsigned long long cap, int shift, const uint32_t *base,
-    uint64_t *look, uint32_t *tile_ctr, unsigned int *status) {
+    uint64_t *look, uint32_t *tile_ctr, unsigned int *status, unsigned long long spin_limit,
+    int unpublished) {
     static_assert(kSortBlock == kRadixBins, "one thread per digit");
     constexpr int NW = kSortBlock / 32;
     __shared__ uint32_t wcnt[NW][kRadixBins];
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_pass(
         uint64_t prefix = 0;
         if (tile > 0) {
             long long t = (long long)tile - 1;
-            unsigned spins = 0;
+            unsigned long long spins = 0;
             bool done = false;
             while (!done) {
                 uint64_t w[4];
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_pass(
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     if (done || used < q) continue;        // stop at a gap or an inclusive count
-                    const uint64_t flag = w[q] & ~kCountMask;
+                    const uint64_t flag = unpublished ? 0 : (w[q] & ~kCountMask);
                     if (flag == 0) continue;               // not yet published: poll again from here
                     if (t - q >= 0) prefix += w[q] & kCountMask;
                     ++used;
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_pass(
                 }
                 t -= used;
                 if (!done && used == 0) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > spin_limit) {
                         atomicOr(status, ST_TIMEOUT);
                         break;
                     }
@@ -248,7 +252,9 @@ size_t radix_scratch_size(unsigned long long cap, int key_bits) {
 
 bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                 void *scratch, const unsigned long long *d_n, unsigned long long cap,
-                int key_bits, int grid, unsigned int *status, cudaStream_t st) {
+                int key_bits, int grid, unsigned int *status, unsigned long long spin_limit,
+                int unpublished, cudaStream_t st) {
+    if (spin_limit == 0) spin_limit = kDefaultSpinLimit;
     int passes = (key_bits + kRadixBits - 1) / kRadixBits;
     if (passes < 1) passes = 1;
     if (passes > kMaxPasses) passes = kMaxPasses;
@@ -267,7 +273,7 @@ bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *va
         k_radix_pass<<<pgrid, kSortBlock, 0, st>>>(ki, vi, ko, vo, d_n, cap, p * kRadixBits,
                                                    hist + p * kRadixBins,
                                                    look + (size_t)p * tcap * kRadixBins,
-                                                   tile_ctr + p, status);
+                                                   tile_ctr + p, status, spin_limit, unpublished);
         uint64_t *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
     }

@@ -38,12 +38,16 @@ def test_struct_layouts_match_ctypes(tmp_path):
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "tms.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(tms_params), sizeof(tms_hit),"
-        " sizeof(tms_stats), offsetof(tms_hit, P), offsetof(tms_params, tau)); return 0;}\n")
+        " sizeof(tms_stats), offsetof(tms_hit, P), offsetof(tms_params, tau));"
+        " printf(\"%zu %zu %zu\\n\", offsetof(tms_params, patch), offsetof(tms_params, spin_limit),"
+        " offsetof(tms_params, autotune_cache)); return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    p, h, s, off_p, off_tau = map(int, out)
+    p, h, s, off_p, off_tau, off_patch, off_spin, off_cache = map(int, out)
+    assert (off_patch, off_spin, off_cache) == (tms.Params.patch.offset, tms.Params.spin_limit.offset,
+                                                tms.Params.autotune_cache.offset)
     assert p == ctypes.sizeof(tms.Params)
     assert h == tms.HIT_BYTES == 128
     assert s == ctypes.sizeof(tms.Stats)
@@ -79,7 +83,7 @@ def test_noalloc_layout_fits_its_static_array():
     needed, reserved = ctypes.c_ulonglong(), ctypes.c_ulonglong()
     lib.tms_noalloc_footprint.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     assert lib.tms_noalloc_footprint(ctypes.byref(needed), ctypes.byref(reserved)) == tms.TMS_OK
-    assert reserved.value == 64 << 20
+    assert reserved.value == 72 << 20
     assert 0 < needed.value <= reserved.value
 
 

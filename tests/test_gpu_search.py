@@ -202,34 +202,6 @@ def test_disjoint_meshes_empty_world():
     assert tms.last_stats()["empty"] == 1
 
 
-@pytest.mark.slow
-def test_config3_full_size_sampled_parity():
-    """4096 x 512 meshes in the benchmark's launch configuration: planted hits
-    with closed forms, no planted near-miss reported, every GPU hit confirmed by
-    the oracle, and exact per-triangle parity on sampled A triangles."""
-    p = synth.config3()
-    OA, OB = oracle.OMesh.from_grid(p.A), oracle.OMesh.from_grid(p.B)
-    g = gpu_search(p)
-    check_sorted_unique(g)
-    keys = {k: h for h, k in enumerate(zip(g["triA"].tolist(), g["triB"].tolist()))}
-    pl = p.planted
-    for j in range(len(pl)):
-        k = (int(pl.triA[j]), int(pl.triB[j]))
-        if int(pl.kind[j]) == 1:
-            assert k not in keys
-            continue
-        h = keys[k]
-        assert np.abs(g["z"][h] - pl.abcd[j].numpy()).max() <= 1e-10
-        assert np.abs(g["P"][h] - pl.P[j].numpy()).max() <= 1e-10 * max(1, np.abs(pl.P[j].numpy()).max())
-    r = oracle.eval_pairs(OA, OB, g["triA"], g["triB"])
-    assert ((r["hit"] == 1) | oracle.in_band(r)).all()
-    rng = np.random.default_rng(11)
-    sample = np.unique(np.concatenate([rng.choice(OA.n_tri_ids, 300, replace=False),
-                                       g["triA"][rng.choice(len(g["triA"]), 300, replace=False)]]))
-    ref = oracle.merge_and_sort(OA, OB, oracle.hits_for_A(OA, OB, sample))
-    compare(OA, OB, g, ref, restrict_A=sample)
-
-
 # ---------------------------------------------------------------------------
 # errors and fault injection (host side; no GPU fault)
 # ---------------------------------------------------------------------------
@@ -275,6 +247,38 @@ def test_capacity_retry_and_injected_errors():
     assert len(h["triA"]) == len(base["triA"])
 
 
+def test_device_wait_runs_out_then_exact():
+    """The hit sort's look-back is the search's one device-side wait.  With
+    inject bit 4 every earlier tile reads as unpublished, so each wait gives up
+    after spin_limit polls: the kernel records the timeout, writes nothing out
+    of bounds and returns (no fault), the merge keeps nothing, and the call
+    reports TMS_ERR_TIMEOUT with the output buffer untouched.  The next call is
+    exact.  2582 raw hits make two sort tiles, so a wait exists."""
+    p = synth.build_pair(777, 384, 128, 384, 128, stretch="exp", n_folds=3, sites=(96, 24), n_hits=0)
+    OA, OB = oracle.OMesh.from_grid(p.A), oracle.OMesh.from_grid(p.B)
+    ref = oracle.search(OA, OB)
+    A = tms.Mesh.from_grid(p.A)
+    B = tms.Mesh.from_grid(p.B)
+    base = gpu_records(tms.search(A, B))
+    assert tms.last_stats()["raw_hits"] > 2048
+    compare(OA, OB, base, ref)
+    out = torch.full((4096, tms.HIT_BYTES), 0xA5, dtype=torch.uint8, device="cuda")
+    for limit in (1, 16):
+        with pytest.raises(tms.TmsError) as e:
+            tms.search(A, B, out=out, inject=16, spin_limit=limit)
+        assert e.value.status == tms.TMS_ERR_TIMEOUT
+        assert "look-back" in str(e.value)
+        torch.cuda.synchronize()
+        assert bool((out == 0xA5).all()), "a timed-out search wrote hit records"
+        again = gpu_records(tms.search(A, B, out=out))
+        for k in base:
+            assert np.array_equal(again[k], base[k]), k
+        out.fill_(0xA5)
+    # the same parameters without the switch: the bounded wait never runs out
+    h = gpu_records(tms.search(A, B, spin_limit=1 << 20))
+    assert list(zip(h["triA"], h["triB"])) == list(zip(base["triA"], base["triB"]))
+
+
 def test_bad_arguments():
     p = cached("c1", synth.config1)
     X = p.A.X.cuda()
@@ -287,3 +291,7 @@ def test_bad_arguments():
     A = tms.Mesh(X, p.A.s)
     with pytest.raises(tms.TmsError):
         tms.search(A, A, cell_mult=0.5)            # cells narrower than faces
+    with pytest.raises(tms.TmsError):
+        tms.search(A, A, spin_limit=-1)
+    with pytest.raises(tms.TmsError):
+        tms.search(A, A, patch=2)
