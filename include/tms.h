@@ -257,6 +257,8 @@ typedef struct {
     long long fp32_solves;  /* triangle pairs through the verified FP32 solve */
     long long sat_tests;    /* triangle pairs through the separating-axis prefilter */
     long long quad_tests;   /* quad candidates through the quad-level prefilter */
+    long long patch_pairs;  /* patch level: patch pairs with overlapping boxes */
+    long long patch_tests;  /* patch level: quad pairs box-tested inside them */
 } tms_stats;
 
 tms_status tms_last_stats(void *stream, tms_stats *out);
@@ -556,9 +558,12 @@ tms_status tms_phase_align(const double *dWr, const double *dWprev, int N, int n
  *   3 bitmap clear           4 face pass: mark A         5 face pass: probe B
  *   6 face pass: probe A (or emit all)  7 cell table: counts and ranks
  *   8 cells and scatter of the face ids
- *   9 candidate emission     10 narrow phase             11 sort hits
- *   12 merge + output        13 counter read-back
- * Writes min(cap, 14) values; *n receives 14. */
+ *   9 candidate emission (patch level: patch pairs)
+ *   10 patch level: quad pairs of the patch pairs (0 otherwise)
+ *   11 narrow phase          12 sort hits
+ *   13 merge + output        14 counter read-back
+ * The face passes, cell table and emission work on patches at the patch
+ * level.  Writes min(cap, 15) values; *n receives 15. */
 tms_status tms_last_stage_ms(void *stream, float *ms, int cap, int *n);
 
 /* Frees the scratch and cached plans created for `stream`; NULL frees those of

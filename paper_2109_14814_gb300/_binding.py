@@ -72,6 +72,8 @@ class Stats(ctypes.Structure):
         ("fp32_solves", _c.c_longlong),
         ("sat_tests", _c.c_longlong),
         ("quad_tests", _c.c_longlong),
+        ("patch_pairs", _c.c_longlong),
+        ("patch_tests", _c.c_longlong),
     ]
 
     def as_dict(self):
@@ -451,7 +453,7 @@ def last_stats(stream=None) -> dict:
 
 
 STAGES = ["init", "face_bounds", "grid_params", "bitmap_clear", "face_mark_A", "face_probe_B",
-          "face_probe_A", "group_count", "group_cells", "emit", "narrow", "sort_hits",
+          "face_probe_A", "group_count", "group_cells", "emit", "patch_quads", "narrow", "sort_hits",
           "merge_output", "readback"]
 
 

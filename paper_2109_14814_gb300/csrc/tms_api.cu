@@ -69,6 +69,13 @@ struct Plan {
     // mesh tables
     int n_meshes = 0;
     MeshDev *d_meshes = nullptr;
+    // patch level: the patch views (one "face" per patch, its box in pbox),
+    // which the cell passes and the grid emission read instead of the meshes
+    bool patch = false;
+    MeshDev *d_pmeshes = nullptr;
+    unsigned char *pbox = nullptr;    // patch boxes of all meshes
+    Cand *ppairs = nullptr;
+    unsigned long long ppair_cap = 0;
     int2 *d_pairs = nullptr;
     PassEntry *d_pass_all = nullptr, *d_pass_A = nullptr, *d_pass_B = nullptr;
     int n_pass_all = 0, n_pass_A = 0, n_pass_B = 0;
@@ -109,7 +116,7 @@ struct Plan {
     cudaStream_t st = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t exec = nullptr;
-    static constexpr int kStages = 14;
+    static constexpr int kStages = 15;
     cudaEvent_t tev[kStages + 1] = {};
     float stage_ms[kStages] = {};
     int kernels = 0;
@@ -119,9 +126,10 @@ struct Plan {
     void free_scratch() {
         void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, crec, tcnt, tstart,
                         sort_scratch, cand, surv, hits, hk, hk2, okeys, hv, hv2,
-                        keep, kscan};
+                        keep, kscan, ppairs};
         for (void *p : ptrs)
             if (p) cudaFree(p);
+        ppairs = nullptr;
         bmA = bmH = nullptr; ek = nullptr; ev = eslot = erank = grouped = nullptr;
         tkey = nullptr; crec = nullptr; tcnt = nullptr; tstart = nullptr;
         sort_scratch = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
@@ -132,7 +140,7 @@ struct Plan {
         if (st) cudaStreamSynchronize(st);
         free_scratch();
         void *ptrs[] = {d_meshes, d_pairs, d_pass_all, d_pass_A, d_pass_B, d_bounds, d_grids,
-                        d_ctr, partials, split, fbox};
+                        d_ctr, partials, split, fbox, d_pmeshes, pbox};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         if (h_ctr) cudaFreeHost(h_ctr);
@@ -169,6 +177,7 @@ struct Plan {
         TMS_CK(dalloc(reinterpret_cast<unsigned char **>(&sort_scratch),
                       radix_scratch_size(hit_cap, 2 * tri_bits + pair_bits)));
         TMS_CK(dalloc(&cand, cand_cap));
+        if (patch) TMS_CK(dalloc(&ppairs, ppair_cap));
         TMS_CK(dalloc(&surv, surv_cap));
         TMS_CK(dalloc(&hits, hit_cap));
         TMS_CK(dalloc(&hk, hit_cap));
@@ -227,7 +236,11 @@ struct Plan {
 
         fa.entries = d_pass_all; fa.n_entries = n_pass_all; fa.total_tiles = tiles_all;
         fa.mode = MODE_BOUNDS;
+        fa.patch = patch ? 1 : 0;
         launch_face_pass(fa, prec, fl, block, s);
+        // the cell passes and the grid emission work on the patches (patch level)
+        fa.patch = 0;
+        if (patch) fa.meshes = d_pmeshes;
         mark(2, s);
         launch_grid_params(d_bounds, d_pairs, nPairs, d_grids, p.cell_mult, s);
         kernels += 2;
@@ -269,9 +282,24 @@ struct Plan {
         ea.cells = crec; ea.vals = grouped;
         ea.grids = d_grids; ea.meshes = d_meshes; ea.pairs = d_pairs; ea.ctr = d_ctr;
         ea.ent_cap = ent_cap; ea.cand = cand; ea.cand_cap = cand_cap; ea.moller = p.moller;
+        ea.cand_ctr = &d_ctr->cand;
+        if (patch) {
+            // patch pairs with overlapping boxes, each once (owner cell)
+            ea.meshes = d_pmeshes; ea.cand = ppairs; ea.cand_cap = ppair_cap;
+            ea.cand_ctr = &d_ctr->ppairs; ea.moller = 0;
+        }
         launch_emit(ea, prec, fl, grid / 2, s);
         kernels += 1;
         mark(10, s);
+        if (patch) {
+            PatchArgs pa;
+            pa.ppairs = ppairs; pa.ppair_cap = ppair_cap; pa.meshes = d_meshes; pa.pairs = d_pairs;
+            pa.ctr = d_ctr; pa.ent_cap = ent_cap; pa.cand = cand; pa.cand_cap = cand_cap;
+            pa.moller = p.moller;
+            launch_patch_quads(pa, prec, grid / 2, s);
+            kernels += 1;
+        }
+        mark(11, s);
 
         NarrowArgs na;
         na.cand = cand; na.cand_cap = cand_cap; na.surv = surv; na.surv_cap = surv_cap;
@@ -280,14 +308,14 @@ struct Plan {
         na.tau = p.tau; na.tri_bits = tri_bits; na.fp32_filter = p.narrow_filter;
         launch_narrow(na, fl, grid / 2, grid * 4, s);
         kernels += 2;
-        mark(11, s);
+        mark(12, s);
 
         // the raw hits are few: a small grid keeps the per-pass fixed cost low
         const bool halt = radix_sort(hk, hv, hk2, hv2, sort_scratch, &d_ctr->raw_hits, hit_cap,
                                      2 * tri_bits + pair_bits, sort_grid, &d_ctr->status,
                                      (unsigned long long)p.spin_limit, (p.inject & 16u) ? 1 : 0, s);
         kernels += 2 + sort_passes_h;
-        mark(12, s);
+        mark(13, s);
         DedupArgs da;
         da.keys = halt ? hk2 : hk; da.vals = halt ? hv2 : hv; da.raw = hits;
         da.meshes = d_meshes; da.pairs = d_pairs; da.ctr = d_ctr; da.raw_cap = hit_cap;
@@ -296,11 +324,11 @@ struct Plan {
         da.offsets = dOffsets; da.n_pairs = nPairs; da.tri_bits = tri_bits; da.tau = p.tau;
         launch_dedup(da, grid, s);
         kernels += 5 + (dOffsets ? 1 : 0);
-        mark(13, s);
+        mark(14, s);
 
         cudaMemcpyAsync(h_ctr, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(h_grid0, d_grids, sizeof(Grid), cudaMemcpyDeviceToHost, s);
-        mark(14, s);
+        mark(15, s);
     }
 
     tms_status run() {
@@ -381,8 +409,10 @@ tms_status check_mesh(tms_mesh m, int device) {
     return TMS_OK;
 }
 
+// a mesh in a pass: bounds-pass tiles over its quads; cell-pass slots over its
+// faces, or over its patches (patch level)
 void fill_pass(std::vector<PassEntry> &v, long long &tiles, long long &fslots, const tms_mesh m,
-               int mesh_index, int pair, int role, int block, int rows, int face_level) {
+               int mesh_index, int pair, int role, int block, int rows, int face_level, bool patch) {
     PassEntry e;
     e.mesh = mesh_index;
     e.pair = pair;
@@ -392,7 +422,8 @@ void fill_pass(std::vector<PassEntry> &v, long long &tiles, long long &fslots, c
     e.tile_base = tiles;
     tiles += (long long)e.tiles_i * tiles_k;
     e.face_base = fslots;
-    e.faces = (long long)face_slots(m->dev, face_level);
+    e.faces = patch ? (long long)((m->dev.nqi + kPatchI - 1) / kPatchI) * ((m->dev.nqk + kPatchK - 1) / kPatchK)
+                    : (long long)face_slots(m->dev, face_level);
     fslots += (e.faces + 31) / 32 * 32;
     v.push_back(e);
 }
@@ -413,6 +444,8 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     const int block = (prm.block_faces == 64 || prm.block_faces == 256) ? prm.block_faces : 128;
     const int rows = prm.tile_rows == 8 ? 8 : 4;
     P->prm.tile_rows = rows;
+    P->patch = prm.patch == 1 && prm.face_level == 1;
+    const bool patch = P->patch;
 
     std::vector<MeshDev> meshes;
     std::vector<int2> pairs;
@@ -425,36 +458,61 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
         meshes.push_back(B[i]->dev);
         pairs.push_back(make_int2(ia, ib));
         const unsigned long long fpq = prm.face_level == 0 ? 2 : 1;
-        P->facesA += fpq * A[i]->dev.nqi * A[i]->dev.nqk;
-        P->facesB += fpq * B[i]->dev.nqi * B[i]->dev.nqk;
+        auto cells_of = [&](const MeshDev &d) -> unsigned long long {
+            if (patch)
+                return (unsigned long long)((d.nqi + kPatchI - 1) / kPatchI) * ((d.nqk + kPatchK - 1) / kPatchK);
+            return fpq * (unsigned long long)d.nqi * d.nqk;
+        };
+        P->facesA += cells_of(A[i]->dev);
+        P->facesB += cells_of(B[i]->dev);
         max_tri = std::max(max_tri, 2ULL * A[i]->dev.N * A[i]->dev.nqk);
         max_tri = std::max(max_tri, 2ULL * B[i]->dev.N * B[i]->dev.nqk);
     }
     const int fl = prm.face_level;
     for (int i = 0; i < nPairs; ++i) {
-        fill_pass(pall, P->tiles_all, P->fslots_all, A[i], pairs[i].x, i, 0, block, rows, fl);
-        fill_pass(pall, P->tiles_all, P->fslots_all, B[i], pairs[i].y, i, 1, block, rows, fl);
-        fill_pass(pa, P->tiles_A, P->fslots_A, A[i], pairs[i].x, i, 0, block, rows, fl);
-        fill_pass(pb, P->tiles_B, P->fslots_B, B[i], pairs[i].y, i, 1, block, rows, fl);
+        fill_pass(pall, P->tiles_all, P->fslots_all, A[i], pairs[i].x, i, 0, block, rows, fl, patch);
+        fill_pass(pall, P->tiles_all, P->fslots_all, B[i], pairs[i].y, i, 1, block, rows, fl, patch);
+        fill_pass(pa, P->tiles_A, P->fslots_A, A[i], pairs[i].x, i, 0, block, rows, fl, patch);
+        fill_pass(pb, P->tiles_B, P->fslots_B, B[i], pairs[i].y, i, 1, block, rows, fl, patch);
     }
     // FP32 split vertex copies (32 bytes per view vertex) and face boxes (32 or
     // 64 bytes per face slot), written by the bounds pass
     const unsigned long long box_bytes = prm.precision == 1 ? 32 : 64;
-    std::vector<unsigned long long> fbox_off;
-    unsigned long long fbox_total = 0;
+    std::vector<unsigned long long> fbox_off, pbox_off;
+    unsigned long long fbox_total = 0, pbox_total = 0;
     for (auto &md : meshes) {
         P->split_off.push_back(P->split_total);
         P->split_total += 2ULL * (unsigned long long)md.N * (unsigned long long)md.M;
         fbox_off.push_back(fbox_total);
         fbox_total += (face_slots(md, fl) * box_bytes + 255) / 256 * 256;
+        md.npi = patch ? (md.nqi + kPatchI - 1) / kPatchI : 0;
+        md.npk = patch ? (md.nqk + kPatchK - 1) / kPatchK : 0;
+        md.pbox = nullptr;
+        pbox_off.push_back(pbox_total);
+        pbox_total += ((unsigned long long)md.npi * md.npk * box_bytes + 255) / 256 * 256;
     }
+    std::vector<MeshDev> pmeshes;
     {
         cudaError_t se = dalloc(&P->split, P->split_total);
         if (se == cudaSuccess) se = dalloc(&P->fbox, fbox_total);
+        if (se == cudaSuccess && patch) se = dalloc(&P->pbox, pbox_total);
         if (se != cudaSuccess) { g_err = cudaGetErrorString(se); delete P; return TMS_ERR_CUDA; }
         for (size_t i = 0; i < meshes.size(); ++i) {
             meshes[i].split = P->split + P->split_off[i];
             meshes[i].fbox = P->fbox + fbox_off[i];
+            if (patch) meshes[i].pbox = P->pbox + pbox_off[i];
+        }
+        // a patch view is a mesh of npi x npk quad-like slots, all valid
+        for (const MeshDev &md : meshes) {
+            MeshDev v = md;
+            v.N = md.npi;
+            v.M = md.npk + 1;
+            v.periodic = 1;
+            v.nqi = md.npi;
+            v.nqk = md.npk;
+            v.fbox = md.pbox;
+            v.split = nullptr;
+            pmeshes.push_back(v);
         }
     }
     P->n_meshes = (int)meshes.size();
@@ -476,6 +534,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     cudaError_t e;
 #define TMS_PCK(call) do { if ((e = (call)) != cudaSuccess) { g_err = cudaGetErrorString(e); delete P; return TMS_ERR_CUDA; } } while (0)
     TMS_PCK(dalloc(&P->d_meshes, meshes.size()));
+    TMS_PCK(dalloc(&P->d_pmeshes, pmeshes.size()));
     TMS_PCK(dalloc(&P->d_pairs, pairs.size()));
     TMS_PCK(dalloc(&P->d_pass_all, pall.size()));
     TMS_PCK(dalloc(&P->d_pass_A, pa.size()));
@@ -487,6 +546,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     TMS_PCK(cudaMallocHost((void **)&P->h_ctr, sizeof(Counters)));
     TMS_PCK(cudaMallocHost((void **)&P->h_grid0, sizeof(Grid)));
     TMS_PCK(cudaMemcpy(P->d_meshes, meshes.data(), meshes.size() * sizeof(MeshDev), cudaMemcpyHostToDevice));
+    TMS_PCK(cudaMemcpy(P->d_pmeshes, pmeshes.data(), pmeshes.size() * sizeof(MeshDev), cudaMemcpyHostToDevice));
     TMS_PCK(cudaMemcpy(P->d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice));
     TMS_PCK(cudaMemcpy(P->d_pass_all, pall.data(), pall.size() * sizeof(PassEntry), cudaMemcpyHostToDevice));
     TMS_PCK(cudaMemcpy(P->d_pass_A, pa.data(), pa.size() * sizeof(PassEntry), cudaMemcpyHostToDevice));
@@ -500,12 +560,21 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
 
     const unsigned long long faces = P->facesA + P->facesB;
     unsigned long long ent = prm.entry_capacity > 0 ? (unsigned long long)prm.entry_capacity
+                             : patch ? 4 * faces + (1 << 16)
                              : (prm.cell_filter ? std::max<unsigned long long>(1 << 16, faces / 2)
                                                 : 4 * faces + (1 << 16));
     if (prm.inject & 1u) ent = 1;
     P->ent_cap = std::min<unsigned long long>(ent, 0x7fffffffULL);
+    // patch level: candidates are quad pairs, about one per quad of A
+    const unsigned long long quadsA = [&] {
+        unsigned long long q = 0;
+        for (int i = 0; i < nPairs; ++i) q += (unsigned long long)A[i]->dev.nqi * A[i]->dev.nqk;
+        return q;
+    }();
     P->cand_cap = prm.cand_capacity > 0 ? (unsigned long long)prm.cand_capacity
-                                        : std::max<unsigned long long>(1 << 16, 2 * P->ent_cap);
+                  : patch ? std::max<unsigned long long>(1 << 16, quadsA + quadsA / 4)
+                          : std::max<unsigned long long>(1 << 16, 2 * P->ent_cap);
+    P->ppair_cap = patch ? std::max<unsigned long long>(1 << 16, 4 * faces) : 0;
     P->hit_cap = prm.hit_capacity > 0 ? (unsigned long long)prm.hit_capacity
                                       : std::max<unsigned long long>(1 << 14, P->cand_cap / 16);
     P->surv_cap = std::max<unsigned long long>(1 << 16, P->cand_cap / 8);
@@ -562,6 +631,7 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
     if (!(g_configured_mask & (1 << device))) {
         TMS_CK(configure_face_pass());
         configure_emit();
+        configure_patch_quads();
         configure_narrow();
         g_configured_mask |= 1 << device;
     }
@@ -606,6 +676,10 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
             P->cand_cap = std::max(P->cand_cap, 2 * P->ent_cap);
             grow = true;
         }
+        if (!grow && P->patch && c.ppairs > P->ppair_cap) {
+            P->ppair_cap = c.ppairs + c.ppairs / 4 + 1024;
+            grow = true;
+        }
         if (!grow && c.cand > P->cand_cap) {
             P->cand_cap = c.cand + c.cand / 4 + 1024;
             grow = true;
@@ -640,6 +714,8 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
     st.fp32_solves = (long long)c.fp32;
     st.sat_tests = (long long)c.sat;
     st.quad_tests = (long long)c.quad;
+    st.patch_pairs = (long long)c.ppairs;
+    st.patch_tests = (long long)c.ptests;
     st.raw_hits = (long long)c.raw_hits;
     st.hits = (long long)c.out;
     for (int d = 0; d < 4; ++d) st.grid_n[d] = P->h_grid0->n[d];
@@ -649,7 +725,7 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
     g_stats[user] = st;
     if (prm.timing) g_stage_ms[user] = std::vector<float>(P->stage_ms, P->stage_ms + Plan::kStages);
     if (c.entries > P->ent_cap || c.cand > P->cand_cap || c.fp64 > P->surv_cap ||
-        c.raw_hits > P->hit_cap) {
+        c.raw_hits > P->hit_cap || (P->patch && c.ppairs > P->ppair_cap)) {
         g_err = "scratch capacity still exceeded after retries";
         *nHits = (long long)c.out;
         return TMS_ERR_CAPACITY;
@@ -691,6 +767,7 @@ void tms_params_default(tms_params *p) {
     p->use_graph = 1;
     p->block_faces = 128;
     p->tile_rows = 4;
+    p->patch = 1;
 }
 
 const char *tms_status_str(tms_status s) {

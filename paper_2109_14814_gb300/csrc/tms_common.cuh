@@ -61,7 +61,18 @@ struct MeshDev {
     int nqi;              // quads per row (N or N-1)
     int nqk;              // quad rows (M-1)
     int pad;
+    void *pbox;           // plan scratch (patch level): per patch of kPatchI x
+                          // kPatchK quads the union of their boxes, in the
+                          // format of fbox, written by the bounds pass; slot =
+                          // patch row * npi + patch column
+    int npi;              // patches per quad row, ceil(nqi / kPatchI) (0: none)
+    int npk;              // patch rows, ceil(nqk / kPatchK)
 };
+
+// Patch level of the broad phase: quads grouped into patches of kPatchI quads
+// along theta by kPatchK quad rows -- 32 quads, one per lane of a warp.
+constexpr int kPatchI = 8;
+constexpr int kPatchK = 4;
 
 struct PassEntry {        // one mesh processed by a face pass
     int mesh;             // index into the mesh table
@@ -108,6 +119,8 @@ struct Counters {
     unsigned long long sat;        // triangle pairs through the separating-axis prefilter
     unsigned long long quad;       // quad candidates through the quad-level prefilter
     unsigned long long claimed;    // cell-table slots claimed by this search
+    unsigned long long ppairs;     // patch pairs with overlapping boxes (patch level)
+    unsigned long long ptests;     // quad-pair box tests inside those patch pairs
     unsigned long long raw_hits;
     unsigned long long out;
     unsigned int status;
@@ -356,6 +369,8 @@ struct FacePassArgs {
     uint32_t *ent_val;             // face id
     Counters *ctr;
     unsigned long long ent_cap;
+    int patch;                     // bounds pass: also the patch boxes, and the
+                                   // widest patch (not face) extent for the grid
 };
 
 void launch_face_pass(const FacePassArgs &a, int precision, int face_level, int block,
@@ -439,11 +454,31 @@ struct EmitArgs {
     unsigned long long ent_cap;
     Cand *cand;
     unsigned long long cand_cap;
+    unsigned long long *cand_ctr;  // the output's counter (candidates, or patch pairs)
     int moller;
 };
 // whole waves of resident blocks on `sms` SMs
 void launch_emit(const EmitArgs &a, int precision, int face_level, int sms, cudaStream_t st);
 void configure_emit();
+
+// Quad pairs of the patch pairs (patch level): one warp per patch pair, one
+// lane per quad of each patch; each side's quads are first tested against the
+// other patch's box, then every surviving pair, and the box-overlapping quad
+// pairs are appended as candidates.  A quad pair lies in exactly one patch
+// pair, so each is emitted once.
+struct PatchArgs {
+    const Cand *ppairs;            // patch pairs (faceA, faceB = patch ids)
+    unsigned long long ppair_cap;
+    const MeshDev *meshes;         // the meshes (quad and patch boxes)
+    const int2 *pairs;
+    Counters *ctr;
+    unsigned long long ent_cap;
+    Cand *cand;
+    unsigned long long cand_cap;
+    int moller;
+};
+void launch_patch_quads(const PatchArgs &a, int precision, int sms, cudaStream_t st);
+void configure_patch_quads();
 
 struct NarrowArgs {
     const Cand *cand;

@@ -152,22 +152,53 @@ struct GridView<0> {
     }
 };
 
-// the box of a face into its slot of the mesh's face-box array
+// the box of a face (or patch) into slot `face` of a box array
 template <int PREC>
-__device__ __forceinline__ void write_fbox(const MeshDev &m, uint32_t face, const BoxT<PREC> &b);
+__device__ __forceinline__ void write_box(void *arr, uint32_t face, const BoxT<PREC> &b);
 template <>
-__device__ __forceinline__ void write_fbox<1>(const MeshDev &m, uint32_t face, const BoxT<1> &b) {
-    float4 *p = reinterpret_cast<float4 *>(m.fbox) + 2 * (size_t)face;
+__device__ __forceinline__ void write_box<1>(void *arr, uint32_t face, const BoxT<1> &b) {
+    float4 *p = reinterpret_cast<float4 *>(arr) + 2 * (size_t)face;
     p[0] = make_float4(b.lo[0], b.lo[1], b.lo[2], b.lo[3]);
     p[1] = make_float4(b.hi[0], b.hi[1], b.hi[2], b.hi[3]);
 }
 template <>
-__device__ __forceinline__ void write_fbox<0>(const MeshDev &m, uint32_t face, const BoxT<0> &b) {
-    double2 *p = reinterpret_cast<double2 *>(m.fbox) + 4 * (size_t)face;
+__device__ __forceinline__ void write_box<0>(void *arr, uint32_t face, const BoxT<0> &b) {
+    double2 *p = reinterpret_cast<double2 *>(arr) + 4 * (size_t)face;
     p[0] = make_double2(b.lo[0], b.lo[1]);
     p[1] = make_double2(b.lo[2], b.lo[3]);
     p[2] = make_double2(b.hi[0], b.hi[1]);
     p[3] = make_double2(b.hi[2], b.hi[3]);
+}
+template <int PREC>
+__device__ __forceinline__ void write_fbox(const MeshDev &m, uint32_t face, const BoxT<PREC> &b) {
+    write_box<PREC>(m.fbox, face, b);
+}
+
+// a box that contains nothing (identity of the union)
+__device__ __forceinline__ void box_empty(BoxT<1> &b) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) { b.lo[d] = __int_as_float(0x7f800000); b.hi[d] = -b.lo[d]; }
+}
+__device__ __forceinline__ void box_empty(BoxT<0> &b) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) { b.lo[d] = __longlong_as_double(0x7ff0000000000000LL); b.hi[d] = -b.lo[d]; }
+}
+template <int PREC>
+__device__ __forceinline__ void box_union(BoxT<PREC> &b, const BoxT<PREC> &x) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) { b.lo[d] = min(b.lo[d], x.lo[d]); b.hi[d] = max(b.hi[d], x.hi[d]); }
+}
+// union over the kPatchI lanes of a patch (aligned groups of lanes)
+template <int PREC>
+__device__ __forceinline__ void box_reduce_patch(BoxT<PREC> &b) {
+#pragma unroll
+    for (int off = 1; off < kPatchI; off <<= 1) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            b.lo[d] = min(b.lo[d], __shfl_xor_sync(0xffffffffu, b.lo[d], off));
+            b.hi[d] = max(b.hi[d], __shfl_xor_sync(0xffffffffu, b.hi[d], off));
+        }
+    }
 }
 
 template <int PREC>
@@ -201,13 +232,20 @@ struct BoundAcc<1> {
         seen = 0;
     }
     __device__ void add(const BoxT<1> &b) {
+        add_bounds(b);
+        add_width(b);
+    }
+    __device__ void add_bounds(const BoxT<1> &b) {
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
             lo[d] = fminf(lo[d], b.lo[d]);
             hi[d] = fmaxf(hi[d], b.hi[d]);
-            w[d] = fmaxf(w[d], b.hi[d] - b.lo[d]);
         }
         seen = 1;
+    }
+    __device__ void add_width(const BoxT<1> &b) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) w[d] = fmaxf(w[d], b.hi[d] - b.lo[d]);
     }
     __device__ double get_lo(int d) const { return (double)lo[d]; }
     __device__ double get_hi(int d) const { return (double)hi[d]; }
@@ -223,13 +261,20 @@ struct BoundAcc<0> {
         seen = 0;
     }
     __device__ void add(const BoxT<0> &b) {
+        add_bounds(b);
+        add_width(b);
+    }
+    __device__ void add_bounds(const BoxT<0> &b) {
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
             lo[d] = fmin(lo[d], b.lo[d]);
             hi[d] = fmax(hi[d], b.hi[d]);
-            w[d] = fmax(w[d], b.hi[d] - b.lo[d]);
         }
         seen = 1;
+    }
+    __device__ void add_width(const BoxT<0> &b) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) w[d] = fmax(w[d], b.hi[d] - b.lo[d]);
     }
     __device__ double get_lo(int d) const { return lo[d]; }
     __device__ double get_hi(int d) const { return hi[d]; }
@@ -320,7 +365,48 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
     const int t = threadIdx.x;
     const bool col_valid = t < cols_q;
     const int i = i0 + t;
-    if (FACE == 1 && col_valid) {
+    if (FACE == 1 && a.patch) {
+        // quad faces with patches: as below, and each column's box over the
+        // patch row (kPatchK quad rows; tiles are whole patch rows) united across
+        // the kPatchI lanes of the patch (every lane of the block takes part:
+        // the row loop and its shuffles are uniform).  The widest extent the
+        // grid needs is then the widest patch's.
+        BoxT<PREC> prev, pcol;
+        box_empty(prev);
+        box_empty(pcol);
+        if (col_valid) {
+            box_init(prev, sv[t]);
+            box_add(prev, sv[t + 1]);
+        }
+        for (int r = 0; r < rows_q; ++r) {
+            if (col_valid) {
+                BoxT<PREC> next;
+                box_init(next, sv[(r + 1) * W + t]);
+                box_add(next, sv[(r + 1) * W + t + 1]);
+                BoxT<PREC> bq;
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    bq.lo[d] = min(prev.lo[d], next.lo[d]);
+                    bq.hi[d] = max(prev.hi[d], next.hi[d]);
+                }
+                const uint32_t q = (uint32_t)(kq0 + r) * (uint32_t)m.N + (uint32_t)i;
+                acc.add_bounds(bq);
+                write_fbox<PREC>(m, q, bq);
+                box_union<PREC>(pcol, bq);
+                prev = next;
+            }
+            if ((r % kPatchK) == kPatchK - 1 || r == rows_q - 1) {
+                box_reduce_patch<PREC>(pcol);
+                if (col_valid && (t % kPatchI) == 0) {
+                    const uint32_t p = (uint32_t)((kq0 + r) / kPatchK) * (uint32_t)m.npi +
+                                       (uint32_t)(i / kPatchI);
+                    write_box<PREC>(m.pbox, p, pcol);
+                    acc.add_width(pcol);
+                }
+                box_empty(pcol);
+            }
+        }
+    } else if (FACE == 1 && col_valid) {
         // quad faces: the extremes of the two vertex columns of each row once, each
         // quad box from two consecutive rows (exact: min and max only)
         BoxT<PREC> prev;
@@ -341,7 +427,7 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
             write_fbox<PREC>(m, q, bq);
             prev = next;
         }
-    } else if (col_valid) {
+    } else if (FACE == 0 && col_valid) {
         for (int r = 0; r < rows_q; ++r) {
             const int k = kq0 + r;
             const Vtx<PREC> va = sv[r * W + t];             // (i, k)

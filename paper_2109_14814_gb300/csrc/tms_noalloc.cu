@@ -17,6 +17,10 @@
 // TMS_ERR_ARG (mesh too large) or TMS_ERR_CAPACITY (a stage overflowed) with a
 // message in tms_last_error(); it never grows anything.
 //
+// The broad phase runs on the faces themselves (the patch level of tms_search
+// is not used: tms_params.patch is ignored); the hit set and every hit record
+// are the same.
+//
 // Every call shares the one array and leaves its contents behind; each call
 // clears what must start at zero (counters, occupancy bitmaps).  Calls whose
 // GPU work overlaps -- on two streams, or from two host threads -- race on the
@@ -327,6 +331,7 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     ea.cells = b.crec; ea.vals = b.grouped;
     ea.grids = b.grids; ea.meshes = b.tables->meshes; ea.pairs = b.tables->pairs; ea.ctr = b.ctr;
     ea.ent_cap = kEntCap; ea.cand = b.cand; ea.cand_cap = kCandCap; ea.moller = p.moller;
+    ea.cand_ctr = &b.ctr->cand;
     launch_emit(ea, p.precision, p.face_level, grid / 2, s);
     NarrowArgs na;
     na.cand = b.cand; na.cand_cap = kCandCap; na.surv = b.surv; na.surv_cap = kSurvCap;

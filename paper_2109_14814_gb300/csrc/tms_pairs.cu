@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps, (PREC == 1 && !MOLLER) ? 5 : 
     auto flush = [&]() {
         __syncwarp();
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&a.ctr->cand, (unsigned long long)staged);
+        if (lane == 0) base = atomicAdd(a.cand_ctr, (unsigned long long)staged);
         base = __shfl_sync(FULL, base, 0);
         for (unsigned k = lane; k < staged; k += 32)
             if (base + k < cap) cand_out[base + k] = stage[k];
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps, (PREC == 1 && !MOLLER) ? 5 : 
         if (total > kStageCap) {
             // a dense tile: its candidates straight to one reserved range
             unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(&a.ctr->cand, (unsigned long long)total);
+            if (lane == 0) base = atomicAdd(a.cand_ctr, (unsigned long long)total);
             base = __shfl_sync(FULL, base, 0);
             unsigned long long pos = base + incl - cnt;
             for (uint32_t k = K; k; k &= k - 1, ++pos)
@@ -383,7 +383,153 @@ void emit_waves(const EmitArgs &a, int face_level, int sms, cudaStream_t st) {
         a, face_level);
 }
 
+// ---------------------------------------------------------------------------
+// quad pairs of the patch pairs (patch level)
+// ---------------------------------------------------------------------------
+constexpr int kPatchWarps = 8;
+constexpr unsigned kPatchFlush = 64;   // staged candidates per atomic
+
+// One warp per patch pair, grid-stride over the pairs.  Lane l holds quad
+// (row l / kPatchI, column l % kPatchI) of each patch.  A quad whose box misses
+// the other patch's box cannot overlap any quad of it (the patch box holds
+// them all), so each side is first cut to its quads that meet the other
+// patch; the pairs of the survivors (nA x nB of them, 32 per round, pair t =
+// (t / nB, t % nB)) take the box test of Sec. 6.2.2, optionally the Moller
+// test of Sec. 6.2.3, and are appended through a per-warp stage.
+template <int PREC, bool MOLLER>
+__global__ void __launch_bounds__(32 * kPatchWarps) k_patch_quads(PatchArgs a) {
+    __shared__ EBox<PREC> sA[kPatchWarps][32], sB[kPatchWarps][32];
+    __shared__ uint32_t sQA[kPatchWarps][32], sQB[kPatchWarps][32];
+    __shared__ Cand sOut[kPatchWarps][kPatchFlush + 32];
+    // nothing to do after an overflow of the patch-level grid (the host retries)
+    if (a.ctr->entries > a.ent_cap || a.ctr->pair_slots > kMaxPairSlots) return;
+    const unsigned long long n = clamp_count(&a.ctr->ppairs, a.ppair_cap);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    const unsigned long long gw = blockIdx.x * (unsigned long long)kPatchWarps + warp;
+    const unsigned long long nw = (unsigned long long)gridDim.x * kPatchWarps;
+    const int r = lane / kPatchI, c = lane % kPatchI;
+    Cand *stage = sOut[warp];
+    unsigned staged = 0;
+    unsigned long long tests = 0;
+    Cand *const cand_out = a.cand;
+    const unsigned long long cap = a.cand_cap;
+    auto store = [cand_out, cap](unsigned long long pos, const Cand &rec) {
+        if (pos < cap) cand_out[pos] = rec;
+    };
+    uint32_t cached_pair = 0xFFFFFFFFu;
+    const void *fbA = nullptr, *fbB = nullptr, *pbA = nullptr, *pbB = nullptr;
+    int NA = 1, nqiA = 0, nqkA = 0, npiA = 1, NB = 1, nqiB = 0, nqkB = 0, npiB = 1;
+    int2 pr = make_int2(0, 0);
+    for (unsigned long long j = gw; j < n; j += nw) {
+        const Cand pp = a.ppairs[j];
+        if (pp.pair != cached_pair) {
+            pr = a.pairs[pp.pair];
+            const MeshDev &ma = a.meshes[pr.x];
+            const MeshDev &mb = a.meshes[pr.y];
+            fbA = ma.fbox; pbA = ma.pbox; NA = ma.N; nqiA = ma.nqi; nqkA = ma.nqk; npiA = ma.npi;
+            fbB = mb.fbox; pbB = mb.pbox; NB = mb.N; nqiB = mb.nqi; nqkB = mb.nqk; npiB = mb.npi;
+            cached_pair = pp.pair;
+        }
+        const uint32_t pka = pp.faceA / (uint32_t)npiA, pia = pp.faceA - pka * (uint32_t)npiA;
+        const uint32_t pkb = pp.faceB / (uint32_t)npiB, pib = pp.faceB - pkb * (uint32_t)npiB;
+        const int kqa = (int)pka * kPatchK + r, iqa = (int)pia * kPatchI + c;
+        const int kqb = (int)pkb * kPatchK + r, iqb = (int)pib * kPatchI + c;
+        const bool va = kqa < nqkA && iqa < nqiA, vb = kqb < nqkB && iqb < nqiB;
+        const uint32_t qa = (uint32_t)kqa * (uint32_t)NA + (uint32_t)iqa;
+        const uint32_t qb = (uint32_t)kqb * (uint32_t)NB + (uint32_t)iqb;
+        EBox<PREC> ba, bb, PA, PB;
+        PA.load(pbA, pp.faceA);
+        PB.load(pbB, pp.faceB);
+        ba.set_empty();
+        bb.set_empty();
+        if (va) ba.load(fbA, qa);
+        if (vb) bb.load(fbB, qb);
+        const bool sa = va && boxes_overlap(ba, PB);
+        const bool sb = vb && boxes_overlap(bb, PA);
+        const uint32_t mA = __ballot_sync(FULL, sa), mB = __ballot_sync(FULL, sb);
+        if (!mA || !mB) continue;
+        const uint32_t nA = __popc(mA), nB = __popc(mB);
+        __syncwarp();                          // the previous pair's survivors are read
+        if (sa) {
+            const int k = __popc(mA & lt);
+            sA[warp][k] = ba;
+            sQA[warp][k] = qa;
+        }
+        if (sb) {
+            const int k = __popc(mB & lt);
+            sB[warp][k] = bb;
+            sQB[warp][k] = qb;
+        }
+        __syncwarp();
+        const uint32_t T = nA * nB;
+        tests += T;
+        // t / nB for t < 1024 <= 2^10: ceil(2^32 / nB) * t / 2^32 errs by less
+        // than 2^-22, below the 1/32 gap to the next integer
+        const unsigned long long magic = ((1ULL << 32) + nB - 1) / nB;
+        for (uint32_t base = 0; base < T; base += 32) {
+            const uint32_t t = base + lane;
+            bool ov = false;
+            uint32_t ia = 0, ib = 0;
+            if (t < T) {
+                ia = (uint32_t)(((unsigned long long)t * magic) >> 32);
+                ib = t - ia * nB;
+                ov = boxes_overlap(sA[warp][ia], sB[warp][ib]);
+                if (MOLLER && ov)
+                    ov = !moller_reject(a.meshes[pr.x], sQA[warp][ia], a.meshes[pr.y], sQB[warp][ib], 1);
+            }
+            Cand cd;
+            cd.faceA = sQA[warp][ia];
+            cd.faceB = sQB[warp][ib];
+            cd.pair = pp.pair;
+            cd.pad = 0;
+            stage_push<kPatchFlush>(stage, staged, ov, cd, &a.ctr->cand, store);
+        }
+    }
+    __syncwarp();
+    stage_flush<kPatchFlush>(stage, staged, &a.ctr->cand, store);
+    for (int off = 16; off > 0; off >>= 1) tests += __shfl_xor_sync(FULL, tests, off);
+    if (lane == 0 && tests) atomicAdd(&a.ctr->ptests, tests);
+}
+
+int g_patch_resident[2][2] = {};
+
+template <int PREC, bool MOLLER>
+int patch_resident() {
+    int &res = g_patch_resident[PREC][MOLLER ? 1 : 0];
+    if (res == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_patch_quads<PREC, MOLLER>, 32 * kPatchWarps,
+                                                          0) != cudaSuccess || nb < 1)
+            nb = 1;
+        res = nb;
+    }
+    return res;
+}
+
+template <int PREC, bool MOLLER>
+void patch_waves(const PatchArgs &a, int sms, cudaStream_t st) {
+    k_patch_quads<PREC, MOLLER><<<sms * patch_resident<PREC, MOLLER>(), 32 * kPatchWarps, 0, st>>>(a);
+}
+
 }  // namespace
+
+void configure_patch_quads() {
+    patch_resident<0, false>();
+    patch_resident<0, true>();
+    patch_resident<1, false>();
+    patch_resident<1, true>();
+}
+
+void launch_patch_quads(const PatchArgs &a, int precision, int sms, cudaStream_t st) {
+    if (precision == 1) {
+        if (a.moller) patch_waves<1, true>(a, sms, st);
+        else patch_waves<1, false>(a, sms, st);
+    } else {
+        if (a.moller) patch_waves<0, true>(a, sms, st);
+        else patch_waves<0, false>(a, sms, st);
+    }
+}
 
 // Looks up the emission's resident blocks per SM once, outside stream capture
 // (a failed lookup leaves one block per SM).

@@ -57,7 +57,8 @@ def test_struct_layouts_match_ctypes(tmp_path):
 
 def test_defaults_and_status_strings():
     p = tms.params()
-    assert (p.precision, p.face_level, p.cell_filter, p.narrow_filter, p.use_graph) == (1, 1, 1, 1, 1)
+    assert (p.precision, p.face_level, p.cell_filter, p.narrow_filter, p.use_graph, p.patch) == (1, 1, 1, 1, 1, 1)
+    assert p.spin_limit == 0 and p.autotune_cache is None
     assert abs(p.tau - 1e-12) < 1e-30 and p.cell_mult > 1.0
     assert tms.status_str(tms.TMS_ERR_CAPACITY) == "capacity exceeded"
     assert "sm_103a" in tms.version()

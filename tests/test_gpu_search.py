@@ -105,13 +105,21 @@ VARIANTS = [
     dict(block_faces=256),
     dict(tile_rows=4),
     dict(use_graph=0),
+    dict(patch=0),
+    dict(patch=0, precision=0),
+    dict(patch=0, moller=1),
+    dict(patch=0, cell_filter=0),
+    dict(patch=0, cell_mult=2.0),
+    dict(block_faces=64, tile_rows=8),
+    dict(block_faces=256, tile_rows=8, precision=0),
 ]
 
 
 @pytest.mark.parametrize("variant", VARIANTS, ids=lambda v: ",".join(f"{k}={x}" for k, x in v.items()))
 def test_variants_same_hit_set(variant):
-    """The hit set does not depend on precision mode, face level, Moller test,
-    occupancy filter, FP32 pre-solve, cell size, tiling or graph use."""
+    """The hit set does not depend on precision mode, face level, broad-phase
+    level (faces or patches in the grid), Moller test, occupancy filter, FP32
+    pre-solve, cell size, tiling or graph use."""
     p = cached("c2", synth.config2)
     OA, OB, ref = oracle_hits("c2", p)
     base = gpu_search(p)
@@ -128,6 +136,8 @@ def test_ragged_tiles_and_open_strip_against_bruteforce():
     ref = oracle.search(OA, OB, method="brute")
     g = gpu_search(p, block_faces=64, tile_rows=8)
     compare(OA, OB, g, ref)
+    for kw in (dict(patch=0), dict(patch=1, tile_rows=4), dict(patch=1, precision=0)):
+        compare(OA, OB, gpu_search(p, **kw), ref)
     # open strip version of A
     Ao = synth.MeshGrid(p.A.X, p.A.s, periodic=False)
     OAo = oracle.OMesh.from_grid(Ao)
@@ -156,19 +166,22 @@ def test_minimal_meshes():
         B = synth.MeshGrid(XB, torch.tensor([0.0, 1.0], dtype=torch.float64))
         OA, OB = oracle.OMesh.from_grid(A), oracle.OMesh.from_grid(B)
         ref = oracle.search(OA, OB, method="brute")
-        g = gpu_search(synth.MeshPair(A, B, None))
-        compare(OA, OB, g, ref)
+        for patch in (0, 1):
+            g = gpu_search(synth.MeshPair(A, B, None), patch=patch)
+            compare(OA, OB, g, ref)
 
 
+@pytest.mark.parametrize("patch", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_dense_cells_every_overlap_emitted_once(precision):
+def test_dense_cells_every_overlap_emitted_once(precision, patch):
     """Both meshes inside one small ball: 89% of all quad pairs have overlapping
     boxes, the grid has 1 x 2 x 2 x 1 cells and every face lies in several of
     them, and one 32 x 32 tile keeps about 980 pairs (more than the emission's
     per-warp stage holds, so its dense-tile path writes them).  Every
     box-overlapping pair must be a candidate exactly once (the nearest
     non-overlapping pair is 1.6e-6 apart, far above FP32 rounding), and the hits
-    must match brute force."""
+    must match brute force.  The same holds at the patch level: a quad pair
+    lies in exactly one patch pair, which the patch-level grid finds once."""
     g0 = torch.Generator().manual_seed(11)
     XA = 0.01 * torch.randn(4, 13, 12, generator=g0, dtype=torch.float64)
     XB = 0.01 * torch.randn(4, 13, 12, generator=g0, dtype=torch.float64)
@@ -176,7 +189,7 @@ def test_dense_cells_every_overlap_emitted_once(precision):
     A, B = synth.MeshGrid(XA, s), synth.MeshGrid(XB, s)
     OA, OB = oracle.OMesh.from_grid(A), oracle.OMesh.from_grid(B)
     ref = oracle.search(OA, OB, method="brute")
-    g = gpu_search(synth.MeshPair(A, B, None), precision=precision)
+    g = gpu_search(synth.MeshPair(A, B, None), precision=precision, patch=patch)
     compare(OA, OB, g, ref)
 
     def quad_boxes(X):
