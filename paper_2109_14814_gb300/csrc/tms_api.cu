@@ -74,8 +74,10 @@ struct Plan {
     bool patch = false;
     MeshDev *d_pmeshes = nullptr;
     unsigned char *pbox = nullptr;    // patch boxes of all meshes
-    Cand *ppairs = nullptr;
+    Cand *ppairs = nullptr, *ppairs_sorted = nullptr;
     unsigned long long ppair_cap = 0;
+    uint32_t *pp_rank = nullptr, *pp_cnt = nullptr, *pp_off = nullptr, *d_abase = nullptr;
+    unsigned long long *d_aslots = nullptr;
     int2 *d_pairs = nullptr;
     PassEntry *d_pass_all = nullptr, *d_pass_A = nullptr, *d_pass_B = nullptr;
     int n_pass_all = 0, n_pass_A = 0, n_pass_B = 0;
@@ -126,10 +128,11 @@ struct Plan {
     void free_scratch() {
         void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, crec, tcnt, tstart,
                         sort_scratch, cand, surv, hits, hk, hk2, okeys, hv, hv2,
-                        keep, kscan, ppairs};
+                        keep, kscan, ppairs, ppairs_sorted, pp_rank};
         for (void *p : ptrs)
             if (p) cudaFree(p);
-        ppairs = nullptr;
+        ppairs = ppairs_sorted = nullptr;
+        pp_rank = nullptr;
         bmA = bmH = nullptr; ek = nullptr; ev = eslot = erank = grouped = nullptr;
         tkey = nullptr; crec = nullptr; tcnt = nullptr; tstart = nullptr;
         sort_scratch = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
@@ -140,7 +143,8 @@ struct Plan {
         if (st) cudaStreamSynchronize(st);
         free_scratch();
         void *ptrs[] = {d_meshes, d_pairs, d_pass_all, d_pass_A, d_pass_B, d_bounds, d_grids,
-                        d_ctr, partials, split, fbox, d_pmeshes, pbox};
+                        d_ctr, partials, split, fbox, d_pmeshes, pbox, pp_cnt, pp_off, d_abase,
+                        d_aslots};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         if (h_ctr) cudaFreeHost(h_ctr);
@@ -177,7 +181,11 @@ struct Plan {
         TMS_CK(dalloc(reinterpret_cast<unsigned char **>(&sort_scratch),
                       radix_scratch_size(hit_cap, 2 * tri_bits + pair_bits)));
         TMS_CK(dalloc(&cand, cand_cap));
-        if (patch) TMS_CK(dalloc(&ppairs, ppair_cap));
+        if (patch) {
+            TMS_CK(dalloc(&ppairs, ppair_cap));
+            TMS_CK(dalloc(&ppairs_sorted, ppair_cap));
+            TMS_CK(dalloc(&pp_rank, ppair_cap));
+        }
         TMS_CK(dalloc(&surv, surv_cap));
         TMS_CK(dalloc(&hits, hit_cap));
         TMS_CK(dalloc(&hk, hit_cap));
@@ -292,8 +300,15 @@ struct Plan {
         kernels += 1;
         mark(10, s);
         if (patch) {
+            // the patch pairs grouped by A patch, then their quad pairs
+            PatchSortArgs so;
+            so.in = ppairs; so.out = ppairs_sorted; so.d_n = &d_ctr->ppairs; so.cap = ppair_cap;
+            so.abase = d_abase; so.cnt = pp_cnt; so.off = pp_off; so.rank = pp_rank;
+            so.n_slots = (unsigned long long)fslots_A; so.d_slots = d_aslots; so.partials = partials;
+            launch_ppair_sort(so, grid, s);
+            kernels += 6;
             PatchArgs pa;
-            pa.ppairs = ppairs; pa.ppair_cap = ppair_cap; pa.meshes = d_meshes; pa.pairs = d_pairs;
+            pa.ppairs = ppairs_sorted; pa.ppair_cap = ppair_cap; pa.meshes = d_meshes; pa.pairs = d_pairs;
             pa.ctr = d_ctr; pa.ent_cap = ent_cap; pa.cand = cand; pa.cand_cap = cand_cap;
             pa.moller = p.moller;
             launch_patch_quads(pa, prec, grid / 2, s);
@@ -551,6 +566,18 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     TMS_PCK(cudaMemcpy(P->d_pass_all, pall.data(), pall.size() * sizeof(PassEntry), cudaMemcpyHostToDevice));
     TMS_PCK(cudaMemcpy(P->d_pass_A, pa.data(), pa.size() * sizeof(PassEntry), cudaMemcpyHostToDevice));
     TMS_PCK(cudaMemcpy(P->d_pass_B, pb.data(), pb.size() * sizeof(PassEntry), cudaMemcpyHostToDevice));
+    if (patch) {
+        // A patch slots of the A pass: pair i's patches from its face_base on
+        std::vector<uint32_t> abase;
+        for (auto &e : pa) abase.push_back((uint32_t)e.face_base);
+        const unsigned long long nslots = (unsigned long long)P->fslots_A;
+        TMS_PCK(dalloc(&P->d_abase, abase.size()));
+        TMS_PCK(dalloc(&P->pp_cnt, nslots));
+        TMS_PCK(dalloc(&P->pp_off, nslots));
+        TMS_PCK(dalloc(&P->d_aslots, 1));
+        TMS_PCK(cudaMemcpy(P->d_abase, abase.data(), abase.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        TMS_PCK(cudaMemcpy(P->d_aslots, &nslots, sizeof(nslots), cudaMemcpyHostToDevice));
+    }
     TMS_PCK(cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking));
     TMS_PCK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
     TMS_PCK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));

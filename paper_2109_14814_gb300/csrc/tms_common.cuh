@@ -478,6 +478,21 @@ struct PatchArgs {
     int moller;
 };
 void launch_patch_quads(const PatchArgs &a, int precision, int sms, cudaStream_t st);
+
+// Patch pairs grouped by A patch (a counting sort, 5 launches); a pair's A slot
+// is abase[pair] + faceA, below n_slots.
+struct PatchSortArgs {
+    const Cand *in;
+    Cand *out;
+    const unsigned long long *d_n; // patch pair count
+    unsigned long long cap;
+    const uint32_t *abase;         // per mesh pair: its A patches' first slot
+    uint32_t *cnt, *off, *rank;    // [n_slots], [n_slots], [cap]
+    unsigned long long n_slots;
+    const unsigned long long *d_slots;  // device copy of n_slots (the scan's count)
+    unsigned long long *partials;
+};
+void launch_ppair_sort(const PatchSortArgs &a, int grid, cudaStream_t st);
 void configure_patch_quads();
 
 struct NarrowArgs {
