@@ -58,6 +58,35 @@ SAT_FLOPS = 551
 QUAD_SAT_FLOPS = 964
 
 
+# the broad phase's stages (tms_last_stage_ms labels), and per reported stage the
+# labels it sums and its kernels (the keys of profiles/traffic.json)
+BROAD_STAGES = ("init", "face_bounds", "grid_params", "bitmap_clear", "face_mark_A", "face_probe_B",
+                "face_probe_A", "group_count", "group_cells", "emit", "patch_quads")
+STAGE_PARTS = {
+    "face_bounds": ("face_bounds",),
+    "face_mark": ("face_mark_A",),
+    "face_probe": ("face_probe_B", "face_probe_A"),
+    "group_count": ("group_count",),
+    "group_cells": ("group_cells",),
+    "emit": ("emit", "patch_quads"),
+    "narrow": ("narrow",),
+    "sort_merge": ("sort_hits", "merge_output"),
+}
+STAGE_KERNELS = {
+    "face_bounds": "tms::k_bounds_pass",
+    "face_mark": "tms::k_cell_pass<MARK>",
+    "face_probe": "tms::k_cell_pass<PROBE_MARK, PROBE>",
+    "group_count": "tms::k_group_count",
+    "group_cells": "tms::k_cells_* + k_group_scatter",
+    "emit": "tms::k_emit + k_patch_quads",
+    "narrow": "tms::k_narrow_filter + k_narrow_fp64",
+    "sort_merge": "tms::k_radix_* + k_dedup_*",
+}
+BROAD_KERNELS = ("k_search_init", "k_bounds_pass", "k_grid_params", "k_cell_pass", "k_group_count",
+                 "k_cells_reduce", "k_cells_partials", "k_cells_down", "k_group_scatter", "k_emit",
+                 "k_patch_quads")
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -83,43 +112,70 @@ def job_times(total_ms: float, steps: int, ws: int):
     return total_ms / (steps * ws), total_ms / steps
 
 
-def committed_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (profiles/traffic.json), or None when absent or taken on other sources."""
+def _traffic_table():
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        entry = t.get(kernel)
-        if not entry or entry.get("source_hash") != source_hash():
-            return None
-        return entry.get("dram_bytes_per_launch")
+        return t if t.get("source_hash") == source_hash() else None
     except (OSError, ValueError):
         return None
 
 
-# ncu kernel names of each stage label (the keys of profiles/traffic.json)
-TRAFFIC_STAGES = {
-    "tms::k_bounds_pass": ("k_bounds_pass",),
-    "tms::k_cell_pass<MARK>": ("k_cell_pass<1, 1>",),
-    "tms::k_cell_pass<PROBE_MARK, PROBE>": ("k_cell_pass<1, 2>", "k_cell_pass<1, 3>"),
-    "tms::k_group_count": ("k_group_count",),
-    "tms::k_cells_* + k_group_scatter": ("k_cells_reduce", "k_cells_partials", "k_cells_down",
-                                         "k_group_scatter"),
-    "tms::k_emit": ("k_emit",),
-    "tms::k_narrow_filter + k_narrow_fp64": ("k_narrow_filter", "k_narrow_fp64"),
-}
-TRAFFIC_COMMAND = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-                   "--clock-control none -s 60 -c 60 --csv --log-file traffic.csv "
-                   "python bench.py --steps 1 --warmup 3 --no-e2e --no-cpu")
+def committed_traffic(label: str):
+    """DRAM bytes per search of a reported stage (STAGE_KERNELS label) from the
+    committed ncu summary (profiles/traffic.json), or None when absent or taken
+    on other sources."""
+    t = _traffic_table()
+    if not t:
+        return None
+    st = t.get("stages", {}).get(label)
+    return st.get("dram_bytes_per_search") if st else None
 
 
-def write_traffic(csv_path: str) -> dict:
-    """profiles/traffic.json from an ncu CSV of TRAFFIC_COMMAND: the DRAM bytes of
-    the last complete search in the capture (from k_search_init to the last
-    kernel before the next one), per stage label and per launch."""
+def broad_traffic():
+    """ncu DRAM bytes of the broad phase's kernels per search, or None."""
+    t = _traffic_table()
+    return t.get("broad_dram_bytes_per_search") if t else None
+
+
+# One ncu capture per kernel (the pool's rule for counters beyond the launch
+# list: one kernel, one to three launches), on the bench workload (about 1 GB on
+# the device, inputs larger than L2), after three warm-up searches.  Per kernel:
+# (regex, launches per search, stage label, in the broad phase).
+TRAFFIC_KERNELS = [
+    ("k_search_init", 1, None, True),
+    ("k_bounds_pass", 1, "face_bounds", True),
+    ("k_grid_params", 1, None, True),
+    ("k_cell_pass", 3, "face_probe", True),
+    ("k_group_count", 1, "group_count", True),
+    ("k_cells_reduce", 1, "group_cells", True),
+    ("k_cells_partials", 1, "group_cells", True),
+    ("k_cells_down", 1, "group_cells", True),
+    ("k_group_scatter", 1, "group_cells", True),
+    ("k_emit", 1, "emit", True),
+    ("k_patch_quads", 1, "emit", True),
+    ("k_narrow_filter", 1, "narrow", False),
+    ("k_narrow_fp64", 1, "narrow", False),
+]
+TRAFFIC_METRICS = "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum"
+TRAFFIC_BENCH = "python bench.py --steps 1 --warmup 3 --no-e2e --no-cpu --workload-cache {cache}"
+
+
+def traffic_commands(out_dir: str, cache: str):
+    """The ncu command of each TRAFFIC_KERNELS entry (CSV into out_dir)."""
+    cmds = []
+    for i, (rx, per, _, _) in enumerate(TRAFFIC_KERNELS):
+        cmds.append(f"ncu --metrics {TRAFFIC_METRICS} --clock-control none -k regex:^{rx} "
+                    f"-s {2 * per} -c {per} --csv --log-file {out_dir}/traffic_{i:02d}.csv "
+                    + TRAFFIC_BENCH.format(cache=cache))
+    return cmds
+
+
+def _ncu_rows(path: str):
     import csv
-    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1024.0, "MB": 1048576.0}
-    rows = list(csv.reader(open(csv_path)))
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1024.0, "MB": 1048576.0,
+             "nsecond": 1e-9, "usecond": 1e-6, "msecond": 1e-3}
+    rows = list(csv.reader(open(path)))
     hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
     h = rows[hi]
     ci = {k: h.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
@@ -127,29 +183,42 @@ def write_traffic(csv_path: str) -> dict:
     for r in rows[hi + 1:]:
         if len(r) < len(h):
             continue
-        name = r[ci["Kernel Name"]].split("(")[0].replace("tms::", "").replace("void ", "")
-        name = name.replace("(anonymous namespace)::", "").replace("<unnamed>::", "").strip()
-        L = launches.setdefault(int(r[ci["ID"]]), {"name": name, "bytes": 0.0})
+        L = launches.setdefault(int(r[ci["ID"]]), {"name": r[ci["Kernel Name"]], "bytes": 0.0, "s": 0.0})
+        v = float(r[ci["Metric Value"]].replace(",", "")) * scale.get(r[ci["Metric Unit"]], 1.0)
         if r[ci["Metric Name"]] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-            L["bytes"] += float(r[ci["Metric Value"]].replace(",", "")) * scale[r[ci["Metric Unit"]]]
-    seq = [launches[k] for k in sorted(launches)]
-    starts = [i for i, L in enumerate(seq) if L["name"].startswith(("k_search_init", "k_bounds_init"))]
-    if len(starts) < 2:
-        raise SystemExit("the capture holds no complete search")
-    one = seq[starts[-2]:starts[-1]]
-    out = {}
-    for label, names in TRAFFIC_STAGES.items():
-        ks = [L for L in one if any(L["name"].startswith(n) for n in names)]
-        if not ks:
+            L["bytes"] += v
+        elif r[ci["Metric Name"]] == "gpu__time_duration.sum":
+            L["s"] += v
+    return [launches[k] for k in sorted(launches)]
+
+
+def write_traffic(csv_dir: str) -> dict:
+    """profiles/traffic.json from the per-kernel CSVs of traffic_commands(): DRAM
+    bytes per search of every kernel, per reported stage, and over the broad
+    phase's kernels."""
+    out = {"source_hash": source_hash(), "kernels": {}, "stages": {},
+           "workload": "4096x512 vs 4096x512 vertex meshes, quad faces, patch level, mixed "
+                       "precision (the bench workload)",
+           "commands": traffic_commands("<dir>", "<cache>")}
+    broad = 0.0
+    for i, (rx, per, label, is_broad) in enumerate(TRAFFIC_KERNELS):
+        path = os.path.join(csv_dir, f"traffic_{i:02d}.csv")
+        if not os.path.exists(path):
             continue
-        per = {}
-        for L in ks:
-            per[L["name"]] = per.get(L["name"], 0.0) + L["bytes"]
-        out[label] = {"dram_bytes_per_launch": sum(L["bytes"] for L in ks) / len(ks),
-                      "kernels": per, "source_hash": source_hash(),
-                      "workload": "4096x512 vs 4096x512 vertex meshes, quad faces, mixed precision "
-                                  "(the bench workload)",
-                      "command": TRAFFIC_COMMAND}
+        ls = _ncu_rows(path)
+        if not ls:
+            continue
+        b = sum(L["bytes"] for L in ls)       # one search's launches of this kernel
+        out["kernels"][rx] = {"dram_bytes_per_search": b, "launches": len(ls),
+                              "duration_us_serialised": sum(L["s"] for L in ls) * 1e6}
+        if label:
+            key = STAGE_KERNELS[label]
+            st = out["stages"].setdefault(key, {"dram_bytes_per_search": 0.0, "kernels": []})
+            st["dram_bytes_per_search"] += b
+            st["kernels"].append(rx)
+        if is_broad:
+            broad += b
+    out["broad_dram_bytes_per_search"] = broad
     with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
@@ -240,9 +309,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def build_workload(device):
+def build_workload(device, cache: str = ""):
+    """The 4096 x 512 pair; with `cache`, read from that file when it exists
+    (else generated and written there), so that repeated runs of the bench in
+    one session (profiler captures) skip the generator."""
     import synth
+    if cache and os.path.exists(cache):
+        return torch.load(cache, weights_only=False)
     pair = synth.config3()
+    if cache:
+        torch.save(pair, cache)
     return pair
 
 
@@ -259,7 +335,7 @@ def run_tms(args, ws, rank, local):
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     peaks, peaks_kind = measured_peaks()
-    pair = build_workload(device)
+    pair = build_workload(device, args.workload_cache)
     XA = pair.A.X.to(device).contiguous()
     XB = pair.B.X.to(device).contiguous()
     A = tms.Mesh(XA, pair.A.s, True)
@@ -319,72 +395,49 @@ def run_tms(args, ws, rank, local):
     value, ms_per_step = job_times(total_ms, args.steps, ws)
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
 
-    # Roofline per kernel (stage).  Memory-bound stages: algorithmic bytes per
-    # launch (what the stage must move at least, from the workload and the
-    # search's statistics) against the measured copy bandwidth.  ALU-bound
-    # stages: algorithmic FP32 operations against the FP32 lane rate of this
-    # GPU (SMs x 128 lanes x the maximum SM clock; an FMA counts 2 FLOPs).
-    # The slowest stage is reported as `roofline`.  V vertices and F faces per
-    # mesh (quads), E face-cell entries, P proposed face pairs, C candidate
-    # quad pairs, QSAT quad candidates through the quad-level test, SAT triangle
-    # pairs through the separating-axis prefilter,
-    # S32 / S64 triangle pairs through the FP32 / FP64 solve.
-    V = pair.A.N * pair.A.M
-    F = pair.A.N * (pair.A.M - 1)
-    E, C, S = stats["entries"], stats["candidates"], stats["fp64_solves"]
-    P, S32, SAT = stats["pair_slots"], stats["fp32_solves"], stats["sat_tests"]
-    QSAT = stats["quad_tests"]
-    sms = torch.cuda.get_device_properties(device).multi_processor_count
-    sm_hz = float(NOMINAL_SM_MAX_MHZ) * 1e6
-    lane_ops = sms * 128 * sm_hz                   # FP32 lane operations per second
-    algo = {
-        # vertices read (4 x f64), FP32 split copy written (2 x float4), face box written (2 x float4)
-        "face_bounds": ("tms::k_bounds_pass", "hbm", 1, 2 * (32 * V + 32 * V + 32 * F)),
-        # face boxes read (mark A, probe B, probe A) and entries written (u64 key + u32 face)
-        "face_mark_A": ("tms::k_cell_pass<MARK>", "hbm", 1, 32 * F),
-        "face_probe_B+A": ("tms::k_cell_pass<PROBE_MARK, PROBE>", "hbm", 2, 2 * 32 * F + ENTRY_BYTES * E),
-        # grouping by cell: keys read, table slot and rank written ...
-        "group_count": ("tms::k_group_count", "hbm", 1, E * (8 + 4 + 4)),
-        # ... then slot, key, rank and face read and the face written per entry,
-        # and per cell its key, starts and tile offset
-        "group_cells": ("tms::k_cells_* + k_group_scatter", "hbm", 4,
-                        E * (4 + 8 + 4 + 4 + 4) + stats["cells"] * 24),
-        # the box test of every proposed face pair: 8 FP32 compares
-        "emit": ("tms::k_emit", "alu", 1, 8 * P),
-        # the quad-level test per quad candidate, the triangle-level test per pair
-        # of the candidates it cannot clear whose boxes overlap, the verified FP32
-        # solve for the pairs left
-        "narrow": ("tms::k_narrow_filter + k_narrow_fp64", "alu", 2,
-                   QUAD_SAT_FLOPS * QSAT + SAT_FLOPS * SAT + FP32_SOLVE_FLOPS * S32),
-    }
-    stage_time = dict(stage_ms)
-    stage_time["face_probe_B+A"] = stage_ms.get("face_probe_B", 0.0) + stage_ms.get("face_probe_A", 0.0)
+    # Roofline of the broad phase (A2-A7: bounds pass through candidate emission),
+    # the search's HBM-bound part, as one unit: its algorithmic bytes
+    #   B_broad = V * 32 (each mesh's FP64 vertices read once, both meshes)
+    #           + E * 16 (one 8-byte (key, id) entry written and read per
+    #                     face-cell incidence the grid registers)
+    #           + K * 8  (one 8-byte candidate pair written)
+    # with E and K this search's counts (at the patch level E counts patch-cell
+    # incidences and K quad pairs), divided by the summed device time of the
+    # broad stages; and the ncu DRAM bytes of the same kernels (profiles/
+    # traffic.json, taken on the same sources) over the same time.  Both
+    # against the measured copy bandwidth.  Per stage, the share of B_broad that
+    # stage moves: the vertex read (bounds pass), the entry writes (cell passes),
+    # the entry reads (cell table), the candidate writes (emission).
+    V2 = pair.A.N * pair.A.M + pair.B.N * pair.B.M
+    E, K = stats["entries"], stats["candidates"]
+    hbm = peaks.get("hbm_gbs")
+    broad_stages = BROAD_STAGES
+    broad_ms = sum(stage_ms.get(k, 0.0) for k in broad_stages)
+    b_broad = 32 * V2 + 16 * E + 8 * K
+    share = {"face_bounds": 32 * V2, "face_probe": 8 * E, "group_count": 8 * E,
+             "emit": 8 * K}
     kernels = {}
-    for st_name, (kname, bound, launches, work) in algo.items():
-        t = stage_time.get(st_name, 0.0)
-        if bound == "hbm":
-            ach = (work / 1e9) / (t / 1e3) if t > 0 else None
-            peak, unit = peaks.get("hbm_gbs"), "GB/s"
-        elif st_name == "narrow":
-            ach = (work / 1e12) / (t / 1e3) if t > 0 else None
-            peak, unit = 2 * lane_ops / 1e12, "TFLOP/s"
-        else:
-            ach = (work / 1e12) / (t / 1e3) if t > 0 else None
-            peak, unit = lane_ops / 1e12, "Tops/s"
-        kernels[st_name] = {"kernel": kname, "bound": bound, "launches": launches, "ms": t,
-                            "algorithmic_work": work, "achieved": ach, "peak": peak, "unit": unit,
-                            "frac": ach / peak if (ach and peak) else None,
+    for st_name, kname in STAGE_KERNELS.items():
+        t = sum(stage_ms.get(x, 0.0) for x in STAGE_PARTS[st_name])
+        byt = share.get(st_name, 0)
+        ach = (byt / 1e9) / (t / 1e3) if (t > 0 and byt) else None
+        kernels[st_name] = {"kernel": kname, "ms": t, "algorithmic_bytes": byt, "achieved_gbs": ach,
+                            "frac": ach / hbm if (ach and hbm) else None,
                             "traffic": committed_traffic(kname)}
-    dom = max(kernels, key=lambda k: kernels[k]["ms"])
-    d = kernels[dom]
-    roofline = {"kernel": d["kernel"], "stage": dom, "bound": d["bound"], "achieved": d["achieved"],
-                "peak": d["peak"], "unit": d["unit"], "frac": d["frac"],
-                "traffic": committed_traffic(d["kernel"]),
-                "peak_kind": (f"{peaks_kind} copy bandwidth" if d["bound"] == "hbm" else
-                              f"derived: {sms} SMs x 128 FP32 lanes x {NOMINAL_SM_MAX_MHZ} MHz"
-                              + (" x 2 (FMA)" if d["unit"] == "TFLOP/s" else "")),
-                "algorithmic_work_per_launch": d["algorithmic_work"] / d["launches"],
-                "launches": d["launches"], "share_of_step": d["ms"] / ms_per_step if ms_per_step else None,
+    traffic = broad_traffic()
+    ach = (b_broad / 1e9) / (broad_ms / 1e3) if broad_ms > 0 else None
+    roofline = {"kernel": "broad phase: " + ", ".join(BROAD_KERNELS), "stage": "broad (A2-A7)",
+                "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm if (ach and hbm) else None, "traffic": traffic,
+                "peak_kind": f"{peaks_kind} copy bandwidth",
+                "algorithmic_bytes": b_broad,
+                "algorithmic_formula": "32 V + 16 E + 8 K (V vertices of both meshes, E face-cell "
+                                       "entries, K candidate pairs)",
+                "V": V2, "E": E, "K": K, "ms": broad_ms,
+                "share_of_step": broad_ms / ms_per_step if ms_per_step else None,
+                "ncu_achieved": (traffic / 1e9) / (broad_ms / 1e3) if (traffic and broad_ms) else None,
+                "ncu_frac": ((traffic / 1e9) / (broad_ms / 1e3) / hbm) if (traffic and broad_ms and hbm)
+                else None,
                 "largest_stage": max(stage_ms, key=stage_ms.get)}
     # FP64 utilisation of the narrow phase
     fp64 = None
@@ -867,16 +920,26 @@ def main():
                     help="also time the plain FP64 path, the batched 256-pair search, the adjoint, "
                          "the refinement of the hits, their continuation, the layer sweep and "
                          "the theta-grid operations")
-    ap.add_argument("--write-traffic", default="", metavar="CSV",
-                    help="write profiles/traffic.json from an ncu CSV of one search's DRAM bytes "
-                         "(see TRAFFIC_COMMAND) and exit; needs no GPU")
+    ap.add_argument("--write-traffic", default="", metavar="DIR",
+                    help="write profiles/traffic.json from the per-kernel ncu CSVs in DIR "
+                         "(made by the --traffic-commands lines) and exit; needs no GPU")
+    ap.add_argument("--traffic-commands", default="", metavar="DIR",
+                    help="print the per-kernel ncu commands (CSV into DIR) and exit")
+    ap.add_argument("--workload-cache", default="", metavar="PATH",
+                    help="read the workload from PATH if it exists, else generate and write it")
     ap.add_argument("--only-extras", default="",
                     help="comma-separated extras to run alone (no main timing): plain_fp64, batched, "
                          "adjoint, refine, continuation, layers, theta, e2e_pipelined")
     args = ap.parse_args()
     if args.write_traffic:
-        for k, v in write_traffic(args.write_traffic).items():
-            print(f"{k}: {v['dram_bytes_per_launch'] / 1e6:.1f} MB per launch")
+        t = write_traffic(args.write_traffic)
+        for k, v in t["kernels"].items():
+            print(f"{k}: {v['dram_bytes_per_search'] / 1e6:.1f} MB per search ({v['launches']} launches)")
+        print(f"broad phase: {t['broad_dram_bytes_per_search'] / 1e6:.1f} MB per search")
+        return
+    if args.traffic_commands:
+        for c in traffic_commands(args.traffic_commands, args.workload_cache or "/tmp/tms_c3.pt"):
+            print(c)
         return
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()

@@ -453,8 +453,8 @@ def last_stats(stream=None) -> dict:
 
 
 STAGES = ["init", "face_bounds", "grid_params", "bitmap_clear", "face_mark_A", "face_probe_B",
-          "face_probe_A", "group_count", "group_cells", "emit", "patch_quads", "narrow", "sort_hits",
-          "merge_output", "readback"]
+          "face_probe_A", "group_count", "group_cells", "emit", "patch_quads", "narrow",
+          "sort_hits", "merge_output", "readback"]
 
 
 def last_stage_ms(stream=None) -> dict:

@@ -56,6 +56,10 @@ cudaError_t dalloc(T **p, size_t n) {
     return cudaMalloc((void **)p, n * sizeof(T));
 }
 
+// the counters and pair 0's grid share one allocation (and one read-back copy)
+constexpr size_t kGridOffset = (sizeof(Counters) + 255) / 256 * 256;
+constexpr size_t kReadback = kGridOffset + sizeof(Grid);
+
 struct Plan {
     // identity
     std::vector<long long> ids;     // A ids then B ids
@@ -74,10 +78,8 @@ struct Plan {
     bool patch = false;
     MeshDev *d_pmeshes = nullptr;
     unsigned char *pbox = nullptr;    // patch boxes of all meshes
-    Cand *ppairs = nullptr, *ppairs_sorted = nullptr;
+    Cand *ppairs = nullptr;
     unsigned long long ppair_cap = 0;
-    uint32_t *pp_rank = nullptr, *pp_cnt = nullptr, *pp_off = nullptr, *d_abase = nullptr;
-    unsigned long long *d_aslots = nullptr;
     int2 *d_pairs = nullptr;
     PassEntry *d_pass_all = nullptr, *d_pass_A = nullptr, *d_pass_B = nullptr;
     int n_pass_all = 0, n_pass_A = 0, n_pass_B = 0;
@@ -128,11 +130,10 @@ struct Plan {
     void free_scratch() {
         void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, crec, tcnt, tstart,
                         sort_scratch, cand, surv, hits, hk, hk2, okeys, hv, hv2,
-                        keep, kscan, ppairs, ppairs_sorted, pp_rank};
+                        keep, kscan, ppairs};
         for (void *p : ptrs)
             if (p) cudaFree(p);
-        ppairs = ppairs_sorted = nullptr;
-        pp_rank = nullptr;
+        ppairs = nullptr;
         bmA = bmH = nullptr; ek = nullptr; ev = eslot = erank = grouped = nullptr;
         tkey = nullptr; crec = nullptr; tcnt = nullptr; tstart = nullptr;
         sort_scratch = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
@@ -142,13 +143,11 @@ struct Plan {
     ~Plan() {
         if (st) cudaStreamSynchronize(st);
         free_scratch();
-        void *ptrs[] = {d_meshes, d_pairs, d_pass_all, d_pass_A, d_pass_B, d_bounds, d_grids,
-                        d_ctr, partials, split, fbox, d_pmeshes, pbox, pp_cnt, pp_off, d_abase,
-                        d_aslots};
+        void *ptrs[] = {d_meshes, d_pairs, d_pass_all, d_pass_A, d_pass_B, d_bounds,
+                        d_ctr, partials, split, fbox, d_pmeshes, pbox};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         if (h_ctr) cudaFreeHost(h_ctr);
-        if (h_grid0) cudaFreeHost(h_grid0);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
         for (auto &e : tev)
@@ -181,11 +180,7 @@ struct Plan {
         TMS_CK(dalloc(reinterpret_cast<unsigned char **>(&sort_scratch),
                       radix_scratch_size(hit_cap, 2 * tri_bits + pair_bits)));
         TMS_CK(dalloc(&cand, cand_cap));
-        if (patch) {
-            TMS_CK(dalloc(&ppairs, ppair_cap));
-            TMS_CK(dalloc(&ppairs_sorted, ppair_cap));
-            TMS_CK(dalloc(&pp_rank, ppair_cap));
-        }
+        if (patch) TMS_CK(dalloc(&ppairs, ppair_cap));
         TMS_CK(dalloc(&surv, surv_cap));
         TMS_CK(dalloc(&hits, hit_cap));
         TMS_CK(dalloc(&hk, hit_cap));
@@ -215,8 +210,11 @@ struct Plan {
         const int sort_passes_h = (2 * tri_bits + pair_bits + kRadixBits - 1) / kRadixBits;
         kernels = 0;
         mark(0, s);
-        launch_search_init(d_bounds, n_meshes, d_ctr, p.cell_filter ? bmA : nullptr,
-                           (unsigned long long)1 << bmA_bits, p.cell_filter ? bmH : nullptr,
+        // the occupancy filter runs at the face level only: patches are few, and
+        // nearly every patch-cell incidence lies in a cell both meshes occupy
+        const bool filter = p.cell_filter && !patch;
+        launch_search_init(d_bounds, n_meshes, d_ctr, filter ? bmA : nullptr,
+                           (unsigned long long)1 << bmA_bits, filter ? bmH : nullptr,
                            (unsigned long long)1 << bmH_bits, grid, s);
         GroupArgs ga;
         ga.ent_key = ek; ga.ent_face = ev; ga.d_n = &d_ctr->entries; ga.cap = ent_cap;
@@ -254,7 +252,7 @@ struct Plan {
         kernels += 2;
         mark(3, s);
 
-        if (p.cell_filter) {
+        if (filter) {
             mark(4, s);
             fa.entries = d_pass_A; fa.n_entries = n_pass_A; fa.total_faces = fslots_A;
             fa.mode = MODE_MARK;
@@ -291,24 +289,20 @@ struct Plan {
         ea.grids = d_grids; ea.meshes = d_meshes; ea.pairs = d_pairs; ea.ctr = d_ctr;
         ea.ent_cap = ent_cap; ea.cand = cand; ea.cand_cap = cand_cap; ea.moller = p.moller;
         ea.cand_ctr = &d_ctr->cand;
+        ea.waves = 0;
         if (patch) {
-            // patch pairs with overlapping boxes, each once (owner cell)
+            // patch pairs with overlapping boxes, each once (owner cell); few
+            // tiles (about one per cell), so one wave of blocks
             ea.meshes = d_pmeshes; ea.cand = ppairs; ea.cand_cap = ppair_cap;
-            ea.cand_ctr = &d_ctr->ppairs; ea.moller = 0;
+            ea.cand_ctr = &d_ctr->ppairs; ea.moller = 0; ea.waves = 1;
         }
         launch_emit(ea, prec, fl, grid / 2, s);
         kernels += 1;
         mark(10, s);
         if (patch) {
-            // the patch pairs grouped by A patch, then their quad pairs
-            PatchSortArgs so;
-            so.in = ppairs; so.out = ppairs_sorted; so.d_n = &d_ctr->ppairs; so.cap = ppair_cap;
-            so.abase = d_abase; so.cnt = pp_cnt; so.off = pp_off; so.rank = pp_rank;
-            so.n_slots = (unsigned long long)fslots_A; so.d_slots = d_aslots; so.partials = partials;
-            launch_ppair_sort(so, grid, s);
-            kernels += 6;
+            // the quad pairs of the patch pairs
             PatchArgs pa;
-            pa.ppairs = ppairs_sorted; pa.ppair_cap = ppair_cap; pa.meshes = d_meshes; pa.pairs = d_pairs;
+            pa.ppairs = ppairs; pa.ppair_cap = ppair_cap; pa.meshes = d_meshes; pa.pairs = d_pairs;
             pa.ctr = d_ctr; pa.ent_cap = ent_cap; pa.cand = cand; pa.cand_cap = cand_cap;
             pa.moller = p.moller;
             launch_patch_quads(pa, prec, grid / 2, s);
@@ -341,8 +335,8 @@ struct Plan {
         kernels += 5 + (dOffsets ? 1 : 0);
         mark(14, s);
 
-        cudaMemcpyAsync(h_ctr, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(h_grid0, d_grids, sizeof(Grid), cudaMemcpyDeviceToHost, s);
+        // the counters and pair 0's grid, adjacent on the device: one copy
+        cudaMemcpyAsync(h_ctr, d_ctr, kReadback, cudaMemcpyDeviceToHost, s);
         mark(15, s);
     }
 
@@ -502,6 +496,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
         fbox_total += (face_slots(md, fl) * box_bytes + 255) / 256 * 256;
         md.npi = patch ? (md.nqi + kPatchI - 1) / kPatchI : 0;
         md.npk = patch ? (md.nqk + kPatchK - 1) / kPatchK : 0;
+        md.pmagic = md.npi >= 2 ? ~0ULL / (unsigned long long)md.npi + 1 : 0;
         md.pbox = nullptr;
         pbox_off.push_back(pbox_total);
         pbox_total += ((unsigned long long)md.npi * md.npk * box_bytes + 255) / 256 * 256;
@@ -555,29 +550,26 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     TMS_PCK(dalloc(&P->d_pass_A, pa.size()));
     TMS_PCK(dalloc(&P->d_pass_B, pb.size()));
     TMS_PCK(dalloc(&P->d_bounds, meshes.size()));
-    TMS_PCK(dalloc(&P->d_grids, pairs.size()));
-    TMS_PCK(dalloc(&P->d_ctr, 1));
+    // counters, then the grids of all pairs (pair 0's right after the counters)
+    {
+        unsigned char *blk = nullptr;
+        TMS_PCK(dalloc(&blk, kGridOffset + pairs.size() * sizeof(Grid)));
+        P->d_ctr = reinterpret_cast<Counters *>(blk);
+        P->d_grids = reinterpret_cast<Grid *>(blk + kGridOffset);
+    }
     TMS_PCK(dalloc(&P->partials, 5 * 1024));
-    TMS_PCK(cudaMallocHost((void **)&P->h_ctr, sizeof(Counters)));
-    TMS_PCK(cudaMallocHost((void **)&P->h_grid0, sizeof(Grid)));
+    {
+        unsigned char *hb = nullptr;
+        TMS_PCK(cudaMallocHost((void **)&hb, kReadback));
+        P->h_ctr = reinterpret_cast<Counters *>(hb);
+        P->h_grid0 = reinterpret_cast<Grid *>(hb + kGridOffset);
+    }
     TMS_PCK(cudaMemcpy(P->d_meshes, meshes.data(), meshes.size() * sizeof(MeshDev), cudaMemcpyHostToDevice));
     TMS_PCK(cudaMemcpy(P->d_pmeshes, pmeshes.data(), pmeshes.size() * sizeof(MeshDev), cudaMemcpyHostToDevice));
     TMS_PCK(cudaMemcpy(P->d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice));
     TMS_PCK(cudaMemcpy(P->d_pass_all, pall.data(), pall.size() * sizeof(PassEntry), cudaMemcpyHostToDevice));
     TMS_PCK(cudaMemcpy(P->d_pass_A, pa.data(), pa.size() * sizeof(PassEntry), cudaMemcpyHostToDevice));
     TMS_PCK(cudaMemcpy(P->d_pass_B, pb.data(), pb.size() * sizeof(PassEntry), cudaMemcpyHostToDevice));
-    if (patch) {
-        // A patch slots of the A pass: pair i's patches from its face_base on
-        std::vector<uint32_t> abase;
-        for (auto &e : pa) abase.push_back((uint32_t)e.face_base);
-        const unsigned long long nslots = (unsigned long long)P->fslots_A;
-        TMS_PCK(dalloc(&P->d_abase, abase.size()));
-        TMS_PCK(dalloc(&P->pp_cnt, nslots));
-        TMS_PCK(dalloc(&P->pp_off, nslots));
-        TMS_PCK(dalloc(&P->d_aslots, 1));
-        TMS_PCK(cudaMemcpy(P->d_abase, abase.data(), abase.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-        TMS_PCK(cudaMemcpy(P->d_aslots, &nslots, sizeof(nslots), cudaMemcpyHostToDevice));
-    }
     TMS_PCK(cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking));
     TMS_PCK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
     TMS_PCK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));

@@ -67,6 +67,8 @@ struct MeshDev {
                           // patch row * npi + patch column
     int npi;              // patches per quad row, ceil(nqi / kPatchI) (0: none)
     int npk;              // patch rows, ceil(nqk / kPatchK)
+    unsigned long long pmagic;  // ceil(2^64 / npi) for npi >= 2: a patch id's row
+                                // is __umul64hi(id, pmagic) (exact for 32-bit ids)
 };
 
 // Patch level of the broad phase: quads grouped into patches of kPatchI quads
@@ -456,6 +458,7 @@ struct EmitArgs {
     unsigned long long cand_cap;
     unsigned long long *cand_ctr;  // the output's counter (candidates, or patch pairs)
     int moller;
+    int waves;                     // waves of resident blocks (0: the default, 4)
 };
 // whole waves of resident blocks on `sms` SMs
 void launch_emit(const EmitArgs &a, int precision, int face_level, int sms, cudaStream_t st);
@@ -479,20 +482,6 @@ struct PatchArgs {
 };
 void launch_patch_quads(const PatchArgs &a, int precision, int sms, cudaStream_t st);
 
-// Patch pairs grouped by A patch (a counting sort, 5 launches); a pair's A slot
-// is abase[pair] + faceA, below n_slots.
-struct PatchSortArgs {
-    const Cand *in;
-    Cand *out;
-    const unsigned long long *d_n; // patch pair count
-    unsigned long long cap;
-    const uint32_t *abase;         // per mesh pair: its A patches' first slot
-    uint32_t *cnt, *off, *rank;    // [n_slots], [n_slots], [cap]
-    unsigned long long n_slots;
-    const unsigned long long *d_slots;  // device copy of n_slots (the scan's count)
-    unsigned long long *partials;
-};
-void launch_ppair_sort(const PatchSortArgs &a, int grid, cudaStream_t st);
 void configure_patch_quads();
 
 struct NarrowArgs {

@@ -332,6 +332,7 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     ea.grids = b.grids; ea.meshes = b.tables->meshes; ea.pairs = b.tables->pairs; ea.ctr = b.ctr;
     ea.ent_cap = kEntCap; ea.cand = b.cand; ea.cand_cap = kCandCap; ea.moller = p.moller;
     ea.cand_ctr = &b.ctr->cand;
+    ea.waves = 0;
     launch_emit(ea, p.precision, p.face_level, grid / 2, s);
     NarrowArgs na;
     na.cand = b.cand; na.cand_cap = kCandCap; na.surv = b.surv; na.surv_cap = kSurvCap;

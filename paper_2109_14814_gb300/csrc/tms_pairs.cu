@@ -43,7 +43,19 @@ template <int PREC>
 struct EBox;
 template <>
 struct __align__(16) EBox<1> {
+    typedef float4 Half;
     float lo[4], hi[4];
+    __device__ void store_halves(Half &l, Half &h) const {
+        l = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        h = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    }
+    // closed overlap of two boxes given by halves (touching is overlap)
+    static __device__ __forceinline__ bool halves_overlap(const Half &xl, const Half &xh, const Half &yl,
+                                                          const Half &yh) {
+        const float4 a = xl, b = xh, c = yl, d = yh;
+        return !(b.x < c.x) & !(d.x < a.x) & !(b.y < c.y) & !(d.y < a.y) & !(b.z < c.z) & !(d.z < a.z) &
+               !(b.w < c.w) & !(d.w < a.w);
+    }
     __device__ void load(const void *fbox, uint32_t face) {
         const float4 *p = reinterpret_cast<const float4 *>(fbox) + 2 * (size_t)face;
         const float4 l = __ldg(p), h = __ldg(p + 1);
@@ -65,7 +77,19 @@ struct __align__(16) EBox<1> {
 };
 template <>
 struct __align__(16) EBox<0> {
+    struct __align__(16) Half { double v[4]; };
     double lo[4], hi[4];
+    __device__ void store_halves(Half &l, Half &h) const {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) { l.v[d] = lo[d]; h.v[d] = hi[d]; }
+    }
+    static __device__ __forceinline__ bool halves_overlap(const Half &xl, const Half &xh, const Half &yl,
+                                                          const Half &yh) {
+        bool ov = true;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) ov &= !(xh.v[d] < yl.v[d]) & !(yh.v[d] < xl.v[d]);
+        return ov;
+    }
     __device__ void load(const void *fbox, uint32_t face) {
         const double2 *p = reinterpret_cast<const double2 *>(fbox) + 4 * (size_t)face;
         const double2 x0 = __ldg(p), x1 = __ldg(p + 1), x2 = __ldg(p + 2), x3 = __ldg(p + 3);
@@ -379,7 +403,8 @@ int emit_resident() {
 
 template <int PREC, bool MOLLER>
 void emit_waves(const EmitArgs &a, int face_level, int sms, cudaStream_t st) {
-    k_emit<PREC, MOLLER><<<sms * emit_resident<PREC, MOLLER>() * kEmitWaves, 32 * kEmitWarps, 0, st>>>(
+    const int waves = a.waves > 0 ? a.waves : kEmitWaves;
+    k_emit<PREC, MOLLER><<<sms * emit_resident<PREC, MOLLER>() * waves, 32 * kEmitWarps, 0, st>>>(
         a, face_level);
 }
 
@@ -388,10 +413,6 @@ void emit_waves(const EmitArgs &a, int face_level, int sms, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 constexpr int kPatchWarps = 8;
 constexpr unsigned kPatchFlush = 64;   // staged candidates per atomic
-#ifndef TMS_PATCH_MIN_BLOCKS
-#define TMS_PATCH_MIN_BLOCKS 2
-#endif
-constexpr int kPatchMinBlocks = TMS_PATCH_MIN_BLOCKS;   // resident blocks per SM the registers allow
 
 // Patch pairs in A-major order: each warp takes a contiguous range of the pairs
 // sorted by A patch (k_ppair_rank / k_ppair_place), so a patch of A usually
@@ -421,9 +442,27 @@ __device__ __forceinline__ void load_side(const QuadSide &m, uint32_t patch, int
     if (valid) box.load(m.fbox, q);
 }
 
+// One warp per patch pair, grid-stride over the pairs.  Lane l holds quad
+// (row l / kPatchI, column l % kPatchI) of each patch.  A quad whose box misses
+// the other patch's box cannot overlap any quad of it (the patch box holds
+// them all), so each side is first cut to its quads that meet the other
+// patch; the pairs of the survivors (nA x nB of them, 32 per round, pair t =
+// (t / nB, t % nB)) take the box test of Sec. 6.2.2, optionally the Moller
+// test of Sec. 6.2.3, and are appended through a per-warp stage.
+// patch id -> (patch row, patch column): the quotient by npi from a 64-bit
+// reciprocal (exact for 32-bit ids, npi >= 2)
+__device__ __forceinline__ void patch_rc(uint32_t patch, uint32_t npi, unsigned long long magic,
+                                         uint32_t &pk, uint32_t &pi) {
+    pk = npi == 1 ? patch : (uint32_t)__umul64hi((unsigned long long)patch, magic);
+    pi = patch - pk * npi;
+}
+
 template <int PREC, bool MOLLER>
-__global__ void __launch_bounds__(32 * kPatchWarps, kPatchMinBlocks) k_patch_quads(PatchArgs a) {
-    __shared__ EBox<PREC> sA[kPatchWarps][32], sB[kPatchWarps][32];
+__global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 : 2) k_patch_quads(PatchArgs a) {
+    // survivors' boxes as separate low and high halves (16-byte rows for FP32:
+    // the cross test's reads at varying indices stay free of bank conflicts)
+    __shared__ typename EBox<PREC>::Half sAlo[kPatchWarps][32], sAhi[kPatchWarps][32];
+    __shared__ typename EBox<PREC>::Half sBlo[kPatchWarps][32], sBhi[kPatchWarps][32];
     __shared__ uint32_t sQA[kPatchWarps][32], sQB[kPatchWarps][32];
     __shared__ Cand sOut[kPatchWarps][kPatchFlush + 32];
     // nothing to do after an overflow of the patch-level grid (the host retries)
@@ -433,8 +472,6 @@ __global__ void __launch_bounds__(32 * kPatchWarps, kPatchMinBlocks) k_patch_qua
     const uint32_t lt = lanemask_lt();
     const unsigned long long gw = blockIdx.x * (unsigned long long)kPatchWarps + warp;
     const unsigned long long nw = (unsigned long long)gridDim.x * kPatchWarps;
-    const unsigned long long per = (n + nw - 1) / nw;
-    const unsigned long long j0 = min(gw * per, n), j1 = min(j0 + per, n);
     const int r = lane / kPatchI, c = lane % kPatchI;
     Cand *stage = sOut[warp];
     unsigned staged = 0;
@@ -444,145 +481,85 @@ __global__ void __launch_bounds__(32 * kPatchWarps, kPatchMinBlocks) k_patch_qua
     auto store = [cand_out, cap](unsigned long long pos, const Cand &rec) {
         if (pos < cap) cand_out[pos] = rec;
     };
-    if (j0 < j1) {
-        // the records of pairs [jc, jc + 32), one per lane, read by broadcast
-        unsigned long long jc = j0;
-        uint3 rec = make_uint3(0u, 0u, 0u);
-        auto load_chunk = [&]() {
-            if (jc + lane < j1) {
-                const Cand x = a.ppairs[jc + lane];
-                rec = make_uint3(x.faceA, x.faceB, x.pair);
-            }
-        };
-        auto record = [&](unsigned long long j) {
-            const int src = (int)(j - jc);
-            return make_uint3(__shfl_sync(FULL, rec.x, src), __shfl_sync(FULL, rec.y, src),
-                              __shfl_sync(FULL, rec.z, src));
-        };
-        QuadSide mA, mB;
-        auto sides = [&](uint32_t pair) {
-            const int2 pr = a.pairs[pair];
+    uint32_t cached_pair = 0xFFFFFFFFu;
+    const void *fbA = nullptr, *fbB = nullptr, *pbA = nullptr, *pbB = nullptr;
+    int NA = 1, nqiA = 0, nqkA = 0, NB = 1, nqiB = 0, nqkB = 0;
+    uint32_t npiA = 1, npiB = 1;
+    unsigned long long mgA = 0, mgB = 0;
+    int2 pr = make_int2(0, 0);
+    for (unsigned long long j = gw; j < n; j += nw) {
+        const Cand pp = a.ppairs[j];
+        if (pp.pair != cached_pair) {
+            pr = a.pairs[pp.pair];
             const MeshDev &ma = a.meshes[pr.x];
             const MeshDev &mb = a.meshes[pr.y];
-            mA = QuadSide{ma.fbox, ma.pbox, ma.N, ma.nqi, ma.nqk, ma.npi};
-            mB = QuadSide{mb.fbox, mb.pbox, mb.N, mb.nqi, mb.nqk, mb.npi};
-        };
-        load_chunk();
-        uint3 pp = record(j0);
-        uint32_t side_pair = pp.z;
-        sides(side_pair);
-        EBox<PREC> bb, PB, ba, PA;
-        bool vb, va = false;
-        uint32_t qb, qa = 0;
-        load_side<PREC>(mB, pp.y, r, c, bb, PB, vb, qb);
-        uint32_t curA = 0xFFFFFFFFu, curA_pair = 0xFFFFFFFFu;
-        for (unsigned long long j = j0; j < j1; ++j) {
-            // the next pair's record and (same mesh pair) its B side, in flight
-            // during this pair's tests
-            const bool more = j + 1 < j1;
-            uint3 ppn = pp;
-            if (more) {
-                if (j + 1 == jc + 32) {
-                    jc += 32;
-                    load_chunk();
-                }
-                ppn = record(j + 1);
+            fbA = ma.fbox; pbA = ma.pbox; NA = ma.N; nqiA = ma.nqi; nqkA = ma.nqk; npiA = ma.npi;
+            fbB = mb.fbox; pbB = mb.pbox; NB = mb.N; nqiB = mb.nqi; nqkB = mb.nqk; npiB = mb.npi;
+            mgA = ma.pmagic;
+            mgB = mb.pmagic;
+            cached_pair = pp.pair;
+        }
+        uint32_t pka, pia, pkb, pib;
+        patch_rc(pp.faceA, npiA, mgA, pka, pia);
+        patch_rc(pp.faceB, npiB, mgB, pkb, pib);
+        const int kqa = (int)pka * kPatchK + r, iqa = (int)pia * kPatchI + c;
+        const int kqb = (int)pkb * kPatchK + r, iqb = (int)pib * kPatchI + c;
+        const bool va = kqa < nqkA && iqa < nqiA, vb = kqb < nqkB && iqb < nqiB;
+        const uint32_t qa = (uint32_t)kqa * (uint32_t)NA + (uint32_t)iqa;
+        const uint32_t qb = (uint32_t)kqb * (uint32_t)NB + (uint32_t)iqb;
+        EBox<PREC> ba, bb, PA, PB;
+        PA.load(pbA, pp.faceA);
+        PB.load(pbB, pp.faceB);
+        ba.set_empty();
+        bb.set_empty();
+        if (va) ba.load(fbA, qa);
+        if (vb) bb.load(fbB, qb);
+        const bool sa = va && boxes_overlap(ba, PB);
+        const bool sb = vb && boxes_overlap(bb, PA);
+        const uint32_t mA = __ballot_sync(FULL, sa), mB = __ballot_sync(FULL, sb);
+        if (!mA || !mB) continue;
+        const uint32_t nA = __popc(mA), nB = __popc(mB);
+        __syncwarp();                          // the previous pair's survivors are read
+        if (sa) {
+            const int k = __popc(mA & lt);
+            ba.store_halves(sAlo[warp][k], sAhi[warp][k]);
+            sQA[warp][k] = qa;
+        }
+        if (sb) {
+            const int k = __popc(mB & lt);
+            bb.store_halves(sBlo[warp][k], sBhi[warp][k]);
+            sQB[warp][k] = qb;
+        }
+        __syncwarp();
+        const uint32_t T = nA * nB;
+        tests += T;
+        // t / nB for t < 1024, nB <= 32: (t + 1/2) / nB lies at least 1/64 from
+        // an integer, far beyond the FP32 error of (t + 1/2) * (1 / nB)
+        const float rB = 1.0f / (float)nB;
+        for (uint32_t base = 0; base < T; base += 32) {
+            const uint32_t t = base + lane;
+            bool ov = false;
+            uint32_t ia = 0, ib = 0;
+            if (t < T) {
+                ia = (uint32_t)(((float)t + 0.5f) * rB);
+                ib = t - ia * nB;
+                ov = EBox<PREC>::halves_overlap(sAlo[warp][ia], sAhi[warp][ia], sBlo[warp][ib],
+                                                sBhi[warp][ib]);
+                if (MOLLER && ov)
+                    ov = !moller_reject(a.meshes[pr.x], sQA[warp][ia], a.meshes[pr.y], sQB[warp][ib], 1);
             }
-            const bool pf = more && ppn.z == side_pair;
-            EBox<PREC> bbn, PBn;
-            bool vbn = false;
-            uint32_t qbn = 0;
-            if (pf) load_side<PREC>(mB, ppn.y, r, c, bbn, PBn, vbn, qbn);
-            if (pp.x != curA || pp.z != curA_pair) {
-                load_side<PREC>(mA, pp.x, r, c, ba, PA, va, qa);
-                curA = pp.x;
-                curA_pair = pp.z;
-            }
-            const bool sa = va && boxes_overlap(ba, PB);
-            const bool sb = vb && boxes_overlap(bb, PA);
-            const uint32_t mAm = __ballot_sync(FULL, sa), mBm = __ballot_sync(FULL, sb);
-            if (mAm && mBm) {
-                const uint32_t nA_ = __popc(mAm), nB_ = __popc(mBm);
-                __syncwarp();                  // the previous pair's survivors are read
-                if (sa) {
-                    const int k = __popc(mAm & lt);
-                    sA[warp][k] = ba;
-                    sQA[warp][k] = qa;
-                }
-                if (sb) {
-                    const int k = __popc(mBm & lt);
-                    sB[warp][k] = bb;
-                    sQB[warp][k] = qb;
-                }
-                __syncwarp();
-                const uint32_t T = nA_ * nB_;
-                tests += T;
-                // t / nB for t < 1024 <= 2^10: ceil(2^32 / nB) * t / 2^32 errs by
-                // less than 2^-22, below the 1/32 gap to the next integer
-                const unsigned long long magic = ((1ULL << 32) + nB_ - 1) / nB_;
-                for (uint32_t base = 0; base < T; base += 32) {
-                    const uint32_t t = base + lane;
-                    bool ov = false;
-                    uint32_t ia = 0, ib = 0;
-                    if (t < T) {
-                        ia = (uint32_t)(((unsigned long long)t * magic) >> 32);
-                        ib = t - ia * nB_;
-                        ov = boxes_overlap(sA[warp][ia], sB[warp][ib]);
-                        if (MOLLER && ov) {
-                            const int2 pr = a.pairs[pp.z];
-                            ov = !moller_reject(a.meshes[pr.x], sQA[warp][ia], a.meshes[pr.y],
-                                                sQB[warp][ib], 1);
-                        }
-                    }
-                    Cand cd;
-                    cd.faceA = sQA[warp][ia];
-                    cd.faceB = sQB[warp][ib];
-                    cd.pair = pp.z;
-                    cd.pad = 0;
-                    stage_push<kPatchFlush>(stage, staged, ov, cd, &a.ctr->cand, store);
-                }
-            }
-            if (more) {
-                pp = ppn;
-                if (pf) {
-                    bb = bbn;
-                    PB = PBn;
-                    vb = vbn;
-                    qb = qbn;
-                } else {
-                    side_pair = pp.z;
-                    sides(side_pair);
-                    load_side<PREC>(mB, pp.y, r, c, bb, PB, vb, qb);
-                }
-            }
+            Cand cd;
+            cd.faceA = sQA[warp][ia];
+            cd.faceB = sQB[warp][ib];
+            cd.pair = pp.pair;
+            cd.pad = 0;
+            stage_push<kPatchFlush>(stage, staged, ov, cd, &a.ctr->cand, store);
         }
     }
     __syncwarp();
     stage_flush<kPatchFlush>(stage, staged, &a.ctr->cand, store);
     for (int off = 16; off > 0; off >>= 1) tests += __shfl_xor_sync(FULL, tests, off);
     if (lane == 0 && tests) atomicAdd(&a.ctr->ptests, tests);
-}
-
-// Counting sort of the patch pairs by A patch: each pair's rank among the pairs
-// of its A patch (slot = the A patch's place in the A pass) and the per-patch
-// counts, then, after an exclusive scan of the counts, each pair to its place.
-__global__ void k_ppair_rank(PatchSortArgs a) {
-    const unsigned long long n = clamp_count(a.d_n, a.cap);
-    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
-        const Cand pp = a.in[j];
-        a.rank[j] = atomicAdd(a.cnt + a.abase[pp.pair] + pp.faceA, 1u);
-    }
-}
-
-__global__ void k_ppair_place(PatchSortArgs a) {
-    const unsigned long long n = clamp_count(a.d_n, a.cap);
-    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
-        const Cand pp = a.in[j];
-        const unsigned long long pos = (unsigned long long)a.off[a.abase[pp.pair] + pp.faceA] + a.rank[j];
-        if (pos < a.cap) a.out[pos] = pp;
-    }
 }
 
 int g_patch_resident[2][2] = {};
@@ -612,13 +589,6 @@ void configure_patch_quads() {
     patch_resident<0, true>();
     patch_resident<1, false>();
     patch_resident<1, true>();
-}
-
-void launch_ppair_sort(const PatchSortArgs &a, int grid, cudaStream_t st) {
-    cudaMemsetAsync(a.cnt, 0, (size_t)a.n_slots * sizeof(uint32_t), st);
-    k_ppair_rank<<<grid, 256, 0, st>>>(a);
-    scan_u32(a.cnt, a.off, a.d_slots, a.n_slots, a.partials, nullptr, grid, st);
-    k_ppair_place<<<grid, 256, 0, st>>>(a);
 }
 
 void launch_patch_quads(const PatchArgs &a, int precision, int sms, cudaStream_t st) {

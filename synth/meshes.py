@@ -517,6 +517,98 @@ def build_pair(seed: int, NA: int, MA: int, NB: int, MB: int, *, stretch: str = 
 # the five configurations
 # ----------------------------------------------------------------------------
 
+def independent_pair(seed: int, NA: int = 64, MA: int = 32, NB: int = 64, MB: int = 32,
+                     n_hits: int = 5, stretch: str = "linear", n_folds: int = 0,
+                     device: str = "cpu") -> MeshPair:
+    """Mesh A and an independent second surface B of the same family form (its own
+    seeded coefficients; no reparameterisation of A and no crossing term), bent
+    to pass through n_hits planted points of A: for each, a point p at weights
+    (a, b) (margins >= 0.1) in a random A triangle; among 64 random B triangles
+    whose bump supports are still free, the one whose point q at its chosen
+    weights (c, d) lies nearest to p; B's vertices get (p - q) times a bump that
+    is exactly 1 on that triangle's 2 x 2 vertex block (the triangle moves
+    rigidly and holds p at (c, d)) and tapers to 0 over two cells.  Pairs whose
+    triangle planes are not transverse are skipped.  The planted records carry
+    (a, b, c, d), P and (theta, s) in closed form."""
+    gen = torch.Generator().manual_seed(seed)
+    famA = _make_family(torch.Generator().manual_seed(seed), stretch, 4.0, n_folds, 12.0)
+    famB = _make_family(torch.Generator().manual_seed(seed + 7919), stretch, 4.0, n_folds, 12.0)
+    thA = torch.arange(NA, dtype=torch.float64) * (TWO_PI / NA)
+    thB = torch.arange(NB, dtype=torch.float64) * (TWO_PI / NB)
+    sA = torch.linspace(0.0, 1.0, MA, dtype=torch.float64)
+    sB = torch.linspace(0.0, 1.0, MB, dtype=torch.float64)
+    XA = _surface_A(famA, thA, sA, 0.0)[0]
+    XB = _surface_A(famB, thB, sB, 0.0)[0].clone()
+    sA_list, sB_list = sA.tolist(), sB.tolist()
+    T_taper = 2
+    wts = _bump_weights(T_taper)
+    usedB = torch.zeros(MB, NB, dtype=torch.bool)
+    rec = dict(kind=[], triA=[], triB=[], abcd=[], P=[], params=[], dist=[])
+    attempts = 0
+    while len(rec["triA"]) < n_hits and attempts < 200 * max(n_hits, 1):
+        attempts += 1
+        triA = int(torch.randint(0, 2 * NA * (MA - 1), (1,), generator=gen))
+        a, b = _shrink(float(torch.rand(1, generator=gen)), float(torch.rand(1, generator=gen)) * 0.5, 0.1)
+        va = tri_vertex_ij(NA, triA)
+        xv = [XA[:, vk, vi] for (vi, vk) in va]
+        p = a * xv[0] + (1.0 - a - b) * xv[1] + b * xv[2]
+        best = None
+        for _ in range(64):
+            triB = int(torch.randint(0, 2 * NB * (MB - 1), (1,), generator=gen))
+            q_, tau_b = divmod(triB, 2)
+            kb, ib = divmod(q_, NB)
+            rows = [kb + dk for dk in range(-T_taper, 2 + T_taper) if 0 <= kb + dk < MB]
+            cols = [(ib + di) % NB for di in range(-T_taper, 2 + T_taper)]
+            if usedB[rows][:, cols].any():
+                continue
+            c, d = _shrink(float(torch.rand(1, generator=gen)), float(torch.rand(1, generator=gen)) * 0.5, 0.1)
+            yv = [XB[:, vk, vi] for (vi, vk) in tri_vertex_ij(NB, triB)]
+            q = c * yv[0] + (1.0 - c - d) * yv[1] + d * yv[2]
+            dist = float((p - q).norm())
+            if best is None or dist < best[0]:
+                best = (dist, triB, c, d, kb, ib, rows, cols, q, yv)
+        if best is None:
+            continue
+        _, triB, c, d, kb, ib, rows, cols, q, yv = best
+        if _plane_transversality(xv, yv) < 0.01:
+            continue
+        delta = p - q
+        for r in rows:
+            usedB[r, cols] = True
+        for dk in range(-T_taper, 2 + T_taper):
+            r = kb + dk
+            if not (0 <= r < MB):
+                continue
+            wk = wts[0] if dk in (0, 1) else wts[(-dk) if dk < 0 else dk - 1]
+            for di in range(-T_taper, 2 + T_taper):
+                col = (ib + di) % NB
+                wi = wts[0] if di in (0, 1) else wts[(-di) if di < 0 else di - 1]
+                XB[:, r, col] += (wk * wi) * delta
+        thu, su = _point_params(NA, sA_list, triA, a, b)
+        ths, sss = _point_params(NB, sB_list, triB, c, d)
+        rec["kind"].append(0)
+        rec["triA"].append(triA)
+        rec["triB"].append(triB)
+        rec["abcd"].append([a, b, c, d])
+        rec["P"].append(p.tolist())
+        rec["params"].append([thu, su, ths, sss])
+        rec["dist"].append(0.0)
+    planted = Planted(
+        kind=torch.tensor(rec["kind"], dtype=torch.int32),
+        triA=torch.tensor(rec["triA"], dtype=torch.int64),
+        triB=torch.tensor(rec["triB"], dtype=torch.int64),
+        abcd=torch.tensor(rec["abcd"], dtype=torch.float64).reshape(-1, 4),
+        P=torch.tensor(rec["P"], dtype=torch.float64).reshape(-1, 4),
+        params=torch.tensor(rec["params"], dtype=torch.float64).reshape(-1, 4),
+        dist=torch.tensor(rec["dist"], dtype=torch.float64),
+    )
+    dev = torch.device(device)
+    A = MeshGrid(XA.contiguous().to(dev), sA.to(dev), True)
+    B = MeshGrid(XB.contiguous().to(dev), sB.to(dev), True)
+    meta = dict(seed=seed, NA=NA, MA=MA, NB=NB, MB=MB, independent=True, stretch=stretch)
+    return MeshPair(A, B, planted, meta, None)
+
+
 def config_seed(config: int, replica: int = 0) -> int:
     return SEED_BASE + 100 * config + replica
 
@@ -525,6 +617,13 @@ def config1(replica: int = 0, device: str = "cpu") -> MeshPair:
     """Plain FP64: 64 x 32 grids, (1 + s) trig surfaces, 5 planted hits."""
     return build_pair(config_seed(1, replica), 64, 32, 64, 32, stretch="linear",
                       n_folds=0, sites=(6, 1), n_hits=5, device=device)
+
+
+def config1_independent(replica: int = 0, device: str = "cpu") -> MeshPair:
+    """Plain FP64, 64 x 32 grids: (1 + s) trig surface A and an independent
+    seeded trig surface B bent through 5 planted points of A."""
+    return independent_pair(config_seed(1, replica) + 50, 64, 32, 64, 32, n_hits=5,
+                            stretch="linear", n_folds=0, device=device)
 
 
 def config2(replica: int = 0, device: str = "cpu") -> MeshPair:

@@ -10,63 +10,59 @@ import shutil
 import bench
 
 
-def _ncu_csv(path):
-    # two searches' worth of launches in the shape ncu --csv writes (one row per metric)
+def _ncu_csv(path, name, launches):
+    """One kernel's capture in the shape ncu --csv writes (one row per metric):
+    `launches` is a list of (read MB, write MB)."""
     hdr = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream",
            "Block Size", "Grid Size", "Device", "CC", "Section Name", "Metric Name",
            "Metric Unit", "Metric Value"]
-    seq = [("tms::k_search_init(tms::Bounds *)", 0.0, 0.0),
-           ("void tms::k_bounds_pass<1, 1, 4>(tms::FacePassArgs)", 134.4, 205.8),
-           ("tms::k_grid_params(tms::GridArgs)", 0.0, 0.0),
-           ("void tms::k_cell_pass<1, 1>(tms::FacePassArgs, int)", 69.1, 0.0),
-           ("void tms::k_cell_pass<1, 2>(tms::FacePassArgs, int)", 81.4, 9.6),
-           ("void tms::k_cell_pass<1, 3>(tms::FacePassArgs, int)", 82.0, 13.3),
-           ("tms::k_group_count(tms::GroupArgs)", 70.8, 18.6),
-           ("tms::k_cells_reduce(tms::GroupArgs)", 8.4, 0.0),
-           ("tms::k_cells_partials(tms::GroupArgs, int)", 0.0, 0.0),
-           ("tms::k_cells_down(tms::GroupArgs)", 16.1, 0.0),
-           ("tms::k_group_scatter(tms::GroupArgs)", 95.8, 7.1),
-           ("void tms::k_emit<1, 0>(tms::EmitArgs, int)", 232.0, 17.4),
-           ("void tms::k_narrow_filter<1>(tms::NarrowArgs)", 82.3, 0.2),
-           ("tms::k_narrow_fp64(tms::NarrowArgs)", 25.1, 0.0),
-           ("tms::k_radix_pass(tms::RadixArgs)", 0.2, 0.0)]
-    rows, i = [hdr], 0
-    for _ in range(2):
-        for name, rd, wr in seq + [("void at::vectorized_elementwise_kernel<4>(int)", 0.0, 268.4)]:
-            for metric, unit, val in (("dram__bytes_read.sum", "Mbyte", rd),
-                                      ("dram__bytes_write.sum", "Mbyte", wr),
-                                      ("gpu__time_duration.sum", "usecond", 10.0)):
-                rows.append([str(i), "1", "python", "h", name, "1", "7", "(256, 1, 1)", "(1, 1, 1)",
-                             "0", "10.3", "Command line profiler metrics", metric, unit, f"{val:,.2f}"])
-            i += 1
-    rows.append([str(i), "1", "python", "h", "tms::k_search_init(tms::Bounds *)", "1", "7", "", "",
-                 "0", "10.3", "", "dram__bytes_read.sum", "byte", "0"])
+    rows = [hdr]
+    for i, (rd, wr) in enumerate(launches):
+        for metric, unit, val in (("dram__bytes_read.sum", "Mbyte", rd),
+                                  ("dram__bytes_write.sum", "Mbyte", wr),
+                                  ("gpu__time_duration.sum", "usecond", 10.0)):
+            rows.append([str(i), "1", "python", "h", name, "1", "7", "(256, 1, 1)", "(1, 1, 1)",
+                         "0", "10.3", "Command line profiler metrics", metric, unit, f"{val:,.2f}"])
     with open(path, "w", newline="") as f:
         f.write('==PROF== Connected to process 1\n')
         csv.writer(f).writerows(rows)
 
 
-def test_write_traffic_takes_the_last_complete_search(tmp_path, monkeypatch):
+def test_write_traffic_sums_kernels_per_search_and_broad_phase(tmp_path, monkeypatch):
     prof = tmp_path / "profiles"
     prof.mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     shutil.copytree(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                                  "paper_2109_14814_gb300", "csrc"),
                     tmp_path / "paper_2109_14814_gb300" / "csrc")
-    _ncu_csv(tmp_path / "t.csv")
-    out = bench.write_traffic(str(tmp_path / "t.csv"))
+    caps = tmp_path / "caps"
+    caps.mkdir()
+    idx = {rx: i for i, (rx, _, _, _) in enumerate(bench.TRAFFIC_KERNELS)}
+    _ncu_csv(caps / f"traffic_{idx['k_bounds_pass']:02d}.csv", "void tms::k_bounds_pass<1, 1, 4>(x)",
+             [(134.4, 205.8)])
+    _ncu_csv(caps / f"traffic_{idx['k_cell_pass']:02d}.csv", "void tms::k_cell_pass<1, 1>(x)",
+             [(1.0, 0.0), (2.0, 0.5), (3.0, 0.5)])
+    _ncu_csv(caps / f"traffic_{idx['k_patch_quads']:02d}.csv", "void tms::k_patch_quads<1, 0>(x)",
+             [(60.0, 13.6)])
+    _ncu_csv(caps / f"traffic_{idx['k_narrow_filter']:02d}.csv", "void tms::k_narrow_filter<1>(x)",
+             [(80.0, 1.0)])
+    out = bench.write_traffic(str(caps))
     saved = json.load(open(prof / "traffic.json"))
     assert saved == json.loads(json.dumps(out))
-    assert abs(out["tms::k_bounds_pass"]["dram_bytes_per_launch"] - 340.2e6) < 1.0
-    # two launches in the probe stage: per-launch average
-    assert abs(out["tms::k_cell_pass<PROBE_MARK, PROBE>"]["dram_bytes_per_launch"] - 93.15e6) < 1.0
-    # four launches in the cells + scatter stage
-    assert abs(out["tms::k_cells_* + k_group_scatter"]["dram_bytes_per_launch"] - 127.4e6 / 4) < 1.0
-    assert set(out["tms::k_narrow_filter + k_narrow_fp64"]["kernels"]) == {"k_narrow_filter<1>",
-                                                                           "k_narrow_fp64"}
-    # torch's L2-flush fill is not a stage; every entry carries the source hash
-    assert all(v["source_hash"] == bench.source_hash() for v in out.values())
-    assert bench.committed_traffic("tms::k_emit") == out["tms::k_emit"]["dram_bytes_per_launch"]
+    assert out["source_hash"] == bench.source_hash()
+    assert abs(out["kernels"]["k_bounds_pass"]["dram_bytes_per_search"] - 340.2e6) < 1.0
+    # a kernel launched three times per search: its launches summed
+    assert out["kernels"]["k_cell_pass"]["launches"] == 3
+    assert abs(out["kernels"]["k_cell_pass"]["dram_bytes_per_search"] - 7.0e6) < 1.0
+    # the narrow phase is not in the broad phase's total
+    assert abs(out["broad_dram_bytes_per_search"] - (340.2e6 + 7.0e6 + 73.6e6)) < 1.0
+    assert bench.broad_traffic() == out["broad_dram_bytes_per_search"]
+    assert bench.committed_traffic("tms::k_bounds_pass") == out["kernels"]["k_bounds_pass"][
+        "dram_bytes_per_search"]
+    # commands: one kernel, one to three launches, clocks left alone
+    for c in bench.traffic_commands("d", "w.pt"):
+        assert "--clock-control none" in c and " -k regex:^" in c
+        assert int(c.split(" -c ")[1].split()[0]) in (1, 2, 3)
 
 
 def test_source_hash_covers_only_the_search_sources():

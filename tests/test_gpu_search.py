@@ -74,6 +74,22 @@ def test_config1_parity_and_planted():
         assert (a, b) in keys
 
 
+@pytest.mark.parametrize("patch", [0, 1])
+def test_config1_independent_surface_parity(patch):
+    """B an independent seeded surface (not A reparameterised) bent through 5
+    planted points of A: the GPU hits equal brute force, planted ones included."""
+    p = cached("c1i", synth.config1_independent)
+    OA, OB = oracle.OMesh.from_grid(p.A), oracle.OMesh.from_grid(p.B)
+    ref = cached("oracle:c1i", lambda: oracle.search(OA, OB, method="brute"))
+    g = gpu_search(p, patch=patch)
+    check_sorted_unique(g)
+    s = compare(OA, OB, g, ref)
+    assert s["common"] >= 5
+    keys = set(zip(g["triA"].tolist(), g["triB"].tolist()))
+    for a, b in zip(p.planted.triA.tolist(), p.planted.triB.tolist()):
+        assert (a, b) in keys
+
+
 def test_config2_parity():
     p = cached("c2", synth.config2)
     OA, OB, ref = oracle_hits("c2", p)

@@ -141,6 +141,20 @@ def test_config1_pruned_equals_bruteforce():
     assert np.array_equal(a["z"], b["z"])
 
 
+def test_config1_independent_surface_planted_and_pruned():
+    """Config 1 with B an independent seeded surface bent through 5 planted
+    points of A: brute force holds every planted hit at its closed form, and
+    the pruned oracle finds the same set."""
+    p = synth.config1_independent()
+    OA, OB = om(p.A), om(p.B)
+    a = oracle.merge_and_sort(OA, OB, oracle.bruteforce(OA, OB))
+    assert len(p.planted) == 5
+    _check_planted(p, a)
+    b = oracle.merge_and_sort(OA, OB, oracle.pruned(OA, OB))
+    assert np.array_equal(a["triA"], b["triA"]) and np.array_equal(a["triB"], b["triB"])
+    assert np.array_equal(a["z"], b["z"])
+
+
 def test_config1_box_pairs_bruteforce():
     """Closed-box overlap pairs from the hierarchy equal a direct all-pairs check."""
     p = synth.config1()
