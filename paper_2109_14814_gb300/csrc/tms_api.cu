@@ -106,6 +106,7 @@ struct Plan {
     void *sort_scratch = nullptr;
     unsigned long long *partials = nullptr;
     Cand *cand = nullptr, *surv = nullptr;
+    uint32_t *qsurv = nullptr;        // candidates left by the quad-level test
     float4 *split = nullptr;          // FP32 split vertex copies of all meshes
     unsigned long long split_total = 0;
     std::vector<unsigned long long> split_off;
@@ -130,10 +131,11 @@ struct Plan {
     void free_scratch() {
         void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, crec, tcnt, tstart,
                         sort_scratch, cand, surv, hits, hk, hk2, okeys, hv, hv2,
-                        keep, kscan, ppairs};
+                        keep, kscan, ppairs, qsurv};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         ppairs = nullptr;
+        qsurv = nullptr;
         bmA = bmH = nullptr; ek = nullptr; ev = eslot = erank = grouped = nullptr;
         tkey = nullptr; crec = nullptr; tcnt = nullptr; tstart = nullptr;
         sort_scratch = nullptr; cand = surv = nullptr; hits = nullptr; hk = hk2 = okeys = nullptr;
@@ -180,6 +182,7 @@ struct Plan {
         TMS_CK(dalloc(reinterpret_cast<unsigned char **>(&sort_scratch),
                       radix_scratch_size(hit_cap, 2 * tri_bits + pair_bits)));
         TMS_CK(dalloc(&cand, cand_cap));
+        TMS_CK(dalloc(&qsurv, cand_cap));
         if (patch) TMS_CK(dalloc(&ppairs, ppair_cap));
         TMS_CK(dalloc(&surv, surv_cap));
         TMS_CK(dalloc(&hits, hit_cap));
@@ -312,6 +315,7 @@ struct Plan {
 
         NarrowArgs na;
         na.cand = cand; na.cand_cap = cand_cap; na.surv = surv; na.surv_cap = surv_cap;
+        na.qsurv = qsurv;
         na.meshes = d_meshes; na.pairs = d_pairs;
         na.ctr = d_ctr; na.hits = hits; na.hit_key = hk; na.hit_val = hv; na.hit_cap = hit_cap;
         na.tau = p.tau; na.tri_bits = tri_bits; na.fp32_filter = p.narrow_filter;
@@ -496,7 +500,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
         fbox_total += (face_slots(md, fl) * box_bytes + 255) / 256 * 256;
         md.npi = patch ? (md.nqi + kPatchI - 1) / kPatchI : 0;
         md.npk = patch ? (md.nqk + kPatchK - 1) / kPatchK : 0;
-        md.pmagic = md.npi >= 2 ? ~0ULL / (unsigned long long)md.npi + 1 : 0;
+        md.pmagic = recip64((unsigned long long)md.npi);
         md.pbox = nullptr;
         pbox_off.push_back(pbox_total);
         pbox_total += ((unsigned long long)md.npi * md.npk * box_bytes + 255) / 256 * 256;
@@ -852,6 +856,7 @@ tms_status tms_build_mesh(const double *dX, const double *dY, const double *dPx,
     m->dev.nqi = nqi;
     m->dev.nqk = k1 - k0 - 1;
     m->dev.pad = 0;
+    m->dev.nmagic = recip64((unsigned long long)N);
     *out = m;
     return TMS_OK;
 }

@@ -69,7 +69,14 @@ struct MeshDev {
     int npk;              // patch rows, ceil(nqk / kPatchK)
     unsigned long long pmagic;  // ceil(2^64 / npi) for npi >= 2: a patch id's row
                                 // is __umul64hi(id, pmagic) (exact for 32-bit ids)
+    unsigned long long nmagic;  // ceil(2^64 / N): a quad id's row is
+                                // __umul64hi(q, nmagic) (N >= 2, exact for 32-bit ids)
 };
+
+// (i, k) of quad q = k N + i, by the reciprocal of N (no integer division)
+__host__ __device__ inline unsigned long long recip64(unsigned long long d) {
+    return d >= 2 ? ~0ULL / d + 1 : 0;
+}
 
 // Patch level of the broad phase: quads grouped into patches of kPatchI quads
 // along theta by kPatchK quad rows -- 32 quads, one per lane of a warp.
@@ -120,6 +127,7 @@ struct Counters {
     unsigned long long fp32;       // triangle pairs through the verified FP32 solve
     unsigned long long sat;        // triangle pairs through the separating-axis prefilter
     unsigned long long quad;       // quad candidates through the quad-level prefilter
+    unsigned long long qkeep;      // quad candidates it could not clear
     unsigned long long claimed;    // cell-table slots claimed by this search
     unsigned long long ppairs;     // patch pairs with overlapping boxes (patch level)
     unsigned long long ptests;     // quad-pair box tests inside those patch pairs
@@ -487,6 +495,7 @@ void configure_patch_quads();
 struct NarrowArgs {
     const Cand *cand;
     unsigned long long cand_cap;
+    uint32_t *qsurv;               // [cand_cap] candidates the quad-level test left
     Cand *surv;                    // triangle pairs left for the FP64 solve
     unsigned long long surv_cap;
     const MeshDev *meshes;
@@ -500,7 +509,8 @@ struct NarrowArgs {
     int tri_bits;
     int fp32_filter;
 };
-// the filter as one wave of resident blocks on `sms` SMs, the FP64 solve on `grid` blocks
+// the quad-level test over all candidates (quad faces), then the filter on what it
+// left as one wave of resident blocks on `sms` SMs, the FP64 solve on `grid` blocks
 void launch_narrow(const NarrowArgs &a, int face_level, int sms, int grid, cudaStream_t st);
 void configure_narrow();
 

@@ -128,9 +128,17 @@ __device__ __forceinline__ float comp(const float4 &v, int c) {
     return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 
+// (i, k) of quad q = k N + i
+__device__ __forceinline__ void quad_ik(const MeshDev &m, uint32_t q, int &i, int &k) {
+    const uint32_t kk = (uint32_t)__umul64hi((unsigned long long)q, m.nmagic);
+    k = (int)kk;
+    i = (int)(q - kk * (uint32_t)m.N);
+}
+
 // split copies of the quad's vertices (i,k), (i+1,k), (i,k+1), (i+1,k+1)
 __device__ __forceinline__ void gather_quad_split(const MeshDev &m, uint32_t q, float4 v[4][2]) {
-    const int i = (int)(q % (uint32_t)m.N), k = (int)(q / (uint32_t)m.N);
+    int i, k;
+    quad_ik(m, q, i, k);
     const int ip = (i + 1 == m.N) ? 0 : i + 1;
     const size_t idx[4] = {(size_t)k * m.N + i, (size_t)k * m.N + ip, (size_t)(k + 1) * m.N + i,
                            (size_t)(k + 1) * m.N + ip};
@@ -139,6 +147,17 @@ __device__ __forceinline__ void gather_quad_split(const MeshDev &m, uint32_t q, 
         v[j][0] = __ldg(m.split + 2 * idx[j]);
         v[j][1] = __ldg(m.split + 2 * idx[j] + 1);
     }
+}
+
+// the high halves of those split copies (the FP32 rounding of each coordinate)
+__device__ __forceinline__ void gather_quad_hi(const MeshDev &m, uint32_t q, float4 v[4]) {
+    int i, k;
+    quad_ik(m, q, i, k);
+    const int ip = (i + 1 == m.N) ? 0 : i + 1;
+    const size_t idx[4] = {(size_t)k * m.N + i, (size_t)k * m.N + ip, (size_t)(k + 1) * m.N + i,
+                           (size_t)(k + 1) * m.N + ip};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = __ldg(m.split + 2 * idx[j]);
 }
 
 // (x1, x2, x3) of T1 = ((i+1,k), (i,k), (i,k+1)) or T2 = ((i,k+1), (i+1,k+1), (i+1,k))
@@ -357,6 +376,28 @@ __device__ __forceinline__ SplitVec split_vec(const float4 P[2], const float4 Q[
     return r;
 }
 
+// p - q from the FP32 roundings hp = RN32(p), hq = RN32(q) alone: p = hp + dp
+// with |dp| <= u |hp| + 2^-150 (subnormal spacing), so t = fl(hp - hq) has
+// |t - (p - q)| <= u |t| / (1 - u) + u (|hp| + |hq|) + 2^-149, bounded with margin.
+// Looser than split_vec by about |hp| / |p - q|, which the quad-level test
+// absorbs except for near-misses far below a face's size.
+__device__ __forceinline__ SplitVec hi_vec(const float4 &P, const float4 &Q) {
+    const float u = 5.9604645e-08f;
+    SplitVec r;
+    float tm = 0.0f, hm = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float hp = comp(P, c), hq = comp(Q, c);
+        const float t = hp - hq;
+        r.v[c] = t;
+        tm = fmaxf(tm, fabsf(t));
+        hm = fmaxf(hm, fabsf(hp) + fabsf(hq));
+    }
+    r.E = ((1.001f * u) * tm + (1.001f * u) * hm) * 1.001f + 3e-45f;
+    r.M = tm;
+    return r;
+}
+
 // a + b of two vectors with bounds
 __device__ __forceinline__ SplitVec add_vec(const SplitVec &a, const SplitVec &b) {
     const float u = 5.9604645e-08f;
@@ -473,16 +514,11 @@ __device__ __forceinline__ float det_lo_of(const float mE[6], float epsE, const 
 // 2 delta (D_A + D_B) is larger than 2 delta (D_Ta + D_Tb) for every pair.
 // delta uses the largest kappa of the four pairs.  Axes: the two longest
 // duals of each quad's first triangle.
-__device__ __forceinline__ bool quad_sat_reject(const float4 QA[4][2], const float4 QB[4][2],
-                                                double tau) {
+// the quad-level test on the edge vectors of both quads relative to v0 of A
+__device__ __forceinline__ bool quad_sat_vectors(const SplitVec &a1, const SplitVec &a2, const SplitVec &a3,
+                                                 const SplitVec &b1, const SplitVec &b2, const SplitVec &b3,
+                                                 const SplitVec &r0, double tau) {
     const float u = 5.9604645e-08f;
-    // vertices v0 (i,k), v1 (i+1,k), v2 (i,k+1), v3 (i+1,k+1); T1 = (v1, v0, v2),
-    // T2 = (v2, v3, v1): T1's edges are (v1 - v0, v2 - v0), T2's (v2 - v3, v1 - v3)
-    const SplitVec a1 = split_vec(QA[1], QA[0]), a2 = split_vec(QA[2], QA[0]);
-    const SplitVec a3 = split_vec(QA[3], QA[0]);
-    const SplitVec b1 = split_vec(QB[1], QB[0]), b2 = split_vec(QB[2], QB[0]);
-    const SplitVec b3 = split_vec(QB[3], QB[0]);
-    const SplitVec r0 = split_vec(QB[0], QA[0]);
     float mA1[6], mB1[6], epsA1, epsB1;
     plucker(a1, a2, mA1, epsA1);
     plucker(b1, b2, mB1, epsB1);
@@ -536,6 +572,30 @@ __device__ __forceinline__ bool quad_sat_reject(const float4 QA[4][2], const flo
         if (gap > need) return true;
     }
     return false;
+}
+
+// The test from the quads' FP32 vertex roundings alone (hi_vec bounds), which
+// clears most candidates with half the data of the split copies; a candidate it
+// cannot clear goes on to the tests on the split copies.
+__device__ __forceinline__ bool quad_sat_reject_hi(const float4 QA[4], const float4 QB[4], double tau) {
+    const SplitVec a1 = hi_vec(QA[1], QA[0]), a2 = hi_vec(QA[2], QA[0]);
+    const SplitVec a3 = hi_vec(QA[3], QA[0]);
+    const SplitVec b1 = hi_vec(QB[1], QB[0]), b2 = hi_vec(QB[2], QB[0]);
+    const SplitVec b3 = hi_vec(QB[3], QB[0]);
+    const SplitVec r0 = hi_vec(QB[0], QA[0]);
+    return quad_sat_vectors(a1, a2, a3, b1, b2, b3, r0, tau);
+}
+
+__device__ __forceinline__ bool quad_sat_reject(const float4 QA[4][2], const float4 QB[4][2],
+                                                double tau) {
+    // vertices v0 (i,k), v1 (i+1,k), v2 (i,k+1), v3 (i+1,k+1); T1 = (v1, v0, v2),
+    // T2 = (v2, v3, v1): T1's edges are (v1 - v0, v2 - v0), T2's (v2 - v3, v1 - v3)
+    const SplitVec a1 = split_vec(QA[1], QA[0]), a2 = split_vec(QA[2], QA[0]);
+    const SplitVec a3 = split_vec(QA[3], QA[0]);
+    const SplitVec b1 = split_vec(QB[1], QB[0]), b2 = split_vec(QB[2], QB[0]);
+    const SplitVec b3 = split_vec(QB[3], QB[0]);
+    const SplitVec r0 = split_vec(QB[0], QA[0]);
+    return quad_sat_vectors(a1, a2, a3, b1, b2, b3, r0, tau);
 }
 
 // true when the separating-axis test proves the margin below -delta (not a hit,
@@ -673,15 +733,14 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
     constexpr int kW = 8, kQ = 32 + 4 * 32;
     __shared__ uint32_t q_cand[kW][kQ];          // triangle pairs for the verified solve
     __shared__ uint8_t q_sub[kW][kQ];
-    __shared__ uint32_t c_cand[kW][64];          // quad candidates for the per-pair path
+    __shared__ uint32_t c_cand[kW][32];          // quad candidates for the per-pair path
     if (a.ctr->cand > a.cand_cap) return;
     const unsigned long long n = a.ctr->cand;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
-    unsigned long long n_quad = 0, n_sat = 0, n_full = 0;   // tests run, per warp
+    unsigned long long n_sat = 0, n_full = 0;               // tests run, per warp
     unsigned qn = 0;                                        // queued pairs (warp-uniform)
-    unsigned cn = 0;                                        // queued candidates
 
     // the verified solve of pair-queue items [base, base + cnt)
     auto drain = [&](unsigned base, unsigned cnt) {
@@ -757,6 +816,29 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
         drain_full();
     };
 
+    if (FACE == 1 && a.fp32_filter) {
+        // the candidates the quad-level test (k_quad_filter) could not clear, 32
+        // per warp round, through the per-pair path
+        const unsigned long long nk = clamp_count(&a.ctr->qkeep, a.cand_cap);
+        const unsigned long long wstride = (unsigned long long)gridDim.x * (blockDim.x >> 5) * 32;
+        for (unsigned long long b0 = (blockIdx.x * (unsigned long long)(blockDim.x >> 5) + warp) * 32; b0 < nk;
+             b0 += wstride) {
+            const unsigned cnt = (unsigned)min(32ULL, nk - b0);
+            if ((unsigned)lane < cnt) c_cand[warp][lane] = a.qsurv[b0 + lane];
+            __syncwarp();
+            cand_round(0, cnt);
+            __syncwarp();
+        }
+        if (qn) {
+            drain(0, qn);
+            __syncwarp();
+        }
+        if (lane == 0) {
+            if (n_sat) atomicAdd(&a.ctr->sat, n_sat);
+            if (n_full) atomicAdd(&a.ctr->fp32, n_full);
+        }
+        return;
+    }
     for (unsigned long long g0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x - lane;
          g0 < n; g0 += stride) {
         const unsigned long long g = g0 + lane;
@@ -791,41 +873,45 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
             }
             pair_tests(valid, (uint32_t)g, 0, X, Y, false);
             drain_full();
-        } else {
-            // the quads' four vertices, (i,k) (i+1,k) (i,k+1) (i+1,k+1), and the
-            // quad-level test
-            bool need = false;
-            if (valid) {
-                float4 QA[4][2], QB[4][2];
-                gather_quad_split(a.meshes[pr.x], cd.faceA, QA);
-                gather_quad_split(a.meshes[pr.y], cd.faceB, QB);
-                need = !quad_sat_reject(QA, QB, a.tau);
-            }
-            n_quad += __popc(__ballot_sync(FULL, valid));
-            const uint32_t want = __ballot_sync(FULL, need);
-            if (need) c_cand[warp][cn + __popc(want & lt)] = (uint32_t)g;
-            cn += __popc(want);
-            __syncwarp();
-            if (cn >= 32) {
-                cn -= 32;
-                cand_round(cn, 32);
-                __syncwarp();
-            }
         }
-    }
-    if (FACE == 1 && cn) {
-        cand_round(0, cn);
-        __syncwarp();
     }
     if (qn) {
         drain(0, qn);
         __syncwarp();
     }
     if (lane == 0) {
-        if (n_quad) atomicAdd(&a.ctr->quad, n_quad);
         if (n_sat) atomicAdd(&a.ctr->sat, n_sat);
         if (n_full) atomicAdd(&a.ctr->fp32, n_full);
     }
+}
+
+// Stage 1a (quad faces): the quad-level separating-axis test of every candidate
+// on the FP32 roundings of its quads' vertices; the candidates it cannot clear
+// are listed for the per-pair path of k_narrow_filter.
+__global__ void __launch_bounds__(256, 3) k_quad_filter(NarrowArgs a) {
+    if (a.ctr->cand > a.cand_cap) return;
+    const unsigned long long n = a.ctr->cand;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    unsigned long long n_quad = 0;
+    for (unsigned long long g0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x - lane;
+         g0 < n; g0 += stride) {
+        const unsigned long long g = g0 + lane;
+        const bool valid = g < n;
+        bool need = false;
+        if (valid) {
+            const Cand cd = a.cand[g];
+            const int2 pr = a.pairs[cd.pair];
+            float4 QA[4], QB[4];
+            gather_quad_hi(a.meshes[pr.x], cd.faceA, QA);
+            gather_quad_hi(a.meshes[pr.y], cd.faceB, QB);
+            need = !quad_sat_reject_hi(QA, QB, a.tau);
+        }
+        n_quad += __popc(__ballot_sync(FULL, valid));
+        const unsigned long long pos = warp_append(&a.ctr->qkeep, need, FULL);
+        if (need && pos < a.cand_cap) a.qsurv[pos] = (uint32_t)g;
+    }
+    if (lane == 0 && n_quad) atomicAdd(&a.ctr->quad, n_quad);
 }
 
 // Stage 2: the FP64 solve for the survivors
@@ -1100,8 +1186,12 @@ void configure_narrow() {
 }
 
 void launch_narrow(const NarrowArgs &a, int face_level, int sms, int grid, cudaStream_t st) {
-    if (face_level == 0) k_narrow_filter<0><<<sms * filter_resident<0>(), 256, 0, st>>>(a);
-    else k_narrow_filter<1><<<sms * filter_resident<1>(), 256, 0, st>>>(a);
+    if (face_level == 0) {
+        k_narrow_filter<0><<<sms * filter_resident<0>(), 256, 0, st>>>(a);
+    } else {
+        if (a.fp32_filter) k_quad_filter<<<sms * 3 * 4, 256, 0, st>>>(a);
+        k_narrow_filter<1><<<sms * filter_resident<1>(), 256, 0, st>>>(a);
+    }
     k_narrow_fp64<<<grid, 256, 0, st>>>(a);
 }
 

@@ -97,6 +97,7 @@ struct Buffers {
     uint2 *tstart;
     void *sort_scratch;
     Cand *cand, *surv;
+    uint32_t *qsurv;
     tms_hit *hits;
     uint64_t *hk, *hk2, *okeys;
     uint32_t *hv, *hv2, *keep, *kscan;
@@ -139,6 +140,7 @@ size_t carve(unsigned char *base, Buffers &b) {
     // narrow phase and merge, over the broad phase's bytes
     c.off = phase;
     b.surv = c.take<Cand>(kSurvCap);
+    b.qsurv = c.take<uint32_t>(kCandCap);
     b.hits = c.take<tms_hit>(kRawHitCap);
     b.hk = c.take<uint64_t>(kRawHitCap);
     b.hk2 = c.take<uint64_t>(kRawHitCap);
@@ -336,6 +338,7 @@ extern "C" tms_status tms_search_noalloc(tms_mesh A, tms_mesh B, const tms_param
     launch_emit(ea, p.precision, p.face_level, grid / 2, s);
     NarrowArgs na;
     na.cand = b.cand; na.cand_cap = kCandCap; na.surv = b.surv; na.surv_cap = kSurvCap;
+    na.qsurv = b.qsurv;
     na.meshes = b.tables->meshes; na.pairs = b.tables->pairs; na.ctr = b.ctr; na.hits = b.hits;
     na.hit_key = b.hk; na.hit_val = b.hv; na.hit_cap = kRawHitCap; na.tau = p.tau;
     na.tri_bits = tri_bits; na.fp32_filter = p.narrow_filter;

@@ -534,8 +534,9 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
         const uint32_t T = nA * nB;
         tests += T;
         // t / nB for t < 1024, nB <= 32: (t + 1/2) / nB lies at least 1/64 from
-        // an integer, far beyond the FP32 error of (t + 1/2) * (1 / nB)
-        const float rB = 1.0f / (float)nB;
+        // an integer, far beyond the error of (t + 1/2) times an approximate
+        // reciprocal of nB (a few ulps: below 1e-4 absolute here)
+        const float rB = __fdividef(1.0f, (float)nB);
         for (uint32_t base = 0; base < T; base += 32) {
             const uint32_t t = base + lane;
             bool ov = false;
