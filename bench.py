@@ -56,6 +56,12 @@ SAT_FLOPS = 551
 # (180), kappa and delta (40), two dual choices (28), four interval tests over
 # eight vertices (360)
 QUAD_SAT_FLOPS = 964
+# FP64 operations of one narrow-phase solve of Eq. (precise) (an FMA counts 2):
+# the 16 matrix entries and 4 right-hand-side entries (20), the squared column
+# norms (28), elimination with partial pivoting (46) and back substitution
+# (16); the 4 pivot reciprocals, the margin, the point, rho and the (theta, s)
+# estimates are not counted
+FP64_SOLVE_FLOPS = 110
 
 
 # the broad phase's stages (tms_last_stage_ms labels), and per reported stage the
@@ -343,18 +349,29 @@ def run_tms(args, ws, rank, local):
     stream = torch.cuda.Stream(device)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device)
     out = torch.empty((1 << 17, tms.HIT_BYTES), dtype=torch.uint8, device=device)
-    kw = dict(timing=1)
+    kw = dict(timing=0)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             h = tms.search(A, B, out=out, stream=stream, **kw)
         n_hits = len(h)
         stats = tms.last_stats(stream)
+        # per-stage device times from a separate plan whose graph records an event
+        # between stages (the events cost time, so the timed steps run without them)
+        stage_sum = {}
+        n_stage_runs = 10
+        for i in range(3 + n_stage_runs):
+            flush.fill_(i & 0xFF)
+            tms.search(A, B, out=out, stream=stream, timing=1)
+            if i >= 3:
+                for k, v in tms.last_stage_ms(stream).items():
+                    stage_sum[k] = stage_sum.get(k, 0.0) + v
+        stage_ms = {k: v / n_stage_runs for k, v in stage_sum.items()}
 
     if args.only_extras:
         # just the named secondary measurements (for profiling them on their own)
         fp64_tf = tms.probe_fp64_tflops()
-        runs = {"plain_fp64": lambda: plain_fp64(tms, A, B, out, stream, flush, h),
+        runs = {"plain_fp64": lambda: plain_fp64(tms, A, B, out, stream, flush, h, fp64_tf),
                 "batched": lambda: batched_search(tms, device, stream, flush),
                 "adjoint": lambda: adjoint_timing(tms, device, stream),
                 "refine": lambda: refine_timing(tms, pair, h, stream, flush, fp64_tf),
@@ -375,7 +392,6 @@ def run_tms(args, ws, rank, local):
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage_sum = {}
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
@@ -384,8 +400,6 @@ def run_tms(args, ws, rank, local):
                 starts[i].record(stream)
                 h = tms.search(A, B, out=out, stream=stream, **kw)
                 ends[i].record(stream)
-                for k, v in tms.last_stage_ms(stream).items():
-                    stage_sum[k] = stage_sum.get(k, 0.0) + v
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -393,7 +407,6 @@ def run_tms(args, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     value, ms_per_step = job_times(total_ms, args.steps, ws)
-    stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
 
     # Roofline of the broad phase (A2-A7: bounds pass through candidate emission),
     # the search's HBM-bound part, as one unit: its algorithmic bytes
@@ -443,11 +456,11 @@ def run_tms(args, ws, rank, local):
     fp64 = None
     try:
         peak64 = tms.probe_fp64_tflops()
-        flops = 110.0 * stats["fp64_solves"]
+        flops = float(FP64_SOLVE_FLOPS) * stats["fp64_solves"]
         t_narrow = stage_ms.get("narrow", 0.0)
         ach = flops / (t_narrow / 1e3) / 1e12 if t_narrow > 0 else None
         fp64 = {"kernel": "tms::k_narrow", "solves_fp64": stats["fp64_solves"],
-                "candidates": stats["candidates"], "flops_per_solve": 110,
+                "candidates": stats["candidates"], "flops_per_solve": FP64_SOLVE_FLOPS,
                 "achieved_tflops": ach, "peak_tflops": peak64,
                 "frac": (ach / peak64) if (ach and peak64) else None,
                 "peak_kind": "measured FP64 FMA-chain probe on this GPU"}
@@ -488,7 +501,8 @@ def run_tms(args, ws, rank, local):
 
     extras = None
     if args.extras:
-        extras = {"plain_fp64": plain_fp64(tms, A, B, out, stream, flush, h),
+        extras = {"plain_fp64": plain_fp64(tms, A, B, out, stream, flush, h,
+                                           (fp64 or {}).get("peak_tflops")),
                   "batched": batched_search(tms, device, stream, flush),
                   "adjoint": adjoint_timing(tms, device, stream),
                   "refine": refine_timing(tms, pair, h, stream, flush,
@@ -537,22 +551,37 @@ def _timed(fn, stream, flush, steps):
     return statistics.median(ts)
 
 
-def plain_fp64(tms, A, B, out, stream, flush, mixed_hits):
+def plain_fp64(tms, A, B, out, stream, flush, mixed_hits, fp64_tf=None):
     """The same search with FP64 boxes and cell keys and no FP32 filters (the
-    plain path): its time and whether it finds the identical hit set."""
+    plain path): its time, whether it finds the identical hit set, and the FP64
+    rate of its narrow stage (every triangle pair of every candidate solved,
+    FP64_SOLVE_FLOPS each) against the measured FP64 peak."""
     kw = dict(precision=0, narrow_filter=0)
     with torch.cuda.stream(stream):
         for _ in range(3):
             h = tms.search(A, B, out=out, stream=stream, **kw)
         same = (torch.equal(h.triA, mixed_hits.triA) and torch.equal(h.triB, mixed_hits.triB))
     ms = _timed(lambda: tms.search(A, B, out=out, stream=stream, **kw), stream, flush, 20)
+    with torch.cuda.stream(stream):
+        tms.search(A, B, out=out, stream=stream, timing=1, **kw)
+    st = tms.last_stats(stream)
+    stage = tms.last_stage_ms(stream)
+    t_n = stage.get("narrow", 0.0)
+    ach = FP64_SOLVE_FLOPS * st["fp64_solves"] / (t_n * 1e-3) / 1e12 if t_n > 0 else None
     return {"ms_per_search": ms, "hits": len(h), "identical_hit_set_to_mixed": bool(same),
+            "fp64_solves": st["fp64_solves"], "narrow_ms": t_n,
+            "fp64": {"kernel": "tms::k_narrow_fp64", "flops_per_solve": FP64_SOLVE_FLOPS,
+                     "achieved_tflops": ach, "peak_tflops": fp64_tf,
+                     "frac": (ach / fp64_tf) if (ach and fp64_tf) else None,
+                     "peak_kind": "measured FP64 FMA-chain probe on this GPU"},
             "params": "precision=0 (FP64 boxes and keys), narrow_filter=0 (every pair to FP64)"}
 
 
 def batched_search(tms, device, stream, flush, n_pairs=256):
     """The batched search of the 256 uneven mesh pairs of the alpha sweep (one
-    CUDA graph replay per batch): total and per-pair time."""
+    CUDA graph replay per batch): total and per-pair time; beside it the same
+    sweep as a loop of one search per pair, in the plain FP64 form and in the
+    mixed form, and the batched plain form, each with the identical hit set."""
     import synth
     sizes = synth.config4_sizes(n_pairs=n_pairs)
     pairs = [synth.config4_pair(p, n_pairs=n_pairs, sizes=sizes) for p in range(n_pairs)]
@@ -563,15 +592,62 @@ def batched_search(tms, device, stream, flush, n_pairs=256):
     tris = sum(2 * p.A.N * (p.A.M - 1) + 2 * p.B.N * (p.B.M - 1) for p in pairs)
     out = torch.empty((1 << 18, tms.HIT_BYTES), dtype=torch.uint8, device=device)
     offs = torch.empty(n_pairs + 1, dtype=torch.int64, device=device)
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            h = tms.search_batched(As, Bs, out=out, offsets=offs, stream=stream)
-    stats = tms.last_stats(stream)
-    ms = _timed(lambda: tms.search_batched(As, Bs, out=out, offsets=offs, stream=stream),
-                stream, flush, 10)
+
+    def keys(h):
+        return list(zip(h.pair.tolist(), h.triA.tolist(), h.triB.tolist()))
+
+    def batched(**kw):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                h = tms.search_batched(As, Bs, out=out, offsets=offs, stream=stream, **kw)
+        k = keys(h)
+        st = tms.last_stats(stream)
+        ms = _timed(lambda: tms.search_batched(As, Bs, out=out, offsets=offs, stream=stream, **kw),
+                    stream, flush, 10)
+        return ms, k, st
+
+    one = torch.empty((1 << 14, tms.HIT_BYTES), dtype=torch.uint8, device=device)
+
+    def loop(**kw):
+        found = []
+
+        def run():
+            found.clear()
+            for p in range(n_pairs):
+                h = tms.search(As[p], Bs[p], out=one, stream=stream, **kw)
+                found.extend((p, a, b) for a, b in zip(h.triA.tolist(), h.triB.tolist()))
+        with torch.cuda.stream(stream):
+            run()
+        ms = _timed(run, stream, flush, 2)
+        return ms, sorted(found)
+
+    ms, k, stats = batched()
+    # the autotuner's per-size-class choice, read back through the cache file
+    cache = os.path.join(tempfile.mkdtemp(), "tune.txt")
+    t0 = time.perf_counter()
+    best, _ = tms.autotune(As, Bs, cache_path=cache, stream=stream)
+    tune_s = time.perf_counter() - t0
+    ms_tuned, k_tuned, _ = batched(autotune_cache=cache)
+    classes = [l.split() for l in open(cache).read().splitlines() if l.startswith("C|")]
+    ms_plain_b, k_plain_b, _ = batched(precision=0, narrow_filter=0)
+    ms_loop_plain, k_loop_plain = loop(precision=0, narrow_filter=0)
+    ms_loop_mixed, k_loop_mixed = loop()
     return {"pairs": n_pairs, "triangles_total": tris, "ms_per_batch": ms,
-            "ms_per_pair": ms / n_pairs, "hits": len(h), "launches_per_batch": stats["kernels"],
-            "entries": stats["entries"], "candidates": stats["candidates"]}
+            "ms_per_pair": ms / n_pairs, "hits": len(k), "launches_per_batch": stats["kernels"],
+            "entries": stats["entries"], "candidates": stats["candidates"],
+            "tuned_ms_per_batch": ms_tuned, "tuning_s": tune_s,
+            "tuned": {"face_level": best["face_level"], "patch": best["patch"],
+                      "block_faces": best["block_faces"], "tile_rows": best["tile_rows"],
+                      "cell_mult_by_size_class": {c[0].split("class=")[1].split("|")[0]: float(c[1])
+                                                  for c in classes}},
+            "plain_fp64_batched_ms": ms_plain_b,
+            "plain_fp64_loop_ms": ms_loop_plain,
+            "mixed_loop_ms": ms_loop_mixed,
+            "speedup_batched_vs_plain_loop": ms_loop_plain / ms if ms > 0 else None,
+            "identical_hit_set": {"plain_batched": k_plain_b == k, "plain_loop": k_loop_plain == k,
+                                  "mixed_loop": k_loop_mixed == k, "tuned": k_tuned == k},
+            "loop_note": "one tms_search per pair on the same stream (each synchronises to read "
+                         "its count), host time included"}
 
 
 def adjoint_timing(tms, device, stream):

@@ -77,7 +77,11 @@ struct Plan {
     // which the cell passes and the grid emission read instead of the meshes
     bool patch = false;
     MeshDev *d_pmeshes = nullptr;
+    // per-pair cell multipliers (size classes tuned by tms_autotune), or empty
+    std::vector<float> cm_pair;
+    float *d_cm_pair = nullptr;
     unsigned char *pbox = nullptr;    // patch boxes of all meshes
+    unsigned char *qbox = nullptr;    // their quarter boxes
     Cand *ppairs = nullptr;
     unsigned long long ppair_cap = 0;
     int2 *d_pairs = nullptr;
@@ -146,7 +150,7 @@ struct Plan {
         if (st) cudaStreamSynchronize(st);
         free_scratch();
         void *ptrs[] = {d_meshes, d_pairs, d_pass_all, d_pass_A, d_pass_B, d_bounds,
-                        d_ctr, partials, split, fbox, d_pmeshes, pbox};
+                        d_ctr, partials, split, fbox, d_pmeshes, pbox, qbox, d_cm_pair};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         if (h_ctr) cudaFreeHost(h_ctr);
@@ -251,7 +255,7 @@ struct Plan {
         fa.patch = 0;
         if (patch) fa.meshes = d_pmeshes;
         mark(2, s);
-        launch_grid_params(d_bounds, d_pairs, nPairs, d_grids, p.cell_mult, s);
+        launch_grid_params(d_bounds, d_pairs, nPairs, d_grids, p.cell_mult, s, d_cm_pair);
         kernels += 2;
         mark(3, s);
 
@@ -442,10 +446,12 @@ void fill_pass(std::vector<PassEntry> &v, long long &tiles, long long &fslots, c
 }
 
 tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms_params &prm,
-                     cudaStream_t user, void *dHits, long long hitCap, long long *dOffsets,
-                     int device, Plan **out) {
+                     const std::vector<float> &cm_pair, cudaStream_t user, void *dHits,
+                     long long hitCap, long long *dOffsets, int device, Plan **out) {
     Plan *P = new Plan();
     P->prm = prm;
+    P->prm.autotune_cache = nullptr;
+    P->cm_pair = cm_pair;
     P->user = user;
     P->dHits = dHits;
     P->hitCap = hitCap;
@@ -502,6 +508,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
         md.npk = patch ? (md.nqk + kPatchK - 1) / kPatchK : 0;
         md.pmagic = recip64((unsigned long long)md.npi);
         md.pbox = nullptr;
+        md.qbox = nullptr;
         pbox_off.push_back(pbox_total);
         pbox_total += ((unsigned long long)md.npi * md.npk * box_bytes + 255) / 256 * 256;
     }
@@ -510,11 +517,15 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
         cudaError_t se = dalloc(&P->split, P->split_total);
         if (se == cudaSuccess) se = dalloc(&P->fbox, fbox_total);
         if (se == cudaSuccess && patch) se = dalloc(&P->pbox, pbox_total);
+        if (se == cudaSuccess && patch) se = dalloc(&P->qbox, 4 * pbox_total);
         if (se != cudaSuccess) { g_err = cudaGetErrorString(se); delete P; return TMS_ERR_CUDA; }
         for (size_t i = 0; i < meshes.size(); ++i) {
             meshes[i].split = P->split + P->split_off[i];
             meshes[i].fbox = P->fbox + fbox_off[i];
-            if (patch) meshes[i].pbox = P->pbox + pbox_off[i];
+            if (patch) {
+                meshes[i].pbox = P->pbox + pbox_off[i];
+                meshes[i].qbox = P->qbox + 4 * pbox_off[i];
+            }
         }
         // a patch view is a mesh of npi x npk quad-like slots, all valid
         for (const MeshDev &md : meshes) {
@@ -549,6 +560,11 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
 #define TMS_PCK(call) do { if ((e = (call)) != cudaSuccess) { g_err = cudaGetErrorString(e); delete P; return TMS_ERR_CUDA; } } while (0)
     TMS_PCK(dalloc(&P->d_meshes, meshes.size()));
     TMS_PCK(dalloc(&P->d_pmeshes, pmeshes.size()));
+    if (!cm_pair.empty()) {
+        TMS_PCK(dalloc(&P->d_cm_pair, cm_pair.size()));
+        TMS_PCK(cudaMemcpy(P->d_cm_pair, cm_pair.data(), cm_pair.size() * sizeof(float),
+                           cudaMemcpyHostToDevice));
+    }
     TMS_PCK(dalloc(&P->d_pairs, pairs.size()));
     TMS_PCK(dalloc(&P->d_pass_all, pall.size()));
     TMS_PCK(dalloc(&P->d_pass_A, pa.size()));
@@ -610,10 +626,11 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
 }
 
 Plan *find_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms_params &prm,
-                cudaStream_t user, void *dHits, long long hitCap, long long *dOffsets, int device) {
+                const std::vector<float> &cm_pair, cudaStream_t user, void *dHits, long long hitCap,
+                long long *dOffsets, int device) {
     for (Plan *P : g_plans) {
         if (P->device != device || P->user != user || P->dHits != dHits || P->hitCap != hitCap ||
-            P->dOffsets != dOffsets || P->nPairs != nPairs)
+            P->dOffsets != dOffsets || P->nPairs != nPairs || P->cm_pair != cm_pair)
             continue;
         tms_params q = prm;
         q.tile_rows = q.tile_rows == 8 ? 8 : 4;
@@ -634,15 +651,17 @@ void drop_plans_if(bool (*pred)(Plan *, void *), void *ctx) {
     g_plans.swap(keep);
 }
 
-tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms_params *params,
-                       tms_hit *dHits, long long hitCap, long long *dOffsets, long long *nHits,
-                       void *stream) {
+tms_status search_core(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms_params &prm,
+                       const std::vector<float> &cm_pair, tms_hit *dHits, long long hitCap,
+                       long long *dOffsets, long long *nHits, void *stream) {
     if (!nHits || nPairs <= 0 || !A || !B || hitCap < 0 || (hitCap > 0 && !dHits)) return TMS_ERR_ARG;
-    tms_params prm;
-    tms_params_default(&prm);
-    if (params) prm = *params;
     tms_status s = validate_params(prm);
     if (s != TMS_OK) return s;
+    if (!cm_pair.empty()) {
+        if ((int)cm_pair.size() != nPairs) return TMS_ERR_ARG;
+        for (float c : cm_pair)
+            if (!(c >= 1.0f) || !(c < 1e6f)) return TMS_ERR_ARG;
+    }
     int device = 0;
     TMS_CK(cudaGetDevice(&device));
     for (int i = 0; i < nPairs; ++i) {
@@ -658,7 +677,7 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
         configure_narrow();
         g_configured_mask |= 1 << device;
     }
-    Plan *P = find_plan(A, B, nPairs, prm, user, dHits, hitCap, dOffsets, device);
+    Plan *P = find_plan(A, B, nPairs, prm, cm_pair, user, dHits, hitCap, dOffsets, device);
     if (!P) {
         if (g_plans.size() >= 16) {
             auto it = std::min_element(g_plans.begin(), g_plans.end(),
@@ -666,7 +685,7 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
             delete *it;
             g_plans.erase(it);
         }
-        s = make_plan(A, B, nPairs, prm, user, dHits, hitCap, dOffsets, device, &P);
+        s = make_plan(A, B, nPairs, prm, cm_pair, user, dHits, hitCap, dOffsets, device, &P);
         if (s != TMS_OK) return s;
         g_plans.push_back(P);
     }
@@ -765,6 +784,27 @@ tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
     return TMS_OK;
 }
 
+tms_status search_impl(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms_params *params,
+                       tms_hit *dHits, long long hitCap, long long *dOffsets, long long *nHits,
+                       void *stream) {
+    if (!nHits || nPairs <= 0 || !A || !B) return TMS_ERR_ARG;
+    tms_params prm;
+    tms_params_default(&prm);
+    if (params) prm = *params;
+    std::vector<float> cm_pair;
+    if (prm.autotune_cache) {
+        for (int i = 0; i < nPairs; ++i) {
+            MeshDev v;
+            int d;
+            if (!A[i] || !B[i] || mesh_view(A[i], &v, &d) != TMS_OK || mesh_view(B[i], &v, &d) != TMS_OK)
+                return TMS_ERR_STATE;
+        }
+        tune_lookup(A, B, nPairs, prm.autotune_cache, &prm, &cm_pair);
+        prm.autotune_cache = nullptr;
+    }
+    return search_core(A, B, nPairs, prm, cm_pair, dHits, hitCap, dOffsets, nHits, stream);
+}
+
 bool plan_uses(Plan *P, void *ctx) {
     long long id = *(long long *)ctx;
     return std::find(P->ids.begin(), P->ids.end(), id) != P->ids.end();
@@ -774,6 +814,14 @@ bool plan_on_stream(Plan *P, void *ctx) {
 }
 
 }  // namespace
+
+tms_status tms::search_with_cm(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms_params &params,
+                               const std::vector<float> &cm_pair, tms_hit *dHits, long long hitCap,
+                               long long *dOffsets, long long *nHits, void *stream) {
+    tms_params prm = params;
+    prm.autotune_cache = nullptr;
+    return search_core(A, B, nPairs, prm, cm_pair, dHits, hitCap, dOffsets, nHits, stream);
+}
 
 extern "C" {
 

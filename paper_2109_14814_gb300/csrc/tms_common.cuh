@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/tms.h"
 
@@ -65,6 +66,10 @@ struct MeshDev {
                           // kPatchK quads the union of their boxes, in the
                           // format of fbox, written by the bounds pass; slot =
                           // patch row * npi + patch column
+    void *qbox;           // plan scratch (patch level): per patch its four
+                          // quarter boxes -- quad rows (0-1, 2-3) x columns
+                          // (0-3, 4-7), slot 4 p + 2 row half + column half;
+                          // a quarter without quads holds an empty box
     int npi;              // patches per quad row, ceil(nqi / kPatchI) (0: none)
     int npk;              // patch rows, ceil(nqk / kPatchK)
     unsigned long long pmagic;  // ceil(2^64 / npi) for npi >= 2: a patch id's row
@@ -390,8 +395,9 @@ cudaError_t configure_face_pass();
 // counts are multiples of four
 void launch_search_init(Bounds *b, int n, Counters *ctr, uint32_t *bmA, unsigned long long n32a,
                         uint32_t *bmH, unsigned long long n32h, int grid, cudaStream_t st);
+// cm_pair: per-pair cell multipliers (device, n_pairs), or NULL for cell_mult
 void launch_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *g,
-                        float cell_mult, cudaStream_t st);
+                        float cell_mult, cudaStream_t st, const float *cm_pair = nullptr);
 
 // polls of one device-side wait when tms_params.spin_limit is 0
 constexpr unsigned long long kDefaultSpinLimit = 1ULL << 22;
@@ -604,6 +610,19 @@ void launch_adjoint(const AdjointArgs &a, cudaStream_t st);
 
 // device view of a mesh handle (TMS_ERR_STATE for an invalid handle)
 tms_status mesh_view(tms_mesh m, MeshDev *view, int *device);
+
+// The search with per-pair cell multipliers (empty: params->cell_mult for all);
+// tms_search and tms_search_batched after resolving params->autotune_cache.
+tms_status search_with_cm(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms_params &params,
+                          const std::vector<float> &cm_pair, tms_hit *dHits, long long hitCap,
+                          long long *dOffsets, long long *nHits, void *stream);
+
+// Tuned settings for these meshes from an autotune cache file: overrides the
+// face level, patch level, bounds-pass tile and cell multiplier in *p and sets
+// per-pair multipliers (empty when no size class has its own); false when the
+// file holds nothing for them.  Each file is read once per batch and process.
+bool tune_lookup(const tms_mesh *A, const tms_mesh *B, int nPairs, const char *path, tms_params *p,
+                 std::vector<float> *cm_pair);
 
 // Message returned by tms_last_error() on the calling thread.
 void set_last_error(const std::string &msg);

@@ -188,11 +188,11 @@ __device__ __forceinline__ void box_union(BoxT<PREC> &b, const BoxT<PREC> &x) {
 #pragma unroll
     for (int d = 0; d < 4; ++d) { b.lo[d] = min(b.lo[d], x.lo[d]); b.hi[d] = max(b.hi[d], x.hi[d]); }
 }
-// union over the kPatchI lanes of a patch (aligned groups of lanes)
+// union over aligned groups of `lanes` lanes (a quarter's 4 columns, a patch's 8)
 template <int PREC>
-__device__ __forceinline__ void box_reduce_patch(BoxT<PREC> &b) {
+__device__ __forceinline__ void box_reduce_lanes(BoxT<PREC> &b, int from, int lanes) {
 #pragma unroll
-    for (int off = 1; off < kPatchI; off <<= 1) {
+    for (int off = from; off < lanes; off <<= 1) {
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
             b.lo[d] = min(b.lo[d], __shfl_xor_sync(0xffffffffu, b.lo[d], off));
@@ -371,9 +371,13 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
         // the kPatchI lanes of the patch (every lane of the block takes part:
         // the row loop and its shuffles are uniform).  The widest extent the
         // grid needs is then the widest patch's.
-        BoxT<PREC> prev, pcol;
+        // this column's boxes over the upper and lower halves of the patch row
+        BoxT<PREC> prev, ptop, pbot;
         box_empty(prev);
-        box_empty(pcol);
+        box_empty(ptop);
+        box_empty(pbot);
+        // the patch exists when its first column is in the tile
+        const bool patch_lane = (t & ~(kPatchI - 1)) < cols_q;
         if (col_valid) {
             box_init(prev, sv[t]);
             box_add(prev, sv[t + 1]);
@@ -392,18 +396,30 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
                 const uint32_t q = (uint32_t)(kq0 + r) * (uint32_t)m.N + (uint32_t)i;
                 acc.add_bounds(bq);
                 write_fbox<PREC>(m, q, bq);
-                box_union<PREC>(pcol, bq);
+                if ((r % kPatchK) < kPatchK / 2) box_union<PREC>(ptop, bq);
+                else box_union<PREC>(pbot, bq);
                 prev = next;
             }
             if ((r % kPatchK) == kPatchK - 1 || r == rows_q - 1) {
-                box_reduce_patch<PREC>(pcol);
-                if (col_valid && (t % kPatchI) == 0) {
-                    const uint32_t p = (uint32_t)((kq0 + r) / kPatchK) * (uint32_t)m.npi +
-                                       (uint32_t)(i / kPatchI);
-                    write_box<PREC>(m.pbox, p, pcol);
-                    acc.add_width(pcol);
+                // quarters over 4 columns, then the patch over both column halves
+                box_reduce_lanes<PREC>(ptop, 1, kPatchI / 2);
+                box_reduce_lanes<PREC>(pbot, 1, kPatchI / 2);
+                BoxT<PREC> pb = ptop;
+                box_union<PREC>(pb, pbot);
+                box_reduce_lanes<PREC>(pb, kPatchI / 2, kPatchI);
+                const uint32_t p = (uint32_t)((kq0 + r) / kPatchK) * (uint32_t)m.npi +
+                                   (uint32_t)(i / kPatchI);
+                if (patch_lane && (t % (kPatchI / 2)) == 0) {
+                    const uint32_t half = (uint32_t)((t % kPatchI) / (kPatchI / 2));
+                    write_box<PREC>(m.qbox, 4 * p + half, ptop);
+                    write_box<PREC>(m.qbox, 4 * p + 2 + half, pbot);
                 }
-                box_empty(pcol);
+                if (patch_lane && (t % kPatchI) == 0) {
+                    write_box<PREC>(m.pbox, p, pb);
+                    acc.add_width(pb);
+                }
+                box_empty(ptop);
+                box_empty(pbot);
             }
         }
     } else if (FACE == 1 && col_valid) {
@@ -686,7 +702,7 @@ __global__ void k_search_init(Bounds *b, int n, Counters *ctr, uint32_t *bmA,
 // the widest face extent of either mesh, so that a face spans at most two cells
 // per coordinate; capped so that a pair's grid has fewer than 2^31 cells.
 __global__ void k_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *grids,
-                              float cell_mult) {
+                              float cell_mult, const float *cm_pair) {
     // one warp per pair, lane d & 3 speaks for coordinate d: the FP64 chain of
     // one coordinate instead of four (FP64 arithmetic is slow on GB300)
     const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -697,7 +713,8 @@ __global__ void k_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, G
     const double o = fmax(ord_dec(A.lo[d]), ord_dec(B.lo[d]));
     const double e = fmin(ord_dec(A.hi[d]), ord_dec(B.hi[d]));
     const int empty = (A.faces == 0 || B.faces == 0 || __any_sync(FULL, !(o <= e))) ? 1 : 0;
-    double step = (double)cell_mult * fmax(ord_dec(A.w[d]), ord_dec(B.w[d]));
+    const float cm = cm_pair ? cm_pair[p] : cell_mult;
+    double step = (double)cm * fmax(ord_dec(A.w[d]), ord_dec(B.w[d]));
     const double range = empty ? 0.0 : e - o;
     int n;
     if (!(range > 0.0) || !(step > 0.0)) {
@@ -803,8 +820,8 @@ void launch_search_init(Bounds *b, int n, Counters *ctr, uint32_t *bmA, unsigned
 }
 
 void launch_grid_params(const Bounds *b, const int2 *pairs, int n_pairs, Grid *g,
-                        float cell_mult, cudaStream_t st) {
-    k_grid_params<<<(n_pairs + 3) / 4, 128, 0, st>>>(b, pairs, n_pairs, g, cell_mult);
+                        float cell_mult, cudaStream_t st, const float *cm_pair) {
+    k_grid_params<<<(n_pairs + 3) / 4, 128, 0, st>>>(b, pairs, n_pairs, g, cell_mult, cm_pair);
 }
 
 }  // namespace tms

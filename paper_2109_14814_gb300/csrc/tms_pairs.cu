@@ -442,13 +442,16 @@ __device__ __forceinline__ void load_side(const QuadSide &m, uint32_t patch, int
     if (valid) box.load(m.fbox, q);
 }
 
-// One warp per patch pair, grid-stride over the pairs.  Lane l holds quad
-// (row l / kPatchI, column l % kPatchI) of each patch.  A quad whose box misses
-// the other patch's box cannot overlap any quad of it (the patch box holds
-// them all), so each side is first cut to its quads that meet the other
-// patch; the pairs of the survivors (nA x nB of them, 32 per round, pair t =
-// (t / nB, t % nB)) take the box test of Sec. 6.2.2, optionally the Moller
-// test of Sec. 6.2.3, and are appended through a per-warp stage.
+// One warp per patch pair, grid-stride over the pairs.  Each patch carries
+// four quarter boxes (2 x 2 blocks of 4 x 2 quads).  First the 16 quarter
+// pairs, one per lane: a patch pair none of whose quarter pairs overlap holds
+// no overlapping quad pair and is done before any quad box is read.  Then lane
+// l holds quad (row l / kPatchI, column l % kPatchI) of each patch; a quad
+// that meets none of the other patch's quarter boxes cannot overlap any of its
+// quads (they all lie in those boxes), so each side is cut to its quads that
+// meet one; the pairs of the survivors (nA x nB of them, 32 per round, pair t =
+// (t / nB, t % nB)) take the box test of Sec. 6.2.2, optionally the Moller test
+// of Sec. 6.2.3, and are appended through a per-warp stage.
 // patch id -> (patch row, patch column): the quotient by npi from a 64-bit
 // reciprocal (exact for 32-bit ids, npi >= 2)
 __device__ __forceinline__ void patch_rc(uint32_t patch, uint32_t npi, unsigned long long magic,
@@ -473,6 +476,7 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
     const unsigned long long gw = blockIdx.x * (unsigned long long)kPatchWarps + warp;
     const unsigned long long nw = (unsigned long long)gridDim.x * kPatchWarps;
     const int r = lane / kPatchI, c = lane % kPatchI;
+    const uint32_t qi = (uint32_t)(lane >> 2) & 3u, qj = (uint32_t)lane & 3u;   // this lane's quarter pair
     Cand *stage = sOut[warp];
     unsigned staged = 0;
     unsigned long long tests = 0;
@@ -482,7 +486,7 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
         if (pos < cap) cand_out[pos] = rec;
     };
     uint32_t cached_pair = 0xFFFFFFFFu;
-    const void *fbA = nullptr, *fbB = nullptr, *pbA = nullptr, *pbB = nullptr;
+    const void *fbA = nullptr, *fbB = nullptr, *qbA = nullptr, *qbB = nullptr;
     int NA = 1, nqiA = 0, nqkA = 0, NB = 1, nqiB = 0, nqkB = 0;
     uint32_t npiA = 1, npiB = 1;
     unsigned long long mgA = 0, mgB = 0;
@@ -493,11 +497,18 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
             pr = a.pairs[pp.pair];
             const MeshDev &ma = a.meshes[pr.x];
             const MeshDev &mb = a.meshes[pr.y];
-            fbA = ma.fbox; pbA = ma.pbox; NA = ma.N; nqiA = ma.nqi; nqkA = ma.nqk; npiA = ma.npi;
-            fbB = mb.fbox; pbB = mb.pbox; NB = mb.N; nqiB = mb.nqi; nqkB = mb.nqk; npiB = mb.npi;
+            fbA = ma.fbox; qbA = ma.qbox; NA = ma.N; nqiA = ma.nqi; nqkA = ma.nqk; npiA = ma.npi;
+            fbB = mb.fbox; qbB = mb.qbox; NB = mb.N; nqiB = mb.nqi; nqkB = mb.nqk; npiB = mb.npi;
             mgA = ma.pmagic;
             mgB = mb.pmagic;
             cached_pair = pp.pair;
+        }
+        // the 16 quarter pairs (lanes 16..31 repeat lanes 0..15)
+        {
+            EBox<PREC> xa, xb;
+            xa.load(qbA, 4 * pp.faceA + qi);
+            xb.load(qbB, 4 * pp.faceB + qj);
+            if (!__any_sync(FULL, boxes_overlap(xa, xb))) continue;
         }
         uint32_t pka, pia, pkb, pib;
         patch_rc(pp.faceA, npiA, mgA, pka, pia);
@@ -507,15 +518,23 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
         const bool va = kqa < nqkA && iqa < nqiA, vb = kqb < nqkB && iqb < nqiB;
         const uint32_t qa = (uint32_t)kqa * (uint32_t)NA + (uint32_t)iqa;
         const uint32_t qb = (uint32_t)kqb * (uint32_t)NB + (uint32_t)iqb;
-        EBox<PREC> ba, bb, PA, PB;
-        PA.load(pbA, pp.faceA);
-        PB.load(pbB, pp.faceB);
+        EBox<PREC> ba, bb;
         ba.set_empty();
         bb.set_empty();
         if (va) ba.load(fbA, qa);
         if (vb) bb.load(fbB, qb);
-        const bool sa = va && boxes_overlap(ba, PB);
-        const bool sb = vb && boxes_overlap(bb, PA);
+        // survivors: quads meeting some quarter of the other patch
+        bool sa = false, sb = false;
+#pragma unroll 1
+        for (uint32_t k = 0; k < 4; ++k) {
+            EBox<PREC> xa, xb;
+            xb.load(qbB, 4 * pp.faceB + k);
+            xa.load(qbA, 4 * pp.faceA + k);
+            sa |= boxes_overlap(ba, xb);
+            sb |= boxes_overlap(bb, xa);
+        }
+        sa &= va;
+        sb &= vb;
         const uint32_t mA = __ballot_sync(FULL, sa), mB = __ballot_sync(FULL, sb);
         if (!mA || !mB) continue;
         const uint32_t nA = __popc(mA), nB = __popc(mB);
