@@ -523,7 +523,9 @@ def run_tms(args, ws, rank, local):
                        parallelism=f"replicas x{ws}" if ws > 1 else "1 GPU",
                        hits=n_hits, candidates=stats["candidates"], entries=stats["entries"],
                        cells=stats["cells"], pair_slots=stats["pair_slots"],
-                       fp64_solves=stats["fp64_solves"]),
+                       patch_pairs=stats["patch_pairs"], patch_tests=stats["patch_tests"],
+                       quad_tests=stats["quad_tests"], sat_tests=stats["sat_tests"],
+                       fp32_solves=stats["fp32_solves"], fp64_solves=stats["fp64_solves"]),
         "roofline": roofline, "kernels": kernels, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clk.summary(), "gpu_launches": stats["kernels"] * args.steps,
         "source_hash": source_hash(),

@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
     }
     __syncwarp();
     stage_flush<kPatchFlush>(stage, staged, &a.ctr->cand, store);
-    for (int off = 16; off > 0; off >>= 1) tests += __shfl_xor_sync(FULL, tests, off);
+    // every lane counted the same tests (T is warp-uniform): one lane adds them
     if (lane == 0 && tests) atomicAdd(&a.ctr->ptests, tests);
 }
 
