@@ -595,6 +595,13 @@ struct DedupArgs {
 };
 void launch_dedup(const DedupArgs &a, int grid, cudaStream_t st);
 
+// The hit tail (sort, merge, output, offsets) in one block when the raw-hit
+// capacity is at most kSmallHits; keys are the unsorted hit keys, a.keys and
+// a.vals unused.  configure_hit_tail sets its shared-memory size (outside capture).
+constexpr unsigned kSmallHits = 16384;
+void launch_hit_tail(const DedupArgs &a, const uint64_t *keys, int key_bits, cudaStream_t st);
+cudaError_t configure_hit_tail();
+
 struct AdjointArgs {
     const tms_hit *hits;
     long long n;
