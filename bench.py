@@ -524,7 +524,8 @@ def run_tms(args, ws, rank, local):
                        hits=n_hits, candidates=stats["candidates"], entries=stats["entries"],
                        cells=stats["cells"], pair_slots=stats["pair_slots"],
                        patch_pairs=stats["patch_pairs"], patch_tests=stats["patch_tests"],
-                       quad_tests=stats["quad_tests"], sat_tests=stats["sat_tests"],
+                       quad_tests=stats["quad_tests"], quad_kept=stats["quad_kept"],
+                       sat_tests=stats["sat_tests"],
                        fp32_solves=stats["fp32_solves"], fp64_solves=stats["fp64_solves"]),
         "roofline": roofline, "kernels": kernels, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clk.summary(), "gpu_launches": stats["kernels"] * args.steps,

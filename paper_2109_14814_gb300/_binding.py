@@ -74,6 +74,7 @@ class Stats(ctypes.Structure):
         ("quad_tests", _c.c_longlong),
         ("patch_pairs", _c.c_longlong),
         ("patch_tests", _c.c_longlong),
+        ("quad_kept", _c.c_longlong),
     ]
 
     def as_dict(self):

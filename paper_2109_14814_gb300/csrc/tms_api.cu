@@ -200,12 +200,6 @@ struct Plan {
         return TMS_OK;
     }
 
-    // The hit tail runs in one block when the raw hits fit its shared memory; a
-    // search that finds more grows hit_cap and is replanned onto the multi-kernel
-    // sort and merge.  The device-wait test switch (inject bit 4) needs the
-    // multi-kernel sort, whose look-back is the wait.
-    bool small_tail() const { return hit_cap <= kSmallHits && !(prm.inject & 16u); }
-
     // The whole search as a stream-ordered launch sequence (no host round trip).
     // inside stream capture an event record becomes a graph node only with the
     // external flag
@@ -339,23 +333,15 @@ struct Plan {
         da.keep = keep; da.keep_scan = kscan; da.partials = partials;
         da.out = (tms_hit *)dHits; da.out_cap = (unsigned long long)hitCap; da.out_keys = okeys;
         da.offsets = dOffsets; da.n_pairs = nPairs; da.tri_bits = tri_bits; da.tau = p.tau;
-        if (small_tail()) {
-            // sort, merge and output in one block (raw-hit capacity <= kSmallHits)
-            da.keys = nullptr; da.vals = nullptr;
-            launch_hit_tail(da, hk, 2 * tri_bits + pair_bits, s);
-            kernels += 1;
-            mark(13, s);
-        } else {
-            // the raw hits are few: a small grid keeps the per-pass fixed cost low
-            const bool halt = radix_sort(hk, hv, hk2, hv2, sort_scratch, &d_ctr->raw_hits, hit_cap,
-                                         2 * tri_bits + pair_bits, sort_grid, &d_ctr->status,
-                                         (unsigned long long)p.spin_limit, (p.inject & 16u) ? 1 : 0, s);
-            kernels += 2 + sort_passes_h;
-            mark(13, s);
-            da.keys = halt ? hk2 : hk; da.vals = halt ? hv2 : hv;
-            launch_dedup(da, grid, s);
-            kernels += 5 + (dOffsets ? 1 : 0);
-        }
+        // the raw hits are few: a small grid keeps the per-pass fixed cost low
+        const bool halt = radix_sort(hk, hv, hk2, hv2, sort_scratch, &d_ctr->raw_hits, hit_cap,
+                                     2 * tri_bits + pair_bits, sort_grid, &d_ctr->status,
+                                     (unsigned long long)p.spin_limit, (p.inject & 16u) ? 1 : 0, s);
+        kernels += 2 + sort_passes_h;
+        mark(13, s);
+        da.keys = halt ? hk2 : hk; da.vals = halt ? hv2 : hv;
+        launch_dedup(da, grid, s);
+        kernels += 5 + (dOffsets ? 1 : 0);
         mark(14, s);
 
         cudaMemcpyAsync(h_ctr, d_ctr, kReadback, cudaMemcpyDeviceToHost, s);
@@ -628,9 +614,8 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
                   : patch ? std::max<unsigned long long>(1 << 16, quadsA + quadsA / 4)
                           : std::max<unsigned long long>(1 << 16, 2 * P->ent_cap);
     P->ppair_cap = patch ? std::max<unsigned long long>(1 << 16, 4 * faces) : 0;
-    // raw hits before merging: few (far fewer than candidates); start at the one-block
-    // tail's capacity, grown (onto the multi-kernel tail) when a search finds more
-    P->hit_cap = prm.hit_capacity > 0 ? (unsigned long long)prm.hit_capacity : kSmallHits;
+    P->hit_cap = prm.hit_capacity > 0 ? (unsigned long long)prm.hit_capacity
+                                      : std::max<unsigned long long>(1 << 14, P->cand_cap / 16);
     P->surv_cap = std::max<unsigned long long>(1 << 16, P->cand_cap / 8);
     P->bmA_bits = std::min(26, std::max(11, ceil_log2(std::max<unsigned long long>(P->facesA, 1) * 8) - 5));
     P->bmH_bits = std::min(25, std::max(11, ceil_log2(P->ent_cap * 8) - 5));
@@ -690,7 +675,6 @@ tms_status search_core(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
         configure_emit();
         configure_patch_quads();
         configure_narrow();
-        TMS_CK(configure_hit_tail());
         g_configured_mask |= 1 << device;
     }
     Plan *P = find_plan(A, B, nPairs, prm, cm_pair, user, dHits, hitCap, dOffsets, device);
@@ -774,6 +758,7 @@ tms_status search_core(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
     st.quad_tests = (long long)c.quad;
     st.patch_pairs = (long long)c.ppairs;
     st.patch_tests = (long long)c.ptests;
+    st.quad_kept = (long long)c.qkeep;
     st.raw_hits = (long long)c.raw_hits;
     st.hits = (long long)c.out;
     for (int d = 0; d < 4; ++d) st.grid_n[d] = P->h_grid0->n[d];

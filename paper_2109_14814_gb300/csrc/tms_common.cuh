@@ -49,9 +49,11 @@ enum StatusBits : unsigned int {
 struct MeshDev {
     const double *c[4];   // x, y, px, py, offset to the first view column
     const double *s;      // s values of the view (M entries), device
-    float4 *split;        // plan scratch: per view vertex (k*N + i) two float4,
-                          // hi = RN32(x) and lo = RN32(x - hi), written by the
-                          // bounds pass and gathered by the FP32 narrow filter
+    float4 *split;        // plan scratch: the FP32 split of every view vertex
+                          // (k*N + i): hi = RN32(x) at [k*N + i], lo = RN32(x - hi)
+                          // at [N*M + k*N + i] (hi and lo in separate halves, so a
+                          // gather of the hi parts alone reads dense 16-byte rows),
+                          // written by the bounds pass, gathered by the narrow filters
     void *fbox;           // plan scratch: per face slot its box, written by the
                           // bounds pass (mixed precision: float4 lo, float4 hi,
                           // rounded outward; plain: 8 doubles lo[4], hi[4]);
@@ -344,7 +346,8 @@ __device__ __forceinline__ int cell_of(double v, double o, double inv, int n) {
 __device__ __forceinline__ void tri_ij(const MeshDev &m, uint32_t t, int ii[3], int kk[3]) {
     uint32_t q = t >> 1;
     int tau = t & 1;
-    int i = (int)(q % (uint32_t)m.N), k = (int)(q / (uint32_t)m.N);
+    const uint32_t kq = (uint32_t)__umul64hi((unsigned long long)q, m.nmagic);   // q / N
+    int i = (int)(q - kq * (uint32_t)m.N), k = (int)kq;
     int ip = (i + 1 == m.N) ? 0 : i + 1;
     if (tau == 0) {
         ii[0] = ip; kk[0] = k;
@@ -595,12 +598,6 @@ struct DedupArgs {
 };
 void launch_dedup(const DedupArgs &a, int grid, cudaStream_t st);
 
-// The hit tail (sort, merge, output, offsets) in one block when the raw-hit
-// capacity is at most kSmallHits; keys are the unsorted hit keys, a.keys and
-// a.vals unused.  configure_hit_tail sets its shared-memory size (outside capture).
-constexpr unsigned kSmallHits = 16384;
-void launch_hit_tail(const DedupArgs &a, const uint64_t *keys, int key_bits, cudaStream_t st);
-cudaError_t configure_hit_tail();
 
 struct AdjointArgs {
     const tms_hit *hits;

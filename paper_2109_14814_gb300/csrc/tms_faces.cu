@@ -102,8 +102,8 @@ __device__ __forceinline__ void write_split(const MeshDev &m, size_t idx, const 
     split_f32(x[1], hi.y, lo.y);
     split_f32(x[2], hi.z, lo.z);
     split_f32(x[3], hi.w, lo.w);
-    m.split[2 * idx] = hi;
-    m.split[2 * idx + 1] = lo;
+    m.split[idx] = hi;
+    m.split[(size_t)m.N * m.M + idx] = lo;
 }
 
 // The tile's own vertex: its FP32 bounds for the boxes and its split copy,
@@ -121,8 +121,8 @@ __device__ __forceinline__ void vtx_and_split<1>(const double x[4], Vtx<1> &out,
     f32_all(x[2], v.lo[2], v.hi[2], hi.z, lo.z);
     f32_all(x[3], v.lo[3], v.hi[3], hi.w, lo.w);
     out = v;
-    m.split[2 * idx] = hi;
-    m.split[2 * idx + 1] = lo;
+    m.split[idx] = hi;
+    m.split[(size_t)m.N * m.M + idx] = lo;
 }
 template <>
 __device__ __forceinline__ void vtx_and_split<0>(const double x[4], Vtx<0> &out, const MeshDev &m,

@@ -134,30 +134,47 @@ __global__ void __launch_bounds__(kCellScanBlock) k_cells_reduce(GroupArgs a) {
     }
 }
 
-// exclusive scan of the per-block sums (one block of 1024 threads, g <= 1024)
+// exclusive scan of the per-block sums (one block of 1024 threads, g <= 1024):
+// the five quantities at once, each by a warp scan and a scan of the 32 warp sums
 __global__ void __launch_bounds__(1024) k_cells_partials(GroupArgs a, int g) {
-    __shared__ unsigned long long p[1024];
+    __shared__ unsigned long long wsum[5][32];
     if (a.ctr->entries > a.cap) return;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    unsigned long long x[5], incl[5];
+#pragma unroll
     for (int k = 0; k < 5; ++k) {
-        const unsigned long long x = threadIdx.x < g ? a.partials[k * g + threadIdx.x] : 0;
-        p[threadIdx.x] = x;
-        __syncthreads();
-        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-            const unsigned long long y = threadIdx.x >= off ? p[threadIdx.x - off] : 0;
-            __syncthreads();
-            p[threadIdx.x] += y;
-            __syncthreads();
+        x[k] = t < g ? a.partials[k * g + t] : 0;
+        incl[k] = x[k];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULL, incl[k], off);
+            if (lane >= off) incl[k] += y;
         }
-        if (threadIdx.x < g) a.partials[k * g + threadIdx.x] = p[threadIdx.x] - x;
-        if (threadIdx.x == blockDim.x - 1) {
-            const unsigned long long tot = p[threadIdx.x];
-            if (k == 0) a.ctr->cells = tot;
-            else if (k == 1) a.ctr->grouped = tot;
-            else if (k == 2) a.ctr->tiles = tot;
-            else if (k == 3) a.ctr->pair_slots = tot;
-            else a.ctr->claimed = tot;   // the host grows a crowded table
+        if (lane == 31) wsum[k][warp] = incl[k];
+    }
+    __syncthreads();
+    if (warp < 5) {
+        const unsigned long long w = wsum[warp][lane];
+        unsigned long long wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULL, wi, off);
+            if (lane >= off) wi += y;
         }
-        __syncthreads();
+        wsum[warp][lane] = wi - w;
+        if (lane == 31) {
+            // totals: the counters the emission and the host read
+            if (warp == 0) a.ctr->cells = wi;
+            else if (warp == 1) a.ctr->grouped = wi;
+            else if (warp == 2) a.ctr->tiles = wi;
+            else if (warp == 3) a.ctr->pair_slots = wi;
+            else a.ctr->claimed = wi;   // the host grows a crowded table
+        }
+    }
+    __syncthreads();
+    if (t < g) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) a.partials[k * g + t] = wsum[k][warp] + incl[k] - x[k];
     }
 }
 

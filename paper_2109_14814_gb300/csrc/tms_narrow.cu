@@ -118,9 +118,9 @@ __device__ __forceinline__ void gather_split(const MeshDev &m, uint32_t t, float
     tri_ij(m, t, ii, kk);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const size_t idx = 2 * ((size_t)kk[j] * m.N + ii[j]);
+        const size_t idx = (size_t)kk[j] * m.N + ii[j];
         v[j][0] = __ldg(m.split + idx);
-        v[j][1] = __ldg(m.split + idx + 1);
+        v[j][1] = __ldg(m.split + (size_t)m.N * m.M + idx);
     }
 }
 
@@ -144,8 +144,8 @@ __device__ __forceinline__ void gather_quad_split(const MeshDev &m, uint32_t q, 
                            (size_t)(k + 1) * m.N + ip};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        v[j][0] = __ldg(m.split + 2 * idx[j]);
-        v[j][1] = __ldg(m.split + 2 * idx[j] + 1);
+        v[j][0] = __ldg(m.split + idx[j]);
+        v[j][1] = __ldg(m.split + (size_t)m.N * m.M + idx[j]);
     }
 }
 
@@ -157,7 +157,7 @@ __device__ __forceinline__ void gather_quad_hi(const MeshDev &m, uint32_t q, flo
     const size_t idx[4] = {(size_t)k * m.N + i, (size_t)k * m.N + ip, (size_t)(k + 1) * m.N + i,
                            (size_t)(k + 1) * m.N + ip};
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = __ldg(m.split + 2 * idx[j]);
+    for (int j = 0; j < 4; ++j) v[j] = __ldg(m.split + idx[j]);
 }
 
 // (x1, x2, x3) of T1 = ((i+1,k), (i,k), (i,k+1)) or T2 = ((i,k+1), (i+1,k+1), (i+1,k))
@@ -1078,186 +1078,6 @@ __global__ void k_dedup_out(DedupArgs a) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// the whole hit tail in one block, for at most kSmallHits raw hits: a stable LSD
-// radix sort (8-bit digits) of a 16-bit index permutation over keys held in
-// shared memory, then the merge of duplicate hits and the sorted output.  The
-// multi-kernel path (radix_sort, launch_dedup) does the same for more hits; one
-// block is quicker here because the stages are latency-bound, not data-bound.
-// ---------------------------------------------------------------------------
-constexpr int kTailThreads = 1024;
-constexpr int kTailWarps = kTailThreads / 32;
-
-__device__ __forceinline__ bool same_feature_earlier(const DedupArgs &a, const uint64_t *K,
-                                                     const uint16_t *P, unsigned m, const tms_hit &h,
-                                                     uint64_t key) {
-    const int2 pr = a.pairs[h.pair];
-    const MeshDev ma = a.meshes[pr.x], mb = a.meshes[pr.y];
-    uint32_t incA[6], incB[6];
-    int nA, nB;
-    const uint32_t fA = feature_of(ma, h.triA, h.a, h.b, a.tau, incA, nA);
-    const uint32_t fB = feature_of(mb, h.triB, h.c, h.d, a.tau, incB, nB);
-    if ((fA >> 30) == 0 && (fB >> 30) == 0) return false;
-    for (int p = 0; p < nA; ++p) {
-        for (int q = 0; q < nB; ++q) {
-            const uint32_t ta = incA[p], tb = incB[q];
-            if (ta == h.triA && tb == h.triB) continue;
-            const uint64_t k2 = ((uint64_t)h.pair << (2 * a.tri_bits)) | ((uint64_t)ta << a.tri_bits) | (uint64_t)tb;
-            if (k2 >= key) continue;
-            unsigned lo = 0, hi = m;
-            while (lo < hi) {
-                const unsigned mid = (lo + hi) >> 1;
-                if (K[P[mid]] < k2) lo = mid + 1; else hi = mid;
-            }
-            if (lo < m && K[P[lo]] == k2) {
-                const tms_hit &o = a.raw[P[lo]];
-                uint32_t t1[6], t2[6];
-                int n1, n2;
-                if (feature_of(ma, o.triA, o.a, o.b, a.tau, t1, n1) == fA &&
-                    feature_of(mb, o.triB, o.c, o.d, a.tau, t2, n2) == fB)
-                    return true;
-            }
-        }
-    }
-    return false;
-}
-
-__global__ void __launch_bounds__(kTailThreads, 1) k_hit_tail(DedupArgs a, const uint64_t *keys_in, int key_bits) {
-    extern __shared__ __align__(16) unsigned char tail_smem[];
-    uint64_t *K = reinterpret_cast<uint64_t *>(tail_smem);                       // [kSmallHits]
-    uint16_t *P0 = reinterpret_cast<uint16_t *>(K + kSmallHits);                 // [kSmallHits]
-    uint16_t *P1 = P0 + kSmallHits;                                              // [kSmallHits]
-    uint16_t *cnt = P1 + kSmallHits;                                             // [kTailWarps][256]
-    __shared__ unsigned wsum[kTailWarps];
-    __shared__ unsigned long long s_total;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t lt = lanemask_lt();
-    const unsigned n = (unsigned)clamp_count(&a.ctr->raw_hits, a.raw_cap < (unsigned long long)kSmallHits
-                                                                   ? a.raw_cap : (unsigned long long)kSmallHits);
-    for (unsigned i = tid; i < n; i += kTailThreads) {
-        K[i] = keys_in[i];
-        P0[i] = (uint16_t)i;
-    }
-    __syncthreads();
-    // each warp owns a chunk of whole 32-item rounds
-    const unsigned chunk = ((n + kTailWarps - 1) / kTailWarps + 31) & ~31u;
-    const unsigned c0 = min(n, warp * chunk), c1 = min(n, c0 + chunk);
-    uint16_t *wc = cnt + warp * 256;
-    const int passes = (key_bits + 7) / 8;
-    for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
-        for (int d = lane; d < 256; d += 32) wc[d] = 0;
-        __syncwarp();
-        for (unsigned b = c0; b < c1; b += 32) {
-            const unsigned i = b + lane;
-            const unsigned d = i < c1 ? (unsigned)(K[P0[i]] >> shift) & 255u : 0xFFFFu;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (d != 0xFFFFu && lane == __ffs(peers) - 1) wc[d] = (uint16_t)(wc[d] + __popc(peers));
-            __syncwarp();
-        }
-        __syncthreads();
-        // offsets in digit-major, warp-minor order
-        if (tid < 256) {
-            unsigned tot = 0;
-            for (int w = 0; w < kTailWarps; ++w) tot += cnt[w * 256 + tid];
-            unsigned incl = tot;
-            for (int off = 1; off < 32; off <<= 1) {
-                const unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += y;
-            }
-            if (lane == 31) wsum[warp] = incl;
-            __syncwarp();
-            // warps 0..7 hold the 256 digits; their totals scanned by each
-            unsigned before = 0;
-            asm volatile("bar.sync 1, 256;");
-            for (int w = 0; w < warp; ++w) before += wsum[w];
-            unsigned run = before + incl - tot;
-            for (int w = 0; w < kTailWarps; ++w) {
-                const unsigned c = cnt[w * 256 + tid];
-                cnt[w * 256 + tid] = (uint16_t)run;
-                run += c;
-            }
-        }
-        __syncthreads();
-        for (unsigned b = c0; b < c1; b += 32) {
-            const unsigned i = b + lane;
-            const unsigned d = i < c1 ? (unsigned)(K[P0[i]] >> shift) & 255u : 0xFFFFu;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            unsigned before = 0;
-            if (d != 0xFFFFu) before = wc[d];
-            __syncwarp();
-            if (d != 0xFFFFu) {
-                P1[before + __popc(peers & lt)] = P0[i];
-                if (lane == __ffs(peers) - 1) wc[d] = (uint16_t)(before + __popc(peers));
-            }
-            __syncwarp();
-        }
-        __syncthreads();
-        uint16_t *t = P0;
-        P0 = P1;
-        P1 = t;
-    }
-    // merge: keep[m] into P1 (as a flag), then a block scan places the kept hits
-    const unsigned per = (n + kTailThreads - 1) / kTailThreads;
-    const unsigned m0 = min(n, tid * per), m1 = min(n, m0 + per);
-    unsigned kept = 0;
-    for (unsigned m = m0; m < m1; ++m) {
-        const tms_hit &h = a.raw[P0[m]];
-        const bool keep = !same_feature_earlier(a, K, P0, m, h, K[P0[m]]);
-        P1[m] = keep ? 1 : 0;
-        kept += keep ? 1u : 0u;
-    }
-    unsigned incl = kept;
-    for (int off = 1; off < 32; off <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += y;
-    }
-    __syncthreads();
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const unsigned w = wsum[lane];
-        unsigned wi = w;
-        for (int off = 1; off < 32; off <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, wi, off);
-            if (lane >= off) wi += y;
-        }
-        wsum[lane] = wi - w;
-        if (lane == 31) s_total = wi;
-    }
-    __syncthreads();
-    unsigned pos = wsum[warp] + incl - kept;
-    for (unsigned m = m0; m < m1; ++m) {
-        if (!P1[m]) continue;
-        tms_hit h = a.raw[P0[m]];
-        const int2 pr = a.pairs[h.pair];
-        uint32_t inc[6];
-        int ninc;
-        const uint32_t fA = feature_of(a.meshes[pr.x], h.triA, h.a, h.b, a.tau, inc, ninc);
-        const uint32_t fB = feature_of(a.meshes[pr.y], h.triB, h.c, h.d, a.tau, inc, ninc);
-        if ((fA >> 30) != 0 || (fB >> 30) != 0) h.flags |= 2u;
-        a.out_keys[pos] = K[P0[m]];
-        if (pos < a.out_cap) a.out[pos] = h;
-        ++pos;
-    }
-    if (tid == 0) a.ctr->out = s_total;
-    __syncthreads();
-    if (a.offsets) {
-        // pair p's hits start at the first output key of pair p
-        const unsigned long long tot = s_total;
-        for (int p = tid; p <= a.n_pairs; p += kTailThreads) {
-            if (p == a.n_pairs) { a.offsets[p] = (long long)tot; continue; }
-            const uint64_t k = (uint64_t)p << (2 * a.tri_bits);
-            unsigned long long lo = 0, hi = tot;
-            while (lo < hi) {
-                const unsigned long long mid = (lo + hi) >> 1;
-                if (a.out_keys[mid] < k) lo = mid + 1; else hi = mid;
-            }
-            a.offsets[p] = (long long)lo;
-        }
-    }
-}
-
 __global__ void k_offsets(const uint64_t *out_keys, const unsigned long long *d_out,
                           unsigned long long raw_cap, int n_pairs, int tri_bits, long long *offsets) {
     const unsigned long long n = clamp_count(d_out, raw_cap);
@@ -1373,18 +1193,6 @@ void launch_narrow(const NarrowArgs &a, int face_level, int sms, int grid, cudaS
         k_narrow_filter<1><<<sms * filter_resident<1>(), 256, 0, st>>>(a);
     }
     k_narrow_fp64<<<grid, 256, 0, st>>>(a);
-}
-
-size_t hit_tail_smem() {
-    return (size_t)kSmallHits * (sizeof(uint64_t) + 2 * sizeof(uint16_t)) + kTailWarps * 256 * sizeof(uint16_t);
-}
-
-cudaError_t configure_hit_tail() {
-    return cudaFuncSetAttribute(k_hit_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hit_tail_smem());
-}
-
-void launch_hit_tail(const DedupArgs &a, const uint64_t *keys, int key_bits, cudaStream_t st) {
-    k_hit_tail<<<1, kTailThreads, hit_tail_smem(), st>>>(a, keys, key_bits);
 }
 
 void launch_dedup(const DedupArgs &a, int grid, cudaStream_t st) {
