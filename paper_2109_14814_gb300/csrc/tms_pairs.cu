@@ -449,9 +449,12 @@ __device__ __forceinline__ void load_side(const QuadSide &m, uint32_t patch, int
 // l holds quad (row l / kPatchI, column l % kPatchI) of each patch; a quad
 // that meets none of the other patch's quarter boxes cannot overlap any of its
 // quads (they all lie in those boxes), so each side is cut to its quads that
-// meet one; the pairs of the survivors (nA x nB of them, 32 per round, pair t =
-// (t / nB, t % nB)) take the box test of Sec. 6.2.2, optionally the Moller test
-// of Sec. 6.2.3, and are appended through a per-warp stage.
+// meet one.  The survivors' pairs take the box test of Sec. 6.2.2 (optionally
+// the Moller test of Sec. 6.2.3) and are appended through a per-warp stage:
+// the smaller side's survivors stay in registers, one per lane and repeated in
+// G = 32 / n groups of lanes, while each round reads G of the other side's
+// survivors from shared memory (close to a broadcast), so a round costs two
+// short shared-memory reads and no division.
 // patch id -> (patch row, patch column): the quotient by npi from a 64-bit
 // reciprocal (exact for 32-bit ids, npi >= 2)
 __device__ __forceinline__ void patch_rc(uint32_t patch, uint32_t npi, unsigned long long magic,
@@ -462,11 +465,10 @@ __device__ __forceinline__ void patch_rc(uint32_t patch, uint32_t npi, unsigned 
 
 template <int PREC, bool MOLLER>
 __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 : 2) k_patch_quads(PatchArgs a) {
-    // survivors' boxes as separate low and high halves (16-byte rows for FP32:
-    // the cross test's reads at varying indices stay free of bank conflicts)
-    __shared__ typename EBox<PREC>::Half sAlo[kPatchWarps][32], sAhi[kPatchWarps][32];
-    __shared__ typename EBox<PREC>::Half sBlo[kPatchWarps][32], sBhi[kPatchWarps][32];
-    __shared__ uint32_t sQA[kPatchWarps][32], sQB[kPatchWarps][32];
+    // survivors' boxes as separate low and high halves (16-byte rows for FP32)
+    __shared__ typename EBox<PREC>::Half sLo[kPatchWarps][2][32], sHi[kPatchWarps][2][32];
+    __shared__ uint32_t sQ[kPatchWarps][2][32];     // survivors' quad ids, [0] A, [1] B
+    __shared__ EBox<PREC> sQuart[kPatchWarps][8];   // the pair's quarter boxes, A's then B's
     __shared__ Cand sOut[kPatchWarps][kPatchFlush + 32];
     // nothing to do after an overflow of the patch-level grid (the host retries)
     if (a.ctr->entries > a.ent_cap || a.ctr->pair_slots > kMaxPairSlots) return;
@@ -509,6 +511,10 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
             xa.load(qbA, 4 * pp.faceA + qi);
             xb.load(qbB, 4 * pp.faceB + qj);
             if (!__any_sync(FULL, boxes_overlap(xa, xb))) continue;
+            __syncwarp();                      // the previous pair's quarter boxes are read
+            if (lane < 4) sQuart[warp][4 + lane] = xb;          // B's quarter `lane`
+            if ((lane & 3) == 0 && lane < 16) sQuart[warp][lane >> 2] = xa;   // A's quarter lane / 4
+            __syncwarp();
         }
         uint32_t pka, pia, pkb, pib;
         patch_rc(pp.faceA, npiA, mgA, pka, pia);
@@ -526,12 +532,9 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
         // survivors: quads meeting some quarter of the other patch
         bool sa = false, sb = false;
 #pragma unroll 1
-        for (uint32_t k = 0; k < 4; ++k) {
-            EBox<PREC> xa, xb;
-            xb.load(qbB, 4 * pp.faceB + k);
-            xa.load(qbA, 4 * pp.faceA + k);
-            sa |= boxes_overlap(ba, xb);
-            sb |= boxes_overlap(bb, xa);
+        for (int k = 0; k < 4; ++k) {
+            sa |= boxes_overlap(ba, sQuart[warp][4 + k]);
+            sb |= boxes_overlap(bb, sQuart[warp][k]);
         }
         sa &= va;
         sb &= vb;
@@ -541,36 +544,44 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
         __syncwarp();                          // the previous pair's survivors are read
         if (sa) {
             const int k = __popc(mA & lt);
-            ba.store_halves(sAlo[warp][k], sAhi[warp][k]);
-            sQA[warp][k] = qa;
+            ba.store_halves(sLo[warp][0][k], sHi[warp][0][k]);
+            sQ[warp][0][k] = qa;
         }
         if (sb) {
             const int k = __popc(mB & lt);
-            bb.store_halves(sBlo[warp][k], sBhi[warp][k]);
-            sQB[warp][k] = qb;
+            bb.store_halves(sLo[warp][1][k], sHi[warp][1][k]);
+            sQ[warp][1][k] = qb;
         }
         __syncwarp();
-        const uint32_t T = nA * nB;
-        tests += T;
-        // t / nB for t < 1024, nB <= 32: (t + 1/2) / nB lies at least 1/64 from
-        // an integer, far beyond the error of (t + 1/2) times an approximate
-        // reciprocal of nB (a few ulps: below 1e-4 absolute here)
-        const float rB = __fdividef(1.0f, (float)nB);
-        for (uint32_t base = 0; base < T; base += 32) {
-            const uint32_t t = base + lane;
+        tests += nA * nB;
+        // the smaller side in registers: lane = (group g, member m), m < nR
+        const int R = nB <= nA ? 1 : 0, I = 1 - R;
+        const uint32_t nR = R ? nB : nA, nI = R ? nA : nB;
+        // lane / nR and 32 / nR from FP32 reciprocals: (x + 1/2) / nR lies at
+        // least 1/64 from an integer for x <= 32, far above the reciprocal's error
+        const float rR = __fdividef(1.0f, (float)nR);
+        const uint32_t g = (uint32_t)(((float)lane + 0.5f) * rR);
+        const uint32_t G = (uint32_t)(32.5f * rR);
+        const uint32_t m = (uint32_t)lane - g * nR;
+        const bool member = g < G;
+        const typename EBox<PREC>::Half rlo = sLo[warp][R][member ? m : 0], rhi = sHi[warp][R][member ? m : 0];
+        const uint32_t rq = sQ[warp][R][member ? m : 0];
+        for (uint32_t base = 0; base < nI; base += G) {
+            const uint32_t ii = base + g;
+            const bool act = member && ii < nI;
             bool ov = false;
-            uint32_t ia = 0, ib = 0;
-            if (t < T) {
-                ia = (uint32_t)(((float)t + 0.5f) * rB);
-                ib = t - ia * nB;
-                ov = EBox<PREC>::halves_overlap(sAlo[warp][ia], sAhi[warp][ia], sBlo[warp][ib],
-                                                sBhi[warp][ib]);
-                if (MOLLER && ov)
-                    ov = !moller_reject(a.meshes[pr.x], sQA[warp][ia], a.meshes[pr.y], sQB[warp][ib], 1);
+            uint32_t iq = 0;
+            if (act) {
+                ov = EBox<PREC>::halves_overlap(sLo[warp][I][ii], sHi[warp][I][ii], rlo, rhi);
+                iq = sQ[warp][I][ii];
+                if (MOLLER && ov) {
+                    const uint32_t fa = R ? iq : rq, fb = R ? rq : iq;
+                    ov = !moller_reject(a.meshes[pr.x], fa, a.meshes[pr.y], fb, 1);
+                }
             }
             Cand cd;
-            cd.faceA = sQA[warp][ia];
-            cd.faceB = sQB[warp][ib];
+            cd.faceA = R ? iq : rq;
+            cd.faceB = R ? rq : iq;
             cd.pair = pp.pair;
             cd.pad = 0;
             stage_push<kPatchFlush>(stage, staged, ov, cd, &a.ctr->cand, store);
@@ -578,7 +589,7 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
     }
     __syncwarp();
     stage_flush<kPatchFlush>(stage, staged, &a.ctr->cand, store);
-    // every lane counted the same tests (T is warp-uniform): one lane adds them
+    // every lane counted the same tests (warp-uniform): one lane adds them
     if (lane == 0 && tests) atomicAdd(&a.ctr->ptests, tests);
 }
 
