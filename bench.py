@@ -81,11 +81,11 @@ STAGE_PARTS = {
 STAGE_KERNELS = {
     "face_bounds": "tms::k_bounds_pass",
     "face_mark": "tms::k_cell_pass<MARK>",
-    "face_probe": "tms::k_cell_pass<PROBE_MARK, PROBE>",
+    "face_probe": "tms::k_cell_pass<EMIT_ALL>",
     "group_count": "tms::k_group_count",
     "group_cells": "tms::k_cells_* + k_group_scatter",
     "emit": "tms::k_emit + k_patch_quads",
-    "narrow": "tms::k_narrow_filter + k_narrow_fp64",
+    "narrow": "tms::k_quad_filter + k_narrow_filter + k_narrow_fp64",
     "sort_merge": "tms::k_radix_* + k_dedup_*",
 }
 BROAD_KERNELS = ("k_search_init", "k_bounds_pass", "k_grid_params", "k_cell_pass", "k_group_count",
@@ -152,7 +152,7 @@ TRAFFIC_KERNELS = [
     ("k_search_init", 1, None, True),
     ("k_bounds_pass", 1, "face_bounds", True),
     ("k_grid_params", 1, None, True),
-    ("k_cell_pass", 3, "face_probe", True),
+    ("k_cell_pass", 1, "face_probe", True),
     ("k_group_count", 1, "group_count", True),
     ("k_cells_reduce", 1, "group_cells", True),
     ("k_cells_partials", 1, "group_cells", True),
@@ -160,6 +160,7 @@ TRAFFIC_KERNELS = [
     ("k_group_scatter", 1, "group_cells", True),
     ("k_emit", 1, "emit", True),
     ("k_patch_quads", 1, "emit", True),
+    ("k_quad_filter", 1, "narrow", False),
     ("k_narrow_filter", 1, "narrow", False),
     ("k_narrow_fp64", 1, "narrow", False),
 ]
@@ -315,14 +316,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def build_workload(device, cache: str = ""):
-    """The 4096 x 512 pair; with `cache`, read from that file when it exists
-    (else generated and written there), so that repeated runs of the bench in
-    one session (profiler captures) skip the generator."""
+# the smaller workload offered for profiler captures (the pool's rule: counters
+# beyond the launch list on a case of a few GB at most, inputs larger than L2)
+WORKLOAD_1024 = dict(workload="mesh-vs-mesh search, 1024x256 vs 1024x256 vertex grids "
+                              "(522,240 triangles per mesh), lambda=4 stretch, 3 folds, 64 planted hits",
+                     N=1024, M=256, triangles_per_mesh=522240)
+
+
+def build_workload(device, cache: str = "", config: int = 3):
+    """The 4096 x 512 pair (config 3), or the 1024 x 256 pair (config 2); with
+    `cache`, read from that file when it exists (else generated and written
+    there), so that repeated runs of the bench in one session (profiler
+    captures) skip the generator."""
     import synth
     if cache and os.path.exists(cache):
         return torch.load(cache, weights_only=False)
-    pair = synth.config3()
+    pair = synth.config2() if config == 2 else synth.config3()
     if cache:
         torch.save(pair, cache)
     return pair
@@ -341,7 +350,7 @@ def run_tms(args, ws, rank, local):
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     peaks, peaks_kind = measured_peaks()
-    pair = build_workload(device, args.workload_cache)
+    pair = build_workload(device, args.workload_cache, args.config)
     XA = pair.A.X.to(device).contiguous()
     XB = pair.B.X.to(device).contiguous()
     A = tms.Mesh(XA, pair.A.s, True)
@@ -518,7 +527,7 @@ def run_tms(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded manifold-like meshes)",
-        "config": dict(WORKLOAD, precision="FP32 outward boxes and certified FP32 pre-solve, FP64 narrow phase",
+        "config": dict(WORKLOAD if args.config == 3 else WORKLOAD_1024, precision="FP32 outward boxes and certified FP32 pre-solve, FP64 narrow phase",
                        l2="256 MiB buffer written between steps, outside the step events",
                        parallelism=f"replicas x{ws}" if ws > 1 else "1 GPU",
                        hits=n_hits, candidates=stats["candidates"], entries=stats["entries"],
@@ -1004,6 +1013,9 @@ def main():
                          "(made by the --traffic-commands lines) and exit; needs no GPU")
     ap.add_argument("--traffic-commands", default="", metavar="DIR",
                     help="print the per-kernel ncu commands (CSV into DIR) and exit")
+    ap.add_argument("--config", type=int, default=3, choices=[2, 3],
+                    help="3: the 4096 x 512 benchmark workload (default); 2: the 1024 x 256 "
+                         "workload, for profiler captures of a small case")
     ap.add_argument("--workload-cache", default="", metavar="PATH",
                     help="read the workload from PATH if it exists, else generate and write it")
     ap.add_argument("--only-extras", default="",

@@ -31,6 +31,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "tms_common.cuh"
 
 namespace tms {
@@ -281,6 +283,32 @@ struct BoundAcc<0> {
     __device__ double get_w(int d) const { return w[d]; }
 };
 
+// ord_enc of the value as a double: FP64 values directly; FP32 values through the
+// exact float -> double conversion done on the bits (integer operations only)
+__device__ __forceinline__ unsigned long long ord_enc_any(double v) { return ord_enc(v); }
+__device__ __forceinline__ unsigned long long ord_enc_any(float v) {
+    const unsigned b = __float_as_uint(v);
+    const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
+    const unsigned e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    unsigned long long db;
+    if (e == 255u) {
+        db = sgn | (0x7ffULL << 52) | ((unsigned long long)m << 29);          // inf, NaN
+    } else if (e == 0u) {
+        if (m == 0u) {
+            db = sgn;                                                         // +-0
+        } else {
+            // subnormal m 2^-149 = 1.f 2^(p - 149), p the top bit of m
+            const int p = 31 - __clz(m);
+            const unsigned long long frac = ((unsigned long long)m << (52 - p)) & 0xFFFFFFFFFFFFFULL;
+            db = sgn | ((unsigned long long)(p - 149 + 1023) << 52) | frac;
+        }
+    } else {
+        db = sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    }
+    const long long bb = (long long)db;
+    return (bb >= 0) ? (db | 0x8000000000000000ULL) : ~db;
+}
+
 // the pass entry (mesh of a pass) holding global index x, by binary search
 __device__ __forceinline__ int find_entry(const FacePassArgs &a, long long x, bool by_face) {
     int lo = 0, hi = a.n_entries - 1;
@@ -469,7 +497,10 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
     }
 
     // block reduction, then one set of atomics per block
-    __shared__ double red[8][13];
+    // in the accumulators' own type: FP32 in the mixed mode (no FP64 instruction
+    // in this kernel: GB300's FP64 pipe is narrow), FP64 in the plain mode
+    typedef typename std::remove_reference<decltype(acc.lo[0])>::type AccT;
+    __shared__ AccT red[8][12];
     __shared__ unsigned redf[8][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -484,7 +515,7 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
     unsigned seen = __reduce_or_sync(FULL, acc.seen);
     if (lane == 0) {
 #pragma unroll
-        for (int d = 0; d < 4; ++d) { red[warp][d] = acc.get_lo(d); red[warp][4 + d] = acc.get_hi(d); red[warp][8 + d] = acc.get_w(d); }
+        for (int d = 0; d < 4; ++d) { red[warp][d] = acc.lo[d]; red[warp][4 + d] = acc.hi[d]; red[warp][8 + d] = acc.w[d]; }
         redf[warp][0] = fl;
         redf[warp][1] = seen;
     }
@@ -497,15 +528,15 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
         if (s) {
 #pragma unroll
             for (int d = 0; d < 4; ++d) {
-                double l = red[0][d], h = red[0][4 + d], ww = red[0][8 + d];
+                AccT l = red[0][d], h = red[0][4 + d], ww = red[0][8 + d];
                 for (int w = 1; w < nw; ++w) {
-                    l = fmin(l, red[w][d]);
-                    h = fmax(h, red[w][4 + d]);
-                    ww = fmax(ww, red[w][8 + d]);
+                    l = min(l, red[w][d]);
+                    h = max(h, red[w][4 + d]);
+                    ww = max(ww, red[w][8 + d]);
                 }
-                atomicMin(&B->lo[d], ord_enc(l));
-                atomicMax(&B->hi[d], ord_enc(h));
-                atomicMax(&B->w[d], ord_enc(ww));
+                atomicMin(&B->lo[d], ord_enc_any(l));
+                atomicMax(&B->hi[d], ord_enc_any(h));
+                atomicMax(&B->w[d], ord_enc_any(ww));
             }
             atomicOr(&B->faces, 1u);
         }

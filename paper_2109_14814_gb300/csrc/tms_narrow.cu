@@ -197,7 +197,7 @@ __device__ __forceinline__ bool split_boxes_overlap(const float4 X[3][2], const 
 
 // true when the verified FP32 solve proves margin < -2 tau (not a hit)
 __device__ __noinline__ bool fp32_verified_reject(const float4 X[3][2], const float4 Y[3][2],
-                                                  double tau) {
+                                                  float tau) {
     const float u = 5.9604645e-08f;
     float A[4][4], EA[4][4], r[4], Er[4];
 #pragma unroll
@@ -322,7 +322,7 @@ __device__ __noinline__ bool fp32_verified_reject(const float4 X[3][2], const fl
     m = fminf(m, 1.0f - z[2] - z[3] + 2.0f * err + slack * (1.0f + fabsf(z[2]) + fabsf(z[3])));
     // allowance for an FP64 solve of the same system (its own rounding)
     const float kappa = cnorm * anorm;
-    const float allow = 2.0f * (float)tau + 32.0f * 1.1102230e-16f * kappa * (1.0f + zmax);
+    const float allow = 2.0f * tau + 32.0f * 1.1102230e-16f * kappa * (1.0f + zmax);
     return isfinite(m) && isfinite(err) && (m < -allow);
 }
 
@@ -517,7 +517,7 @@ __device__ __forceinline__ float det_lo_of(const float mE[6], float epsE, const 
 // the quad-level test on the edge vectors of both quads relative to v0 of A
 __device__ __forceinline__ bool quad_sat_vectors(const SplitVec &a1, const SplitVec &a2, const SplitVec &a3,
                                                  const SplitVec &b1, const SplitVec &b2, const SplitVec &b3,
-                                                 const SplitVec &r0, double tau) {
+                                                 const SplitVec &r0, float tau) {
     const float u = 5.9604645e-08f;
     float mA1[6], mB1[6], epsA1, epsB1;
     plucker(a1, a2, mA1, epsA1);
@@ -544,7 +544,7 @@ __device__ __forceinline__ bool quad_sat_vectors(const SplitVec &a1, const Split
             kmax = fmaxf(kmax, F4[k] / D[k]);
         }
     }
-    const float delta = 2.0f * (float)tau * 1.001f + 9.1e-13f * kmax * 1.001f;
+    const float delta = 2.0f * tau * 1.001f + 9.1e-13f * kmax * 1.001f;
     int kA1, kA2, kB1, kB2;
     top2_duals(mA1, kA1, kA2);
     top2_duals(mB1, kB1, kB2);
@@ -577,7 +577,7 @@ __device__ __forceinline__ bool quad_sat_vectors(const SplitVec &a1, const Split
 // The test from the quads' FP32 vertex roundings alone (hi_vec bounds), which
 // clears most candidates with half the data of the split copies; a candidate it
 // cannot clear goes on to the tests on the split copies.
-__device__ __forceinline__ bool quad_sat_reject_hi(const float4 QA[4], const float4 QB[4], double tau) {
+__device__ __forceinline__ bool quad_sat_reject_hi(const float4 QA[4], const float4 QB[4], float tau) {
     const SplitVec a1 = hi_vec(QA[1], QA[0]), a2 = hi_vec(QA[2], QA[0]);
     const SplitVec a3 = hi_vec(QA[3], QA[0]);
     const SplitVec b1 = hi_vec(QB[1], QB[0]), b2 = hi_vec(QB[2], QB[0]);
@@ -587,7 +587,7 @@ __device__ __forceinline__ bool quad_sat_reject_hi(const float4 QA[4], const flo
 }
 
 __device__ __forceinline__ bool quad_sat_reject(const float4 QA[4][2], const float4 QB[4][2],
-                                                double tau) {
+                                                float tau) {
     // vertices v0 (i,k), v1 (i+1,k), v2 (i,k+1), v3 (i+1,k+1); T1 = (v1, v0, v2),
     // T2 = (v2, v3, v1): T1's edges are (v1 - v0, v2 - v0), T2's (v2 - v3, v1 - v3)
     const SplitVec a1 = split_vec(QA[1], QA[0]), a2 = split_vec(QA[2], QA[0]);
@@ -601,7 +601,7 @@ __device__ __forceinline__ bool quad_sat_reject(const float4 QA[4][2], const flo
 // true when the separating-axis test proves the margin below -delta (not a hit,
 // also for an FP64 solve of the same system)
 __device__ __noinline__ bool fp32_sat_reject(const float4 X[3][2], const float4 Y[3][2],
-                                                double tau) {
+                                                float tau) {
     const float u = 5.9604645e-08f;
     // vectors relative to x2
     const SplitVec e1 = split_vec(X[0], X[1]);    // x1 - x2
@@ -640,7 +640,7 @@ __device__ __noinline__ bool fp32_sat_reject(const float4 X[3][2], const float4 
     // kappa = F4 / det_lo <= 1e10, and delta from it
     if (!(det_lo > 0.0f) || !(F4 <= 1e10f * det_lo)) return false;
     const float kappa = F4 / det_lo * 1.001f;
-    const float delta = 2.0f * (float)tau * 1.001f + 9.1e-13f * kappa;
+    const float delta = 2.0f * tau * 1.001f + 9.1e-13f * kappa;
     int kE1, kE2, kF1, kF2;
     top2_duals(mE, kE1, kE2);
     top2_duals(mF, kF1, kF2);
@@ -739,6 +739,8 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
+    // tau rounded up once per thread: the FP32 tests only widen by it
+    const float tauf = __double2float_ru(a.tau);
     unsigned long long n_sat = 0, n_full = 0;               // tests run, per warp
     unsigned qn = 0;                                        // queued pairs (warp-uniform)
 
@@ -757,7 +759,7 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
             float4 X[3][2], Y[3][2];
             gather_split(a.meshes[pr.x], ta, X);
             gather_split(a.meshes[pr.y], tb, Y);
-            keep = !fp32_verified_reject(X, Y, a.tau);
+            keep = !fp32_verified_reject(X, Y, tauf);
         }
         n_full += cnt;
         const unsigned long long pos = warp_append(&a.ctr->fp64, keep, FULL);
@@ -775,7 +777,7 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
     auto pair_tests = [&](bool valid, uint32_t g, int sub, const float4 X[3][2], const float4 Y[3][2],
                           bool boxes) {
         const bool tested = valid && (!boxes || split_boxes_overlap(X, Y));
-        const bool need = tested && !fp32_sat_reject(X, Y, a.tau);
+        const bool need = tested && !fp32_sat_reject(X, Y, tauf);
         n_sat += __popc(__ballot_sync(FULL, tested));
         const uint32_t want = __ballot_sync(FULL, need);
         if (need) {
@@ -893,6 +895,7 @@ __global__ void __launch_bounds__(256, 3) k_quad_filter(NarrowArgs a) {
     const unsigned long long n = a.ctr->cand;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
+    const float tauf = __double2float_ru(a.tau);
     unsigned long long n_quad = 0;
     for (unsigned long long g0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x - lane;
          g0 < n; g0 += stride) {
@@ -905,7 +908,7 @@ __global__ void __launch_bounds__(256, 3) k_quad_filter(NarrowArgs a) {
             float4 QA[4], QB[4];
             gather_quad_hi(a.meshes[pr.x], cd.faceA, QA);
             gather_quad_hi(a.meshes[pr.y], cd.faceB, QB);
-            need = !quad_sat_reject_hi(QA, QB, a.tau);
+            need = !quad_sat_reject_hi(QA, QB, tauf);
         }
         n_quad += __popc(__ballot_sync(FULL, valid));
         const unsigned long long pos = warp_append(&a.ctr->qkeep, need, FULL);
