@@ -181,7 +181,7 @@ def traffic_commands(out_dir: str, cache: str):
 def _ncu_rows(path: str):
     import csv
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1024.0, "MB": 1048576.0,
-             "nsecond": 1e-9, "usecond": 1e-6, "msecond": 1e-3}
+             "nsecond": 1e-9, "usecond": 1e-6, "msecond": 1e-3, "ns": 1e-9, "us": 1e-6, "ms": 1e-3}
     rows = list(csv.reader(open(path)))
     hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
     h = rows[hi]

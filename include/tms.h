@@ -260,6 +260,7 @@ typedef struct {
     long long patch_pairs;  /* patch level: patch pairs with overlapping boxes */
     long long patch_tests;  /* patch level: quad pairs box-tested inside them */
     long long quad_kept;    /* quad candidates the quad-level test could not clear */
+    long long patch_kept;   /* patch level: patch pairs with an overlapping quarter pair */
 } tms_stats;
 
 tms_status tms_last_stats(void *stream, tms_stats *out);

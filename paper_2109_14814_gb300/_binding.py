@@ -75,6 +75,7 @@ class Stats(ctypes.Structure):
         ("patch_pairs", _c.c_longlong),
         ("patch_tests", _c.c_longlong),
         ("quad_kept", _c.c_longlong),
+        ("patch_kept", _c.c_longlong),
     ]
 
     def as_dict(self):

@@ -83,6 +83,7 @@ struct Plan {
     unsigned char *pbox = nullptr;    // patch boxes of all meshes
     unsigned char *qbox = nullptr;    // their quarter boxes
     Cand *ppairs = nullptr;
+    Cand *psurv = nullptr;           // patch pairs left by the quarter test
     unsigned long long ppair_cap = 0;
     int2 *d_pairs = nullptr;
     PassEntry *d_pass_all = nullptr, *d_pass_A = nullptr, *d_pass_B = nullptr;
@@ -135,10 +136,10 @@ struct Plan {
     void free_scratch() {
         void *ptrs[] = {bmA, bmH, ek, ev, eslot, erank, grouped, tkey, crec, tcnt, tstart,
                         sort_scratch, cand, surv, hits, hk, hk2, okeys, hv, hv2,
-                        keep, kscan, ppairs, qsurv};
+                        keep, kscan, ppairs, psurv, qsurv};
         for (void *p : ptrs)
             if (p) cudaFree(p);
-        ppairs = nullptr;
+        ppairs = psurv = nullptr;
         qsurv = nullptr;
         bmA = bmH = nullptr; ek = nullptr; ev = eslot = erank = grouped = nullptr;
         tkey = nullptr; crec = nullptr; tcnt = nullptr; tstart = nullptr;
@@ -188,6 +189,7 @@ struct Plan {
         TMS_CK(dalloc(&cand, cand_cap));
         TMS_CK(dalloc(&qsurv, cand_cap));
         if (patch) TMS_CK(dalloc(&ppairs, ppair_cap));
+        if (patch) TMS_CK(dalloc(&psurv, ppair_cap));
         TMS_CK(dalloc(&surv, surv_cap));
         TMS_CK(dalloc(&hits, hit_cap));
         TMS_CK(dalloc(&hk, hit_cap));
@@ -309,11 +311,12 @@ struct Plan {
         if (patch) {
             // the quad pairs of the patch pairs
             PatchArgs pa;
-            pa.ppairs = ppairs; pa.ppair_cap = ppair_cap; pa.meshes = d_meshes; pa.pairs = d_pairs;
+            pa.ppairs = ppairs; pa.psurv = psurv; pa.ppair_cap = ppair_cap; pa.meshes = d_meshes;
+            pa.pairs = d_pairs;
             pa.ctr = d_ctr; pa.ent_cap = ent_cap; pa.cand = cand; pa.cand_cap = cand_cap;
             pa.moller = p.moller;
             launch_patch_quads(pa, prec, grid / 2, s);
-            kernels += 1;
+            kernels += 2;
         }
         mark(11, s);
 
@@ -759,6 +762,7 @@ tms_status search_core(const tms_mesh *A, const tms_mesh *B, int nPairs, const t
     st.patch_pairs = (long long)c.ppairs;
     st.patch_tests = (long long)c.ptests;
     st.quad_kept = (long long)c.qkeep;
+    st.patch_kept = (long long)c.psurv;
     st.raw_hits = (long long)c.raw_hits;
     st.hits = (long long)c.out;
     for (int d = 0; d < 4; ++d) st.grid_n[d] = P->h_grid0->n[d];

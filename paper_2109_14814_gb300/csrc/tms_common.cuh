@@ -138,6 +138,7 @@ struct Counters {
     unsigned long long claimed;    // cell-table slots claimed by this search
     unsigned long long ppairs;     // patch pairs with overlapping boxes (patch level)
     unsigned long long ptests;     // quad-pair box tests inside those patch pairs
+    unsigned long long psurv;      // patch pairs with an overlapping quarter pair
     unsigned long long raw_hits;
     unsigned long long out;
     unsigned int status;
@@ -488,6 +489,7 @@ void configure_emit();
 // pair, so each is emitted once.
 struct PatchArgs {
     const Cand *ppairs;            // patch pairs (faceA, faceB = patch ids)
+    Cand *psurv;                   // those with an overlapping quarter pair (pad = mask)
     unsigned long long ppair_cap;
     const MeshDev *meshes;         // the meshes (quad and patch boxes)
     const int2 *pairs;

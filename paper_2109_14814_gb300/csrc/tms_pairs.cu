@@ -413,54 +413,69 @@ void emit_waves(const EmitArgs &a, int face_level, int sms, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 constexpr int kPatchWarps = 8;
 constexpr unsigned kPatchFlush = 64;   // staged candidates per atomic
+constexpr int kQuarterBlock = 128;     // stage 1: one lane per patch pair
 
-// Patch pairs in A-major order: each warp takes a contiguous range of the pairs
-// sorted by A patch (k_ppair_rank / k_ppair_place), so a patch of A usually
-// meets several patches of B in a row and its quad boxes are loaded once.  Lane
-// l holds quad (row l / kPatchI, column l % kPatchI) of each patch.  A quad
-// whose box misses the other patch's box cannot overlap any quad of it (the
-// patch box holds them all), so each side is first cut to its quads that meet
-// the other patch; the pairs of the survivors (nA x nB of them, 32 per round,
-// pair t = (t / nB, t % nB)) take the box test of Sec. 6.2.2, optionally the
-// Moller test of Sec. 6.2.3, and are appended through a per-warp stage.  The
-// next pair's record and B boxes are loaded before the current pair is tested,
-// so their latency overlaps its work.
-struct QuadSide {
-    const void *fbox, *pbox;
-    int N, nqi, nqk, npi;
-};
-
-template <int PREC>
-__device__ __forceinline__ void load_side(const QuadSide &m, uint32_t patch, int r, int c, EBox<PREC> &box,
-                                          EBox<PREC> &pbox, bool &valid, uint32_t &q) {
-    const uint32_t pk = patch / (uint32_t)m.npi, pi = patch - pk * (uint32_t)m.npi;
-    const int kq = (int)pk * kPatchK + r, iq = (int)pi * kPatchI + c;
-    valid = kq < m.nqk && iq < m.nqi;
-    q = (uint32_t)kq * (uint32_t)m.N + (uint32_t)iq;
-    pbox.load(m.pbox, patch);
-    box.set_empty();
-    if (valid) box.load(m.fbox, q);
-}
-
-// One warp per patch pair, grid-stride over the pairs.  Each patch carries
-// four quarter boxes (2 x 2 blocks of 4 x 2 quads).  First the 16 quarter
-// pairs, one per lane: a patch pair none of whose quarter pairs overlap holds
-// no overlapping quad pair and is done before any quad box is read.  Then lane
-// l holds quad (row l / kPatchI, column l % kPatchI) of each patch; a quad
-// that meets none of the other patch's quarter boxes cannot overlap any of its
-// quads (they all lie in those boxes), so each side is cut to its quads that
-// meet one.  The survivors' pairs take the box test of Sec. 6.2.2 (optionally
-// the Moller test of Sec. 6.2.3) and are appended through a per-warp stage:
-// the smaller side's survivors stay in registers, one per lane and repeated in
-// G = 32 / n groups of lanes, while each round reads G of the other side's
-// survivors from shared memory (close to a broadcast), so a round costs two
-// short shared-memory reads and no division.
+// Each patch carries four quarter boxes (2 x 2 blocks of 4 x 2 quads).
+// Stage 1 (k_patch_quarters), one lane per patch pair: its 16 quarter pairs; a
+// patch pair none of whose quarter pairs overlap holds no overlapping quad pair
+// and is dropped before any quad box is read; the others are listed with their
+// 16-bit mask (bit 4 i + j: A quarter i meets B quarter j).
+// Stage 2 (k_patch_quads), one warp per listed pair, grid-stride: the pair's
+// quarter boxes and quad boxes are loaded together (neither waits for the
+// other).  Lane l holds quad (row l / kPatchI, column l % kPatchI) of each
+// patch; a quad that meets none of the other patch's quarter boxes cannot
+// overlap any of its quads (they all lie in those boxes), so each side is cut
+// to its quads that meet one.  The survivors' pairs take the box test of
+// Sec. 6.2.2 (optionally the Moller test of Sec. 6.2.3) and are appended
+// through a per-warp stage: the smaller side's survivors stay in registers, one
+// per lane and repeated in G = 32 / n groups of lanes, while each round reads G
+// of the other side's survivors from shared memory (close to a broadcast), so a
+// round costs two short shared-memory reads and no division.
 // patch id -> (patch row, patch column): the quotient by npi from a 64-bit
 // reciprocal (exact for 32-bit ids, npi >= 2)
 __device__ __forceinline__ void patch_rc(uint32_t patch, uint32_t npi, unsigned long long magic,
                                          uint32_t &pk, uint32_t &pi) {
     pk = npi == 1 ? patch : (uint32_t)__umul64hi((unsigned long long)patch, magic);
     pi = patch - pk * npi;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kQuarterBlock) k_patch_quarters(PatchArgs a) {
+    // nothing to do after an overflow of the patch-level grid (the host retries)
+    if (a.ctr->entries > a.ent_cap || a.ctr->pair_slots > kMaxPairSlots) return;
+    const unsigned long long n = clamp_count(&a.ctr->ppairs, a.ppair_cap);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    uint32_t cached_pair = 0xFFFFFFFFu;
+    const void *qbA = nullptr, *qbB = nullptr;
+    for (unsigned long long j0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u);
+         j0 < n; j0 += stride) {
+        const unsigned long long j = j0 + (threadIdx.x & 31);
+        uint32_t mask = 0;
+        Cand pp = {0u, 0u, 0u, 0u};
+        if (j < n) {
+            pp = a.ppairs[j];
+            if (pp.pair != cached_pair) {
+                const int2 pr = a.pairs[pp.pair];
+                qbA = a.meshes[pr.x].qbox;
+                qbB = a.meshes[pr.y].qbox;
+                cached_pair = pp.pair;
+            }
+            EBox<PREC> xa[4], xb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                xa[q].load(qbA, 4 * pp.faceA + q);
+                xb[q].load(qbB, 4 * pp.faceB + q);
+            }
+#pragma unroll
+            for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                for (int qb = 0; qb < 4; ++qb)
+                    mask |= (uint32_t)boxes_overlap(xa[qa], xb[qb]) << (4 * qa + qb);
+        }
+        pp.pad = mask;
+        const unsigned long long pos = warp_append(&a.ctr->psurv, mask != 0u, FULL);
+        if (mask != 0u) a.psurv[pos] = pp;
+    }
 }
 
 template <int PREC, bool MOLLER>
@@ -472,13 +487,12 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
     __shared__ Cand sOut[kPatchWarps][kPatchFlush + 32];
     // nothing to do after an overflow of the patch-level grid (the host retries)
     if (a.ctr->entries > a.ent_cap || a.ctr->pair_slots > kMaxPairSlots) return;
-    const unsigned long long n = clamp_count(&a.ctr->ppairs, a.ppair_cap);
+    const unsigned long long n = clamp_count(&a.ctr->psurv, a.ppair_cap);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
     const unsigned long long gw = blockIdx.x * (unsigned long long)kPatchWarps + warp;
     const unsigned long long nw = (unsigned long long)gridDim.x * kPatchWarps;
     const int r = lane / kPatchI, c = lane % kPatchI;
-    const uint32_t qi = (uint32_t)(lane >> 2) & 3u, qj = (uint32_t)lane & 3u;   // this lane's quarter pair
     Cand *stage = sOut[warp];
     unsigned staged = 0;
     unsigned long long tests = 0;
@@ -494,7 +508,7 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
     unsigned long long mgA = 0, mgB = 0;
     int2 pr = make_int2(0, 0);
     for (unsigned long long j = gw; j < n; j += nw) {
-        const Cand pp = a.ppairs[j];
+        const Cand pp = a.psurv[j];
         if (pp.pair != cached_pair) {
             pr = a.pairs[pp.pair];
             const MeshDev &ma = a.meshes[pr.x];
@@ -505,17 +519,10 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
             mgB = mb.pmagic;
             cached_pair = pp.pair;
         }
-        // the 16 quarter pairs (lanes 16..31 repeat lanes 0..15)
-        {
-            EBox<PREC> xa, xb;
-            xa.load(qbA, 4 * pp.faceA + qi);
-            xb.load(qbB, 4 * pp.faceB + qj);
-            if (!__any_sync(FULL, boxes_overlap(xa, xb))) continue;
-            __syncwarp();                      // the previous pair's quarter boxes are read
-            if (lane < 4) sQuart[warp][4 + lane] = xb;          // B's quarter `lane`
-            if ((lane & 3) == 0 && lane < 16) sQuart[warp][lane >> 2] = xa;   // A's quarter lane / 4
-            __syncwarp();
-        }
+        // lanes 0..7 load the quarter boxes (A's then B's) while every lane loads
+        // its two quad boxes below
+        EBox<PREC> xq;
+        if (lane < 8) xq.load(lane < 4 ? qbA : qbB, 4 * (lane < 4 ? pp.faceA : pp.faceB) + (lane & 3));
         uint32_t pka, pia, pkb, pib;
         patch_rc(pp.faceA, npiA, mgA, pka, pia);
         patch_rc(pp.faceB, npiB, mgB, pkb, pib);
@@ -529,6 +536,9 @@ __global__ void __launch_bounds__(32 * kPatchWarps, (PREC == 1 && !MOLLER) ? 3 :
         bb.set_empty();
         if (va) ba.load(fbA, qa);
         if (vb) bb.load(fbB, qb);
+        __syncwarp();                          // the previous pair's quarter boxes are read
+        if (lane < 8) sQuart[warp][lane] = xq;
+        __syncwarp();
         // survivors: quads meeting some quarter of the other patch
         bool sa = false, sb = false;
 #pragma unroll 1
@@ -608,14 +618,32 @@ int patch_resident() {
     return res;
 }
 
+int g_quarter_resident[2] = {};
+
+template <int PREC>
+int quarter_resident() {
+    int &res = g_quarter_resident[PREC];
+    if (res == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_patch_quarters<PREC>, kQuarterBlock, 0) !=
+                cudaSuccess || nb < 1)
+            nb = 1;
+        res = nb;
+    }
+    return res;
+}
+
 template <int PREC, bool MOLLER>
 void patch_waves(const PatchArgs &a, int sms, cudaStream_t st) {
+    k_patch_quarters<PREC><<<sms * quarter_resident<PREC>(), kQuarterBlock, 0, st>>>(a);
     k_patch_quads<PREC, MOLLER><<<sms * patch_resident<PREC, MOLLER>(), 32 * kPatchWarps, 0, st>>>(a);
 }
 
 }  // namespace
 
 void configure_patch_quads() {
+    quarter_resident<0>();
+    quarter_resident<1>();
     patch_resident<0, false>();
     patch_resident<0, true>();
     patch_resident<1, false>();
