@@ -84,13 +84,13 @@ STAGE_KERNELS = {
     "face_probe": "tms::k_cell_pass<EMIT_ALL>",
     "group_count": "tms::k_group_count",
     "group_cells": "tms::k_cells_* + k_group_scatter",
-    "emit": "tms::k_emit + k_patch_quads",
+    "emit": "tms::k_emit + k_patch_quarters + k_patch_quads",
     "narrow": "tms::k_quad_filter + k_narrow_filter + k_narrow_fp64",
     "sort_merge": "tms::k_radix_* + k_dedup_*",
 }
 BROAD_KERNELS = ("k_search_init", "k_bounds_pass", "k_grid_params", "k_cell_pass", "k_group_count",
                  "k_cells_reduce", "k_cells_partials", "k_cells_down", "k_group_scatter", "k_emit",
-                 "k_patch_quads")
+                 "k_patch_quarters", "k_patch_quads")
 
 
 def dist_env():
@@ -159,6 +159,7 @@ TRAFFIC_KERNELS = [
     ("k_cells_down", 1, "group_cells", True),
     ("k_group_scatter", 1, "group_cells", True),
     ("k_emit", 1, "emit", True),
+    ("k_patch_quarters", 1, "emit", True),
     ("k_patch_quads", 1, "emit", True),
     ("k_quad_filter", 1, "narrow", False),
     ("k_narrow_filter", 1, "narrow", False),
