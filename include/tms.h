@@ -121,7 +121,10 @@ typedef struct {
                              every earlier tile as not yet published, so each of
                              its bounded waits runs out after spin_limit polls
                              (no fault: the kernel records ST_TIMEOUT, keeps its
-                             writes in bounds and returns; TMS_ERR_TIMEOUT) */
+                             writes in bounds and returns; TMS_ERR_TIMEOUT),
+                             bit5 = start the patch-pair, candidate, survivor and
+                             raw-hit buffers at one record (exercises each growth
+                             and its retry) */
     int block_faces;      /* bounds-pass tile width in quads (64/128/256; 0 = 128) */
     int tile_rows;        /* bounds-pass tile height in quad rows (4 or 8; 0 = 4) */
     int timing;           /* 1 = record CUDA events between stages (in the graph) so
@@ -174,6 +177,27 @@ typedef struct {
 tms_status tms_search(tms_mesh A, tms_mesh B, const tms_params *params,
                       tms_hit *dHits, long long hitCap, long long *nHits,
                       void *stream);
+
+/*
+ * tms_search_host -- tms_search for meshes whose coordinates are given in host
+ * memory: copies the view rows [k0, k1) of both meshes' four coordinate arrays
+ * from host memory into the device arrays the meshes were built on, searches,
+ * and copies the merged hits to host memory; returns when they are there.
+ *   hostA, hostB : host, four pointers each (x, y, px, py), each a full M x N
+ *                  array in the layout of the device arrays (vertex (i, k) at
+ *                  k*N + i); pinned memory copies fastest.  The device arrays
+ *                  are overwritten with them.
+ *   hostHits     : host, room for hitCap records; nHits as in tms_search.
+ *   stream       : the copies and the search are ordered on it.
+ * Pinned (page-locked) hostHits receive the records directly from the merge;
+ * otherwise they pass through a per-device buffer of the library, grown on
+ * demand (the first call for a larger hitCap allocates).  Errors as
+ * tms_search; TMS_ERR_ARG for a NULL pointer.
+ */
+tms_status tms_search_host(tms_mesh A, const double *const hostA[4], tms_mesh B,
+                           const double *const hostB[4], const tms_params *params,
+                           tms_hit *hostHits, long long hitCap, long long *nHits,
+                           void *stream);
 
 /*
  * tms_search_batched -- nPairs independent searches (A[p], B[p]) of uneven

@@ -16,7 +16,7 @@ from ._binding import (CONTINUE_STATUS, HIT_BYTES, REFINE_STATUS, STAGES, Contin
                        surface_pair, TMS_ERR_ARG, TMS_ERR_CAPACITY, TMS_ERR_CUDA,
                        TMS_ERR_STATE, TMS_ERR_TIMEOUT, TMS_OK, HitPoint, Hits, Mesh, Params, Stats,
                        TmsError, autotune, backward, last_error, last_stage_ms, last_stats, lib, params,
-                       probe_fp64_tflops, release_workspace, search, search_batched,
+                       probe_fp64_tflops, release_workspace, search, search_batched, search_host,
                        search_noalloc, status_str, version)
 
 __all__ = ["CONTINUE_STATUS", "HIT_BYTES", "REFINE_STATUS", "STAGES", "ContinueParams", "Continued",
@@ -26,4 +26,4 @@ __all__ = ["CONTINUE_STATUS", "HIT_BYTES", "REFINE_STATUS", "STAGES", "ContinueP
            "TMS_ERR_STATE", "TMS_ERR_TIMEOUT", "TMS_OK", "HitPoint", "Hits", "Mesh", "Params",
            "Stats", "TmsError", "autotune", "backward", "last_error", "last_stage_ms", "last_stats", "lib",
            "params", "probe_fp64_tflops", "release_workspace", "search", "search_batched",
-           "search_noalloc", "status_str", "version"]
+           "search_host", "search_noalloc", "status_str", "version"]

@@ -147,6 +147,8 @@ def lib():
     L.tms_search.argtypes = [P, P, _c.POINTER(Params), P, LL, _c.POINTER(LL), P]
     L.tms_search.restype = I
     L.tms_search_batched.argtypes = [P, P, I, _c.POINTER(Params), P, LL, P, _c.POINTER(LL), P]
+    L.tms_search_host.argtypes = [P, P, P, P, _c.POINTER(Params), P, LL, _c.POINTER(LL), P]
+    L.tms_search_host.restype = I
     L.tms_search_batched.restype = I
     L.tms_backward.argtypes = [P, P, P, LL, P, P, P, P, P, P, P, P]
     L.tms_backward.restype = I
@@ -404,6 +406,29 @@ def search(A: Mesh, B: Mesh, hit_capacity: int = 1 << 16, stream=None, out=None,
                               _c.byref(n), st)
     if rc != TMS_OK:
         raise TmsError(rc, "tms_search")
+    return Hits(buf[: n.value])
+
+
+def search_host(A: Mesh, B: Mesh, XA: torch.Tensor, XB: torch.Tensor, out: torch.Tensor = None,
+                hit_capacity: int = 1 << 16, stream=None, **kw) -> Hits:
+    """tms_search_host: the search from host coordinates.  XA, XB: CPU float64
+    tensors of the meshes' full (4, M, N) shape (pinned memory copies fastest),
+    copied into the meshes' device arrays; the hits land in `out` (a CPU uint8
+    tensor of hit records, pinned for speed) or a new one."""
+    for X, m in ((XA, A), (XB, B)):
+        if X.device.type != "cpu" or X.dtype != torch.float64 or tuple(X.shape) != tuple(m.X.shape) \
+                or not X.is_contiguous():
+            raise ValueError("host coordinates must be contiguous CPU float64 of the mesh's shape")
+    p = params(**kw)
+    st = _stream(stream)
+    buf = out if out is not None else torch.empty((max(hit_capacity, 1), HIT_BYTES), dtype=torch.uint8)
+    ha = (_c.c_void_p * 4)(*[XA[c].data_ptr() for c in range(4)])
+    hb = (_c.c_void_p * 4)(*[XB[c].data_ptr() for c in range(4)])
+    n = _c.c_longlong(0)
+    rc = lib().tms_search_host(A.handle, ha, B.handle, hb, _c.byref(p), buf.data_ptr(), buf.shape[0],
+                               _c.byref(n), st)
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_search_host")
     return Hits(buf[: n.value])
 
 

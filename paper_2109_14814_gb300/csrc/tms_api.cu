@@ -620,6 +620,12 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     P->hit_cap = prm.hit_capacity > 0 ? (unsigned long long)prm.hit_capacity
                                       : std::max<unsigned long long>(1 << 14, P->cand_cap / 16);
     P->surv_cap = std::max<unsigned long long>(1 << 16, P->cand_cap / 8);
+    if (prm.inject & 32u) {
+        // test switch: the patch-pair, candidate, survivor and raw-hit buffers
+        // start at one record, so that each grows in turn
+        P->ppair_cap = patch ? 1 : 0;
+        P->cand_cap = P->surv_cap = P->hit_cap = 1;
+    }
     P->bmA_bits = std::min(26, std::max(11, ceil_log2(std::max<unsigned long long>(P->facesA, 1) * 8) - 5));
     P->bmH_bits = std::min(25, std::max(11, ceil_log2(P->ent_cap * 8) - 5));
     tms_status s = P->alloc_scratch();
@@ -944,6 +950,69 @@ tms_status tms_destroy_mesh(tms_mesh m) {
 tms_status tms_search(tms_mesh A, tms_mesh B, const tms_params *params, tms_hit *dHits,
                       long long hitCap, long long *nHits, void *stream) {
     return search_impl(&A, &B, 1, params, dHits, hitCap, nullptr, nHits, stream);
+}
+
+namespace {
+// the device output of tms_search_host, per device
+struct HostOut {
+    tms_hit *buf = nullptr;
+    long long cap = 0;
+};
+std::mutex g_host_mu;
+HostOut g_host_out[64];
+
+// the view rows of a mesh's four coordinate arrays from host memory
+tms_status upload_view(tms_mesh m, const double *const host[4], cudaStream_t st) {
+    for (int c = 0; c < 4; ++c)
+        if (!host[c]) return TMS_ERR_ARG;
+    const size_t off = (size_t)m->k0 * m->N;
+    const size_t bytes = (size_t)(m->k1 - m->k0) * m->N * sizeof(double);
+    for (int c = 0; c < 4; ++c)
+        TMS_CK(cudaMemcpyAsync(const_cast<double *>(m->dev.c[c]), host[c] + off, bytes,
+                               cudaMemcpyHostToDevice, st));
+    return TMS_OK;
+}
+}  // namespace
+
+tms_status tms_search_host(tms_mesh A, const double *const hostA[4], tms_mesh B,
+                           const double *const hostB[4], const tms_params *params,
+                           tms_hit *hostHits, long long hitCap, long long *nHits, void *stream) {
+    if (!hostA || !hostB || !nHits || hitCap < 0 || (hitCap > 0 && !hostHits)) return TMS_ERR_ARG;
+    int device = 0;
+    TMS_CK(cudaGetDevice(&device));
+    if (device < 0 || device >= 64) return TMS_ERR_ARG;
+    tms_status s;
+    if ((s = check_mesh(A, device)) != TMS_OK) return s;
+    if ((s = check_mesh(B, device)) != TMS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = upload_view(A, hostA, st)) != TMS_OK) return s;
+    if ((s = upload_view(B, hostB, st)) != TMS_OK) return s;
+    // pinned host output: the merge writes the records there directly (no copy
+    // back, no second synchronisation)
+    if (hitCap > 0) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, hostHits) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer)
+            return tms_search(A, B, params, static_cast<tms_hit *>(at.devicePointer), hitCap, nHits, stream);
+        cudaGetLastError();
+    }
+    // one caller at a time per device owns the output buffer for the whole call
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    HostOut &o = g_host_out[device];
+    const long long need = hitCap > 0 ? hitCap : 1;
+    if (o.cap < need) {
+        if (o.buf) cudaFree(o.buf);
+        o.buf = nullptr;
+        o.cap = 0;
+        TMS_CK(cudaMalloc((void **)&o.buf, (size_t)need * sizeof(tms_hit)));
+        o.cap = need;
+    }
+    s = tms_search(A, B, params, o.buf, hitCap, nHits, stream);
+    if (s != TMS_OK && s != TMS_ERR_CAPACITY) return s;
+    const long long n = *nHits < hitCap ? *nHits : hitCap;
+    if (n > 0) TMS_CK(cudaMemcpyAsync(hostHits, o.buf, (size_t)n * sizeof(tms_hit), cudaMemcpyDeviceToHost, st));
+    TMS_CK(cudaStreamSynchronize(st));
+    return s;
 }
 
 tms_status tms_search_batched(const tms_mesh *A, const tms_mesh *B, int nPairs,

@@ -260,6 +260,14 @@ def test_capacity_retry_and_injected_errors():
     assert list(zip(h["triA"], h["triB"])) == list(zip(base["triA"], base["triB"]))
     assert np.array_equal(h["z"], base["z"])
     assert tms.last_stats()["retries"] >= 1
+    # patch-pair, candidate, survivor and raw-hit buffers started at one record:
+    # each overflows in turn and is grown; the final search matches bit for bit
+    for kw in (dict(), dict(patch=0)):
+        ref = gpu_records(tms.search(A, B, **kw))
+        h = gpu_records(tms.search(A, B, inject=32, **kw))
+        for k in ref:
+            assert np.array_equal(h[k], ref[k], equal_nan=ref[k].dtype.kind == "f"), k
+        assert tms.last_stats()["retries"] >= (4 if not kw else 3)
     # too-small output buffer: TMS_ERR_CAPACITY with the required count
     out = torch.empty((3, tms.HIT_BYTES), dtype=torch.uint8, device="cuda")
     with pytest.raises(tms.TmsError) as e:
@@ -324,3 +332,71 @@ def test_bad_arguments():
         tms.search(A, A, spin_limit=-1)
     with pytest.raises(tms.TmsError):
         tms.search(A, A, patch=2)
+
+
+def test_search_host_matches_device_search():
+    """tms_search_host: host coordinates copied into the meshes' device arrays,
+    the search, the hits copied back -- bit for bit the device search, for
+    pinned and pageable host memory and for a half-layer view."""
+    p = cached("c2", synth.config2)
+    XA = torch.empty_like(p.A.X, device="cuda")
+    XB = torch.empty_like(p.B.X, device="cuda")
+    A = tms.Mesh(XA, p.A.s, True)
+    B = tms.Mesh(XB, p.B.s, True)
+    ref = gpu_search(p)
+    for pin in (False, True):
+        hA = p.A.X.contiguous().pin_memory() if pin else p.A.X.contiguous()
+        hB = p.B.X.contiguous().pin_memory() if pin else p.B.X.contiguous()
+        XA.zero_()
+        XB.zero_()
+        # pinned output: the records are written there by the device directly
+        out = torch.empty((1 << 12, tms.HIT_BYTES), dtype=torch.uint8)
+        h = tms.search_host(A, B, hA, hB, out=out.pin_memory() if pin else out)
+        assert h.raw.device.type == "cpu"
+        g = gpu_records(h)
+        for k in ref:
+            assert np.array_equal(g[k], ref[k], equal_nan=ref[k].dtype.kind == "f"), k
+        assert torch.equal(XA.cpu(), p.A.X) and torch.equal(XB.cpu(), p.B.X)
+    # a view: only its columns are copied
+    XA.zero_()
+    Av = tms.Mesh(XA, p.A.s, True, k0=40, k1=200)
+    Bf = tms.Mesh.from_grid(p.B)
+    hv = gpu_records(tms.search_host(Av, Bf, p.A.X.contiguous(), p.B.X.contiguous()))
+    Xv = p.A.X.cuda()
+    rv = gpu_records(tms.search(tms.Mesh(Xv, p.A.s, True, k0=40, k1=200), Bf))
+    assert list(zip(hv["triA"], hv["triB"])) == list(zip(rv["triA"], rv["triB"]))
+    assert float(XA[:, :40].abs().sum()) == 0.0
+    # a host output too small: TMS_ERR_CAPACITY (pageable and pinned)
+    for pin in (False, True):
+        out = torch.empty((3, tms.HIT_BYTES), dtype=torch.uint8)
+        with pytest.raises(tms.TmsError) as e:
+            tms.search_host(A, B, p.A.X.contiguous(), p.B.X.contiguous(), out=out.pin_memory() if pin else out)
+        assert e.value.status == tms.TMS_ERR_CAPACITY
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small_pairs_against_bruteforce(seed):
+    """Seeded random small pairs -- sizes that leave ragged strips, patches and
+    tiles, periodic or open A, a half-layer view -- in every precision mode and
+    broad-phase level, each against the oracle's brute force."""
+    rng = np.random.default_rng(1000 + seed)
+    NA, MA = int(rng.integers(3, 70)), int(rng.integers(2, 30))
+    NB, MB = int(rng.integers(3, 70)), int(rng.integers(2, 30))
+    p = synth.build_pair(5000 + seed, NA, MA, NB, MB, stretch="exp", n_folds=int(rng.integers(0, 3)),
+                         sites=(2 * int(rng.integers(1, 4)), int(rng.integers(1, 3))),
+                         n_hits=int(rng.integers(0, 6)))
+    A = p.A
+    if seed % 3 == 1:
+        A = synth.MeshGrid(p.A.X, p.A.s, periodic=False)
+    OA, OB = oracle.OMesh.from_grid(A), oracle.OMesh.from_grid(p.B)
+    ref = oracle.search(OA, OB, method="brute")
+    for kw in (dict(), dict(patch=0), dict(precision=0), dict(face_level=0), dict(precision=0, patch=0)):
+        g = gpu_search(synth.MeshPair(A, p.B, None), **kw)
+        check_sorted_unique(g)
+        compare(OA, OB, g, ref)
+    if MA >= 6:
+        k0, k1 = 1, MA - 2
+        XA = A.X.cuda()
+        h = gpu_records(tms.search(tms.Mesh(XA, A.s, A.periodic, k0=k0, k1=k1), tms.Mesh.from_grid(p.B)))
+        OAv = oracle.OMesh(A.X[:, k0:k1].numpy(), A.s[k0:k1].numpy(), A.periodic)
+        compare(OAv, OB, h, oracle.search(OAv, OB, method="brute"))
