@@ -189,8 +189,7 @@ tms_status tms_search(tms_mesh A, tms_mesh B, const tms_params *params,
  *                  are overwritten with them.
  *   hostHits     : host, room for hitCap records; nHits as in tms_search.
  *   stream       : the copies and the search are ordered on it.
- * Pinned (page-locked) hostHits receive the records directly from the merge;
- * otherwise they pass through a per-device buffer of the library, grown on
+ * The device output lives in a per-device buffer of the library, grown on
  * demand (the first call for a larger hitCap allocates).  Errors as
  * tms_search; TMS_ERR_ARG for a NULL pointer.
  */

@@ -31,6 +31,13 @@ namespace {
 
 constexpr unsigned kMagic = 0x746d7331u;  // "tms1"
 std::mutex g_mu;
+// tms_search_host: the first n output records copied to host memory right
+// after the search on its stream, before the synchronisation that reads the count
+struct EarlyCopy {
+    tms_hit *host = nullptr;
+    long long n = 0;
+};
+thread_local EarlyCopy g_early;
 std::atomic<long long> g_next_id{1};
 thread_local std::string g_err;
 
@@ -379,6 +386,9 @@ struct Plan {
             enqueue(st);
             TMS_CK(cudaGetLastError());
         }
+        if (g_early.host && g_early.n > 0 && dHits)
+            TMS_CK(cudaMemcpyAsync(g_early.host, dHits, (size_t)g_early.n * sizeof(tms_hit),
+                                   cudaMemcpyDeviceToHost, st));
         TMS_CK(cudaEventRecord(ev_out, st));
         TMS_CK(cudaStreamWaitEvent(user, ev_out, 0));
         TMS_CK(cudaEventSynchronize(ev_out));
@@ -957,16 +967,27 @@ namespace {
 struct HostOut {
     tms_hit *buf = nullptr;
     long long cap = 0;
+    long long last_n = 0;   // the previous call's count: records copied with the count
 };
 std::mutex g_host_mu;
 HostOut g_host_out[64];
 
-// the view rows of a mesh's four coordinate arrays from host memory
+// the view rows of a mesh's four coordinate arrays from host memory: one 2D
+// copy when the four arrays are equally spaced on both sides (one tensor of
+// shape (4, M, N), say), else one copy per coordinate
 tms_status upload_view(tms_mesh m, const double *const host[4], cudaStream_t st) {
     for (int c = 0; c < 4; ++c)
         if (!host[c]) return TMS_ERR_ARG;
     const size_t off = (size_t)m->k0 * m->N;
     const size_t bytes = (size_t)(m->k1 - m->k0) * m->N * sizeof(double);
+    const ptrdiff_t dp = m->dev.c[1] - m->dev.c[0], hp = host[1] - host[0];
+    bool even = dp > 0 && hp > 0 && (size_t)dp * sizeof(double) >= bytes && (size_t)hp * sizeof(double) >= bytes;
+    for (int c = 2; c < 4; ++c) even = even && m->dev.c[c] - m->dev.c[c - 1] == dp && host[c] - host[c - 1] == hp;
+    if (even) {
+        TMS_CK(cudaMemcpy2DAsync(const_cast<double *>(m->dev.c[0]), (size_t)dp * sizeof(double), host[0] + off,
+                                 (size_t)hp * sizeof(double), bytes, 4, cudaMemcpyHostToDevice, st));
+        return TMS_OK;
+    }
     for (int c = 0; c < 4; ++c)
         TMS_CK(cudaMemcpyAsync(const_cast<double *>(m->dev.c[c]), host[c] + off, bytes,
                                cudaMemcpyHostToDevice, st));
@@ -987,15 +1008,6 @@ tms_status tms_search_host(tms_mesh A, const double *const hostA[4], tms_mesh B,
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = upload_view(A, hostA, st)) != TMS_OK) return s;
     if ((s = upload_view(B, hostB, st)) != TMS_OK) return s;
-    // pinned host output: the merge writes the records there directly (no copy
-    // back, no second synchronisation)
-    if (hitCap > 0) {
-        cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, hostHits) == cudaSuccess && at.type == cudaMemoryTypeHost &&
-            at.devicePointer)
-            return tms_search(A, B, params, static_cast<tms_hit *>(at.devicePointer), hitCap, nHits, stream);
-        cudaGetLastError();
-    }
     // one caller at a time per device owns the output buffer for the whole call
     std::lock_guard<std::mutex> lk(g_host_mu);
     HostOut &o = g_host_out[device];
@@ -1007,11 +1019,21 @@ tms_status tms_search_host(tms_mesh A, const double *const hostA[4], tms_mesh B,
         TMS_CK(cudaMalloc((void **)&o.buf, (size_t)need * sizeof(tms_hit)));
         o.cap = need;
     }
+    // the records are copied back in the same round trip as the count, as many
+    // as the previous call found and a margin; the rest, if any, after it
+    const long long guess = std::min(hitCap, o.last_n + o.last_n / 8 + 64);
+    g_early.host = hostHits;
+    g_early.n = guess;
     s = tms_search(A, B, params, o.buf, hitCap, nHits, stream);
+    g_early = EarlyCopy();
     if (s != TMS_OK && s != TMS_ERR_CAPACITY) return s;
     const long long n = *nHits < hitCap ? *nHits : hitCap;
-    if (n > 0) TMS_CK(cudaMemcpyAsync(hostHits, o.buf, (size_t)n * sizeof(tms_hit), cudaMemcpyDeviceToHost, st));
-    TMS_CK(cudaStreamSynchronize(st));
+    o.last_n = n;
+    if (n > guess) {
+        TMS_CK(cudaMemcpyAsync(hostHits + guess, o.buf + guess, (size_t)(n - guess) * sizeof(tms_hit),
+                               cudaMemcpyDeviceToHost, st));
+        TMS_CK(cudaStreamSynchronize(st));
+    }
     return s;
 }
 

@@ -349,7 +349,6 @@ def test_search_host_matches_device_search():
         hB = p.B.X.contiguous().pin_memory() if pin else p.B.X.contiguous()
         XA.zero_()
         XB.zero_()
-        # pinned output: the records are written there by the device directly
         out = torch.empty((1 << 12, tms.HIT_BYTES), dtype=torch.uint8)
         h = tms.search_host(A, B, hA, hB, out=out.pin_memory() if pin else out)
         assert h.raw.device.type == "cpu"
