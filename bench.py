@@ -47,15 +47,17 @@ REF_MAX_STEPS = 10                     # timed oracle searches of the reference 
 FP32_SOLVE_FLOPS = 956
 # FP32 operations of the separating-axis prefilter with all four axes: five
 # split difference vectors with bounds (80), two offset vectors (16), two sets
-# of Plucker coordinates (56), det A with its error bound (46), the Frobenius
-# bound and kappa (70), the two dual choices (28), four interval tests (260)
-SAT_FLOPS = 551
+# of Plucker coordinates (56), the FP64 solve's reach (12), the two dual
+# choices (28), four interval tests (260)
+SAT_FLOPS = 452
 # FP32 operations of the quad-level test of one quad candidate: seven split
-# difference vectors (112), four edge differences (32), four sets of Plucker
-# coordinates (112), eight squared-norm bounds (112), four determinant bounds
-# (180), kappa and delta (40), two dual choices (28), four interval tests over
-# eight vertices (360)
-QUAD_SAT_FLOPS = 964
+# difference vectors (112), two sets of Plucker coordinates (56), the FP64
+# solve's reach (20), two dual choices (28), four interval tests over eight
+# vertices (360)
+QUAD_SAT_FLOPS = 576
+# FP32 lane operations per second of one GB300 (152 SMs x 128 lanes x 2070 MHz,
+# an FMA counted 2)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # FP64 operations of one narrow-phase solve of Eq. (precise) (an FMA counts 2):
 # the 16 matrix entries and 4 right-hand-side entries (20), the squared column
 # norms (28), elimination with partial pivoting (46) and back substitution
@@ -476,6 +478,19 @@ def run_tms(args, ws, rank, local):
                 "peak_kind": "measured FP64 FMA-chain probe on this GPU"}
     except Exception as e:  # the probe is optional diagnostics
         fp64 = {"error": str(e)}
+    # FP32 arithmetic of the narrow phase's filters (quad-level and triangle-level
+    # separating axes, verified solves) over the narrow stage's time, against the
+    # FP32 lane rate at the maximum clock
+    t_narrow = stage_ms.get("narrow", 0.0)
+    f32 = (QUAD_SAT_FLOPS * stats["quad_tests"] + SAT_FLOPS * stats["sat_tests"]
+           + FP32_SOLVE_FLOPS * stats["fp32_solves"])
+    ach32 = f32 / (t_narrow / 1e3) / 1e12 if t_narrow > 0 else None
+    narrow_fp32 = {"bound": "alu", "flops": f32, "ms": t_narrow, "achieved_tflops": ach32,
+                   "peak_tflops": FP32_PEAK_TFLOPS,
+                   "frac": ach32 / FP32_PEAK_TFLOPS if ach32 else None,
+                   "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz, FMA = 2",
+                   "counts": {"quad_tests": stats["quad_tests"], "sat_tests": stats["sat_tests"],
+                              "fp32_solves": stats["fp32_solves"]}}
 
     # end to end through the C ABI with host buffers (tms_search_host: the
     # vertices copied from pinned host memory, the search, the hits copied back)
@@ -535,7 +550,8 @@ def run_tms(args, ws, rank, local):
                        quad_tests=stats["quad_tests"], quad_kept=stats["quad_kept"],
                        sat_tests=stats["sat_tests"],
                        fp32_solves=stats["fp32_solves"], fp64_solves=stats["fp64_solves"]),
-        "roofline": roofline, "kernels": kernels, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "kernels": kernels, "fp64": fp64, "narrow_fp32": narrow_fp32,
+        "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clk.summary(), "gpu_launches": stats["kernels"] * args.steps,
         "source_hash": source_hash(),
         "stage_ms": stage_ms, "wall_s": wall,

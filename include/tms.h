@@ -100,9 +100,11 @@ typedef struct {
     int cell_filter;      /* 1 = register only faces in grid cells occupied by
                              both meshes before grouping (default); 0 = emit
                              every face-cell incidence (the paper's per-box lists). */
-    int narrow_filter;    /* 1 = reject candidates with an FP32 solve whose
-                             forward-error bound certifies margin < -2 tau
-                             (default); undecided candidates get the FP64 solve. */
+    int narrow_filter;    /* 1 = reject candidates the FP32 tests prove are no
+                             FP64 hit: separating axes against the FP64 solve's
+                             backward error, and a verified FP32 solve whose
+                             error bound certifies margin < -2 tau (default);
+                             undecided candidates get the FP64 solve. */
     float cell_mult;      /* grid cell edge = cell_mult x widest face extent per
                              coordinate (Sec. 6.2.1 requires > 1 x); default 1.0625 */
     double tau;           /* margin tolerance of the hit test, default 1e-12 */

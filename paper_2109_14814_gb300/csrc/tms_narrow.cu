@@ -331,16 +331,13 @@ __device__ __noinline__ bool fp32_verified_reject(const float4 X[3][2], const fl
 // verified solve, which it precedes.
 //
 // Lemma.  For any direction w let I_X = [min_i w.x_i, max_i w.x_i] (length D_X)
-// and I_Y likewise.  If the exact margin m >= -delta, the common point
-// P = sum_i beta_i x_i = sum_j gamma_j y_j has weights >= -delta summing to 1,
-// so w.P lies within 2 delta D_X of I_X and within 2 delta D_Y of I_Y; hence a
-// gap g > 2 delta (D_X + D_Y) between I_X and I_Y proves m < -delta.
-// delta = 2 tau + 8192 u64 kappa covers the FP64 solve's own error: with
-// kappa >= cond_2(A) (here kappa = |A|_F^4 / |det A|, since
-// sigma_4 >= |det A| / sigma_1^3), partial pivoting on a 4x4 system moves z by
-// at most about 1536 u64 kappa |z|_inf; if |z|_inf <= 2 that is below delta - tau,
-// and if |z|_inf = L > 2 the exact margin is at most -(L - 1) / 2, which such
-// an error cannot lift to -tau while kappa <= 1e10 (checked).
+// and I_Y likewise.  A point of a triangle widened to weights >= -t projects
+// within 3 t D_X of I_X (weights w_i = (1 + 3t) l_i - t with l on the simplex).
+// If the FP64 solve reports a hit, its weights are >= -tau' and the two points
+// it describes lie within fp64_reach of each other (backward error, below), so
+// a gap g > 3 tau' (D_X + D_Y) + |w|_1 reach between I_X and I_Y proves that
+// it reports none -- with no condition on the system, so near-parallel
+// triangle planes are cleared too.
 // Directions: for each triangle the two longest of the four vectors orthogonal
 // to its plane (the duals of e1 ^ e2 ^ axis_k, read off the plane's Plucker
 // coordinates m_ij = e1_i e2_j - e1_j e2_i); any direction is valid, these
@@ -449,10 +446,31 @@ __device__ __forceinline__ float dot4(const float w[4], const SplitVec &v) {
     return fmaf(w[3], v.v[3], fmaf(w[2], v.v[2], fmaf(w[1], v.v[1], w[0] * v.v[0])));
 }
 
-// the gap test along w for X = {0, e1, e2} and Y = {r, s1, s3} (all relative to x2)
+// How far apart two triangles can be and still make an FP64 hit.  The FP64
+// solve (Gaussian elimination with partial pivoting, reciprocal pivots, on the
+// 4 x 4 system of Eq. (precise)) returns z with (A + E) z = r + e, where
+// |E_ij| <= gamma_30 (|L||U|)_ij + u64 |A_ij| <= 1.1e-13 max|A| (multipliers <= 1,
+// growth <= 2^3, the rounding of A's entries from the vertices included) and
+// |e| <= u64 |r|.  A hit has weights >= -tau' (tau' = tau plus the rounding of the
+// margin, 1e-15 at most), so |z| <= 1 + 2 tau' and the points x2 + a e1 + b e2
+// and y2 + c f1 + d f2 of the two triangles, widened to weights >= -tau', differ
+// by A z - r = e - E z: at most fp64_reach(max|A|, |r|) in every coordinate.
+// A separating-axis test that proves the widened triangles further apart than
+// that therefore proves that the FP64 solve reports no hit -- whatever the
+// system's condition.
+__device__ __forceinline__ float fp64_reach(float amax, float rmax) {
+    return (5e-13f * amax + 1.2e-16f * rmax) * 1.01f + 1e-37f;
+}
+
+// along w, a triangle's projection widened to weights >= -tau' grows by at most
+// 3 tau' times its length on each side; tp = 3 tau' from tau (FP32, rounded up)
+__device__ __forceinline__ float widen3(float tau) { return 3.0f * tau * 1.001f + 3e-15f; }
+
+// the gap test along w for X = {0, e1, e2} and Y = {r, s1, s3} (all relative to x2):
+// the widened projections apart by more than |w|_1 reach
 __device__ __forceinline__ bool separated(const float w[4], const SplitVec &e1, const SplitVec &e2,
                                           const SplitVec &r, const SplitVec &s1, const SplitVec &s3,
-                                          float delta) {
+                                          float tp, float reach) {
     const float u = 5.9604645e-08f;
     const float w1 = fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]) + fabsf(w[3]);
     // |fl(w.v) - w.v_exact| <= |w|_1 (4.01 u M_v + E_v)
@@ -464,56 +482,19 @@ __device__ __forceinline__ bool separated(const float w[4], const SplitVec &e1, 
     const float xl = fminf(0.0f, fminf(a1, a3)), xh = fmaxf(0.0f, fmaxf(a1, a3));
     const float yl = fminf(b2, fminf(b1, b3)), yh = fmaxf(b2, fmaxf(b1, b3));
     const float DX = (xh - xl) + 2.0f * ex, DY = (yh - yl) + 2.0f * ey;
-    const float need = (2.0f * delta * (DX + DY) + ex + ey) * 1.001f;
+    const float need = (tp * (DX + DY) + w1 * reach + ex + ey) * 1.001f;
     const float gap = fmaxf(yl - xh, xl - yh) * (1.0f - 4.0f * u);
     return gap > need;
 }
 
-// a - b of two vectors with bounds
-__device__ __forceinline__ SplitVec sub_vec(const SplitVec &a, const SplitVec &b) {
-    const float u = 5.9604645e-08f;
-    SplitVec r;
-    float vm = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        r.v[c] = a.v[c] - b.v[c];
-        vm = fmaxf(vm, fabsf(r.v[c]));
-    }
-    r.E = (a.E + b.E + u * vm) * 1.001f;
-    r.M = vm;
-    return r;
-}
-
-// an upper bound of |v|^2 for the exact vector
-__device__ __forceinline__ float sq_hi(const SplitVec &v) {
-    float q = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) q = fmaf(v.v[c], v.v[c], q);
-    return (q + 8.0f * v.E * v.M + 4.0f * v.E * v.E) * 1.0005f;
-}
-
-// a lower bound of |det [e1 e2 f1 f2]| from the two planes' Plucker coordinates
-__device__ __forceinline__ float det_lo_of(const float mE[6], float epsE, const float mF[6], float epsF) {
-    const float u = 5.9604645e-08f;
-    const float det = mE[0] * mF[5] - mE[1] * mF[4] + mE[2] * mF[3] + mE[3] * mF[2] - mE[4] * mF[1] +
-                      mE[5] * mF[0];
-    float tE = 0.0f, tF = 0.0f, sabs = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        tE += fabsf(mE[k]);
-        tF += fabsf(mF[k]);
-        sabs = fmaf(fabsf(mE[k]), fabsf(mF[5 - k]), sabs);
-    }
-    return fabsf(det) - (epsF * tE + epsE * tF + 6.0f * epsE * epsF + (8.0f * u) * sabs) * 1.01f;
-}
-
-// Quad-level form of the separating-axis test: true when every one of the four
-// triangle pairs of the quad candidate is proven to have margin below -delta.
-// A triangle's vertices are among its quad's, so its projected interval lies
-// inside the quad's: a gap between the quads' intervals larger than
-// 2 delta (D_A + D_B) is larger than 2 delta (D_Ta + D_Tb) for every pair.
-// delta uses the largest kappa of the four pairs.  Axes: the two longest
-// duals of each quad's first triangle.
+// Quad-level form of the separating-axis test: true when no one of the four
+// triangle pairs of the quad candidate can be an FP64 hit (fp64_reach).  A
+// triangle's vertices are among its quad's, so its projected interval lies
+// inside the quad's, and its widening (3 tau' times its length) is at most the
+// quad's.  Axes: the two longest duals of each quad's first triangle.  Every
+// triangle's edges are differences of the quad's vertices (|A_ij| <= 2 max of
+// the edge vectors below), and every offset y2 - x2 is r0 plus at most the
+// vectors to each quad's far vertex.
 // the quad-level test on the edge vectors of both quads relative to v0 of A
 __device__ __forceinline__ bool quad_sat_vectors(const SplitVec &a1, const SplitVec &a2, const SplitVec &a3,
                                                  const SplitVec &b1, const SplitVec &b2, const SplitVec &b3,
@@ -522,29 +503,11 @@ __device__ __forceinline__ bool quad_sat_vectors(const SplitVec &a1, const Split
     float mA1[6], mB1[6], epsA1, epsB1;
     plucker(a1, a2, mA1, epsA1);
     plucker(b1, b2, mB1, epsB1);
-    float kmax;
-    {
-        const SplitVec a23 = sub_vec(a2, a3), a13 = sub_vec(a1, a3);
-        const SplitVec b23 = sub_vec(b2, b3), b13 = sub_vec(b1, b3);
-        float mA2[6], mB2[6], epsA2, epsB2;
-        plucker(a23, a13, mA2, epsA2);
-        plucker(b23, b13, mB2, epsB2);
-        const float FA[2] = {sq_hi(a1) + sq_hi(a2), sq_hi(a23) + sq_hi(a13)};
-        const float FB[2] = {sq_hi(b1) + sq_hi(b2), sq_hi(b23) + sq_hi(b13)};
-        const float d11 = det_lo_of(mA1, epsA1, mB1, epsB1), d12 = det_lo_of(mA1, epsA1, mB2, epsB2);
-        const float d21 = det_lo_of(mA2, epsA2, mB1, epsB1), d22 = det_lo_of(mA2, epsA2, mB2, epsB2);
-        const float f11 = (FA[0] + FB[0]) * 1.0005f, f12 = (FA[0] + FB[1]) * 1.0005f;
-        const float f21 = (FA[1] + FB[0]) * 1.0005f, f22 = (FA[1] + FB[1]) * 1.0005f;
-        const float F4[4] = {f11 * f11, f12 * f12, f21 * f21, f22 * f22};
-        const float D[4] = {d11, d12, d21, d22};
-        kmax = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (!(D[k] > 0.0f) || !(F4[k] <= 1e10f * D[k])) return false;
-            kmax = fmaxf(kmax, F4[k] / D[k]);
-        }
-    }
-    const float delta = 2.0f * tau * 1.001f + 9.1e-13f * kmax * 1.001f;
+    const float amax = 2.0f * fmaxf(fmaxf(fmaxf(a1.M + a1.E, a2.M + a2.E), fmaxf(a3.M + a3.E, b1.M + b1.E)),
+                                    fmaxf(b2.M + b2.E, b3.M + b3.E));
+    const float rmax = (r0.M + r0.E) + (a3.M + a3.E) + (b3.M + b3.E);
+    const float reach = fp64_reach(amax * 1.001f, rmax * 1.001f);
+    const float tp = widen3(tau);
     int kA1, kA2, kB1, kB2;
     top2_duals(mA1, kA1, kA2);
     top2_duals(mB1, kB1, kB2);
@@ -567,7 +530,7 @@ __device__ __forceinline__ bool quad_sat_vectors(const SplitVec &a1, const Split
         const float xl = fminf(fminf(0.0f, p1), fminf(p2, p3)), xh = fmaxf(fmaxf(0.0f, p1), fmaxf(p2, p3));
         const float yl = fminf(fminf(q0, s1), fminf(s2, s3)), yh = fmaxf(fmaxf(q0, s1), fmaxf(s2, s3));
         const float DX = (xh - xl) + 2.0f * ea, DY = (yh - yl) + 2.0f * eb;
-        const float need = (2.0f * delta * (DX + DY) + ea + eb) * 1.001f;
+        const float need = (tp * (DX + DY) + w1 * reach + ea + eb) * 1.001f;
         const float gap = fmaxf(yl - xh, xl - yh) * (1.0f - 4.0f * u);
         if (gap > need) return true;
     }
@@ -586,23 +549,10 @@ __device__ __forceinline__ bool quad_sat_reject_hi(const float4 QA[4], const flo
     return quad_sat_vectors(a1, a2, a3, b1, b2, b3, r0, tau);
 }
 
-__device__ __forceinline__ bool quad_sat_reject(const float4 QA[4][2], const float4 QB[4][2],
-                                                float tau) {
-    // vertices v0 (i,k), v1 (i+1,k), v2 (i,k+1), v3 (i+1,k+1); T1 = (v1, v0, v2),
-    // T2 = (v2, v3, v1): T1's edges are (v1 - v0, v2 - v0), T2's (v2 - v3, v1 - v3)
-    const SplitVec a1 = split_vec(QA[1], QA[0]), a2 = split_vec(QA[2], QA[0]);
-    const SplitVec a3 = split_vec(QA[3], QA[0]);
-    const SplitVec b1 = split_vec(QB[1], QB[0]), b2 = split_vec(QB[2], QB[0]);
-    const SplitVec b3 = split_vec(QB[3], QB[0]);
-    const SplitVec r0 = split_vec(QB[0], QA[0]);
-    return quad_sat_vectors(a1, a2, a3, b1, b2, b3, r0, tau);
-}
-
-// true when the separating-axis test proves the margin below -delta (not a hit,
-// also for an FP64 solve of the same system)
+// true when the separating-axis test proves that the FP64 solve of the pair
+// reports no hit (fp64_reach)
 __device__ __noinline__ bool fp32_sat_reject(const float4 X[3][2], const float4 Y[3][2],
                                                 float tau) {
-    const float u = 5.9604645e-08f;
     // vectors relative to x2
     const SplitVec e1 = split_vec(X[0], X[1]);    // x1 - x2
     const SplitVec e2 = split_vec(X[2], X[1]);    // x3 - x2
@@ -613,34 +563,9 @@ __device__ __noinline__ bool fp32_sat_reject(const float4 X[3][2], const float4 
     float mE[6], mF[6], epsE, epsF;
     plucker(e1, e2, mE, epsE);
     plucker(f1, f2, mF, epsF);
-    // det [e1 e2 f1 f2] (= det A up to sign) and a bound on its error
-    const float det = mE[0] * mF[5] - mE[1] * mF[4] + mE[2] * mF[3] + mE[3] * mF[2] - mE[4] * mF[1] +
-                      mE[5] * mF[0];
-    float tE = 0.0f, tF = 0.0f, sabs = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        tE += fabsf(mE[k]);
-        tF += fabsf(mF[k]);
-        sabs = fmaf(fabsf(mE[k]), fabsf(mF[5 - k]), sabs);
-    }
-    const float derr = (epsF * tE + epsE * tF + 6.0f * epsE * epsF + (8.0f * u) * sabs) * 1.01f;
-    const float det_lo = fabsf(det) - derr;
-    // |A|_F^2 upper bound from the four edge vectors
-    float f2sum = 0.0f;
-    const SplitVec *cols[4] = {&e1, &e2, &f1, &f2};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        float q = 0.0f;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) q = fmaf(cols[j]->v[c], cols[j]->v[c], q);
-        f2sum += q + 8.0f * cols[j]->E * cols[j]->M + 4.0f * cols[j]->E * cols[j]->E;
-    }
-    f2sum *= 1.001f;
-    const float F4 = f2sum * f2sum;
-    // kappa = F4 / det_lo <= 1e10, and delta from it
-    if (!(det_lo > 0.0f) || !(F4 <= 1e10f * det_lo)) return false;
-    const float kappa = F4 / det_lo * 1.001f;
-    const float delta = 2.0f * tau * 1.001f + 9.1e-13f * kappa;
+    const float amax = fmaxf(fmaxf(e1.M + e1.E, e2.M + e2.E), fmaxf(f1.M + f1.E, f2.M + f2.E));
+    const float reach = fp64_reach(amax * 1.001f, (r.M + r.E) * 1.001f);
+    const float tp = widen3(tau);
     int kE1, kE2, kF1, kF2;
     top2_duals(mE, kE1, kE2);
     top2_duals(mF, kF1, kF2);
@@ -653,7 +578,7 @@ __device__ __noinline__ bool fp32_sat_reject(const float4 X[3][2], const float4 
         for (int k = 0; k < 6; ++k) m[k] = ax < 2 ? mE[k] : mF[k];
         float w[4];
         dual_dir(m, ax == 0 ? kE1 : (ax == 1 ? kE2 : (ax == 2 ? kF1 : kF2)), w);
-        if (separated(w, e1, e2, r, s1, s3, delta)) return true;
+        if (separated(w, e1, e2, r, s1, s3, tp, reach)) return true;
     }
     return false;
 }
