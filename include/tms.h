@@ -597,6 +597,26 @@ tms_status tms_last_stage_ms(void *stream, float *ms, int cap, int *n);
  * every stream.  Synchronises the plans' work first. */
 tms_status tms_release_workspace(void *stream);
 
+/* Read-back of the patch frames of the last search on `stream` (patch level,
+ * mixed precision, narrow_filter 1), so that tests can check their bounds
+ * against the FP64 vertices.  side: 0 = mesh A, 1 = mesh B of pair 0.
+ * host_out: host, room for cap floats; receives, per patch in slot order
+ * (patch row * npi + patch column), 28 floats: c[4], e_0..e_3 (4 each),
+ * h_0..h_3, rho, L, n_2, n_3 -- an FP32 point c, four FP32 axes and bounds
+ * that hold for every FP64 vertex V of the patch:
+ *   |e_k . (V - c)| <= h_k,  max_i |r_i| <= rho with
+ *   r = (V - c) - sum_k (e_k . (V - c)) e_k,  max_i |V_i| <= L,
+ *   n_2 >= |e_2|_1,  n_3 >= |e_3|_1
+ * (h and rho are +inf on a patch without a usable frame).  The patch-pair
+ * test drops a pair when along e_2 or e_3 of either patch the two patches'
+ * intervals are further apart than the FP64 solve's backward error and the
+ * hit tolerance allow (no triangle pair in them can be an FP64 hit).
+ * *n_patches, *npi (host): patches and patches per quad row.  Synchronises
+ * the stream.  TMS_ERR_STATE when no such search was made on `stream`;
+ * TMS_ERR_CAPACITY (with the counts set) when cap < 28 * patches. */
+tms_status tms_last_patch_frames(void *stream, int side, float *host_out, long long cap,
+                                 long long *n_patches, int *npi);
+
 /* Measures this GPU's FP64 fused-multiply-add throughput (TFLOP/s) with a
  * short dependent-chain kernel on `stream`; the denominator of the narrow
  * phase's FP64 utilisation.  Allocates a small buffer; synchronises. */

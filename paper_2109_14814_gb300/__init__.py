@@ -15,7 +15,8 @@ from ._binding import (CONTINUE_STATUS, HIT_BYTES, REFINE_STATUS, STAGES, Contin
                        Refined, RefineParams, SurfacePair, continue_branches, refine, refine_params,
                        surface_pair, TMS_ERR_ARG, TMS_ERR_CAPACITY, TMS_ERR_CUDA,
                        TMS_ERR_STATE, TMS_ERR_TIMEOUT, TMS_OK, HitPoint, Hits, Mesh, Params, Stats,
-                       TmsError, autotune, backward, last_error, last_stage_ms, last_stats, lib, params,
+                       TmsError, autotune, backward, last_error, last_patch_frames, last_stage_ms, last_stats,
+                       lib, params,
                        probe_fp64_tflops, release_workspace, search, search_batched, search_host,
                        search_noalloc, status_str, version)
 
@@ -24,6 +25,7 @@ __all__ = ["CONTINUE_STATUS", "HIT_BYTES", "REFINE_STATUS", "STAGES", "ContinueP
            "Refined", "RefineParams", "SurfacePair", "continue_branches", "refine", "refine_params",
            "surface_pair", "TMS_ERR_ARG", "TMS_ERR_CAPACITY", "TMS_ERR_CUDA",
            "TMS_ERR_STATE", "TMS_ERR_TIMEOUT", "TMS_OK", "HitPoint", "Hits", "Mesh", "Params",
-           "Stats", "TmsError", "autotune", "backward", "last_error", "last_stage_ms", "last_stats", "lib",
+           "Stats", "TmsError", "autotune", "backward", "last_error", "last_patch_frames", "last_stage_ms",
+           "last_stats", "lib",
            "params", "probe_fp64_tflops", "release_workspace", "search", "search_batched",
            "search_host", "search_noalloc", "status_str", "version"]

@@ -158,6 +158,8 @@ def lib():
     L.tms_last_stage_ms.restype = I
     L.tms_release_workspace.argtypes = [P]
     L.tms_release_workspace.restype = I
+    L.tms_last_patch_frames.argtypes = [P, I, _c.POINTER(_c.c_float), LL, _c.POINTER(LL), _c.POINTER(I)]
+    L.tms_last_patch_frames.restype = I
     L.tms_status_str.argtypes = [I]
     L.tms_status_str.restype = _c.c_char_p
     L.tms_version.argtypes = []
@@ -492,6 +494,24 @@ def last_stage_ms(stream=None) -> dict:
     if rc != TMS_OK:
         raise TmsError(rc, "tms_last_stage_ms")
     return {STAGES[i]: float(buf[i]) for i in range(min(n.value, len(STAGES)))}
+
+
+def last_patch_frames(side: int = 0, stream=None):
+    """The patch frames of the last search on `stream` (mesh A for side 0, B
+    for side 1) as a float32 array (patch rows, patches per row, 28): c, e_0..e_3,
+    h_0..h_3, rho, L, n_2, n_3 (tms_last_patch_frames)."""
+    import numpy as np
+    n = _c.c_longlong(0)
+    npi = _c.c_int(0)
+    rc = lib().tms_last_patch_frames(_stream(stream), side, None, 0, _c.byref(n), _c.byref(npi))
+    if rc not in (TMS_OK, TMS_ERR_CAPACITY):
+        raise TmsError(rc, "tms_last_patch_frames")
+    out = np.zeros((max(n.value, 1), 28), dtype=np.float32)
+    rc = lib().tms_last_patch_frames(_stream(stream), side, out.ctypes.data_as(_c.POINTER(_c.c_float)),
+                                     out.size, _c.byref(n), _c.byref(npi))
+    if rc != TMS_OK:
+        raise TmsError(rc, "tms_last_patch_frames")
+    return out[:n.value].reshape(-1, max(npi.value, 1), 28)
 
 
 def surface_pair(sp, alpha_u=None, alpha_s=None) -> SurfacePair:

@@ -80,15 +80,20 @@ struct Plan {
     // mesh tables
     int n_meshes = 0;
     MeshDev *d_meshes = nullptr;
+    std::vector<MeshDev> h_meshes;    // host copy of the mesh table
     // patch level: the patch views (one "face" per patch, its box in pbox),
     // which the cell passes and the grid emission read instead of the meshes
     bool patch = false;
+    // patch frames (mixed precision with the FP32 filters): the patch-pair
+    // test drops pairs that no triangle pair in them can make an FP64 hit
+    bool frames = false;
     MeshDev *d_pmeshes = nullptr;
     // per-pair cell multipliers (size classes tuned by tms_autotune), or empty
     std::vector<float> cm_pair;
     float *d_cm_pair = nullptr;
     unsigned char *pbox = nullptr;    // patch boxes of all meshes
     unsigned char *qbox = nullptr;    // their quarter boxes
+    float4 *pframe = nullptr;         // their frames (kFrameF4 float4 per patch)
     Cand *ppairs = nullptr;
     Cand *psurv = nullptr;           // patch pairs left by the quarter test
     unsigned long long ppair_cap = 0;
@@ -158,7 +163,7 @@ struct Plan {
         if (st) cudaStreamSynchronize(st);
         free_scratch();
         void *ptrs[] = {d_meshes, d_pairs, d_pass_all, d_pass_A, d_pass_B, d_bounds,
-                        d_ctr, partials, split, fbox, d_pmeshes, pbox, qbox, d_cm_pair};
+                        d_ctr, partials, split, fbox, d_pmeshes, pbox, qbox, pframe, d_cm_pair};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         if (h_ctr) cudaFreeHost(h_ctr);
@@ -259,9 +264,11 @@ struct Plan {
         fa.entries = d_pass_all; fa.n_entries = n_pass_all; fa.total_tiles = tiles_all;
         fa.mode = MODE_BOUNDS;
         fa.patch = patch ? 1 : 0;
+        fa.frames = frames ? 1 : 0;
         launch_face_pass(fa, prec, fl, block, s);
         // the cell passes and the grid emission work on the patches (patch level)
         fa.patch = 0;
+        fa.frames = 0;
         if (patch) fa.meshes = d_pmeshes;
         mark(2, s);
         launch_grid_params(d_bounds, d_pairs, nPairs, d_grids, p.cell_mult, s, d_cm_pair);
@@ -322,6 +329,8 @@ struct Plan {
             pa.pairs = d_pairs;
             pa.ctr = d_ctr; pa.ent_cap = ent_cap; pa.cand = cand; pa.cand_cap = cand_cap;
             pa.moller = p.moller;
+            pa.frames = frames ? 1 : 0;
+            pa.tau = p.tau;
             launch_patch_quads(pa, prec, grid / 2, s);
             kernels += 2;
         }
@@ -478,6 +487,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     P->prm.tile_rows = rows;
     P->patch = prm.patch == 1 && prm.face_level == 1;
     const bool patch = P->patch;
+    P->frames = patch && prm.precision == 1 && prm.narrow_filter == 1;
 
     std::vector<MeshDev> meshes;
     std::vector<int2> pairs;
@@ -510,8 +520,8 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
     // FP32 split vertex copies (32 bytes per view vertex) and face boxes (32 or
     // 64 bytes per face slot), written by the bounds pass
     const unsigned long long box_bytes = prm.precision == 1 ? 32 : 64;
-    std::vector<unsigned long long> fbox_off, pbox_off;
-    unsigned long long fbox_total = 0, pbox_total = 0;
+    std::vector<unsigned long long> fbox_off, pbox_off, pframe_off;
+    unsigned long long fbox_total = 0, pbox_total = 0, pframe_total = 0;
     for (auto &md : meshes) {
         P->split_off.push_back(P->split_total);
         P->split_total += 2ULL * (unsigned long long)md.N * (unsigned long long)md.M;
@@ -522,8 +532,11 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
         md.pmagic = recip64((unsigned long long)md.npi);
         md.pbox = nullptr;
         md.qbox = nullptr;
+        md.pframe = nullptr;
         pbox_off.push_back(pbox_total);
         pbox_total += ((unsigned long long)md.npi * md.npk * box_bytes + 255) / 256 * 256;
+        pframe_off.push_back(pframe_total);
+        pframe_total += ((unsigned long long)md.npi * md.npk * kFrameF4 + 15) / 16 * 16;
     }
     std::vector<MeshDev> pmeshes;
     {
@@ -531,6 +544,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
         if (se == cudaSuccess) se = dalloc(&P->fbox, fbox_total);
         if (se == cudaSuccess && patch) se = dalloc(&P->pbox, pbox_total);
         if (se == cudaSuccess && patch) se = dalloc(&P->qbox, 4 * pbox_total);
+        if (se == cudaSuccess && P->frames) se = dalloc(&P->pframe, pframe_total);
         if (se != cudaSuccess) { g_err = cudaGetErrorString(se); delete P; return TMS_ERR_CUDA; }
         for (size_t i = 0; i < meshes.size(); ++i) {
             meshes[i].split = P->split + P->split_off[i];
@@ -538,6 +552,7 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
             if (patch) {
                 meshes[i].pbox = P->pbox + pbox_off[i];
                 meshes[i].qbox = P->qbox + 4 * pbox_off[i];
+                if (P->frames) meshes[i].pframe = P->pframe + pframe_off[i];
             }
         }
         // a patch view is a mesh of npi x npk quad-like slots, all valid
@@ -550,10 +565,12 @@ tms_status make_plan(const tms_mesh *A, const tms_mesh *B, int nPairs, const tms
             v.nqk = md.npk;
             v.fbox = md.pbox;
             v.split = nullptr;
+            v.pframe = nullptr;
             pmeshes.push_back(v);
         }
     }
     P->n_meshes = (int)meshes.size();
+    P->h_meshes = meshes;
     P->n_pass_all = (int)pall.size();
     P->n_pass_A = (int)pa.size();
     P->n_pass_B = (int)pb.size();
@@ -1092,6 +1109,26 @@ tms_status tms_last_stage_ms(void *stream, float *ms, int cap, int *n) {
     if (it == g_stage_ms.end()) return TMS_ERR_STATE;
     if (n) *n = (int)it->second.size();
     for (int i = 0; i < cap && i < (int)it->second.size(); ++i) ms[i] = it->second[i];
+    return TMS_OK;
+}
+
+tms_status tms_last_patch_frames(void *stream, int side, float *host_out, long long cap,
+                                 long long *n_patches, int *npi) {
+    if (side != 0 && side != 1) return TMS_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Plan *P = nullptr;
+    for (Plan *Q : g_plans)
+        if (Q->user == (cudaStream_t)stream && (!P || Q->last_use > P->last_use)) P = Q;
+    if (!P || !P->frames || (int)P->h_meshes.size() < 2) return TMS_ERR_STATE;
+    const MeshDev &md = P->h_meshes[side];
+    const long long n = (long long)md.npi * md.npk;
+    if (n_patches) *n_patches = n;
+    if (npi) *npi = md.npi;
+    if (cap < 4LL * kFrameF4 * n) return TMS_ERR_CAPACITY;
+    if (!host_out && n > 0) return TMS_ERR_ARG;
+    TMS_CK(cudaStreamSynchronize(P->user));
+    if (n > 0)
+        TMS_CK(cudaMemcpy(host_out, md.pframe, (size_t)n * kFrameF4 * sizeof(float4), cudaMemcpyDeviceToHost));
     return TMS_OK;
 }
 

@@ -78,6 +78,9 @@ struct MeshDev {
                                 // is __umul64hi(id, pmagic) (exact for 32-bit ids)
     unsigned long long nmagic;  // ceil(2^64 / N): a quad id's row is
                                 // __umul64hi(q, nmagic) (N >= 2, exact for 32-bit ids)
+    float4 *pframe;       // plan scratch (patch level, mixed precision, FP32
+                          // filters on): per patch its frame, kFrameF4 float4
+                          // at slot * kFrameF4 (layout at kFrameF4); else NULL
 };
 
 // (i, k) of quad q = k N + i, by the reciprocal of N (no integer division)
@@ -89,6 +92,22 @@ __host__ __device__ inline unsigned long long recip64(unsigned long long d) {
 // along theta by kPatchK quad rows -- 32 quads, one per lane of a warp.
 constexpr int kPatchI = 8;
 constexpr int kPatchK = 4;
+
+// A patch frame, written by the bounds pass and read by the patch-pair test:
+// an FP32 point c, four FP32 axes e_0..e_3 (e_0, e_1 along the patch's two
+// parameter directions, e_2, e_3 completing them) and bounds rigorous for the
+// patch's FP64 vertices V:
+//   h_k >= max_V |e_k . (V - c)|,
+//   rho >= max_V max_i |r_i| + 4.0001 u max|e| sum_k h_k,
+//   r = (V - c) - sum_k (e_k . (V - c)) e_k
+// (r is what the frame does not reproduce: rounding-small when the axes are
+// orthonormal, and no such assumption is made), L >= max |V_i|, and n_k >=
+// |e_k|_1 for the two completing axes.  For any direction w then
+//   |w . (V - c)| <= sum_k |w . e_k| h_k + |w|_1 rho
+// with w . e_k rounded in FP32 (the second term of rho covers that rounding),
+// and |e_k . (V - c)| <= h_k.  Layout: c, e_0, e_1, e_2, e_3, (h_0..h_3),
+// (rho, L, n_2, n_3).
+constexpr int kFrameF4 = 7;
 
 struct PassEntry {        // one mesh processed by a face pass
     int mesh;             // index into the mesh table
@@ -176,6 +195,26 @@ __host__ __device__ inline double ord_dec(unsigned long long u) {
     return v;
 #endif
 }
+
+// How far apart two triangles can be and still make an FP64 hit.  The FP64
+// solve (Gaussian elimination with partial pivoting, reciprocal pivots, on the
+// 4 x 4 system of Eq. (precise)) returns z with (A + E) z = r + e, where
+// |E_ij| <= gamma_30 (|L||U|)_ij + u64 |A_ij| <= 1.1e-13 max|A| (multipliers <= 1,
+// growth <= 2^3, the rounding of A's entries from the vertices included) and
+// |e| <= u64 |r|.  A hit has weights >= -tau' (tau' = tau plus the rounding of the
+// margin, 1e-15 at most), so |z| <= 1 + 2 tau' and the points x2 + a e1 + b e2
+// and y2 + c f1 + d f2 of the two triangles, widened to weights >= -tau', differ
+// by A z - r = e - E z: at most fp64_reach(max|A|, |r|) in every coordinate.
+// A separating-axis test that proves the widened triangles further apart than
+// that therefore proves that the FP64 solve reports no hit -- whatever the
+// system's condition.
+__device__ __forceinline__ float fp64_reach(float amax, float rmax) {
+    return (5e-13f * amax + 1.2e-16f * rmax) * 1.01f + 1e-37f;
+}
+
+// along w, a triangle's projection widened to weights >= -tau' grows by at most
+// 3 tau' times its length on each side; tp = 3 tau' from tau (FP32, rounded up)
+__device__ __forceinline__ float widen3(float tau) { return 3.0f * tau * 1.001f + 3e-15f; }
 
 // 64-bit mixer (MurmurHash3 finaliser) for hashing (pair, cell) into a bitmap.
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -390,6 +429,8 @@ struct FacePassArgs {
     unsigned long long ent_cap;
     int patch;                     // bounds pass: also the patch boxes, and the
                                    // widest patch (not face) extent for the grid
+    int frames;                    // bounds pass, patch level, mixed precision:
+                                   // also the patch frames (MeshDev::pframe)
 };
 
 void launch_face_pass(const FacePassArgs &a, int precision, int face_level, int block,
@@ -498,6 +539,9 @@ struct PatchArgs {
     Cand *cand;
     unsigned long long cand_cap;
     int moller;
+    int frames;                    // 1: patch pairs whose frames prove that no
+                                   // triangle pair in them is an FP64 hit are dropped
+    double tau;                    // the hit test's margin tolerance
 };
 void launch_patch_quads(const PatchArgs &a, int precision, int sms, cudaStream_t st);
 

@@ -321,6 +321,184 @@ __device__ __forceinline__ int find_entry(const FacePassArgs &a, long long x, bo
 }
 
 // ---------------------------------------------------------------------------
+// patch frames (mixed precision; the record and its bounds are described at
+// kFrameF4).  The axes need not be orthonormal for the bounds to hold: the
+// remainder r absorbs whatever the rounded axes fail to reproduce, and is
+// bounded through the axes' Gram matrix.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dot4f(const float a[4], const float b[4]) {
+    return fmaf(a[3], b[3], fmaf(a[2], b[2], fmaf(a[1], b[1], a[0] * b[0])));
+}
+__device__ __forceinline__ float det3(float a0, float a1, float a2, float b0, float b1, float b2,
+                                      float c0, float c1, float c2) {
+    return a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0);
+}
+// the vector orthogonal to a, b and c in R^4 (cofactor expansion of the
+// 4 x 4 determinant with rows (x, a, b, c))
+__device__ __forceinline__ void cross4(const float a[4], const float b[4], const float c[4], float x[4]) {
+    x[0] = det3(a[1], a[2], a[3], b[1], b[2], b[3], c[1], c[2], c[3]);
+    x[1] = -det3(a[0], a[2], a[3], b[0], b[2], b[3], c[0], c[2], c[3]);
+    x[2] = det3(a[0], a[1], a[3], b[0], b[1], b[3], c[0], c[1], c[3]);
+    x[3] = -det3(a[0], a[1], a[2], b[0], b[1], b[2], c[0], c[1], c[2]);
+}
+// non-negative floats (and NaN, above +inf) compare as their bit patterns:
+// an integer maximum of |x| keeps a NaN, which fmaxf would drop
+__device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+
+// The frame of a patch, computed by its kPatchI lanes at the close of its patch
+// row and written as kFrameF4 float4 by its first lane.  Every lane of the
+// warp calls it (the shuffles are uniform).  pr0: the patch's first vertex
+// row in the tile's vertex array sv; rq: its quad rows; pb: its box (held by
+// every lane of the patch).
+// Axes: e_0, e_1 from the patch's two parameter directions (sums of opposite
+// edges, one Gram-Schmidt step), e_2 orthogonal to e_0, e_1 and the coordinate
+// axis farthest from their span, e_3 orthogonal to e_0, e_1, e_2.  A patch
+// whose parameter directions are zero or unbounded gets a frame that
+// separates nothing.
+// Bounds, with u = 2^-24, the exact vertex V in its FP32 bounds [lo, hi] and
+// d = V - c:
+//   |d|_inf <= D = max_i max(pb.hi_i - c_i, c_i - pb.lo_i)   (all V in pb)
+//   hi_i - lo_i <= 2^-23 L + 2^-149                           (adjacent floats)
+//   d~ = fl(hi - c): |d_i - d~_i| <= (hi_i - lo_i) + u |d~_i|, |d~_i| <= D (1 + u)
+//   a~_k = fl(e_k . d~) (4 FMAs, error <= gamma_4 sum_i |e_ki||d~_i|, gamma_4 <
+//   4.0001 u), so |e_k . d - a~_k| <= n_k nu, nu = 2^-23 L + 5.001 u D (+ 2^-149)
+//   and h_k = max |a~_k| + n_k nu (n_k >= |e_k|_1);
+//   r = (I - E^T E) d, so |r|_inf <= g D with g >= ||I - E^T E||_inf, from
+//   G~_ij = fl(delta_ij - sum_k e_ki e_kj) (4 FMAs, error <= gamma_4 (1 + 4 e_max^2)).
+// Sums and products of non-negative terms are rounded up by a factor 1.0001
+// (a handful of roundings of 2^-24 each); absolute terms cover underflow.
+__device__ __forceinline__ void patch_frame(const Vtx<1> *sv, int W, int t, int cols_q, int pr0, int rq,
+                                            const BoxT<1> &pb, float4 *out, uint32_t p, bool patch_lane) {
+    const float u = 5.9604645e-08f;
+    const float inf = __int_as_float(0x7f800000);
+    const int p0 = t & ~(kPatchI - 1), l = t - p0;
+    const int cq = patch_lane ? min(kPatchI, cols_q - p0) : 0;    // the patch's quad columns
+    const int pr1 = pr0 + rq;
+    float c[4], L = 0.0f, D = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        c[i] = 0.5f * (pb.lo[i] + pb.hi[i]);
+        L = fmaxf(L, fmaxf(fabsf(pb.lo[i]), fabsf(pb.hi[i])));
+        D = fmaxf(D, fmaxf(pb.hi[i] - c[i], c[i] - pb.lo[i]));
+    }
+    D *= 1.0001f;
+    float t1[4] = {0.0f, 0.0f, 0.0f, 0.0f}, t2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (patch_lane) {
+        const float4 v00 = *reinterpret_cast<const float4 *>(sv[pr0 * W + p0].hi);
+        const float4 v01 = *reinterpret_cast<const float4 *>(sv[pr0 * W + p0 + cq].hi);
+        const float4 v10 = *reinterpret_cast<const float4 *>(sv[pr1 * W + p0].hi);
+        const float4 v11 = *reinterpret_cast<const float4 *>(sv[pr1 * W + p0 + cq].hi);
+        t1[0] = (v01.x - v00.x) + (v11.x - v10.x); t2[0] = (v10.x - v00.x) + (v11.x - v01.x);
+        t1[1] = (v01.y - v00.y) + (v11.y - v10.y); t2[1] = (v10.y - v00.y) + (v11.y - v01.y);
+        t1[2] = (v01.z - v00.z) + (v11.z - v10.z); t2[2] = (v10.z - v00.z) + (v11.z - v01.z);
+        t1[3] = (v01.w - v00.w) + (v11.w - v10.w); t2[3] = (v10.w - v00.w) + (v11.w - v01.w);
+    }
+    float E[4][4];
+    const float n1 = dot4f(t1, t1);
+    const float s1 = rsqrtf(n1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) E[0][i] = t1[i] * s1;
+    const float pj = dot4f(t2, E[0]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t2[i] = fmaf(-pj, E[0][i], t2[i]);
+    const float n2 = dot4f(t2, t2);
+    const float s2 = rsqrtf(n2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) E[1][i] = t2[i] * s2;
+    // zero or unbounded parameter directions: no frame
+    bool bad = !(n1 > 1e-30f && n1 < 1e30f && n2 > 1e-30f && n2 < 1e30f);
+    {
+        // e_2 from the coordinate axis k farthest from span(e_0, e_1): the one
+        // with the least e_0k^2 + e_1k^2 (|cross4(e_0, e_1, axis_k)|^2 is one minus
+        // that for orthonormal e_0, e_1)
+        int kb = 0;
+        float best = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float sk = fmaf(E[0][k], E[0][k], E[1][k] * E[1][k]);
+            if (sk < best) { best = sk; kb = k; }
+        }
+        float ax[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ax[i] = i == kb ? 1.0f : 0.0f;
+        float x[4];
+        cross4(E[0], E[1], ax, x);
+        const float s3 = rsqrtf(dot4f(x, x));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) E[2][i] = x[i] * s3;
+        cross4(E[0], E[1], E[2], x);
+        const float s4 = rsqrtf(dot4f(x, x));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) E[3][i] = x[i] * s4;
+    }
+    // the vertices: lane l takes column p0 + l of the patch (rows pr0..pr1), and
+    // lanes 0..rq the closing column p0 + cq, one vertex each; the integer
+    // maximum keeps NaN
+    unsigned am[4] = {0u, 0u, 0u, 0u};
+    auto vertex = [&](const Vtx<1> &v) {
+        const float4 hv = *reinterpret_cast<const float4 *>(v.hi);
+        const float d[4] = {hv.x - c[0], hv.y - c[1], hv.z - c[2], hv.w - c[3]};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) am[k] = max(am[k], abs_bits(dot4f(E[k], d)));
+    };
+    if (l < cq)
+        for (int rr = pr0; rr <= pr1; ++rr) vertex(sv[rr * W + t]);
+    if (cq > 0 && l <= rq) vertex(sv[(pr0 + l) * W + p0 + cq]);
+#pragma unroll
+    for (int off = 1; off < kPatchI; off <<= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) am[k] = max(am[k], __shfl_xor_sync(0xffffffffu, am[k], off));
+    // per-patch terms (every lane alike)
+    float nk[4], emax = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        nk[k] = (fabsf(E[k][0]) + fabsf(E[k][1]) + fabsf(E[k][2]) + fabsf(E[k][3])) * 1.0001f;
+        emax = fmaxf(emax, fmaxf(fmaxf(fabsf(E[k][0]), fabsf(E[k][1])), fmaxf(fabsf(E[k][2]), fabsf(E[k][3]))));
+    }
+    // |I - E^T E| (symmetric: ten entries)
+    float G[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i; j < 4; ++j) {
+            float gij = i == j ? 1.0f : 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gij = fmaf(-E[k][i], E[k][j], gij);
+            G[i][j] = G[j][i] = fabsf(gij);
+        }
+    float g = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g = fmaxf(g, (G[i][0] + G[i][1]) + (G[i][2] + G[i][3]));
+    g = fmaf((4.0f * 4.0001f) * u, fmaf(4.0f * emax, emax, 1.0f), g) * 1.0001f;
+    const float nu = fmaf(5.001f * u, D, 1.1921e-7f * L) * 1.0001f + 1e-30f;
+    float h[4], hs = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        h[k] = fmaf(nk[k], nu, __uint_as_float(am[k])) * 1.0001f + 1e-36f;
+        hs += h[k];
+        bad |= !(h[k] < inf);
+    }
+    // plus the rounding of fl(w . e_k) in the pair test: gamma_4 |w|_1 e_max
+    // per unit of h_k
+    float rho = fmaf((4.0001f * u) * emax, hs * 1.0001f, g * D * 1.0001f) * 1.0001f + 1e-36f;
+    bad |= !(rho < inf) || !(fabsf(E[2][0] + E[2][1] + E[2][2] + E[2][3] + E[3][0] + E[3][1] + E[3][2] + E[3][3]) < inf);
+    if (bad) {
+        h[0] = h[1] = h[2] = h[3] = inf;
+        rho = inf;
+    }
+    if (patch_lane && l == 0) {
+        float4 *o = out + (size_t)p * kFrameF4;
+        o[0] = make_float4(c[0], c[1], c[2], c[3]);
+        o[1] = make_float4(E[0][0], E[0][1], E[0][2], E[0][3]);
+        o[2] = make_float4(E[1][0], E[1][1], E[1][2], E[1][3]);
+        o[3] = make_float4(E[2][0], E[2][1], E[2][2], E[2][3]);
+        o[4] = make_float4(E[3][0], E[3][1], E[3][2], E[3][3]);
+        o[5] = make_float4(h[0], h[1], h[2], h[3]);
+        o[6] = make_float4(rho, L, nk[2], nk[3]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // bounds pass
 // ---------------------------------------------------------------------------
 template <int PREC, int FACE, int TK>
@@ -400,10 +578,12 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
         // the row loop and its shuffles are uniform).  The widest extent the
         // grid needs is then the widest patch's.
         // this column's boxes over the upper and lower halves of the patch row
-        BoxT<PREC> prev, ptop, pbot;
+        BoxT<PREC> prev, ptop, pbot, pb0, pb1;   // pb0, pb1: the boxes of the tile's patch rows
         box_empty(prev);
         box_empty(ptop);
         box_empty(pbot);
+        box_empty(pb0);
+        box_empty(pb1);
         // the patch exists when its first column is in the tile
         const bool patch_lane = (t & ~(kPatchI - 1)) < cols_q;
         if (col_valid) {
@@ -446,8 +626,22 @@ __global__ void __launch_bounds__(256) k_bounds_pass(FacePassArgs a) {
                     write_box<PREC>(m.pbox, p, pb);
                     acc.add_width(pb);
                 }
+                if (r < kPatchK) pb0 = pb;
+                else pb1 = pb;
                 box_empty(ptop);
                 box_empty(pbot);
+            }
+        }
+        // the frames of the tile's patches, after its rows (fewer registers live
+        // than at the close of each patch row)
+        if constexpr (PREC == 1) {
+            if (a.frames) {
+                for (int pr = 0; pr * kPatchK < rows_q; ++pr) {
+                    const BoxT<1> pbx = pr == 0 ? pb0 : pb1;
+                    const uint32_t p = (uint32_t)(kq0 / kPatchK + pr) * (uint32_t)m.npi + (uint32_t)(i / kPatchI);
+                    patch_frame(sv, W, t, cols_q, pr * kPatchK, min(kPatchK, rows_q - pr * kPatchK), pbx,
+                                m.pframe, p, patch_lane);
+                }
             }
         }
     } else if (FACE == 1 && col_valid) {

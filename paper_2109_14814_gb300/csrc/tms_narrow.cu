@@ -446,25 +446,8 @@ __device__ __forceinline__ float dot4(const float w[4], const SplitVec &v) {
     return fmaf(w[3], v.v[3], fmaf(w[2], v.v[2], fmaf(w[1], v.v[1], w[0] * v.v[0])));
 }
 
-// How far apart two triangles can be and still make an FP64 hit.  The FP64
-// solve (Gaussian elimination with partial pivoting, reciprocal pivots, on the
-// 4 x 4 system of Eq. (precise)) returns z with (A + E) z = r + e, where
-// |E_ij| <= gamma_30 (|L||U|)_ij + u64 |A_ij| <= 1.1e-13 max|A| (multipliers <= 1,
-// growth <= 2^3, the rounding of A's entries from the vertices included) and
-// |e| <= u64 |r|.  A hit has weights >= -tau' (tau' = tau plus the rounding of the
-// margin, 1e-15 at most), so |z| <= 1 + 2 tau' and the points x2 + a e1 + b e2
-// and y2 + c f1 + d f2 of the two triangles, widened to weights >= -tau', differ
-// by A z - r = e - E z: at most fp64_reach(max|A|, |r|) in every coordinate.
-// A separating-axis test that proves the widened triangles further apart than
-// that therefore proves that the FP64 solve reports no hit -- whatever the
-// system's condition.
-__device__ __forceinline__ float fp64_reach(float amax, float rmax) {
-    return (5e-13f * amax + 1.2e-16f * rmax) * 1.01f + 1e-37f;
-}
-
-// along w, a triangle's projection widened to weights >= -tau' grows by at most
-// 3 tau' times its length on each side; tp = 3 tau' from tau (FP32, rounded up)
-__device__ __forceinline__ float widen3(float tau) { return 3.0f * tau * 1.001f + 3e-15f; }
+// fp64_reach and widen3 (the FP64 solve's backward error and the widening of
+// a triangle's projection) are in tms_common.cuh: the patch-pair test uses them too.
 
 // the gap test along w for X = {0, e1, e2} and Y = {r, s1, s3} (all relative to x2):
 // the widened projections apart by more than |w|_1 reach

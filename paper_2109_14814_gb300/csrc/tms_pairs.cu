@@ -439,6 +439,77 @@ __device__ __forceinline__ void patch_rc(uint32_t patch, uint32_t npi, unsigned 
     pi = patch - pk * npi;
 }
 
+// Patch frames (the record at kFrameF4).  For a direction w the points of a
+// patch lie within S(w) of w . c along w, where S(e_m) = h_m along the patch's
+// own axis e_m and S(w) = sum_k |fl(w . e_k)| h_k + |w|_1 rho for any other w.
+// A triangle of the patch has its vertices among the patch's, so its
+// projection lies in that interval, and widened to weights >= -tau' it lies in
+// (1 + 6 tau') S(w) of w . c (its length is at most 2 S(w); see widen3).  Two
+// patches X, Y are dropped when along some w
+//   |w . (c_X - c_Y)| > (1 + 6 tau') (S_X(w) + S_Y(w)) + |w|_1 reach,
+// reach the FP64 solve's backward error (fp64_reach) for any triangle pair of
+// the two patches: every entry of the system is an edge, |A_ij| <= 2 max(L_X,
+// L_Y), and |r| <= L_X + L_Y, so reach <= 1.011e-12 (L_X + L_Y).  Then no
+// triangle pair of the patch pair is an FP64 hit, as in the triangle-level
+// separating-axis test.  The left side is computed as
+// fl(w . fl(c_X - c_Y)), within 5.001 u sum_i |w_i||fl(c_X - c_Y)_i| of the
+// exact value; every bound on the right is rounded up (factor 1.0001).
+// Directions: the two completing axes (approximate normals) of each patch.
+struct PFrame {
+    float c[4], e[4][4], h[4];
+    float rho, L, n2, n3;
+};
+__device__ __forceinline__ void load_frame(const float4 *f, uint32_t patch, PFrame &F) {
+    const float4 *q = f + (size_t)patch * kFrameF4;
+    const float4 x0 = __ldg(q), x1 = __ldg(q + 1), x2 = __ldg(q + 2), x3 = __ldg(q + 3);
+    const float4 x4 = __ldg(q + 4), x5 = __ldg(q + 5), x6 = __ldg(q + 6);
+    F.c[0] = x0.x; F.c[1] = x0.y; F.c[2] = x0.z; F.c[3] = x0.w;
+    F.e[0][0] = x1.x; F.e[0][1] = x1.y; F.e[0][2] = x1.z; F.e[0][3] = x1.w;
+    F.e[1][0] = x2.x; F.e[1][1] = x2.y; F.e[1][2] = x2.z; F.e[1][3] = x2.w;
+    F.e[2][0] = x3.x; F.e[2][1] = x3.y; F.e[2][2] = x3.z; F.e[2][3] = x3.w;
+    F.e[3][0] = x4.x; F.e[3][1] = x4.y; F.e[3][2] = x4.z; F.e[3][3] = x4.w;
+    F.h[0] = x5.x; F.h[1] = x5.y; F.h[2] = x5.z; F.h[3] = x5.w;
+    F.rho = x6.x; F.L = x6.y; F.n2 = x6.z; F.n3 = x6.w;
+}
+__device__ __forceinline__ float fdot4(const float a[4], const float b[4]) {
+    return fmaf(a[3], b[3], fmaf(a[2], b[2], fmaf(a[1], b[1], a[0] * b[0])));
+}
+// the gap test along w (|w|_1 <= nw) for a patch whose own axis it is (half
+// width hx) against patch Y, given pw[k] = fl(w . e_k^Y)
+__device__ __forceinline__ bool frame_gap(const float w[4], float nw, float hx, const PFrame &Y,
+                                          const float pw[4], const float dc[4], float tw, float reach) {
+    const float g = fabsf(fdot4(w, dc));
+    const float q = fmaf(fabsf(w[3]), fabsf(dc[3]),
+                         fmaf(fabsf(w[2]), fabsf(dc[2]), fmaf(fabsf(w[1]), fabsf(dc[1]), fabsf(w[0]) * fabsf(dc[0]))));
+    float sy = nw * Y.rho;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sy = fmaf(fabsf(pw[k]), Y.h[k], sy);
+    const float need = fmaf(tw, hx + sy, nw * reach);
+    return g > fmaf(3.0e-7f, q, need) * 1.0001f;
+}
+// true when the frames prove that no triangle pair of the two patches is an
+// FP64 hit; tw = 1 + 6 tau' rounded up
+__device__ __forceinline__ bool frames_separated(const PFrame &X, const PFrame &Y, float tw) {
+    float dc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dc[i] = X.c[i] - Y.c[i];
+    const float reach = 1.03e-12f * (X.L + Y.L) + 1e-37f;
+    // p[m][k] = fl(e_m^X . e_k^Y) for X's normals; q[m][k] = fl(e_m^Y . e_k^X)
+    // for Y's normals (its k = 2, 3 entries are p's)
+    float p2[4], p3[4], q2[4], q3[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        p2[k] = fdot4(X.e[2], Y.e[k]);
+        p3[k] = fdot4(X.e[3], Y.e[k]);
+    }
+    q2[0] = fdot4(Y.e[2], X.e[0]); q2[1] = fdot4(Y.e[2], X.e[1]); q2[2] = p2[2]; q2[3] = p3[2];
+    q3[0] = fdot4(Y.e[3], X.e[0]); q3[1] = fdot4(Y.e[3], X.e[1]); q3[2] = p2[3]; q3[3] = p3[3];
+    return frame_gap(X.e[2], X.n2, X.h[2], Y, p2, dc, tw, reach) ||
+           frame_gap(X.e[3], X.n3, X.h[3], Y, p3, dc, tw, reach) ||
+           frame_gap(Y.e[2], Y.n2, Y.h[2], X, q2, dc, tw, reach) ||
+           frame_gap(Y.e[3], Y.n3, Y.h[3], X, q3, dc, tw, reach);
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kQuarterBlock) k_patch_quarters(PatchArgs a) {
     // nothing to do after an overflow of the patch-level grid (the host retries)
@@ -447,6 +518,9 @@ __global__ void __launch_bounds__(kQuarterBlock) k_patch_quarters(PatchArgs a) {
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     uint32_t cached_pair = 0xFFFFFFFFu;
     const void *qbA = nullptr, *qbB = nullptr;
+    const float4 *pfA = nullptr, *pfB = nullptr;
+    // 1 + 6 tau', tau' = tau + 1e-15 (the margin's rounding), rounded up
+    const float tw = 1.0f + 2.0f * widen3(__double2float_ru(a.tau));
     for (unsigned long long j0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u);
          j0 < n; j0 += stride) {
         const unsigned long long j = j0 + (threadIdx.x & 31);
@@ -458,6 +532,8 @@ __global__ void __launch_bounds__(kQuarterBlock) k_patch_quarters(PatchArgs a) {
                 const int2 pr = a.pairs[pp.pair];
                 qbA = a.meshes[pr.x].qbox;
                 qbB = a.meshes[pr.y].qbox;
+                pfA = a.meshes[pr.x].pframe;
+                pfB = a.meshes[pr.y].pframe;
                 cached_pair = pp.pair;
             }
             EBox<PREC> xa[4], xb[4];
@@ -471,6 +547,12 @@ __global__ void __launch_bounds__(kQuarterBlock) k_patch_quarters(PatchArgs a) {
 #pragma unroll
                 for (int qb = 0; qb < 4; ++qb)
                     mask |= (uint32_t)boxes_overlap(xa[qa], xb[qb]) << (4 * qa + qb);
+            if (a.frames && mask != 0u) {
+                PFrame X, Y;
+                load_frame(pfA, pp.faceA, X);
+                load_frame(pfB, pp.faceB, Y);
+                if (frames_separated(X, Y, tw)) mask = 0u;
+            }
         }
         pp.pad = mask;
         const unsigned long long pos = warp_append(&a.ctr->psurv, mask != 0u, FULL);

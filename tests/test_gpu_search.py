@@ -399,3 +399,93 @@ def test_random_small_pairs_against_bruteforce(seed):
         h = gpu_records(tms.search(tms.Mesh(XA, A.s, A.periodic, k0=k0, k1=k1), tms.Mesh.from_grid(p.B)))
         OAv = oracle.OMesh(A.X[:, k0:k1].numpy(), A.s[k0:k1].numpy(), A.periodic)
         compare(OAv, OB, h, oracle.search(OAv, OB, method="brute"))
+
+
+def test_patch_frames_cull_without_changing_hits():
+    """The patch-frame test drops patch pairs (fewer listed than with the FP32
+    filters off) and the hit set stays the same."""
+    p = cached("c2", synth.config2)
+    base = gpu_search(p)
+    kept_on = tms.last_stats()["patch_kept"]
+    off = gpu_search(p, narrow_filter=0)
+    kept_off = tms.last_stats()["patch_kept"]
+    assert kept_on < kept_off
+    assert list(zip(base["triA"], base["triB"])) == list(zip(off["triA"], off["triB"]))
+
+
+@pytest.mark.parametrize("delta", [1e-5, 1e-9, 0.0])
+@pytest.mark.parametrize("tau", [1e-12, 1e-6])
+def test_patch_frames_near_contact(delta, tau):
+    """B is A moved by delta along a fixed direction: every patch pair along
+    the diagonal is a near miss (or, at delta = 0, coincident), the case where
+    a frame test without its error terms would drop a pair with hits.  The
+    hit set equals the one with the FP32 filters and frames off, in both
+    precision modes, and the oracle's brute force."""
+    pr = synth.build_pair(77, 40, 14, 40, 14, stretch="exp", n_folds=1, sites=(2, 1), n_hits=3)
+    v = torch.tensor([0.5, -0.5, 0.5, 0.5], dtype=torch.float64)
+    XB = (pr.A.X + delta * v[:, None, None]).contiguous()
+    B = synth.MeshGrid(XB, pr.A.s.clone(), True)
+    pair = synth.MeshPair(pr.A, B, None)
+    OA, OB = oracle.OMesh.from_grid(pr.A), oracle.OMesh.from_grid(B)
+    ref = oracle.search(OA, OB, tau=tau, method="brute")
+    base = gpu_search(pair, tau=tau, narrow_filter=0)
+    keys = list(zip(base["triA"], base["triB"]))
+    for kw in (dict(), dict(tile_rows=8), dict(block_faces=64)):
+        g = gpu_search(pair, tau=tau, **kw)
+        assert list(zip(g["triA"], g["triB"])) == keys
+    compare(OA, OB, base, ref, tau=tau)
+
+
+def _check_frames(F, grid):
+    """Every FP64 vertex of every patch within the bounds of its frame (the
+    record of tms_last_patch_frames), evaluated in FP64 with a margin far below
+    the frame's own rounding terms; returns the share of patches with a frame."""
+    X = grid.X.numpy()
+    M, N = X.shape[1], X.shape[2]
+    nqk, nqi = M - 1, (N if grid.periodic else N - 1)
+    npk, npi = F.shape[0], F.shape[1]
+    assert npk == (nqk + 3) // 4 and npi == (nqi + 7) // 8
+    usable = 0
+    for pk in range(npk):
+        rows = np.arange(4 * pk, min(4 * pk + 4, nqk) + 1)
+        for pi in range(npi):
+            cols = np.arange(8 * pi, min(8 * pi + 8, nqi) + 1) % N
+            V = X[:, rows][:, :, cols].reshape(4, -1).T
+            f = F[pk, pi].astype(np.float64)
+            c, E, h, rho, L, n2, n3 = f[0:4], f[4:20].reshape(4, 4), f[20:24], f[24], f[25], f[26], f[27]
+            assert np.abs(V).max() <= L
+            if not np.isfinite(h).all():
+                continue
+            usable += 1
+            d = V - c
+            a = d @ E.T
+            tol = 1e-13 * max(1.0, np.abs(V).max())
+            assert (np.abs(a).max(0) <= h + tol).all(), (pk, pi, np.abs(a).max(0), h)
+            r = d - a @ E
+            assert np.abs(r).max() <= rho + tol, (pk, pi, np.abs(r).max(), rho)
+            assert n2 >= np.abs(E[2]).sum() and n3 >= np.abs(E[3]).sum()
+    return usable / (npk * npi)
+
+
+@pytest.mark.parametrize("case", ["config2", "ragged_open_tile8", "block64"])
+def test_patch_frames_bound_every_vertex(case):
+    """The frames the bounds pass writes hold every vertex of their patch, and
+    nearly every patch gets one (with normal extents below its tangent ones)."""
+    if case == "config2":
+        p, kw = cached("c2", synth.config2), {}
+    else:
+        q = synth.build_pair(91, 131, 27, 75, 19, stretch="exp", n_folds=2, sites=(4, 2), n_hits=6)
+        if case == "ragged_open_tile8":
+            p = synth.MeshPair(synth.MeshGrid(q.A.X, q.A.s, periodic=False), q.B, None)
+            kw = dict(tile_rows=8)
+        else:
+            p, kw = q, dict(block_faces=64)
+    A, B = tms.Mesh.from_grid(p.A), tms.Mesh.from_grid(p.B)
+    tms.search(A, B, **kw)
+    torch.cuda.synchronize()
+    for side, grid in ((0, p.A), (1, p.B)):
+        F = tms.last_patch_frames(side)
+        assert _check_frames(F, grid) >= 0.9
+        h = F[..., 20:24].reshape(-1, 4)
+        h = h[np.isfinite(h).all(1)]
+        assert np.median(h[:, 2:].max(1)) < np.median(h[:, :2].max(1))
