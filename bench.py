@@ -506,8 +506,8 @@ def run_tms(args, ws, rank, local):
                 ev0 = torch.cuda.Event(enable_timing=True)
                 ev1 = torch.cuda.Event(enable_timing=True)
                 ev0.record(stream)
-                h = tms.search_host(A, B, hA, hB, out=hout, stream=stream)
-                n = len(h)
+                he = tms.search_host(A, B, hA, hB, out=hout, stream=stream)
+                n = len(he)
                 ev1.record(stream)
                 stream.synchronize()
                 if i >= 2:
