@@ -608,9 +608,11 @@ tms_status tms_release_workspace(void *stream);
  *   r = (V - c) - sum_k (e_k . (V - c)) e_k,  max_i |V_i| <= L,
  *   n_2 >= |e_2|_1,  n_3 >= |e_3|_1
  * (h and rho are +inf on a patch without a usable frame).  The patch-pair
- * test drops a pair when along e_2 or e_3 of either patch the two patches'
- * intervals are further apart than the FP64 solve's backward error and the
- * hit tolerance allow (no triangle pair in them can be an FP64 hit).
+ * test drops a pair when along e_2 or e_3 of either patch, or along a
+ * direction orthogonal to e_0, e_1 of one patch and e_0 or e_1 of the other,
+ * the two patches' intervals are further apart than the FP64 solve's backward
+ * error and the hit tolerance allow (no triangle pair in them can be an FP64
+ * hit).
  * *n_patches, *npi (host): patches and patches per quad row.  Synchronises
  * the stream.  TMS_ERR_STATE when no such search was made on `stream`;
  * TMS_ERR_CAPACITY (with the counts set) when cap < 28 * patches. */

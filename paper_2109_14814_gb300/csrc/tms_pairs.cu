@@ -454,7 +454,9 @@ __device__ __forceinline__ void patch_rc(uint32_t patch, uint32_t npi, unsigned 
 // separating-axis test.  The left side is computed as
 // fl(w . fl(c_X - c_Y)), within 5.001 u sum_i |w_i||fl(c_X - c_Y)_i| of the
 // exact value; every bound on the right is rounded up (factor 1.0001).
-// Directions: the two completing axes (approximate normals) of each patch.
+// Directions: the two completing axes (approximate normals) of each patch,
+// then the four directions orthogonal to one patch's parameter directions and
+// one of the other's.
 struct PFrame {
     float c[4], e[4][4], h[4];
     float rho, L, n2, n3;
@@ -487,6 +489,35 @@ __device__ __forceinline__ bool frame_gap(const float w[4], float nw, float hx, 
     const float need = fmaf(tw, hx + sy, nw * reach);
     return g > fmaf(3.0e-7f, q, need) * 1.0001f;
 }
+// the vector orthogonal to a, b and c in R^4 (cofactor expansion of the 4 x 4
+// determinant with rows (x, a, b, c))
+__device__ __forceinline__ float det3f(float a0, float a1, float a2, float b0, float b1, float b2,
+                                       float c0, float c1, float c2) {
+    return a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0);
+}
+__device__ __forceinline__ void cross4f(const float a[4], const float b[4], const float c[4], float x[4]) {
+    x[0] = det3f(a[1], a[2], a[3], b[1], b[2], b[3], c[1], c[2], c[3]);
+    x[1] = -det3f(a[0], a[2], a[3], b[0], b[2], b[3], c[0], c[2], c[3]);
+    x[2] = det3f(a[0], a[1], a[3], b[0], b[1], b[3], c[0], c[1], c[3]);
+    x[3] = -det3f(a[0], a[1], a[2], b[0], b[1], b[2], c[0], c[1], c[2]);
+}
+// the gap test along any w: both patches through their frames,
+// S(w) = sum_k |fl(w . e_k)| h_k + |w|_1 rho
+__device__ __forceinline__ bool frame_gap_any(const float w[4], const PFrame &X, const PFrame &Y,
+                                              const float dc[4], float tw, float reach) {
+    const float nw = (fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]) + fabsf(w[3])) * 1.0001f;
+    float sx = nw * X.rho, sy = nw * Y.rho;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        sx = fmaf(fabsf(fdot4(w, X.e[k])), X.h[k], sx);
+        sy = fmaf(fabsf(fdot4(w, Y.e[k])), Y.h[k], sy);
+    }
+    const float g = fabsf(fdot4(w, dc));
+    const float q = fmaf(fabsf(w[3]), fabsf(dc[3]),
+                         fmaf(fabsf(w[2]), fabsf(dc[2]), fmaf(fabsf(w[1]), fabsf(dc[1]), fabsf(w[0]) * fabsf(dc[0]))));
+    const float need = fmaf(tw, sx + sy, nw * reach);
+    return g > fmaf(3.0e-7f, q, need) * 1.0001f;
+}
 // true when the frames prove that no triangle pair of the two patches is an
 // FP64 hit; tw = 1 + 6 tau' rounded up
 __device__ __forceinline__ bool frames_separated(const PFrame &X, const PFrame &Y, float tw) {
@@ -504,10 +535,23 @@ __device__ __forceinline__ bool frames_separated(const PFrame &X, const PFrame &
     }
     q2[0] = fdot4(Y.e[2], X.e[0]); q2[1] = fdot4(Y.e[2], X.e[1]); q2[2] = p2[2]; q2[3] = p3[2];
     q3[0] = fdot4(Y.e[3], X.e[0]); q3[1] = fdot4(Y.e[3], X.e[1]); q3[2] = p2[3]; q3[3] = p3[3];
-    return frame_gap(X.e[2], X.n2, X.h[2], Y, p2, dc, tw, reach) ||
-           frame_gap(X.e[3], X.n3, X.h[3], Y, p3, dc, tw, reach) ||
-           frame_gap(Y.e[2], Y.n2, Y.h[2], X, q2, dc, tw, reach) ||
-           frame_gap(Y.e[3], Y.n3, Y.h[3], X, q3, dc, tw, reach);
+    if (frame_gap(X.e[2], X.n2, X.h[2], Y, p2, dc, tw, reach) ||
+        frame_gap(X.e[3], X.n3, X.h[3], Y, p3, dc, tw, reach) ||
+        frame_gap(Y.e[2], Y.n2, Y.h[2], X, q2, dc, tw, reach) ||
+        frame_gap(Y.e[3], Y.n3, Y.h[3], X, q3, dc, tw, reach))
+        return true;
+    // mixed directions: orthogonal to one patch's two parameter directions and
+    // one of the other's (both patches thin along it when their tangent planes
+    // share a direction); any w serves, so w is not normalised
+    float w[4];
+    cross4f(X.e[0], X.e[1], Y.e[0], w);
+    if (frame_gap_any(w, X, Y, dc, tw, reach)) return true;
+    cross4f(X.e[0], X.e[1], Y.e[1], w);
+    if (frame_gap_any(w, X, Y, dc, tw, reach)) return true;
+    cross4f(Y.e[0], Y.e[1], X.e[0], w);
+    if (frame_gap_any(w, X, Y, dc, tw, reach)) return true;
+    cross4f(Y.e[0], Y.e[1], X.e[1], w);
+    return frame_gap_any(w, X, Y, dc, tw, reach);
 }
 
 template <int PREC>
