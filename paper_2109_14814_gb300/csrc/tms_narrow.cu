@@ -478,11 +478,49 @@ __device__ __forceinline__ bool separated(const float w[4], const SplitVec &e1, 
 // triangle's edges are differences of the quad's vertices (|A_ij| <= 2 max of
 // the edge vectors below), and every offset y2 - x2 is r0 plus at most the
 // vectors to each quad's far vertex.
+// One axis of the quad-level test: A's vertices at 0, a1, a2, a3 and B's at r0,
+// r0 + b1, r0 + b2, r0 + b3 (all relative to A's v0) projected on w, each with
+// its rounding and input error; true when the widened intervals are further
+// apart than |w|_1 reach.
+__device__ __forceinline__ bool quad_gap(const float w[4], const SplitVec &a1, const SplitVec &a2,
+                                         const SplitVec &a3, const SplitVec &b1, const SplitVec &b2,
+                                         const SplitVec &b3, const SplitVec &r0, float tp, float reach) {
+    const float u = 5.9604645e-08f;
+    const float w1 = fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]) + fabsf(w[3]);
+    const float p1 = dot4(w, a1), p2 = dot4(w, a2), p3 = dot4(w, a3);
+    const float ea = w1 * fmaxf(fmaxf(fmaf(4.01f * u, a1.M, a1.E), fmaf(4.01f * u, a2.M, a2.E)),
+                                fmaf(4.01f * u, a3.M, a3.E));
+    const float q0 = dot4(w, r0);
+    const float s1 = q0 + dot4(w, b1), s2 = q0 + dot4(w, b2), s3 = q0 + dot4(w, b3);
+    const float eb = w1 * (fmaf(4.01f * u, r0.M, r0.E) +
+                           fmaxf(fmaxf(fmaf(4.01f * u, b1.M, b1.E), fmaf(4.01f * u, b2.M, b2.E)),
+                                 fmaf(4.01f * u, b3.M, b3.E))) +
+                     u * fmaxf(fmaxf(fabsf(s1), fabsf(s2)), fabsf(s3));
+    const float xl = fminf(fminf(0.0f, p1), fminf(p2, p3)), xh = fmaxf(fmaxf(0.0f, p1), fmaxf(p2, p3));
+    const float yl = fminf(fminf(q0, s1), fminf(s2, s3)), yh = fmaxf(fmaxf(q0, s1), fmaxf(s2, s3));
+    const float DX = (xh - xl) + 2.0f * ea, DY = (yh - yl) + 2.0f * eb;
+    const float need = (tp * (DX + DY) + w1 * reach + ea + eb) * 1.001f;
+    const float gap = fmaxf(yl - xh, xl - yh) * (1.0f - 4.0f * u);
+    return gap > need;
+}
+
+// the vector orthogonal to a, b and c in R^4 (cofactor expansion of the 4 x 4
+// determinant with rows (x, a, b, c))
+__device__ __forceinline__ float det3v(float a0, float a1, float a2, float b0, float b1, float b2,
+                                       float c0, float c1, float c2) {
+    return a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0);
+}
+__device__ __forceinline__ void cross4v(const float a[4], const float b[4], const float c[4], float x[4]) {
+    x[0] = det3v(a[1], a[2], a[3], b[1], b[2], b[3], c[1], c[2], c[3]);
+    x[1] = -det3v(a[0], a[2], a[3], b[0], b[2], b[3], c[0], c[2], c[3]);
+    x[2] = det3v(a[0], a[1], a[3], b[0], b[1], b[3], c[0], c[1], c[3]);
+    x[3] = -det3v(a[0], a[1], a[2], b[0], b[1], b[2], c[0], c[1], c[2]);
+}
+
 // the quad-level test on the edge vectors of both quads relative to v0 of A
 __device__ __forceinline__ bool quad_sat_vectors(const SplitVec &a1, const SplitVec &a2, const SplitVec &a3,
                                                  const SplitVec &b1, const SplitVec &b2, const SplitVec &b3,
                                                  const SplitVec &r0, float tau) {
-    const float u = 5.9604645e-08f;
     float mA1[6], mB1[6], epsA1, epsB1;
     plucker(a1, a2, mA1, epsA1);
     plucker(b1, b2, mB1, epsB1);
@@ -500,24 +538,36 @@ __device__ __forceinline__ bool quad_sat_vectors(const SplitVec &a1, const Split
 #pragma unroll
         for (int k = 0; k < 6; ++k) m[k] = ax < 2 ? mA1[k] : mB1[k];
         dual_dir(m, ax == 0 ? kA1 : (ax == 1 ? kA2 : (ax == 2 ? kB1 : kB2)), w);
-        const float w1 = fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]) + fabsf(w[3]);
-        const float p1 = dot4(w, a1), p2 = dot4(w, a2), p3 = dot4(w, a3);
-        const float ea = w1 * fmaxf(fmaxf(fmaf(4.01f * u, a1.M, a1.E), fmaf(4.01f * u, a2.M, a2.E)),
-                                    fmaf(4.01f * u, a3.M, a3.E));
-        const float q0 = dot4(w, r0);
-        const float s1 = q0 + dot4(w, b1), s2 = q0 + dot4(w, b2), s3 = q0 + dot4(w, b3);
-        const float eb = w1 * (fmaf(4.01f * u, r0.M, r0.E) +
-                               fmaxf(fmaxf(fmaf(4.01f * u, b1.M, b1.E), fmaf(4.01f * u, b2.M, b2.E)),
-                                     fmaf(4.01f * u, b3.M, b3.E))) +
-                         u * fmaxf(fmaxf(fabsf(s1), fabsf(s2)), fabsf(s3));
-        const float xl = fminf(fminf(0.0f, p1), fminf(p2, p3)), xh = fmaxf(fmaxf(0.0f, p1), fmaxf(p2, p3));
-        const float yl = fminf(fminf(q0, s1), fminf(s2, s3)), yh = fmaxf(fmaxf(q0, s1), fmaxf(s2, s3));
-        const float DX = (xh - xl) + 2.0f * ea, DY = (yh - yl) + 2.0f * eb;
-        const float need = (tp * (DX + DY) + w1 * reach + ea + eb) * 1.001f;
-        const float gap = fmaxf(yl - xh, xl - yh) * (1.0f - 4.0f * u);
-        if (gap > need) return true;
+        if (quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach)) return true;
     }
     return false;
+}
+
+// Mixed directions of the quad-level test, for the candidates the dual axes
+// leave: each orthogonal to the first triangle's two edges of one quad and one
+// of those edges of the other (both quads thin along it when their planes
+// share a direction).  Any direction serves (the bounds hold for the FP32 w as
+// computed), so w is not normalised.
+__device__ __forceinline__ bool quad_mixed_reject_hi(const float4 QA[4], const float4 QB[4], float tau) {
+    const SplitVec a1 = hi_vec(QA[1], QA[0]), a2 = hi_vec(QA[2], QA[0]);
+    const SplitVec a3 = hi_vec(QA[3], QA[0]);
+    const SplitVec b1 = hi_vec(QB[1], QB[0]), b2 = hi_vec(QB[2], QB[0]);
+    const SplitVec b3 = hi_vec(QB[3], QB[0]);
+    const SplitVec r0 = hi_vec(QB[0], QA[0]);
+    const float amax = 2.0f * fmaxf(fmaxf(fmaxf(a1.M + a1.E, a2.M + a2.E), fmaxf(a3.M + a3.E, b1.M + b1.E)),
+                                    fmaxf(b2.M + b2.E, b3.M + b3.E));
+    const float rmax = (r0.M + r0.E) + (a3.M + a3.E) + (b3.M + b3.E);
+    const float reach = fp64_reach(amax * 1.001f, rmax * 1.001f);
+    const float tp = widen3(tau);
+    float w[4];
+    cross4v(a1.v, a2.v, b1.v, w);
+    if (quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach)) return true;
+    cross4v(a1.v, a2.v, b2.v, w);
+    if (quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach)) return true;
+    cross4v(b1.v, b2.v, a1.v, w);
+    if (quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach)) return true;
+    cross4v(b1.v, b2.v, a2.v, w);
+    return quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach);
 }
 
 // The test from the quads' FP32 vertex roundings alone (hi_vec bounds), which
@@ -796,15 +846,37 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
 }
 
 // Stage 1a (quad faces): the quad-level separating-axis test of every candidate
-// on the FP32 roundings of its quads' vertices; the candidates it cannot clear
-// are listed for the per-pair path of k_narrow_filter.
-__global__ void __launch_bounds__(256, 3) k_quad_filter(NarrowArgs a) {
+// on the FP32 roundings of its quads' vertices, the dual axes first; the
+// candidates they leave gather in a per-warp queue, and every 32 of them take
+// the mixed directions with all lanes busy; those still not cleared are listed
+// for the per-pair path of k_narrow_filter.
+constexpr int kQuadWarps = 8;
+__global__ void __launch_bounds__(32 * kQuadWarps, 3) k_quad_filter(NarrowArgs a) {
+    __shared__ uint32_t s_q[kQuadWarps][64];
     if (a.ctr->cand > a.cand_cap) return;
     const unsigned long long n = a.ctr->cand;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
     const float tauf = __double2float_ru(a.tau);
     unsigned long long n_quad = 0;
+    unsigned qn = 0;                                 // queued candidates (warp-uniform)
+    // the mixed directions for queue items [base, base + cnt)
+    auto drain = [&](unsigned base, unsigned cnt) {
+        bool keep = false;
+        uint32_t g = 0;
+        if ((unsigned)lane < cnt) {
+            g = s_q[warp][base + lane];
+            const Cand cd = a.cand[g];
+            const int2 pr = a.pairs[cd.pair];
+            float4 QA[4], QB[4];
+            gather_quad_hi(a.meshes[pr.x], cd.faceA, QA);
+            gather_quad_hi(a.meshes[pr.y], cd.faceB, QB);
+            keep = !quad_mixed_reject_hi(QA, QB, tauf);
+        }
+        const unsigned long long pos = warp_append(&a.ctr->qkeep, keep, FULL);
+        if (keep && pos < a.cand_cap) a.qsurv[pos] = g;
+    };
     for (unsigned long long g0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x - lane;
          g0 < n; g0 += stride) {
         const unsigned long long g = g0 + lane;
@@ -819,8 +891,19 @@ __global__ void __launch_bounds__(256, 3) k_quad_filter(NarrowArgs a) {
             need = !quad_sat_reject_hi(QA, QB, tauf);
         }
         n_quad += __popc(__ballot_sync(FULL, valid));
-        const unsigned long long pos = warp_append(&a.ctr->qkeep, need, FULL);
-        if (need && pos < a.cand_cap) a.qsurv[pos] = (uint32_t)g;
+        const uint32_t want = __ballot_sync(FULL, need);
+        if (need) s_q[warp][qn + __popc(want & lt)] = (uint32_t)g;
+        qn += __popc(want);
+        __syncwarp();
+        if (qn >= 32) {
+            qn -= 32;
+            drain(qn, 32);
+            __syncwarp();
+        }
+    }
+    if (qn) {
+        drain(0, qn);
+        __syncwarp();
     }
     if (lane == 0 && n_quad) atomicAdd(&a.ctr->quad, n_quad);
 }
@@ -1100,7 +1183,7 @@ void launch_narrow(const NarrowArgs &a, int face_level, int sms, int grid, cudaS
     if (face_level == 0) {
         k_narrow_filter<0><<<sms * filter_resident<0>(), 256, 0, st>>>(a);
     } else {
-        if (a.fp32_filter) k_quad_filter<<<sms * 3 * 4, 256, 0, st>>>(a);
+        if (a.fp32_filter) k_quad_filter<<<sms * 3 * 4, 32 * kQuadWarps, 0, st>>>(a);
         k_narrow_filter<1><<<sms * filter_resident<1>(), 256, 0, st>>>(a);
     }
     k_narrow_fp64<<<grid, 256, 0, st>>>(a);
