@@ -543,12 +543,16 @@ __device__ __forceinline__ bool quad_sat_vectors(const SplitVec &a1, const Split
     return false;
 }
 
-// Mixed directions of the quad-level test, for the candidates the dual axes
-// leave: each orthogonal to the first triangle's two edges of one quad and one
-// of those edges of the other (both quads thin along it when their planes
-// share a direction).  Any direction serves (the bounds hold for the FP32 w as
-// computed), so w is not normalised.
-__device__ __forceinline__ bool quad_mixed_reject_hi(const float4 QA[4], const float4 QB[4], float tau) {
+// The quad-level test from the quads' FP32 vertex roundings alone (hi_vec
+// bounds, half the data of the split copies).  Directions: the mixed ones
+// MLO..MHI-1 -- 0: orthogonal to A's first-triangle edges a1, a2 and B's b1,
+// 1: to a1, a2, b2, 2: to b1, b2, a1, 3: to b1, b2, a2 (both quads thin along
+// each when their planes share a direction) -- then, with DUALS, the dual axes
+// of quad_sat_vectors.  Any direction serves (the bounds hold for the FP32 w as
+// computed), so w is not normalised.  A candidate it cannot clear goes on to
+// the tests on the split copies.
+template <int MLO, int MHI, bool DUALS>
+__device__ __forceinline__ bool quad_reject_hi(const float4 QA[4], const float4 QB[4], float tau) {
     const SplitVec a1 = hi_vec(QA[1], QA[0]), a2 = hi_vec(QA[2], QA[0]);
     const SplitVec a3 = hi_vec(QA[3], QA[0]);
     const SplitVec b1 = hi_vec(QB[1], QB[0]), b2 = hi_vec(QB[2], QB[0]);
@@ -560,27 +564,29 @@ __device__ __forceinline__ bool quad_mixed_reject_hi(const float4 QA[4], const f
     const float reach = fp64_reach(amax * 1.001f, rmax * 1.001f);
     const float tp = widen3(tau);
     float w[4];
-    cross4v(a1.v, a2.v, b1.v, w);
-    if (quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach)) return true;
-    cross4v(a1.v, a2.v, b2.v, w);
-    if (quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach)) return true;
-    cross4v(b1.v, b2.v, a1.v, w);
-    if (quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach)) return true;
-    cross4v(b1.v, b2.v, a2.v, w);
-    return quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach);
+    if (MLO <= 0 && 0 < MHI) {
+        cross4v(a1.v, a2.v, b1.v, w);
+        if (quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach)) return true;
+    }
+    if (MLO <= 1 && 1 < MHI) {
+        cross4v(a1.v, a2.v, b2.v, w);
+        if (quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach)) return true;
+    }
+    if (MLO <= 2 && 2 < MHI) {
+        cross4v(b1.v, b2.v, a1.v, w);
+        if (quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach)) return true;
+    }
+    if (MLO <= 3 && 3 < MHI) {
+        cross4v(b1.v, b2.v, a2.v, w);
+        if (quad_gap(w, a1, a2, a3, b1, b2, b3, r0, tp, reach)) return true;
+    }
+    if (DUALS) return quad_sat_vectors(a1, a2, a3, b1, b2, b3, r0, tau);
+    return false;
 }
 
-// The test from the quads' FP32 vertex roundings alone (hi_vec bounds), which
-// clears most candidates with half the data of the split copies; a candidate it
-// cannot clear goes on to the tests on the split copies.
-__device__ __forceinline__ bool quad_sat_reject_hi(const float4 QA[4], const float4 QB[4], float tau) {
-    const SplitVec a1 = hi_vec(QA[1], QA[0]), a2 = hi_vec(QA[2], QA[0]);
-    const SplitVec a3 = hi_vec(QA[3], QA[0]);
-    const SplitVec b1 = hi_vec(QB[1], QB[0]), b2 = hi_vec(QB[2], QB[0]);
-    const SplitVec b3 = hi_vec(QB[3], QB[0]);
-    const SplitVec r0 = hi_vec(QB[0], QA[0]);
-    return quad_sat_vectors(a1, a2, a3, b1, b2, b3, r0, tau);
-}
+// the mixed directions every candidate takes in k_quad_filter's first stage; the
+// rest, and the dual axes, only the candidates these leave
+constexpr int kQuadFirstAxes = 2;
 
 // true when the separating-axis test proves that the FP64 solve of the pair
 // reports no hit (fp64_reach)
@@ -846,10 +852,10 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
 }
 
 // Stage 1a (quad faces): the quad-level separating-axis test of every candidate
-// on the FP32 roundings of its quads' vertices, the dual axes first; the
-// candidates they leave gather in a per-warp queue, and every 32 of them take
-// the mixed directions with all lanes busy; those still not cleared are listed
-// for the per-pair path of k_narrow_filter.
+// on the FP32 roundings of its quads' vertices, the first mixed directions
+// first; the candidates they leave gather in a per-warp queue, and every 32 of
+// them take the other directions with all lanes busy; those still not cleared
+// are listed for the per-pair path of k_narrow_filter.
 constexpr int kQuadWarps = 8;
 __global__ void __launch_bounds__(32 * kQuadWarps, 3) k_quad_filter(NarrowArgs a) {
     __shared__ uint32_t s_q[kQuadWarps][64];
@@ -872,7 +878,7 @@ __global__ void __launch_bounds__(32 * kQuadWarps, 3) k_quad_filter(NarrowArgs a
             float4 QA[4], QB[4];
             gather_quad_hi(a.meshes[pr.x], cd.faceA, QA);
             gather_quad_hi(a.meshes[pr.y], cd.faceB, QB);
-            keep = !quad_mixed_reject_hi(QA, QB, tauf);
+            keep = !quad_reject_hi<kQuadFirstAxes, 4, true>(QA, QB, tauf);
         }
         const unsigned long long pos = warp_append(&a.ctr->qkeep, keep, FULL);
         if (keep && pos < a.cand_cap) a.qsurv[pos] = g;
@@ -888,7 +894,7 @@ __global__ void __launch_bounds__(32 * kQuadWarps, 3) k_quad_filter(NarrowArgs a
             float4 QA[4], QB[4];
             gather_quad_hi(a.meshes[pr.x], cd.faceA, QA);
             gather_quad_hi(a.meshes[pr.y], cd.faceB, QB);
-            need = !quad_sat_reject_hi(QA, QB, tauf);
+            need = !quad_reject_hi<0, kQuadFirstAxes, false>(QA, QB, tauf);
         }
         n_quad += __popc(__ballot_sync(FULL, valid));
         const uint32_t want = __ballot_sync(FULL, need);
