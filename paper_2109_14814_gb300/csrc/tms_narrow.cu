@@ -135,21 +135,8 @@ __device__ __forceinline__ void quad_ik(const MeshDev &m, uint32_t q, int &i, in
     i = (int)(q - kk * (uint32_t)m.N);
 }
 
-// split copies of the quad's vertices (i,k), (i+1,k), (i,k+1), (i+1,k+1)
-__device__ __forceinline__ void gather_quad_split(const MeshDev &m, uint32_t q, float4 v[4][2]) {
-    int i, k;
-    quad_ik(m, q, i, k);
-    const int ip = (i + 1 == m.N) ? 0 : i + 1;
-    const size_t idx[4] = {(size_t)k * m.N + i, (size_t)k * m.N + ip, (size_t)(k + 1) * m.N + i,
-                           (size_t)(k + 1) * m.N + ip};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        v[j][0] = __ldg(m.split + idx[j]);
-        v[j][1] = __ldg(m.split + (size_t)m.N * m.M + idx[j]);
-    }
-}
-
-// the high halves of those split copies (the FP32 rounding of each coordinate)
+// the high halves of the split copies of the quad's vertices (i,k), (i+1,k),
+// (i,k+1), (i+1,k+1) (the FP32 rounding of each coordinate)
 __device__ __forceinline__ void gather_quad_hi(const MeshDev &m, uint32_t q, float4 v[4]) {
     int i, k;
     quad_ik(m, q, i, k);
@@ -158,17 +145,6 @@ __device__ __forceinline__ void gather_quad_hi(const MeshDev &m, uint32_t q, flo
                            (size_t)(k + 1) * m.N + ip};
 #pragma unroll
     for (int j = 0; j < 4; ++j) v[j] = __ldg(m.split + idx[j]);
-}
-
-// (x1, x2, x3) of T1 = ((i+1,k), (i,k), (i,k+1)) or T2 = ((i,k+1), (i+1,k+1), (i+1,k))
-__device__ __forceinline__ void quad_tri(const float4 Q[4][2], int tau, float4 X[3][2]) {
-    // constant indices and selects keep Q in registers
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        X[0][h] = tau ? Q[2][h] : Q[1][h];
-        X[1][h] = tau ? Q[3][h] : Q[0][h];
-        X[2][h] = tau ? Q[1][h] : Q[2][h];
-    }
 }
 
 // closed overlap of the two triangles' boxes, each coordinate widened by its
@@ -697,7 +673,6 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
     constexpr int kW = 8, kQ = 32 + 4 * 32;
     __shared__ uint32_t q_cand[kW][kQ];          // triangle pairs for the verified solve
     __shared__ uint8_t q_sub[kW][kQ];
-    __shared__ uint32_t c_cand[kW][32];          // quad candidates for the per-pair path
     if (a.ctr->cand > a.cand_cap) return;
     const unsigned long long n = a.ctr->cand;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -759,41 +734,28 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
             __syncwarp();
         }
     };
-    // the per-pair path for candidate-queue items [base, base + cnt)
-    auto cand_round = [&](unsigned base, unsigned cnt) {
-        const bool valid = (unsigned)lane < cnt;
-        const uint32_t g = valid ? c_cand[warp][base + lane] : 0u;
-        Cand cd;
-        cd.faceA = cd.faceB = cd.pair = 0;
-        if (valid) cd = a.cand[g];
-        const int2 pr = a.pairs[valid ? cd.pair : 0];
-        float4 QA[4][2], QB[4][2];
-        if (valid) {
-            gather_quad_split(a.meshes[pr.x], cd.faceA, QA);
-            gather_quad_split(a.meshes[pr.y], cd.faceB, QB);
-        }
-#pragma unroll 1
-        for (int sub = 0; sub < 4; ++sub) {
-            float4 X[3][2], Y[3][2];
-            quad_tri(QA, sub & 1, X);
-            quad_tri(QB, sub >> 1, Y);
-            pair_tests(valid, g, sub, X, Y, true);
-        }
-        drain_full();
-    };
-
     if (FACE == 1 && a.fp32_filter) {
-        // the candidates the quad-level test (k_quad_filter) could not clear, 32
-        // per warp round, through the per-pair path
-        const unsigned long long nk = clamp_count(&a.ctr->qkeep, a.cand_cap);
-        const unsigned long long wstride = (unsigned long long)gridDim.x * (blockDim.x >> 5) * 32;
-        for (unsigned long long b0 = (blockIdx.x * (unsigned long long)(blockDim.x >> 5) + warp) * 32; b0 < nk;
-             b0 += wstride) {
-            const unsigned cnt = (unsigned)min(32ULL, nk - b0);
-            if ((unsigned)lane < cnt) c_cand[warp][lane] = a.qsurv[b0 + lane];
-            __syncwarp();
-            cand_round(0, cnt);
-            __syncwarp();
+        // the candidates the quad-level test (k_quad_filter) could not clear: each
+        // of their four triangle pairs on a lane of its own (triangle boxes, the
+        // triangle-level separating axes), the pairs left queued for the
+        // verified solve, 32 at a time
+        const unsigned long long ni = 4 * clamp_count(&a.ctr->qkeep, a.cand_cap);
+        for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x - lane; i0 < ni;
+             i0 += stride) {
+            const unsigned long long it = i0 + lane;
+            const bool valid = it < ni;
+            uint32_t g = 0;
+            const int sub = (int)(it & 3);
+            float4 X[3][2], Y[3][2];
+            if (valid) {
+                g = a.qsurv[it >> 2];
+                const Cand cd = a.cand[g];
+                const int2 pr = a.pairs[cd.pair];
+                gather_split(a.meshes[pr.x], 2 * cd.faceA + (sub & 1), X);
+                gather_split(a.meshes[pr.y], 2 * cd.faceB + (sub >> 1), Y);
+            }
+            pair_tests(valid, g, sub, X, Y, true);
+            drain_full();
         }
         if (qn) {
             drain(0, qn);
