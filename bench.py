@@ -50,11 +50,12 @@ FP32_SOLVE_FLOPS = 956
 # of Plucker coordinates (56), the FP64 solve's reach (12), the two dual
 # choices (28), four interval tests (260)
 SAT_FLOPS = 452
-# FP32 operations of the quad-level test of one quad candidate: seven split
-# difference vectors (112), two sets of Plucker coordinates (56), the FP64
-# solve's reach (20), two dual choices (28), four interval tests over eight
-# vertices (360)
-QUAD_SAT_FLOPS = 576
+# FP32 operations of the quad-level test every quad candidate takes: seven split
+# difference vectors (112), the FP64 solve's reach (20), two mixed directions
+# (4D cross products, 56 each) and their interval tests over eight vertices (90
+# each).  The second stage, on the tenth or so of the candidates these leave
+# (two more mixed directions and the dual axes), is not counted.
+QUAD_SAT_FLOPS = 424
 # FP32 lane operations per second of one GB300 (152 SMs x 128 lanes x 2070 MHz,
 # an FMA counted 2)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
