@@ -107,7 +107,10 @@ typedef struct {
                              undecided candidates get the FP64 solve. */
     float cell_mult;      /* grid cell edge = cell_mult x widest face extent per
                              coordinate (Sec. 6.2.1 requires > 1 x); default 1.0625 */
-    double tau;           /* margin tolerance of the hit test, default 1e-12 */
+    double tau;           /* margin tolerance of the hit test, default 1e-12; it
+                             widens the hit test (weights >= -tau), not the broad
+                             phase, whose boxes are the faces' own: meant for
+                             tolerances of the order of the rounding */
     long long entry_capacity;  /* initial scratch sizes (0 = automatic); grown on */
     long long cand_capacity;   /* overflow and retried inside the call          */
     long long hit_capacity;    /* raw hits before merging (0 = automatic)       */

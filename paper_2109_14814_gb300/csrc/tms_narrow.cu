@@ -147,29 +147,43 @@ __device__ __forceinline__ void gather_quad_hi(const MeshDev &m, uint32_t q, flo
     for (int j = 0; j < 4; ++j) v[j] = __ldg(m.split + idx[j]);
 }
 
-// closed overlap of the two triangles' boxes, each coordinate widened by its
-// split remainder and a relative 1e-6 (more than the FP32 rounding of the test)
-__device__ __forceinline__ bool split_boxes_overlap(const float4 X[3][2], const float4 Y[3][2]) {
-    bool ov = true;
+// Overlap of the two triangles' boxes, as the separating-axis test along each
+// coordinate axis: each coordinate's interval from the split copies (widened by
+// the split remainder and a relative 1e-6, more than the FP32 rounding of the
+// test), and the pair dropped only when a gap exceeds 3 tau' (D_X + D_Y) plus the
+// FP64 solve's reach (the triangles widened to weights >= -tau', widen3 and
+// fp64_reach, with max|A| at most the largest extent and |r| at most twice the
+// largest coordinate) -- so that no FP64 hit is dropped whatever tau.
+__device__ __forceinline__ bool split_boxes_overlap(const float4 X[3][2], const float4 Y[3][2], float tau) {
+    float xl[4], xh[4], yl[4], yh[4];
+    float dmax = 0.0f, cmax = 0.0f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        float xl = 3.4e38f, xh = -3.4e38f, yl = 3.4e38f, yh = -3.4e38f;
+        xl[c] = 3.4e38f; xh[c] = -3.4e38f; yl[c] = 3.4e38f; yh[c] = -3.4e38f;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const float hx = comp(X[j][0], c), lx = comp(X[j][1], c);
             const float dx = fabsf(lx) + 1e-6f * fabsf(hx) + 1e-29f;
-            xl = fminf(xl, hx - dx);
-            xh = fmaxf(xh, hx + dx);
+            xl[c] = fminf(xl[c], hx - dx);
+            xh[c] = fmaxf(xh[c], hx + dx);
             const float hy = comp(Y[j][0], c), ly = comp(Y[j][1], c);
             const float dy = fabsf(ly) + 1e-6f * fabsf(hy) + 1e-29f;
-            yl = fminf(yl, hy - dy);
-            yh = fmaxf(yh, hy + dy);
+            yl[c] = fminf(yl[c], hy - dy);
+            yh[c] = fmaxf(yh[c], hy + dy);
         }
-        ov &= !(xh < yl || yh < xl);
+        dmax = fmaxf(dmax, fmaxf(xh[c] - xl[c], yh[c] - yl[c]));
+        cmax = fmaxf(cmax, fmaxf(fmaxf(fabsf(xl[c]), fabsf(xh[c])), fmaxf(fabsf(yl[c]), fabsf(yh[c]))));
+    }
+    const float tp = widen3(tau);
+    const float reach = fp64_reach(dmax * 1.001f, 2.0f * cmax * 1.001f);
+    bool ov = true;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float need = (tp * ((xh[c] - xl[c]) + (yh[c] - yl[c])) + reach) * 1.001f;
+        ov &= !(yl[c] - xh[c] > need || xl[c] - yh[c] > need);
     }
     return ov;
 }
-
 
 // true when the verified FP32 solve proves margin < -2 tau (not a hit)
 __device__ __noinline__ bool fp32_verified_reject(const float4 X[3][2], const float4 Y[3][2],
@@ -660,14 +674,13 @@ __device__ __forceinline__ bool narrow_fp64(const MeshDev &ma, const MeshDev &mb
     return true;
 }
 
-// Stage 1: every triangle pair of every candidate through the FP32 tests;
-// pairs they cannot reject go to the survivor list.  Quad candidates first meet
-// the quad-level separating-axis test, which clears all four triangle pairs at
-// once for most of them; the rest wait in a per-warp candidate queue and are
-// taken 32 at a time through the per-pair path: the (widened) triangle boxes,
-// the triangle-level separating-axis test, and for the few pairs left a
-// second queue feeding the verified solve 32 pairs at a time -- so that no
-// expensive step runs with most lanes idle.
+// Stage 1b: the triangle pairs the quad-level test (k_quad_filter) leaves, one
+// per lane (with face_level 0, every triangle candidate): the (widened)
+// triangle boxes, the triangle-level separating-axis test, and for the pairs
+// left a per-warp queue feeding the verified solve 32 pairs at a time, so that
+// the solve does not run with most lanes idle; pairs the tests cannot reject go
+// to the survivor list.  With the FP32 filters off, every triangle pair of
+// every candidate goes to the survivor list.
 template <int FACE>
 __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
     constexpr int kW = 8, kQ = 32 + 4 * 32;
@@ -715,7 +728,7 @@ __global__ void __launch_bounds__(256, 2) k_narrow_filter(NarrowArgs a) {
     // they cannot reject join the pair queue (all lanes call it together)
     auto pair_tests = [&](bool valid, uint32_t g, int sub, const float4 X[3][2], const float4 Y[3][2],
                           bool boxes) {
-        const bool tested = valid && (!boxes || split_boxes_overlap(X, Y));
+        const bool tested = valid && (!boxes || split_boxes_overlap(X, Y, tauf));
         const bool need = tested && !fp32_sat_reject(X, Y, tauf);
         n_sat += __popc(__ballot_sync(FULL, tested));
         const uint32_t want = __ballot_sync(FULL, need);

@@ -414,26 +414,30 @@ def test_patch_frames_cull_without_changing_hits():
 
 
 @pytest.mark.parametrize("delta", [1e-5, 1e-9, 0.0])
-@pytest.mark.parametrize("tau", [1e-12, 1e-6])
+@pytest.mark.parametrize("tau", [1e-12, 1e-6, 0.05])
 def test_patch_frames_near_contact(delta, tau):
     """B is A moved by delta along a fixed direction: every patch pair along
     the diagonal is a near miss (or, at delta = 0, coincident), the case where
     a frame test without its error terms would drop a pair with hits.  The
-    hit set equals the one with the FP32 filters and frames off, in both
-    precision modes, and the oracle's brute force."""
+    hit set equals the one with the FP32 filters and frames off, and, for the
+    small tolerances the hit test is meant for, the oracle's brute force.  A
+    large tau (0.05) widens the hit test but not the broad phase (the boxes are
+    the triangles' own), so there the oracle, which tries every pair, finds
+    more; the filters must still drop no FP64 hit."""
     pr = synth.build_pair(77, 40, 14, 40, 14, stretch="exp", n_folds=1, sites=(2, 1), n_hits=3)
     v = torch.tensor([0.5, -0.5, 0.5, 0.5], dtype=torch.float64)
     XB = (pr.A.X + delta * v[:, None, None]).contiguous()
     B = synth.MeshGrid(XB, pr.A.s.clone(), True)
     pair = synth.MeshPair(pr.A, B, None)
     OA, OB = oracle.OMesh.from_grid(pr.A), oracle.OMesh.from_grid(B)
-    ref = oracle.search(OA, OB, tau=tau, method="brute")
+    ref = oracle.search(OA, OB, tau=tau, method="brute") if tau < 1e-3 else None
     base = gpu_search(pair, tau=tau, narrow_filter=0)
     keys = list(zip(base["triA"], base["triB"]))
     for kw in (dict(), dict(tile_rows=8), dict(block_faces=64)):
         g = gpu_search(pair, tau=tau, **kw)
         assert list(zip(g["triA"], g["triB"])) == keys
-    compare(OA, OB, base, ref, tau=tau)
+    if tau < 1e-3:
+        compare(OA, OB, base, ref, tau=tau)
 
 
 def _check_frames(F, grid):
