@@ -96,7 +96,8 @@ typedef struct {
                              the paper's kernel (4 triangle pairs per candidate;
                              default). */
     int moller;           /* 1 = apply the Moller quick test of Sec. 6.2.3 (FP64,
-                             with a rounding guard) to candidates; default 0. */
+                             with a rounding guard) to candidates; default 0.
+                             Like the boxes, it is not widened by tau. */
     int cell_filter;      /* 1 = register only faces in grid cells occupied by
                              both meshes before grouping (default); 0 = emit
                              every face-cell incidence (the paper's per-box lists). */
