@@ -204,12 +204,13 @@ __host__ __device__ inline double ord_dec(unsigned long long u) {
 // |e| <= u64 |r|.  A hit has weights >= -tau' (tau' = tau plus the rounding of the
 // margin, 1e-15 at most), so |z| <= 1 + 2 tau' and the points x2 + a e1 + b e2
 // and y2 + c f1 + d f2 of the two triangles, widened to weights >= -tau', differ
-// by A z - r = e - E z: at most fp64_reach(max|A|, |r|) in every coordinate.
-// A separating-axis test that proves the widened triangles further apart than
-// that therefore proves that the FP64 solve reports no hit -- whatever the
-// system's condition.
-__device__ __forceinline__ float fp64_reach(float amax, float rmax) {
-    return (5e-13f * amax + 1.2e-16f * rmax) * 1.01f + 1e-37f;
+// by A z - r = e - E z: |E z| <= 1.1e-13 max|A| sum_j |z_j| <= 4.4e-13 (1 + 2 tau')
+// max|A| and |e| <= 1.12e-16 |r|, at most fp64_reach(max|A|, |r|, tau) in every
+// coordinate.  A separating-axis test that proves the widened triangles further
+// apart than that therefore proves that the FP64 solve reports no hit --
+// whatever the system's condition.
+__device__ __forceinline__ float fp64_reach(float amax, float rmax, float tau) {
+    return (5e-13f * (1.0f + 2.0f * tau) * amax + 1.2e-16f * rmax) * 1.01f + 1e-37f;
 }
 
 // along w, a triangle's projection widened to weights >= -tau' grows by at most

@@ -175,7 +175,7 @@ __device__ __forceinline__ bool split_boxes_overlap(const float4 X[3][2], const 
         cmax = fmaxf(cmax, fmaxf(fmaxf(fabsf(xl[c]), fabsf(xh[c])), fmaxf(fabsf(yl[c]), fabsf(yh[c]))));
     }
     const float tp = widen3(tau);
-    const float reach = fp64_reach(dmax * 1.001f, 2.0f * cmax * 1.001f);
+    const float reach = fp64_reach(dmax * 1.001f, 2.0f * cmax * 1.001f, tau);
     bool ov = true;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -517,7 +517,7 @@ __device__ __forceinline__ bool quad_sat_vectors(const SplitVec &a1, const Split
     const float amax = 2.0f * fmaxf(fmaxf(fmaxf(a1.M + a1.E, a2.M + a2.E), fmaxf(a3.M + a3.E, b1.M + b1.E)),
                                     fmaxf(b2.M + b2.E, b3.M + b3.E));
     const float rmax = (r0.M + r0.E) + (a3.M + a3.E) + (b3.M + b3.E);
-    const float reach = fp64_reach(amax * 1.001f, rmax * 1.001f);
+    const float reach = fp64_reach(amax * 1.001f, rmax * 1.001f, tau);
     const float tp = widen3(tau);
     int kA1, kA2, kB1, kB2;
     top2_duals(mA1, kA1, kA2);
@@ -551,7 +551,7 @@ __device__ __forceinline__ bool quad_reject_hi(const float4 QA[4], const float4 
     const float amax = 2.0f * fmaxf(fmaxf(fmaxf(a1.M + a1.E, a2.M + a2.E), fmaxf(a3.M + a3.E, b1.M + b1.E)),
                                     fmaxf(b2.M + b2.E, b3.M + b3.E));
     const float rmax = (r0.M + r0.E) + (a3.M + a3.E) + (b3.M + b3.E);
-    const float reach = fp64_reach(amax * 1.001f, rmax * 1.001f);
+    const float reach = fp64_reach(amax * 1.001f, rmax * 1.001f, tau);
     const float tp = widen3(tau);
     float w[4];
     if (MLO <= 0 && 0 < MHI) {
@@ -593,7 +593,7 @@ __device__ __noinline__ bool fp32_sat_reject(const float4 X[3][2], const float4 
     plucker(e1, e2, mE, epsE);
     plucker(f1, f2, mF, epsF);
     const float amax = fmaxf(fmaxf(e1.M + e1.E, e2.M + e2.E), fmaxf(f1.M + f1.E, f2.M + f2.E));
-    const float reach = fp64_reach(amax * 1.001f, (r.M + r.E) * 1.001f);
+    const float reach = fp64_reach(amax * 1.001f, (r.M + r.E) * 1.001f, tau);
     const float tp = widen3(tau);
     int kE1, kE2, kF1, kF2;
     top2_duals(mE, kE1, kE2);

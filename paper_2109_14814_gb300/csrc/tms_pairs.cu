@@ -449,7 +449,7 @@ __device__ __forceinline__ void patch_rc(uint32_t patch, uint32_t npi, unsigned 
 //   |w . (c_X - c_Y)| > (1 + 6 tau') (S_X(w) + S_Y(w)) + |w|_1 reach,
 // reach the FP64 solve's backward error (fp64_reach) for any triangle pair of
 // the two patches: every entry of the system is an edge, |A_ij| <= 2 max(L_X,
-// L_Y), and |r| <= L_X + L_Y, so reach <= 1.011e-12 (L_X + L_Y).  Then no
+// L_Y), and |r| <= L_X + L_Y, so reach <= 1.011e-12 (1 + 2 tau') (L_X + L_Y).  Then no
 // triangle pair of the patch pair is an FP64 hit, as in the triangle-level
 // separating-axis test.  The left side is computed as
 // fl(w . fl(c_X - c_Y)), within 5.001 u sum_i |w_i||fl(c_X - c_Y)_i| of the
@@ -524,7 +524,9 @@ __device__ __forceinline__ bool frames_separated(const PFrame &X, const PFrame &
     float dc[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) dc[i] = X.c[i] - Y.c[i];
-    const float reach = 1.03e-12f * (X.L + Y.L) + 1e-37f;
+    // fp64_reach with max|A| <= 2 (L_X + L_Y) and |r| <= L_X + L_Y; tw = 1 + 6 tau'
+    // bounds 1 + 2 tau'
+    const float reach = 1.03e-12f * tw * (X.L + Y.L) + 1e-37f;
     // p[m][k] = fl(e_m^X . e_k^Y) for X's normals; q[m][k] = fl(e_m^Y . e_k^X)
     // for Y's normals (its k = 2, 3 entries are p's)
     float p2[4], p3[4], q2[4], q3[4];
