@@ -16,10 +16,10 @@ namespace tms {
 // ---------------------------------------------------------------------------
 // tunables
 // ---------------------------------------------------------------------------
-constexpr int kRadixBits = 8;
+constexpr int kRadixBits = 9;            // five passes for the 44-bit hit keys of 4M-triangle meshes
 constexpr int kRadixBins = 1 << kRadixBits;
-constexpr int kSortBlock = 256;          // threads per radix block (8 warps)
-constexpr int kSortItems = 8;            // keys per thread per tile
+constexpr int kSortBlock = 512;          // threads per radix block (16 warps, one per digit)
+constexpr int kSortItems = 4;            // keys per thread per tile
 constexpr int kSortTile = kSortBlock * kSortItems;
 constexpr int kScanBlock = 512;
 constexpr int kCellBits = 31;            // a pair's grid has < 2^31 cells

@@ -2,10 +2,10 @@
 // exclusive scans, both with the element count read from device memory so that
 // a whole search can be captured in a CUDA graph without host round trips.
 //
-// Sort (one sweep per 8-bit digit):
+// Sort (one sweep per kRadixBits-bit digit):
 //   k_radix_hist   one read of the keys: the digit histograms of every pass,
 //                  and the look-back words of the tiles in use cleared;
-//   k_radix_bases  per pass, the exclusive scan of the 256 digit counts (the
+//   k_radix_bases  per pass, the exclusive scan of the digit counts (the
 //                  global start of every digit);
 //   k_radix_pass   per pass, persistent blocks take 2048-key tiles in order
 //                  from an atomic counter; a tile is ranked (warp match on the
@@ -39,8 +39,8 @@ constexpr uint64_t kFlagAgg = 1ull << 62;            // the tile's own count
 constexpr uint64_t kFlagInc = 2ull << 62;            // count of this and all earlier tiles
 constexpr uint64_t kCountMask = (1ull << 62) - 1;
 
-// scratch layout: hist[kMaxPasses][256] (u32), tile counters[kMaxPasses] (u32),
-// then per pass the look-back words of every tile, tiles x 256 (u64)
+// scratch layout: hist[kMaxPasses][kRadixBins] (u32), tile counters[kMaxPasses] (u32),
+// then per pass the look-back words of every tile, tiles x kRadixBins (u64)
 constexpr size_t kHistBytes = (size_t)kMaxPasses * kRadixBins * sizeof(uint32_t);
 constexpr size_t kHeadBytes = kHistBytes + 256;
 
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_hist(const uint64_t *keys,
     }
 }
 
-// per pass, exclusive scan of the 256 digit counts in place (one block of 256)
+// per pass, exclusive scan of the digit counts in place (one block, a thread a digit)
 __global__ void __launch_bounds__(kRadixBins) k_radix_bases(uint32_t *hist, int passes) {
     __shared__ uint32_t wsum[kRadixBins / 32];
     const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_pass(
     int unpublished) {
     static_assert(kSortBlock == kRadixBins, "one thread per digit");
     constexpr int NW = kSortBlock / 32;
-    __shared__ uint32_t wcnt[NW][kRadixBins];
+    __shared__ uint16_t wcnt[NW][kRadixBins];   // per-warp digit counts, then offsets (< kSortTile)
     __shared__ uint32_t t_excl[kRadixBins];     // start of each digit's run in the tile
     __shared__ uint32_t g_off[kRadixBins];      // global start of that run
     __shared__ uint32_t wsum[NW];
